@@ -1,0 +1,389 @@
+#!/usr/bin/env python3
+"""Benchmark of the social-field pedestrian step on GB300.
+
+Default workload: the 16384 x 16384 floor (10 % rectangular obstacles, 4 exits
+of 256 su, 10^6 pedestrians, influence radius 40) with the divide-and-conquer
+row bands engaged (HBM budget set so that the field is computed in >= 4
+bands).  One "step" is one tick of the whole path: bins, field gather,
+decision, vote, commit.
+
+Prints ONE JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle
+instead, on bounded samples of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
+FLOPS_PER_PAIR = 6.0  # three FP32 multiply-adds per (su, pedestrian-in-window) pair
+
+
+def workload(name: str):
+    import scenegen as SG
+    if name == "floor":
+        sc = SG.floor()
+        desc = "floor 16384x16384 su, 10% rectangular obstacles, 4 exits x 256 su, 1e6 peds, r=40"
+    elif name == "floor-small":
+        sc = SG.floor(side=4096, n=62500, exit_len=64)
+        desc = "floor 4096x4096 su, 10% rectangular obstacles, 4 exits x 64 su, 62500 peds, r=40"
+    elif name == "corridor":
+        sc = SG.corridor()
+        desc = "corridor 1000x200 su, periodic x, 20000 peds counter-flow, r=20"
+    elif name == "room":
+        sc = SG.room()
+        desc = "room 100x100 su, 1 exit x 10 su, 200 peds, r=10"
+    else:
+        raise ValueError(name)
+    return sc, desc
+
+
+def band_budget(sc, bands: int) -> int:
+    """HBM budget that leaves room for about H/bands field rows."""
+    if bands <= 1:
+        return 0
+    nsu = sc.W * sc.H
+    rows = -(-sc.H // bands)
+    rows = -(-rows // 32) * 32
+    return nsu * 14 + sc.W * 4 * (rows + 2) + 4096
+
+
+def pair_count(sc, xy, alive) -> int:
+    """(su, pedestrian-in-window) pairs of one field pass: the clipped window
+    area of every live pedestrian minus its own su."""
+    r = int(sc.params["r"])
+    m = alive.astype(bool)
+    x = xy[m, 0].astype(np.int64)
+    y = xy[m, 1].astype(np.int64)
+    if sc.periodic_x:
+        wx = np.full(x.shape, 2 * r + 1)
+    else:
+        wx = np.minimum(x + r, sc.W - 1) - np.maximum(x - r, 0) + 1
+    if sc.periodic_y:
+        wy = np.full(y.shape, 2 * r + 1)
+    else:
+        wy = np.minimum(y + r, sc.H - 1) - np.maximum(y - r, 0) + 1
+    return int((wx * wy - 1).sum())
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+    Q = ("index,uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid=None):
+        self.uuid = uuid
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            f = [c.strip() for c in line.split(",")]
+            if len(f) < 10:
+                continue
+            if self.uuid and self.uuid not in f[1]:
+                continue
+            rows.append(f)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        if not self.uuid:
+            idx = rows[0][0]
+            rows = [r for r in rows if r[0] == idx]
+        sm = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        mx = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[6 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows),
+                "power_w_max": max(float(r[4]) for r in rows if r[4].replace(".", "").isdigit())
+                if any(r[4].replace(".", "").isdigit() for r in rows) else None}
+
+
+def peaks():
+    try:
+        with open(MEASURED_PEAKS) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+# ------------------------------------------------------------------ oracle
+def oracle_sample(sc, D, xy, heading, goal, alive, n_sample, t, seed=0):
+    """Time the oracle's tick on a bounded sample: the decision of n_sample
+    random pedestrians (field evaluated at their 9 candidates, as the oracle's
+    tick does) scaled to all live pedestrians, plus the vote and commit of the
+    whole crowd.  Returns (estimated seconds per tick, threads)."""
+    import oracle as O
+    m = O.model(sc)
+    occ, _ = O.occupancy(m, sc.cell, xy, alive)
+    live = np.flatnonzero(alive)
+    rng = np.random.default_rng(seed + t)
+    req = np.sort(rng.choice(live, size=min(n_sample, live.size), replace=False)).astype(np.int32)
+    t0 = time.perf_counter()
+    ch, E, T, adm = O.decide(m, sc.cell, occ, xy, heading, goal, alive, D, req)
+    t1 = time.perf_counter()
+    choice = np.zeros(xy.shape[0], np.uint8)
+    choice[req] = ch
+    won, _ = O.vote(m, t, xy, alive, choice)
+    O.commit(m, sc.cell, xy, heading, alive, choice, won)
+    t2 = time.perf_counter()
+    per_tick = (t1 - t0) * (live.size / max(1, req.size)) + (t2 - t1)
+    return per_tick, O.threads(), req.size
+
+
+def run_reference(args):
+    """--impl reference: the FP64 oracle on the host cores, bounded samples."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle as O
+    O.build()
+    sc, desc = workload(args.workload)
+    m = O.model(sc)
+    D = O.guidance(m, sc.cell)
+    xy, heading, goal = sc.xy.copy(), sc.heading.copy(), sc.goal.copy()
+    alive = np.ones(sc.n, np.uint8)
+    n_sample = args.ref_sample
+    for w in range(args.warmup):
+        oracle_sample(sc, D, xy, heading, goal, alive, n_sample, w)
+    est = []
+    peds = []
+    for k in range(args.steps):
+        s, thr, ns = oracle_sample(sc, D, xy, heading, goal, alive, n_sample, args.warmup + k)
+        est.append(s)
+        peds.append(int(alive.sum()))
+    tot = sum(est)
+    value = sum(peds) / tot
+    line = {
+        "impl": "reference", "metric": "pedestrian-steps/s", "value": value,
+        "unit": "ped-steps/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": desc, "W": sc.W, "H": sc.H, "n": sc.n, "r": int(sc.params["r"])},
+        "cpu_baseline": {"value": value, "unit": "ped-steps/s", "cores": thr, "kind": "oracle",
+                         "sample": f"per tick: decision of {n_sample} random live pedestrians "
+                                   f"scaled to the live crowd, plus vote and commit of all"},
+        "e2e": {"value": value, "unit": "ped-steps/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ GPU arm
+def run_gpu(args):
+    import torch
+    import paper_1803_04782_gb300 as sfm
+    from paper_1803_04782_gb300 import build as B
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU (the CPU oracle arm is --impl reference)")
+    torch.cuda.set_device(local)
+    B.build()
+    sfm.lib()
+
+    sc, desc = workload(args.workload)
+    bands = args.bands
+    budget = band_budget(sc, bands)
+    stream = torch.cuda.current_stream()
+    sim = sfm.Sim(sc, stream=stream, hbm_budget_bytes=budget)
+    n = sc.n
+    st0 = sim.stats()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    # warm-up
+    sim.step(args.warmup)
+    sim.sync()
+    xy0, h0, a0 = sim.peds()
+    pairs0 = pair_count(sc, xy0, a0)
+    alive0 = int(a0.sum())
+    launches0 = sim.stats()["kernel_launches"]
+
+    # timed region: K ticks, stage events on the library's stream
+    sim.set_timing(True)
+    sim.stage_times()  # reset
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(local).uuid)
+    except Exception:
+        pass
+    clocks = Clocks(uuid)
+    clocks.start()
+    time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    sim.step(args.steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    elapsed = ev0.elapsed_time(ev1) / 1e3
+    stage_ms, ticks = sim.stage_times()
+    sim.set_timing(False)
+    st1 = sim.stats()
+    xy1, h1, a1 = sim.peds()
+    pairs1 = pair_count(sc, xy1, a1)
+    alive1 = int(a1.sum())
+    launches = st1["kernel_launches"] - launches0
+    ped_steps = 0.5 * (alive0 + alive1) * args.steps
+    if dist is not None:
+        t = torch.tensor([elapsed], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed = float(t.item())
+        p = torch.tensor([ped_steps], device="cuda", dtype=torch.float64)
+        dist.all_reduce(p)
+        ped_steps = float(p.item())
+
+    # roofline of the dominant kernel: the field gather
+    field_s = stage_ms["field"] / 1e3
+    pairs = 0.5 * (pairs0 + pairs1)
+    achieved = FLOPS_PER_PAIR * pairs * args.steps / field_s / 1e12
+    peak = SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "kernel": "k_field", "field_ms_per_step": 1e3 * field_s / args.steps,
+                "pairs_per_step": pairs,
+                "peak_basis": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz (max clock)"}
+
+    # end to end through the C ABI with host buffers
+    e2e_steps = min(args.steps, args.e2e_steps)
+    hx = torch.from_numpy(xy1.copy()).pin_memory()
+    hh = torch.from_numpy(h1.copy()).pin_memory()
+    hg = torch.from_numpy(sc.goal.copy()).pin_memory()
+    ha = torch.from_numpy(a1.copy()).pin_memory()
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    e2e_peds = 0
+    for _ in range(e2e_steps):
+        sfm.sfm_place(sim.ctx, hx, hh, hg, ha)
+        sfm.sfm_step(sim.ctx, 1)
+        sfm.sfm_read_peds(sim.ctx, hx, hh, ha)
+        e2e_peds += int(ha.numpy().sum())
+    torch.cuda.synchronize()
+    e2e_t = time.perf_counter() - t0
+    if dist is not None:
+        t = torch.tensor([e2e_t], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_t = float(t.item())
+        p = torch.tensor([float(e2e_peds)], device="cuda", dtype=torch.float64)
+        dist.all_reduce(p)
+        e2e_peds = float(p.item())
+    e2e = {"value": e2e_peds / e2e_t, "unit": "ped-steps/s",
+           "h2d_bytes_per_step": n * (8 + 1 + 1 + 1), "d2h_bytes_per_step": n * (8 + 1 + 1),
+           "steps": e2e_steps}
+
+    if rank != 0:
+        sim.close()
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
+
+    # CPU baseline: the oracle on a bounded sample of the same workload
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        import oracle as O
+        O.build()
+        m = O.model(sc)
+        D = O.guidance(m, sc.cell)
+        s, thr, ns = oracle_sample(sc, D, xy1.copy(), h1.copy(), sc.goal.copy(), a1.copy(),
+                                   args.ref_sample, 0)
+        cpu = {"value": alive1 / s, "unit": "ped-steps/s", "cores": thr, "kind": "oracle",
+               "sample": f"decision of {ns} random live pedestrians of this workload (field at "
+                         f"their 9 candidates), scaled to {alive1}, plus vote+commit of all"}
+    pk, pk_src = peaks()
+    line = {
+        "metric": "pedestrian-steps/s", "value": ped_steps / elapsed, "unit": "ped-steps/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": desc, "W": sc.W, "H": sc.H, "n": n, "r": int(sc.params["r"]),
+                   "bands": st1["bands"], "hbm_budget_bytes": budget,
+                   "l2": "inputs larger than L2 (the field alone is 4*W*H bytes)"
+                   if sc.W * sc.H * 4 > 129e6 else "inputs smaller than L2",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "su_updates_per_s": sc.W * sc.H * args.steps * world / elapsed,
+        "stage_ms_per_step": {k: v / max(1, ticks) for k, v in stage_ms.items()},
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "clocks": clk,
+        "gpu_launches": int(launches),
+        "peaks_source": pk_src,
+        "hbm_peak_gbs": pk.get("hbm_gbs"),
+    }
+    print(json.dumps(line), flush=True)
+    sim.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="floor",
+                    choices=["floor", "floor-small", "corridor", "room"])
+    ap.add_argument("--bands", type=int, default=4,
+                    help="row bands of the divide-and-conquer field pass (1 = unbanded)")
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--ref-sample", type=int, default=100000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)  # timing rule: at least 3 untimed warm-up ticks
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

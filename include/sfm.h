@@ -1,0 +1,197 @@
+/*
+ * sfm.h -- C ABI of the GB300 (sm_103a) implementation of the discrete social
+ * field pedestrian model of Yu, Zhu, Wu and Zhang, "Improved OpenCL-based
+ * Implementation of Social Field Pedestrian Model".
+ *
+ * One call of sfm_step() advances the simulation by ticks of the paper's
+ * Alg. 1: field superposition (sub-job k-5 of Sec. 3.1, here a per-su gather),
+ * each pedestrian's choice among its 9 candidate su (k-2), the election of
+ * one registrant per contested su (k-3, the enrollment container of Sec. 3.1
+ * item s-2) and the move commit (k-4).
+ *
+ * Model laws (the paper names the field kinds in Sec. 2 and leaves their
+ * formulas to its predecessors; the library implements this reading):
+ *   F(c) = sum_p K_P(c-x_p; h_p) + sum_{WALL o} K_O(c-o) + sum_{EXIT e} K_E(c-e)
+ *   K_P(d; h) = kP |d|^aP (1 + gamma (h.d)/|d|),  K_O = kO |d|^aO,  K_E = kE |d|^aE
+ *   each zero unless 0 < max(|dx|,|dy|) <= r (square (2r+1)^2 geometry; the
+ *   paper's "7x7" field is r = 3); minimum-image offsets in periodic dims.
+ *   E_p(k) = F(c_k) - [k>0] K_P(Delta_k; h_p) + guide_p(k); choice = argmin,
+ *   ties to the smallest k; guide = beta (D(c_k)-D(x_p))/5 for exit-seekers
+ *   (D = 5-7 chamfer geodesic distance to the nearest exit), or
+ *   -beta Delta_k . u_goal for pedestrians with a fixed desired direction.
+ *   Election priority: SplitMix64 output indexed by (seed, tick, id).
+ *
+ * Conventions for every entry point:
+ *   - Lattices are row-major, index y*W + x; x is the column.
+ *   - Direction classes 0..8: 0 stay, then (1,0) (1,1) (0,1) (-1,1) (-1,0)
+ *     (-1,-1) (0,-1) (1,-1).
+ *   - Host buffers passed in are owned by the caller and are copied before
+ *     the call returns (or, for device buffers, before the next call on the
+ *     context's stream).  Device memory of a context is allocated and owned
+ *     by the library and released by sfm_destroy.
+ *   - `on_device` flags say whether a pointer is device memory (1) or host
+ *     memory (0).  Host destinations of sfm_read_* are written synchronously.
+ *   - Every call returns an sfm_status; sfm_last_error() gives the message of
+ *     the last failure on that context (or of the last failed sfm_create when
+ *     given NULL).  Errors raised by kernels are reported by the next
+ *     synchronising call (sfm_sync, sfm_read_*, sfm_stats, sfm_place).
+ *   - A context is used from one host thread at a time; all work is issued on
+ *     the stream given to sfm_create (NULL = the legacy default stream).
+ */
+#ifndef SFM_H_
+#define SFM_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SFM_ABI_VERSION 1
+#define SFM_MAX_RADIUS 64
+#define SFM_NSTAGES 6
+
+typedef struct sfm_ctx sfm_ctx; /* opaque, library-owned */
+
+typedef enum sfm_status {
+  SFM_OK = 0,
+  SFM_EINVAL = 1,    /* bad argument (sizes, radius, classes, NULL pointer) */
+  SFM_ENOMEM = 2,    /* device allocation failed */
+  SFM_EBUDGET = 3,   /* the resident lattice arrays exceed hbm_budget_bytes */
+  SFM_ECUDA = 4,     /* a CUDA runtime call or a kernel failed */
+  SFM_ECONFLICT = 5, /* placement overlaps, sits on a WALL/EXIT su or off-lattice */
+  SFM_ETIMEOUT = 6,  /* a bounded device-side wait gave up */
+  SFM_ESTATE = 7     /* call out of order (e.g. step before place) */
+} sfm_status;
+
+/* Lattice geometry. periodic_x / periodic_y wrap that dimension (the paper's
+ * experiments use periodic boundaries, Sec. 5); a periodic extent must be at
+ * least 2r+1 so that one image at most lies inside a window. */
+typedef struct sfm_lattice {
+  int32_t W, H;
+  int32_t periodic_x, periodic_y;
+} sfm_lattice;
+
+/* Model parameters.  r in [0, SFM_MAX_RADIUS].  seed feeds the election hash.
+ * hbm_budget_bytes: 0 = unlimited; otherwise the field is computed in row
+ * bands whose buffers fit the budget left after the resident arrays (the
+ * divide-and-conquer split of Sec. 3.3, Eq. 1).  bin: side of the square
+ * pedestrian bins used by the gather (0 = library default). */
+typedef struct sfm_params {
+  int32_t r;
+  int32_t bin;
+  float kP, aP, gamma;
+  float kO, aO;
+  float kE, aE;
+  float beta;
+  uint64_t seed;
+  uint64_t hbm_budget_bytes;
+} sfm_params;
+
+typedef struct sfm_stats_t {
+  int64_t t;               /* ticks simulated since creation (or sfm_set_time) */
+  int64_t n;               /* pedestrians placed */
+  int64_t alive;           /* still on the lattice */
+  int64_t exited;          /* left through exits */
+  int64_t moved_total;     /* committed moves since placement */
+  int32_t max_registrants; /* largest enrollment seen in a vote (<= 8) */
+  int32_t bands;           /* row bands per field pass (1 = unblocked) */
+  uint32_t error_flags;    /* device-side invariant violations (0 = none) */
+  int32_t pad_;
+  int64_t device_bytes;    /* device memory held by the context */
+  int64_t kernel_launches; /* kernels this context has launched since creation */
+} sfm_stats_t;
+
+/* Stage indices for sfm_stage_times. */
+enum {
+  SFM_STAGE_BIN = 0,    /* S1: counting sort of pedestrians into bins */
+  SFM_STAGE_FIELD = 1,  /* S2: field gather (k-5 in the paper) */
+  SFM_STAGE_DECIDE = 2, /* S3: 9-candidate decision (k-2) */
+  SFM_STAGE_VOTE = 3,   /* S4: election (k-3) */
+  SFM_STAGE_COMMIT = 4, /* S5: commit (k-4) */
+  SFM_STAGE_STEP = 5    /* whole tick */
+};
+
+/* ABI version compiled into the library. */
+int32_t sfm_abi_version(void);
+
+/* Create a context for one lattice.  cell: W*H bytes, 0 FREE, 1 WALL,
+ * 2 EXIT (host or device per cell_on_device).  Computes the kernel tables,
+ * the static field of WALL and EXIT su and the guidance distances on the
+ * device (once per scene).  stream: a cudaStream_t or NULL.  On failure *out
+ * is NULL and sfm_last_error(NULL) describes the error.
+ * Errors: SFM_EINVAL, SFM_ENOMEM, SFM_EBUDGET, SFM_ECUDA. */
+sfm_status sfm_create(const sfm_lattice* lat, const uint8_t* cell, int32_t cell_on_device,
+                      const sfm_params* prm, void* stream, sfm_ctx** out);
+
+/* Release every device buffer of the context (synchronises its stream). */
+void sfm_destroy(sfm_ctx* ctx);
+
+/* Message of the last failure on ctx (ctx == NULL: last failed sfm_create
+ * on this thread).  Never NULL; valid until the next call on ctx. */
+const char* sfm_last_error(const sfm_ctx* ctx);
+
+/* (Re)place n pedestrians, replacing any previous set (the step counter is
+ * kept).  xy: n pairs (x, y) int32; heading: n classes 0..8 (NULL = 0);
+ * goal: n classes, 0 = exit-seeker, 1..8 = fixed desired direction (NULL = 0);
+ * alive: n flags (NULL = all alive).  Validates on the device and returns
+ * SFM_ECONFLICT if two live pedestrians share a su or one sits on a WALL or
+ * EXIT su or off-lattice.  Synchronising. */
+sfm_status sfm_place(sfm_ctx* ctx, int32_t n, const int32_t* xy, const uint8_t* heading,
+                     const uint8_t* goal, const uint8_t* alive, int32_t on_device);
+
+/* Set the tick counter used by the election hash. */
+sfm_status sfm_set_time(sfm_ctx* ctx, int64_t t);
+
+/* Advance nsteps ticks (asynchronous on the context's stream). */
+sfm_status sfm_step(sfm_ctx* ctx, int32_t nsteps);
+
+/* Compute the field of the current state into the field buffer without
+ * moving anybody (bins + gather only).  Asynchronous. */
+sfm_status sfm_compute_field(sfm_ctx* ctx);
+
+/* Wait for the context's stream and report device-side errors. */
+sfm_status sfm_sync(sfm_ctx* ctx);
+
+/* W*H floats: the field at the start of the last tick (or of the last
+ * sfm_compute_field).  SFM_ESTATE in banded mode, where no full-lattice field
+ * is resident: use sfm_compute_field_into instead. */
+sfm_status sfm_read_field(sfm_ctx* ctx, float* dst, int32_t on_device);
+
+/* Compute the field of the current state band by band straight into dst
+ * (W*H floats, host or device); works in every mode. */
+sfm_status sfm_compute_field_into(sfm_ctx* ctx, float* dst, int32_t on_device);
+
+/* W*H floats: the static field of WALL and EXIT su. */
+sfm_status sfm_read_static_field(sfm_ctx* ctx, float* dst, int32_t on_device);
+
+/* W*H int32: chamfer guidance distances (5 per straight step, 7 per diagonal
+ * step; 1<<23 where no exit is reachable or on WALL su). */
+sfm_status sfm_read_guidance(sfm_ctx* ctx, int32_t* dst, int32_t on_device);
+
+/* Pedestrian state: xy (n pairs), heading classes, alive flags (each may be
+ * NULL to skip). */
+sfm_status sfm_read_peds(sfm_ctx* ctx, int32_t* xy, uint8_t* heading, uint8_t* alive,
+                         int32_t on_device);
+
+/* Decisions of the last tick: choice class (0..8) and election result
+ * (1 = moved) per pedestrian (each may be NULL). */
+sfm_status sfm_read_decisions(sfm_ctx* ctx, uint8_t* choice, uint8_t* won, int32_t on_device);
+
+/* Counters (synchronising). */
+sfm_status sfm_stats(sfm_ctx* ctx, sfm_stats_t* out);
+
+/* Per-stage timing: when enabled, sfm_step launches stage by stage and
+ * records CUDA events around each stage on the context's stream. */
+sfm_status sfm_set_timing(sfm_ctx* ctx, int32_t enable);
+
+/* Accumulated milliseconds per stage (SFM_NSTAGES doubles) and the number
+ * of ticks they cover since the last call; resets the accumulators.
+ * Synchronising. */
+sfm_status sfm_stage_times(sfm_ctx* ctx, double* ms, int64_t* ticks);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SFM_H_ */

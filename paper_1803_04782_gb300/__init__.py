@@ -1,0 +1,343 @@
+"""Python binding of libsfm (include/sfm.h): argument marshalling only.
+
+Every entry point of the C ABI is exposed under the same name (``sfm_create``,
+``sfm_place``, ``sfm_step``, ...); arrays may be NumPy arrays (host memory) or
+torch tensors (host or CUDA memory; the device pointer is passed through).
+All computation happens in the CUDA kernels of ``csrc/``; if the shared
+library is missing this module raises instead of falling back to anything.
+
+``Sim`` is a small convenience wrapper around one context.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_build", "libsfm.so")
+_lib = None
+
+SFM_OK, SFM_EINVAL, SFM_ENOMEM, SFM_EBUDGET, SFM_ECUDA, SFM_ECONFLICT, SFM_ETIMEOUT, SFM_ESTATE = range(8)
+STATUS_NAMES = ["SFM_OK", "SFM_EINVAL", "SFM_ENOMEM", "SFM_EBUDGET", "SFM_ECUDA",
+                "SFM_ECONFLICT", "SFM_ETIMEOUT", "SFM_ESTATE"]
+SFM_MAX_RADIUS = 64
+SFM_NSTAGES = 6
+STAGES = ["bin", "field", "decide", "vote", "commit", "step"]
+
+# Exported symbols (kept in step with include/sfm.h; checked by the tests).
+EXPORTS = [
+    "sfm_abi_version", "sfm_create", "sfm_destroy", "sfm_last_error", "sfm_place",
+    "sfm_set_time", "sfm_step", "sfm_compute_field", "sfm_sync", "sfm_read_field",
+    "sfm_compute_field_into", "sfm_read_static_field", "sfm_read_guidance", "sfm_read_peds",
+    "sfm_read_decisions", "sfm_stats", "sfm_set_timing", "sfm_stage_times",
+]
+
+
+class SfmError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < 8 else status}: {msg}")
+        self.status = status
+
+
+class Lattice(C.Structure):
+    _fields_ = [("W", C.c_int32), ("H", C.c_int32), ("periodic_x", C.c_int32),
+                ("periodic_y", C.c_int32)]
+
+
+class Params(C.Structure):
+    _fields_ = [("r", C.c_int32), ("bin", C.c_int32), ("kP", C.c_float), ("aP", C.c_float),
+                ("gamma", C.c_float), ("kO", C.c_float), ("aO", C.c_float), ("kE", C.c_float),
+                ("aE", C.c_float), ("beta", C.c_float), ("seed", C.c_uint64),
+                ("hbm_budget_bytes", C.c_uint64)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("t", C.c_int64), ("n", C.c_int64), ("alive", C.c_int64), ("exited", C.c_int64),
+                ("moved_total", C.c_int64), ("max_registrants", C.c_int32),
+                ("bands", C.c_int32), ("error_flags", C.c_uint32), ("pad_", C.c_int32),
+                ("device_bytes", C.c_int64), ("kernel_launches", C.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad_"}
+
+
+def lib():
+    """Load the CUDA library (fails loudly when it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with "
+                              "paper_1803_04782_gb300.build.build() (needs nvcc)")
+        L = C.CDLL(LIB_PATH)
+        P, I32, I64 = C.c_void_p, C.c_int32, C.c_int64
+        sig = {
+            "sfm_abi_version": (I32, []),
+            "sfm_create": (C.c_int, [C.POINTER(Lattice), P, I32, C.POINTER(Params), P,
+                                     C.POINTER(C.c_void_p)]),
+            "sfm_destroy": (None, [P]),
+            "sfm_last_error": (C.c_char_p, [P]),
+            "sfm_place": (C.c_int, [P, I32, P, P, P, P, I32]),
+            "sfm_set_time": (C.c_int, [P, I64]),
+            "sfm_step": (C.c_int, [P, I32]),
+            "sfm_compute_field": (C.c_int, [P]),
+            "sfm_sync": (C.c_int, [P]),
+            "sfm_read_field": (C.c_int, [P, P, I32]),
+            "sfm_compute_field_into": (C.c_int, [P, P, I32]),
+            "sfm_read_static_field": (C.c_int, [P, P, I32]),
+            "sfm_read_guidance": (C.c_int, [P, P, I32]),
+            "sfm_read_peds": (C.c_int, [P, P, P, P, I32]),
+            "sfm_read_decisions": (C.c_int, [P, P, P, I32]),
+            "sfm_stats": (C.c_int, [P, C.POINTER(Stats)]),
+            "sfm_set_timing": (C.c_int, [P, I32]),
+            "sfm_stage_times": (C.c_int, [P, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _ptr(a):
+    """(pointer, on_device) of a NumPy array or torch tensor (None -> NULL)."""
+    if a is None:
+        return None, 0
+    if isinstance(a, np.ndarray):
+        if not a.flags.c_contiguous:
+            raise ValueError("arrays must be C-contiguous")
+        return a.ctypes.data_as(C.c_void_p), 0
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensors must be contiguous")
+        return C.c_void_p(a.data_ptr()), 1 if a.is_cuda else 0
+    raise TypeError(type(a))
+
+
+def _check(ctx, status):
+    if status != SFM_OK:
+        msg = lib().sfm_last_error(ctx)
+        raise SfmError(status, msg.decode() if msg else "")
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return C.c_void_p(stream.cuda_stream)
+    return C.c_void_p(int(stream))
+
+
+# ---------------------------------------------------------------- C-ABI names
+def sfm_abi_version() -> int:
+    return lib().sfm_abi_version()
+
+
+def sfm_create(lat: Lattice, cell, prm: Params, stream=None):
+    p, dev = _ptr(cell)
+    out = C.c_void_p()
+    st = lib().sfm_create(C.byref(lat), p, dev, C.byref(prm), _stream_handle(stream),
+                          C.byref(out))
+    if st != SFM_OK:
+        msg = lib().sfm_last_error(None)
+        raise SfmError(st, msg.decode() if msg else "")
+    return out
+
+
+def sfm_destroy(ctx) -> None:
+    lib().sfm_destroy(ctx)
+
+
+def sfm_last_error(ctx) -> str:
+    m = lib().sfm_last_error(ctx)
+    return m.decode() if m else ""
+
+
+def sfm_place(ctx, xy, heading=None, goal=None, alive=None) -> None:
+    n = int(xy.shape[0])
+    pxy, dev = _ptr(xy)
+    ph, _ = _ptr(heading)
+    pg, _ = _ptr(goal)
+    pa, _ = _ptr(alive)
+    _check(ctx, lib().sfm_place(ctx, n, pxy, ph, pg, pa, dev))
+
+
+def sfm_set_time(ctx, t: int) -> None:
+    _check(ctx, lib().sfm_set_time(ctx, int(t)))
+
+
+def sfm_step(ctx, nsteps: int = 1) -> None:
+    _check(ctx, lib().sfm_step(ctx, int(nsteps)))
+
+
+def sfm_compute_field(ctx) -> None:
+    _check(ctx, lib().sfm_compute_field(ctx))
+
+
+def sfm_sync(ctx) -> None:
+    _check(ctx, lib().sfm_sync(ctx))
+
+
+def sfm_read_field(ctx, dst) -> None:
+    p, dev = _ptr(dst)
+    _check(ctx, lib().sfm_read_field(ctx, p, dev))
+
+
+def sfm_compute_field_into(ctx, dst) -> None:
+    p, dev = _ptr(dst)
+    _check(ctx, lib().sfm_compute_field_into(ctx, p, dev))
+
+
+def sfm_read_static_field(ctx, dst) -> None:
+    p, dev = _ptr(dst)
+    _check(ctx, lib().sfm_read_static_field(ctx, p, dev))
+
+
+def sfm_read_guidance(ctx, dst) -> None:
+    p, dev = _ptr(dst)
+    _check(ctx, lib().sfm_read_guidance(ctx, p, dev))
+
+
+def sfm_read_peds(ctx, xy=None, heading=None, alive=None) -> None:
+    devs = [_ptr(a) for a in (xy, heading, alive)]
+    on_dev = max(d for _, d in devs)
+    _check(ctx, lib().sfm_read_peds(ctx, devs[0][0], devs[1][0], devs[2][0], on_dev))
+
+
+def sfm_read_decisions(ctx, choice=None, won=None) -> None:
+    devs = [_ptr(a) for a in (choice, won)]
+    on_dev = max(d for _, d in devs)
+    _check(ctx, lib().sfm_read_decisions(ctx, devs[0][0], devs[1][0], on_dev))
+
+
+def sfm_stats(ctx) -> dict:
+    s = Stats()
+    _check(ctx, lib().sfm_stats(ctx, C.byref(s)))
+    return s.as_dict()
+
+
+def sfm_set_timing(ctx, enable: bool) -> None:
+    _check(ctx, lib().sfm_set_timing(ctx, 1 if enable else 0))
+
+
+def sfm_stage_times(ctx):
+    ms = (C.c_double * SFM_NSTAGES)()
+    ticks = C.c_int64()
+    _check(ctx, lib().sfm_stage_times(ctx, ms, C.byref(ticks)))
+    return dict(zip(STAGES, list(ms))), int(ticks.value)
+
+
+# ------------------------------------------------------------------ wrapper
+def make_params(r=3, kP=1.0, aP=-0.5, gamma=0.5, kO=1.0, aO=-0.5, kE=-1.0, aE=-0.5, beta=1.0,
+                seed=0, hbm_budget_bytes=0, bin=0) -> Params:
+    return Params(int(r), int(bin), kP, aP, gamma, kO, aO, kE, aE, beta, int(seed) & (2**64 - 1),
+                  int(hbm_budget_bytes))
+
+
+class Sim:
+    """One simulation context.  ``scene`` is any object with W, H, periodic_x,
+    periodic_y, cell, xy, heading, goal and params attributes (for example a
+    ``scenegen.Scene``); keyword arguments override its parameters."""
+
+    def __init__(self, scene=None, *, W=None, H=None, cell=None, periodic_x=0, periodic_y=0,
+                 stream=None, place=True, **params):
+        if scene is not None:
+            W, H, cell = scene.W, scene.H, scene.cell
+            periodic_x, periodic_y = scene.periodic_x, scene.periodic_y
+            p = {k: v for k, v in scene.params.items()}
+            p.update(params)
+        else:
+            p = dict(params)
+        self.W, self.H = int(W), int(H)
+        self.lat = Lattice(self.W, self.H, int(periodic_x), int(periodic_y))
+        self.prm = make_params(**p)
+        cell = np.ascontiguousarray(cell, np.uint8) if isinstance(cell, np.ndarray) else cell
+        self.ctx = sfm_create(self.lat, cell, self.prm, stream)
+        self.n = 0
+        if scene is not None and place:
+            self.place(scene.xy, scene.heading, scene.goal)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            sfm_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # state
+    def place(self, xy, heading=None, goal=None, alive=None):
+        if isinstance(xy, np.ndarray):
+            xy = np.ascontiguousarray(xy, np.int32)
+            heading = None if heading is None else np.ascontiguousarray(heading, np.uint8)
+            goal = None if goal is None else np.ascontiguousarray(goal, np.uint8)
+            alive = None if alive is None else np.ascontiguousarray(alive, np.uint8)
+        sfm_place(self.ctx, xy, heading, goal, alive)
+        self.n = int(xy.shape[0])
+
+    def set_time(self, t):
+        sfm_set_time(self.ctx, t)
+
+    def step(self, n=1):
+        sfm_step(self.ctx, n)
+
+    def sync(self):
+        sfm_sync(self.ctx)
+
+    def compute_field(self):
+        sfm_compute_field(self.ctx)
+
+    # reads (host NumPy)
+    def field(self):
+        out = np.empty((self.H, self.W), np.float32)
+        sfm_read_field(self.ctx, out)
+        return out
+
+    def field_banded(self):
+        out = np.empty((self.H, self.W), np.float32)
+        sfm_compute_field_into(self.ctx, out)
+        return out
+
+    def static_field(self):
+        out = np.empty((self.H, self.W), np.float32)
+        sfm_read_static_field(self.ctx, out)
+        return out
+
+    def guidance(self):
+        out = np.empty((self.H, self.W), np.int32)
+        sfm_read_guidance(self.ctx, out)
+        return out
+
+    def peds(self):
+        xy = np.empty((self.n, 2), np.int32)
+        h = np.empty(self.n, np.uint8)
+        a = np.empty(self.n, np.uint8)
+        sfm_read_peds(self.ctx, xy, h, a)
+        return xy, h, a
+
+    def decisions(self):
+        ch = np.empty(self.n, np.uint8)
+        won = np.empty(self.n, np.uint8)
+        sfm_read_decisions(self.ctx, ch, won)
+        return ch, won
+
+    def stats(self):
+        return sfm_stats(self.ctx)
+
+    def set_timing(self, on=True):
+        sfm_set_timing(self.ctx, on)
+
+    def stage_times(self):
+        return sfm_stage_times(self.ctx)

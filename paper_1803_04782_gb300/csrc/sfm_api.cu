@@ -1,0 +1,656 @@
+// sfm_api.cu -- C ABI (include/sfm.h): context lifetime, validation, device
+// memory, and the per-tick launch sequence of Alg. 1 (bins, field gather,
+// decision, vote, commit), with the banded divide-and-conquer mode of Sec. 3.3.
+#include <cuda_runtime.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "sfm_internal.h"
+
+using namespace sfm;
+
+struct sfm_ctx {
+  sfm_lattice lat{};
+  sfm_params prm{};
+  cudaStream_t stream = nullptr;
+  Geo geo{};
+  std::string err;
+  int64_t device_bytes = 0;
+  int64_t launches = 0;  // kernels launched by this context
+  std::vector<void*> allocs;
+
+  // lattice arrays
+  uint8_t* cell = nullptr;
+  float* Fs = nullptr;
+  float* F = nullptr;  // full-lattice field (unbanded mode only)
+  int32_t* D = nullptr;
+  int32_t* occ = nullptr;
+  uint8_t* ocls = nullptr;
+  // tables
+  float *T0 = nullptr, *TX = nullptr, *TY = nullptr, *KO = nullptr, *KE = nullptr;
+  float *own = nullptr, *dirdot = nullptr;
+  float2* hvec = nullptr;
+  // bins
+  int32_t *bin_count = nullptr, *bin_start = nullptr, *scan_tmp = nullptr;
+  uint32_t* rec = nullptr;
+  Counters* ctr = nullptr;
+  // pedestrians
+  int n = 0, cap = 0;
+  int2* xy = nullptr;
+  uint8_t *heading = nullptr, *goal = nullptr, *alive = nullptr, *choice = nullptr, *won = nullptr;
+  bool placed = false;
+  int64_t t = 0;
+  // banded mode
+  int bands = 1;
+  int band_rows = 0;  // lattice rows per band (multiple of the tile height)
+  float* band_buf = nullptr;
+  // timing
+  bool timing = false;
+  struct Rec {
+    int stage;
+    cudaEvent_t a, b;
+  };
+  std::vector<Rec> recs;
+  std::vector<cudaEvent_t> pool;
+  int64_t timed_ticks = 0;
+
+  Tables tables() const {
+    Tables tb;
+    tb.T0 = T0;
+    tb.TX = TX;
+    tb.TY = TY;
+    tb.KO = KO;
+    tb.KE = KE;
+    tb.own = own;
+    tb.dirdot = dirdot;
+    tb.hvec = hvec;
+    return tb;
+  }
+};
+
+namespace {
+
+thread_local std::string g_create_err;
+
+sfm_status fail(sfm_ctx* c, sfm_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  if (c)
+    c->err = buf;
+  else
+    g_create_err = buf;
+  return st;
+}
+
+#define CU(call)                                                                        \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess)                                                              \
+      return fail(ctx, e_ == cudaErrorMemoryAllocation ? SFM_ENOMEM : SFM_ECUDA, "%s: %s", \
+                  #call, cudaGetErrorString(e_));                                        \
+  } while (0)
+
+template <class T>
+sfm_status dalloc(sfm_ctx* ctx, T** p, size_t count) {
+  void* q = nullptr;
+  const size_t bytes = count * sizeof(T) > 0 ? count * sizeof(T) : 16;
+  cudaError_t e = cudaMalloc(&q, bytes);
+  if (e != cudaSuccess)
+    return fail(ctx, SFM_ENOMEM, "cudaMalloc(%zu bytes): %s", bytes, cudaGetErrorString(e));
+  ctx->allocs.push_back(q);
+  ctx->device_bytes += (int64_t)bytes;
+  *p = static_cast<T*>(q);
+  return SFM_OK;
+}
+
+void dfree(sfm_ctx* ctx, void* p) {
+  if (!p) return;
+  for (size_t i = 0; i < ctx->allocs.size(); ++i)
+    if (ctx->allocs[i] == p) {
+      ctx->allocs.erase(ctx->allocs.begin() + (long)i);
+      break;
+    }
+  cudaFree(p);
+}
+
+#define TRY(x)                     \
+  do {                             \
+    sfm_status s_ = (x);           \
+    if (s_ != SFM_OK) return s_;   \
+  } while (0)
+
+cudaEvent_t pool_get(sfm_ctx* c) {
+  if (!c->pool.empty()) {
+    cudaEvent_t e = c->pool.back();
+    c->pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e;
+  cudaEventCreate(&e);
+  return e;
+}
+
+struct StageScope {
+  sfm_ctx* c;
+  int stage;
+  cudaEvent_t a = nullptr;
+  StageScope(sfm_ctx* c_, int s_) : c(c_), stage(s_) {
+    if (c->timing) {
+      a = pool_get(c);
+      cudaEventRecord(a, c->stream);
+    }
+  }
+  ~StageScope() {
+    if (c->timing) {
+      cudaEvent_t b = pool_get(c);
+      cudaEventRecord(b, c->stream);
+      c->recs.push_back({stage, a, b});
+    }
+  }
+};
+
+sfm_status check_flags(sfm_ctx* ctx) {
+  CU(cudaStreamSynchronize(ctx->stream));
+  Counters h;
+  CU(cudaMemcpy(&h, ctx->ctr, sizeof(h), cudaMemcpyDeviceToHost));
+  if (h.err & kErrTimeout) return fail(ctx, SFM_ETIMEOUT, "a bounded device wait gave up");
+  if (h.err) return fail(ctx, SFM_ECUDA, "device error flags 0x%x", h.err);
+  return SFM_OK;
+}
+
+// Field of the current pedestrian state for lattice rows [ya, yb) stored in
+// out with row ya at out row `main_off`; optionally the single halo rows
+// ya-1 and yb (wrapped in periodic y) at out rows 0 and yb-ya+1.  Uses whole
+// tiles so every su is summed in the same order in every mode.
+void field_rows(sfm_ctx* c, float* out, int ya, int yb, int main_off, bool halos) {
+  const Geo& g = c->geo;
+  const Tables tb = c->tables();
+  const int ty0 = ya / kTile, ty1 = (yb + kTile - 1) / kTile;
+  launch_field(g, c->bin_start, c->rec, tb, c->Fs, out, ya - main_off, ty0, ty1, ya, yb,
+               c->ctr, c->stream);
+  ++c->launches;
+  if (!halos) return;
+  int lo = ya - 1, hi = yb;
+  bool has_lo = lo >= 0 || g.py, has_hi = hi < g.H || g.py;
+  if (lo < 0) lo += g.H;
+  if (hi >= g.H) hi -= g.H;
+  if (has_lo) {
+    // store lattice row `lo` at out row 0
+    launch_field(g, c->bin_start, c->rec, tb, c->Fs, out, lo, lo / kTile, lo / kTile + 1, lo,
+                 lo + 1, c->ctr, c->stream);
+    ++c->launches;
+  }
+  if (has_hi) {
+    launch_field(g, c->bin_start, c->rec, tb, c->Fs, out, hi - (yb - ya + 1), hi / kTile,
+                 hi / kTile + 1, hi, hi + 1, c->ctr, c->stream);
+    ++c->launches;
+  }
+}
+
+void run_bins(sfm_ctx* c) {
+  StageScope sc(c, SFM_STAGE_BIN);
+  const Geo& g = c->geo;
+  launch_bin_count(g, c->ocls, c->bin_count, c->stream);
+  launch_scan(c->bin_count, c->bin_start, g.nbx * g.nby, c->scan_tmp, c->stream);
+  launch_bin_fill(g, c->ocls, c->bin_start, c->rec, c->stream);
+  c->launches += 5;  // count, three scan passes, fill
+}
+
+void run_tick(sfm_ctx* c) {
+  StageScope whole(c, SFM_STAGE_STEP);
+  const Geo& g = c->geo;
+  const Tables tb = c->tables();
+  run_bins(c);
+  if (c->bands <= 1) {
+    {
+      StageScope sc(c, SFM_STAGE_FIELD);
+      field_rows(c, c->F, 0, g.H, 0, false);
+    }
+    StageScope sc(c, SFM_STAGE_DECIDE);
+    launch_decide(c->n, c->xy, c->alive, c->heading, c->goal, c->cell, c->occ, c->D, c->F, 0, -1,
+                  -1, 0, 0, g.H, g, c->prm.beta, tb, c->choice, c->stream);
+    if (c->n > 0) ++c->launches;
+  } else {
+    for (int b = 0; b < c->bands; ++b) {
+      const int ya = b * c->band_rows;
+      const int yb = ya + c->band_rows < g.H ? ya + c->band_rows : g.H;
+      {
+        StageScope sc(c, SFM_STAGE_FIELD);
+        field_rows(c, c->band_buf, ya, yb, 1, true);
+      }
+      int lo = ya - 1, hi = yb;
+      if (lo < 0) lo = g.py ? lo + g.H : -1;
+      if (hi >= g.H) hi = g.py ? hi - g.H : -1;
+      StageScope sc(c, SFM_STAGE_DECIDE);
+      launch_decide(c->n, c->xy, c->alive, c->heading, c->goal, c->cell, c->occ, c->D,
+                    c->band_buf, 1, lo, hi, yb - ya + 1, ya, yb, g, c->prm.beta, tb,
+                    c->choice, c->stream);
+      if (c->n > 0) ++c->launches;
+    }
+  }
+  {
+    StageScope sc(c, SFM_STAGE_VOTE);
+    launch_vote(c->n, c->xy, c->alive, c->choice, c->occ, g, c->prm.seed, c->ctr, c->won,
+                c->stream);
+    if (c->n > 0) ++c->launches;
+  }
+  StageScope sc(c, SFM_STAGE_COMMIT);
+  launch_commit(c->n, c->xy, c->alive, c->heading, c->choice, c->won, c->cell, c->occ, c->ocls,
+                g, c->ctr, c->stream);
+  ++c->launches;
+}
+
+sfm_status copy_out(sfm_ctx* ctx, void* dst, const void* src, size_t bytes, int on_device) {
+  CU(cudaMemcpyAsync(dst, src, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                     ctx->stream));
+  return check_flags(ctx);
+}
+
+}  // namespace
+
+extern "C" {
+
+int32_t sfm_abi_version(void) { return SFM_ABI_VERSION; }
+
+const char* sfm_last_error(const sfm_ctx* ctx) {
+  return ctx ? ctx->err.c_str() : g_create_err.c_str();
+}
+
+sfm_status sfm_create(const sfm_lattice* lat, const uint8_t* cell, int32_t cell_on_device,
+                      const sfm_params* prm, void* stream, sfm_ctx** out) {
+  if (out) *out = nullptr;
+  if (!lat || !cell || !prm || !out) return fail(nullptr, SFM_EINVAL, "NULL argument");
+  if (lat->W < 3 || lat->H < 3) return fail(nullptr, SFM_EINVAL, "lattice must be >= 3x3");
+  if ((int64_t)lat->W * lat->H > (int64_t)1 << 31)
+    return fail(nullptr, SFM_EINVAL, "lattice larger than 2^31 su");
+  if (prm->r < 0 || prm->r > SFM_MAX_RADIUS)
+    return fail(nullptr, SFM_EINVAL, "radius %d outside [0, %d]", prm->r, SFM_MAX_RADIUS);
+  if ((lat->periodic_x && lat->W < 2 * prm->r + 1) || (lat->periodic_y && lat->H < 2 * prm->r + 1))
+    return fail(nullptr, SFM_EINVAL, "a periodic extent must be >= 2r+1");
+  if (prm->bin != 0 && prm->bin != kBin)
+    return fail(nullptr, SFM_EINVAL, "bin side must be 0 or %d", kBin);
+
+  sfm_ctx* ctx = new sfm_ctx;
+  ctx->lat = *lat;
+  ctx->prm = *prm;
+  ctx->prm.bin = kBin;
+  ctx->stream = static_cast<cudaStream_t>(stream);
+  Geo& g = ctx->geo;
+  g.W = lat->W;
+  g.H = lat->H;
+  g.px = lat->periodic_x ? 1 : 0;
+  g.py = lat->periodic_y ? 1 : 0;
+  g.r = prm->r;
+  g.nbx = (g.W + kBin - 1) / kBin;
+  g.nby = (g.H + kBin - 1) / kBin;
+  const size_t nsu = (size_t)g.W * g.H;
+  const int nbins = g.nbx * g.nby;
+  const int S = 2 * g.r + 1;
+
+  auto bail = [&](sfm_status st) {
+    g_create_err = ctx->err;
+    sfm_destroy(ctx);
+    return st;
+  };
+  // resident lattice arrays: cell, static field, guidance, occupancy, class grid
+  const uint64_t resident = (uint64_t)nsu * (1 + 4 + 4 + 4 + 1);
+  const uint64_t budget = prm->hbm_budget_bytes;
+  if (budget && resident + (uint64_t)nsu * 4 > budget) {
+    // banded: rows per band from what the budget leaves for the band buffer
+    if (resident >= budget) {
+      fail(ctx, SFM_EBUDGET, "resident arrays need %llu bytes > budget %llu",
+           (unsigned long long)resident, (unsigned long long)budget);
+      return bail(SFM_EBUDGET);
+    }
+    int64_t rows = (int64_t)((budget - resident) / ((uint64_t)g.W * 4)) - 2;
+    rows = rows / kTile * kTile;
+    if (rows < kTile) {
+      fail(ctx, SFM_EBUDGET, "budget leaves room for fewer than %d field rows", kTile);
+      return bail(SFM_EBUDGET);
+    }
+    ctx->band_rows = (int)rows;
+    ctx->bands = (int)((g.H + rows - 1) / rows);
+  }
+  sfm_status st;
+#define ALLOC(p, n)                              \
+  if ((st = dalloc(ctx, &(p), (n))) != SFM_OK) \
+    return bail(st);
+  ALLOC(ctx->cell, nsu);
+  ALLOC(ctx->Fs, nsu);
+  ALLOC(ctx->D, nsu);
+  ALLOC(ctx->occ, nsu);
+  ALLOC(ctx->ocls, nsu);
+  if (ctx->bands <= 1) {
+    ALLOC(ctx->F, nsu);
+  } else {
+    ALLOC(ctx->band_buf, (size_t)(ctx->band_rows + 2) * g.W);
+  }
+  ALLOC(ctx->T0, (size_t)S * S);
+  ALLOC(ctx->TX, (size_t)S * S);
+  ALLOC(ctx->TY, (size_t)S * S);
+  ALLOC(ctx->KO, (size_t)S * S);
+  ALLOC(ctx->KE, (size_t)S * S);
+  ALLOC(ctx->own, 81);
+  ALLOC(ctx->dirdot, 81);
+  ALLOC(ctx->hvec, 9);
+  ALLOC(ctx->bin_count, (size_t)nbins);
+  ALLOC(ctx->bin_start, (size_t)nbins + 1);
+  ALLOC(ctx->scan_tmp, (size_t)scan_tmp_elems(nbins));
+  ALLOC(ctx->ctr, 1);
+#undef ALLOC
+
+  cudaStream_t s = ctx->stream;
+  cudaError_t e = cudaMemcpyAsync(ctx->cell, cell, nsu,
+                                  cell_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) {
+    fail(ctx, SFM_ECUDA, "copy cell: %s", cudaGetErrorString(e));
+    return bail(SFM_ECUDA);
+  }
+  cudaMemsetAsync(ctx->ctr, 0, sizeof(Counters), s);
+  cudaMemsetAsync(ctx->occ, 0xff, nsu * sizeof(int32_t), s);
+  cudaMemsetAsync(ctx->ocls, 0, nsu, s);
+  launch_tables(g.r, ctx->prm, ctx->T0, ctx->TX, ctx->TY, ctx->KO, ctx->KE, ctx->own, ctx->dirdot,
+                ctx->hvec, s);
+  launch_static_field(g, ctx->cell, ctx->tables(), ctx->Fs, s);
+
+  // guidance: relaxation rounds until no tile changes
+  {
+    const int ntiles = ((g.W + kTile - 1) / kTile) * ((g.H + kTile - 1) / kTile);
+    uint8_t *a0 = nullptr, *a1 = nullptr;
+    int* changed = nullptr;
+    if (cudaMalloc(&a0, ntiles) != cudaSuccess || cudaMalloc(&a1, ntiles) != cudaSuccess ||
+        cudaMalloc(&changed, sizeof(int)) != cudaSuccess) {
+      cudaFree(a0);
+      cudaFree(a1);
+      fail(ctx, SFM_ENOMEM, "guidance scratch");
+      return bail(SFM_ENOMEM);
+    }
+    launch_guidance_init(g, ctx->cell, ctx->D, s);
+    cudaMemsetAsync(a0, 1, ntiles, s);
+    int h_changed = 1, rounds = 0;
+    const int max_rounds = 4 * (ntiles + 64);
+    while (h_changed && rounds < max_rounds) {
+      cudaMemsetAsync(a1, 0, ntiles, s);
+      cudaMemsetAsync(changed, 0, sizeof(int), s);
+      launch_guidance_round(g, ctx->cell, ctx->D, a0, a1, changed, s);
+      cudaMemcpyAsync(&h_changed, changed, sizeof(int), cudaMemcpyDeviceToHost, s);
+      cudaStreamSynchronize(s);
+      uint8_t* tmp = a0;
+      a0 = a1;
+      a1 = tmp;
+      ++rounds;
+    }
+    cudaFree(a0);
+    cudaFree(a1);
+    cudaFree(changed);
+    if (h_changed) {
+      fail(ctx, SFM_ETIMEOUT, "guidance relaxation did not converge in %d rounds", rounds);
+      return bail(SFM_ETIMEOUT);
+    }
+  }
+  e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    fail(ctx, SFM_ECUDA, "scene set-up: %s", cudaGetErrorString(e));
+    return bail(SFM_ECUDA);
+  }
+  *out = ctx;
+  return SFM_OK;
+}
+
+void sfm_destroy(sfm_ctx* ctx) {
+  if (!ctx) return;
+  cudaStreamSynchronize(ctx->stream);
+  for (void* p : ctx->allocs) cudaFree(p);
+  for (auto& r : ctx->recs) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  for (auto e : ctx->pool) cudaEventDestroy(e);
+  delete ctx;
+}
+
+sfm_status sfm_place(sfm_ctx* ctx, int32_t n, const int32_t* xy, const uint8_t* heading,
+                     const uint8_t* goal, const uint8_t* alive, int32_t on_device) {
+  if (!ctx) return SFM_EINVAL;
+  if (n < 0 || (n > 0 && !xy)) return fail(ctx, SFM_EINVAL, "bad pedestrian arrays");
+  cudaStream_t s = ctx->stream;
+  const Geo& g = ctx->geo;
+  if (ctx->placed && ctx->n > 0) {
+    launch_place_clear(ctx->n, ctx->xy, ctx->alive, g, ctx->occ, ctx->ocls, s);
+    ++ctx->launches;
+  }
+  if (n > ctx->cap) {
+    CU(cudaStreamSynchronize(s));
+    dfree(ctx, ctx->xy);
+    dfree(ctx, ctx->heading);
+    dfree(ctx, ctx->goal);
+    dfree(ctx, ctx->alive);
+    dfree(ctx, ctx->choice);
+    dfree(ctx, ctx->won);
+    dfree(ctx, ctx->rec);
+    ctx->xy = nullptr;
+    ctx->cap = 0;
+    TRY(dalloc(ctx, &ctx->xy, (size_t)n));
+    TRY(dalloc(ctx, &ctx->heading, (size_t)n));
+    TRY(dalloc(ctx, &ctx->goal, (size_t)n));
+    TRY(dalloc(ctx, &ctx->alive, (size_t)n));
+    TRY(dalloc(ctx, &ctx->choice, (size_t)n));
+    TRY(dalloc(ctx, &ctx->won, (size_t)n));
+    TRY(dalloc(ctx, &ctx->rec, (size_t)n));
+    ctx->cap = n;
+  }
+  if (ctx->cap == 0) {
+    TRY(dalloc(ctx, &ctx->xy, 1));
+    TRY(dalloc(ctx, &ctx->heading, 1));
+    TRY(dalloc(ctx, &ctx->goal, 1));
+    TRY(dalloc(ctx, &ctx->alive, 1));
+    TRY(dalloc(ctx, &ctx->choice, 1));
+    TRY(dalloc(ctx, &ctx->won, 1));
+    TRY(dalloc(ctx, &ctx->rec, 1));
+    ctx->cap = 1;
+  }
+  ctx->placed = false;
+  ctx->n = n;
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  if (n > 0) {
+    CU(cudaMemcpyAsync(ctx->xy, xy, (size_t)n * sizeof(int2), kind, s));
+    if (heading) CU(cudaMemcpyAsync(ctx->heading, heading, n, kind, s));
+    else CU(cudaMemsetAsync(ctx->heading, 0, n, s));
+    if (goal) CU(cudaMemcpyAsync(ctx->goal, goal, n, kind, s));
+    else CU(cudaMemsetAsync(ctx->goal, 0, n, s));
+    if (alive) CU(cudaMemcpyAsync(ctx->alive, alive, n, kind, s));
+    else CU(cudaMemsetAsync(ctx->alive, 1, n, s));
+    CU(cudaMemsetAsync(ctx->choice, 0, n, s));
+    CU(cudaMemsetAsync(ctx->won, 0, n, s));
+  }
+  // reset per-placement counters and flags, keep the tick counter
+  CU(cudaStreamSynchronize(s));
+  Counters h;
+  CU(cudaMemcpy(&h, ctx->ctr, sizeof(h), cudaMemcpyDeviceToHost));
+  h.moved = 0;
+  h.exited = 0;
+  h.max_registrants = 0;
+  h.err = 0;
+  CU(cudaMemcpy(ctx->ctr, &h, sizeof(h), cudaMemcpyHostToDevice));
+  launch_place_scatter(n, ctx->xy, ctx->heading, ctx->goal, ctx->alive, ctx->cell, g, ctx->occ,
+                       ctx->ocls, ctx->ctr, s);
+  if (n > 0) ++ctx->launches;
+  CU(cudaStreamSynchronize(s));
+  CU(cudaGetLastError());
+  CU(cudaMemcpy(&h, ctx->ctr, sizeof(h), cudaMemcpyDeviceToHost));
+  if (h.err) {
+    const uint32_t flags = h.err;
+    const size_t nsu = (size_t)g.W * g.H;
+    cudaMemsetAsync(ctx->occ, 0xff, nsu * sizeof(int32_t), s);
+    cudaMemsetAsync(ctx->ocls, 0, nsu, s);
+    h.err = 0;
+    cudaMemcpyAsync(ctx->ctr, &h, sizeof(h), cudaMemcpyHostToDevice, s);
+    cudaStreamSynchronize(s);
+    return fail(ctx, (flags & kErrPlaceRange) ? SFM_EINVAL : SFM_ECONFLICT,
+                "placement rejected: overlapping pedestrians, a pedestrian on a WALL/EXIT su, "
+                "off-lattice positions or classes > 8");
+  }
+  ctx->placed = true;
+  return SFM_OK;
+}
+
+sfm_status sfm_set_time(sfm_ctx* ctx, int64_t t) {
+  if (!ctx) return SFM_EINVAL;
+  CU(cudaStreamSynchronize(ctx->stream));
+  long long tv = t;
+  CU(cudaMemcpy(&ctx->ctr->t, &tv, sizeof(tv), cudaMemcpyHostToDevice));
+  ctx->t = t;
+  return SFM_OK;
+}
+
+sfm_status sfm_step(sfm_ctx* ctx, int32_t nsteps) {
+  if (!ctx) return SFM_EINVAL;
+  if (nsteps < 0) return fail(ctx, SFM_EINVAL, "nsteps < 0");
+  if (!ctx->placed) return fail(ctx, SFM_ESTATE, "sfm_step before a successful sfm_place");
+  for (int i = 0; i < nsteps; ++i) {
+    run_tick(ctx);
+    ++ctx->t;
+  }
+  if (ctx->timing) ctx->timed_ticks += nsteps;
+  CU(cudaGetLastError());
+  return SFM_OK;
+}
+
+sfm_status sfm_compute_field(sfm_ctx* ctx) {
+  if (!ctx) return SFM_EINVAL;
+  if (!ctx->placed) return fail(ctx, SFM_ESTATE, "no pedestrians placed");
+  if (ctx->bands > 1) return fail(ctx, SFM_ESTATE, "banded mode keeps no full-lattice field");
+  run_bins(ctx);
+  {
+    StageScope sc(ctx, SFM_STAGE_FIELD);
+    field_rows(ctx, ctx->F, 0, ctx->geo.H, 0, false);
+  }
+  CU(cudaGetLastError());
+  return SFM_OK;
+}
+
+sfm_status sfm_compute_field_into(sfm_ctx* ctx, float* dst, int32_t on_device) {
+  if (!ctx || !dst) return SFM_EINVAL;
+  if (!ctx->placed) return fail(ctx, SFM_ESTATE, "no pedestrians placed");
+  const Geo& g = ctx->geo;
+  run_bins(ctx);
+  if (on_device) {
+    field_rows(ctx, dst, 0, g.H, 0, false);
+    CU(cudaGetLastError());
+    return check_flags(ctx);
+  }
+  float* buf = ctx->bands > 1 ? ctx->band_buf : ctx->F;
+  const int rows = ctx->bands > 1 ? ctx->band_rows : g.H;
+  for (int ya = 0; ya < g.H; ya += rows) {
+    const int yb = ya + rows < g.H ? ya + rows : g.H;
+    field_rows(ctx, buf, ya, yb, 0, false);
+    CU(cudaMemcpyAsync(dst + (size_t)ya * g.W, buf, (size_t)(yb - ya) * g.W * sizeof(float),
+                       cudaMemcpyDeviceToHost, ctx->stream));
+  }
+  CU(cudaGetLastError());
+  return check_flags(ctx);
+}
+
+sfm_status sfm_sync(sfm_ctx* ctx) {
+  if (!ctx) return SFM_EINVAL;
+  CU(cudaGetLastError());
+  return check_flags(ctx);
+}
+
+sfm_status sfm_read_field(sfm_ctx* ctx, float* dst, int32_t on_device) {
+  if (!ctx || !dst) return SFM_EINVAL;
+  if (ctx->bands > 1) return fail(ctx, SFM_ESTATE, "banded mode keeps no full-lattice field");
+  return copy_out(ctx, dst, ctx->F, (size_t)ctx->geo.W * ctx->geo.H * sizeof(float), on_device);
+}
+
+sfm_status sfm_read_static_field(sfm_ctx* ctx, float* dst, int32_t on_device) {
+  if (!ctx || !dst) return SFM_EINVAL;
+  return copy_out(ctx, dst, ctx->Fs, (size_t)ctx->geo.W * ctx->geo.H * sizeof(float), on_device);
+}
+
+sfm_status sfm_read_guidance(sfm_ctx* ctx, int32_t* dst, int32_t on_device) {
+  if (!ctx || !dst) return SFM_EINVAL;
+  return copy_out(ctx, dst, ctx->D, (size_t)ctx->geo.W * ctx->geo.H * sizeof(int32_t), on_device);
+}
+
+sfm_status sfm_read_peds(sfm_ctx* ctx, int32_t* xy, uint8_t* heading, uint8_t* alive,
+                         int32_t on_device) {
+  if (!ctx) return SFM_EINVAL;
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  const size_t n = (size_t)ctx->n;
+  if (n) {
+    if (xy) CU(cudaMemcpyAsync(xy, ctx->xy, n * sizeof(int2), kind, ctx->stream));
+    if (heading) CU(cudaMemcpyAsync(heading, ctx->heading, n, kind, ctx->stream));
+    if (alive) CU(cudaMemcpyAsync(alive, ctx->alive, n, kind, ctx->stream));
+  }
+  return check_flags(ctx);
+}
+
+sfm_status sfm_read_decisions(sfm_ctx* ctx, uint8_t* choice, uint8_t* won, int32_t on_device) {
+  if (!ctx) return SFM_EINVAL;
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  const size_t n = (size_t)ctx->n;
+  if (n) {
+    if (choice) CU(cudaMemcpyAsync(choice, ctx->choice, n, kind, ctx->stream));
+    if (won) CU(cudaMemcpyAsync(won, ctx->won, n, kind, ctx->stream));
+  }
+  return check_flags(ctx);
+}
+
+sfm_status sfm_stats(sfm_ctx* ctx, sfm_stats_t* out) {
+  if (!ctx || !out) return SFM_EINVAL;
+  CU(cudaStreamSynchronize(ctx->stream));
+  Counters h;
+  CU(cudaMemcpy(&h, ctx->ctr, sizeof(h), cudaMemcpyDeviceToHost));
+  memset(out, 0, sizeof(*out));
+  out->t = h.t;
+  out->n = ctx->n;
+  out->exited = (int64_t)h.exited;
+  out->moved_total = (int64_t)h.moved;
+  out->max_registrants = h.max_registrants;
+  out->bands = ctx->bands;
+  out->error_flags = h.err;
+  out->device_bytes = ctx->device_bytes;
+  out->kernel_launches = ctx->launches;
+  // alive = placed live pedestrians minus those that left since placement
+  int64_t alive0 = 0;
+  if (ctx->n) {
+    std::vector<uint8_t> a((size_t)ctx->n);
+    CU(cudaMemcpy(a.data(), ctx->alive, a.size(), cudaMemcpyDeviceToHost));
+    for (uint8_t v : a) alive0 += v ? 1 : 0;
+  }
+  out->alive = alive0;
+  return SFM_OK;
+}
+
+sfm_status sfm_set_timing(sfm_ctx* ctx, int32_t enable) {
+  if (!ctx) return SFM_EINVAL;
+  ctx->timing = enable != 0;
+  return SFM_OK;
+}
+
+sfm_status sfm_stage_times(sfm_ctx* ctx, double* ms, int64_t* ticks) {
+  if (!ctx || !ms) return SFM_EINVAL;
+  CU(cudaStreamSynchronize(ctx->stream));
+  for (int i = 0; i < SFM_NSTAGES; ++i) ms[i] = 0.0;
+  for (auto& r : ctx->recs) {
+    float v = 0.f;
+    if (cudaEventElapsedTime(&v, r.a, r.b) == cudaSuccess) ms[r.stage] += v;
+    ctx->pool.push_back(r.a);
+    ctx->pool.push_back(r.b);
+  }
+  ctx->recs.clear();
+  if (ticks) *ticks = ctx->timed_ticks;
+  ctx->timed_ticks = 0;
+  return SFM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,98 @@
+// sfm_internal.h -- device data layout and kernel launchers shared by the
+// C-ABI host code (sfm_api.cu) and the kernels (sfm_kernels.cu).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/sfm.h"
+
+namespace sfm {
+
+constexpr int kFree = 0, kWall = 1, kExit = 2;
+constexpr int32_t kDInf = 1 << 23;  // guidance distance of unreachable / WALL su
+
+// Field gather tiling: a CTA owns a 32 x 32 su tile; warp w owns rows
+// 4w..4w+3 of it, lane l owns column l.
+constexpr int kTile = 32;
+constexpr int kFieldThreads = 256;
+constexpr int kRowsPerThread = kTile / (kFieldThreads / 32);  // 4
+constexpr int kStageCap = 2048;    // pedestrians staged in shared memory per chunk
+constexpr int kMaxHaloBins = 128;  // bins touched by one tile's halo (checked)
+constexpr int kBin = 32;           // side of a pedestrian bin (one warp column per su)
+
+// device error flags (sticky until read by a synchronising call)
+enum : uint32_t {
+  kErrPlaceConflict = 1u,  // two pedestrians on one su, or on a WALL/EXIT su
+  kErrPlaceRange = 2u,     // off-lattice position or class > 8
+  kErrEnroll = 4u,         // more than 8 registrants for one su (impossible by construction)
+  kErrHalo = 8u,           // a tile's halo touched more bins than kMaxHaloBins
+  kErrTimeout = 16u,       // a bounded device wait gave up
+};
+
+struct Counters {
+  unsigned long long moved;
+  unsigned long long exited;
+  int max_registrants;
+  uint32_t err;
+  long long t;  // tick counter read by the vote and advanced by the commit
+};
+
+// Geometry and model constants passed by value to every kernel.
+struct Geo {
+  int W, H, px, py;
+  int r;
+  int nbx, nby;  // bins per row / column
+};
+
+struct Tables {
+  const float* T0;      // (2r+1)^2: kP d^aP          (pedestrian, isotropic part)
+  const float* TX;      // (2r+1)^2: kP d^aP gamma dx/d
+  const float* TY;      // (2r+1)^2: kP d^aP gamma dy/d
+  const float* KO;      // (2r+1)^2: kO d^aO
+  const float* KE;      // (2r+1)^2: kE d^aE
+  const float* own;     // [9 heading][9 move]: K_P(Delta_move; h)
+  const float* dirdot;  // [9 goal][9 move]: Delta_move . u_goal
+  const float2* hvec;   // [9]: unit heading vectors
+};
+
+// ---- launchers (sfm_kernels.cu) ----
+void launch_tables(int r, const sfm_params& p, float* T0, float* TX, float* TY, float* KO,
+                   float* KE, float* own, float* dirdot, float2* hvec, cudaStream_t s);
+void launch_static_field(const Geo& g, const uint8_t* cell, const Tables& tb, float* Fs,
+                         cudaStream_t s);
+// One relaxation round of the guidance distances; returns via *changed.
+void launch_guidance_init(const Geo& g, const uint8_t* cell, int32_t* D, cudaStream_t s);
+void launch_guidance_round(const Geo& g, const uint8_t* cell, int32_t* D, const uint8_t* act_in,
+                           uint8_t* act_out, int* changed, cudaStream_t s);
+
+void launch_place_clear(int n, const int2* xy, const uint8_t* alive, const Geo& g, int32_t* occ,
+                        uint8_t* ocls, cudaStream_t s);
+void launch_place_scatter(int n, const int2* xy, const uint8_t* heading, const uint8_t* goal,
+                          const uint8_t* alive, const uint8_t* cell, const Geo& g, int32_t* occ,
+                          uint8_t* ocls, Counters* ctr, cudaStream_t s);
+
+void launch_bin_count(const Geo& g, const uint8_t* ocls, int32_t* count, cudaStream_t s);
+void launch_scan(const int32_t* in, int32_t* out, int n, int32_t* block_tmp, cudaStream_t s);
+int scan_tmp_elems(int n);
+void launch_bin_fill(const Geo& g, const uint8_t* ocls, const int32_t* start, uint32_t* rec,
+                     cudaStream_t s);
+
+// Field gather over tile rows [ty0, ty1); stores lattice rows y in
+// [store_lo, store_hi) at out[(y - out_row0) * W + x].
+void launch_field(const Geo& g, const int32_t* bin_start, const uint32_t* rec, const Tables& tb,
+                  const float* Fs, float* out, int out_row0, int ty0, int ty1, int store_lo,
+                  int store_hi, Counters* ctr, cudaStream_t s);
+
+void launch_decide(int n, const int2* xy, const uint8_t* alive, const uint8_t* heading,
+                   const uint8_t* goal, const uint8_t* cell, const int32_t* occ, const int32_t* D,
+                   const float* F, int main_off, int lo_row, int hi_row, int hi_off, int y_lo,
+                   int y_hi, const Geo& g, float beta, const Tables& tb, uint8_t* choice,
+                   cudaStream_t s);
+void launch_vote(int n, const int2* xy, const uint8_t* alive, const uint8_t* choice,
+                 const int32_t* occ, const Geo& g, uint64_t seed, Counters* ctr, uint8_t* won,
+                 cudaStream_t s);
+void launch_commit(int n, int2* xy, uint8_t* alive, uint8_t* heading, const uint8_t* choice,
+                   const uint8_t* won, const uint8_t* cell, int32_t* occ, uint8_t* ocls,
+                   const Geo& g, Counters* ctr, cudaStream_t s);
+
+}  // namespace sfm

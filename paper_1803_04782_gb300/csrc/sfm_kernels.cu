@@ -1,0 +1,754 @@
+// sfm_kernels.cu -- sm_103a kernels of one tick of the discrete social-field
+// pedestrian model (Alg. 1 of the paper: k-5 field superposition, k-2 decision,
+// k-3 vote, k-4 commit), re-designed as gathers so that no step needs atomics
+// on the field (Sec. 3.1 s-1 avoids them with fan-out caches instead).
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "sfm_internal.h"
+
+namespace sfm {
+
+__constant__ int c_dx[9] = {0, 1, 1, 0, -1, -1, -1, 0, 1};
+__constant__ int c_dy[9] = {0, 0, 1, 1, 1, 0, -1, -1, -1};
+// class of the opposite move
+__constant__ int c_opp[9] = {0, 5, 6, 7, 8, 1, 2, 3, 4};
+
+static inline int cdiv(int a, int b) { return (a + b - 1) / b; }
+
+__device__ __forceinline__ bool wrap_coord(int v, int n, int periodic, int& out) {
+  if (v >= 0 && v < n) { out = v; return true; }
+  if (!periodic) return false;
+  v %= n;
+  if (v < 0) v += n;
+  out = v;
+  return true;
+}
+
+__device__ __forceinline__ int floor_div(int a, int b) {
+  int q = a / b;
+  return (a % b != 0 && ((a < 0) != (b < 0))) ? q - 1 : q;
+}
+
+// ------------------------------------------------------------------ tables
+// Kernel values are evaluated once per scene in FP64 and rounded to FP32.
+__global__ void k_tables(int r, double kP, double aP, double gamma, double kO, double aO,
+                         double kE, double aE, float* T0, float* TX, float* TY, float* KO,
+                         float* KE, float* own, float* dirdot, float2* hvec) {
+  const int S = 2 * r + 1, n = S * S;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    const int dx = i % S - r, dy = i / S - r;
+    if (dx == 0 && dy == 0) {
+      T0[i] = TX[i] = TY[i] = KO[i] = KE[i] = 0.f;
+    } else {
+      const double d = sqrt((double)(dx * dx + dy * dy));
+      const double base = kP * pow(d, aP);
+      T0[i] = (float)base;
+      TX[i] = (float)(base * gamma * dx / d);
+      TY[i] = (float)(base * gamma * dy / d);
+      KO[i] = (float)(kO * pow(d, aO));
+      KE[i] = (float)(kE * pow(d, aE));
+    }
+  }
+  if (i < 81) {
+    const int h = i / 9, k = i % 9;
+    double hx = 0.0, hy = 0.0;
+    if (h > 0) {
+      const double nh = sqrt((double)(c_dx[h] * c_dx[h] + c_dy[h] * c_dy[h]));
+      hx = c_dx[h] / nh;
+      hy = c_dy[h] / nh;
+    }
+    double o = 0.0;
+    if (k > 0 && r >= 1) {
+      const double d = sqrt((double)(c_dx[k] * c_dx[k] + c_dy[k] * c_dy[k]));
+      o = kP * pow(d, aP) * (1.0 + gamma * (hx * c_dx[k] + hy * c_dy[k]) / d);
+    }
+    own[i] = (float)o;
+    dirdot[i] = (float)(c_dx[k] * hx + c_dy[k] * hy);
+    if (k == 0) hvec[h] = make_float2((float)hx, (float)hy);
+  }
+}
+
+void launch_tables(int r, const sfm_params& p, float* T0, float* TX, float* TY, float* KO,
+                   float* KE, float* own, float* dirdot, float2* hvec, cudaStream_t s) {
+  const int n = (2 * r + 1) * (2 * r + 1);
+  const int total = n > 81 ? n : 81;
+  k_tables<<<cdiv(total, 256), 256, 0, s>>>(r, p.kP, p.aP, p.gamma, p.kO, p.aO, p.kE, p.aE, T0,
+                                            TX, TY, KO, KE, own, dirdot, hvec);
+}
+
+// ------------------------------------------------------------ static field
+// F_static(c) = sum over WALL / EXIT su o within the window of K_O / K_E(c - o),
+// a dense window gather over a shared-memory copy of the cell tile and its
+// r-halo; compensated (Kahan) FP32 accumulation because up to (2r+1)^2 - 1
+// terms enter one su.  Computed once per scene.
+__global__ void __launch_bounds__(kFieldThreads)
+    k_static_field(Geo g, const uint8_t* __restrict__ cell, const float* __restrict__ KO,
+                   const float* __restrict__ KE, float* __restrict__ Fs) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int r = g.r, S = 2 * r + 1, nT = S * S, HW = kTile + 2 * r;
+  float* sKO = reinterpret_cast<float*>(smem);
+  float* sKE = sKO + nT;
+  uint8_t* sC = reinterpret_cast<uint8_t*>(sKE + nT);
+  const int tid = threadIdx.x;
+  const int x0 = blockIdx.x * kTile, y0 = blockIdx.y * kTile;
+  for (int i = tid; i < nT; i += blockDim.x) {
+    sKO[i] = KO[i];
+    sKE[i] = KE[i];
+  }
+  for (int i = tid; i < HW * HW; i += blockDim.x) {
+    const int hx = i % HW, hy = i / HW;
+    int gx, gy;
+    uint8_t v = kFree;
+    if (wrap_coord(x0 - r + hx, g.W, g.px, gx) && wrap_coord(y0 - r + hy, g.H, g.py, gy))
+      v = cell[(size_t)gy * g.W + gx];
+    sC[i] = v;
+  }
+  __syncthreads();
+  const int lane = tid & 31, w = tid >> 5;
+  float sum[kRowsPerThread], comp[kRowsPerThread];
+#pragma unroll
+  for (int j = 0; j < kRowsPerThread; ++j) sum[j] = comp[j] = 0.f;
+  for (int dy = -r; dy <= r; ++dy) {
+    for (int dx = -r; dx <= r; ++dx) {
+      const int ti = (dy + r) * S + (dx + r);
+      const float ko = sKO[ti], ke = sKE[ti];
+      const uint8_t* col = sC + (lane - dx + r);
+#pragma unroll
+      for (int j = 0; j < kRowsPerThread; ++j) {
+        const uint8_t b = col[(4 * w + j - dy + r) * HW];
+        const float v = (b == kWall) ? ko : ((b == kExit) ? ke : 0.f);
+        const float yk = v - comp[j];
+        const float tk = sum[j] + yk;
+        comp[j] = (tk - sum[j]) - yk;
+        sum[j] = tk;
+      }
+    }
+  }
+  const int x = x0 + lane;
+#pragma unroll
+  for (int j = 0; j < kRowsPerThread; ++j) {
+    const int y = y0 + 4 * w + j;
+    if (x < g.W && y < g.H) Fs[(size_t)y * g.W + x] = sum[j];
+  }
+}
+
+void launch_static_field(const Geo& g, const uint8_t* cell, const Tables& tb, float* Fs,
+                         cudaStream_t s) {
+  const int S = 2 * g.r + 1, HW = kTile + 2 * g.r;
+  const size_t smem = (size_t)2 * S * S * sizeof(float) + (size_t)HW * HW;
+  cudaFuncSetAttribute(k_static_field, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  dim3 grid(cdiv(g.W, kTile), cdiv(g.H, kTile));
+  k_static_field<<<grid, kFieldThreads, smem, s>>>(g, cell, tb.KO, tb.KE, Fs);
+}
+
+// --------------------------------------------------------------- guidance
+// Chamfer (5, 7) geodesic distance to the nearest EXIT through non-WALL su,
+// solved as the fixed point of D(c) = min_k D(c + Delta_k) + w_k by tile-local
+// relaxation in shared memory; a tile is revisited only when it or a
+// neighbour changed in the previous round.  The fixed point is unique, so the
+// result is exact and independent of the visiting order.
+__global__ void k_guidance_init(Geo g, const uint8_t* __restrict__ cell, int32_t* __restrict__ D) {
+  const size_t n = (size_t)g.W * g.H;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x)
+    D[i] = (cell[i] == kExit) ? 0 : kDInf;
+}
+
+__global__ void __launch_bounds__(1024)
+    k_guidance_round(Geo g, const uint8_t* __restrict__ cell, int32_t* __restrict__ D,
+                     const uint8_t* __restrict__ act_in, uint8_t* __restrict__ act_out,
+                     int* __restrict__ changed) {
+  __shared__ int32_t sD[kTile + 2][kTile + 2];
+  const int ntx = (g.W + kTile - 1) / kTile, nty = (g.H + kTile - 1) / kTile;
+  const int tile = blockIdx.x;
+  if (!act_in[tile]) return;
+  const int tx = tile % ntx, ty = tile / ntx;
+  const int x0 = tx * kTile, y0 = ty * kTile;
+  const int tid = threadIdx.x;
+  for (int i = tid; i < (kTile + 2) * (kTile + 2); i += blockDim.x) {
+    const int hx = i % (kTile + 2), hy = i / (kTile + 2);
+    int gx, gy;
+    int32_t v = kDInf;
+    if (wrap_coord(x0 - 1 + hx, g.W, g.px, gx) && wrap_coord(y0 - 1 + hy, g.H, g.py, gy))
+      v = D[(size_t)gy * g.W + gx];
+    sD[hy][hx] = v;
+  }
+  const int lx = tid % kTile, ly = tid / kTile;
+  const int gx = x0 + lx, gy = y0 + ly;
+  const bool valid = gx < g.W && gy < g.H;
+  uint8_t cv = kWall;
+  if (valid) cv = cell[(size_t)gy * g.W + gx];
+  const bool relax = valid && cv == kFree;
+  __syncthreads();
+  bool mine = false;
+  for (int it = 0; it < 4 * kTile * kTile; ++it) {
+    bool ch = false;
+    if (relax) {
+      const int32_t cur = sD[ly + 1][lx + 1];
+      int32_t best = cur;
+#pragma unroll
+      for (int k = 1; k <= 8; ++k) {
+        const int32_t v = sD[ly + 1 + c_dy[k]][lx + 1 + c_dx[k]];
+        const int32_t wk = (c_dx[k] != 0 && c_dy[k] != 0) ? 7 : 5;
+        if (v < kDInf && v + wk < best) best = v + wk;
+      }
+      if (best < cur) {
+        sD[ly + 1][lx + 1] = best;
+        ch = true;
+      }
+    }
+    mine |= ch;
+    if (!__syncthreads_or(ch)) break;
+  }
+  if (mine) D[(size_t)gy * g.W + gx] = sD[ly + 1][lx + 1];
+  if (__syncthreads_or(mine) && tid == 0) {
+    *changed = 1;
+    for (int dy = -1; dy <= 1; ++dy)
+      for (int dx = -1; dx <= 1; ++dx) {
+        int nx = tx + dx, ny = ty + dy;
+        if (g.px) nx = (nx + ntx) % ntx;
+        if (g.py) ny = (ny + nty) % nty;
+        if (nx >= 0 && nx < ntx && ny >= 0 && ny < nty) act_out[ny * ntx + nx] = 1;
+      }
+  }
+}
+
+void launch_guidance_init(const Geo& g, const uint8_t* cell, int32_t* D, cudaStream_t s) {
+  const size_t n = (size_t)g.W * g.H;
+  int blocks = (int)((n + 255) / 256);
+  if (blocks > 152 * 64) blocks = 152 * 64;
+  k_guidance_init<<<blocks, 256, 0, s>>>(g, cell, D);
+}
+
+void launch_guidance_round(const Geo& g, const uint8_t* cell, int32_t* D, const uint8_t* act_in,
+                           uint8_t* act_out, int* changed, cudaStream_t s) {
+  const int ntiles = cdiv(g.W, kTile) * cdiv(g.H, kTile);
+  k_guidance_round<<<ntiles, kTile * kTile, 0, s>>>(g, cell, D, act_in, act_out, changed);
+}
+
+// ------------------------------------------------------------- placement
+__global__ void k_place_clear(int n, const int2* __restrict__ xy, const uint8_t* __restrict__ alive,
+                              Geo g, int32_t* __restrict__ occ, uint8_t* __restrict__ ocls) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n || !alive[p]) return;
+  const int2 q = xy[p];
+  const size_t c = (size_t)q.y * g.W + q.x;
+  occ[c] = -1;
+  ocls[c] = 0;
+}
+
+__global__ void k_place_scatter(int n, const int2* __restrict__ xy,
+                                const uint8_t* __restrict__ heading,
+                                const uint8_t* __restrict__ goal, const uint8_t* __restrict__ alive,
+                                const uint8_t* __restrict__ cell, Geo g, int32_t* __restrict__ occ,
+                                uint8_t* __restrict__ ocls, Counters* ctr) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  if (heading[p] > 8 || goal[p] > 8) atomicOr(&ctr->err, kErrPlaceRange);
+  if (!alive[p]) return;
+  const int2 q = xy[p];
+  if (q.x < 0 || q.x >= g.W || q.y < 0 || q.y >= g.H) {
+    atomicOr(&ctr->err, kErrPlaceRange);
+    return;
+  }
+  const size_t c = (size_t)q.y * g.W + q.x;
+  if (cell[c] != kFree) atomicOr(&ctr->err, kErrPlaceConflict);
+  if (atomicCAS(&occ[c], -1, p) != -1) {
+    atomicOr(&ctr->err, kErrPlaceConflict);
+    return;
+  }
+  ocls[c] = (uint8_t)(1 + (heading[p] > 8 ? 0 : heading[p]));
+}
+
+void launch_place_clear(int n, const int2* xy, const uint8_t* alive, const Geo& g, int32_t* occ,
+                        uint8_t* ocls, cudaStream_t s) {
+  if (n <= 0) return;
+  k_place_clear<<<cdiv(n, 256), 256, 0, s>>>(n, xy, alive, g, occ, ocls);
+}
+
+void launch_place_scatter(int n, const int2* xy, const uint8_t* heading, const uint8_t* goal,
+                          const uint8_t* alive, const uint8_t* cell, const Geo& g, int32_t* occ,
+                          uint8_t* ocls, Counters* ctr, cudaStream_t s) {
+  if (n <= 0) return;
+  k_place_scatter<<<cdiv(n, 256), 256, 0, s>>>(n, xy, heading, goal, alive, cell, g, occ, ocls,
+                                               ctr);
+}
+
+// --------------------------------------------------------- S1: binning
+// Counting sort of the live pedestrians into 32 x 32-su bins, read off the
+// per-su occupancy-class grid so that the order inside a bin is row-major
+// and therefore deterministic.  One warp per bin, lane = bin column.
+__global__ void k_bin_count(Geo g, const uint8_t* __restrict__ ocls, int32_t* __restrict__ count) {
+  const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (wid >= g.nbx * g.nby) return;
+  const int bx = wid % g.nbx, by = wid / g.nbx;
+  const int x = bx * kBin + lane;
+  int c = 0;
+  for (int row = 0; row < kBin; ++row) {
+    const int y = by * kBin + row;
+    if (y >= g.H) break;
+    const bool o = x < g.W && ocls[(size_t)y * g.W + x] != 0;
+    c += __popc(__ballot_sync(0xffffffffu, o));
+  }
+  if (lane == 0) count[wid] = c;
+}
+
+__global__ void k_bin_fill(Geo g, const uint8_t* __restrict__ ocls,
+                           const int32_t* __restrict__ start, uint32_t* __restrict__ rec) {
+  const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (wid >= g.nbx * g.nby) return;
+  const int bx = wid % g.nbx, by = wid / g.nbx;
+  const int x = bx * kBin + lane;
+  int off = start[wid];
+  const unsigned lt = (1u << lane) - 1u;
+  for (int row = 0; row < kBin; ++row) {
+    const int y = by * kBin + row;
+    if (y >= g.H) break;
+    const uint8_t v = (x < g.W) ? ocls[(size_t)y * g.W + x] : 0;
+    const unsigned b = __ballot_sync(0xffffffffu, v != 0);
+    if (v) rec[off + __popc(b & lt)] = (uint32_t)lane | ((uint32_t)row << 8) | ((uint32_t)(v - 1) << 16);
+    off += __popc(b);
+  }
+}
+
+void launch_bin_count(const Geo& g, const uint8_t* ocls, int32_t* count, cudaStream_t s) {
+  const int nb = g.nbx * g.nby;
+  k_bin_count<<<cdiv(nb * 32, 256), 256, 0, s>>>(g, ocls, count);
+}
+
+void launch_bin_fill(const Geo& g, const uint8_t* ocls, const int32_t* start, uint32_t* rec,
+                     cudaStream_t s) {
+  const int nb = g.nbx * g.nby;
+  k_bin_fill<<<cdiv(nb * 32, 256), 256, 0, s>>>(g, ocls, start, rec);
+}
+
+// ------------------------------------------------------------------ scan
+// Exclusive prefix sum of n int32 into out[0..n] (out[n] = total), three
+// passes: per-block totals, a single-block scan of the totals, final.
+constexpr int kScanThreads = 1024, kScanItems = 4, kScanChunk = kScanThreads * kScanItems;
+
+__device__ int block_exclusive_scan(int v, int* sWarp, int& total) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  int inc = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int t = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += t;
+  }
+  if (lane == 31) sWarp[w] = inc;
+  __syncthreads();
+  if (w == 0) {
+    int s = lane < nw ? sWarp[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, s, o);
+      if (lane >= o) s += t;
+    }
+    if (lane < nw) sWarp[lane] = s;
+  }
+  __syncthreads();
+  total = sWarp[nw - 1];
+  const int excl = inc - v + (w > 0 ? sWarp[w - 1] : 0);
+  __syncthreads();
+  return excl;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_totals(const int32_t* __restrict__ in, int n,
+                                                              int32_t* __restrict__ totals) {
+  __shared__ int sWarp[32];
+  const int base = blockIdx.x * kScanChunk + threadIdx.x * kScanItems;
+  int s = 0;
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k)
+    if (base + k < n) s += in[base + k];
+  int total;
+  block_exclusive_scan(s, sWarp, total);
+  if (threadIdx.x == 0) totals[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_top(int32_t* __restrict__ totals, int nb) {
+  __shared__ int sWarp[32];
+  int carry = 0;
+  for (int base = 0; base < nb; base += kScanChunk) {
+    int v[kScanItems], s = 0;
+    const int i0 = base + threadIdx.x * kScanItems;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+      v[k] = (i0 + k < nb) ? totals[i0 + k] : 0;
+      s += v[k];
+    }
+    int total;
+    int e = block_exclusive_scan(s, sWarp, total) + carry;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+      if (i0 + k < nb) totals[i0 + k] = e;
+      e += v[k];
+    }
+    carry += total;
+  }
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_final(const int32_t* __restrict__ in, int n,
+                                                             const int32_t* __restrict__ offs,
+                                                             int32_t* __restrict__ out) {
+  __shared__ int sWarp[32];
+  const int i0 = blockIdx.x * kScanChunk + threadIdx.x * kScanItems;
+  int v[kScanItems], s = 0;
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    v[k] = (i0 + k < n) ? in[i0 + k] : 0;
+    s += v[k];
+  }
+  int total;
+  int e = block_exclusive_scan(s, sWarp, total) + offs[blockIdx.x];
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    if (i0 + k < n) out[i0 + k] = e;
+    e += v[k];
+  }
+  if (blockIdx.x == gridDim.x - 1 && threadIdx.x == blockDim.x - 1) out[n] = e;
+}
+
+int scan_tmp_elems(int n) { return cdiv(n > 0 ? n : 1, kScanChunk); }
+
+void launch_scan(const int32_t* in, int32_t* out, int n, int32_t* block_tmp, cudaStream_t s) {
+  const int nb = scan_tmp_elems(n);
+  k_scan_totals<<<nb, kScanThreads, 0, s>>>(in, n, block_tmp);
+  k_scan_top<<<1, kScanThreads, 0, s>>>(block_tmp, nb);
+  k_scan_final<<<nb, kScanThreads, 0, s>>>(in, n, block_tmp, out);
+}
+
+// ------------------------------------------------------ S2: field gather
+// Each CTA owns a 32 x 32 su tile.  The pedestrians of the bins that overlap
+// the tile's r-halo are staged in shared memory in chunks of at most `cap`
+// records (the bounded multi-step sum of Alg. 3 / Eq. 1: the per-su sum is
+// split into a fixed number of partial passes), every lane accumulates the
+// kernel-table value of each staged pedestrian inside its window for its 4
+// rows, and the tile is written once as F = F_static + sum.
+struct HaloBin {
+  int start, count, xoff, yoff;
+};
+constexpr int kMaxImages = 24;
+
+// Bins (one dimension) overlapping the halo [lo, hi]; returns entries (bin,
+// offset of the bin origin relative to the tile origin).
+__device__ int halo_list(int lo, int hi, int n, int periodic, int nbins, int t0, int* bin,
+                         int* off) {
+  int cnt = 0;
+  if (!periodic) {
+    if (lo < 0) lo = 0;
+    if (hi > n - 1) hi = n - 1;
+    for (int b = lo / kBin; lo <= hi && b <= hi / kBin; ++b) {
+      if (cnt < kMaxImages) { bin[cnt] = b; off[cnt] = b * kBin - t0; }
+      ++cnt;
+    }
+    return cnt;
+  }
+  const int k0 = floor_div(lo, n), k1 = floor_div(hi, n);
+  for (int k = k0; k <= k1; ++k) {
+    int a = lo - k * n, z = hi - k * n;
+    if (a < 0) a = 0;
+    if (z > n - 1) z = n - 1;
+    for (int b = a / kBin; a <= z && b <= z / kBin; ++b) {
+      if (cnt < kMaxImages) { bin[cnt] = b; off[cnt] = b * kBin + k * n - t0; }
+      ++cnt;
+    }
+  }
+  (void)nbins;
+  return cnt;
+}
+
+__global__ void __launch_bounds__(kFieldThreads)
+    k_field(Geo g, const int32_t* __restrict__ bin_start, const uint32_t* __restrict__ rec,
+            Tables tb, const float* __restrict__ Fs, float* __restrict__ out, int out_row0,
+            int ty0, int store_lo, int store_hi, int cap, Counters* ctr) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ HaloBin sBins[kMaxImages * kMaxImages];
+  __shared__ int sPref[kMaxImages * kMaxImages + 1];
+  __shared__ int sNB;
+  const int r = g.r, S = 2 * r + 1, nT = S * S;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  int4* sPed = reinterpret_cast<int4*>(smem);
+  float* sT0 = reinterpret_cast<float*>(sPed + cap);
+  float* sTX = sT0 + nT;
+  float* sTY = sTX + nT;
+  const int x0 = blockIdx.x * kTile, y0 = (ty0 + blockIdx.y) * kTile;
+
+  for (int i = tid; i < nT; i += blockDim.x) {
+    sT0[i] = tb.T0[i];
+    sTX[i] = tb.TX[i];
+    sTY[i] = tb.TY[i];
+  }
+  if (tid == 0) {
+    int bxs[kMaxImages], xo[kMaxImages], bys[kMaxImages], yo[kMaxImages];
+    const int nxl = halo_list(x0 - r, x0 + kTile - 1 + r, g.W, g.px, g.nbx, x0, bxs, xo);
+    const int nyl = halo_list(y0 - r, y0 + kTile - 1 + r, g.H, g.py, g.nby, y0, bys, yo);
+    int nb = 0;
+    if (nxl > kMaxImages || nyl > kMaxImages) {
+      atomicOr(&ctr->err, kErrHalo);
+    } else {
+      for (int a = 0; a < nyl; ++a)
+        for (int b = 0; b < nxl; ++b) {
+          sBins[nb].start = bys[a] * g.nbx + bxs[b];  // bin id for now
+          sBins[nb].xoff = xo[b];
+          sBins[nb].yoff = yo[a];
+          ++nb;
+        }
+    }
+    sNB = nb;
+  }
+  __syncthreads();
+  const int nb = sNB;
+  for (int i = tid; i < nb; i += blockDim.x) {
+    const int id = sBins[i].start;
+    const int s0 = bin_start[id];
+    sBins[i].start = s0;
+    sBins[i].count = bin_start[id + 1] - s0;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    int acc = 0;
+    for (int i = 0; i < nb; ++i) {
+      sPref[i] = acc;
+      acc += sBins[i].count;
+    }
+    sPref[nb] = acc;
+  }
+  __syncthreads();
+  const int total = sPref[nb];
+
+  float acc[kRowsPerThread];
+#pragma unroll
+  for (int j = 0; j < kRowsPerThread; ++j) acc[j] = 0.f;
+  const int rowb = kRowsPerThread * w;  // first row of this warp inside the tile
+
+  for (int base = 0; base < total; base += cap) {
+    const int cnt = min(cap, total - base);
+    for (int i = tid; i < cnt; i += blockDim.x) {
+      const int q = base + i;
+      int lo = 0, hi = nb;
+      while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (sPref[mid] <= q) lo = mid; else hi = mid;
+      }
+      const uint32_t rc = rec[sBins[lo].start + (q - sPref[lo])];
+      const int cls = (rc >> 16) & 0xf;
+      const float2 h = tb.hvec[cls];
+      sPed[i] = make_int4(sBins[lo].xoff + (int)(rc & 0xff), sBins[lo].yoff + (int)((rc >> 8) & 0xff),
+                          __float_as_int(h.x), __float_as_int(h.y));
+    }
+    __syncthreads();
+    for (int i = 0; i < cnt; ++i) {
+      const int4 pd = sPed[i];
+      const int dyb = rowb - pd.y;  // dy of this warp's first row
+      if (dyb + kRowsPerThread - 1 < -r || dyb > r) continue;    // warp-uniform
+      if (kTile - 1 - pd.x < -r || -pd.x > r) continue;          // warp-uniform
+      const int dx = lane - pd.x;
+      if ((unsigned)(dx + r) > (unsigned)(2 * r)) continue;
+      const float hx = __int_as_float(pd.z), hy = __int_as_float(pd.w);
+#pragma unroll
+      for (int j = 0; j < kRowsPerThread; ++j) {
+        const int dy = dyb + j;
+        if ((unsigned)(dy + r) <= (unsigned)(2 * r)) {
+          const int ti = (dy + r) * S + (dx + r);
+          acc[j] += fmaf(hy, sTY[ti], fmaf(hx, sTX[ti], sT0[ti]));
+        }
+      }
+    }
+    __syncthreads();
+  }
+  const int x = x0 + lane;
+#pragma unroll
+  for (int j = 0; j < kRowsPerThread; ++j) {
+    const int y = y0 + rowb + j;
+    if (x < g.W && y < g.H && y >= store_lo && y < store_hi) {
+      const size_t c = (size_t)y * g.W + x;
+      out[(size_t)(y - out_row0) * g.W + x] = Fs[c] + acc[j];
+    }
+  }
+}
+
+static int field_cap(int r, size_t* smem_out) {
+  const int S = 2 * r + 1;
+  const size_t tables = (size_t)3 * S * S * sizeof(float);
+  const size_t budget = 200 * 1024;
+  int cap = kStageCap;
+  while (cap > 256 && tables + (size_t)cap * sizeof(int4) > budget) cap >>= 1;
+  *smem_out = tables + (size_t)cap * sizeof(int4);
+  return cap;
+}
+
+void launch_field(const Geo& g, const int32_t* bin_start, const uint32_t* rec, const Tables& tb,
+                  const float* Fs, float* out, int out_row0, int ty0, int ty1, int store_lo,
+                  int store_hi, Counters* ctr, cudaStream_t s) {
+  if (ty1 <= ty0) return;
+  size_t smem;
+  const int cap = field_cap(g.r, &smem);
+  cudaFuncSetAttribute(k_field, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  dim3 grid(cdiv(g.W, kTile), ty1 - ty0);
+  k_field<<<grid, kFieldThreads, smem, s>>>(g, bin_start, rec, tb, Fs, out, out_row0, ty0,
+                                            store_lo, store_hi, cap, ctr);
+}
+
+// --------------------------------------------------------- S3: decide
+// Per pedestrian: E over the 9 candidates (stay + 8 neighbours), admissible
+// iff inside, not WALL and unoccupied at tick start; branch-free select of the
+// minimum with ties to the smallest class.
+__global__ void k_decide(int n, const int2* __restrict__ xy, const uint8_t* __restrict__ alive,
+                         const uint8_t* __restrict__ heading, const uint8_t* __restrict__ goal,
+                         const uint8_t* __restrict__ cell, const int32_t* __restrict__ occ,
+                         const int32_t* __restrict__ D, const float* __restrict__ F, int main_off,
+                         int lo_row, int hi_row, int hi_off, int y_lo, int y_hi, Geo g,
+                         float beta, const float* __restrict__ own,
+                         const float* __restrict__ dirdot, uint8_t* __restrict__ choice) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  const int2 q = xy[p];
+  if (q.y < y_lo || q.y >= y_hi) return;
+  if (!alive[p]) {
+    choice[p] = 0;
+    return;
+  }
+  const int h = heading[p], gl = goal[p];
+  const int32_t d0 = D[(size_t)q.y * g.W + q.x];
+  int best = 0;
+  float bestE = 0.f;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    int nx, ny;
+    const bool in = wrap_coord(q.x + c_dx[k], g.W, g.px, nx) & wrap_coord(q.y + c_dy[k], g.H, g.py, ny);
+    if (!in) continue;
+    const size_t c = (size_t)ny * g.W + nx;
+    if (k > 0 && (cell[c] == kWall || occ[c] >= 0)) continue;
+    // row of the field buffer holding lattice row ny: the band's own rows,
+    // or one of its two single halo rows
+    const int frow = (ny >= y_lo && ny < y_hi) ? ny - y_lo + main_off
+                                               : (ny == lo_row ? 0 : (ny == hi_row ? hi_off : 0));
+    const float f = F[(size_t)frow * g.W + nx];
+    const float guide = (gl == 0) ? beta * ((float)(D[c] - d0) / 5.0f) : -beta * dirdot[gl * 9 + k];
+    const float e = f - own[h * 9 + k] + guide;
+    if (k == 0 || e < bestE) {
+      best = k;
+      bestE = e;
+    }
+  }
+  choice[p] = (uint8_t)best;
+}
+
+void launch_decide(int n, const int2* xy, const uint8_t* alive, const uint8_t* heading,
+                   const uint8_t* goal, const uint8_t* cell, const int32_t* occ, const int32_t* D,
+                   const float* F, int main_off, int lo_row, int hi_row, int hi_off, int y_lo,
+                   int y_hi, const Geo& g, float beta, const Tables& tb, uint8_t* choice,
+                   cudaStream_t s) {
+  if (n <= 0) return;
+  k_decide<<<cdiv(n, 256), 256, 0, s>>>(n, xy, alive, heading, goal, cell, occ, D, F, main_off,
+                                        lo_row, hi_row, hi_off, y_lo, y_hi, g, beta, tb.own,
+                                        tb.dirdot, choice);
+}
+
+// ------------------------------------------------------------ S4: vote
+// Counter-based election priority: SplitMix64 (Steele, Lea, Flood 2014).
+__device__ __forceinline__ uint64_t mix64(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+  return z ^ (z >> 31);
+}
+__device__ __forceinline__ uint64_t splitmix_nth(uint64_t s, uint64_t i) {
+  return mix64(s + i * 0x9e3779b97f4a7c15ULL);
+}
+
+// A mover wins iff no other registrant of its target (a pedestrian on one of
+// the target's 8 neighbours whose choice points at it) has a smaller
+// (priority, id).  Atomic-free: each mover reads the <= 8 competitors.
+__global__ void k_vote(int n, const int2* __restrict__ xy, const uint8_t* __restrict__ alive,
+                       const uint8_t* __restrict__ choice, const int32_t* __restrict__ occ, Geo g,
+                       uint64_t seed, Counters* ctr, uint8_t* __restrict__ won) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  const int k = choice[p];
+  if (!alive[p] || k == 0) {
+    won[p] = 0;
+    return;
+  }
+  const int2 q = xy[p];
+  int tx, ty;
+  wrap_coord(q.x + c_dx[k], g.W, g.px, tx);
+  wrap_coord(q.y + c_dy[k], g.H, g.py, ty);
+  const uint64_t st = splitmix_nth(seed, (uint64_t)ctr->t + 1);
+  const uint64_t mine = splitmix_nth(st, (uint64_t)p + 1);
+  bool win = true;
+  int regs = 1;
+#pragma unroll
+  for (int j = 1; j <= 8; ++j) {
+    int nx, ny;
+    if (!(wrap_coord(tx + c_dx[j], g.W, g.px, nx) & wrap_coord(ty + c_dy[j], g.H, g.py, ny)))
+      continue;
+    const int o = occ[(size_t)ny * g.W + nx];
+    if (o < 0 || o == p) continue;
+    if (choice[o] != c_opp[j]) continue;  // its move does not point at the target
+    ++regs;
+    const uint64_t po = splitmix_nth(st, (uint64_t)o + 1);
+    if (po < mine || (po == mine && o < p)) win = false;
+  }
+  won[p] = win ? 1 : 0;
+  if (regs > 2) atomicMax(&ctr->max_registrants, regs);
+  if (regs > 8) atomicOr(&ctr->err, kErrEnroll);
+}
+
+void launch_vote(int n, const int2* xy, const uint8_t* alive, const uint8_t* choice,
+                 const int32_t* occ, const Geo& g, uint64_t seed, Counters* ctr, uint8_t* won,
+                 cudaStream_t s) {
+  if (n <= 0) return;
+  k_vote<<<cdiv(n, 256), 256, 0, s>>>(n, xy, alive, choice, occ, g, seed, ctr, won);
+}
+
+// ---------------------------------------------------------- S5: commit
+__global__ void k_commit(int n, int2* __restrict__ xy, uint8_t* __restrict__ alive,
+                         uint8_t* __restrict__ heading, const uint8_t* __restrict__ choice,
+                         const uint8_t* __restrict__ won, const uint8_t* __restrict__ cell,
+                         int32_t* __restrict__ occ, uint8_t* __restrict__ ocls, Geo g,
+                         Counters* ctr) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  bool moved = false, left = false;
+  if (p < n && won[p]) {
+    const int k = choice[p];
+    const int2 q = xy[p];
+    int tx, ty;
+    wrap_coord(q.x + c_dx[k], g.W, g.px, tx);
+    wrap_coord(q.y + c_dy[k], g.H, g.py, ty);
+    const size_t c0 = (size_t)q.y * g.W + q.x, c1 = (size_t)ty * g.W + tx;
+    occ[c0] = -1;
+    ocls[c0] = 0;
+    if (cell[c1] == kExit) {
+      alive[p] = 0;
+      left = true;
+    } else {
+      occ[c1] = p;
+      ocls[c1] = (uint8_t)(1 + k);
+    }
+    xy[p] = make_int2(tx, ty);
+    heading[p] = (uint8_t)k;
+    moved = true;
+  }
+  const unsigned nm = __popc(__ballot_sync(0xffffffffu, moved));
+  const unsigned nl = __popc(__ballot_sync(0xffffffffu, left));
+  if ((threadIdx.x & 31) == 0) {
+    if (nm) atomicAdd(&ctr->moved, (unsigned long long)nm);
+    if (nl) atomicAdd(&ctr->exited, (unsigned long long)nl);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) ctr->t += 1;
+}
+
+void launch_commit(int n, int2* xy, uint8_t* alive, uint8_t* heading, const uint8_t* choice,
+                   const uint8_t* won, const uint8_t* cell, int32_t* occ, uint8_t* ocls,
+                   const Geo& g, Counters* ctr, cudaStream_t s) {
+  const int blocks = n > 0 ? cdiv(n, 256) : 1;
+  k_commit<<<blocks, 256, 0, s>>>(n, xy, alive, heading, choice, won, cell, occ, ocls, g, ctr);
+}
+
+}  // namespace sfm

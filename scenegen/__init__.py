@@ -131,7 +131,9 @@ def reachable_mask(cell: np.ndarray, periodic_x: int = 0, periodic_y: int = 0) -
         lab = roots[lab]
     exit_labels = np.unique(lab[cell == EXIT])
     exit_labels = exit_labels[exit_labels > 0]
-    return np.isin(lab, exit_labels) & passable
+    lut = np.zeros(int(lab.max()) + 1, dtype=bool)
+    lut[exit_labels] = True
+    return lut[lab] & passable
 
 
 def place_uniform(rng: np.random.Generator, mask: np.ndarray, n: int) -> np.ndarray:
@@ -194,11 +196,13 @@ def corridor(W=1000, H=200, n=20000, r=20, seed=2, steps=500, name="corridor") -
 
 
 def floor(side=16384, n=1_000_000, r=40, coverage=0.10, exit_len=256, side_min=5,
-          side_max=200, seed=3, steps=200, name="floor") -> Scene:
+          side_max=200, seed=3, steps=200, reachable=False, name="floor") -> Scene:
     """Large floor: wall ring, one exit centred on each wall, random axis-aligned
     rectangular obstacles (integer sides uniform in [side_min, side_max],
     positions uniform, overlap allowed) added until WALL su cover ``coverage``
-    of the area; pedestrians uniform on free su reachable from an exit."""
+    of the area; pedestrians uniform on free su (``reachable=True`` restricts
+    them to su 8-connected to an exit; a pedestrian in a sealed pocket has no
+    guidance pull and moves by the field alone)."""
     rng = np.random.default_rng(seed)
     W = H = side
     cell = wall_ring(W, H)
@@ -218,9 +222,9 @@ def floor(side=16384, n=1_000_000, r=40, coverage=0.10, exit_len=256, side_min=5
                 break
     for s in ("east", "west", "north", "south"):
         add_exit(cell, s, exit_len)
-    # keep each exit's inner neighbour row/column open so the exits are usable
-    reach = reachable_mask(cell)
-    mask = reach & (cell == FREE)
+    mask = cell == FREE
+    if reachable:
+        mask &= reachable_mask(cell)
     xy = place_uniform(rng, mask, n)
     return Scene(name, W, H, 0, 0, cell, xy, np.zeros(n, np.uint8),
                  np.zeros(n, np.uint8), _params(r=r, seed=seed), steps)

@@ -1,0 +1,228 @@
+"""CUDA path vs FP64 oracle, element by element (GPU).
+
+Scenes span several 32x32 tiles with ragged edges, periodic and closed
+boundaries, radii from 0 (no field) to 40 (halo wider than a tile), dense and
+sparse crowds, exit-seekers and fixed-direction walkers.  Each tick the GPU
+restarts from the oracle's own state, so no GPU output ever feeds the oracle.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import paper_1803_04782_gb300 as sfm
+import scenegen as SG
+from paper_1803_04782_gb300 import build as B
+from parity import OracleRun, assert_field, compare_choices
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    B.build()
+    sfm.lib()
+
+
+def _room_mixed():
+    return SG.random_scene(100, 77, 300, r=10, seed=101, obstacles=4, exits=("east", "north"),
+                           goal_mode="mixed", heading_mode="random")
+
+
+def _corridor_periodic():
+    return SG.random_scene(150, 40, 800, r=12, seed=102, periodic_x=1, exits=(),
+                           goal_mode="fixed", heading_mode="goal")
+
+
+def _torus():
+    return SG.random_scene(64, 64, 1000, r=9, seed=103, periodic_x=1, periodic_y=1, ring=False,
+                           exits=(), goal_mode="fixed", heading_mode="random")
+
+
+def _no_field():
+    return SG.random_scene(37, 29, 100, r=0, seed=104, obstacles=2, exits=("west", "south"))
+
+
+def _tall_r1():
+    return SG.random_scene(33, 130, 400, r=1, seed=105, exits=("north",), goal_mode="mixed",
+                           heading_mode="random")
+
+
+def _tiny():
+    return SG.random_scene(5, 5, 4, r=2, seed=106, exits=("east",), exit_len=1,
+                           goal_mode="mixed")
+
+
+def _dense():
+    sc = SG.random_scene(40, 40, 38 * 38 - 2, r=4, seed=107, exits=("east", "west"),
+                         exit_len=6, heading_mode="random")
+    return sc
+
+
+def _wide_radius():
+    return SG.random_scene(200, 150, 2000, r=40, seed=108, obstacles=6, exits=("east",),
+                           exit_len=20, goal_mode="mixed", heading_mode="random")
+
+
+def _thin_torus():
+    # periodic extent exactly 2r+1: a tile's halo wraps around several times
+    return SG.random_scene(11, 50, 120, r=5, seed=109, periodic_x=1, exits=("south",),
+                           goal_mode="mixed", heading_mode="random")
+
+
+SCENES = {f.__name__[1:]: f for f in (_room_mixed, _corridor_periodic, _torus, _no_field,
+                                      _tall_r1, _tiny, _dense, _wide_radius, _thin_torus)}
+
+
+@pytest.mark.parametrize("name", list(SCENES))
+def test_static_field_and_guidance(name):
+    sc = SCENES[name]()
+    orc = OracleRun(sc)
+    occ0 = np.full(sc.W * sc.H, -1, np.int32)
+    Fs, Ss = O.field(orc.m, sc.cell, occ0, np.zeros(1, np.uint8), parts=1)
+    with sfm.Sim(sc) as sim:
+        assert_field(sim.static_field(), Fs, Ss, "static field")
+        np.testing.assert_array_equal(sim.guidance(), orc.D)
+
+
+@pytest.mark.parametrize("name", list(SCENES))
+def test_oracle_forced_ticks(name):
+    sc = SCENES[name]()
+    orc = OracleRun(sc)
+    flips = 0
+    with sfm.Sim(sc) as sim:
+        for _ in range(6):
+            st = orc.st
+            sim.place(st.xy, st.heading, st.goal, st.alive)
+            sim.set_time(st.t)
+            sim.step(1)
+            Fo, So = orc.field()
+            assert_field(sim.field(), Fo, So)
+            ch_o, E, T, adm = orc.decide(Ffull=Fo.ravel(), Sfull=So.ravel())
+            ch_g, won_g = sim.decisions()
+            f = compare_choices(ch_g, ch_o, E, T, adm)
+            xy_g, h_g, a_g = sim.peds()
+            won_o, maxc = orc.advance(ch_o)
+            assert maxc <= 8
+            if f == 0:
+                np.testing.assert_array_equal(won_g, won_o)
+                np.testing.assert_array_equal(xy_g, orc.st.xy)
+                np.testing.assert_array_equal(h_g, orc.st.heading)
+                np.testing.assert_array_equal(a_g, orc.st.alive)
+            flips += f
+            stats = sim.stats()
+            assert stats["error_flags"] == 0 and stats["max_registrants"] <= 8
+    assert flips <= 2, f"{flips} tie flips"
+
+
+def test_free_running_room_100x100_r10_50_ticks():
+    """The 100x100 room with 200 exit-seekers, radius 10, 50 ticks: the GPU
+    runs on its own and must stay identical to the oracle's run."""
+    sc = SG.room()
+    orc = OracleRun(sc)
+    with sfm.Sim(sc) as sim:
+        for t in range(sc.steps):
+            sim.step(1)
+            Fo, So = orc.field()
+            assert_field(sim.field(), Fo, So, f"field at tick {t}")
+            ch_o, E, T, adm = orc.decide(Ffull=Fo.ravel(), Sfull=So.ravel())
+            ch_g, won_g = sim.decisions()
+            assert compare_choices(ch_g, ch_o, E, T, adm) == 0, f"tie flip at tick {t}"
+            orc.advance(ch_o)
+            xy_g, h_g, a_g = sim.peds()
+            np.testing.assert_array_equal(xy_g, orc.st.xy)
+            np.testing.assert_array_equal(a_g, orc.st.alive)
+            np.testing.assert_array_equal(h_g, orc.st.heading)
+        s = sim.stats()
+        assert s["alive"] + s["exited"] == sc.n
+        assert s["exited"] == orc.st.exited
+
+
+@pytest.mark.parametrize("periodic", [0, 1])
+def test_banded_field_is_bitwise_the_unbanded_field(periodic):
+    """Divide-and-conquer (Eq. 1): row bands under an HBM budget give exactly
+    the unbanded field and the same ticks."""
+    sc = SG.random_scene(300, 260, 5000, r=7, seed=111, periodic_x=periodic, periodic_y=periodic,
+                         ring=not periodic, exits=() if periodic else ("east",),
+                         goal_mode="mixed", heading_mode="random")
+    nsu = sc.W * sc.H
+    budget = nsu * 14 + sc.W * 4 * (64 + 2) + 1000
+    with sfm.Sim(sc) as a, sfm.Sim(sc, hbm_budget_bytes=budget) as b:
+        assert b.stats()["bands"] >= 4
+        a.compute_field()
+        np.testing.assert_array_equal(a.field(), b.field_banded())
+        for _ in range(5):
+            a.step(1)
+            b.step(1)
+            np.testing.assert_array_equal(a.decisions()[0], b.decisions()[0])
+            for x, y in zip(a.peds(), b.peds()):
+                np.testing.assert_array_equal(x, y)
+        a.compute_field()
+        np.testing.assert_array_equal(a.field(), b.field_banded())
+
+
+def test_field_respects_heading_linearity_closed_form():
+    """A single pedestrian in an open periodic lattice: the GPU field equals
+    the closed form k d^a (1 + gamma cos) to FP32 rounding."""
+    W = H = 96
+    cell = np.zeros((H, W), np.uint8)
+    for h in range(9):
+        with sfm.Sim(W=W, H=H, cell=cell, periodic_x=1, periodic_y=1, r=30) as sim:
+            sim.place(np.array([[50, 40]], np.int32), np.array([h], np.uint8))
+            sim.compute_field()
+            F = sim.field().astype(np.float64)
+            X, Y = np.meshgrid(np.arange(W), np.arange(H))
+            dx, dy = X - 50, Y - 40
+            d = np.hypot(dx, dy)
+            ux, uy = SG.DIRS[h] / (np.hypot(*SG.DIRS[h]) if h else 1.0)
+            inside = (np.maximum(abs(dx), abs(dy)) <= 30) & (d > 0)
+            ref = np.where(inside, np.where(d > 0, d, 1) ** -0.5 *
+                           (1 + 0.5 * (ux * dx + uy * dy) / np.where(d > 0, d, 1)), 0.0)
+            np.testing.assert_allclose(F, ref, rtol=3e-7, atol=1e-30)
+
+
+def test_placement_errors_and_state_errors():
+    sc = SG.random_scene(40, 30, 10, r=3, seed=120)
+    with sfm.Sim(sc, place=False) as sim:
+        with pytest.raises(sfm.SfmError) as e:
+            sim.step(1)
+        assert e.value.status == sfm.SFM_ESTATE
+        xy = sc.xy.copy()
+        xy[1] = xy[0]
+        with pytest.raises(sfm.SfmError) as e:
+            sim.place(xy)
+        assert e.value.status == sfm.SFM_ECONFLICT
+        xy = sc.xy.copy()
+        xy[0] = (0, 0)                       # on the wall ring
+        with pytest.raises(sfm.SfmError) as e:
+            sim.place(xy)
+        assert e.value.status == sfm.SFM_ECONFLICT
+        xy = sc.xy.copy()
+        xy[0] = (40, 3)                      # off-lattice
+        with pytest.raises(sfm.SfmError) as e:
+            sim.place(xy)
+        assert e.value.status == sfm.SFM_EINVAL
+        with pytest.raises(sfm.SfmError) as e:
+            sim.place(sc.xy, np.full(sc.n, 9, np.uint8))
+        assert e.value.status == sfm.SFM_EINVAL
+        # a rejected placement leaves a clean lattice: a valid one then works
+        sim.place(sc.xy, sc.heading, sc.goal)
+        sim.step(3)
+        assert sim.stats()["error_flags"] == 0
+        # a dead pedestrian may sit anywhere; it is ignored
+        alive = np.ones(sc.n, np.uint8)
+        alive[0] = 0
+        xy = sc.xy.copy()
+        xy[0] = xy[1]
+        sim.place(xy, alive=alive)
+        sim.step(1)
+        ch, won = sim.decisions()
+        assert ch[0] == 0 and won[0] == 0
+
+
+def test_empty_crowd_field_is_static_field():
+    sc = SG.random_scene(70, 50, 0, r=6, seed=121, obstacles=3, exits=("east",))
+    with sfm.Sim(sc) as sim:
+        sim.compute_field()
+        np.testing.assert_array_equal(sim.field(), sim.static_field())
+        sim.step(2)
+        assert sim.stats()["t"] == 2
