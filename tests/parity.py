@@ -40,7 +40,8 @@ def tie_sets(E, T, adm, ch_o):
     Ea = np.where(adm == 1, E, np.inf)
     best = Ea[np.arange(n), ch_o]
     Tb = T[np.arange(n), ch_o]
-    return np.abs(Ea - best[:, None]) <= TIE_RTOL * (T + Tb[:, None])
+    with np.errstate(invalid="ignore"):
+        return np.abs(Ea - best[:, None]) <= TIE_RTOL * (T + Tb[:, None])
 
 
 def compare_choices(ch_gpu, ch_o, E, T, adm):
