@@ -34,6 +34,7 @@ struct sfm_ctx {
   float *T0 = nullptr, *TX = nullptr, *TY = nullptr, *KO = nullptr, *KE = nullptr;
   float *own = nullptr, *dirdot = nullptr;
   float2* hvec = nullptr;
+  float* CT = nullptr;  // heading-class tables of the v2 gather
   // bins
   int32_t *bin_count = nullptr, *bin_start = nullptr, *scan_tmp = nullptr;
   uint32_t* rec = nullptr;
@@ -68,6 +69,7 @@ struct sfm_ctx {
     tb.own = own;
     tb.dirdot = dirdot;
     tb.hvec = hvec;
+    tb.CT = CT;
     return tb;
   }
 };
@@ -172,9 +174,8 @@ sfm_status check_flags(sfm_ctx* ctx) {
 void field_rows(sfm_ctx* c, float* out, int ya, int yb, int main_off, bool halos) {
   const Geo& g = c->geo;
   const Tables tb = c->tables();
-  const int ty0 = ya / kTile, ty1 = (yb + kTile - 1) / kTile;
-  launch_field(g, c->bin_start, c->rec, tb, c->Fs, out, ya - main_off, ty0, ty1, ya, yb,
-               c->ctr, c->stream);
+  launch_field(g, c->bin_start, c->rec, tb, c->Fs, out, ya - main_off, ya, yb, c->ctr,
+               c->stream);
   ++c->launches;
   if (!halos) return;
   int lo = ya - 1, hi = yb;
@@ -183,13 +184,12 @@ void field_rows(sfm_ctx* c, float* out, int ya, int yb, int main_off, bool halos
   if (hi >= g.H) hi -= g.H;
   if (has_lo) {
     // store lattice row `lo` at out row 0
-    launch_field(g, c->bin_start, c->rec, tb, c->Fs, out, lo, lo / kTile, lo / kTile + 1, lo,
-                 lo + 1, c->ctr, c->stream);
+    launch_field(g, c->bin_start, c->rec, tb, c->Fs, out, lo, lo, lo + 1, c->ctr, c->stream);
     ++c->launches;
   }
   if (has_hi) {
-    launch_field(g, c->bin_start, c->rec, tb, c->Fs, out, hi - (yb - ya + 1), hi / kTile,
-                 hi / kTile + 1, hi, hi + 1, c->ctr, c->stream);
+    launch_field(g, c->bin_start, c->rec, tb, c->Fs, out, hi - (yb - ya + 1), hi, hi + 1,
+                 c->ctr, c->stream);
     ++c->launches;
   }
 }
@@ -340,6 +340,7 @@ sfm_status sfm_create(const sfm_lattice* lat, const uint8_t* cell, int32_t cell_
   ALLOC(ctx->own, 81);
   ALLOC(ctx->dirdot, 81);
   ALLOC(ctx->hvec, 9);
+  if (class_table_floats(g.r)) ALLOC(ctx->CT, class_table_floats(g.r));
   ALLOC(ctx->bin_count, (size_t)nbins);
   ALLOC(ctx->bin_start, (size_t)nbins + 1);
   ALLOC(ctx->scan_tmp, (size_t)scan_tmp_elems(nbins));
@@ -358,6 +359,7 @@ sfm_status sfm_create(const sfm_lattice* lat, const uint8_t* cell, int32_t cell_
   cudaMemsetAsync(ctx->ocls, 0, nsu, s);
   launch_tables(g.r, ctx->prm, ctx->T0, ctx->TX, ctx->TY, ctx->KO, ctx->KE, ctx->own, ctx->dirdot,
                 ctx->hvec, s);
+  if (ctx->CT) launch_class_tables(g.r, ctx->prm, ctx->CT, s);
   launch_static_field(g, ctx->cell, ctx->tables(), ctx->Fs, s);
 
   // guidance: relaxation rounds until no tile changes

@@ -19,6 +19,11 @@ constexpr int kRowsPerThread = kTile / (kFieldThreads / 32);  // 4
 constexpr int kStageCap = 2048;    // pedestrians staged in shared memory per chunk
 constexpr int kMaxHaloBins = 128;  // bins touched by one tile's halo (checked)
 constexpr int kBin = 32;           // side of a pedestrian bin (one warp column per su)
+// v2 gather: 32 x 8 su footprint per warp, 32 warps per CTA, table row stride
+// a multiple of 16 up to kMaxV2Stride (radius <= 47)
+constexpr int kV2Rows = 8;
+constexpr int kV2Threads = 1024;
+constexpr int kMaxV2Stride = 96;
 
 // device error flags (sticky until read by a synchronising call)
 enum : uint32_t {
@@ -53,6 +58,7 @@ struct Tables {
   const float* own;     // [9 heading][9 move]: K_P(Delta_move; h)
   const float* dirdot;  // [9 goal][9 move]: Delta_move . u_goal
   const float2* hvec;   // [9]: unit heading vectors
+  const float* CT;      // 4 padded heading-class tables of the v2 gather (or NULL)
 };
 
 // ---- launchers (sfm_kernels.cu) ----
@@ -77,11 +83,15 @@ int scan_tmp_elems(int n);
 void launch_bin_fill(const Geo& g, const uint8_t* ocls, const int32_t* start, uint32_t* rec,
                      cudaStream_t s);
 
-// Field gather over tile rows [ty0, ty1); stores lattice rows y in
-// [store_lo, store_hi) at out[(y - out_row0) * W + x].
+// Field gather; stores lattice rows y in [store_lo, store_hi) at
+// out[(y - out_row0) * W + x].  Every su is summed in the same order whatever
+// the row range, so banded and unbanded passes agree bit for bit.
 void launch_field(const Geo& g, const int32_t* bin_start, const uint32_t* rec, const Tables& tb,
-                  const float* Fs, float* out, int out_row0, int ty0, int ty1, int store_lo,
-                  int store_hi, Counters* ctr, cudaStream_t s);
+                  const float* Fs, float* out, int out_row0, int store_lo, int store_hi,
+                  Counters* ctr, cudaStream_t s);
+int class_table_stride(int r);
+size_t class_table_floats(int r);
+void launch_class_tables(int r, const sfm_params& p, float* T, cudaStream_t s);
 
 void launch_decide(int n, const int2* xy, const uint8_t* alive, const uint8_t* heading,
                    const uint8_t* goal, const uint8_t* cell, const int32_t* occ, const int32_t* D,

@@ -583,9 +583,10 @@ static int field_cap(int r, size_t* smem_out) {
   return cap;
 }
 
-void launch_field(const Geo& g, const int32_t* bin_start, const uint32_t* rec, const Tables& tb,
-                  const float* Fs, float* out, int out_row0, int ty0, int ty1, int store_lo,
-                  int store_hi, Counters* ctr, cudaStream_t s) {
+static void launch_field_v1(const Geo& g, const int32_t* bin_start, const uint32_t* rec,
+                            const Tables& tb, const float* Fs, float* out, int out_row0,
+                            int store_lo, int store_hi, Counters* ctr, cudaStream_t s) {
+  const int ty0 = store_lo / kTile, ty1 = (store_hi + kTile - 1) / kTile;
   if (ty1 <= ty0) return;
   size_t smem;
   const int cap = field_cap(g.r, &smem);
@@ -593,6 +594,251 @@ void launch_field(const Geo& g, const int32_t* bin_start, const uint32_t* rec, c
   dim3 grid(cdiv(g.W, kTile), ty1 - ty0);
   k_field<<<grid, kFieldThreads, smem, s>>>(g, bin_start, rec, tb, Fs, out, out_row0, ty0,
                                             store_lo, store_hi, cap, ctr);
+}
+
+
+// ---------------------------------------------- S2 (v2): persistent warps
+// One warp owns a 32 x 8 su footprint (lane = column, 8 rows per lane) and
+// walks the bins overlapping the footprint's r-halo.  Records are fetched
+// lane-parallel (coalesced, L1-shared by the neighbouring footprints other
+// warps of the SM work on) and broadcast with a shuffle; each (su, pedestrian)
+// pair then costs one shared-memory table read and one FP32 add, because the
+// heading of a pedestrian is one of 9 classes and the kernel of every class
+// is stored precomputed (4 tables, the other 5 classes by x/y mirroring).
+// Tables carry kFieldPad zero rows above and below the window so the 8 rows
+// of a lane need no row test, and a compile-time row stride SP lets the 8
+// reads use immediate offsets.  One CTA of 32 warps per SM loads the tables
+// once for the whole launch.
+constexpr int kFieldPad = kV2Rows - 1;
+
+// class -> (table, x sign, y sign): 0 none, 1 E, 2 N, 3 NE; mirrors cover W, S,
+// NW, SW, SE
+__constant__ int c_ctab[9] = {0, 1, 3, 2, 3, 1, 3, 2, 3};
+__constant__ int c_csx[9] = {1, 1, 1, 1, -1, -1, -1, 1, 1};
+__constant__ int c_csy[9] = {1, 1, 1, 1, 1, 1, -1, -1, -1};
+
+__global__ void k_class_tables(int r, int SP, double kP, double aP, double gamma,
+                               float* __restrict__ T) {
+  const int TR = 2 * r + 1 + 2 * kFieldPad;
+  const int n = 4 * TR * SP;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int t = i / (TR * SP), rem = i % (TR * SP);
+  const int dy = rem / SP - (r + kFieldPad), dx = rem % SP - r;
+  const int adx = dx < 0 ? -dx : dx, ady = dy < 0 ? -dy : dy;
+  double v = 0.0;
+  if (adx <= r && ady <= r && (adx | ady) != 0) {
+    const double hx = (t == 1) ? 1.0 : (t == 3 ? 0.70710678118654752440 : 0.0);
+    const double hy = (t == 2) ? 1.0 : (t == 3 ? 0.70710678118654752440 : 0.0);
+    const double d = sqrt((double)(dx * dx + dy * dy));
+    v = kP * pow(d, aP) * (1.0 + gamma * (hx * dx + hy * dy) / d);
+  }
+  T[i] = (float)v;
+}
+
+int class_table_stride(int r) {
+  const int need = 2 * r + 1;
+  for (int sp = 16; sp <= kMaxV2Stride; sp += 16)
+    if (sp >= need) return sp;
+  return 0;  // radius too large for the v2 gather
+}
+
+size_t class_table_floats(int r) {
+  const int sp = class_table_stride(r);
+  return sp ? (size_t)4 * (2 * r + 1 + 2 * kFieldPad) * sp : 0;
+}
+
+void launch_class_tables(int r, const sfm_params& p, float* T, cudaStream_t s) {
+  const int sp = class_table_stride(r);
+  if (!sp) return;
+  const int n = (int)class_table_floats(r);
+  k_class_tables<<<cdiv(n, 256), 256, 0, s>>>(r, sp, p.kP, p.aP, p.gamma, T);
+}
+
+// Number of (bin, image) entries overlapping [lo, hi] along one dimension.
+__device__ __forceinline__ int halo_count(int lo, int hi, int n, int periodic) {
+  if (!periodic) {
+    lo = max(lo, 0);
+    hi = min(hi, n - 1);
+    return lo > hi ? 0 : hi / kBin - lo / kBin + 1;
+  }
+  const int k0 = floor_div(lo, n), k1 = floor_div(hi, n);
+  int c = 0;
+  for (int k = k0; k <= k1; ++k) {
+    const int a = max(lo - k * n, 0), z = min(hi - k * n, n - 1);
+    if (a <= z) c += z / kBin - a / kBin + 1;
+  }
+  return c;
+}
+
+// i-th entry of that list: bin index and offset of the bin origin (image
+// coordinates) relative to t0.
+__device__ __forceinline__ void halo_entry(int i, int lo, int hi, int n, int periodic, int t0,
+                                           int& bin, int& off) {
+  if (!periodic) {
+    const int b = max(lo, 0) / kBin + i;
+    bin = b;
+    off = b * kBin - t0;
+    return;
+  }
+  const int k0 = floor_div(lo, n), k1 = floor_div(hi, n);
+  bin = 0;
+  off = 0;
+  for (int k = k0; k <= k1; ++k) {
+    const int a = max(lo - k * n, 0), z = min(hi - k * n, n - 1);
+    if (a > z) continue;
+    const int c = z / kBin - a / kBin + 1;
+    if (i < c) {
+      const int b = a / kBin + i;
+      bin = b;
+      off = b * kBin + k * n - t0;
+      return;
+    }
+    i -= c;
+  }
+}
+
+template <int SP>
+__global__ void __launch_bounds__(kV2Threads, 1)
+    k_field_v2(Geo g, const int32_t* __restrict__ bin_start, const uint32_t* __restrict__ rec,
+               const float* __restrict__ CT, const float* __restrict__ Fs,
+               float* __restrict__ out, int out_row0, int fy0, int fy1, int store_lo,
+               int store_hi) {
+  extern __shared__ __align__(16) float sT[];
+  const int r = g.r;
+  const int TR = 2 * r + 1 + 2 * kFieldPad, TS = TR * SP;
+  {
+    const float4* src = reinterpret_cast<const float4*>(CT);
+    float4* dst = reinterpret_cast<float4*>(sT);
+    for (int i = threadIdx.x; i < TS; i += blockDim.x) dst[i] = src[i];  // 4*TS floats
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int wpb = blockDim.x >> 5;
+  const int tw = gridDim.x * wpb;
+  const int nfx = (g.W + 31) >> 5;
+  const int nf = nfx * (fy1 - fy0);
+  for (int f = blockIdx.x * wpb + (threadIdx.x >> 5); f < nf; f += tw) {
+    const int x0 = (f % nfx) << 5, y0 = (fy0 + f / nfx) * kV2Rows;
+    const int x = x0 + lane;
+    float acc[kV2Rows], fs[kV2Rows];
+#pragma unroll
+    for (int j = 0; j < kV2Rows; ++j) {
+      const int y = y0 + j;
+      fs[j] = (x < g.W && y < g.H) ? Fs[(size_t)y * g.W + x] : 0.f;
+      acc[j] = 0.f;
+    }
+    const int xlo = x0 - r, xhi = x0 + 31 + r, ylo = y0 - r, yhi = y0 + kV2Rows - 1 + r;
+    const int nxl = halo_count(xlo, xhi, g.W, g.px);
+    const int ne = nxl * halo_count(ylo, yhi, g.H, g.py);
+    for (int e0 = 0; e0 < ne; e0 += 32) {
+      const int e = e0 + lane;
+      int start = 0, cnt = 0, xoff = 0, yoff = 0;
+      if (e < ne) {
+        int bx, by;
+        halo_entry(e % nxl, xlo, xhi, g.W, g.px, x0, bx, xoff);
+        halo_entry(e / nxl, ylo, yhi, g.H, g.py, y0, by, yoff);
+        const int id = by * g.nbx + bx;
+        start = bin_start[id];
+        cnt = bin_start[id + 1] - start;
+      }
+      int inc = cnt;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += t;
+      }
+      const int total = __shfl_sync(0xffffffffu, inc, 31);
+      const int pre = inc - cnt;
+      for (int q0 = 0; q0 < total; q0 += 32) {
+        const int q = q0 + lane;
+        // entry holding record q: the last lane whose prefix is <= q
+        int lo = 0;
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+          const int p = __shfl_sync(0xffffffffu, pre, lo + step);
+          if (p <= q) lo += step;
+        }
+        const int s_lo = __shfl_sync(0xffffffffu, start, lo);
+        const int p_lo = __shfl_sync(0xffffffffu, pre, lo);
+        const int xo = __shfl_sync(0xffffffffu, xoff, lo);
+        const int yo = __shfl_sync(0xffffffffu, yoff, lo);
+        uint32_t w = 0u;  // decodes to ry = -512: skipped
+        if (q < total) {
+          const uint32_t rc = rec[s_lo + (q - p_lo)];
+          const int rx = xo + (int)(rc & 0xffu), ry = yo + (int)((rc >> 8) & 0xffu);
+          w = (uint32_t)(rx + 512) | ((uint32_t)(ry + 512) << 10) | ((rc >> 16) & 0xfu) << 20;
+        }
+        const int m = min(32, total - q0);
+        for (int j = 0; j < m; ++j) {
+          const uint32_t pw = __shfl_sync(0xffffffffu, w, j);
+          const int ry = (int)((pw >> 10) & 0x3ffu) - 512;
+          if (ry < -r || ry > kV2Rows - 1 + r) continue;  // no row of this footprint in reach
+          const int dx = lane - ((int)(pw & 0x3ffu) - 512);
+          if ((unsigned)(dx + r) > (unsigned)(2 * r)) continue;
+          const int cls = (int)(pw >> 20);
+          const int sy = c_csy[cls];
+          const float* p = sT + c_ctab[cls] * TS + (r + kFieldPad - sy * ry) * SP + c_csx[cls] * dx + r;
+          if (sy > 0) {
+#pragma unroll
+            for (int jj = 0; jj < kV2Rows; ++jj) acc[jj] += p[jj * SP];
+          } else {
+#pragma unroll
+            for (int jj = 0; jj < kV2Rows; ++jj) acc[jj] += p[-jj * SP];
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < kV2Rows; ++j) {
+      const int y = y0 + j;
+      if (x < g.W && y < g.H && y >= store_lo && y < store_hi)
+        out[(size_t)(y - out_row0) * g.W + x] = fs[j] + acc[j];
+    }
+  }
+}
+
+static int g_num_sms = 0;
+
+template <int SP>
+static void launch_v2(const Geo& g, const int32_t* bin_start, const uint32_t* rec, const float* CT,
+                      const float* Fs, float* out, int out_row0, int fy0, int fy1, int store_lo,
+                      int store_hi, cudaStream_t s) {
+  const size_t smem = class_table_floats(g.r) * sizeof(float);
+  cudaFuncSetAttribute(k_field_v2<SP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (!g_num_sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (g_num_sms <= 0) g_num_sms = 1;
+  }
+  const int nf = ((g.W + 31) / 32) * (fy1 - fy0);
+  const int wpb = kV2Threads / 32;
+  int blocks = (nf + wpb - 1) / wpb;
+  if (blocks > g_num_sms) blocks = g_num_sms;
+  if (blocks < 1) blocks = 1;
+  k_field_v2<SP><<<blocks, kV2Threads, smem, s>>>(g, bin_start, rec, CT, Fs, out, out_row0, fy0,
+                                                  fy1, store_lo, store_hi);
+}
+
+void launch_field(const Geo& g, const int32_t* bin_start, const uint32_t* rec, const Tables& tb,
+                  const float* Fs, float* out, int out_row0, int store_lo, int store_hi,
+                  Counters* ctr, cudaStream_t s) {
+  if (store_hi <= store_lo) return;
+  const int sp = tb.CT ? class_table_stride(g.r) : 0;
+  if (!sp) {
+    launch_field_v1(g, bin_start, rec, tb, Fs, out, out_row0, store_lo, store_hi, ctr, s);
+    return;
+  }
+  const int fy0 = store_lo / kV2Rows, fy1 = (store_hi + kV2Rows - 1) / kV2Rows;
+  switch (sp) {
+    case 16: launch_v2<16>(g, bin_start, rec, tb.CT, Fs, out, out_row0, fy0, fy1, store_lo, store_hi, s); break;
+    case 32: launch_v2<32>(g, bin_start, rec, tb.CT, Fs, out, out_row0, fy0, fy1, store_lo, store_hi, s); break;
+    case 48: launch_v2<48>(g, bin_start, rec, tb.CT, Fs, out, out_row0, fy0, fy1, store_lo, store_hi, s); break;
+    case 64: launch_v2<64>(g, bin_start, rec, tb.CT, Fs, out, out_row0, fy0, fy1, store_lo, store_hi, s); break;
+    case 80: launch_v2<80>(g, bin_start, rec, tb.CT, Fs, out, out_row0, fy0, fy1, store_lo, store_hi, s); break;
+    default: launch_v2<96>(g, bin_start, rec, tb.CT, Fs, out, out_row0, fy0, fy1, store_lo, store_hi, s); break;
+  }
 }
 
 // --------------------------------------------------------- S3: decide

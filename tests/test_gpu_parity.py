@@ -69,8 +69,21 @@ def _thin_torus():
                            goal_mode="mixed", heading_mode="random")
 
 
+def _radius47():
+    # largest radius of the shared-memory class-table gather (row stride 96)
+    return SG.random_scene(160, 170, 1500, r=47, seed=110, periodic_y=1, exits=("east",),
+                           goal_mode="mixed", heading_mode="random")
+
+
+def _radius50():
+    # beyond the class-table gather: the three-component gather takes over
+    return SG.random_scene(230, 140, 1200, r=50, seed=112, obstacles=3, exits=("west",),
+                           goal_mode="mixed", heading_mode="random")
+
+
 SCENES = {f.__name__[1:]: f for f in (_room_mixed, _corridor_periodic, _torus, _no_field,
-                                      _tall_r1, _tiny, _dense, _wide_radius, _thin_torus)}
+                                      _tall_r1, _tiny, _dense, _wide_radius, _thin_torus,
+                                      _radius47, _radius50)}
 
 
 @pytest.mark.parametrize("name", list(SCENES))
