@@ -52,12 +52,12 @@ def workload(name: str):
 
 def band_budget(sc, bands: int) -> int:
     """HBM budget that leaves room for about H/bands field rows."""
+    import paper_1803_04782_gb300 as sfm
     if bands <= 1:
         return 0
-    nsu = sc.W * sc.H
     rows = -(-sc.H // bands)
     rows = -(-rows // 32) * 32
-    return nsu * 14 + sc.W * 4 * (rows + 2) + 4096
+    return sfm.band_budget(sc.W, sc.H, rows) + 4096
 
 
 def pair_count(sc, xy, alive) -> int:

@@ -116,6 +116,12 @@ enum {
 /* ABI version compiled into the library. */
 int32_t sfm_abi_version(void);
 
+/* Bytes of the lattice-sized arrays a context keeps resident whatever the
+ * budget (cells, static field, guidance distances, occupancy and its class
+ * grid).  A budget of sfm_resident_bytes(lat) + 4*W*(rows+2) leaves room for
+ * field bands of `rows` rows (rounded down to a multiple of 32). */
+uint64_t sfm_resident_bytes(const sfm_lattice* lat);
+
 /* Create a context for one lattice.  cell: W*H bytes, 0 FREE, 1 WALL,
  * 2 EXIT (host or device per cell_on_device).  Computes the kernel tables,
  * the static field of WALL and EXIT su and the guidance distances on the

@@ -29,7 +29,7 @@ STAGES = ["bin", "field", "decide", "vote", "commit", "step"]
 
 # Exported symbols (kept in step with include/sfm.h; checked by the tests).
 EXPORTS = [
-    "sfm_abi_version", "sfm_create", "sfm_destroy", "sfm_last_error", "sfm_place",
+    "sfm_abi_version", "sfm_resident_bytes", "sfm_create", "sfm_destroy", "sfm_last_error", "sfm_place",
     "sfm_set_time", "sfm_step", "sfm_compute_field", "sfm_sync", "sfm_read_field",
     "sfm_compute_field_into", "sfm_read_static_field", "sfm_read_guidance", "sfm_read_peds",
     "sfm_read_decisions", "sfm_stats", "sfm_set_timing", "sfm_stage_times",
@@ -75,6 +75,7 @@ def lib():
         P, I32, I64 = C.c_void_p, C.c_int32, C.c_int64
         sig = {
             "sfm_abi_version": (I32, []),
+            "sfm_resident_bytes": (C.c_uint64, [C.POINTER(Lattice)]),
             "sfm_create": (C.c_int, [C.POINTER(Lattice), P, I32, C.POINTER(Params), P,
                                      C.POINTER(C.c_void_p)]),
             "sfm_destroy": (None, [P]),
@@ -134,6 +135,16 @@ def _stream_handle(stream):
 # ---------------------------------------------------------------- C-ABI names
 def sfm_abi_version() -> int:
     return lib().sfm_abi_version()
+
+
+def sfm_resident_bytes(lat: Lattice) -> int:
+    return int(lib().sfm_resident_bytes(C.byref(lat)))
+
+
+def band_budget(W: int, H: int, rows: int, periodic_x: int = 0, periodic_y: int = 0) -> int:
+    """HBM budget that makes the field pass run in bands of ``rows`` rows."""
+    lat = Lattice(int(W), int(H), int(periodic_x), int(periodic_y))
+    return sfm_resident_bytes(lat) + 4 * int(W) * (int(rows) + 2)
 
 
 def sfm_create(lat: Lattice, cell, prm: Params, stream=None):

@@ -38,6 +38,7 @@ struct sfm_ctx {
   // bins
   int32_t *bin_count = nullptr, *bin_start = nullptr, *scan_tmp = nullptr;
   uint32_t* rec = nullptr;
+  int32_t* rec_id = nullptr;  // pedestrian of each bin record
   Counters* ctr = nullptr;
   // pedestrians
   int n = 0, cap = 0;
@@ -199,7 +200,7 @@ void run_bins(sfm_ctx* c) {
   const Geo& g = c->geo;
   launch_bin_count(g, c->ocls, c->bin_count, c->stream);
   launch_scan(c->bin_count, c->bin_start, g.nbx * g.nby, c->scan_tmp, c->stream);
-  launch_bin_fill(g, c->ocls, c->bin_start, c->rec, c->stream);
+  launch_bin_fill(g, c->ocls, c->occ, c->bin_start, c->rec, c->rec_id, c->stream);
   c->launches += 5;  // count, three scan passes, fill
 }
 
@@ -207,6 +208,12 @@ void run_tick(sfm_ctx* c) {
   StageScope whole(c, SFM_STAGE_STEP);
   const Geo& g = c->geo;
   const Tables tb = c->tables();
+  const int nbins = g.nbx * g.nby;
+  {
+    StageScope sc(c, SFM_STAGE_BIN);
+    launch_clear_dead(c->n, c->alive, c->choice, c->won, c->stream);
+    if (c->n > 0) ++c->launches;
+  }
   run_bins(c);
   if (c->bands <= 1) {
     {
@@ -214,8 +221,9 @@ void run_tick(sfm_ctx* c) {
       field_rows(c, c->F, 0, g.H, 0, false);
     }
     StageScope sc(c, SFM_STAGE_DECIDE);
-    launch_decide(c->n, c->xy, c->alive, c->heading, c->goal, c->cell, c->occ, c->D, c->F, 0, -1,
-                  -1, 0, 0, g.H, g, c->prm.beta, tb, c->choice, c->stream);
+    launch_decide(c->n, c->rec_id, c->bin_start, 0, nbins, c->xy, c->heading, c->goal, c->cell,
+                  c->occ, c->D, c->F, 0, -1, -1, 0, 0, g.H, g, c->prm.beta, tb, c->choice,
+                  c->stream);
     if (c->n > 0) ++c->launches;
   } else {
     for (int b = 0; b < c->bands; ++b) {
@@ -229,21 +237,22 @@ void run_tick(sfm_ctx* c) {
       if (lo < 0) lo = g.py ? lo + g.H : -1;
       if (hi >= g.H) hi = g.py ? hi - g.H : -1;
       StageScope sc(c, SFM_STAGE_DECIDE);
-      launch_decide(c->n, c->xy, c->alive, c->heading, c->goal, c->cell, c->occ, c->D,
-                    c->band_buf, 1, lo, hi, yb - ya + 1, ya, yb, g, c->prm.beta, tb,
+      launch_decide(c->n, c->rec_id, c->bin_start, (ya / kBin) * g.nbx,
+                    ((yb + kBin - 1) / kBin) * g.nbx, c->xy, c->heading, c->goal, c->cell, c->occ,
+                    c->D, c->band_buf, 1, lo, hi, yb - ya + 1, ya, yb, g, c->prm.beta, tb,
                     c->choice, c->stream);
       if (c->n > 0) ++c->launches;
     }
   }
   {
     StageScope sc(c, SFM_STAGE_VOTE);
-    launch_vote(c->n, c->xy, c->alive, c->choice, c->occ, g, c->prm.seed, c->ctr, c->won,
-                c->stream);
+    launch_vote(c->n, c->rec_id, c->bin_start, c->xy, c->choice, c->occ, g, c->prm.seed, c->ctr,
+                c->won, c->stream);
     if (c->n > 0) ++c->launches;
   }
   StageScope sc(c, SFM_STAGE_COMMIT);
-  launch_commit(c->n, c->xy, c->alive, c->heading, c->choice, c->won, c->cell, c->occ, c->ocls,
-                g, c->ctr, c->stream);
+  launch_commit(c->n, c->rec_id, c->bin_start, c->xy, c->alive, c->heading, c->choice, c->won,
+                c->cell, c->occ, c->ocls, g, c->ctr, c->stream);
   ++c->launches;
 }
 
@@ -258,6 +267,13 @@ sfm_status copy_out(sfm_ctx* ctx, void* dst, const void* src, size_t bytes, int 
 extern "C" {
 
 int32_t sfm_abi_version(void) { return SFM_ABI_VERSION; }
+
+uint64_t sfm_resident_bytes(const sfm_lattice* lat) {
+  if (!lat || lat->W <= 0 || lat->H <= 0) return 0;
+  const uint64_t nsu = (uint64_t)lat->W * lat->H;
+  const uint64_t opitch = ((uint64_t)lat->W + 127) / 128 * 128;
+  return nsu * (1 + 4 + 4 + 4) + opitch * lat->H;
+}
 
 const char* sfm_last_error(const sfm_ctx* ctx) {
   return ctx ? ctx->err.c_str() : g_create_err.c_str();
@@ -290,6 +306,7 @@ sfm_status sfm_create(const sfm_lattice* lat, const uint8_t* cell, int32_t cell_
   g.r = prm->r;
   g.nbx = (g.W + kBin - 1) / kBin;
   g.nby = (g.H + kBin - 1) / kBin;
+  g.opitch = (g.W + 127) / 128 * 128;
   const size_t nsu = (size_t)g.W * g.H;
   const int nbins = g.nbx * g.nby;
   const int S = 2 * g.r + 1;
@@ -300,7 +317,7 @@ sfm_status sfm_create(const sfm_lattice* lat, const uint8_t* cell, int32_t cell_
     return st;
   };
   // resident lattice arrays: cell, static field, guidance, occupancy, class grid
-  const uint64_t resident = (uint64_t)nsu * (1 + 4 + 4 + 4 + 1);
+  const uint64_t resident = sfm_resident_bytes(lat);
   const uint64_t budget = prm->hbm_budget_bytes;
   if (budget && resident + (uint64_t)nsu * 4 > budget) {
     // banded: rows per band from what the budget leaves for the band buffer
@@ -326,7 +343,7 @@ sfm_status sfm_create(const sfm_lattice* lat, const uint8_t* cell, int32_t cell_
   ALLOC(ctx->Fs, nsu);
   ALLOC(ctx->D, nsu);
   ALLOC(ctx->occ, nsu);
-  ALLOC(ctx->ocls, nsu);
+  ALLOC(ctx->ocls, (size_t)g.opitch * g.H);
   if (ctx->bands <= 1) {
     ALLOC(ctx->F, nsu);
   } else {
@@ -356,7 +373,7 @@ sfm_status sfm_create(const sfm_lattice* lat, const uint8_t* cell, int32_t cell_
   }
   cudaMemsetAsync(ctx->ctr, 0, sizeof(Counters), s);
   cudaMemsetAsync(ctx->occ, 0xff, nsu * sizeof(int32_t), s);
-  cudaMemsetAsync(ctx->ocls, 0, nsu, s);
+  cudaMemsetAsync(ctx->ocls, 0, (size_t)g.opitch * g.H, s);
   launch_tables(g.r, ctx->prm, ctx->T0, ctx->TX, ctx->TY, ctx->KO, ctx->KE, ctx->own, ctx->dirdot,
                 ctx->hvec, s);
   if (ctx->CT) launch_class_tables(g.r, ctx->prm, ctx->CT, s);
@@ -438,6 +455,7 @@ sfm_status sfm_place(sfm_ctx* ctx, int32_t n, const int32_t* xy, const uint8_t* 
     dfree(ctx, ctx->choice);
     dfree(ctx, ctx->won);
     dfree(ctx, ctx->rec);
+    dfree(ctx, ctx->rec_id);
     ctx->xy = nullptr;
     ctx->cap = 0;
     TRY(dalloc(ctx, &ctx->xy, (size_t)n));
@@ -447,6 +465,7 @@ sfm_status sfm_place(sfm_ctx* ctx, int32_t n, const int32_t* xy, const uint8_t* 
     TRY(dalloc(ctx, &ctx->choice, (size_t)n));
     TRY(dalloc(ctx, &ctx->won, (size_t)n));
     TRY(dalloc(ctx, &ctx->rec, (size_t)n));
+    TRY(dalloc(ctx, &ctx->rec_id, (size_t)n));
     ctx->cap = n;
   }
   if (ctx->cap == 0) {
@@ -457,6 +476,7 @@ sfm_status sfm_place(sfm_ctx* ctx, int32_t n, const int32_t* xy, const uint8_t* 
     TRY(dalloc(ctx, &ctx->choice, 1));
     TRY(dalloc(ctx, &ctx->won, 1));
     TRY(dalloc(ctx, &ctx->rec, 1));
+    TRY(dalloc(ctx, &ctx->rec_id, 1));
     ctx->cap = 1;
   }
   ctx->placed = false;
@@ -492,7 +512,7 @@ sfm_status sfm_place(sfm_ctx* ctx, int32_t n, const int32_t* xy, const uint8_t* 
     const uint32_t flags = h.err;
     const size_t nsu = (size_t)g.W * g.H;
     cudaMemsetAsync(ctx->occ, 0xff, nsu * sizeof(int32_t), s);
-    cudaMemsetAsync(ctx->ocls, 0, nsu, s);
+    cudaMemsetAsync(ctx->ocls, 0, (size_t)g.opitch * g.H, s);
     h.err = 0;
     cudaMemcpyAsync(ctx->ctr, &h, sizeof(h), cudaMemcpyHostToDevice, s);
     cudaStreamSynchronize(s);

@@ -19,9 +19,9 @@ constexpr int kRowsPerThread = kTile / (kFieldThreads / 32);  // 4
 constexpr int kStageCap = 2048;    // pedestrians staged in shared memory per chunk
 constexpr int kMaxHaloBins = 128;  // bins touched by one tile's halo (checked)
 constexpr int kBin = 32;           // side of a pedestrian bin (one warp column per su)
-// v2 gather: 32 x 8 su footprint per warp, 32 warps per CTA, table row stride
+// v2 gather: 32 x 16 su footprint per warp, 32 warps per CTA, table row stride
 // a multiple of 16 up to kMaxV2Stride (radius <= 47)
-constexpr int kV2Rows = 8;
+constexpr int kV2Rows = 16;
 constexpr int kV2Threads = 1024;
 constexpr int kMaxV2Stride = 96;
 
@@ -47,6 +47,7 @@ struct Geo {
   int W, H, px, py;
   int r;
   int nbx, nby;  // bins per row / column
+  int opitch;    // row pitch (bytes) of the occupancy-class grid, a multiple of 128
 };
 
 struct Tables {
@@ -80,8 +81,12 @@ void launch_place_scatter(int n, const int2* xy, const uint8_t* heading, const u
 void launch_bin_count(const Geo& g, const uint8_t* ocls, int32_t* count, cudaStream_t s);
 void launch_scan(const int32_t* in, int32_t* out, int n, int32_t* block_tmp, cudaStream_t s);
 int scan_tmp_elems(int n);
-void launch_bin_fill(const Geo& g, const uint8_t* ocls, const int32_t* start, uint32_t* rec,
-                     cudaStream_t s);
+// Records of each bin in row-major su order, and the pedestrian id of each
+// record (the per-pedestrian stages walk pedestrians in this spatial order).
+void launch_bin_fill(const Geo& g, const uint8_t* ocls, const int32_t* occ, const int32_t* start,
+                     uint32_t* rec, int32_t* rec_id, cudaStream_t s);
+// choice = won = 0 for pedestrians that are not alive.
+void launch_clear_dead(int n, const uint8_t* alive, uint8_t* choice, uint8_t* won, cudaStream_t s);
 
 // Field gather; stores lattice rows y in [store_lo, store_hi) at
 // out[(y - out_row0) * W + x].  Every su is summed in the same order whatever
@@ -93,16 +98,21 @@ int class_table_stride(int r);
 size_t class_table_floats(int r);
 void launch_class_tables(int r, const sfm_params& p, float* T, cudaStream_t s);
 
-void launch_decide(int n, const int2* xy, const uint8_t* alive, const uint8_t* heading,
-                   const uint8_t* goal, const uint8_t* cell, const int32_t* occ, const int32_t* D,
-                   const float* F, int main_off, int lo_row, int hi_row, int hi_off, int y_lo,
-                   int y_hi, const Geo& g, float beta, const Tables& tb, uint8_t* choice,
+// The per-pedestrian stages visit the live pedestrians of bins [b_lo, b_hi)
+// through rec_id (n bounds the launch).  F rows: lattice rows [y_lo, y_hi) at
+// buffer row (y - y_lo + main_off), lattice row lo_row at buffer row 0 and
+// hi_row at buffer row hi_off.
+void launch_decide(int n, const int32_t* rec_id, const int32_t* bin_start, int b_lo, int b_hi,
+                   const int2* xy, const uint8_t* heading, const uint8_t* goal,
+                   const uint8_t* cell, const int32_t* occ, const int32_t* D, const float* F,
+                   int main_off, int lo_row, int hi_row, int hi_off, int y_lo, int y_hi,
+                   const Geo& g, float beta, const Tables& tb, uint8_t* choice, cudaStream_t s);
+void launch_vote(int n, const int32_t* rec_id, const int32_t* bin_start, const int2* xy,
+                 const uint8_t* choice, const int32_t* occ, const Geo& g, uint64_t seed,
+                 Counters* ctr, uint8_t* won, cudaStream_t s);
+void launch_commit(int n, const int32_t* rec_id, const int32_t* bin_start, int2* xy,
+                   uint8_t* alive, uint8_t* heading, const uint8_t* choice, const uint8_t* won,
+                   const uint8_t* cell, int32_t* occ, uint8_t* ocls, const Geo& g, Counters* ctr,
                    cudaStream_t s);
-void launch_vote(int n, const int2* xy, const uint8_t* alive, const uint8_t* choice,
-                 const int32_t* occ, const Geo& g, uint64_t seed, Counters* ctr, uint8_t* won,
-                 cudaStream_t s);
-void launch_commit(int n, int2* xy, uint8_t* alive, uint8_t* heading, const uint8_t* choice,
-                   const uint8_t* won, const uint8_t* cell, int32_t* occ, uint8_t* ocls,
-                   const Geo& g, Counters* ctr, cudaStream_t s);
 
 }  // namespace sfm

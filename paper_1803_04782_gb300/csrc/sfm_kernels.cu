@@ -235,9 +235,8 @@ __global__ void k_place_clear(int n, const int2* __restrict__ xy, const uint8_t*
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= n || !alive[p]) return;
   const int2 q = xy[p];
-  const size_t c = (size_t)q.y * g.W + q.x;
-  occ[c] = -1;
-  ocls[c] = 0;
+  occ[(size_t)q.y * g.W + q.x] = -1;
+  ocls[(size_t)q.y * g.opitch + q.x] = 0;
 }
 
 __global__ void k_place_scatter(int n, const int2* __restrict__ xy,
@@ -260,7 +259,7 @@ __global__ void k_place_scatter(int n, const int2* __restrict__ xy,
     atomicOr(&ctr->err, kErrPlaceConflict);
     return;
   }
-  ocls[c] = (uint8_t)(1 + (heading[p] > 8 ? 0 : heading[p]));
+  ocls[(size_t)q.y * g.opitch + q.x] = (uint8_t)(1 + (heading[p] > 8 ? 0 : heading[p]));
 }
 
 void launch_place_clear(int n, const int2* xy, const uint8_t* alive, const Geo& g, int32_t* occ,
@@ -280,51 +279,95 @@ void launch_place_scatter(int n, const int2* xy, const uint8_t* heading, const u
 // --------------------------------------------------------- S1: binning
 // Counting sort of the live pedestrians into 32 x 32-su bins, read off the
 // per-su occupancy-class grid so that the order inside a bin is row-major
-// and therefore deterministic.  One warp per bin, lane = bin column.
+// and therefore deterministic.  One warp covers 4 bins side by side (128
+// columns of a 128-byte-pitched grid, 4 bytes per lane) for 32 rows; lanes
+// 8b..8b+7 cover bin b.
+__device__ __forceinline__ int nonzero_bytes(uint32_t v) {
+  return __popc((((v & 0x7f7f7f7fu) + 0x7f7f7f7fu) | v) & 0x80808080u);
+}
+
 __global__ void k_bin_count(Geo g, const uint8_t* __restrict__ ocls, int32_t* __restrict__ count) {
   const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
-  if (wid >= g.nbx * g.nby) return;
-  const int bx = wid % g.nbx, by = wid / g.nbx;
-  const int x = bx * kBin + lane;
+  const int ngx = (g.nbx + 3) >> 2;
+  if (wid >= ngx * g.nby) return;
+  const int gx = wid % ngx, by = wid / ngx;
+  const uint8_t* base = ocls + (size_t)by * kBin * g.opitch + gx * 128 + 4 * lane;
+  const int rows = min(kBin, g.H - by * kBin);
   int c = 0;
-  for (int row = 0; row < kBin; ++row) {
-    const int y = by * kBin + row;
-    if (y >= g.H) break;
-    const bool o = x < g.W && ocls[(size_t)y * g.W + x] != 0;
-    c += __popc(__ballot_sync(0xffffffffu, o));
-  }
-  if (lane == 0) count[wid] = c;
+  for (int row = 0; row < rows; ++row)
+    c += nonzero_bytes(*reinterpret_cast<const uint32_t*>(base + (size_t)row * g.opitch));
+  c += __shfl_xor_sync(0xffffffffu, c, 1);
+  c += __shfl_xor_sync(0xffffffffu, c, 2);
+  c += __shfl_xor_sync(0xffffffffu, c, 4);
+  const int bx = gx * 4 + (lane >> 3);
+  if ((lane & 7) == 0 && bx < g.nbx) count[by * g.nbx + bx] = c;
 }
 
-__global__ void k_bin_fill(Geo g, const uint8_t* __restrict__ ocls,
-                           const int32_t* __restrict__ start, uint32_t* __restrict__ rec) {
+__global__ void k_bin_fill(Geo g, const uint8_t* __restrict__ ocls, const int32_t* __restrict__ occ,
+                           const int32_t* __restrict__ start, uint32_t* __restrict__ rec,
+                           int32_t* __restrict__ rec_id) {
   const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
-  if (wid >= g.nbx * g.nby) return;
-  const int bx = wid % g.nbx, by = wid / g.nbx;
-  const int x = bx * kBin + lane;
-  int off = start[wid];
-  const unsigned lt = (1u << lane) - 1u;
-  for (int row = 0; row < kBin; ++row) {
-    const int y = by * kBin + row;
-    if (y >= g.H) break;
-    const uint8_t v = (x < g.W) ? ocls[(size_t)y * g.W + x] : 0;
-    const unsigned b = __ballot_sync(0xffffffffu, v != 0);
-    if (v) rec[off + __popc(b & lt)] = (uint32_t)lane | ((uint32_t)row << 8) | ((uint32_t)(v - 1) << 16);
-    off += __popc(b);
+  const int ngx = (g.nbx + 3) >> 2;
+  if (wid >= ngx * g.nby) return;
+  const int gx = wid % ngx, by = wid / ngx;
+  const int sub = lane & 7;
+  const int bx = gx * 4 + (lane >> 3);
+  const int x = gx * 128 + 4 * lane;
+  const uint8_t* base = ocls + (size_t)by * kBin * g.opitch + x;
+  const int rows = min(kBin, g.H - by * kBin);
+  int off = bx < g.nbx ? start[by * g.nbx + bx] : 0;
+  for (int row = 0; row < rows; ++row) {
+    const uint32_t v = *reinterpret_cast<const uint32_t*>(base + (size_t)row * g.opitch);
+    const int nz = nonzero_bytes(v);
+    int inc = nz;
+#pragma unroll
+    for (int o = 1; o < 8; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, inc, o, 8);
+      if (sub >= o) inc += t;
+    }
+    const int grp = __shfl_sync(0xffffffffu, inc, 7, 8);
+    if (nz) {
+      int k = off + inc - nz;
+      const int y = by * kBin + row;
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        const uint32_t cls = (v >> (8 * b)) & 0xffu;
+        if (cls) {
+          rec[k] = (uint32_t)(4 * sub + b) | ((uint32_t)row << 8) | ((cls - 1u) << 16);
+          rec_id[k] = occ[(size_t)y * g.W + x + b];
+          ++k;
+        }
+      }
+    }
+    off += grp;
   }
 }
 
 void launch_bin_count(const Geo& g, const uint8_t* ocls, int32_t* count, cudaStream_t s) {
-  const int nb = g.nbx * g.nby;
-  k_bin_count<<<cdiv(nb * 32, 256), 256, 0, s>>>(g, ocls, count);
+  const int nw = ((g.nbx + 3) >> 2) * g.nby;
+  k_bin_count<<<cdiv(nw * 32, 256), 256, 0, s>>>(g, ocls, count);
 }
 
-void launch_bin_fill(const Geo& g, const uint8_t* ocls, const int32_t* start, uint32_t* rec,
-                     cudaStream_t s) {
-  const int nb = g.nbx * g.nby;
-  k_bin_fill<<<cdiv(nb * 32, 256), 256, 0, s>>>(g, ocls, start, rec);
+void launch_bin_fill(const Geo& g, const uint8_t* ocls, const int32_t* occ, const int32_t* start,
+                     uint32_t* rec, int32_t* rec_id, cudaStream_t s) {
+  const int nw = ((g.nbx + 3) >> 2) * g.nby;
+  k_bin_fill<<<cdiv(nw * 32, 256), 256, 0, s>>>(g, ocls, occ, start, rec, rec_id);
+}
+
+__global__ void k_clear_dead(int n, const uint8_t* __restrict__ alive, uint8_t* __restrict__ choice,
+                             uint8_t* __restrict__ won) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < n && !alive[p]) {
+    choice[p] = 0;
+    won[p] = 0;
+  }
+}
+
+void launch_clear_dead(int n, const uint8_t* alive, uint8_t* choice, uint8_t* won, cudaStream_t s) {
+  if (n <= 0) return;
+  k_clear_dead<<<cdiv(n, 256), 256, 0, s>>>(n, alive, choice, won);
 }
 
 // ------------------------------------------------------------------ scan
@@ -598,17 +641,19 @@ static void launch_field_v1(const Geo& g, const int32_t* bin_start, const uint32
 
 
 // ---------------------------------------------- S2 (v2): persistent warps
-// One warp owns a 32 x 8 su footprint (lane = column, 8 rows per lane) and
-// walks the bins overlapping the footprint's r-halo.  Records are fetched
-// lane-parallel (coalesced, L1-shared by the neighbouring footprints other
-// warps of the SM work on) and broadcast with a shuffle; each (su, pedestrian)
-// pair then costs one shared-memory table read and one FP32 add, because the
-// heading of a pedestrian is one of 9 classes and the kernel of every class
-// is stored precomputed (4 tables, the other 5 classes by x/y mirroring).
-// Tables carry kFieldPad zero rows above and below the window so the 8 rows
-// of a lane need no row test, and a compile-time row stride SP lets the 8
-// reads use immediate offsets.  One CTA of 32 warps per SM loads the tables
-// once for the whole launch.
+// One warp owns a 32 x 16 su footprint (lane = column, 16 rows per lane) and
+// walks the bins overlapping the footprint's r-halo in batches of 32
+// records, fetched lane-parallel (coalesced, L1-shared by the neighbouring
+// footprints other warps of the SM work on).  Each lane screens its record,
+// precomputes its table offset and lane range, and the records in reach are
+// compacted into a per-warp shared-memory scratch read back by broadcast.
+// Each (su, pedestrian) pair then costs one shared-memory table read and one
+// FP32 add, because the heading of a pedestrian is one of 9 classes and the
+// kernel of every class is stored precomputed (4 tables, the other 5 classes
+// by x/y mirroring).  Tables carry kFieldPad zero rows above and below the
+// window so the 16 rows of a lane need no row test, and a compile-time row
+// stride SP lets the 16 reads use immediate offsets.  One CTA of 32 warps per
+// SM loads the tables once for the whole launch.
 constexpr int kFieldPad = kV2Rows - 1;
 
 // class -> (table, x sign, y sign): 0 none, 1 E, 2 N, 3 NE; mirrors cover W, S,
@@ -707,27 +752,26 @@ __global__ void __launch_bounds__(kV2Threads, 1)
   extern __shared__ __align__(16) float sT[];
   const int r = g.r;
   const int TR = 2 * r + 1 + 2 * kFieldPad, TS = TR * SP;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // per-warp scratch: the batch's pedestrians in reach of the footprint, as
+  // (table offset of lane 0's first row, lane range | mirror bits)
+  int2* scr = reinterpret_cast<int2*>(sT + 4 * TS) + warp * 32;
   {
     const float4* src = reinterpret_cast<const float4*>(CT);
     float4* dst = reinterpret_cast<float4*>(sT);
     for (int i = threadIdx.x; i < TS; i += blockDim.x) dst[i] = src[i];  // 4*TS floats
   }
   __syncthreads();
-  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
   const int wpb = blockDim.x >> 5;
   const int tw = gridDim.x * wpb;
   const int nfx = (g.W + 31) >> 5;
   const int nf = nfx * (fy1 - fy0);
-  for (int f = blockIdx.x * wpb + (threadIdx.x >> 5); f < nf; f += tw) {
+  for (int f = blockIdx.x * wpb + warp; f < nf; f += tw) {
     const int x0 = (f % nfx) << 5, y0 = (fy0 + f / nfx) * kV2Rows;
-    const int x = x0 + lane;
-    float acc[kV2Rows], fs[kV2Rows];
+    float acc[kV2Rows];
 #pragma unroll
-    for (int j = 0; j < kV2Rows; ++j) {
-      const int y = y0 + j;
-      fs[j] = (x < g.W && y < g.H) ? Fs[(size_t)y * g.W + x] : 0.f;
-      acc[j] = 0.f;
-    }
+    for (int j = 0; j < kV2Rows; ++j) acc[j] = 0.f;
     const int xlo = x0 - r, xhi = x0 + 31 + r, ylo = y0 - r, yhi = y0 + kV2Rows - 1 + r;
     const int nxl = halo_count(xlo, xhi, g.W, g.px);
     const int ne = nxl * halo_count(ylo, yhi, g.H, g.py);
@@ -763,37 +807,50 @@ __global__ void __launch_bounds__(kV2Threads, 1)
         const int p_lo = __shfl_sync(0xffffffffu, pre, lo);
         const int xo = __shfl_sync(0xffffffffu, xoff, lo);
         const int yo = __shfl_sync(0xffffffffu, yoff, lo);
-        uint32_t w = 0u;  // decodes to ry = -512: skipped
+        bool keep = false;
+        int2 item = make_int2(0, 0);
         if (q < total) {
           const uint32_t rc = rec[s_lo + (q - p_lo)];
           const int rx = xo + (int)(rc & 0xffu), ry = yo + (int)((rc >> 8) & 0xffu);
-          w = (uint32_t)(rx + 512) | ((uint32_t)(ry + 512) << 10) | ((rc >> 16) & 0xfu) << 20;
-        }
-        const int m = min(32, total - q0);
-        for (int j = 0; j < m; ++j) {
-          const uint32_t pw = __shfl_sync(0xffffffffu, w, j);
-          const int ry = (int)((pw >> 10) & 0x3ffu) - 512;
-          if (ry < -r || ry > kV2Rows - 1 + r) continue;  // no row of this footprint in reach
-          const int dx = lane - ((int)(pw & 0x3ffu) - 512);
-          if ((unsigned)(dx + r) > (unsigned)(2 * r)) continue;
-          const int cls = (int)(pw >> 20);
-          const int sy = c_csy[cls];
-          const float* p = sT + c_ctab[cls] * TS + (r + kFieldPad - sy * ry) * SP + c_csx[cls] * dx + r;
-          if (sy > 0) {
-#pragma unroll
-            for (int jj = 0; jj < kV2Rows; ++jj) acc[jj] += p[jj * SP];
-          } else {
-#pragma unroll
-            for (int jj = 0; jj < kV2Rows; ++jj) acc[jj] += p[-jj * SP];
+          const int cls = (int)((rc >> 16) & 0xfu);
+          // some row of the footprint and some lane within the window
+          keep = ry >= -r && ry <= kV2Rows - 1 + r && rx >= -r && rx <= 31 + r;
+          if (keep) {
+            const int sx = c_csx[cls], sy = c_csy[cls];
+            const int llo = max(0, rx - r), lhi = min(31, rx + r);
+            item.x = c_ctab[cls] * TS + (r + kFieldPad - sy * ry) * SP + r - sx * rx;
+            item.y = llo | (lhi << 5) | (sx < 0 ? 1024 : 0) | (sy < 0 ? 2048 : 0);
           }
         }
+        const unsigned bal = __ballot_sync(0xffffffffu, keep);
+        if (keep) scr[__popc(bal & lt)] = item;
+        __syncwarp();
+        const int m = __popc(bal);
+        for (int j = 0; j < m; ++j) {
+          const int2 it = scr[j];
+          const int llo = it.y & 31, lhi = (it.y >> 5) & 31;
+          if (lane >= llo && lane <= lhi) {
+            const float* p = sT + it.x + ((it.y & 1024) ? -lane : lane);
+            if (it.y & 2048) {
+#pragma unroll
+              for (int jj = 0; jj < kV2Rows; ++jj) acc[jj] += p[-jj * SP];
+            } else {
+#pragma unroll
+              for (int jj = 0; jj < kV2Rows; ++jj) acc[jj] += p[jj * SP];
+            }
+          }
+        }
+        __syncwarp();
       }
     }
+    const int x = x0 + lane;
 #pragma unroll
     for (int j = 0; j < kV2Rows; ++j) {
       const int y = y0 + j;
-      if (x < g.W && y < g.H && y >= store_lo && y < store_hi)
-        out[(size_t)(y - out_row0) * g.W + x] = fs[j] + acc[j];
+      if (x < g.W && y < g.H && y >= store_lo && y < store_hi) {
+        const size_t c = (size_t)y * g.W + x;
+        out[(size_t)(y - out_row0) * g.W + x] = Fs[c] + acc[j];
+      }
     }
   }
 }
@@ -804,7 +861,7 @@ template <int SP>
 static void launch_v2(const Geo& g, const int32_t* bin_start, const uint32_t* rec, const float* CT,
                       const float* Fs, float* out, int out_row0, int fy0, int fy1, int store_lo,
                       int store_hi, cudaStream_t s) {
-  const size_t smem = class_table_floats(g.r) * sizeof(float);
+  const size_t smem = class_table_floats(g.r) * sizeof(float) + kV2Threads / 32 * 32 * sizeof(int2);
   cudaFuncSetAttribute(k_field_v2<SP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (!g_num_sms) {
     int dev = 0;
@@ -842,24 +899,22 @@ void launch_field(const Geo& g, const int32_t* bin_start, const uint32_t* rec, c
 }
 
 // --------------------------------------------------------- S3: decide
-// Per pedestrian: E over the 9 candidates (stay + 8 neighbours), admissible
-// iff inside, not WALL and unoccupied at tick start; branch-free select of the
-// minimum with ties to the smallest class.
-__global__ void k_decide(int n, const int2* __restrict__ xy, const uint8_t* __restrict__ alive,
+// Per live pedestrian (visited in bin order, so neighbouring threads read
+// neighbouring su): E over the 9 candidates (stay + 8 neighbours), admissible
+// iff inside, not WALL and unoccupied at tick start; select of the minimum
+// with ties to the smallest class.
+__global__ void k_decide(const int32_t* __restrict__ rec_id, const int32_t* __restrict__ bin_start,
+                         int b_lo, int b_hi, const int2* __restrict__ xy,
                          const uint8_t* __restrict__ heading, const uint8_t* __restrict__ goal,
                          const uint8_t* __restrict__ cell, const int32_t* __restrict__ occ,
                          const int32_t* __restrict__ D, const float* __restrict__ F, int main_off,
                          int lo_row, int hi_row, int hi_off, int y_lo, int y_hi, Geo g,
                          float beta, const float* __restrict__ own,
                          const float* __restrict__ dirdot, uint8_t* __restrict__ choice) {
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= n) return;
+  const int i = bin_start[b_lo] + blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= bin_start[b_hi]) return;
+  const int p = rec_id[i];
   const int2 q = xy[p];
-  if (q.y < y_lo || q.y >= y_hi) return;
-  if (!alive[p]) {
-    choice[p] = 0;
-    return;
-  }
   const int h = heading[p], gl = goal[p];
   const int32_t d0 = D[(size_t)q.y * g.W + q.x];
   int best = 0;
@@ -886,15 +941,15 @@ __global__ void k_decide(int n, const int2* __restrict__ xy, const uint8_t* __re
   choice[p] = (uint8_t)best;
 }
 
-void launch_decide(int n, const int2* xy, const uint8_t* alive, const uint8_t* heading,
-                   const uint8_t* goal, const uint8_t* cell, const int32_t* occ, const int32_t* D,
-                   const float* F, int main_off, int lo_row, int hi_row, int hi_off, int y_lo,
-                   int y_hi, const Geo& g, float beta, const Tables& tb, uint8_t* choice,
-                   cudaStream_t s) {
-  if (n <= 0) return;
-  k_decide<<<cdiv(n, 256), 256, 0, s>>>(n, xy, alive, heading, goal, cell, occ, D, F, main_off,
-                                        lo_row, hi_row, hi_off, y_lo, y_hi, g, beta, tb.own,
-                                        tb.dirdot, choice);
+void launch_decide(int n, const int32_t* rec_id, const int32_t* bin_start, int b_lo, int b_hi,
+                   const int2* xy, const uint8_t* heading, const uint8_t* goal,
+                   const uint8_t* cell, const int32_t* occ, const int32_t* D, const float* F,
+                   int main_off, int lo_row, int hi_row, int hi_off, int y_lo, int y_hi,
+                   const Geo& g, float beta, const Tables& tb, uint8_t* choice, cudaStream_t s) {
+  if (n <= 0 || b_hi <= b_lo) return;
+  k_decide<<<cdiv(n, 256), 256, 0, s>>>(rec_id, bin_start, b_lo, b_hi, xy, heading, goal, cell,
+                                        occ, D, F, main_off, lo_row, hi_row, hi_off, y_lo, y_hi,
+                                        g, beta, tb.own, tb.dirdot, choice);
 }
 
 // ------------------------------------------------------------ S4: vote
@@ -911,13 +966,15 @@ __device__ __forceinline__ uint64_t splitmix_nth(uint64_t s, uint64_t i) {
 // A mover wins iff no other registrant of its target (a pedestrian on one of
 // the target's 8 neighbours whose choice points at it) has a smaller
 // (priority, id).  Atomic-free: each mover reads the <= 8 competitors.
-__global__ void k_vote(int n, const int2* __restrict__ xy, const uint8_t* __restrict__ alive,
-                       const uint8_t* __restrict__ choice, const int32_t* __restrict__ occ, Geo g,
-                       uint64_t seed, Counters* ctr, uint8_t* __restrict__ won) {
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= n) return;
+__global__ void k_vote(const int32_t* __restrict__ rec_id, const int32_t* __restrict__ bin_start,
+                       int nbins, const int2* __restrict__ xy, const uint8_t* __restrict__ choice,
+                       const int32_t* __restrict__ occ, Geo g, uint64_t seed, Counters* ctr,
+                       uint8_t* __restrict__ won) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= bin_start[nbins]) return;
+  const int p = rec_id[i];
   const int k = choice[p];
-  if (!alive[p] || k == 0) {
+  if (k == 0) {
     won[p] = 0;
     return;
   }
@@ -946,22 +1003,25 @@ __global__ void k_vote(int n, const int2* __restrict__ xy, const uint8_t* __rest
   if (regs > 8) atomicOr(&ctr->err, kErrEnroll);
 }
 
-void launch_vote(int n, const int2* xy, const uint8_t* alive, const uint8_t* choice,
-                 const int32_t* occ, const Geo& g, uint64_t seed, Counters* ctr, uint8_t* won,
-                 cudaStream_t s) {
+void launch_vote(int n, const int32_t* rec_id, const int32_t* bin_start, const int2* xy,
+                 const uint8_t* choice, const int32_t* occ, const Geo& g, uint64_t seed,
+                 Counters* ctr, uint8_t* won, cudaStream_t s) {
   if (n <= 0) return;
-  k_vote<<<cdiv(n, 256), 256, 0, s>>>(n, xy, alive, choice, occ, g, seed, ctr, won);
+  k_vote<<<cdiv(n, 256), 256, 0, s>>>(rec_id, bin_start, g.nbx * g.nby, xy, choice, occ, g, seed,
+                                      ctr, won);
 }
 
 // ---------------------------------------------------------- S5: commit
-__global__ void k_commit(int n, int2* __restrict__ xy, uint8_t* __restrict__ alive,
+__global__ void k_commit(const int32_t* __restrict__ rec_id, const int32_t* __restrict__ bin_start,
+                         int nbins, int2* __restrict__ xy, uint8_t* __restrict__ alive,
                          uint8_t* __restrict__ heading, const uint8_t* __restrict__ choice,
                          const uint8_t* __restrict__ won, const uint8_t* __restrict__ cell,
                          int32_t* __restrict__ occ, uint8_t* __restrict__ ocls, Geo g,
                          Counters* ctr) {
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int p = i < bin_start[nbins] ? rec_id[i] : -1;
   bool moved = false, left = false;
-  if (p < n && won[p]) {
+  if (p >= 0 && won[p]) {
     const int k = choice[p];
     const int2 q = xy[p];
     int tx, ty;
@@ -969,13 +1029,13 @@ __global__ void k_commit(int n, int2* __restrict__ xy, uint8_t* __restrict__ ali
     wrap_coord(q.y + c_dy[k], g.H, g.py, ty);
     const size_t c0 = (size_t)q.y * g.W + q.x, c1 = (size_t)ty * g.W + tx;
     occ[c0] = -1;
-    ocls[c0] = 0;
+    ocls[(size_t)q.y * g.opitch + q.x] = 0;
     if (cell[c1] == kExit) {
       alive[p] = 0;
       left = true;
     } else {
       occ[c1] = p;
-      ocls[c1] = (uint8_t)(1 + k);
+      ocls[(size_t)ty * g.opitch + tx] = (uint8_t)(1 + k);
     }
     xy[p] = make_int2(tx, ty);
     heading[p] = (uint8_t)k;
@@ -990,11 +1050,13 @@ __global__ void k_commit(int n, int2* __restrict__ xy, uint8_t* __restrict__ ali
   if (blockIdx.x == 0 && threadIdx.x == 0) ctr->t += 1;
 }
 
-void launch_commit(int n, int2* xy, uint8_t* alive, uint8_t* heading, const uint8_t* choice,
-                   const uint8_t* won, const uint8_t* cell, int32_t* occ, uint8_t* ocls,
-                   const Geo& g, Counters* ctr, cudaStream_t s) {
+void launch_commit(int n, const int32_t* rec_id, const int32_t* bin_start, int2* xy,
+                   uint8_t* alive, uint8_t* heading, const uint8_t* choice, const uint8_t* won,
+                   const uint8_t* cell, int32_t* occ, uint8_t* ocls, const Geo& g, Counters* ctr,
+                   cudaStream_t s) {
   const int blocks = n > 0 ? cdiv(n, 256) : 1;
-  k_commit<<<blocks, 256, 0, s>>>(n, xy, alive, heading, choice, won, cell, occ, ocls, g, ctr);
+  k_commit<<<blocks, 256, 0, s>>>(rec_id, bin_start, g.nbx * g.nby, xy, alive, heading, choice,
+                                  won, cell, occ, ocls, g, ctr);
 }
 
 }  // namespace sfm

@@ -81,3 +81,11 @@ def test_create_rejects_bad_arguments_before_touching_the_gpu():
             sfm.sfm_create(L, cell, sfm.make_params(**prm))
         assert e.value.status == sfm.SFM_EINVAL
         assert msg in str(e.value)
+
+
+def test_resident_bytes_and_band_budget():
+    lat = sfm.Lattice(100, 77, 0, 0)
+    assert sfm.sfm_resident_bytes(lat) == 100 * 77 * 13 + 128 * 77
+    lat = sfm.Lattice(16384, 16384, 0, 0)
+    assert sfm.sfm_resident_bytes(lat) == 16384 * 16384 * 14
+    assert sfm.band_budget(16384, 16384, 4096) == 16384 * 16384 * 14 + 4 * 16384 * 4098

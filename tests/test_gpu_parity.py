@@ -161,8 +161,7 @@ def test_banded_field_is_bitwise_the_unbanded_field(periodic):
     sc = SG.random_scene(300, 260, 5000, r=7, seed=111, periodic_x=periodic, periodic_y=periodic,
                          ring=not periodic, exits=() if periodic else ("east",),
                          goal_mode="mixed", heading_mode="random")
-    nsu = sc.W * sc.H
-    budget = nsu * 14 + sc.W * 4 * (64 + 2) + 1000
+    budget = sfm.band_budget(sc.W, sc.H, 64)
     with sfm.Sim(sc) as a, sfm.Sim(sc, hbm_budget_bytes=budget) as b:
         assert b.stats()["bands"] >= 4
         a.compute_field()
