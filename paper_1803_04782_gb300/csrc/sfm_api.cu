@@ -175,22 +175,27 @@ sfm_status check_flags(sfm_ctx* ctx) {
 void field_rows(sfm_ctx* c, float* out, int ya, int yb, int main_off, bool halos) {
   const Geo& g = c->geo;
   const Tables tb = c->tables();
-  launch_field(g, c->bin_start, c->rec, tb, c->Fs, out, ya - main_off, ya, yb, c->ctr,
+  if (!halos) {
+    launch_field(g, c->bin_start, c->rec, tb, c->Fs, out, ya - main_off, ya, yb, c->ctr,
+                 c->stream);
+    ++c->launches;
+    return;
+  }
+  // one launch for the band and its in-lattice halo rows ya-1 and yb (out rows
+  // 0 and yb-ya+1 follow from the same row mapping, main_off == 1)
+  const int lo = ya - 1 >= 0 ? ya - 1 : 0, hi = yb + 1 <= g.H ? yb + 1 : g.H;
+  launch_field(g, c->bin_start, c->rec, tb, c->Fs, out, ya - main_off, lo, hi, c->ctr,
                c->stream);
   ++c->launches;
-  if (!halos) return;
-  int lo = ya - 1, hi = yb;
-  bool has_lo = lo >= 0 || g.py, has_hi = hi < g.H || g.py;
-  if (lo < 0) lo += g.H;
-  if (hi >= g.H) hi -= g.H;
-  if (has_lo) {
-    // store lattice row `lo` at out row 0
-    launch_field(g, c->bin_start, c->rec, tb, c->Fs, out, lo, lo, lo + 1, c->ctr, c->stream);
+  // halo rows that wrap around a periodic y boundary
+  if (g.py && ya == 0) {
+    launch_field(g, c->bin_start, c->rec, tb, c->Fs, out, g.H - 1, g.H - 1, g.H, c->ctr,
+                 c->stream);
     ++c->launches;
   }
-  if (has_hi) {
-    launch_field(g, c->bin_start, c->rec, tb, c->Fs, out, hi - (yb - ya + 1), hi, hi + 1,
-                 c->ctr, c->stream);
+  if (g.py && yb == g.H) {
+    launch_field(g, c->bin_start, c->rec, tb, c->Fs, out, -(yb - ya + 1), 0, 1, c->ctr,
+                 c->stream);
     ++c->launches;
   }
 }
@@ -222,7 +227,7 @@ void run_tick(sfm_ctx* c) {
     }
     StageScope sc(c, SFM_STAGE_DECIDE);
     launch_decide(c->n, c->rec_id, c->bin_start, 0, nbins, c->xy, c->heading, c->goal, c->cell,
-                  c->occ, c->D, c->F, 0, -1, -1, 0, 0, g.H, g, c->prm.beta, tb, c->choice,
+                  c->ocls, c->D, c->F, 0, -1, -1, 0, 0, g.H, g, c->prm.beta, tb, c->choice,
                   c->stream);
     if (c->n > 0) ++c->launches;
   } else {
@@ -238,7 +243,7 @@ void run_tick(sfm_ctx* c) {
       if (hi >= g.H) hi = g.py ? hi - g.H : -1;
       StageScope sc(c, SFM_STAGE_DECIDE);
       launch_decide(c->n, c->rec_id, c->bin_start, (ya / kBin) * g.nbx,
-                    ((yb + kBin - 1) / kBin) * g.nbx, c->xy, c->heading, c->goal, c->cell, c->occ,
+                    ((yb + kBin - 1) / kBin) * g.nbx, c->xy, c->heading, c->goal, c->cell, c->ocls,
                     c->D, c->band_buf, 1, lo, hi, yb - ya + 1, ya, yb, g, c->prm.beta, tb,
                     c->choice, c->stream);
       if (c->n > 0) ++c->launches;

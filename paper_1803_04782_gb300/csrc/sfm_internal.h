@@ -104,7 +104,7 @@ void launch_class_tables(int r, const sfm_params& p, float* T, cudaStream_t s);
 // hi_row at buffer row hi_off.
 void launch_decide(int n, const int32_t* rec_id, const int32_t* bin_start, int b_lo, int b_hi,
                    const int2* xy, const uint8_t* heading, const uint8_t* goal,
-                   const uint8_t* cell, const int32_t* occ, const int32_t* D, const float* F,
+                   const uint8_t* cell, const uint8_t* ocls, const int32_t* D, const float* F,
                    int main_off, int lo_row, int hi_row, int hi_off, int y_lo, int y_hi,
                    const Geo& g, float beta, const Tables& tb, uint8_t* choice, cudaStream_t s);
 void launch_vote(int n, const int32_t* rec_id, const int32_t* bin_start, const int2* xy,

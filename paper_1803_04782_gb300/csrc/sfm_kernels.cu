@@ -906,7 +906,7 @@ void launch_field(const Geo& g, const int32_t* bin_start, const uint32_t* rec, c
 __global__ void k_decide(const int32_t* __restrict__ rec_id, const int32_t* __restrict__ bin_start,
                          int b_lo, int b_hi, const int2* __restrict__ xy,
                          const uint8_t* __restrict__ heading, const uint8_t* __restrict__ goal,
-                         const uint8_t* __restrict__ cell, const int32_t* __restrict__ occ,
+                         const uint8_t* __restrict__ cell, const uint8_t* __restrict__ ocls,
                          const int32_t* __restrict__ D, const float* __restrict__ F, int main_off,
                          int lo_row, int hi_row, int hi_off, int y_lo, int y_hi, Geo g,
                          float beta, const float* __restrict__ own,
@@ -916,24 +916,41 @@ __global__ void k_decide(const int32_t* __restrict__ rec_id, const int32_t* __re
   const int p = rec_id[i];
   const int2 q = xy[p];
   const int h = heading[p], gl = goal[p];
-  const int32_t d0 = D[(size_t)q.y * g.W + q.x];
+  // the 3 x 3 neighbourhood: rows and columns (wrapped or clipped), then every
+  // load issued before any use so the 36 reads overlap
+  int cx[3], ry[3], fr[3];
+  bool okx[3], oky[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    okx[d] = wrap_coord(q.x + d - 1, g.W, g.px, cx[d]);
+    oky[d] = wrap_coord(q.y + d - 1, g.H, g.py, ry[d]);
+    if (!okx[d]) cx[d] = q.x;
+    if (!oky[d]) ry[d] = q.y;
+    const int ny = ry[d];
+    fr[d] = (ny >= y_lo && ny < y_hi) ? ny - y_lo + main_off
+                                      : (ny == lo_row ? 0 : (ny == hi_row ? hi_off : 0));
+  }
+  float f[9];
+  int32_t dd[9];
+  uint8_t cl[9], oc[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    const int xi = c_dx[k] + 1, yi = c_dy[k] + 1;
+    const size_t c = (size_t)ry[yi] * g.W + cx[xi];
+    f[k] = F[(size_t)fr[yi] * g.W + cx[xi]];
+    dd[k] = D[c];
+    cl[k] = cell[c];
+    oc[k] = ocls[(size_t)ry[yi] * g.opitch + cx[xi]];
+  }
   int best = 0;
   float bestE = 0.f;
 #pragma unroll
   for (int k = 0; k < 9; ++k) {
-    int nx, ny;
-    const bool in = wrap_coord(q.x + c_dx[k], g.W, g.px, nx) & wrap_coord(q.y + c_dy[k], g.H, g.py, ny);
-    if (!in) continue;
-    const size_t c = (size_t)ny * g.W + nx;
-    if (k > 0 && (cell[c] == kWall || occ[c] >= 0)) continue;
-    // row of the field buffer holding lattice row ny: the band's own rows,
-    // or one of its two single halo rows
-    const int frow = (ny >= y_lo && ny < y_hi) ? ny - y_lo + main_off
-                                               : (ny == lo_row ? 0 : (ny == hi_row ? hi_off : 0));
-    const float f = F[(size_t)frow * g.W + nx];
-    const float guide = (gl == 0) ? beta * ((float)(D[c] - d0) / 5.0f) : -beta * dirdot[gl * 9 + k];
-    const float e = f - own[h * 9 + k] + guide;
-    if (k == 0 || e < bestE) {
+    const int xi = c_dx[k] + 1, yi = c_dy[k] + 1;
+    const bool adm = (k == 0) || (okx[xi] && oky[yi] && cl[k] != kWall && oc[k] == 0);
+    const float guide = (gl == 0) ? beta * ((float)(dd[k] - dd[0]) / 5.0f) : -beta * dirdot[gl * 9 + k];
+    const float e = f[k] - own[h * 9 + k] + guide;
+    if (adm && (k == 0 || e < bestE)) {
       best = k;
       bestE = e;
     }
@@ -943,12 +960,12 @@ __global__ void k_decide(const int32_t* __restrict__ rec_id, const int32_t* __re
 
 void launch_decide(int n, const int32_t* rec_id, const int32_t* bin_start, int b_lo, int b_hi,
                    const int2* xy, const uint8_t* heading, const uint8_t* goal,
-                   const uint8_t* cell, const int32_t* occ, const int32_t* D, const float* F,
+                   const uint8_t* cell, const uint8_t* ocls, const int32_t* D, const float* F,
                    int main_off, int lo_row, int hi_row, int hi_off, int y_lo, int y_hi,
                    const Geo& g, float beta, const Tables& tb, uint8_t* choice, cudaStream_t s) {
   if (n <= 0 || b_hi <= b_lo) return;
   k_decide<<<cdiv(n, 256), 256, 0, s>>>(rec_id, bin_start, b_lo, b_hi, xy, heading, goal, cell,
-                                        occ, D, F, main_off, lo_row, hi_row, hi_off, y_lo, y_hi,
+                                        ocls, D, F, main_off, lo_row, hi_row, hi_off, y_lo, y_hi,
                                         g, beta, tb.own, tb.dirdot, choice);
 }
 
