@@ -197,6 +197,42 @@ sfm_status sfm_set_timing(sfm_ctx* ctx, int32_t enable);
  * Synchronising. */
 sfm_status sfm_stage_times(sfm_ctx* ctx, double* ms, int64_t* ticks);
 
+/* ---- Field superposition that allocates nothing ------------------------
+ * The paper has no counterpart of this entry point: it serves callers that
+ * cannot call cudaMalloc, such as a host application or framework that
+ * reserves all device memory up front in its own pool and forbids further
+ * allocations (or cannot afford the device synchronisation an allocation
+ * may cause) while it runs.
+ *
+ * Computes field[c] = base[c] + sum_p K_P(c - x_p; h_p) over the live
+ * pedestrians, the same superposition as the context path (summed in another
+ * order, so equal up to FP32 rounding).  Pass the static field read with
+ * sfm_read_static_field as `base` for the whole field, or zeros for the
+ * pedestrian part alone.  No context is needed.
+ *   lat, prm: lattice and model parameters (host).  Only r, kP, aP, gamma are
+ *             used.  r must be <= SFM_NOALLOC_MAX_RADIUS; the lattice may
+ *             need at most SFM_NOALLOC_MAX_BINS bins of 32 x 32 su; n <=
+ *             SFM_NOALLOC_MAX_PEDS.
+ *   xy (n int32 pairs), heading (n classes 0..8, or NULL = 0), alive
+ *             (n flags, or NULL = all alive): device memory, caller-owned.
+ *   base, field: device memory, W*H floats each, caller-owned, not aliased.
+ *   stream: cudaStream_t or NULL.  The call waits for the stream.
+ * Working memory is a fixed array of device memory inside the library
+ * (about 5.2 MB, held by every GPU that loads the library until exit); the
+ * first call on a device looks its address up, and the call never calls
+ * cudaMalloc, cudaFree or an allocating library routine.  Every call reuses
+ * the same array, so calls that overlap on the GPU (other streams or host
+ * threads) race and must not be made.
+ * Returns SFM_EINVAL for sizes beyond the limits above or bad arguments
+ * (before any device work), SFM_ECONFLICT if a live pedestrian is
+ * off-lattice or has a class > 8, SFM_ECUDA on a CUDA failure. */
+#define SFM_NOALLOC_MAX_PEDS (1 << 20)
+#define SFM_NOALLOC_MAX_BINS (1 << 16)
+#define SFM_NOALLOC_MAX_RADIUS 47
+sfm_status sfm_field_noalloc(const sfm_lattice* lat, const sfm_params* prm, int32_t n,
+                             const int32_t* xy, const uint8_t* heading, const uint8_t* alive,
+                             const float* base, float* field, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

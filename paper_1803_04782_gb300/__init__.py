@@ -33,6 +33,7 @@ EXPORTS = [
     "sfm_set_time", "sfm_step", "sfm_compute_field", "sfm_sync", "sfm_read_field",
     "sfm_compute_field_into", "sfm_read_static_field", "sfm_read_guidance", "sfm_read_peds",
     "sfm_read_decisions", "sfm_stats", "sfm_set_timing", "sfm_stage_times",
+    "sfm_field_noalloc",
 ]
 
 
@@ -94,6 +95,8 @@ def lib():
             "sfm_stats": (C.c_int, [P, C.POINTER(Stats)]),
             "sfm_set_timing": (C.c_int, [P, I32]),
             "sfm_stage_times": (C.c_int, [P, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
+            "sfm_field_noalloc": (C.c_int, [C.POINTER(Lattice), C.POINTER(Params), I32, P, P, P,
+                                            P, P, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -239,6 +242,22 @@ def sfm_stage_times(ctx):
     ticks = C.c_int64()
     _check(ctx, lib().sfm_stage_times(ctx, ms, C.byref(ticks)))
     return dict(zip(STAGES, list(ms))), int(ticks.value)
+
+
+SFM_NOALLOC_MAX_PEDS = 1 << 20
+SFM_NOALLOC_MAX_BINS = 1 << 16
+SFM_NOALLOC_MAX_RADIUS = 47
+
+
+def sfm_field_noalloc(lat: Lattice, prm: Params, xy, heading, alive, base, field,
+                      stream=None) -> int:
+    """Field superposition into ``field`` (device) without any device
+    allocation; returns the sfm_status code (0 = SFM_OK).  For callers that
+    cannot allocate device memory while they run; see include/sfm.h."""
+    n = 0 if xy is None else int(xy.shape[0])
+    return int(lib().sfm_field_noalloc(C.byref(lat), C.byref(prm), n, _ptr(xy)[0],
+                                       _ptr(heading)[0], _ptr(alive)[0], _ptr(base)[0],
+                                       _ptr(field)[0], _stream_handle(stream)))
 
 
 # ------------------------------------------------------------------ wrapper
