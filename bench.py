@@ -365,6 +365,103 @@ def run_gpu(args):
     return 0
 
 
+# ------------------------------------------------------------------ batch arm
+def run_batch(args):
+    """256 independent rooms (side U[64,2048], density U[0.05,0.4], radius
+    U[5,30], 1-4 exits) stepped together: one persistent launch per tick, the
+    tick loop replayed from a CUDA graph, tiles from the autotuner.  Beside it,
+    the same scenes stepped one context after another (the plain exact path)."""
+    import torch
+    import paper_1803_04782_gb300 as sfm
+    import scenegen as SG
+    from paper_1803_04782_gb300 import build as B
+
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    B.build()
+    sfm.lib()
+    nsc = 256 if args.workload == "batch" else 32
+    scenes = SG.batch(nscenes=nsc)
+    desc = (f"batch of {nsc} rooms: side U[64,2048], density U[0.05,0.4] of free su, "
+            "radius U[5,30], 1-4 exits, wall ring")
+    stream = torch.cuda.current_stream()
+    n = sum(s.n for s in scenes)
+    su = sum(s.W * s.H for s in scenes)
+    with sfm.Batch(scenes, stream=stream) as bt:
+        t0 = time.perf_counter()
+        rows = bt.autotune()
+        tune_s = time.perf_counter() - t0
+        bt.step(args.warmup)
+        bt.sync()
+        xs, _, al = bt.peds()
+        alive0 = sum(int(a.sum()) for a in al)
+        pairs = sum(pair_count(s, x, a) for s, x, a in zip(scenes, xs, al))
+        clocks = Clocks()
+        clocks.start()
+        time.sleep(0.3)
+        torch.cuda.synchronize()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        bt.step(args.steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        clk = clocks.stop()
+        bt.sync()
+        elapsed = ev0.elapsed_time(ev1) / 1e3
+        _, _, al = bt.peds()
+        alive1 = sum(int(a.sum()) for a in al)
+        # field-only launches (bins + field) time the dominant stage
+        bt.set_timing(True)
+        bt.stage_times()
+        for _ in range(3):
+            bt.compute_field()
+        st_ms, _ = bt.stage_times()
+        bt.set_timing(False)
+        field_s = st_ms["field"] / 3 / 1e3
+        launches = bt.stats()["kernel_launches"]
+    ped_steps = 0.5 * (alive0 + alive1) * args.steps
+    value = ped_steps / elapsed
+
+    # the plain exact path: each scene in its own context, one after another
+    plain_steps = max(3, min(args.steps, 10))
+    sims = [sfm.Sim(s, stream=stream) for s in scenes]
+    for s in sims:
+        s.step(1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for s in sims:
+        s.step(plain_steps)
+    torch.cuda.synchronize()
+    plain_t = time.perf_counter() - t0
+    plain_alive = sum(s.stats()["alive"] for s in sims)
+    for s in sims:
+        s.close()
+    plain_value = plain_alive * plain_steps / plain_t
+
+    peak = SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    achieved = FLOPS_PER_PAIR * pairs / field_s / 1e12
+    line = {
+        "metric": "pedestrian-steps/s", "value": value, "unit": "ped-steps/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": desc, "scenes": nsc, "n": n, "su": su,
+                   "tiles_rows_per_radius_class": rows, "autotune_s": tune_s,
+                   "l2": "inputs larger than L2", "parallelism": "single GPU"},
+        "su_updates_per_s": su * args.steps / elapsed,
+        "plain_exact_path": {"value": plain_value, "unit": "ped-steps/s",
+                             "how": f"{nsc} contexts stepped one after another, {plain_steps} ticks"},
+        "speedup_vs_plain": value / plain_value,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None, "kernel": "k_tick_batch (field only)",
+                     "field_ms": 1e3 * field_s, "pairs_per_step": pairs},
+        "cpu_baseline": None, "e2e": None, "clocks": clk, "gpu_launches": int(launches),
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -372,7 +469,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="floor",
-                    choices=["floor", "floor-small", "corridor", "room"])
+                    choices=["floor", "floor-small", "corridor", "room", "batch", "batch-small"])
     ap.add_argument("--bands", type=int, default=4,
                     help="row bands of the divide-and-conquer field pass (1 = unbanded)")
     ap.add_argument("--e2e-steps", type=int, default=10)
@@ -382,6 +479,8 @@ def main():
     args.warmup = max(3, args.warmup)  # timing rule: at least 3 untimed warm-up ticks
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload.startswith("batch"):
+        return run_batch(args)
     return run_gpu(args)
 
 

@@ -197,6 +197,49 @@ sfm_status sfm_set_timing(sfm_ctx* ctx, int32_t enable);
  * Synchronising. */
 sfm_status sfm_stage_times(sfm_ctx* ctx, double* ms, int64_t* ticks);
 
+/* ---- Batches of independent lattices -------------------------------------
+ * Many small or uneven lattices stepped together: every tick is ONE
+ * persistent (cooperative) kernel launch that runs bins, field, decisions,
+ * vote and commit for all lattices, separated by grid-wide barriers whose
+ * waits are bounded (a barrier that times out ends the launch and the next
+ * synchronising call returns SFM_ETIMEOUT).  The field stage walks a work
+ * list of (lattice, 32-footprint chunk) items sorted by decreasing cost; the
+ * tick launch is captured once in a CUDA graph and replayed.  Each lattice
+ * evolves exactly as it would in its own context (same bins, same summation
+ * order, its own seed and pedestrian numbering), which the tests check bit
+ * for bit.  This batches the paper's concurrency technique (several tasks in
+ * flight, Sec. 4.2) across scenarios.
+ *
+ * sfm_batch_create: nscenes lattices (1..65535); lats[i], cells[i] (host,
+ *   W*H bytes each), prms[i] (r <= 47).  The context then accepts
+ *   sfm_batch_place, sfm_step, sfm_compute_field, sfm_read_field /
+ *   _static_field / _guidance (all lattices concatenated in order, offsets
+ *   from sfm_batch_offsets), sfm_read_peds / _decisions (pedestrians
+ *   concatenated in lattice order), sfm_stats, sfm_set_time, sfm_sync,
+ *   sfm_set_timing / sfm_stage_times (one entry per tick) and sfm_destroy.
+ *   Errors as sfm_create.
+ * sfm_batch_place: counts[nscenes] (host) pedestrians per lattice; xy,
+ *   heading, goal, alive concatenated in lattice order, coordinates local to
+ *   each lattice (host or device per on_device).  Errors as sfm_place.
+ * sfm_batch_offsets: su_off[nscenes+1] and ped_off[nscenes+1] (either may
+ *   be NULL) receive where each lattice starts in the concatenated arrays.
+ * sfm_batch_autotune: times the field stage of each radius class (lattices
+ *   sharing a class-table row stride) with footprints 8 and 16 su high and
+ *   keeps the faster; rows_per_class[6] (may be NULL) receives the choice for
+ *   strides 16, 32, ..., 96.  Needs placed pedestrians; moves nobody.
+ * sfm_batch_test_missing_ctas: test hook of the bounded barrier wait; the
+ *   next tick's barriers wait for `missing` CTAs that are never launched, so
+ *   the tick gives up after about a second and returns SFM_ETIMEOUT (the
+ *   context stays usable). */
+sfm_status sfm_batch_create(int32_t nscenes, const sfm_lattice* lats, const uint8_t* const* cells,
+                            const sfm_params* prms, void* stream, sfm_ctx** out);
+sfm_status sfm_batch_place(sfm_ctx* ctx, const int32_t* counts, const int32_t* xy,
+                           const uint8_t* heading, const uint8_t* goal, const uint8_t* alive,
+                           int32_t on_device);
+sfm_status sfm_batch_offsets(const sfm_ctx* ctx, int64_t* su_off, int64_t* ped_off);
+sfm_status sfm_batch_autotune(sfm_ctx* ctx, int32_t* rows_per_class);
+sfm_status sfm_batch_test_missing_ctas(sfm_ctx* ctx, int32_t missing);
+
 /* ---- Field superposition that allocates nothing ------------------------
  * The paper has no counterpart of this entry point: it serves callers that
  * cannot call cudaMalloc, such as a host application or framework that

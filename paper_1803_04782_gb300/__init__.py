@@ -33,7 +33,8 @@ EXPORTS = [
     "sfm_set_time", "sfm_step", "sfm_compute_field", "sfm_sync", "sfm_read_field",
     "sfm_compute_field_into", "sfm_read_static_field", "sfm_read_guidance", "sfm_read_peds",
     "sfm_read_decisions", "sfm_stats", "sfm_set_timing", "sfm_stage_times",
-    "sfm_field_noalloc",
+    "sfm_field_noalloc", "sfm_batch_create", "sfm_batch_place", "sfm_batch_offsets",
+    "sfm_batch_autotune", "sfm_batch_test_missing_ctas",
 ]
 
 
@@ -97,6 +98,12 @@ def lib():
             "sfm_stage_times": (C.c_int, [P, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
             "sfm_field_noalloc": (C.c_int, [C.POINTER(Lattice), C.POINTER(Params), I32, P, P, P,
                                             P, P, P]),
+            "sfm_batch_create": (C.c_int, [I32, C.POINTER(Lattice), C.POINTER(C.c_void_p),
+                                           C.POINTER(Params), P, C.POINTER(C.c_void_p)]),
+            "sfm_batch_place": (C.c_int, [P, P, P, P, P, P, I32]),
+            "sfm_batch_offsets": (C.c_int, [P, P, P]),
+            "sfm_batch_autotune": (C.c_int, [P, P]),
+            "sfm_batch_test_missing_ctas": (C.c_int, [P, I32]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -244,6 +251,45 @@ def sfm_stage_times(ctx):
     return dict(zip(STAGES, list(ms))), int(ticks.value)
 
 
+def sfm_batch_create(lats, cells, prms, stream=None):
+    n = len(lats)
+    L = (Lattice * n)(*lats)
+    P = (Params * n)(*prms)
+    keep = [np.ascontiguousarray(c, np.uint8) for c in cells]
+    ptrs = (C.c_void_p * n)(*[k.ctypes.data_as(C.c_void_p) for k in keep])
+    out = C.c_void_p()
+    st = lib().sfm_batch_create(n, L, ptrs, P, _stream_handle(stream), C.byref(out))
+    if st != SFM_OK:
+        msg = lib().sfm_last_error(None)
+        raise SfmError(st, msg.decode() if msg else "")
+    return out
+
+
+def sfm_batch_place(ctx, counts, xy, heading=None, goal=None, alive=None) -> None:
+    counts = np.ascontiguousarray(counts, np.int32)
+    pxy, dev = _ptr(xy)
+    _check(ctx, lib().sfm_batch_place(ctx, counts.ctypes.data_as(C.c_void_p), pxy,
+                                      _ptr(heading)[0], _ptr(goal)[0], _ptr(alive)[0], dev))
+
+
+def sfm_batch_offsets(ctx, nscenes: int):
+    su = np.zeros(nscenes + 1, np.int64)
+    pe = np.zeros(nscenes + 1, np.int64)
+    _check(ctx, lib().sfm_batch_offsets(ctx, su.ctypes.data_as(C.c_void_p),
+                                        pe.ctypes.data_as(C.c_void_p)))
+    return su, pe
+
+
+def sfm_batch_autotune(ctx):
+    rows = np.zeros(6, np.int32)
+    _check(ctx, lib().sfm_batch_autotune(ctx, rows.ctypes.data_as(C.c_void_p)))
+    return {16 * (i + 1): int(v) for i, v in enumerate(rows)}
+
+
+def sfm_batch_test_missing_ctas(ctx, missing: int) -> None:
+    _check(ctx, lib().sfm_batch_test_missing_ctas(ctx, int(missing)))
+
+
 SFM_NOALLOC_MAX_PEDS = 1 << 20
 SFM_NOALLOC_MAX_BINS = 1 << 16
 SFM_NOALLOC_MAX_RADIUS = 47
@@ -362,6 +408,106 @@ class Sim:
         won = np.empty(self.n, np.uint8)
         sfm_read_decisions(self.ctx, ch, won)
         return ch, won
+
+    def stats(self):
+        return sfm_stats(self.ctx)
+
+    def set_timing(self, on=True):
+        sfm_set_timing(self.ctx, on)
+
+    def stage_times(self):
+        return sfm_stage_times(self.ctx)
+
+
+class Batch:
+    """A batch of independent scenes stepped by one persistent launch per tick.
+    ``scenes``: objects with the attributes ``Sim`` accepts."""
+
+    def __init__(self, scenes, stream=None, place=True):
+        self.scenes = list(scenes)
+        lats = [Lattice(s.W, s.H, s.periodic_x, s.periodic_y) for s in self.scenes]
+        prms = [make_params(**s.params) for s in self.scenes]
+        self.ctx = sfm_batch_create(lats, [s.cell for s in self.scenes], prms, stream)
+        self.su_off = self.ped_off = None
+        if place:
+            self.place([s.xy for s in self.scenes], [s.heading for s in self.scenes],
+                       [s.goal for s in self.scenes])
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            sfm_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def place(self, xys, headings=None, goals=None, alives=None):
+        counts = [len(x) for x in xys]
+        cat = lambda arrs, dt: (None if arrs is None else
+                                np.ascontiguousarray(np.concatenate(arrs), dt))
+        xy = np.ascontiguousarray(np.concatenate(xys).reshape(-1, 2), np.int32)
+        sfm_batch_place(self.ctx, counts, xy, cat(headings, np.uint8), cat(goals, np.uint8),
+                        cat(alives, np.uint8))
+        self.su_off, self.ped_off = sfm_batch_offsets(self.ctx, len(self.scenes))
+
+    def step(self, n=1):
+        sfm_step(self.ctx, n)
+
+    def sync(self):
+        sfm_sync(self.ctx)
+
+    def compute_field(self):
+        sfm_compute_field(self.ctx)
+
+    def autotune(self):
+        return sfm_batch_autotune(self.ctx)
+
+    def _split(self, flat, off, shape=None):
+        out = []
+        for i, s in enumerate(self.scenes):
+            part = flat[off[i]:off[i + 1]]
+            out.append(part.reshape(s.H, s.W) if shape == "lattice" else part)
+        return out
+
+    def fields(self):
+        out = np.empty(int(self.su_off[-1]), np.float32)
+        sfm_read_field(self.ctx, out)
+        return self._split(out, self.su_off, "lattice")
+
+    def static_fields(self):
+        out = np.empty(int(self.su_off[-1]), np.float32)
+        sfm_read_static_field(self.ctx, out)
+        return self._split(out, self.su_off, "lattice")
+
+    def guidance(self):
+        out = np.empty(int(self.su_off[-1]), np.int32)
+        sfm_read_guidance(self.ctx, out)
+        return self._split(out, self.su_off, "lattice")
+
+    def peds(self):
+        n = int(self.ped_off[-1])
+        xy = np.empty((n, 2), np.int32)
+        h = np.empty(n, np.uint8)
+        a = np.empty(n, np.uint8)
+        sfm_read_peds(self.ctx, xy, h, a)
+        return (self._split(xy, self.ped_off), self._split(h, self.ped_off),
+                self._split(a, self.ped_off))
+
+    def decisions(self):
+        n = int(self.ped_off[-1])
+        ch = np.empty(n, np.uint8)
+        won = np.empty(n, np.uint8)
+        sfm_read_decisions(self.ctx, ch, won)
+        return self._split(ch, self.ped_off), self._split(won, self.ped_off)
 
     def stats(self):
         return sfm_stats(self.ctx)

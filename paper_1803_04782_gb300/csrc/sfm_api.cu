@@ -9,71 +9,9 @@
 #include <string>
 #include <vector>
 
-#include "sfm_internal.h"
+#include "sfm_ctx.h"
 
 using namespace sfm;
-
-struct sfm_ctx {
-  sfm_lattice lat{};
-  sfm_params prm{};
-  cudaStream_t stream = nullptr;
-  Geo geo{};
-  std::string err;
-  int64_t device_bytes = 0;
-  int64_t launches = 0;  // kernels launched by this context
-  std::vector<void*> allocs;
-
-  // lattice arrays
-  uint8_t* cell = nullptr;
-  float* Fs = nullptr;
-  float* F = nullptr;  // full-lattice field (unbanded mode only)
-  int32_t* D = nullptr;
-  int32_t* occ = nullptr;
-  uint8_t* ocls = nullptr;
-  // tables
-  float *T0 = nullptr, *TX = nullptr, *TY = nullptr, *KO = nullptr, *KE = nullptr;
-  float *own = nullptr, *dirdot = nullptr;
-  float2* hvec = nullptr;
-  float* CT = nullptr;  // heading-class tables of the v2 gather
-  // bins
-  int32_t *bin_count = nullptr, *bin_start = nullptr, *scan_tmp = nullptr;
-  uint32_t* rec = nullptr;
-  int32_t* rec_id = nullptr;  // pedestrian of each bin record
-  Counters* ctr = nullptr;
-  // pedestrians
-  int n = 0, cap = 0;
-  int2* xy = nullptr;
-  uint8_t *heading = nullptr, *goal = nullptr, *alive = nullptr, *choice = nullptr, *won = nullptr;
-  bool placed = false;
-  int64_t t = 0;
-  // banded mode
-  int bands = 1;
-  int band_rows = 0;  // lattice rows per band (multiple of the tile height)
-  float* band_buf = nullptr;
-  // timing
-  bool timing = false;
-  struct Rec {
-    int stage;
-    cudaEvent_t a, b;
-  };
-  std::vector<Rec> recs;
-  std::vector<cudaEvent_t> pool;
-  int64_t timed_ticks = 0;
-
-  Tables tables() const {
-    Tables tb;
-    tb.T0 = T0;
-    tb.TX = TX;
-    tb.TY = TY;
-    tb.KO = KO;
-    tb.KE = KE;
-    tb.own = own;
-    tb.dirdot = dirdot;
-    tb.hvec = hvec;
-    tb.CT = CT;
-    return tb;
-  }
-};
 
 namespace {
 
@@ -269,6 +207,47 @@ sfm_status copy_out(sfm_ctx* ctx, void* dst, const void* src, size_t bytes, int 
 
 }  // namespace
 
+void sfm::set_create_error(const std::string& msg) { g_create_err = msg; }
+
+// Guidance distances of one lattice: relaxation rounds until no tile changes
+// (at most 4 * tiles + 256 rounds, then SFM_ETIMEOUT).
+sfm_status sfm::compute_guidance(const Geo& g, const uint8_t* cell, int32_t* D, cudaStream_t s,
+                                 std::string* err) {
+  const int ntiles = ((g.W + kTile - 1) / kTile) * ((g.H + kTile - 1) / kTile);
+  uint8_t *a0 = nullptr, *a1 = nullptr;
+  int* changed = nullptr;
+  if (cudaMalloc(&a0, ntiles) != cudaSuccess || cudaMalloc(&a1, ntiles) != cudaSuccess ||
+      cudaMalloc(&changed, sizeof(int)) != cudaSuccess) {
+    cudaFree(a0);
+    cudaFree(a1);
+    if (err) *err = "guidance scratch allocation failed";
+    return SFM_ENOMEM;
+  }
+  launch_guidance_init(g, cell, D, s);
+  cudaMemsetAsync(a0, 1, ntiles, s);
+  int h_changed = 1, rounds = 0;
+  const int max_rounds = 4 * ntiles + 256;
+  while (h_changed && rounds < max_rounds) {
+    cudaMemsetAsync(a1, 0, ntiles, s);
+    cudaMemsetAsync(changed, 0, sizeof(int), s);
+    launch_guidance_round(g, cell, D, a0, a1, changed, s);
+    cudaMemcpyAsync(&h_changed, changed, sizeof(int), cudaMemcpyDeviceToHost, s);
+    cudaStreamSynchronize(s);
+    uint8_t* tmp = a0;
+    a0 = a1;
+    a1 = tmp;
+    ++rounds;
+  }
+  cudaFree(a0);
+  cudaFree(a1);
+  cudaFree(changed);
+  if (h_changed) {
+    if (err) *err = "guidance relaxation did not converge";
+    return SFM_ETIMEOUT;
+  }
+  return SFM_OK;
+}
+
 extern "C" {
 
 int32_t sfm_abi_version(void) { return SFM_ABI_VERSION; }
@@ -300,6 +279,7 @@ sfm_status sfm_create(const sfm_lattice* lat, const uint8_t* cell, int32_t cell_
 
   sfm_ctx* ctx = new sfm_ctx;
   ctx->lat = *lat;
+  ctx->nsu_total = (int64_t)lat->W * lat->H;
   ctx->prm = *prm;
   ctx->prm.bin = kBin;
   ctx->stream = static_cast<cudaStream_t>(stream);
@@ -384,40 +364,9 @@ sfm_status sfm_create(const sfm_lattice* lat, const uint8_t* cell, int32_t cell_
   if (ctx->CT) launch_class_tables(g.r, ctx->prm, ctx->CT, s);
   launch_static_field(g, ctx->cell, ctx->tables(), ctx->Fs, s);
 
-  // guidance: relaxation rounds until no tile changes
   {
-    const int ntiles = ((g.W + kTile - 1) / kTile) * ((g.H + kTile - 1) / kTile);
-    uint8_t *a0 = nullptr, *a1 = nullptr;
-    int* changed = nullptr;
-    if (cudaMalloc(&a0, ntiles) != cudaSuccess || cudaMalloc(&a1, ntiles) != cudaSuccess ||
-        cudaMalloc(&changed, sizeof(int)) != cudaSuccess) {
-      cudaFree(a0);
-      cudaFree(a1);
-      fail(ctx, SFM_ENOMEM, "guidance scratch");
-      return bail(SFM_ENOMEM);
-    }
-    launch_guidance_init(g, ctx->cell, ctx->D, s);
-    cudaMemsetAsync(a0, 1, ntiles, s);
-    int h_changed = 1, rounds = 0;
-    const int max_rounds = 4 * (ntiles + 64);
-    while (h_changed && rounds < max_rounds) {
-      cudaMemsetAsync(a1, 0, ntiles, s);
-      cudaMemsetAsync(changed, 0, sizeof(int), s);
-      launch_guidance_round(g, ctx->cell, ctx->D, a0, a1, changed, s);
-      cudaMemcpyAsync(&h_changed, changed, sizeof(int), cudaMemcpyDeviceToHost, s);
-      cudaStreamSynchronize(s);
-      uint8_t* tmp = a0;
-      a0 = a1;
-      a1 = tmp;
-      ++rounds;
-    }
-    cudaFree(a0);
-    cudaFree(a1);
-    cudaFree(changed);
-    if (h_changed) {
-      fail(ctx, SFM_ETIMEOUT, "guidance relaxation did not converge in %d rounds", rounds);
-      return bail(SFM_ETIMEOUT);
-    }
+    const sfm_status gst = compute_guidance(g, ctx->cell, ctx->D, s, &ctx->err);
+    if (gst != SFM_OK) return bail(gst);
   }
   e = cudaStreamSynchronize(s);
   if (e == cudaSuccess) e = cudaGetLastError();
@@ -432,6 +381,7 @@ sfm_status sfm_create(const sfm_lattice* lat, const uint8_t* cell, int32_t cell_
 void sfm_destroy(sfm_ctx* ctx) {
   if (!ctx) return;
   cudaStreamSynchronize(ctx->stream);
+  batch_destroy(ctx);
   for (void* p : ctx->allocs) cudaFree(p);
   for (auto& r : ctx->recs) {
     cudaEventDestroy(r.a);
@@ -444,6 +394,7 @@ void sfm_destroy(sfm_ctx* ctx) {
 sfm_status sfm_place(sfm_ctx* ctx, int32_t n, const int32_t* xy, const uint8_t* heading,
                      const uint8_t* goal, const uint8_t* alive, int32_t on_device) {
   if (!ctx) return SFM_EINVAL;
+  if (ctx->batch) return fail(ctx, SFM_ESTATE, "a batch is placed with sfm_batch_place");
   if (n < 0 || (n > 0 && !xy)) return fail(ctx, SFM_EINVAL, "bad pedestrian arrays");
   cudaStream_t s = ctx->stream;
   const Geo& g = ctx->geo;
@@ -541,6 +492,7 @@ sfm_status sfm_set_time(sfm_ctx* ctx, int64_t t) {
 sfm_status sfm_step(sfm_ctx* ctx, int32_t nsteps) {
   if (!ctx) return SFM_EINVAL;
   if (nsteps < 0) return fail(ctx, SFM_EINVAL, "nsteps < 0");
+  if (ctx->batch) return batch_tick(ctx, nsteps, 0);
   if (!ctx->placed) return fail(ctx, SFM_ESTATE, "sfm_step before a successful sfm_place");
   for (int i = 0; i < nsteps; ++i) {
     run_tick(ctx);
@@ -554,6 +506,7 @@ sfm_status sfm_step(sfm_ctx* ctx, int32_t nsteps) {
 sfm_status sfm_compute_field(sfm_ctx* ctx) {
   if (!ctx) return SFM_EINVAL;
   if (!ctx->placed) return fail(ctx, SFM_ESTATE, "no pedestrians placed");
+  if (ctx->batch) return batch_tick(ctx, 1, 1);
   if (ctx->bands > 1) return fail(ctx, SFM_ESTATE, "banded mode keeps no full-lattice field");
   run_bins(ctx);
   {
@@ -567,6 +520,7 @@ sfm_status sfm_compute_field(sfm_ctx* ctx) {
 sfm_status sfm_compute_field_into(sfm_ctx* ctx, float* dst, int32_t on_device) {
   if (!ctx || !dst) return SFM_EINVAL;
   if (!ctx->placed) return fail(ctx, SFM_ESTATE, "no pedestrians placed");
+  if (ctx->batch) return fail(ctx, SFM_ESTATE, "use sfm_compute_field and sfm_read_field on a batch");
   const Geo& g = ctx->geo;
   run_bins(ctx);
   if (on_device) {
@@ -589,23 +543,27 @@ sfm_status sfm_compute_field_into(sfm_ctx* ctx, float* dst, int32_t on_device) {
 sfm_status sfm_sync(sfm_ctx* ctx) {
   if (!ctx) return SFM_EINVAL;
   CU(cudaGetLastError());
+  if (ctx->batch) {
+    const sfm_status bs = batch_sync(ctx);
+    if (bs != SFM_OK) return bs;
+  }
   return check_flags(ctx);
 }
 
 sfm_status sfm_read_field(sfm_ctx* ctx, float* dst, int32_t on_device) {
   if (!ctx || !dst) return SFM_EINVAL;
   if (ctx->bands > 1) return fail(ctx, SFM_ESTATE, "banded mode keeps no full-lattice field");
-  return copy_out(ctx, dst, ctx->F, (size_t)ctx->geo.W * ctx->geo.H * sizeof(float), on_device);
+  return copy_out(ctx, dst, ctx->F, (size_t)ctx->nsu_total * sizeof(float), on_device);
 }
 
 sfm_status sfm_read_static_field(sfm_ctx* ctx, float* dst, int32_t on_device) {
   if (!ctx || !dst) return SFM_EINVAL;
-  return copy_out(ctx, dst, ctx->Fs, (size_t)ctx->geo.W * ctx->geo.H * sizeof(float), on_device);
+  return copy_out(ctx, dst, ctx->Fs, (size_t)ctx->nsu_total * sizeof(float), on_device);
 }
 
 sfm_status sfm_read_guidance(sfm_ctx* ctx, int32_t* dst, int32_t on_device) {
   if (!ctx || !dst) return SFM_EINVAL;
-  return copy_out(ctx, dst, ctx->D, (size_t)ctx->geo.W * ctx->geo.H * sizeof(int32_t), on_device);
+  return copy_out(ctx, dst, ctx->D, (size_t)ctx->nsu_total * sizeof(int32_t), on_device);
 }
 
 sfm_status sfm_read_peds(sfm_ctx* ctx, int32_t* xy, uint8_t* heading, uint8_t* alive,

@@ -1,0 +1,88 @@
+// sfm_ctx.h -- host-side context of the C ABI (one lattice, or a batch of
+// independent lattices stepped by one persistent launch per tick).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "sfm_internal.h"
+
+struct sfm_ctx;
+namespace sfm {
+struct BatchState;  // sfm_batch.cu
+sfm_status compute_guidance(const Geo& g, const uint8_t* cell, int32_t* D, cudaStream_t s,
+                            std::string* err);
+// message returned by sfm_last_error(NULL) on this thread
+void set_create_error(const std::string& msg);
+// batched lattices (sfm_batch.cu)
+sfm_status batch_tick(sfm_ctx* ctx, int nsteps, int field_only);
+sfm_status batch_sync(sfm_ctx* ctx);
+void batch_destroy(sfm_ctx* ctx);
+}  // namespace sfm
+
+struct sfm_ctx {
+  sfm_lattice lat{};
+  sfm_params prm{};
+  cudaStream_t stream = nullptr;
+  sfm::Geo geo{};
+  std::string err;
+  int64_t device_bytes = 0;
+  int64_t nsu_total = 0;  // su of all lattice arrays (W*H, or the batch's sum)
+  int64_t launches = 0;  // kernels launched by this context
+  std::vector<void*> allocs;
+
+  // lattice arrays
+  uint8_t* cell = nullptr;
+  float* Fs = nullptr;
+  float* F = nullptr;  // full-lattice field (unbanded mode only)
+  int32_t* D = nullptr;
+  int32_t* occ = nullptr;
+  uint8_t* ocls = nullptr;
+  // tables
+  float *T0 = nullptr, *TX = nullptr, *TY = nullptr, *KO = nullptr, *KE = nullptr;
+  float *own = nullptr, *dirdot = nullptr;
+  float2* hvec = nullptr;
+  float* CT = nullptr;  // heading-class tables of the v2 gather
+  // bins
+  int32_t *bin_count = nullptr, *bin_start = nullptr, *scan_tmp = nullptr;
+  uint32_t* rec = nullptr;
+  int32_t* rec_id = nullptr;  // pedestrian of each bin record
+  sfm::Counters* ctr = nullptr;
+  // pedestrians
+  int n = 0, cap = 0;
+  int2* xy = nullptr;
+  uint8_t *heading = nullptr, *goal = nullptr, *alive = nullptr, *choice = nullptr, *won = nullptr;
+  bool placed = false;
+  int64_t t = 0;
+  // banded mode
+  int bands = 1;
+  int band_rows = 0;  // lattice rows per band (multiple of the tile height)
+  float* band_buf = nullptr;
+  // timing
+  bool timing = false;
+  struct Rec {
+    int stage;
+    cudaEvent_t a, b;
+  };
+  std::vector<Rec> recs;
+  std::vector<cudaEvent_t> pool;
+  int64_t timed_ticks = 0;
+  // batch of independent lattices (nullptr for a single lattice)
+  sfm::BatchState* batch = nullptr;
+
+  sfm::Tables tables() const {
+    sfm::Tables tb;
+    tb.T0 = T0;
+    tb.TX = TX;
+    tb.TY = TY;
+    tb.KO = KO;
+    tb.KE = KE;
+    tb.own = own;
+    tb.dirdot = dirdot;
+    tb.hvec = hvec;
+    tb.CT = CT;
+    return tb;
+  }
+};
+
