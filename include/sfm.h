@@ -240,6 +240,57 @@ sfm_status sfm_batch_offsets(const sfm_ctx* ctx, int64_t* su_off, int64_t* ped_o
 sfm_status sfm_batch_autotune(sfm_ctx* ctx, int32_t* rows_per_class);
 sfm_status sfm_batch_test_missing_ctas(sfm_ctx* ctx, int32_t missing);
 
+/* ---- Learned field surrogate ----------------------------------------------
+ * F_sur(c) = F_static(c) + [exact pedestrian field within Chebyshev radius
+ * rn of c] + scale * bilinear(Y)(c), where Y is the output of a 4-layer
+ * convolutional network (3->32 5x5, 32->32 3x3, 32->32 3x3, 32->1 3x3, ReLU
+ * between layers, "valid" correlations) run on a grid coarsened s times:
+ * per s x s cell the pedestrian count and the heading sums, / s^2, with a
+ * 5-cell border (wrapped in periodic dimensions, zero otherwise).  Weights
+ * and activations are BF16, accumulation FP32.  With s = 8 the network sees
+ * +-40 su, the radius of the largest workload; s = 1, rn = 0 is the literal
+ * fine-grid network (+-5 su).  Trained on the GPU by this library's forward,
+ * backward and Adam kernels against the exact field's far part (cell
+ * averages of F - F_near, / scale); the exact path stays the judge.  The
+ * paper's future work (Sec. 6) names deep learning only for data collection;
+ * this surrogate is an addition, not a paper method.
+ *
+ * Parameters travel in the order W1 b1 W2 b2 W3 b3 W4 b4, each W laid out
+ * [out][in][ky][kx]: sfm_surrogate_nparams() floats.  Contexts used with a
+ * surrogate are single, unbanded, with W and H multiples of s. */
+typedef struct sfm_surrogate sfm_surrogate; /* opaque */
+typedef struct sfm_surrogate_cfg {
+  int32_t coarsen;     /* s >= 1 */
+  int32_t near_radius; /* rn in [0, r] */
+  float target_scale;  /* field units per network output unit (> 0) */
+  float lr, beta1, beta2, eps; /* Adam */
+  int32_t pad_;
+} sfm_surrogate_cfg;
+int32_t sfm_surrogate_nparams(void);
+sfm_status sfm_surrogate_create(const sfm_surrogate_cfg* cfg, void* stream, sfm_surrogate** out);
+void sfm_surrogate_destroy(sfm_surrogate* sur);
+const char* sfm_surrogate_last_error(const sfm_surrogate* sur);
+/* host arrays of sfm_surrogate_nparams() floats; set resets the Adam state */
+sfm_status sfm_surrogate_set_params(sfm_surrogate* sur, const float* params);
+sfm_status sfm_surrogate_get_params(sfm_surrogate* sur, float* params);
+/* One forward + backward on a given input: X (host, [3][Hin][Win] floats,
+ * rounded to BF16), targets T (host, [Hin-10][Win-10]); loss = 0.5 *
+ * mean((Y-T)^2) and its gradients (host, nparams floats, public order). */
+sfm_status sfm_surrogate_grad(sfm_surrogate* sur, int32_t Hin, int32_t Win, const float* X,
+                              const float* T, float* loss, float* grads);
+/* iters training steps on ctx: each takes the exact field of ctx's current
+ * state, one Adam step on the whole coarse lattice, then ticks ctx once so
+ * the next step sees a new crowd.  loss_curve: iters floats (host) or NULL. */
+sfm_status sfm_surrogate_train(sfm_surrogate* sur, sfm_ctx* ctx, int32_t iters, float* loss_curve);
+/* surrogate field of ctx's current state into out (W*H floats, host or device) */
+sfm_status sfm_surrogate_field(sfm_surrogate* sur, sfm_ctx* ctx, float* out, int32_t on_device);
+/* On ctx's current state: relative field error sum|F_sur - F| / sum|F - F_static|,
+ * the fraction of live pedestrians whose decision changes when taken on
+ * F_sur instead of the exact F, and the time of each field (bins included).
+ * Overwrites ctx's field and decision buffers. */
+sfm_status sfm_surrogate_eval(sfm_surrogate* sur, sfm_ctx* ctx, double* field_rel_err,
+                              double* flip_rate, double* ms_surrogate, double* ms_exact);
+
 /* ---- Field superposition that allocates nothing ------------------------
  * The paper has no counterpart of this entry point: it serves callers that
  * cannot call cudaMalloc, such as a host application or framework that

@@ -34,7 +34,10 @@ EXPORTS = [
     "sfm_compute_field_into", "sfm_read_static_field", "sfm_read_guidance", "sfm_read_peds",
     "sfm_read_decisions", "sfm_stats", "sfm_set_timing", "sfm_stage_times",
     "sfm_field_noalloc", "sfm_batch_create", "sfm_batch_place", "sfm_batch_offsets",
-    "sfm_batch_autotune", "sfm_batch_test_missing_ctas",
+    "sfm_batch_autotune", "sfm_batch_test_missing_ctas", "sfm_surrogate_nparams",
+    "sfm_surrogate_create", "sfm_surrogate_destroy", "sfm_surrogate_last_error",
+    "sfm_surrogate_set_params", "sfm_surrogate_get_params", "sfm_surrogate_grad",
+    "sfm_surrogate_train", "sfm_surrogate_field", "sfm_surrogate_eval",
 ]
 
 
@@ -64,6 +67,12 @@ class Stats(C.Structure):
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad_"}
+
+
+class SurrogateCfg(C.Structure):
+    _fields_ = [("coarsen", C.c_int32), ("near_radius", C.c_int32), ("target_scale", C.c_float),
+                ("lr", C.c_float), ("beta1", C.c_float), ("beta2", C.c_float), ("eps", C.c_float),
+                ("pad_", C.c_int32)]
 
 
 def lib():
@@ -104,6 +113,16 @@ def lib():
             "sfm_batch_offsets": (C.c_int, [P, P, P]),
             "sfm_batch_autotune": (C.c_int, [P, P]),
             "sfm_batch_test_missing_ctas": (C.c_int, [P, I32]),
+            "sfm_surrogate_nparams": (I32, []),
+            "sfm_surrogate_create": (C.c_int, [C.POINTER(SurrogateCfg), P, C.POINTER(C.c_void_p)]),
+            "sfm_surrogate_destroy": (None, [P]),
+            "sfm_surrogate_last_error": (C.c_char_p, [P]),
+            "sfm_surrogate_set_params": (C.c_int, [P, P]),
+            "sfm_surrogate_get_params": (C.c_int, [P, P]),
+            "sfm_surrogate_grad": (C.c_int, [P, I32, I32, P, P, P, P]),
+            "sfm_surrogate_train": (C.c_int, [P, P, I32, P]),
+            "sfm_surrogate_field": (C.c_int, [P, P, P, I32]),
+            "sfm_surrogate_eval": (C.c_int, [P, P, P, P, P, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -517,3 +536,103 @@ class Batch:
 
     def stage_times(self):
         return sfm_stage_times(self.ctx)
+
+
+# ------------------------------------------------------------ surrogate
+def _scheck(sur, status):
+    if status != SFM_OK:
+        m = lib().sfm_surrogate_last_error(sur)
+        raise SfmError(status, m.decode() if m else "")
+
+
+class Surrogate:
+    """Learned field surrogate (see include/sfm.h): exact near field plus a
+    BF16 convolutional far field on an s-times coarsened grid."""
+
+    def __init__(self, coarsen=8, near_radius=3, target_scale=20.0, lr=1e-3, beta1=0.9,
+                 beta2=0.999, eps=1e-8, stream=None, params=None):
+        self.cfg = SurrogateCfg(int(coarsen), int(near_radius), target_scale, lr, beta1, beta2,
+                                eps, 0)
+        out = C.c_void_p()
+        st = lib().sfm_surrogate_create(C.byref(self.cfg), _stream_handle(stream), C.byref(out))
+        if st != SFM_OK:
+            m = lib().sfm_last_error(None)
+            raise SfmError(st, m.decode() if m else "")
+        self.h = out
+        self.nparams = int(lib().sfm_surrogate_nparams())
+        if params is not None:
+            self.set_params(params)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().sfm_surrogate_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def set_params(self, flat):
+        flat = np.ascontiguousarray(flat, np.float32)
+        assert flat.size == self.nparams
+        _scheck(self.h, lib().sfm_surrogate_set_params(self.h, flat.ctypes.data_as(C.c_void_p)))
+
+    def get_params(self):
+        out = np.empty(self.nparams, np.float32)
+        _scheck(self.h, lib().sfm_surrogate_get_params(self.h, out.ctypes.data_as(C.c_void_p)))
+        return out
+
+    def grad(self, X, T):
+        X = np.ascontiguousarray(X, np.float32)
+        T = np.ascontiguousarray(T, np.float32)
+        loss = C.c_float()
+        g = np.empty(self.nparams, np.float32)
+        _scheck(self.h, lib().sfm_surrogate_grad(self.h, X.shape[1], X.shape[2],
+                                                 X.ctypes.data_as(C.c_void_p),
+                                                 T.ctypes.data_as(C.c_void_p), C.byref(loss),
+                                                 g.ctypes.data_as(C.c_void_p)))
+        return float(loss.value), g
+
+    def train(self, sim, iters):
+        curve = np.zeros(int(iters), np.float32)
+        _scheck(self.h, lib().sfm_surrogate_train(self.h, sim.ctx, int(iters),
+                                                  curve.ctypes.data_as(C.c_void_p)))
+        return curve
+
+    def field(self, sim):
+        out = np.empty((sim.H, sim.W), np.float32)
+        _scheck(self.h, lib().sfm_surrogate_field(self.h, sim.ctx, out.ctypes.data_as(C.c_void_p), 0))
+        return out
+
+    def eval(self, sim):
+        v = [C.c_double() for _ in range(4)]
+        _scheck(self.h, lib().sfm_surrogate_eval(self.h, sim.ctx, *[C.byref(x) for x in v]))
+        return {"field_rel_err": v[0].value, "flip_rate": v[1].value,
+                "ms_surrogate": v[2].value, "ms_exact": v[3].value}
+
+
+def flatten_params(params):
+    """Public flat order W1 b1 ... W4 b4 from [(W [out,in,k,k], b [out]), ...]."""
+    return np.concatenate([np.concatenate([np.asarray(W, np.float64).ravel(),
+                                           np.asarray(b, np.float64).ravel()])
+                           for W, b in params]).astype(np.float32)
+
+
+def unflatten_params(flat, layers=((3, 32, 5), (32, 32, 3), (32, 32, 3), (32, 1, 3))):
+    out, off = [], 0
+    for cin, cout, k in layers:
+        nw = cout * cin * k * k
+        W = np.asarray(flat[off:off + nw], np.float64).reshape(cout, cin, k, k)
+        off += nw
+        b = np.asarray(flat[off:off + cout], np.float64)
+        off += cout
+        out.append((W, b))
+    return out

@@ -208,6 +208,10 @@ sfm_status copy_out(sfm_ctx* ctx, void* dst, const void* src, size_t bytes, int 
 }  // namespace
 
 void sfm::set_create_error(const std::string& msg) { g_create_err = msg; }
+void sfm::ctx_run_bins(sfm_ctx* c) { run_bins(c); }
+void sfm::ctx_field_rows(sfm_ctx* c, float* out, int ya, int yb, int main_off, bool halos) {
+  field_rows(c, out, ya, yb, main_off, halos);
+}
 
 // Guidance distances of one lattice: relaxation rounds until no tile changes
 // (at most 4 * tiles + 256 rounds, then SFM_ETIMEOUT).

@@ -15,6 +15,9 @@ sfm_status compute_guidance(const Geo& g, const uint8_t* cell, int32_t* D, cudaS
                             std::string* err);
 // message returned by sfm_last_error(NULL) on this thread
 void set_create_error(const std::string& msg);
+// bins of the context's current state (S1), field rows (S2) into `out`
+void ctx_run_bins(sfm_ctx* c);
+void ctx_field_rows(sfm_ctx* c, float* out, int ya, int yb, int main_off, bool halos);
 // batched lattices (sfm_batch.cu)
 sfm_status batch_tick(sfm_ctx* ctx, int nsteps, int field_only);
 sfm_status batch_sync(sfm_ctx* ctx);

@@ -1,0 +1,849 @@
+// sfm_surrogate.cu -- learned field surrogate: the exact near field (pedestrians
+// within a small Chebyshev radius rn, by the same gather as the exact path)
+// plus a 4-layer convolutional network that predicts the far field from
+// per-cell occupancy and heading channels of an s-times coarsened grid,
+// interpolated back to every su.  BF16 weights and activations, FP32
+// accumulation; trained on the GPU by the kernels below (forward, backward,
+// Adam) on fields the exact path computes; the exact path stays the judge
+// (sfm_surrogate_eval: field error and decision flip rate).
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "sfm_ctx.h"
+#include "sfm_device.cuh"
+
+using namespace sfm;
+
+namespace {
+
+typedef __nv_bfloat16 bf16;
+
+// network layers: (Cin, Cout, kernel)
+constexpr int kL1i = 3, kL1o = 32, kL1k = 5;
+constexpr int kLh = 32, kLk = 3;
+constexpr int kHalo = (kL1k - 1) / 2 + 3 * ((kLk - 1) / 2);  // 5 cells of context
+constexpr int kNW1 = kL1k * kL1k * kL1i * kL1o, kNW2 = kLk * kLk * kLh * kLh,
+              kNW4 = kLk * kLk * kLh * 1;
+constexpr int kNParams = kNW1 + kL1o + 2 * (kNW2 + kLh) + kNW4 + 1;
+// parameter blocks in the internal flat order: W1 b1 W2 b2 W3 b3 W4 b4, each W
+// stored [ky][kx][cin][cout]
+constexpr int kOffW[4] = {0, kNW1 + kL1o, kNW1 + kL1o + kNW2 + kLh,
+                          kNW1 + kL1o + 2 * (kNW2 + kLh)};
+constexpr int kOffB[4] = {kNW1, kNW1 + kL1o + kNW2, kNW1 + kL1o + 2 * kNW2 + kLh,
+                          kNW1 + kL1o + 2 * (kNW2 + kLh) + kNW4};
+constexpr int kTile = 16;  // output pixels per CTA side
+static_assert(kNParams == 3 * 32 * 25 + 32 + 2 * (32 * 32 * 9 + 32) + 32 * 9 + 1, "params");
+
+// --------------------------------------------------------------- forward
+// out[y][x][o] = act(b[o] + sum_{ky,kx,c} W[ky][kx][c][o] * in[y+ky][x+kx][c])
+// ("valid" cross-correlation, channel-last tensors, FP32 accumulation).
+template <int CIN, int COUT, int K, bool RELU>
+__global__ void __launch_bounds__(kTile* kTile)
+    k_conv_fwd(const bf16* __restrict__ in, int Hin, int Win, const float* __restrict__ Wt,
+               const float* __restrict__ b, bf16* __restrict__ out_bf, float* __restrict__ out_f) {
+  constexpr int TI = kTile + K - 1;
+  extern __shared__ __align__(16) float sm[];
+  float* sW = sm;                        // K*K*CIN*COUT
+  float* sIn = sm + K * K * CIN * COUT;  // TI*TI*CIN
+  const int Hout = Hin - K + 1, Wout = Win - K + 1;
+  const int x0 = blockIdx.x * kTile, y0 = blockIdx.y * kTile;
+  const int tid = threadIdx.x;
+  for (int i = tid; i < K * K * CIN * COUT; i += blockDim.x) sW[i] = Wt[i];
+  for (int i = tid; i < TI * TI * CIN; i += blockDim.x) {
+    const int c = i % CIN, p = i / CIN, px = p % TI, py = p / TI;
+    const int gy = y0 + py, gx = x0 + px;
+    sIn[i] = (gy < Hin && gx < Win) ? __bfloat162float(in[((size_t)gy * Win + gx) * CIN + c]) : 0.f;
+  }
+  __syncthreads();
+  const int tx = tid % kTile, ty = tid / kTile;
+  const int y = y0 + ty, x = x0 + tx;
+  float acc[COUT];
+#pragma unroll
+  for (int o = 0; o < COUT; ++o) acc[o] = b[o];
+  for (int ky = 0; ky < K; ++ky)
+    for (int kx = 0; kx < K; ++kx) {
+      const float* xin = sIn + ((ty + ky) * TI + (tx + kx)) * CIN;
+      const float* w = sW + (ky * K + kx) * CIN * COUT;
+#pragma unroll 4
+      for (int c = 0; c < CIN; ++c) {
+        const float v = xin[c];
+#pragma unroll
+        for (int o = 0; o < COUT; ++o) acc[o] = fmaf(v, w[c * COUT + o], acc[o]);
+      }
+    }
+  if (y >= Hout || x >= Wout) return;
+  const size_t base = ((size_t)y * Wout + x) * COUT;
+#pragma unroll
+  for (int o = 0; o < COUT; ++o) {
+    const float v = RELU ? fmaxf(acc[o], 0.f) : acc[o];
+    if (out_bf) out_bf[base + o] = __float2bfloat16(v);
+    if (out_f) out_f[base + o] = v;
+  }
+}
+
+// -------------------------------------------------------------- backward
+// dZ of a layer output: the incoming gradient, masked by the ReLU (A > 0).
+__device__ __forceinline__ float dz_at(const float* dA, const bf16* A, size_t i, bool relu) {
+  return relu ? (__bfloat162float(A[i]) > 0.f ? dA[i] : 0.f) : dA[i];
+}
+
+// dIn[y][x][c] = sum_{ky,kx,o} W[ky][kx][c][o] * dZ[y-ky][x-kx][o]
+template <int CIN, int COUT, int K, bool RELU>
+__global__ void __launch_bounds__(kTile* kTile)
+    k_conv_dx(const float* __restrict__ dA, const bf16* __restrict__ A, int Hout, int Wout,
+              const float* __restrict__ Wt, float* __restrict__ dIn) {
+  constexpr int TI = kTile + K - 1;
+  extern __shared__ __align__(16) float sm[];
+  float* sW = sm;
+  float* sD = sm + K * K * CIN * COUT;  // dZ tile: output rows y0-K+1 .. y0+kTile-1
+  const int Hin = Hout + K - 1, Win = Wout + K - 1;
+  const int x0 = blockIdx.x * kTile, y0 = blockIdx.y * kTile;
+  const int tid = threadIdx.x;
+  for (int i = tid; i < K * K * CIN * COUT; i += blockDim.x) sW[i] = Wt[i];
+  for (int i = tid; i < TI * TI * COUT; i += blockDim.x) {
+    const int o = i % COUT, p = i / COUT, px = p % TI, py = p / TI;
+    const int gy = y0 - (K - 1) + py, gx = x0 - (K - 1) + px;
+    float v = 0.f;
+    if (gy >= 0 && gy < Hout && gx >= 0 && gx < Wout)
+      v = dz_at(dA, A, ((size_t)gy * Wout + gx) * COUT + o, RELU);
+    sD[i] = v;
+  }
+  __syncthreads();
+  const int tx = tid % kTile, ty = tid / kTile;
+  const int y = y0 + ty, x = x0 + tx;
+  float acc[CIN];
+#pragma unroll
+  for (int c = 0; c < CIN; ++c) acc[c] = 0.f;
+  for (int ky = 0; ky < K; ++ky)
+    for (int kx = 0; kx < K; ++kx) {
+      const float* d = sD + ((ty - ky + K - 1) * TI + (tx - kx + K - 1)) * COUT;
+      const float* w = sW + (ky * K + kx) * CIN * COUT;
+      for (int o = 0; o < COUT; ++o) {
+        const float v = d[o];
+#pragma unroll
+        for (int c = 0; c < CIN; ++c) acc[c] = fmaf(v, w[c * COUT + o], acc[c]);
+      }
+    }
+  if (y >= Hin || x >= Win) return;
+#pragma unroll
+  for (int c = 0; c < CIN; ++c) dIn[((size_t)y * Win + x) * CIN + c] = acc[c];
+}
+
+// Per-CTA partial weight and bias gradients over a 16 x 16 tile of output
+// pixels: part[cta][e] for e over W (K*K*CIN*COUT entries) then b (COUT).
+template <int CIN, int COUT, int K, bool RELU>
+__global__ void __launch_bounds__(kTile* kTile)
+    k_conv_dw(const bf16* __restrict__ in, const float* __restrict__ dA, const bf16* __restrict__ A,
+              int Hout, int Wout, float* __restrict__ part) {
+  constexpr int TI = kTile + K - 1;
+  constexpr int NE = K * K * CIN * COUT + COUT;
+  extern __shared__ __align__(16) float sm[];
+  float* sIn = sm;                   // TI*TI*CIN
+  float* sD = sm + TI * TI * CIN;    // kTile*kTile*COUT
+  const int Win = Wout + K - 1, Hin = Hout + K - 1;
+  const int x0 = blockIdx.x * kTile, y0 = blockIdx.y * kTile;
+  const int tid = threadIdx.x;
+  for (int i = tid; i < TI * TI * CIN; i += blockDim.x) {
+    const int c = i % CIN, p = i / CIN, px = p % TI, py = p / TI;
+    const int gy = y0 + py, gx = x0 + px;
+    sIn[i] = (gy < Hin && gx < Win) ? __bfloat162float(in[((size_t)gy * Win + gx) * CIN + c]) : 0.f;
+  }
+  for (int i = tid; i < kTile * kTile * COUT; i += blockDim.x) {
+    const int o = i % COUT, p = i / COUT, px = p % kTile, py = p / kTile;
+    const int gy = y0 + py, gx = x0 + px;
+    sD[i] = (gy < Hout && gx < Wout) ? dz_at(dA, A, ((size_t)gy * Wout + gx) * COUT + o, RELU) : 0.f;
+  }
+  __syncthreads();
+  float* dst = part + (size_t)(blockIdx.y * gridDim.x + blockIdx.x) * NE;
+  for (int e = tid; e < NE; e += blockDim.x) {
+    float s = 0.f;
+    if (e < K * K * CIN * COUT) {
+      const int o = e % COUT, c = (e / COUT) % CIN, kk = e / (COUT * CIN), kx = kk % K, ky = kk / K;
+      for (int p = 0; p < kTile * kTile; ++p) {
+        const int px = p % kTile, py = p / kTile;
+        s = fmaf(sIn[((py + ky) * TI + (px + kx)) * CIN + c], sD[p * COUT + o], s);
+      }
+    } else {
+      const int o = e - K * K * CIN * COUT;
+      for (int p = 0; p < kTile * kTile; ++p) s += sD[p * COUT + o];
+    }
+    dst[e] = s;
+  }
+}
+
+// g[e] = sum over CTAs (fixed order) of part[cta][e]
+__global__ void k_reduce_parts(const float* __restrict__ part, int nparts, int ne,
+                               float* __restrict__ g) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= ne) return;
+  float s = 0.f;
+  for (int k = 0; k < nparts; ++k) s += part[(size_t)k * ne + e];
+  g[e] = s;
+}
+
+// ------------------------------------------------------------------ loss
+// dY = (Y - T) / N; part[cta] = sum of (Y - T)^2 over the CTA's pixels.
+__global__ void k_mse(const float* __restrict__ Y, const float* __restrict__ T, int n,
+                      float* __restrict__ dY, float* __restrict__ part) {
+  __shared__ float s[256];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  float d = 0.f;
+  if (i < n) {
+    d = Y[i] - T[i];
+    dY[i] = d / (float)n;
+  }
+  s[threadIdx.x] = d * d;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) s[threadIdx.x] += s[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = s[0];
+}
+
+// ------------------------------------------------------------------ Adam
+__global__ void k_adam(float* __restrict__ p, float* __restrict__ m, float* __restrict__ v,
+                       const float* __restrict__ g, int n, float lr, float b1, float b2, float eps,
+                       float c1, float c2) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float gi = g[i];
+  const float mi = b1 * m[i] + (1.f - b1) * gi;
+  const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+  m[i] = mi;
+  v[i] = vi;
+  p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
+// BF16 rounding of the FP32 master weights (the forward pass and the data
+// gradient use BF16 weights, held here as floats).
+__global__ void k_round_bf16(const float* __restrict__ p, float* __restrict__ q, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) q[i] = __bfloat162float(__float2bfloat16(p[i]));
+}
+
+// ----------------------------------------------------- lattice <-> coarse
+__constant__ float c_hx[9] = {0.f, 1.f, 0.70710678f, 0.f, -0.70710678f, -1.f, -0.70710678f, 0.f,
+                              0.70710678f};
+__constant__ float c_hy[9] = {0.f, 0.f, 0.70710678f, 1.f, 0.70710678f, 0.f, -0.70710678f, -1.f,
+                              -0.70710678f};
+
+// X[i][j][0..2] over the padded coarse grid (kHalo cells around): pedestrian
+// count and heading sums of the s x s cell, / s^2; wrapped or zero outside.
+__global__ void k_coarse_in(Geo g, const uint8_t* __restrict__ ocls, int s, int Hc, int Wc,
+                            bf16* __restrict__ X) {
+  const int Wp = Wc + 2 * kHalo, Hp = Hc + 2 * kHalo;
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= Wp * Hp) return;
+  int ci = idx / Wp - kHalo, cj = idx % Wp - kHalo;
+  float n = 0.f, hx = 0.f, hy = 0.f;
+  bool ok = true;
+  if (ci < 0 || ci >= Hc) {
+    if (g.py) ci = (ci + Hc) % Hc; else ok = false;
+  }
+  if (cj < 0 || cj >= Wc) {
+    if (g.px) cj = (cj + Wc) % Wc; else ok = false;
+  }
+  if (ok) {
+    for (int dy = 0; dy < s; ++dy) {
+      const uint8_t* row = ocls + (size_t)(ci * s + dy) * g.opitch + cj * s;
+      for (int dx = 0; dx < s; ++dx) {
+        const int v = row[dx];
+        if (v) {
+          n += 1.f;
+          hx += c_hx[v - 1];
+          hy += c_hy[v - 1];
+        }
+      }
+    }
+  }
+  const float inv = 1.f / (float)(s * s);
+  X[(size_t)idx * 3 + 0] = __float2bfloat16(n * inv);
+  X[(size_t)idx * 3 + 1] = __float2bfloat16(hx * inv);
+  X[(size_t)idx * 3 + 2] = __float2bfloat16(hy * inv);
+}
+
+// T[i][j] = mean over the cell of (F - Fnear) / scale: the far part of the
+// exact field (Fnear holds the static field plus the near pedestrian part).
+__global__ void k_targets(const float* __restrict__ F, const float* __restrict__ Fnear, int W,
+                          int s, int Hc, int Wc, float inv_scale, float* __restrict__ T) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= Hc * Wc) return;
+  const int ci = idx / Wc, cj = idx % Wc;
+  double acc = 0.0;
+  for (int dy = 0; dy < s; ++dy)
+    for (int dx = 0; dx < s; ++dx) {
+      const size_t c = (size_t)(ci * s + dy) * W + cj * s + dx;
+      acc += (double)(F[c] - Fnear[c]);
+    }
+  T[idx] = (float)(acc / (s * s)) * inv_scale;
+}
+
+// out = Fnear + scale * bilinear(Y) between coarse cell centres.
+__global__ void k_combine(Geo g, const float* __restrict__ Fnear, const float* __restrict__ Y,
+                          int s, int Hc, int Wc, float scale, float* __restrict__ out) {
+  const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (i >= (size_t)g.W * g.H) return;
+  const int y = (int)(i / g.W), x = (int)(i % g.W);
+  const float fy = (y + 0.5f) / s - 0.5f, fx = (x + 0.5f) / s - 0.5f;
+  const int y0 = (int)floorf(fy), x0 = (int)floorf(fx);
+  const float ty = fy - y0, tx = fx - x0;
+  float v = 0.f;
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      int yy = y0 + a, xx = x0 + b;
+      if (g.py) yy = (yy + Hc) % Hc; else yy = min(max(yy, 0), Hc - 1);
+      if (g.px) xx = (xx + Wc) % Wc; else xx = min(max(xx, 0), Wc - 1);
+      v += (a ? ty : 1.f - ty) * (b ? tx : 1.f - tx) * Y[(size_t)yy * Wc + xx];
+    }
+  out[i] = Fnear[i] + scale * v;
+}
+
+// number of pedestrians (live, in bin order) whose two decisions differ;
+// sums of |Fa - Fb| and |Fb - Fs| over the lattice (FP64 partials per CTA)
+__global__ void k_diff_choices(const int32_t* __restrict__ rec_id, const int32_t* __restrict__ bin_start,
+                               int nbins, const uint8_t* __restrict__ a, const uint8_t* __restrict__ b,
+                               unsigned long long* __restrict__ cnt) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  bool d = false;
+  if (i < bin_start[nbins]) {
+    const int p = rec_id[i];
+    d = a[p] != b[p];
+  }
+  const unsigned n = __popc(__ballot_sync(0xffffffffu, d));
+  if ((threadIdx.x & 31) == 0 && n) atomicAdd(cnt, (unsigned long long)n);
+}
+
+__global__ void k_field_err(const float* __restrict__ Fa, const float* __restrict__ Fb,
+                            const float* __restrict__ Fs, size_t n, double* __restrict__ part) {
+  __shared__ double s1[256], s2[256];
+  double a = 0.0, b = 0.0;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x) {
+    a += fabs((double)Fa[i] - (double)Fb[i]);
+    b += fabs((double)Fb[i] - (double)Fs[i]);
+  }
+  s1[threadIdx.x] = a;
+  s2[threadIdx.x] = b;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      s1[threadIdx.x] += s1[threadIdx.x + o];
+      s2[threadIdx.x] += s2[threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    part[2 * blockIdx.x] = s1[0];
+    part[2 * blockIdx.x + 1] = s2[0];
+  }
+}
+
+inline int cdiv(int a, int b) { return (a + b - 1) / b; }
+
+}  // namespace
+
+// ======================================================================
+struct sfm_surrogate {
+  sfm_surrogate_cfg cfg{};
+  cudaStream_t stream = nullptr;
+  std::string err;
+  // parameters (internal layout), BF16-rounded copies, Adam state, gradients
+  float *p = nullptr, *pq = nullptr, *m = nullptr, *v = nullptr, *g = nullptr;
+  int adam_t = 0;
+  // activations for an image of (Hc + 2 kHalo) x (Wc + 2 kHalo) coarse cells
+  int Hc = 0, Wc = 0;
+  bf16 *X = nullptr, *A1 = nullptr, *A2 = nullptr, *A3 = nullptr;
+  float *Y = nullptr, *T = nullptr, *dY = nullptr, *dA3 = nullptr, *dA2 = nullptr,
+        *dA1 = nullptr, *part = nullptr;
+  size_t part_cap = 0;
+  // lattice-sized buffers
+  size_t nsu = 0;
+  float *Fnear = nullptr, *Fsur = nullptr;
+  uint8_t* choice2 = nullptr;
+  int choice_cap = 0;
+  float* CTnear = nullptr;  // near-field class tables
+  int near_r_built = -1;
+  double* red = nullptr;
+  unsigned long long* cnt = nullptr;
+  std::vector<void*> allocs;
+};
+
+namespace {
+
+sfm_status sfail(sfm_surrogate* s, sfm_status st, const std::string& msg) {
+  if (s) s->err = msg;
+  else set_create_error(msg);
+  return st;
+}
+
+#define SCU(call)                                                                     \
+  do {                                                                                \
+    cudaError_t e_ = (call);                                                          \
+    if (e_ != cudaSuccess)                                                            \
+      return sfail(S, e_ == cudaErrorMemoryAllocation ? SFM_ENOMEM : SFM_ECUDA,       \
+                   std::string(#call) + ": " + cudaGetErrorString(e_));               \
+  } while (0)
+
+template <class T>
+sfm_status salloc(sfm_surrogate* S, T** p, size_t n) {
+  void* q = nullptr;
+  SCU(cudaMalloc(&q, n * sizeof(T) > 0 ? n * sizeof(T) : 16));
+  S->allocs.push_back(q);
+  *p = static_cast<T*>(q);
+  return SFM_OK;
+}
+
+void sfree(sfm_surrogate* S, void* p) {
+  if (!p) return;
+  for (size_t i = 0; i < S->allocs.size(); ++i)
+    if (S->allocs[i] == p) {
+      S->allocs.erase(S->allocs.begin() + (long)i);
+      break;
+    }
+  cudaFree(p);
+}
+
+#define STRY(x)                  \
+  do {                           \
+    sfm_status s_ = (x);         \
+    if (s_ != SFM_OK) return s_; \
+  } while (0)
+
+// activation buffers for a padded input of (Hc + 2h) x (Wc + 2h) cells
+sfm_status ensure_image(sfm_surrogate* S, int Hc, int Wc) {
+  if (S->Hc == Hc && S->Wc == Wc && S->X) return SFM_OK;
+  for (void* q : {(void*)S->X, (void*)S->A1, (void*)S->A2, (void*)S->A3, (void*)S->Y, (void*)S->T,
+                  (void*)S->dY, (void*)S->dA3, (void*)S->dA2, (void*)S->dA1})
+    sfree(S, q);
+  const size_t p0 = (size_t)(Hc + 2 * kHalo) * (Wc + 2 * kHalo);
+  const size_t p1 = (size_t)(Hc + 6) * (Wc + 6), p2 = (size_t)(Hc + 4) * (Wc + 4),
+               p3 = (size_t)(Hc + 2) * (Wc + 2), p4 = (size_t)Hc * Wc;
+  STRY(salloc(S, &S->X, p0 * 3));
+  STRY(salloc(S, &S->A1, p1 * 32));
+  STRY(salloc(S, &S->A2, p2 * 32));
+  STRY(salloc(S, &S->A3, p3 * 32));
+  STRY(salloc(S, &S->Y, p4));
+  STRY(salloc(S, &S->T, p4));
+  STRY(salloc(S, &S->dY, p4));
+  STRY(salloc(S, &S->dA3, p3 * 32));
+  STRY(salloc(S, &S->dA2, p2 * 32));
+  STRY(salloc(S, &S->dA1, p1 * 32));
+  S->Hc = Hc;
+  S->Wc = Wc;
+  return SFM_OK;
+}
+
+template <int CIN, int COUT, int K>
+size_t fwd_smem() {
+  return ((size_t)K * K * CIN * COUT + (size_t)(kTile + K - 1) * (kTile + K - 1) * CIN) * 4;
+}
+template <int CIN, int COUT, int K>
+size_t dx_smem() {
+  return ((size_t)K * K * CIN * COUT + (size_t)(kTile + K - 1) * (kTile + K - 1) * COUT) * 4;
+}
+template <int CIN, int COUT, int K>
+size_t dw_smem() {
+  return ((size_t)(kTile + K - 1) * (kTile + K - 1) * CIN + (size_t)kTile * kTile * COUT) * 4;
+}
+
+template <int CIN, int COUT, int K, bool RELU>
+void conv_fwd(const bf16* in, int Hin, int Win, const float* W, const float* b, bf16* out_bf,
+              float* out_f, cudaStream_t s) {
+  const size_t sm = fwd_smem<CIN, COUT, K>();
+  cudaFuncSetAttribute(k_conv_fwd<CIN, COUT, K, RELU>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)sm);
+  const int Ho = Hin - K + 1, Wo = Win - K + 1;
+  dim3 grid(cdiv(Wo, kTile), cdiv(Ho, kTile));
+  k_conv_fwd<CIN, COUT, K, RELU><<<grid, kTile * kTile, sm, s>>>(in, Hin, Win, W, b, out_bf, out_f);
+}
+
+template <int CIN, int COUT, int K, bool RELU>
+void conv_dx(const float* dA, const bf16* A, int Hout, int Wout, const float* W, float* dIn,
+             cudaStream_t s) {
+  const size_t sm = dx_smem<CIN, COUT, K>();
+  cudaFuncSetAttribute(k_conv_dx<CIN, COUT, K, RELU>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)sm);
+  dim3 grid(cdiv(Wout + K - 1, kTile), cdiv(Hout + K - 1, kTile));
+  k_conv_dx<CIN, COUT, K, RELU><<<grid, kTile * kTile, sm, s>>>(dA, A, Hout, Wout, W, dIn);
+}
+
+template <int CIN, int COUT, int K, bool RELU>
+sfm_status conv_dw(sfm_surrogate* S, const bf16* in, const float* dA, const bf16* A, int Hout,
+                   int Wout, float* gW, cudaStream_t s) {
+  constexpr int NE = K * K * CIN * COUT + COUT;
+  dim3 grid(cdiv(Wout, kTile), cdiv(Hout, kTile));
+  const size_t nparts = (size_t)grid.x * grid.y;
+  if (nparts * NE > S->part_cap) {
+    sfree(S, S->part);
+    STRY(salloc(S, &S->part, nparts * NE));
+    S->part_cap = nparts * NE;
+  }
+  const size_t sm = dw_smem<CIN, COUT, K>();
+  cudaFuncSetAttribute(k_conv_dw<CIN, COUT, K, RELU>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)sm);
+  k_conv_dw<CIN, COUT, K, RELU><<<grid, kTile * kTile, sm, s>>>(in, dA, A, Hout, Wout, S->part);
+  // W block then b block are adjacent in the flat gradient (W at kOffW, b right after)
+  k_reduce_parts<<<cdiv(NE, 256), 256, 0, s>>>(S->part, (int)nparts, NE, gW);
+  return SFM_OK;
+}
+
+// forward of the whole padded image currently in S->X
+void forward(sfm_surrogate* S, cudaStream_t s) {
+  const int Hp = S->Hc + 2 * kHalo, Wp = S->Wc + 2 * kHalo;
+  const float* q = S->pq;
+  conv_fwd<3, 32, 5, true>(S->X, Hp, Wp, q + kOffW[0], q + kOffB[0], S->A1, nullptr, s);
+  conv_fwd<32, 32, 3, true>(S->A1, Hp - 4, Wp - 4, q + kOffW[1], q + kOffB[1], S->A2, nullptr, s);
+  conv_fwd<32, 32, 3, true>(S->A2, Hp - 6, Wp - 6, q + kOffW[2], q + kOffB[2], S->A3, nullptr, s);
+  conv_fwd<32, 1, 3, false>(S->A3, Hp - 8, Wp - 8, q + kOffW[3], q + kOffB[3], nullptr, S->Y, s);
+}
+
+// loss and gradients (into S->g) for the image in S->X and targets in S->T
+sfm_status backward(sfm_surrogate* S, float* loss_out, cudaStream_t s) {
+  const int Hc = S->Hc, Wc = S->Wc, n = Hc * Wc;
+  const int nb = cdiv(n, 256);
+  if ((size_t)nb > S->part_cap) {
+    sfree(S, S->part);
+    STRY(salloc(S, &S->part, (size_t)nb));
+    S->part_cap = nb;
+  }
+  k_mse<<<nb, 256, 0, s>>>(S->Y, S->T, n, S->dY, S->part);
+  std::vector<float> hp(nb);
+  SCU(cudaMemcpyAsync(hp.data(), S->part, nb * sizeof(float), cudaMemcpyDeviceToHost, s));
+  SCU(cudaStreamSynchronize(s));
+  double L = 0.0;
+  for (float x : hp) L += x;
+  if (loss_out) *loss_out = (float)(0.5 * L / n);
+  const float* q = S->pq;
+  // layer 4 (linear), 3, 2, 1
+  STRY((conv_dw<32, 1, 3, false>(S, S->A3, S->dY, nullptr, Hc, Wc, S->g + kOffW[3], s)));
+  conv_dx<32, 1, 3, false>(S->dY, nullptr, Hc, Wc, q + kOffW[3], S->dA3, s);
+  STRY((conv_dw<32, 32, 3, true>(S, S->A2, S->dA3, S->A3, Hc + 2, Wc + 2, S->g + kOffW[2], s)));
+  conv_dx<32, 32, 3, true>(S->dA3, S->A3, Hc + 2, Wc + 2, q + kOffW[2], S->dA2, s);
+  STRY((conv_dw<32, 32, 3, true>(S, S->A1, S->dA2, S->A2, Hc + 4, Wc + 4, S->g + kOffW[1], s)));
+  conv_dx<32, 32, 3, true>(S->dA2, S->A2, Hc + 4, Wc + 4, q + kOffW[1], S->dA1, s);
+  STRY((conv_dw<3, 32, 5, true>(S, S->X, S->dA1, S->A1, Hc + 6, Wc + 6, S->g + kOffW[0], s)));
+  SCU(cudaGetLastError());
+  return SFM_OK;
+}
+
+// layout conversions between the public order (per layer: W[o][c][ky][kx], b[o])
+// and the internal one (W[ky][kx][c][o], b[o])
+void to_internal(const float* pub, float* in) {
+  const int dims[4][3] = {{3, 32, 5}, {32, 32, 3}, {32, 32, 3}, {32, 1, 3}};
+  size_t off = 0;
+  for (int l = 0; l < 4; ++l) {
+    const int C = dims[l][0], O = dims[l][1], K = dims[l][2];
+    for (int o = 0; o < O; ++o)
+      for (int c = 0; c < C; ++c)
+        for (int ky = 0; ky < K; ++ky)
+          for (int kx = 0; kx < K; ++kx)
+            in[kOffW[l] + ((ky * K + kx) * C + c) * O + o] = pub[off++];
+    for (int o = 0; o < O; ++o) in[kOffB[l] + o] = pub[off++];
+  }
+}
+
+void to_public(const float* in, float* pub) {
+  const int dims[4][3] = {{3, 32, 5}, {32, 32, 3}, {32, 32, 3}, {32, 1, 3}};
+  size_t off = 0;
+  for (int l = 0; l < 4; ++l) {
+    const int C = dims[l][0], O = dims[l][1], K = dims[l][2];
+    for (int o = 0; o < O; ++o)
+      for (int c = 0; c < C; ++c)
+        for (int ky = 0; ky < K; ++ky)
+          for (int kx = 0; kx < K; ++kx)
+            pub[off++] = in[kOffW[l] + ((ky * K + kx) * C + c) * O + o];
+    for (int o = 0; o < O; ++o) pub[off++] = in[kOffB[l] + o];
+  }
+}
+
+sfm_status check_ctx(sfm_surrogate* S, sfm_ctx* ctx) {
+  if (!ctx || ctx->batch) return sfail(S, SFM_EINVAL, "needs a single-lattice context");
+  if (!ctx->placed) return sfail(S, SFM_ESTATE, "context has no pedestrians placed");
+  if (ctx->bands > 1) return sfail(S, SFM_ESTATE, "context is banded (no full field)");
+  const int s = S->cfg.coarsen;
+  if (ctx->geo.W % s || ctx->geo.H % s)
+    return sfail(S, SFM_EINVAL, "lattice sides must be multiples of the coarsening factor");
+  if (ctx->geo.W / s < 1 || ctx->geo.H / s < 1) return sfail(S, SFM_EINVAL, "lattice too small");
+  if (S->cfg.near_radius > ctx->geo.r)
+    return sfail(S, SFM_EINVAL, "near radius larger than the field radius");
+  return SFM_OK;
+}
+
+// lattice buffers and near-field tables for ctx
+sfm_status ensure_lattice(sfm_surrogate* S, sfm_ctx* ctx) {
+  const size_t nsu = (size_t)ctx->geo.W * ctx->geo.H;
+  if (nsu != S->nsu) {
+    sfree(S, S->Fnear);
+    sfree(S, S->Fsur);
+    S->Fnear = S->Fsur = nullptr;
+    STRY(salloc(S, &S->Fnear, nsu));
+    STRY(salloc(S, &S->Fsur, nsu));
+    S->nsu = nsu;
+  }
+  if (ctx->cap > S->choice_cap) {
+    sfree(S, S->choice2);
+    STRY(salloc(S, &S->choice2, (size_t)ctx->cap));
+    S->choice_cap = ctx->cap;
+  }
+  const int rn = S->cfg.near_radius;
+  if (S->near_r_built != rn || !S->CTnear) {
+    sfree(S, S->CTnear);
+    S->CTnear = nullptr;
+    const size_t n = class_table_floats(rn);
+    if (n) {
+      STRY(salloc(S, &S->CTnear, n));
+      launch_class_tables(rn, ctx->prm, S->CTnear, S->stream);
+    }
+    S->near_r_built = rn;
+  }
+  return SFM_OK;
+}
+
+// Fnear = Fs + pedestrian field within rn of the context's current state
+// (bins must be current)
+void near_field(sfm_surrogate* S, sfm_ctx* ctx) {
+  Geo gn = ctx->geo;
+  gn.r = S->cfg.near_radius;
+  Tables tb = ctx->tables();
+  tb.CT = S->CTnear;
+  launch_field(gn, ctx->bin_start, ctx->rec, tb, ctx->Fs, S->Fnear, 0, 0, gn.H, ctx->ctr,
+               ctx->stream);
+}
+
+void coarse_inputs(sfm_surrogate* S, sfm_ctx* ctx) {
+  const int Hp = S->Hc + 2 * kHalo, Wp = S->Wc + 2 * kHalo;
+  k_coarse_in<<<cdiv(Hp * Wp, 256), 256, 0, ctx->stream>>>(ctx->geo, ctx->ocls, S->cfg.coarsen,
+                                                            S->Hc, S->Wc, S->X);
+}
+
+void surrogate_field(sfm_surrogate* S, sfm_ctx* ctx) {
+  ctx_run_bins(ctx);
+  near_field(S, ctx);
+  coarse_inputs(S, ctx);
+  forward(S, ctx->stream);
+  const size_t nsu = (size_t)ctx->geo.W * ctx->geo.H;
+  k_combine<<<(unsigned)((nsu + 255) / 256), 256, 0, ctx->stream>>>(
+      ctx->geo, S->Fnear, S->Y, S->cfg.coarsen, S->Hc, S->Wc, S->cfg.target_scale, S->Fsur);
+}
+
+void round_params(sfm_surrogate* S) {
+  k_round_bf16<<<cdiv(kNParams, 256), 256, 0, S->stream>>>(S->p, S->pq, kNParams);
+}
+
+}  // namespace
+
+extern "C" {
+
+int32_t sfm_surrogate_nparams(void) { return kNParams; }
+
+sfm_status sfm_surrogate_create(const sfm_surrogate_cfg* cfg, void* stream, sfm_surrogate** out) {
+  if (out) *out = nullptr;
+  if (!cfg || !out) return sfail(nullptr, SFM_EINVAL, "NULL argument");
+  if (cfg->coarsen < 1 || cfg->coarsen > 64 || cfg->near_radius < 0 ||
+      cfg->near_radius > SFM_MAX_RADIUS || !(cfg->target_scale > 0.f))
+    return sfail(nullptr, SFM_EINVAL, "bad surrogate configuration");
+  sfm_surrogate* S = new sfm_surrogate;
+  S->cfg = *cfg;
+  S->stream = static_cast<cudaStream_t>(stream);
+  auto bail = [&](sfm_status st) {
+    set_create_error(S->err);
+    sfm_surrogate_destroy(S);
+    return st;
+  };
+  sfm_status st;
+  if ((st = salloc(S, &S->p, kNParams)) != SFM_OK || (st = salloc(S, &S->pq, kNParams)) != SFM_OK ||
+      (st = salloc(S, &S->m, kNParams)) != SFM_OK || (st = salloc(S, &S->v, kNParams)) != SFM_OK ||
+      (st = salloc(S, &S->g, kNParams)) != SFM_OK || (st = salloc(S, &S->red, 2 * 1024)) != SFM_OK ||
+      (st = salloc(S, &S->cnt, 1)) != SFM_OK)
+    return bail(st);
+  cudaMemsetAsync(S->p, 0, kNParams * sizeof(float), S->stream);
+  cudaMemsetAsync(S->m, 0, kNParams * sizeof(float), S->stream);
+  cudaMemsetAsync(S->v, 0, kNParams * sizeof(float), S->stream);
+  round_params(S);
+  if (cudaStreamSynchronize(S->stream) != cudaSuccess) {
+    S->err = "surrogate set-up failed";
+    return bail(SFM_ECUDA);
+  }
+  *out = S;
+  return SFM_OK;
+}
+
+void sfm_surrogate_destroy(sfm_surrogate* S) {
+  if (!S) return;
+  cudaStreamSynchronize(S->stream);
+  for (void* p : S->allocs) cudaFree(p);
+  delete S;
+}
+
+const char* sfm_surrogate_last_error(const sfm_surrogate* S) { return S ? S->err.c_str() : ""; }
+
+sfm_status sfm_surrogate_set_params(sfm_surrogate* S, const float* params) {
+  if (!S || !params) return SFM_EINVAL;
+  std::vector<float> in(kNParams);
+  to_internal(params, in.data());
+  SCU(cudaMemcpyAsync(S->p, in.data(), kNParams * sizeof(float), cudaMemcpyHostToDevice, S->stream));
+  SCU(cudaMemsetAsync(S->m, 0, kNParams * sizeof(float), S->stream));
+  SCU(cudaMemsetAsync(S->v, 0, kNParams * sizeof(float), S->stream));
+  S->adam_t = 0;
+  round_params(S);
+  SCU(cudaStreamSynchronize(S->stream));
+  return SFM_OK;
+}
+
+sfm_status sfm_surrogate_get_params(sfm_surrogate* S, float* params) {
+  if (!S || !params) return SFM_EINVAL;
+  std::vector<float> in(kNParams);
+  SCU(cudaMemcpyAsync(in.data(), S->p, kNParams * sizeof(float), cudaMemcpyDeviceToHost, S->stream));
+  SCU(cudaStreamSynchronize(S->stream));
+  to_public(in.data(), params);
+  return SFM_OK;
+}
+
+sfm_status sfm_surrogate_grad(sfm_surrogate* S, int32_t Hin, int32_t Win, const float* X,
+                              const float* T, float* loss, float* grads) {
+  if (!S || !X || !T) return SFM_EINVAL;
+  if (Hin <= 2 * kHalo || Win <= 2 * kHalo) return sfail(S, SFM_EINVAL, "image too small");
+  const int Hc = Hin - 2 * kHalo, Wc = Win - 2 * kHalo;
+  STRY(ensure_image(S, Hc, Wc));
+  // X given channel-planar [3][Hin][Win]; the network reads channel-last BF16
+  std::vector<bf16> hx((size_t)Hin * Win * 3);
+  for (int c = 0; c < 3; ++c)
+    for (int i = 0; i < Hin * Win; ++i) hx[(size_t)i * 3 + c] = __float2bfloat16(X[(size_t)c * Hin * Win + i]);
+  SCU(cudaMemcpyAsync(S->X, hx.data(), hx.size() * sizeof(bf16), cudaMemcpyHostToDevice, S->stream));
+  SCU(cudaMemcpyAsync(S->T, T, (size_t)Hc * Wc * sizeof(float), cudaMemcpyHostToDevice, S->stream));
+  forward(S, S->stream);
+  STRY(backward(S, loss, S->stream));
+  if (grads) {
+    std::vector<float> in(kNParams);
+    SCU(cudaMemcpyAsync(in.data(), S->g, kNParams * sizeof(float), cudaMemcpyDeviceToHost, S->stream));
+    SCU(cudaStreamSynchronize(S->stream));
+    to_public(in.data(), grads);
+  }
+  SCU(cudaStreamSynchronize(S->stream));
+  return SFM_OK;
+}
+
+sfm_status sfm_surrogate_train(sfm_surrogate* S, sfm_ctx* ctx, int32_t iters, float* loss_curve) {
+  if (!S) return SFM_EINVAL;
+  STRY(check_ctx(S, ctx));
+  STRY(ensure_lattice(S, ctx));
+  const int s = S->cfg.coarsen;
+  STRY(ensure_image(S, ctx->geo.H / s, ctx->geo.W / s));
+  cudaStream_t st = ctx->stream;
+  if (st != S->stream) {
+    SCU(cudaStreamSynchronize(S->stream));
+  }
+  S->stream = st;
+  const float b1 = S->cfg.beta1, b2 = S->cfg.beta2;
+  for (int it = 0; it < iters; ++it) {
+    // exact field of the current state, its near part, inputs and targets
+    ctx_run_bins(ctx);
+    ctx_field_rows(ctx, ctx->F, 0, ctx->geo.H, 0, false);
+    near_field(S, ctx);
+    coarse_inputs(S, ctx);
+    k_targets<<<cdiv(S->Hc * S->Wc, 256), 256, 0, st>>>(ctx->F, S->Fnear, ctx->geo.W, s, S->Hc,
+                                                        S->Wc, 1.f / S->cfg.target_scale, S->T);
+    forward(S, st);
+    float L = 0.f;
+    STRY(backward(S, &L, st));
+    if (loss_curve) loss_curve[it] = L;
+    ++S->adam_t;
+    const float c1 = 1.f - powf(b1, (float)S->adam_t), c2 = 1.f - powf(b2, (float)S->adam_t);
+    k_adam<<<cdiv(kNParams, 256), 256, 0, st>>>(S->p, S->m, S->v, S->g, kNParams, S->cfg.lr, b1, b2,
+                                                S->cfg.eps, c1, c2);
+    round_params(S);
+    // the crowd moves on: a tick of the exact path gives the next sample
+    const sfm_status ss = sfm_step(ctx, 1);
+    if (ss != SFM_OK) return sfail(S, ss, std::string("training tick: ") + ctx->err);
+  }
+  SCU(cudaStreamSynchronize(st));
+  SCU(cudaGetLastError());
+  return SFM_OK;
+}
+
+sfm_status sfm_surrogate_field(sfm_surrogate* S, sfm_ctx* ctx, float* out, int32_t on_device) {
+  if (!S || !out) return SFM_EINVAL;
+  STRY(check_ctx(S, ctx));
+  STRY(ensure_lattice(S, ctx));
+  const int s = S->cfg.coarsen;
+  STRY(ensure_image(S, ctx->geo.H / s, ctx->geo.W / s));
+  S->stream = ctx->stream;
+  surrogate_field(S, ctx);
+  SCU(cudaMemcpyAsync(out, S->Fsur, S->nsu * sizeof(float),
+                      on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ctx->stream));
+  SCU(cudaStreamSynchronize(ctx->stream));
+  SCU(cudaGetLastError());
+  return SFM_OK;
+}
+
+sfm_status sfm_surrogate_eval(sfm_surrogate* S, sfm_ctx* ctx, double* field_rel_err,
+                              double* flip_rate, double* ms_surrogate, double* ms_exact) {
+  if (!S) return SFM_EINVAL;
+  STRY(check_ctx(S, ctx));
+  STRY(ensure_lattice(S, ctx));
+  const int s = S->cfg.coarsen;
+  STRY(ensure_image(S, ctx->geo.H / s, ctx->geo.W / s));
+  S->stream = ctx->stream;
+  cudaStream_t st = ctx->stream;
+  cudaEvent_t e0, e1, e2;
+  SCU(cudaEventCreate(&e0));
+  SCU(cudaEventCreate(&e1));
+  SCU(cudaEventCreate(&e2));
+  // exact field (bins + gather) and the surrogate field of the same state
+  SCU(cudaEventRecord(e0, st));
+  ctx_run_bins(ctx);
+  ctx_field_rows(ctx, ctx->F, 0, ctx->geo.H, 0, false);
+  SCU(cudaEventRecord(e1, st));
+  surrogate_field(S, ctx);
+  SCU(cudaEventRecord(e2, st));
+  // decisions on each field
+  const Geo& g = ctx->geo;
+  const Tables tb = ctx->tables();
+  const int nbins = g.nbx * g.nby;
+  launch_decide(ctx->n, ctx->rec_id, ctx->bin_start, 0, nbins, ctx->xy, ctx->heading, ctx->goal,
+                ctx->cell, ctx->ocls, ctx->D, ctx->F, 0, -1, -1, 0, 0, g.H, g, ctx->prm.beta, tb,
+                ctx->choice, st);
+  launch_decide(ctx->n, ctx->rec_id, ctx->bin_start, 0, nbins, ctx->xy, ctx->heading, ctx->goal,
+                ctx->cell, ctx->ocls, ctx->D, S->Fsur, 0, -1, -1, 0, 0, g.H, g, ctx->prm.beta, tb,
+                S->choice2, st);
+  SCU(cudaMemsetAsync(S->cnt, 0, sizeof(unsigned long long), st));
+  if (ctx->n > 0)
+    k_diff_choices<<<cdiv(ctx->n, 256), 256, 0, st>>>(ctx->rec_id, ctx->bin_start, nbins,
+                                                      ctx->choice, S->choice2, S->cnt);
+  k_field_err<<<1024, 256, 0, st>>>(S->Fsur, ctx->F, ctx->Fs, S->nsu, S->red);
+  std::vector<double> red(2048);
+  unsigned long long cnt = 0;
+  int nrec = 0;
+  SCU(cudaMemcpyAsync(red.data(), S->red, red.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+  SCU(cudaMemcpyAsync(&cnt, S->cnt, sizeof(cnt), cudaMemcpyDeviceToHost, st));
+  SCU(cudaMemcpyAsync(&nrec, ctx->bin_start + nbins, sizeof(int), cudaMemcpyDeviceToHost, st));
+  SCU(cudaStreamSynchronize(st));
+  SCU(cudaGetLastError());
+  double a = 0.0, b = 0.0;
+  for (int i = 0; i < 1024; ++i) {
+    a += red[2 * i];
+    b += red[2 * i + 1];
+  }
+  float t_ex = 0.f, t_su = 0.f;
+  cudaEventElapsedTime(&t_ex, e0, e1);
+  cudaEventElapsedTime(&t_su, e1, e2);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaEventDestroy(e2);
+  if (field_rel_err) *field_rel_err = b > 0 ? a / b : 0.0;
+  if (flip_rate) *flip_rate = nrec > 0 ? (double)cnt / nrec : 0.0;
+  if (ms_surrogate) *ms_surrogate = t_su;
+  if (ms_exact) *ms_exact = t_ex;
+  return SFM_OK;
+}
+
+}  // extern "C"

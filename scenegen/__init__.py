@@ -317,6 +317,25 @@ def training_scene(seed: int, side=1024, r=40, kind="floor") -> Scene:
     return sc
 
 
+def training_canvas(side=4096, r=40, tile=128, rho_lo=0.002, rho_hi=0.25, seed=500,
+                    name="canvas") -> Scene:
+    """Periodic torus without walls for surrogate training: each tile x tile
+    block gets its own crowd density, log-uniform in [rho_lo, rho_hi] (from the
+    sparse large floor to the dense corridor ends); pedestrians walk in fixed
+    random directions (classes 1..8), headed that way."""
+    rng = np.random.default_rng(seed)
+    nt = side // tile
+    rho = np.exp(rng.uniform(np.log(rho_lo), np.log(rho_hi), size=(nt, nt)))
+    u = rng.random((side, side))
+    dens = np.kron(rho, np.ones((tile, tile)))
+    ys, xs = np.nonzero(u < dens)
+    xy = np.stack([xs, ys], axis=1).astype(np.int32)
+    goal = rng.integers(1, 9, size=len(xy)).astype(np.uint8)
+    cell = np.zeros((side, side), np.uint8)
+    return Scene(name, side, side, 1, 1, cell, xy, goal.copy(), goal,
+                 _params(r=r, seed=seed), 1)
+
+
 def config(i: int, **kw):
     """The five evaluation configurations by number (1-based)."""
     if i == 1:
