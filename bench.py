@@ -29,6 +29,26 @@ sys.path.insert(0, ROOT)
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 FLOPS_PER_PAIR = 6.0  # three FP32 multiply-adds per (su, pedestrian-in-window) pair
+# DRAM bytes (read + write) per banded launch of the field gather on the
+# 16384^2 floor with 4 bands, from a one-pass ncu capture of this benchmark
+# (dram__bytes_read.sum + dram__bytes_write.sum); valid only while the
+# gather's sources hash to the value they had when it was taken.
+GATHER_TRAFFIC = {"sha1": "716c2cff6517126f7342cce272ca401959546f3b", "bands": 4,
+                  "workload": "floor", "bytes_per_launch": 492860928}
+GATHER_SOURCES = ("paper_1803_04782_gb300/csrc/sfm_device.cuh",
+                  "paper_1803_04782_gb300/csrc/sfm_kernels.cu")
+
+
+def gather_traffic(workload: str, bands: int):
+    import hashlib
+    h = hashlib.sha1()
+    for f in GATHER_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    t = GATHER_TRAFFIC
+    if h.hexdigest() == t["sha1"] and workload == t["workload"] and bands == t["bands"]:
+        return t["bytes_per_launch"]
+    return None
 
 
 def workload(name: str):
@@ -286,8 +306,9 @@ def run_gpu(args):
     achieved = FLOPS_PER_PAIR * pairs * args.steps / field_s / 1e12
     peak = SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
-                "kernel": "k_field", "field_ms_per_step": 1e3 * field_s / args.steps,
+                "frac": achieved / peak, "traffic": gather_traffic(args.workload, st1["bands"]),
+                "traffic_unit": "bytes per launch",
+                "kernel": "k_field_v2", "field_ms_per_step": 1e3 * field_s / args.steps,
                 "pairs_per_step": pairs,
                 "peak_basis": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz (max clock)"}
 
@@ -462,6 +483,60 @@ def run_batch(args):
     return 0
 
 
+# -------------------------------------------------------------- surrogate arm
+def run_surrogate(args):
+    """Learned surrogate: trained on the GPU on 100 ticks of a 4096^2 periodic
+    canvas (about 10^5 tiles of 128^2 su, densities 0.002-0.25, r = 40), then
+    judged by the exact path inside the 16384^2 floor: field error, decision
+    flip rate and the time of each field.  The literal fine-grid network (s = 1,
+    no exact near part) is trained and judged beside it on the 4096^2 floor."""
+    import torch
+    import paper_1803_04782_gb300 as sfm
+    import scenegen as SG
+    from oracle import surrogate as OS
+    from paper_1803_04782_gb300 import build as B
+
+    B.build()
+    sfm.lib()
+    stream = torch.cuda.current_stream()
+    init = sfm.flatten_params(OS.init_params(0))
+    out = {}
+    for name, s_, rn, train_side, eval_wl, iters in (
+            ("coarse8_near3", 8, 3, 4096, "floor", 100),
+            ("literal", 1, 0, 1024, "floor-small", 100)):
+        canvas = SG.training_canvas(side=train_side, r=40, seed=500)
+        with sfm.Surrogate(coarsen=s_, near_radius=rn, target_scale=20.0, lr=2e-3,
+                           params=init, stream=stream) as sur:
+            with sfm.Sim(canvas, stream=stream) as tsim:
+                t0 = time.perf_counter()
+                curve = sur.train(tsim, iters)
+                train_s = time.perf_counter() - t0
+            sc, desc = workload(eval_wl)
+            with sfm.Sim(sc, stream=stream) as fsim:
+                fsim.step(args.warmup)
+                evs = [sur.eval(fsim) for _ in range(3)]
+        ev = sorted(evs, key=lambda e: e["ms_surrogate"])[1]
+        out[name] = {"coarsen": s_, "near_radius": rn, "train_canvas": train_side,
+                     "train_iters": iters, "train_tiles_128": iters * (train_side // 128) ** 2,
+                     "train_s": train_s, "loss_first": float(curve[0]),
+                     "loss_last": float(curve[-5:].mean()), "eval_workload": desc,
+                     "field_rel_err": ev["field_rel_err"], "flip_rate": ev["flip_rate"],
+                     "ms_surrogate": ev["ms_surrogate"], "ms_exact": ev["ms_exact"],
+                     "speedup": ev["ms_exact"] / ev["ms_surrogate"]}
+    main_r = out["coarse8_near3"]
+    line = {
+        "metric": "surrogate vs exact at set flip rate", "value": main_r["speedup"],
+        "unit": "x (exact field time / surrogate field time)", "n_gpus": 1, "steps": 3,
+        "warmup": args.warmup, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16 weights/activations, f32 accumulation", "data": "synthetic",
+        "config": {"workload": main_r["eval_workload"], "flip_rate_target": 1e-3},
+        "flip_rate": main_r["flip_rate"], "meets_flip_target": main_r["flip_rate"] <= 1e-3,
+        "variants": out,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -469,7 +544,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="floor",
-                    choices=["floor", "floor-small", "corridor", "room", "batch", "batch-small"])
+                    choices=["floor", "floor-small", "corridor", "room", "batch", "batch-small",
+                             "surrogate"])
     ap.add_argument("--bands", type=int, default=4,
                     help="row bands of the divide-and-conquer field pass (1 = unbanded)")
     ap.add_argument("--e2e-steps", type=int, default=10)
@@ -481,6 +557,8 @@ def main():
         return run_reference(args)
     if args.workload.startswith("batch"):
         return run_batch(args)
+    if args.workload == "surrogate":
+        return run_surrogate(args)
     return run_gpu(args)
 
 

@@ -199,6 +199,37 @@ void run_tick(sfm_ctx* c) {
   ++c->launches;
 }
 
+void drop_graph(sfm_ctx* c) {
+  if (c->tick_graph) cudaGraphExecDestroy(c->tick_graph);
+  c->tick_graph = nullptr;
+  c->direct_ticks = 0;
+}
+
+// Capture one tick (all its launches, on a private stream) into a graph.
+cudaError_t build_tick_graph(sfm_ctx* c) {
+  cudaStream_t cs;
+  cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return e;
+  cudaStream_t saved = c->stream;
+  const int64_t l0 = c->launches;
+  cudaGraph_t graph = nullptr;
+  c->stream = cs;
+  e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    run_tick(c);
+    const cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
+    e = e2;
+  }
+  c->stream = saved;
+  c->graph_launches = c->launches - l0;
+  c->launches = l0;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&c->tick_graph, graph, 0);
+  if (graph) cudaGraphDestroy(graph);
+  cudaStreamDestroy(cs);
+  if (e != cudaSuccess) c->tick_graph = nullptr;
+  return e;
+}
+
 sfm_status copy_out(sfm_ctx* ctx, void* dst, const void* src, size_t bytes, int on_device) {
   CU(cudaMemcpyAsync(dst, src, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                      ctx->stream));
@@ -385,6 +416,7 @@ sfm_status sfm_create(const sfm_lattice* lat, const uint8_t* cell, int32_t cell_
 void sfm_destroy(sfm_ctx* ctx) {
   if (!ctx) return;
   cudaStreamSynchronize(ctx->stream);
+  drop_graph(ctx);
   batch_destroy(ctx);
   for (void* p : ctx->allocs) cudaFree(p);
   for (auto& r : ctx->recs) {
@@ -399,6 +431,7 @@ sfm_status sfm_place(sfm_ctx* ctx, int32_t n, const int32_t* xy, const uint8_t* 
                      const uint8_t* goal, const uint8_t* alive, int32_t on_device) {
   if (!ctx) return SFM_EINVAL;
   if (ctx->batch) return fail(ctx, SFM_ESTATE, "a batch is placed with sfm_batch_place");
+  drop_graph(ctx);
   if (n < 0 || (n > 0 && !xy)) return fail(ctx, SFM_EINVAL, "bad pedestrian arrays");
   cudaStream_t s = ctx->stream;
   const Geo& g = ctx->geo;
@@ -499,7 +532,22 @@ sfm_status sfm_step(sfm_ctx* ctx, int32_t nsteps) {
   if (ctx->batch) return batch_tick(ctx, nsteps, 0);
   if (!ctx->placed) return fail(ctx, SFM_ESTATE, "sfm_step before a successful sfm_place");
   for (int i = 0; i < nsteps; ++i) {
-    run_tick(ctx);
+    // timed ticks launch stage by stage (events between stages); otherwise the
+    // first tick after placement runs directly and the rest replay its graph
+    if (ctx->timing || ctx->direct_ticks < 1) {
+      run_tick(ctx);
+      ++ctx->direct_ticks;
+    } else {
+      if (!ctx->tick_graph) {
+        const cudaError_t ge = build_tick_graph(ctx);
+        if (ge != cudaSuccess) {
+          cudaGetLastError();
+          return fail(ctx, SFM_ECUDA, "tick graph: %s", cudaGetErrorString(ge));
+        }
+      }
+      CU(cudaGraphLaunch(ctx->tick_graph, ctx->stream));
+      ctx->launches += ctx->graph_launches;
+    }
     ++ctx->t;
   }
   if (ctx->timing) ctx->timed_ticks += nsteps;

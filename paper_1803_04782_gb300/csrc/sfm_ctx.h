@@ -71,6 +71,10 @@ struct sfm_ctx {
   std::vector<Rec> recs;
   std::vector<cudaEvent_t> pool;
   int64_t timed_ticks = 0;
+  // one tick captured as a CUDA graph (single lattice, untimed ticks)
+  cudaGraphExec_t tick_graph = nullptr;
+  int64_t graph_launches = 0;  // kernels in one replay of tick_graph
+  int64_t direct_ticks = 0;    // ticks launched stage by stage since placement
   // batch of independent lattices (nullptr for a single lattice)
   sfm::BatchState* batch = nullptr;
 

@@ -87,6 +87,123 @@ __global__ void __launch_bounds__(kTile* kTile)
   }
 }
 
+
+// ------------------------------------------- tensor-core 3x3, 32 -> 32
+// Implicit GEMM on mma.sync m16n8k16 (BF16 operands, FP32 accumulators): a
+// CTA computes 8 x 16 output pixels x 32 channels; warp w owns output rows
+// 2w and 2w+1 (one m16 tile each) and all four n8 tiles.  K runs over the 9
+// kernel offsets x 2 blocks of 16 input channels.  The input tile (10 x 18
+// pixels) and the weights sit in shared memory channel-last with rows padded
+// to 40 channels (80 bytes), which keeps the ldmatrix row fetches free of
+// bank conflicts.  Weights in shared memory: [ky][kx][out][in], BF16.
+constexpr int kTcRows = 8, kTcCols = 16, kTcPad = 40;
+
+__device__ __forceinline__ void ldsm_x4(uint32_t addr, uint32_t& r0, uint32_t& r1, uint32_t& r2,
+                                        uint32_t& r3) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+               : "r"(addr));
+}
+
+__device__ __forceinline__ void mma_bf16(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2,
+                                         uint32_t a3, uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+      "{%8,%9}, {%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+__global__ void __launch_bounds__(128)
+    k_conv3_tc(const bf16* __restrict__ in, int Hin, int Win, const bf16* __restrict__ Wt,
+               const float* __restrict__ b, bf16* __restrict__ out) {
+  __shared__ __align__(16) bf16 sIn[(kTcRows + 2) * (kTcCols + 2) * kTcPad];
+  __shared__ __align__(16) bf16 sW[9 * 32 * kTcPad];
+  const int Hout = Hin - 2, Wout = Win - 2;
+  const int x0 = blockIdx.x * kTcCols, y0 = blockIdx.y * kTcRows;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  // weights: 9 x 32 rows of 32 channels (4 chunks of 16 bytes each)
+  for (int i = tid; i < 9 * 32 * 4; i += blockDim.x) {
+    const int q = i & 3, row = i >> 2;
+    *reinterpret_cast<uint4*>(sW + row * kTcPad + q * 8) =
+        *reinterpret_cast<const uint4*>(Wt + row * 32 + q * 8);
+  }
+  // input tile with a 1-pixel halo on the right and bottom (valid conv)
+  for (int i = tid; i < (kTcRows + 2) * (kTcCols + 2) * 4; i += blockDim.x) {
+    const int q = i & 3, p = i >> 2, px = p % (kTcCols + 2), py = p / (kTcCols + 2);
+    const int gy = y0 + py, gx = x0 + px;
+    uint4 v = make_uint4(0, 0, 0, 0);
+    if (gy < Hin && gx < Win) v = *reinterpret_cast<const uint4*>(in + ((size_t)gy * Win + gx) * 32 + q * 8);
+    *reinterpret_cast<uint4*>(sIn + p * kTcPad + q * 8) = v;
+  }
+  __syncthreads();
+  float acc[2][4][4];
+#pragma unroll
+  for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+    for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) acc[mt][nt][k] = 0.f;
+  const uint32_t sIn0 = (uint32_t)__cvta_generic_to_shared(sIn);
+  const uint32_t sW0 = (uint32_t)__cvta_generic_to_shared(sW);
+  // ldmatrix lane roles: A rows (pixels) and column halves; B rows (out channels)
+  const int a_row = (lane & 7) + 8 * ((lane >> 3) & 1), a_col = 8 * (lane >> 4);
+  const int b_n = (lane & 7) + 8 * (lane >> 4), b_k = 8 * ((lane >> 3) & 1);
+#pragma unroll 1
+  for (int kk = 0; kk < 9; ++kk) {
+    const int ky = kk / 3, kx = kk % 3;
+#pragma unroll
+    for (int kb = 0; kb < 2; ++kb) {
+      uint32_t bw[4][2];
+#pragma unroll
+      for (int np = 0; np < 2; ++np) {
+        const uint32_t addr =
+            sW0 + (uint32_t)(((kk * 32 + np * 16 + b_n) * kTcPad + kb * 16 + b_k) * 2);
+        ldsm_x4(addr, bw[2 * np][0], bw[2 * np][1], bw[2 * np + 1][0], bw[2 * np + 1][1]);
+      }
+#pragma unroll
+      for (int mt = 0; mt < 2; ++mt) {
+        const int py = 2 * warp + mt + ky, px = a_row + kx;
+        const uint32_t addr =
+            sIn0 + (uint32_t)(((py * (kTcCols + 2) + px) * kTcPad + kb * 16 + a_col) * 2);
+        uint32_t a0, a1, a2, a3;
+        ldsm_x4(addr, a0, a1, a2, a3);
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt) mma_bf16(acc[mt][nt], a0, a1, a2, a3, bw[nt][0], bw[nt][1]);
+      }
+    }
+  }
+  // epilogue: bias, ReLU, BF16; accumulator (row g = lane/4 and g+8, column
+  // pair 2*(lane%4)) of each m16 x n8 tile
+  const int g = lane >> 2, cp = 2 * (lane & 3);
+#pragma unroll
+  for (int mt = 0; mt < 2; ++mt) {
+    const int y = y0 + 2 * warp + mt;
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+      const int x = x0 + g + 8 * half;
+      if (y >= Hout || x >= Wout) continue;
+      __nv_bfloat162* o = reinterpret_cast<__nv_bfloat162*>(out + ((size_t)y * Wout + x) * 32);
+#pragma unroll
+      for (int nt = 0; nt < 4; ++nt) {
+        const int c = nt * 8 + cp;
+        const float v0 = fmaxf(acc[mt][nt][2 * half] + b[c], 0.f);
+        const float v1 = fmaxf(acc[mt][nt][2 * half + 1] + b[c + 1], 0.f);
+        o[c / 2] = __floats2bfloat162_rn(v0, v1);
+      }
+    }
+  }
+}
+
+// BF16 weights of a 3x3 32->32 layer for the tensor-core kernel:
+// [ky][kx][out][in] from the internal [ky][kx][in][out] floats.
+__global__ void k_pack_w3(const float* __restrict__ w, bf16* __restrict__ wt) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 9 * 32 * 32) return;
+  const int c = i % 32, o = (i / 32) % 32, kk = i / 1024;
+  wt[i] = __float2bfloat16(w[(kk * 32 + c) * 32 + o]);
+}
+
 // -------------------------------------------------------------- backward
 // dZ of a layer output: the incoming gradient, masked by the ReLU (A > 0).
 __device__ __forceinline__ float dz_at(const float* dA, const bf16* A, size_t i, bool relu) {
@@ -358,6 +475,7 @@ struct sfm_surrogate {
   std::string err;
   // parameters (internal layout), BF16-rounded copies, Adam state, gradients
   float *p = nullptr, *pq = nullptr, *m = nullptr, *v = nullptr, *g = nullptr;
+  bf16 *wt2 = nullptr, *wt3 = nullptr;  // layers 2 and 3 packed for the tensor-core kernel
   int adam_t = 0;
   // activations for an image of (Hc + 2 kHalo) x (Wc + 2 kHalo) coarse cells
   int Hc = 0, Wc = 0;
@@ -496,13 +614,20 @@ sfm_status conv_dw(sfm_surrogate* S, const bf16* in, const float* dA, const bf16
   return SFM_OK;
 }
 
-// forward of the whole padded image currently in S->X
+void conv3_tc(const bf16* in, int Hin, int Win, const bf16* wt, const float* b, bf16* out,
+              cudaStream_t s) {
+  dim3 grid(cdiv(Win - 2, kTcCols), cdiv(Hin - 2, kTcRows));
+  k_conv3_tc<<<grid, 128, 0, s>>>(in, Hin, Win, wt, b, out);
+}
+
+// forward of the whole padded image currently in S->X (layers 2 and 3 on the
+// tensor cores, 1 and 4 on the FP32 pipes)
 void forward(sfm_surrogate* S, cudaStream_t s) {
   const int Hp = S->Hc + 2 * kHalo, Wp = S->Wc + 2 * kHalo;
   const float* q = S->pq;
   conv_fwd<3, 32, 5, true>(S->X, Hp, Wp, q + kOffW[0], q + kOffB[0], S->A1, nullptr, s);
-  conv_fwd<32, 32, 3, true>(S->A1, Hp - 4, Wp - 4, q + kOffW[1], q + kOffB[1], S->A2, nullptr, s);
-  conv_fwd<32, 32, 3, true>(S->A2, Hp - 6, Wp - 6, q + kOffW[2], q + kOffB[2], S->A3, nullptr, s);
+  conv3_tc(S->A1, Hp - 4, Wp - 4, S->wt2, q + kOffB[1], S->A2, s);
+  conv3_tc(S->A2, Hp - 6, Wp - 6, S->wt3, q + kOffB[2], S->A3, s);
   conv_fwd<32, 1, 3, false>(S->A3, Hp - 8, Wp - 8, q + kOffW[3], q + kOffB[3], nullptr, S->Y, s);
 }
 
@@ -637,6 +762,8 @@ void surrogate_field(sfm_surrogate* S, sfm_ctx* ctx) {
 
 void round_params(sfm_surrogate* S) {
   k_round_bf16<<<cdiv(kNParams, 256), 256, 0, S->stream>>>(S->p, S->pq, kNParams);
+  k_pack_w3<<<cdiv(9 * 32 * 32, 256), 256, 0, S->stream>>>(S->pq + kOffW[1], S->wt2);
+  k_pack_w3<<<cdiv(9 * 32 * 32, 256), 256, 0, S->stream>>>(S->pq + kOffW[2], S->wt3);
 }
 
 }  // namespace
@@ -663,6 +790,8 @@ sfm_status sfm_surrogate_create(const sfm_surrogate_cfg* cfg, void* stream, sfm_
   if ((st = salloc(S, &S->p, kNParams)) != SFM_OK || (st = salloc(S, &S->pq, kNParams)) != SFM_OK ||
       (st = salloc(S, &S->m, kNParams)) != SFM_OK || (st = salloc(S, &S->v, kNParams)) != SFM_OK ||
       (st = salloc(S, &S->g, kNParams)) != SFM_OK || (st = salloc(S, &S->red, 2 * 1024)) != SFM_OK ||
+      (st = salloc(S, &S->wt2, 9 * 32 * 32)) != SFM_OK ||
+      (st = salloc(S, &S->wt3, 9 * 32 * 32)) != SFM_OK ||
       (st = salloc(S, &S->cnt, 1)) != SFM_OK)
     return bail(st);
   cudaMemsetAsync(S->p, 0, kNParams * sizeof(float), S->stream);
