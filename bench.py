@@ -248,6 +248,7 @@ def run_gpu(args):
     stream = torch.cuda.current_stream()
     sim = sfm.Sim(sc, stream=stream, hbm_budget_bytes=budget)
     n = sc.n
+    footprint = sim.autotune()
     st0 = sim.stats()
 
     def barrier():
@@ -366,6 +367,7 @@ def run_gpu(args):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": desc, "W": sc.W, "H": sc.H, "n": n, "r": int(sc.params["r"]),
                    "bands": st1["bands"], "hbm_budget_bytes": budget,
+                   "field_footprint": footprint,
                    "l2": "inputs larger than L2 (the field alone is 4*W*H bytes)"
                    if sc.W * sc.H * 4 > 129e6 else "inputs smaller than L2",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
@@ -410,7 +412,7 @@ def run_batch(args):
     su = sum(s.W * s.H for s in scenes)
     with sfm.Batch(scenes, stream=stream) as bt:
         t0 = time.perf_counter()
-        rows = bt.autotune()
+        shapes = bt.autotune()
         tune_s = time.perf_counter() - t0
         bt.step(args.warmup)
         bt.sync()
@@ -445,8 +447,11 @@ def run_batch(args):
     value = ped_steps / elapsed
 
     # the plain exact path: each scene in its own context, one after another
+    # (each context's footprint autotuned like the batch's)
     plain_steps = max(3, min(args.steps, 10))
     sims = [sfm.Sim(s, stream=stream) for s in scenes]
+    for s in sims:
+        s.autotune()
     for s in sims:
         s.step(1)
     torch.cuda.synchronize()
@@ -468,7 +473,7 @@ def run_batch(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
         "config": {"workload": desc, "scenes": nsc, "n": n, "su": su,
-                   "tiles_rows_per_radius_class": rows, "autotune_s": tune_s,
+                   "footprint_per_radius_class": shapes, "autotune_s": tune_s,
                    "l2": "inputs larger than L2", "parallelism": "single GPU"},
         "su_updates_per_s": su * args.steps / elapsed,
         "plain_exact_path": {"value": plain_value, "unit": "ped-steps/s",

@@ -157,6 +157,18 @@ sfm_status sfm_step(sfm_ctx* ctx, int32_t nsteps);
  * moving anybody (bins + gather only).  Asynchronous. */
 sfm_status sfm_compute_field(sfm_ctx* ctx);
 
+/* Times the field gather of the current state with each of its two warp
+ * footprints (16 x 16 and 32 x 16 su) and keeps the faster for this context
+ * (the choice survives later placements).  *shape_out (may be NULL): 0 or 1.
+ * The fields computed are identical either way.  Synchronising; moves
+ * nobody. */
+sfm_status sfm_autotune(sfm_ctx* ctx, int32_t* shape_out);
+
+/* Sets the warp footprint of the field gather by hand: 0 = 16 x 16 su,
+ * 1 = 32 x 16 su; anything else is SFM_EINVAL.  Ignored (but accepted) when
+ * the interaction radius exceeds the class-table gather (r > 47). */
+sfm_status sfm_set_field_footprint(sfm_ctx* ctx, int32_t shape);
+
 /* Wait for the context's stream and report device-side errors. */
 sfm_status sfm_sync(sfm_ctx* ctx);
 
@@ -224,9 +236,10 @@ sfm_status sfm_stage_times(sfm_ctx* ctx, double* ms, int64_t* ticks);
  * sfm_batch_offsets: su_off[nscenes+1] and ped_off[nscenes+1] (either may
  *   be NULL) receive where each lattice starts in the concatenated arrays.
  * sfm_batch_autotune: times the field stage of each radius class (lattices
- *   sharing a class-table row stride) with footprints 8 and 16 su high and
- *   keeps the faster; rows_per_class[6] (may be NULL) receives the choice for
- *   strides 16, 32, ..., 96.  Needs placed pedestrians; moves nobody.
+ *   sharing a class-table row stride) with 16 x 16 and 32 x 16 su warp
+ *   footprints and keeps the faster; shape_per_class[6] (may be NULL)
+ *   receives 0 (16 x 16) or 1 (32 x 16) for strides 18, 34, ..., 98.  Needs
+ *   placed pedestrians; moves nobody.
  * sfm_batch_test_missing_ctas: test hook of the bounded barrier wait; the
  *   next tick's barriers wait for `missing` CTAs that are never launched, so
  *   the tick gives up after about a second and returns SFM_ETIMEOUT (the
@@ -237,7 +250,7 @@ sfm_status sfm_batch_place(sfm_ctx* ctx, const int32_t* counts, const int32_t* x
                            const uint8_t* heading, const uint8_t* goal, const uint8_t* alive,
                            int32_t on_device);
 sfm_status sfm_batch_offsets(const sfm_ctx* ctx, int64_t* su_off, int64_t* ped_off);
-sfm_status sfm_batch_autotune(sfm_ctx* ctx, int32_t* rows_per_class);
+sfm_status sfm_batch_autotune(sfm_ctx* ctx, int32_t* shape_per_class);
 sfm_status sfm_batch_test_missing_ctas(sfm_ctx* ctx, int32_t missing);
 
 /* ---- Learned field surrogate ----------------------------------------------

@@ -33,7 +33,7 @@ EXPORTS = [
     "sfm_set_time", "sfm_step", "sfm_compute_field", "sfm_sync", "sfm_read_field",
     "sfm_compute_field_into", "sfm_read_static_field", "sfm_read_guidance", "sfm_read_peds",
     "sfm_read_decisions", "sfm_stats", "sfm_set_timing", "sfm_stage_times",
-    "sfm_field_noalloc", "sfm_batch_create", "sfm_batch_place", "sfm_batch_offsets",
+    "sfm_autotune", "sfm_set_field_footprint", "sfm_field_noalloc", "sfm_batch_create", "sfm_batch_place", "sfm_batch_offsets",
     "sfm_batch_autotune", "sfm_batch_test_missing_ctas", "sfm_surrogate_nparams",
     "sfm_surrogate_create", "sfm_surrogate_destroy", "sfm_surrogate_last_error",
     "sfm_surrogate_set_params", "sfm_surrogate_get_params", "sfm_surrogate_grad",
@@ -104,6 +104,8 @@ def lib():
             "sfm_read_decisions": (C.c_int, [P, P, P, I32]),
             "sfm_stats": (C.c_int, [P, C.POINTER(Stats)]),
             "sfm_set_timing": (C.c_int, [P, I32]),
+            "sfm_autotune": (C.c_int, [P, P]),
+            "sfm_set_field_footprint": (C.c_int, [P, I32]),
             "sfm_stage_times": (C.c_int, [P, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
             "sfm_field_noalloc": (C.c_int, [C.POINTER(Lattice), C.POINTER(Params), I32, P, P, P,
                                             P, P, P]),
@@ -259,6 +261,13 @@ def sfm_stats(ctx) -> dict:
     return s.as_dict()
 
 
+def sfm_autotune(ctx) -> str:
+    """Pick the faster warp footprint of the field gather for this context."""
+    v = C.c_int32()
+    _check(ctx, lib().sfm_autotune(ctx, C.byref(v)))
+    return "32x16" if v.value else "16x16"
+
+
 def sfm_set_timing(ctx, enable: bool) -> None:
     _check(ctx, lib().sfm_set_timing(ctx, 1 if enable else 0))
 
@@ -300,9 +309,11 @@ def sfm_batch_offsets(ctx, nscenes: int):
 
 
 def sfm_batch_autotune(ctx):
-    rows = np.zeros(6, np.int32)
-    _check(ctx, lib().sfm_batch_autotune(ctx, rows.ctypes.data_as(C.c_void_p)))
-    return {16 * (i + 1): int(v) for i, v in enumerate(rows)}
+    """Footprint chosen per radius class (class-table row stride 18, 34, ...,
+    98): "16x16" or "32x16"."""
+    shp = np.zeros(6, np.int32)
+    _check(ctx, lib().sfm_batch_autotune(ctx, shp.ctypes.data_as(C.c_void_p)))
+    return {18 + 16 * i: ("32x16" if v else "16x16") for i, v in enumerate(shp)}
 
 
 def sfm_batch_test_missing_ctas(ctx, missing: int) -> None:
@@ -430,6 +441,12 @@ class Sim:
 
     def stats(self):
         return sfm_stats(self.ctx)
+
+    def autotune(self):
+        return sfm_autotune(self.ctx)
+
+    def set_footprint(self, shape: str):
+        _check(self.ctx, lib().sfm_set_field_footprint(self.ctx, {"16x16": 0, "32x16": 1}[shape]))
 
     def set_timing(self, on=True):
         sfm_set_timing(self.ctx, on)

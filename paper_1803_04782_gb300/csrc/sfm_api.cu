@@ -315,6 +315,7 @@ sfm_status sfm_create(const sfm_lattice* lat, const uint8_t* cell, int32_t cell_
   sfm_ctx* ctx = new sfm_ctx;
   ctx->lat = *lat;
   ctx->nsu_total = (int64_t)lat->W * lat->H;
+  ctx->field_shape = default_field_shape(prm->r);
   ctx->prm = *prm;
   ctx->prm.bin = kBin;
   ctx->stream = static_cast<cudaStream_t>(stream);
@@ -590,6 +591,59 @@ sfm_status sfm_compute_field_into(sfm_ctx* ctx, float* dst, int32_t on_device) {
   }
   CU(cudaGetLastError());
   return check_flags(ctx);
+}
+
+sfm_status sfm_autotune(sfm_ctx* ctx, int32_t* shape_out) {
+  if (!ctx) return SFM_EINVAL;
+  if (ctx->batch) return fail(ctx, SFM_EINVAL, "use sfm_batch_autotune on a batch");
+  if (!ctx->placed) return fail(ctx, SFM_ESTATE, "autotune needs placed pedestrians");
+  if (!ctx->CT) {
+    if (shape_out) *shape_out = ctx->field_shape;
+    return SFM_OK;  // radius beyond the class-table gather: nothing to choose
+  }
+  const Geo& g = ctx->geo;
+  float* out = ctx->bands > 1 ? ctx->band_buf : ctx->F;
+  const int rows = ctx->bands > 1 ? ctx->band_rows : g.H;
+  cudaEvent_t e0, e1;
+  CU(cudaEventCreate(&e0));
+  CU(cudaEventCreate(&e1));
+  run_bins(ctx);
+  float best = 1e30f;
+  int best_shape = ctx->field_shape;
+  for (int shape : {0, 1}) {
+    ctx->field_shape = shape;
+    float tot = 0.f;
+    for (int rep = 0; rep < 3; ++rep) {
+      CU(cudaEventRecord(e0, ctx->stream));
+      field_rows(ctx, out, 0, rows, 0, false);
+      CU(cudaEventRecord(e1, ctx->stream));
+      CU(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (rep > 0) tot += ms;  // the first run warms up
+    }
+    if (tot < best) {
+      best = tot;
+      best_shape = shape;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  ctx->field_shape = best_shape;
+  drop_graph(ctx);
+  if (shape_out) *shape_out = best_shape;
+  return check_flags(ctx);
+}
+
+sfm_status sfm_set_field_footprint(sfm_ctx* ctx, int32_t shape) {
+  if (!ctx) return SFM_EINVAL;
+  if (ctx->batch) return fail(ctx, SFM_EINVAL, "a batch tunes its footprints per radius class");
+  if (shape != 0 && shape != 1) return fail(ctx, SFM_EINVAL, "footprint must be 0 or 1");
+  if (ctx->field_shape != shape) {
+    ctx->field_shape = shape;
+    drop_graph(ctx);
+  }
+  return SFM_OK;
 }
 
 sfm_status sfm_sync(sfm_ctx* ctx) {

@@ -38,10 +38,10 @@ struct BatchScene {
   int pad;
 };
 
-// A field work item: footprints [f0, f0 + 32) (one per warp) of lattice scene,
-// each `rows` su high.
+// A field work item: footprints [f0, f0 + 32) (one per warp) of lattice
+// scene; shape 0 = 16 x 16 su footprints, 1 = 32 x 16.
 struct BatchChunk {
-  int scene, f0, rows, pad;
+  int scene, f0, shape, pad;
 };
 
 struct BatchArgs {
@@ -95,7 +95,7 @@ struct BatchState {
   unsigned int* bar = nullptr;
   int* work = nullptr;
   int max_ts = 0;
-  int rows_of_sp[7] = {16, 16, 16, 16, 16, 16, 16};  // footprint rows per radius class
+  int shape_of_sp[7] = {0, 0, 0, 0, 0, 0, 0};  // footprint shape per radius class
   int missing = 0;  // test hook: CTAs the barrier expects beyond those launched
   int grid = 0;
   std::vector<int> order;  // lattices by decreasing field cost
@@ -161,37 +161,61 @@ __device__ int block_scan_excl(int v, int* sWarp, int& total) {
   return excl;
 }
 
-template <int SP, int R>
+// footprint counts per row of a lattice for each shape
+__host__ __device__ inline int shape_w(int shape) { return shape ? 32 : 16; }
+__host__ __device__ inline int shape_nf(const Geo& g, int shape) {
+  return ((g.W + shape_w(shape) - 1) / shape_w(shape)) * ((g.H + 15) / 16);
+}
+
+template <int SP>
 __device__ __forceinline__ void batch_footprint(const BatchArgs& a, const BatchScene& sc,
-                                                const float* sT, int2* scr, int lane, int f) {
+                                                const float* sT, int2* scr, int lane, int f,
+                                                int shape) {
   const Geo& g = sc.g;
-  const int nfx = (g.W + 31) >> 5;
-  const int x0 = (f % nfx) << 5, y0 = (f / nfx) * R;
-  float acc[R];
+  const int fw = shape_w(shape);
+  const int nfx = (g.W + fw - 1) / fw;
+  const int x0 = (f % nfx) * fw, y0 = (f / nfx) * 16;
+  if (shape == 0) {
+    float acc[8];
 #pragma unroll
-  for (int j = 0; j < R; ++j) acc[j] = 0.f;
-  gather_footprint<SP, R>(g, a.bin_start + sc.bin_off, a.rec, sT, sc.ts, scr, lane, x0, y0, acc);
-  const int x = x0 + lane;
+    for (int j = 0; j < 8; ++j) acc[j] = 0.f;
+    gather_footprint16<SP>(g, a.bin_start + sc.bin_off, a.rec, sT, sc.ts, scr, lane, x0, y0, acc);
+    const int x = x0 + (lane & 15), yl = y0 + (lane >> 4) * 8;
 #pragma unroll
-  for (int j = 0; j < R; ++j) {
-    const int y = y0 + j;
-    if (x < g.W && y < g.H) {
-      const size_t c = (size_t)sc.su_off + (size_t)y * g.W + x;
-      a.F[c] = a.Fs[c] + acc[j];
+    for (int j = 0; j < 8; ++j) {
+      const int y = yl + j;
+      if (x < g.W && y < g.H) {
+        const size_t c = (size_t)sc.su_off + (size_t)y * g.W + x;
+        a.F[c] = a.Fs[c] + acc[j];
+      }
+    }
+  } else {
+    float acc[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) acc[j] = 0.f;
+    gather_footprint32<SP>(g, a.bin_start + sc.bin_off, a.rec, sT, sc.ts, scr, lane, x0, y0, acc);
+    const int x = x0 + lane;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      const int y = y0 + j;
+      if (x < g.W && y < g.H) {
+        const size_t c = (size_t)sc.su_off + (size_t)y * g.W + x;
+        a.F[c] = a.Fs[c] + acc[j];
+      }
     }
   }
 }
 
-template <int R>
 __device__ __forceinline__ void batch_footprint_sp(const BatchArgs& a, const BatchScene& sc,
-                                                   const float* sT, int2* scr, int lane, int f) {
+                                                   const float* sT, int2* scr, int lane, int f,
+                                                   int shape) {
   switch (sc.sp) {
-    case 16: batch_footprint<16, R>(a, sc, sT, scr, lane, f); break;
-    case 32: batch_footprint<32, R>(a, sc, sT, scr, lane, f); break;
-    case 48: batch_footprint<48, R>(a, sc, sT, scr, lane, f); break;
-    case 64: batch_footprint<64, R>(a, sc, sT, scr, lane, f); break;
-    case 80: batch_footprint<80, R>(a, sc, sT, scr, lane, f); break;
-    default: batch_footprint<96, R>(a, sc, sT, scr, lane, f); break;
+    case 18: batch_footprint<18>(a, sc, sT, scr, lane, f, shape); break;
+    case 34: batch_footprint<34>(a, sc, sT, scr, lane, f, shape); break;
+    case 50: batch_footprint<50>(a, sc, sT, scr, lane, f, shape); break;
+    case 66: batch_footprint<66>(a, sc, sT, scr, lane, f, shape); break;
+    case 82: batch_footprint<82>(a, sc, sT, scr, lane, f, shape); break;
+    default: batch_footprint<98>(a, sc, sT, scr, lane, f, shape); break;
   }
 }
 
@@ -286,20 +310,14 @@ __global__ void __launch_bounds__(kBatchThreads, 1) k_tick_batch(BatchArgs a) {
     const BatchChunk ch = a.chunks[c];
     const BatchScene& sc = a.scenes[ch.scene];
     if (s_loaded != ch.scene) {
-      const float4* src = reinterpret_cast<const float4*>(a.CT + sc.ct_off);
-      float4* dst = reinterpret_cast<float4*>(sT);
-      for (int i = tid; i < sc.ts; i += blockDim.x) dst[i] = src[i];  // 4*ts floats
+      const float2* src = reinterpret_cast<const float2*>(a.CT + sc.ct_off);
+      float2* dst = reinterpret_cast<float2*>(sT);
+      for (int i = tid; i < 2 * sc.ts; i += blockDim.x) dst[i] = src[i];  // 4*ts floats
       __syncthreads();
       if (tid == 0) s_loaded = ch.scene;
     }
-    const int nf = ((sc.g.W + 31) >> 5) * ((sc.g.H + ch.rows - 1) / ch.rows);
     const int f = ch.f0 + warp;
-    if (f < nf) {
-      if (ch.rows == 8)
-        batch_footprint_sp<8>(a, sc, sT, scr, lane, f);
-      else
-        batch_footprint_sp<16>(a, sc, sT, scr, lane, f);
-    }
+    if (f < shape_nf(sc.g, ch.shape)) batch_footprint_sp(a, sc, sT, scr, lane, f, ch.shape);
     __syncthreads();
   }
   if (a.field_only) return;
@@ -418,7 +436,7 @@ sfm_status balloc(sfm_ctx* ctx, T** p, size_t count) {
     if (s_ != SFM_OK) return s_; \
   } while (0)
 
-int sp_index(int sp) { return sp / 16 - 1; }  // 16..96 -> 0..5
+int sp_index(int sp) { return (sp - 18) / 16; }  // 18, 34, ..., 98 -> 0..5
 
 // Work list of the field stage: lattices by decreasing cost per footprint,
 // each cut into chunks of 32 footprints of its radius class's height.  When
@@ -428,9 +446,9 @@ void build_chunks(BatchState* B, std::vector<BatchChunk>& out, int only_sp) {
   for (int s : B->order) {
     const BatchScene& sc = B->hs[s];
     if (only_sp > 0 && sc.sp != only_sp) continue;
-    const int rows = B->rows_of_sp[sp_index(sc.sp)];
-    const int nf = ((sc.g.W + 31) / 32) * ((sc.g.H + rows - 1) / rows);
-    for (int f0 = 0; f0 < nf; f0 += 32) out.push_back(BatchChunk{s, f0, rows, 0});
+    const int shape = B->shape_of_sp[sp_index(sc.sp)];
+    const int nf = shape_nf(sc.g, shape);
+    for (int f0 = 0; f0 < nf; f0 += 32) out.push_back(BatchChunk{s, f0, shape, 0});
   }
 }
 
@@ -683,11 +701,10 @@ sfm_status sfm_batch_create(int32_t nscenes, const sfm_lattice* lats, const uint
   BALLOC(B->bar, 1);
   BALLOC(B->work, 1);
   BALLOC(ctx->ctr, 1);
-  // field work list capacity: chunks of 32 footprints at 8 rows
+  // field work list capacity: chunks of 32 footprints of the smaller shape
   {
     long long cap = 0;
-    for (const BatchScene& sc : B->hs)
-      cap += (((long long)(sc.g.W + 31) / 32) * ((sc.g.H + 7) / 8) + 31) / 32;
+    for (const BatchScene& sc : B->hs) cap += ((long long)shape_nf(sc.g, 0) + 31) / 32;
     B->chunk_cap = (int)cap;
     BALLOC(B->chunks, (size_t)cap);
   }
@@ -897,7 +914,7 @@ sfm_status sfm_batch_offsets(const sfm_ctx* ctx, int64_t* su_off, int64_t* ped_o
   return SFM_OK;
 }
 
-sfm_status sfm_batch_autotune(sfm_ctx* ctx, int32_t* rows_per_class) {
+sfm_status sfm_batch_autotune(sfm_ctx* ctx, int32_t* shape_per_class) {
   if (!ctx || !ctx->batch) return SFM_EINVAL;
   if (!ctx->placed) return bfail(ctx, SFM_ESTATE, "autotune needs placed pedestrians");
   BatchState* B = ctx->batch;
@@ -906,14 +923,14 @@ sfm_status sfm_batch_autotune(sfm_ctx* ctx, int32_t* rows_per_class) {
   BCU(cudaEventCreate(&e0));
   BCU(cudaEventCreate(&e1));
   for (int ci = 0; ci < 6; ++ci) {
-    const int sp = 16 * (ci + 1);
+    const int sp = 18 + 16 * ci;
     bool present = false;
     for (const BatchScene& sc : B->hs) present |= sc.sp == sp;
     if (!present) continue;
     float best = 1e30f;
-    int best_rows = 16;
-    for (int rows : {8, 16}) {
-      B->rows_of_sp[ci] = rows;
+    int best_shape = 0;
+    for (int shape : {0, 1}) {
+      B->shape_of_sp[ci] = shape;
       std::vector<BatchChunk> v;
       build_chunks(B, v, sp);
       BTRY(upload_chunks(ctx, v));
@@ -931,10 +948,10 @@ sfm_status sfm_batch_autotune(sfm_ctx* ctx, int32_t* rows_per_class) {
       BTRY(check_batch(ctx));
       if (tot < best) {
         best = tot;
-        best_rows = rows;
+        best_shape = shape;
       }
     }
-    B->rows_of_sp[ci] = best_rows;
+    B->shape_of_sp[ci] = best_shape;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -945,8 +962,8 @@ sfm_status sfm_batch_autotune(sfm_ctx* ctx, int32_t* rows_per_class) {
     cudaGraphExecDestroy(B->graph);
     B->graph = nullptr;
   }
-  if (rows_per_class)
-    for (int ci = 0; ci < 6; ++ci) rows_per_class[ci] = B->rows_of_sp[ci];
+  if (shape_per_class)
+    for (int ci = 0; ci < 6; ++ci) shape_per_class[ci] = B->shape_of_sp[ci];
   return SFM_OK;
 }
 

@@ -47,6 +47,7 @@ struct sfm_ctx {
   float *own = nullptr, *dirdot = nullptr;
   float2* hvec = nullptr;
   float* CT = nullptr;  // heading-class tables of the v2 gather
+  int field_shape = 0;  // footprint of the class-table gather (0: 16x16, 1: 32x16)
   // bins
   int32_t *bin_count = nullptr, *bin_start = nullptr, *scan_tmp = nullptr;
   uint32_t* rec = nullptr;
@@ -89,6 +90,7 @@ struct sfm_ctx {
     tb.dirdot = dirdot;
     tb.hvec = hvec;
     tb.CT = CT;
+    tb.shape = field_shape;
     return tb;
   }
 };

@@ -21,7 +21,7 @@ static __constant__ int c_ctab[9] = {0, 1, 3, 2, 3, 1, 3, 2, 3};
 static __constant__ int c_csx[9] = {1, 1, 1, 1, -1, -1, -1, 1, 1};
 static __constant__ int c_csy[9] = {1, 1, 1, 1, 1, 1, -1, -1, -1};
 
-constexpr int kFieldPad = kV2Rows - 1;  // zero rows above/below each class table
+constexpr int kFieldPad = kFieldPadRows;
 
 // the same move offsets as compile-time functions, so unrolled loops index
 // register arrays with constants
@@ -166,20 +166,20 @@ __device__ __forceinline__ void halo_entry(int i, int lo, int hi, int n, int per
   }
 }
 
-// Adds to acc[j] (row y0 + j, column x0 + lane) the pedestrian field of every
-// record in the bins overlapping the footprint's r-halo.  Records are taken
-// in (bin row, bin column, row-major inside the bin) order, so the order of
-// the terms summed into one su does not depend on the footprint's shape.
-// sT: the 4 heading-class tables (row stride SP, TS floats each, kFieldPad
-// zero rows above and below the window); scr: 32 int2 of per-warp scratch.
-template <int SP, int R>
-__device__ __forceinline__ void gather_footprint(const Geo& g, const int32_t* __restrict__ bin_start,
-                                                 const uint32_t* __restrict__ rec,
-                                                 const float* __restrict__ sT, int TS, int2* scr,
-                                                 int lane, int x0, int y0, float (&acc)[R]) {
+// Walks the bins overlapping [x0-r, x0+FW-1+r] x [y0-r, y0+FH-1+r] in
+// (bin row, bin column, row-major inside the bin) order -- the order of the
+// terms summed into one su therefore does not depend on the footprint's
+// shape -- and calls visit(item) for every record within reach of the
+// footprint, after compacting the batch's records into the warp's scratch.
+// item.x: table offset of the record for footprint column 0 / row 0;
+// item.y: lane-column range llo | lhi << 5 | x mirror << 10 | y mirror << 11.
+template <int SP, int FW, int FH, class Visit>
+__device__ __forceinline__ void walk_footprint(const Geo& g, const int32_t* __restrict__ bin_start,
+                                               const uint32_t* __restrict__ rec, int TS, int2* scr,
+                                               int lane, int x0, int y0, Visit visit) {
   const int r = g.r;
   const unsigned lt = (1u << lane) - 1u;
-  const int xlo = x0 - r, xhi = x0 + 31 + r, ylo = y0 - r, yhi = y0 + R - 1 + r;
+  const int xlo = x0 - r, xhi = x0 + FW - 1 + r, ylo = y0 - r, yhi = y0 + FH - 1 + r;
   const int nxl = halo_count(xlo, xhi, g.W, g.px);
   const int ne = nxl * halo_count(ylo, yhi, g.H, g.py);
   for (int e0 = 0; e0 < ne; e0 += 32) {
@@ -220,11 +220,11 @@ __device__ __forceinline__ void gather_footprint(const Geo& g, const int32_t* __
         const uint32_t rc = rec[s_lo + (q - p_lo)];
         const int rx = xo + (int)(rc & 0xffu), ry = yo + (int)((rc >> 8) & 0xffu);
         const int cls = (int)((rc >> 16) & 0xfu);
-        // some row of the footprint and some lane within the window
-        keep = ry >= -r && ry <= R - 1 + r && rx >= -r && rx <= 31 + r;
+        // some row of the footprint and some column within the window
+        keep = ry >= -r && ry <= FH - 1 + r && rx >= -r && rx <= FW - 1 + r;
         if (keep) {
           const int sx = c_csx[cls], sy = c_csy[cls];
-          const int llo = max(0, rx - r), lhi = min(31, rx + r);
+          const int llo = max(0, rx - r), lhi = min(FW - 1, rx + r);
           item.x = c_ctab[cls] * TS + (r + kFieldPad - sy * ry) * SP + r - sx * rx;
           item.y = llo | (lhi << 5) | (sx < 0 ? 1024 : 0) | (sy < 0 ? 2048 : 0);
         }
@@ -233,23 +233,60 @@ __device__ __forceinline__ void gather_footprint(const Geo& g, const int32_t* __
       if (keep) scr[__popc(bal & lt)] = item;
       __syncwarp();
       const int m = __popc(bal);
-      for (int j = 0; j < m; ++j) {
-        const int2 it = scr[j];
-        const int llo = it.y & 31, lhi = (it.y >> 5) & 31;
-        if (lane >= llo && lane <= lhi) {
-          const float* p = sT + it.x + ((it.y & 1024) ? -lane : lane);
-          if (it.y & 2048) {
-#pragma unroll
-            for (int jj = 0; jj < R; ++jj) acc[jj] += p[-jj * SP];
-          } else {
-#pragma unroll
-            for (int jj = 0; jj < R; ++jj) acc[jj] += p[jj * SP];
-          }
-        }
-      }
+      for (int j = 0; j < m; ++j) visit(scr[j]);
       __syncwarp();
     }
   }
+}
+
+// Adds to acc[j] the pedestrian field of the 16 x 16 footprint at (x0, y0):
+// lane l owns column x0 + (l & 15) and rows y0 + 8 (l >> 4) + j, j < 8.  One
+// shared-memory read and one FP32 add per (su, pedestrian) pair; the two
+// half-warps read rows 8 SP apart, on disjoint banks when SP = 16k + 2.
+// sT: the 4 heading-class tables (row stride SP, TS floats each, kFieldPad
+// zero rows above and below the window); scr: 32 int2 of per-warp scratch.
+template <int SP>
+__device__ __forceinline__ void gather_footprint16(const Geo& g, const int32_t* __restrict__ bin_start,
+                                                   const uint32_t* __restrict__ rec,
+                                                   const float* __restrict__ sT, int TS, int2* scr,
+                                                   int lane, int x0, int y0, float (&acc)[8]) {
+  const int col = lane & 15, hoff = (lane >> 4) * 8 * SP;
+  walk_footprint<SP, 16, 16>(g, bin_start, rec, TS, scr, lane, x0, y0, [&](const int2 it) {
+    const int llo = it.y & 31, lhi = (it.y >> 5) & 31;
+    if (col >= llo && col <= lhi) {
+      const float* p = sT + it.x + ((it.y & 1024) ? -col : col);
+      if (it.y & 2048) {
+        p -= hoff;
+#pragma unroll
+        for (int jj = 0; jj < 8; ++jj) acc[jj] += p[-jj * SP];
+      } else {
+        p += hoff;
+#pragma unroll
+        for (int jj = 0; jj < 8; ++jj) acc[jj] += p[jj * SP];
+      }
+    }
+  });
+}
+
+// The 32 x 16 footprint: lane l owns column x0 + l and rows y0 + j, j < 16.
+template <int SP>
+__device__ __forceinline__ void gather_footprint32(const Geo& g, const int32_t* __restrict__ bin_start,
+                                                   const uint32_t* __restrict__ rec,
+                                                   const float* __restrict__ sT, int TS, int2* scr,
+                                                   int lane, int x0, int y0, float (&acc)[16]) {
+  walk_footprint<SP, 32, 16>(g, bin_start, rec, TS, scr, lane, x0, y0, [&](const int2 it) {
+    const int llo = it.y & 31, lhi = (it.y >> 5) & 31;
+    if (lane >= llo && lane <= lhi) {
+      const float* p = sT + it.x + ((it.y & 1024) ? -lane : lane);
+      if (it.y & 2048) {
+#pragma unroll
+        for (int jj = 0; jj < 16; ++jj) acc[jj] += p[-jj * SP];
+      } else {
+#pragma unroll
+        for (int jj = 0; jj < 16; ++jj) acc[jj] += p[jj * SP];
+      }
+    }
+  });
 }
 
 // ---------------------------------------------------------------- S3 decide

@@ -19,11 +19,14 @@ constexpr int kRowsPerThread = kTile / (kFieldThreads / 32);  // 4
 constexpr int kStageCap = 2048;    // pedestrians staged in shared memory per chunk
 constexpr int kMaxHaloBins = 128;  // bins touched by one tile's halo (checked)
 constexpr int kBin = 32;           // side of a pedestrian bin (one warp column per su)
-// v2 gather: 32 x 16 su footprint per warp, 32 warps per CTA, table row stride
-// a multiple of 16 up to kMaxV2Stride (radius <= 47)
-constexpr int kV2Rows = 16;
+// class-table gather: a warp owns a 16 x 16 su footprint (half-warp h = rows
+// 8h..8h+7, lane = column), 32 warps per CTA; table row stride SP = 16k + 2
+// >= 2r + 1 (radius <= 47), which puts the two half-warps' rows on disjoint
+// banks.  A 32 x 16 footprint (lane = column, 16 rows) is the alternative tile.
+constexpr int kV2Rows = 8;       // rows per lane of the 16 x 16 footprint
+constexpr int kFieldPadRows = 15;  // zero rows above/below each class table
 constexpr int kV2Threads = 1024;
-constexpr int kMaxV2Stride = 96;
+constexpr int kMaxV2Stride = 98;
 
 // device error flags (sticky until read by a synchronising call)
 enum : uint32_t {
@@ -60,7 +63,11 @@ struct Tables {
   const float* dirdot;  // [9 goal][9 move]: Delta_move . u_goal
   const float2* hvec;   // [9]: unit heading vectors
   const float* CT;      // 4 padded heading-class tables of the v2 gather (or NULL)
+  int shape = 0;        // class-table gather footprint: 0 = 16 x 16 su, 1 = 32 x 16 su
 };
+
+// footprint of the class-table gather used when none has been tuned
+inline int default_field_shape(int r) { return r > 30 ? 1 : 0; }
 
 // ---- launchers (sfm_kernels.cu) ----
 void launch_tables(int r, const sfm_params& p, float* T0, float* TX, float* TY, float* KO,

@@ -611,9 +611,9 @@ __global__ void k_class_tables(int r, int SP, double kP, double aP, double gamma
 
 int class_table_stride(int r) {
   const int need = 2 * r + 1;
-  for (int sp = 16; sp <= kMaxV2Stride; sp += 16)
+  for (int sp = 18; sp <= kMaxV2Stride; sp += 16)
     if (sp >= need) return sp;
-  return 0;  // radius too large for the v2 gather
+  return 0;  // radius too large for the class-table gather
 }
 
 size_t class_table_floats(int r) {
@@ -628,42 +628,48 @@ void launch_class_tables(int r, const sfm_params& p, float* T, cudaStream_t s) {
   k_class_tables<<<cdiv(n, 256), 256, 0, s>>>(r, sp, p.kP, p.aP, p.gamma, T);
 }
 
-template <int SP>
+template <int SP, int SHAPE>
 __global__ void __launch_bounds__(kV2Threads, 1)
     k_field_v2(Geo g, const int32_t* __restrict__ bin_start, const uint32_t* __restrict__ rec,
                const float* __restrict__ CT, const float* __restrict__ Fs,
                float* __restrict__ out, int out_row0, int fy0, int fy1, int store_lo,
                int store_hi) {
   extern __shared__ __align__(16) float sT[];
+  constexpr int FW = SHAPE ? 32 : 16, FH = 16, NJ = SHAPE ? 16 : 8;
   const int r = g.r;
   const int TR = 2 * r + 1 + 2 * kFieldPad, TS = TR * SP;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  // per-warp scratch: the batch's pedestrians in reach of the footprint, as
-  // (table offset of lane 0's first row, lane range | mirror bits)
+  // per-warp scratch: the batch's pedestrians in reach of the footprint
   int2* scr = reinterpret_cast<int2*>(sT + 4 * TS) + warp * 32;
   {
-    const float4* src = reinterpret_cast<const float4*>(CT);
-    float4* dst = reinterpret_cast<float4*>(sT);
-    for (int i = threadIdx.x; i < TS; i += blockDim.x) dst[i] = src[i];  // 4*TS floats
+    const float2* src = reinterpret_cast<const float2*>(CT);
+    float2* dst = reinterpret_cast<float2*>(sT);
+    for (int i = threadIdx.x; i < 2 * TS; i += blockDim.x) dst[i] = src[i];  // 4*TS floats
   }
   __syncthreads();
   const int wpb = blockDim.x >> 5;
   const int tw = gridDim.x * wpb;
-  const int nfx = (g.W + 31) >> 5;
+  const int nfx = (g.W + FW - 1) / FW;
   const int nf = nfx * (fy1 - fy0);
+  // this lane's column and first row inside a footprint
+  const int x = SHAPE ? lane : (lane & 15), yl = SHAPE ? 0 : (lane >> 4) * 8;
   for (int f = blockIdx.x * wpb + warp; f < nf; f += tw) {
-    const int x0 = (f % nfx) << 5, y0 = (fy0 + f / nfx) * kV2Rows;
-    float acc[kV2Rows];
+    const int x0 = (f % nfx) * FW, y0 = (fy0 + f / nfx) * FH;
+    float acc[NJ];
 #pragma unroll
-    for (int j = 0; j < kV2Rows; ++j) acc[j] = 0.f;
-    gather_footprint<SP, kV2Rows>(g, bin_start, rec, sT, TS, scr, lane, x0, y0, acc);
-    const int x = x0 + lane;
+    for (int j = 0; j < NJ; ++j) acc[j] = 0.f;
+    if (SHAPE)
+      gather_footprint32<SP>(g, bin_start, rec, sT, TS, scr, lane, x0, y0,
+                             *reinterpret_cast<float(*)[16]>(acc));
+    else
+      gather_footprint16<SP>(g, bin_start, rec, sT, TS, scr, lane, x0, y0,
+                             *reinterpret_cast<float(*)[8]>(acc));
 #pragma unroll
-    for (int j = 0; j < kV2Rows; ++j) {
-      const int y = y0 + j;
-      if (x < g.W && y < g.H && y >= store_lo && y < store_hi) {
-        const size_t c = (size_t)y * g.W + x;
-        out[(size_t)(y - out_row0) * g.W + x] = Fs[c] + acc[j];
+    for (int j = 0; j < NJ; ++j) {
+      const int y = y0 + yl + j, xx = x0 + x;
+      if (xx < g.W && y < g.H && y >= store_lo && y < store_hi) {
+        const size_t c = (size_t)y * g.W + xx;
+        out[(size_t)(y - out_row0) * g.W + xx] = Fs[c] + acc[j];
       }
     }
   }
@@ -671,25 +677,37 @@ __global__ void __launch_bounds__(kV2Threads, 1)
 
 static int g_num_sms = 0;
 
-template <int SP>
+template <int SP, int SHAPE>
 static void launch_v2(const Geo& g, const int32_t* bin_start, const uint32_t* rec, const float* CT,
-                      const float* Fs, float* out, int out_row0, int fy0, int fy1, int store_lo,
-                      int store_hi, cudaStream_t s) {
+                      const float* Fs, float* out, int out_row0, int store_lo, int store_hi,
+                      cudaStream_t s) {
+  constexpr int FW = SHAPE ? 32 : 16, FH = 16;
   const size_t smem = class_table_floats(g.r) * sizeof(float) + kV2Threads / 32 * 32 * sizeof(int2);
-  cudaFuncSetAttribute(k_field_v2<SP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaFuncSetAttribute(k_field_v2<SP, SHAPE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (!g_num_sms) {
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
     if (g_num_sms <= 0) g_num_sms = 1;
   }
-  const int nf = ((g.W + 31) / 32) * (fy1 - fy0);
+  const int fy0 = store_lo / FH, fy1 = (store_hi + FH - 1) / FH;
+  const int nf = ((g.W + FW - 1) / FW) * (fy1 - fy0);
   const int wpb = kV2Threads / 32;
   int blocks = (nf + wpb - 1) / wpb;
   if (blocks > g_num_sms) blocks = g_num_sms;
   if (blocks < 1) blocks = 1;
-  k_field_v2<SP><<<blocks, kV2Threads, smem, s>>>(g, bin_start, rec, CT, Fs, out, out_row0, fy0,
-                                                  fy1, store_lo, store_hi);
+  k_field_v2<SP, SHAPE><<<blocks, kV2Threads, smem, s>>>(g, bin_start, rec, CT, Fs, out, out_row0,
+                                                         fy0, fy1, store_lo, store_hi);
+}
+
+template <int SP>
+static void launch_v2_shape(const Geo& g, const int32_t* bin_start, const uint32_t* rec,
+                            const Tables& tb, const float* Fs, float* out, int out_row0,
+                            int store_lo, int store_hi, cudaStream_t s) {
+  if (tb.shape)
+    launch_v2<SP, 1>(g, bin_start, rec, tb.CT, Fs, out, out_row0, store_lo, store_hi, s);
+  else
+    launch_v2<SP, 0>(g, bin_start, rec, tb.CT, Fs, out, out_row0, store_lo, store_hi, s);
 }
 
 void launch_field(const Geo& g, const int32_t* bin_start, const uint32_t* rec, const Tables& tb,
@@ -701,14 +719,13 @@ void launch_field(const Geo& g, const int32_t* bin_start, const uint32_t* rec, c
     launch_field_v1(g, bin_start, rec, tb, Fs, out, out_row0, store_lo, store_hi, ctr, s);
     return;
   }
-  const int fy0 = store_lo / kV2Rows, fy1 = (store_hi + kV2Rows - 1) / kV2Rows;
   switch (sp) {
-    case 16: launch_v2<16>(g, bin_start, rec, tb.CT, Fs, out, out_row0, fy0, fy1, store_lo, store_hi, s); break;
-    case 32: launch_v2<32>(g, bin_start, rec, tb.CT, Fs, out, out_row0, fy0, fy1, store_lo, store_hi, s); break;
-    case 48: launch_v2<48>(g, bin_start, rec, tb.CT, Fs, out, out_row0, fy0, fy1, store_lo, store_hi, s); break;
-    case 64: launch_v2<64>(g, bin_start, rec, tb.CT, Fs, out, out_row0, fy0, fy1, store_lo, store_hi, s); break;
-    case 80: launch_v2<80>(g, bin_start, rec, tb.CT, Fs, out, out_row0, fy0, fy1, store_lo, store_hi, s); break;
-    default: launch_v2<96>(g, bin_start, rec, tb.CT, Fs, out, out_row0, fy0, fy1, store_lo, store_hi, s); break;
+    case 18: launch_v2_shape<18>(g, bin_start, rec, tb, Fs, out, out_row0, store_lo, store_hi, s); break;
+    case 34: launch_v2_shape<34>(g, bin_start, rec, tb, Fs, out, out_row0, store_lo, store_hi, s); break;
+    case 50: launch_v2_shape<50>(g, bin_start, rec, tb, Fs, out, out_row0, store_lo, store_hi, s); break;
+    case 66: launch_v2_shape<66>(g, bin_start, rec, tb, Fs, out, out_row0, store_lo, store_hi, s); break;
+    case 82: launch_v2_shape<82>(g, bin_start, rec, tb, Fs, out, out_row0, store_lo, store_hi, s); break;
+    default: launch_v2_shape<98>(g, bin_start, rec, tb, Fs, out, out_row0, store_lo, store_hi, s); break;
   }
 }
 

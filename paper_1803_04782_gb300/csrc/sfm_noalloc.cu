@@ -32,7 +32,7 @@ constexpr size_t kNaScanTmp = kNaStart + kNaBins + 64;  // scan block totals
 constexpr size_t kNaErr = kNaScanTmp + 64;              // error word
 constexpr size_t kNaRec = kNaErr + 64;                  // bin records
 constexpr size_t kNaTables = kNaRec + kNaPeds;          // heading-class tables
-constexpr size_t kNaTableFloats = 4 * (2 * SFM_NOALLOC_MAX_RADIUS + 1 + 2 * (kV2Rows - 1)) * 96;
+constexpr size_t kNaTableFloats = 4 * (2 * SFM_NOALLOC_MAX_RADIUS + 1 + 2 * kFieldPadRows) * kMaxV2Stride;
 constexpr size_t kNaWords = (kNaTables + kNaTableFloats + 63) / 64 * 64;
 
 static __device__ __align__(256) uint32_t g_noalloc_scratch[kNaWords];
@@ -141,6 +141,7 @@ extern "C" sfm_status sfm_field_noalloc(const sfm_lattice* lat, const sfm_params
   launch_class_tables(g.r, *prm, tables, s);
   Tables tb{};
   tb.CT = tables;
+  tb.shape = default_field_shape(g.r);
   launch_field(g, start, rec, tb, base, field, 0, 0, g.H, nullptr, s);
 
   uint32_t h_err = 0;

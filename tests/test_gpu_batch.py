@@ -24,7 +24,7 @@ def _built():
 
 def _mixed_batch():
     """Ten lattices of uneven size, crowd and radius (every class-table row
-    stride from 16 to 96), closed, periodic and torus boundaries."""
+    stride from 18 to 98), closed, periodic and torus boundaries."""
     sc = [
         SG.random_scene(64, 64, 300, r=5, seed=201, exits=("east",)),
         SG.random_scene(150, 97, 1500, r=12, seed=202, obstacles=3, exits=("north", "west"),
@@ -92,8 +92,8 @@ def test_batch_matches_independent_contexts_bitwise():
 def test_batch_autotuned_tiles_give_the_same_ticks():
     scenes = _mixed_batch()
     with sfm.Batch(scenes) as b:
-        rows = b.autotune()
-        assert set(rows.values()) <= {8, 16}
+        shapes = b.autotune()
+        assert set(shapes.values()) <= {"16x16", "32x16"}
         _compare_with_single(scenes, b, ticks=3)
 
 

@@ -176,6 +176,31 @@ def test_banded_field_is_bitwise_the_unbanded_field(periodic):
         np.testing.assert_array_equal(a.field(), b.field_banded())
 
 
+@pytest.mark.parametrize("name", ["room_mixed", "torus", "thin_torus", "wide_radius", "radius47"])
+def test_both_gather_footprints_give_the_same_field_and_ticks(name):
+    """The 16x16 and 32x16 warp footprints add each su's terms in the same
+    order: fields and ticks are bitwise equal, with and without the tuner."""
+    sc = SCENES[name]()
+    with sfm.Sim(sc) as a, sfm.Sim(sc) as b, sfm.Sim(sc) as c:
+        a.set_footprint("16x16")
+        b.set_footprint("32x16")
+        assert c.autotune() in ("16x16", "32x16")
+        for s in (a, b, c):
+            s.compute_field()
+        np.testing.assert_array_equal(a.field(), b.field())
+        np.testing.assert_array_equal(a.field(), c.field())
+        for _ in range(3):
+            for s in (a, b, c):
+                s.step(1)
+            for s in (b, c):
+                np.testing.assert_array_equal(a.decisions()[0], s.decisions()[0])
+                for x, y in zip(a.peds(), s.peds()):
+                    np.testing.assert_array_equal(x, y)
+        with pytest.raises(sfm.SfmError) as e:
+            sfm._check(a.ctx, sfm.lib().sfm_set_field_footprint(a.ctx, 2))
+        assert e.value.status == sfm.SFM_EINVAL
+
+
 def test_field_respects_heading_linearity_closed_form():
     """A single pedestrian in an open periodic lattice: the GPU field equals
     the closed form k d^a (1 + gamma cos) to FP32 rounding."""
