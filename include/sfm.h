@@ -48,7 +48,7 @@
 extern "C" {
 #endif
 
-#define SFM_ABI_VERSION 1
+#define SFM_ABI_VERSION 2
 #define SFM_MAX_RADIUS 64
 #define SFM_NSTAGES 6
 
@@ -166,7 +166,7 @@ sfm_status sfm_autotune(sfm_ctx* ctx, int32_t* shape_out);
 
 /* Sets the warp footprint of the field gather by hand: 0 = 16 x 16 su,
  * 1 = 32 x 16 su; anything else is SFM_EINVAL.  Ignored (but accepted) when
- * the interaction radius exceeds the class-table gather (r > 47). */
+ * the interaction radius exceeds the class-table gather (r > 50). */
 sfm_status sfm_set_field_footprint(sfm_ctx* ctx, int32_t shape);
 
 /* Wait for the context's stream and report device-side errors. */
@@ -223,7 +223,7 @@ sfm_status sfm_stage_times(sfm_ctx* ctx, double* ms, int64_t* ticks);
  * flight, Sec. 4.2) across scenarios.
  *
  * sfm_batch_create: nscenes lattices (1..65535); lats[i], cells[i] (host,
- *   W*H bytes each), prms[i] (r <= 47).  The context then accepts
+ *   W*H bytes each), prms[i] (r <= 50).  The context then accepts
  *   sfm_batch_place, sfm_step, sfm_compute_field, sfm_read_field /
  *   _static_field / _guidance (all lattices concatenated in order, offsets
  *   from sfm_batch_offsets), sfm_read_peds / _decisions (pedestrians
@@ -237,8 +237,9 @@ sfm_status sfm_stage_times(sfm_ctx* ctx, double* ms, int64_t* ticks);
  *   be NULL) receive where each lattice starts in the concatenated arrays.
  * sfm_batch_autotune: times the field stage of each radius class (lattices
  *   sharing a class-table row stride) with 16 x 16 and 32 x 16 su warp
- *   footprints and keeps the faster; shape_per_class[6] (may be NULL)
- *   receives 0 (16 x 16) or 1 (32 x 16) for strides 18, 34, ..., 98.  Needs
+ *   footprints and keeps the faster; shape_per_class[7] (may be NULL)
+ *   receives 0 (16 x 16) or 1 (32 x 16) for the strides 34, 50, 66, 82, 98,
+ *   114 (radius <= 1, 9, 17, 25, 33, 41) and 102 (radius 42..50).  Needs
  *   placed pedestrians; moves nobody.
  * sfm_batch_test_missing_ctas: test hook of the bounded barrier wait; the
  *   next tick's barriers wait for `missing` CTAs that are never launched, so

@@ -308,12 +308,16 @@ def sfm_batch_offsets(ctx, nscenes: int):
     return su, pe
 
 
+TABLE_STRIDES = (34, 50, 66, 82, 98, 114, 102)  # class-table row stride per radius class
+
+
 def sfm_batch_autotune(ctx):
-    """Footprint chosen per radius class (class-table row stride 18, 34, ...,
-    98): "16x16" or "32x16"."""
-    shp = np.zeros(6, np.int32)
+    """Footprint chosen per radius class, keyed by the class-table row stride
+    (34, 50, ..., 114 for radius <= 1, 9, ..., 41; 102 for radius 42..50):
+    "16x16" or "32x16"."""
+    shp = np.zeros(len(TABLE_STRIDES), np.int32)
     _check(ctx, lib().sfm_batch_autotune(ctx, shp.ctypes.data_as(C.c_void_p)))
-    return {18 + 16 * i: ("32x16" if v else "16x16") for i, v in enumerate(shp)}
+    return {sp: ("32x16" if v else "16x16") for sp, v in zip(TABLE_STRIDES, shp)}
 
 
 def sfm_batch_test_missing_ctas(ctx, missing: int) -> None:

@@ -95,7 +95,7 @@ struct BatchState {
   unsigned int* bar = nullptr;
   int* work = nullptr;
   int max_ts = 0;
-  int shape_of_sp[7] = {0, 0, 0, 0, 0, 0, 0};  // footprint shape per radius class
+  int shape_of_sp[kNumStrideClasses] = {};  // footprint shape per class-table stride
   int missing = 0;  // test hook: CTAs the barrier expects beyond those launched
   int grid = 0;
   std::vector<int> order;  // lattices by decreasing field cost
@@ -176,9 +176,9 @@ __device__ __forceinline__ void batch_footprint(const BatchArgs& a, const BatchS
   const int nfx = (g.W + fw - 1) / fw;
   const int x0 = (f % nfx) * fw, y0 = (f / nfx) * 16;
   if (shape == 0) {
-    float acc[8];
+    float2 acc[4];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) acc[j] = 0.f;
+    for (int j = 0; j < 4; ++j) acc[j] = make_float2(0.f, 0.f);
     gather_footprint16<SP>(g, a.bin_start + sc.bin_off, a.rec, sT, sc.ts, scr, lane, x0, y0, acc);
     const int x = x0 + (lane & 15), yl = y0 + (lane >> 4) * 8;
 #pragma unroll
@@ -186,13 +186,13 @@ __device__ __forceinline__ void batch_footprint(const BatchArgs& a, const BatchS
       const int y = yl + j;
       if (x < g.W && y < g.H) {
         const size_t c = (size_t)sc.su_off + (size_t)y * g.W + x;
-        a.F[c] = a.Fs[c] + acc[j];
+        a.F[c] = a.Fs[c] + ((j & 1) ? acc[j >> 1].y : acc[j >> 1].x);
       }
     }
   } else {
-    float acc[16];
+    float2 acc[8];
 #pragma unroll
-    for (int j = 0; j < 16; ++j) acc[j] = 0.f;
+    for (int j = 0; j < 8; ++j) acc[j] = make_float2(0.f, 0.f);
     gather_footprint32<SP>(g, a.bin_start + sc.bin_off, a.rec, sT, sc.ts, scr, lane, x0, y0, acc);
     const int x = x0 + lane;
 #pragma unroll
@@ -200,7 +200,7 @@ __device__ __forceinline__ void batch_footprint(const BatchArgs& a, const BatchS
       const int y = y0 + j;
       if (x < g.W && y < g.H) {
         const size_t c = (size_t)sc.su_off + (size_t)y * g.W + x;
-        a.F[c] = a.Fs[c] + acc[j];
+        a.F[c] = a.Fs[c] + ((j & 1) ? acc[j >> 1].y : acc[j >> 1].x);
       }
     }
   }
@@ -210,19 +210,21 @@ __device__ __forceinline__ void batch_footprint_sp(const BatchArgs& a, const Bat
                                                    const float* sT, int2* scr, int lane, int f,
                                                    int shape) {
   switch (sc.sp) {
-    case 18: batch_footprint<18>(a, sc, sT, scr, lane, f, shape); break;
     case 34: batch_footprint<34>(a, sc, sT, scr, lane, f, shape); break;
     case 50: batch_footprint<50>(a, sc, sT, scr, lane, f, shape); break;
     case 66: batch_footprint<66>(a, sc, sT, scr, lane, f, shape); break;
     case 82: batch_footprint<82>(a, sc, sT, scr, lane, f, shape); break;
-    default: batch_footprint<98>(a, sc, sT, scr, lane, f, shape); break;
+    case 98: batch_footprint<98>(a, sc, sT, scr, lane, f, shape); break;
+    case 114: batch_footprint<114>(a, sc, sT, scr, lane, f, shape); break;
+    default: batch_footprint<kNarrowStride>(a, sc, sT, scr, lane, f, shape); break;
   }
 }
 
 constexpr int kScanChunk = kBatchThreads * 4;
 
 __global__ void __launch_bounds__(kBatchThreads, 1) k_tick_batch(BatchArgs a) {
-  extern __shared__ __align__(16) float sT[];
+  extern __shared__ __align__(16) float sm[];
+  float* sT = sm + kTableGuard;  // class tables after a zero guard
   __shared__ int sWarp[32];
   __shared__ int s_chunk, s_loaded;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -302,6 +304,7 @@ __global__ void __launch_bounds__(kBatchThreads, 1) k_tick_batch(BatchArgs a) {
   // S2: field -- chunks of 32 footprints (one per warp) from the cost-sorted
   // work list; a lattice's class tables are loaded when the CTA switches to it
   if (tid == 0) s_loaded = -1;
+  if (tid < kTableGuard) sm[tid] = 0.f;
   for (;;) {
     if (tid == 0) s_chunk = atomicAdd(a.work, 1);
     __syncthreads();
@@ -436,7 +439,6 @@ sfm_status balloc(sfm_ctx* ctx, T** p, size_t count) {
     if (s_ != SFM_OK) return s_; \
   } while (0)
 
-int sp_index(int sp) { return (sp - 18) / 16; }  // 18, 34, ..., 98 -> 0..5
 
 // Work list of the field stage: lattices by decreasing cost per footprint,
 // each cut into chunks of 32 footprints of its radius class's height.  When
@@ -446,7 +448,7 @@ void build_chunks(BatchState* B, std::vector<BatchChunk>& out, int only_sp) {
   for (int s : B->order) {
     const BatchScene& sc = B->hs[s];
     if (only_sp > 0 && sc.sp != only_sp) continue;
-    const int shape = B->shape_of_sp[sp_index(sc.sp)];
+    const int shape = B->shape_of_sp[class_of_stride(sc.sp)];
     const int nf = shape_nf(sc.g, shape);
     for (int f0 = 0; f0 < nf; f0 += 32) out.push_back(BatchChunk{s, f0, shape, 0});
   }
@@ -506,7 +508,8 @@ BatchArgs make_args(sfm_ctx* ctx, int field_only) {
 }
 
 size_t batch_smem(const BatchState* B) {
-  return (size_t)4 * B->max_ts * sizeof(float) + (size_t)kBatchThreads / 32 * 32 * sizeof(int2);
+  return (size_t)(kTableGuard + 4 * B->max_ts) * sizeof(float) +
+         (size_t)kBatchThreads / 32 * 32 * sizeof(int2);
 }
 
 cudaError_t launch_tick(sfm_ctx* ctx, int field_only, cudaStream_t s) {
@@ -620,8 +623,8 @@ sfm_status sfm_batch_create(int32_t nscenes, const sfm_lattice* lats, const uint
     const sfm_params& p = prms[s];
     if (!cells[s] || L.W < 3 || L.H < 3 || (int64_t)L.W * L.H > ((int64_t)1 << 31))
       return bfail(nullptr, SFM_EINVAL, "lattice " + std::to_string(s) + ": bad size or cells");
-    if (p.r < 0 || p.r > 47)
-      return bfail(nullptr, SFM_EINVAL, "lattice " + std::to_string(s) + ": radius outside [0, 47]");
+    if (p.r < 0 || p.r > kMaxTableRadius)
+      return bfail(nullptr, SFM_EINVAL, "lattice " + std::to_string(s) + ": radius outside [0, 50]");
     if ((L.periodic_x && L.W < 2 * p.r + 1) || (L.periodic_y && L.H < 2 * p.r + 1))
       return bfail(nullptr, SFM_EINVAL,
                    "lattice " + std::to_string(s) + ": a periodic extent must be >= 2r+1");
@@ -922,8 +925,8 @@ sfm_status sfm_batch_autotune(sfm_ctx* ctx, int32_t* shape_per_class) {
   cudaEvent_t e0, e1;
   BCU(cudaEventCreate(&e0));
   BCU(cudaEventCreate(&e1));
-  for (int ci = 0; ci < 6; ++ci) {
-    const int sp = 18 + 16 * ci;
+  for (int ci = 0; ci < kNumStrideClasses; ++ci) {
+    const int sp = stride_of_class(ci);
     bool present = false;
     for (const BatchScene& sc : B->hs) present |= sc.sp == sp;
     if (!present) continue;
@@ -963,7 +966,7 @@ sfm_status sfm_batch_autotune(sfm_ctx* ctx, int32_t* shape_per_class) {
     B->graph = nullptr;
   }
   if (shape_per_class)
-    for (int ci = 0; ci < 6; ++ci) shape_per_class[ci] = B->shape_of_sp[ci];
+    for (int ci = 0; ci < kNumStrideClasses; ++ci) shape_per_class[ci] = B->shape_of_sp[ci];
   return SFM_OK;
 }
 

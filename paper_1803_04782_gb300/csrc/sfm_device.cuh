@@ -173,6 +173,16 @@ __device__ __forceinline__ void halo_entry(int i, int lo, int hi, int n, int per
 // footprint, after compacting the batch's records into the warp's scratch.
 // item.x: table offset of the record for footprint column 0 / row 0;
 // item.y: lane-column range llo | lhi << 5 | x mirror << 10 | y mirror << 11.
+// acc[k] += (p[2k S], p[(2k + 1) S]), S = +-SP: one shared-memory read per
+// row, one packed FP32 add per row pair (each half rounded as a scalar add).
+template <int SP, int NP, bool NEG>
+__device__ __forceinline__ void add_row_pairs(const float* __restrict__ p, float2 (&acc)[NP]) {
+  constexpr int S = NEG ? -SP : SP;
+#pragma unroll
+  for (int k = 0; k < NP; ++k)
+    acc[k] = __fadd2_rn(acc[k], make_float2(p[2 * k * S], p[(2 * k + 1) * S]));
+}
+
 template <int SP, int FW, int FH, class Visit>
 __device__ __forceinline__ void walk_footprint(const Geo& g, const int32_t* __restrict__ bin_start,
                                                const uint32_t* __restrict__ rec, int TS, int2* scr,
@@ -239,52 +249,49 @@ __device__ __forceinline__ void walk_footprint(const Geo& g, const int32_t* __re
   }
 }
 
-// Adds to acc[j] the pedestrian field of the 16 x 16 footprint at (x0, y0):
-// lane l owns column x0 + (l & 15) and rows y0 + 8 (l >> 4) + j, j < 8.  One
-// shared-memory read and one FP32 add per (su, pedestrian) pair; the two
-// half-warps read rows 8 SP apart, on disjoint banks when SP = 16k + 2.
-// sT: the 4 heading-class tables (row stride SP, TS floats each, kFieldPad
-// zero rows above and below the window); scr: 32 int2 of per-warp scratch.
+// Adds the pedestrian field of the 16 x 16 footprint at (x0, y0): lane l owns
+// column x0 + (l & 15) and rows y0 + 8 (l >> 4) + j, j < 8, row j in
+// acc[j / 2] (.x even, .y odd).  One shared-memory read per (su, pedestrian)
+// pair; the two half-warps read rows 8 SP apart, on disjoint banks as SP = 2
+// (mod 4).  sT: the 4 heading-class tables (row stride SP, TS floats each,
+// kFieldPad zero rows above and below the window, kTableGuard zero floats in
+// front); scr: 32 int2 of per-warp scratch.  A kept pedestrian lies within r
+// columns of the footprint, so with a wide stride every lane's column offset
+// lies in [-15, 2r + 15]: out-of-reach lanes read zero columns (of its own
+// row, or the row above, or the guard) and need no test.
 template <int SP>
 __device__ __forceinline__ void gather_footprint16(const Geo& g, const int32_t* __restrict__ bin_start,
                                                    const uint32_t* __restrict__ rec,
                                                    const float* __restrict__ sT, int TS, int2* scr,
-                                                   int lane, int x0, int y0, float (&acc)[8]) {
+                                                   int lane, int x0, int y0, float2 (&acc)[4]) {
   const int col = lane & 15, hoff = (lane >> 4) * 8 * SP;
   walk_footprint<SP, 16, 16>(g, bin_start, rec, TS, scr, lane, x0, y0, [&](const int2 it) {
     const int llo = it.y & 31, lhi = (it.y >> 5) & 31;
-    if (col >= llo && col <= lhi) {
+    if (SP != kNarrowStride || (col >= llo && col <= lhi)) {
       const float* p = sT + it.x + ((it.y & 1024) ? -col : col);
-      if (it.y & 2048) {
-        p -= hoff;
-#pragma unroll
-        for (int jj = 0; jj < 8; ++jj) acc[jj] += p[-jj * SP];
-      } else {
-        p += hoff;
-#pragma unroll
-        for (int jj = 0; jj < 8; ++jj) acc[jj] += p[jj * SP];
-      }
+      if (it.y & 2048)
+        add_row_pairs<SP, 4, true>(p - hoff, acc);
+      else
+        add_row_pairs<SP, 4, false>(p + hoff, acc);
     }
   });
 }
 
-// The 32 x 16 footprint: lane l owns column x0 + l and rows y0 + j, j < 16.
+// The 32 x 16 footprint: lane l owns column x0 + l and rows y0 + j, j < 16,
+// row j in acc[j / 2]; column offsets lie in [-31, 2r + 31].
 template <int SP>
 __device__ __forceinline__ void gather_footprint32(const Geo& g, const int32_t* __restrict__ bin_start,
                                                    const uint32_t* __restrict__ rec,
                                                    const float* __restrict__ sT, int TS, int2* scr,
-                                                   int lane, int x0, int y0, float (&acc)[16]) {
+                                                   int lane, int x0, int y0, float2 (&acc)[8]) {
   walk_footprint<SP, 32, 16>(g, bin_start, rec, TS, scr, lane, x0, y0, [&](const int2 it) {
     const int llo = it.y & 31, lhi = (it.y >> 5) & 31;
-    if (lane >= llo && lane <= lhi) {
+    if (SP != kNarrowStride || (lane >= llo && lane <= lhi)) {
       const float* p = sT + it.x + ((it.y & 1024) ? -lane : lane);
-      if (it.y & 2048) {
-#pragma unroll
-        for (int jj = 0; jj < 16; ++jj) acc[jj] += p[-jj * SP];
-      } else {
-#pragma unroll
-        for (int jj = 0; jj < 16; ++jj) acc[jj] += p[jj * SP];
-      }
+      if (it.y & 2048)
+        add_row_pairs<SP, 8, true>(p, acc);
+      else
+        add_row_pairs<SP, 8, false>(p, acc);
     }
   });
 }

@@ -20,13 +20,47 @@ constexpr int kStageCap = 2048;    // pedestrians staged in shared memory per ch
 constexpr int kMaxHaloBins = 128;  // bins touched by one tile's halo (checked)
 constexpr int kBin = 32;           // side of a pedestrian bin (one warp column per su)
 // class-table gather: a warp owns a 16 x 16 su footprint (half-warp h = rows
-// 8h..8h+7, lane = column), 32 warps per CTA; table row stride SP = 16k + 2
-// >= 2r + 1 (radius <= 47), which puts the two half-warps' rows on disjoint
-// banks.  A 32 x 16 footprint (lane = column, 16 rows) is the alternative tile.
-constexpr int kV2Rows = 8;       // rows per lane of the 16 x 16 footprint
+// 8h..8h+7, lane = column) or a 32 x 16 one (lane = column, 16 rows), 32
+// warps per CTA.  The 4 heading-class tables sit in shared memory with row
+// stride SP = 2 (mod 4), which puts the two half-warps' rows (8 SP apart) on
+// disjoint banks.  A "wide" stride leaves >= 31 zero columns after each row's
+// 2r + 1, so a lane outside a pedestrian's reach reads a zero and no lane
+// needs a range test; the narrow stride 102 (radius 42..50, where wide tables
+// would not fit in shared memory) keeps the test.
+constexpr int kV2Rows = 8;         // rows per lane of the 16 x 16 footprint
 constexpr int kFieldPadRows = 15;  // zero rows above/below each class table
 constexpr int kV2Threads = 1024;
-constexpr int kMaxV2Stride = 98;
+constexpr int kTableGuard = 32;    // zero floats in front of the tables in shared memory
+constexpr int kNarrowStride = 102;
+constexpr int kNumStrideClasses = 7;  // the wide strides 34, 50, ..., 114, then 102
+constexpr int kMaxTableRadius = 50;   // largest radius of the class-table gather
+constexpr int kMaxTableStride = 114;
+
+constexpr int stride_of_class(int ci) { return ci < 6 ? 34 + 16 * ci : kNarrowStride; }
+constexpr int class_of_stride(int sp) { return sp == kNarrowStride ? 6 : (sp - 34) / 16; }
+constexpr bool wide_stride(int sp) { return sp != kNarrowStride; }
+
+// Row stride of the class tables for radius r (0: beyond the gather).
+constexpr int class_table_stride_of(int r) {
+  if (r < 0 || r > kMaxTableRadius) return 0;
+  for (int ci = 0; ci < 6; ++ci)
+    if (stride_of_class(ci) >= 2 * r + 32) return stride_of_class(ci);
+  return kNarrowStride;  // 2r + 1 <= 101
+}
+constexpr size_t class_table_floats_of(int r) {
+  return class_table_stride_of(r)
+             ? (size_t)4 * (2 * r + 1 + 2 * kFieldPadRows) * class_table_stride_of(r)
+             : 0;
+}
+constexpr size_t max_class_table_floats(int rmax) {
+  size_t m = 0;
+  for (int r = 0; r <= rmax; ++r) m = class_table_floats_of(r) > m ? class_table_floats_of(r) : m;
+  return m;
+}
+// shared memory of a gather CTA: guard, tables, per-warp record scratch
+static_assert((kTableGuard + max_class_table_floats(kMaxTableRadius)) * 4 +
+                      kV2Threads / 32 * 32 * 8 <= 227 * 1024 - 1024,
+              "class tables exceed shared memory");
 
 // device error flags (sticky until read by a synchronising call)
 enum : uint32_t {

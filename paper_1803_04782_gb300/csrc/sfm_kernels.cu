@@ -609,17 +609,9 @@ __global__ void k_class_tables(int r, int SP, double kP, double aP, double gamma
   T[i] = (float)v;
 }
 
-int class_table_stride(int r) {
-  const int need = 2 * r + 1;
-  for (int sp = 18; sp <= kMaxV2Stride; sp += 16)
-    if (sp >= need) return sp;
-  return 0;  // radius too large for the class-table gather
-}
+int class_table_stride(int r) { return class_table_stride_of(r); }
 
-size_t class_table_floats(int r) {
-  const int sp = class_table_stride(r);
-  return sp ? (size_t)4 * (2 * r + 1 + 2 * kFieldPad) * sp : 0;
-}
+size_t class_table_floats(int r) { return class_table_floats_of(r); }
 
 void launch_class_tables(int r, const sfm_params& p, float* T, cudaStream_t s) {
   const int sp = class_table_stride(r);
@@ -634,17 +626,19 @@ __global__ void __launch_bounds__(kV2Threads, 1)
                const float* __restrict__ CT, const float* __restrict__ Fs,
                float* __restrict__ out, int out_row0, int fy0, int fy1, int store_lo,
                int store_hi) {
-  extern __shared__ __align__(16) float sT[];
+  extern __shared__ __align__(16) float sm[];
   constexpr int FW = SHAPE ? 32 : 16, FH = 16, NJ = SHAPE ? 16 : 8;
   const int r = g.r;
   const int TR = 2 * r + 1 + 2 * kFieldPad, TS = TR * SP;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float* sT = sm + kTableGuard;
   // per-warp scratch: the batch's pedestrians in reach of the footprint
   int2* scr = reinterpret_cast<int2*>(sT + 4 * TS) + warp * 32;
   {
     const float2* src = reinterpret_cast<const float2*>(CT);
     float2* dst = reinterpret_cast<float2*>(sT);
     for (int i = threadIdx.x; i < 2 * TS; i += blockDim.x) dst[i] = src[i];  // 4*TS floats
+    if (threadIdx.x < kTableGuard) sm[threadIdx.x] = 0.f;
   }
   __syncthreads();
   const int wpb = blockDim.x >> 5;
@@ -655,21 +649,19 @@ __global__ void __launch_bounds__(kV2Threads, 1)
   const int x = SHAPE ? lane : (lane & 15), yl = SHAPE ? 0 : (lane >> 4) * 8;
   for (int f = blockIdx.x * wpb + warp; f < nf; f += tw) {
     const int x0 = (f % nfx) * FW, y0 = (fy0 + f / nfx) * FH;
-    float acc[NJ];
+    float2 acc[NJ / 2];
 #pragma unroll
-    for (int j = 0; j < NJ; ++j) acc[j] = 0.f;
-    if (SHAPE)
-      gather_footprint32<SP>(g, bin_start, rec, sT, TS, scr, lane, x0, y0,
-                             *reinterpret_cast<float(*)[16]>(acc));
+    for (int j = 0; j < NJ / 2; ++j) acc[j] = make_float2(0.f, 0.f);
+    if constexpr (SHAPE)
+      gather_footprint32<SP>(g, bin_start, rec, sT, TS, scr, lane, x0, y0, acc);
     else
-      gather_footprint16<SP>(g, bin_start, rec, sT, TS, scr, lane, x0, y0,
-                             *reinterpret_cast<float(*)[8]>(acc));
+      gather_footprint16<SP>(g, bin_start, rec, sT, TS, scr, lane, x0, y0, acc);
 #pragma unroll
     for (int j = 0; j < NJ; ++j) {
       const int y = y0 + yl + j, xx = x0 + x;
       if (xx < g.W && y < g.H && y >= store_lo && y < store_hi) {
         const size_t c = (size_t)y * g.W + xx;
-        out[(size_t)(y - out_row0) * g.W + xx] = Fs[c] + acc[j];
+        out[(size_t)(y - out_row0) * g.W + xx] = Fs[c] + ((j & 1) ? acc[j >> 1].y : acc[j >> 1].x);
       }
     }
   }
@@ -682,7 +674,8 @@ static void launch_v2(const Geo& g, const int32_t* bin_start, const uint32_t* re
                       const float* Fs, float* out, int out_row0, int store_lo, int store_hi,
                       cudaStream_t s) {
   constexpr int FW = SHAPE ? 32 : 16, FH = 16;
-  const size_t smem = class_table_floats(g.r) * sizeof(float) + kV2Threads / 32 * 32 * sizeof(int2);
+  const size_t smem = (kTableGuard + class_table_floats(g.r)) * sizeof(float) +
+                      kV2Threads / 32 * 32 * sizeof(int2);
   cudaFuncSetAttribute(k_field_v2<SP, SHAPE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (!g_num_sms) {
     int dev = 0;
@@ -720,12 +713,13 @@ void launch_field(const Geo& g, const int32_t* bin_start, const uint32_t* rec, c
     return;
   }
   switch (sp) {
-    case 18: launch_v2_shape<18>(g, bin_start, rec, tb, Fs, out, out_row0, store_lo, store_hi, s); break;
     case 34: launch_v2_shape<34>(g, bin_start, rec, tb, Fs, out, out_row0, store_lo, store_hi, s); break;
     case 50: launch_v2_shape<50>(g, bin_start, rec, tb, Fs, out, out_row0, store_lo, store_hi, s); break;
     case 66: launch_v2_shape<66>(g, bin_start, rec, tb, Fs, out, out_row0, store_lo, store_hi, s); break;
     case 82: launch_v2_shape<82>(g, bin_start, rec, tb, Fs, out, out_row0, store_lo, store_hi, s); break;
-    default: launch_v2_shape<98>(g, bin_start, rec, tb, Fs, out, out_row0, store_lo, store_hi, s); break;
+    case 98: launch_v2_shape<98>(g, bin_start, rec, tb, Fs, out, out_row0, store_lo, store_hi, s); break;
+    case 114: launch_v2_shape<114>(g, bin_start, rec, tb, Fs, out, out_row0, store_lo, store_hi, s); break;
+    default: launch_v2_shape<kNarrowStride>(g, bin_start, rec, tb, Fs, out, out_row0, store_lo, store_hi, s); break;
   }
 }
 

@@ -32,7 +32,7 @@ constexpr size_t kNaScanTmp = kNaStart + kNaBins + 64;  // scan block totals
 constexpr size_t kNaErr = kNaScanTmp + 64;              // error word
 constexpr size_t kNaRec = kNaErr + 64;                  // bin records
 constexpr size_t kNaTables = kNaRec + kNaPeds;          // heading-class tables
-constexpr size_t kNaTableFloats = 4 * (2 * SFM_NOALLOC_MAX_RADIUS + 1 + 2 * kFieldPadRows) * kMaxV2Stride;
+constexpr size_t kNaTableFloats = max_class_table_floats(SFM_NOALLOC_MAX_RADIUS);
 constexpr size_t kNaWords = (kNaTables + kNaTableFloats + 63) / 64 * 64;
 
 static __device__ __align__(256) uint32_t g_noalloc_scratch[kNaWords];

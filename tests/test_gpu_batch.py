@@ -24,7 +24,8 @@ def _built():
 
 def _mixed_batch():
     """Ten lattices of uneven size, crowd and radius (every class-table row
-    stride from 18 to 98), closed, periodic and torus boundaries."""
+    stride: 34, 50, ..., 114 and the narrow 102), closed, periodic and torus
+    boundaries."""
     sc = [
         SG.random_scene(64, 64, 300, r=5, seed=201, exits=("east",)),
         SG.random_scene(150, 97, 1500, r=12, seed=202, obstacles=3, exits=("north", "west"),

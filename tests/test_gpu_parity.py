@@ -69,21 +69,33 @@ def _thin_torus():
                            goal_mode="mixed", heading_mode="random")
 
 
+def _radius41():
+    # largest radius of the wide class-table stride (114: no lane range test)
+    return SG.random_scene(150, 140, 1400, r=41, seed=113, periodic_x=1, exits=("north",),
+                           goal_mode="mixed", heading_mode="random")
+
+
 def _radius47():
-    # largest radius of the shared-memory class-table gather (row stride 96)
+    # narrow class-table stride (102): out-of-reach lanes are masked
     return SG.random_scene(160, 170, 1500, r=47, seed=110, periodic_y=1, exits=("east",),
                            goal_mode="mixed", heading_mode="random")
 
 
 def _radius50():
-    # beyond the class-table gather: the three-component gather takes over
+    # largest radius of the class-table gather
     return SG.random_scene(230, 140, 1200, r=50, seed=112, obstacles=3, exits=("west",),
+                           goal_mode="mixed", heading_mode="random")
+
+
+def _radius53():
+    # beyond the class-table gather: the three-component gather takes over
+    return SG.random_scene(200, 150, 1000, r=53, seed=114, obstacles=2, exits=("south",),
                            goal_mode="mixed", heading_mode="random")
 
 
 SCENES = {f.__name__[1:]: f for f in (_room_mixed, _corridor_periodic, _torus, _no_field,
                                       _tall_r1, _tiny, _dense, _wide_radius, _thin_torus,
-                                      _radius47, _radius50)}
+                                      _radius41, _radius47, _radius50, _radius53)}
 
 
 @pytest.mark.parametrize("name", list(SCENES))
@@ -176,7 +188,8 @@ def test_banded_field_is_bitwise_the_unbanded_field(periodic):
         np.testing.assert_array_equal(a.field(), b.field_banded())
 
 
-@pytest.mark.parametrize("name", ["room_mixed", "torus", "thin_torus", "wide_radius", "radius47"])
+@pytest.mark.parametrize("name", ["room_mixed", "torus", "thin_torus", "wide_radius", "radius41",
+                                  "radius47"])
 def test_both_gather_footprints_give_the_same_field_and_ticks(name):
     """The 16x16 and 32x16 warp footprints add each su's terms in the same
     order: fields and ticks are bitwise equal, with and without the tuner."""
