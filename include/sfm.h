@@ -164,6 +164,13 @@ sfm_status sfm_compute_field(sfm_ctx* ctx);
  * nobody. */
 sfm_status sfm_autotune(sfm_ctx* ctx, int32_t* shape_out);
 
+/* How the pedestrians are sorted into bins each tick (the bin records and
+ * every result are identical either way): 1 = by scanning the per-su class
+ * grid (cost follows the lattice area), 2 = from the pedestrian list with
+ * atomic counts and an in-bin rank (cost follows the crowd), 0 = automatic
+ * (the default: the list when n * 64 < W * H).  Anything else is SFM_EINVAL. */
+sfm_status sfm_set_binning(sfm_ctx* ctx, int32_t mode);
+
 /* Sets the warp footprint of the field gather by hand: 0 = 16 x 16 su,
  * 1 = 32 x 16 su; anything else is SFM_EINVAL.  Ignored (but accepted) when
  * the interaction radius exceeds the class-table gather (r > 50). */

@@ -33,7 +33,7 @@ EXPORTS = [
     "sfm_set_time", "sfm_step", "sfm_compute_field", "sfm_sync", "sfm_read_field",
     "sfm_compute_field_into", "sfm_read_static_field", "sfm_read_guidance", "sfm_read_peds",
     "sfm_read_decisions", "sfm_stats", "sfm_set_timing", "sfm_stage_times",
-    "sfm_autotune", "sfm_set_field_footprint", "sfm_field_noalloc", "sfm_batch_create", "sfm_batch_place", "sfm_batch_offsets",
+    "sfm_autotune", "sfm_set_field_footprint", "sfm_set_binning", "sfm_field_noalloc", "sfm_batch_create", "sfm_batch_place", "sfm_batch_offsets",
     "sfm_batch_autotune", "sfm_batch_test_missing_ctas", "sfm_surrogate_nparams",
     "sfm_surrogate_create", "sfm_surrogate_destroy", "sfm_surrogate_last_error",
     "sfm_surrogate_set_params", "sfm_surrogate_get_params", "sfm_surrogate_grad",
@@ -106,6 +106,7 @@ def lib():
             "sfm_set_timing": (C.c_int, [P, I32]),
             "sfm_autotune": (C.c_int, [P, P]),
             "sfm_set_field_footprint": (C.c_int, [P, I32]),
+            "sfm_set_binning": (C.c_int, [P, I32]),
             "sfm_stage_times": (C.c_int, [P, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
             "sfm_field_noalloc": (C.c_int, [C.POINTER(Lattice), C.POINTER(Params), I32, P, P, P,
                                             P, P, P]),
@@ -448,6 +449,10 @@ class Sim:
 
     def autotune(self):
         return sfm_autotune(self.ctx)
+
+    def set_binning(self, mode: str):
+        """"auto", "grid" (scan the class grid) or "peds" (from the pedestrian list)."""
+        _check(self.ctx, lib().sfm_set_binning(self.ctx, {"auto": 0, "grid": 1, "peds": 2}[mode]))
 
     def set_footprint(self, shape: str):
         _check(self.ctx, lib().sfm_set_field_footprint(self.ctx, {"16x16": 0, "32x16": 1}[shape]))

@@ -138,9 +138,22 @@ void field_rows(sfm_ctx* c, float* out, int ya, int yb, int main_off, bool halos
   }
 }
 
+// Pedestrian-list binning when the crowd is sparse: its cost follows the
+// pedestrians (tens of bytes each), the grid scan's the area (2 bytes per su).
+bool bins_from_peds(const sfm_ctx* c) {
+  if (c->binning) return c->binning == 2;
+  return (int64_t)c->n * 64 < (int64_t)c->geo.W * c->geo.H;
+}
+
 void run_bins(sfm_ctx* c) {
   StageScope sc(c, SFM_STAGE_BIN);
   const Geo& g = c->geo;
+  if (bins_from_peds(c)) {
+    launch_bins_from_peds(g, c->n, c->xy, c->alive, c->heading, c->bin_count, c->bin_start,
+                          c->scan_tmp, c->bin_slot, c->bin_key, c->rec, c->rec_id, c->stream);
+    c->launches += c->n > 0 ? 6 : 3;  // count, three scan passes, scatter, rank
+    return;
+  }
   launch_bin_count(g, c->ocls, c->bin_count, c->stream);
   launch_scan(c->bin_count, c->bin_start, g.nbx * g.nby, c->scan_tmp, c->stream);
   launch_bin_fill(g, c->ocls, c->occ, c->bin_start, c->rec, c->rec_id, c->stream);
@@ -450,6 +463,8 @@ sfm_status sfm_place(sfm_ctx* ctx, int32_t n, const int32_t* xy, const uint8_t* 
     dfree(ctx, ctx->won);
     dfree(ctx, ctx->rec);
     dfree(ctx, ctx->rec_id);
+    dfree(ctx, ctx->bin_slot);
+    dfree(ctx, ctx->bin_key);
     ctx->xy = nullptr;
     ctx->cap = 0;
     TRY(dalloc(ctx, &ctx->xy, (size_t)n));
@@ -460,6 +475,8 @@ sfm_status sfm_place(sfm_ctx* ctx, int32_t n, const int32_t* xy, const uint8_t* 
     TRY(dalloc(ctx, &ctx->won, (size_t)n));
     TRY(dalloc(ctx, &ctx->rec, (size_t)n));
     TRY(dalloc(ctx, &ctx->rec_id, (size_t)n));
+    TRY(dalloc(ctx, &ctx->bin_slot, (size_t)n));
+    TRY(dalloc(ctx, &ctx->bin_key, (size_t)n));
     ctx->cap = n;
   }
   if (ctx->cap == 0) {
@@ -471,6 +488,8 @@ sfm_status sfm_place(sfm_ctx* ctx, int32_t n, const int32_t* xy, const uint8_t* 
     TRY(dalloc(ctx, &ctx->won, 1));
     TRY(dalloc(ctx, &ctx->rec, 1));
     TRY(dalloc(ctx, &ctx->rec_id, 1));
+    TRY(dalloc(ctx, &ctx->bin_slot, 1));
+    TRY(dalloc(ctx, &ctx->bin_key, 1));
     ctx->cap = 1;
   }
   ctx->placed = false;
@@ -633,6 +652,17 @@ sfm_status sfm_autotune(sfm_ctx* ctx, int32_t* shape_out) {
   drop_graph(ctx);
   if (shape_out) *shape_out = best_shape;
   return check_flags(ctx);
+}
+
+sfm_status sfm_set_binning(sfm_ctx* ctx, int32_t mode) {
+  if (!ctx) return SFM_EINVAL;
+  if (ctx->batch) return fail(ctx, SFM_EINVAL, "a batch bins from its class grids");
+  if (mode < 0 || mode > 2) return fail(ctx, SFM_EINVAL, "binning mode must be 0, 1 or 2");
+  if (ctx->binning != mode) {
+    ctx->binning = mode;
+    drop_graph(ctx);
+  }
+  return SFM_OK;
 }
 
 sfm_status sfm_set_field_footprint(sfm_ctx* ctx, int32_t shape) {

@@ -52,6 +52,9 @@ struct sfm_ctx {
   int32_t *bin_count = nullptr, *bin_start = nullptr, *scan_tmp = nullptr;
   uint32_t* rec = nullptr;
   int32_t* rec_id = nullptr;  // pedestrian of each bin record
+  int32_t* bin_slot = nullptr;  // pedestrian-list binning: arrival slot in the bin
+  uint32_t* bin_key = nullptr;  // pedestrian-list binning: su keys in slot order
+  int binning = 0;              // 0 automatic, 1 class grid, 2 pedestrian list
   sfm::Counters* ctr = nullptr;
   // pedestrians
   int n = 0, cap = 0;

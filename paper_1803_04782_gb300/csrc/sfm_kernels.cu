@@ -291,6 +291,66 @@ void launch_bin_fill(const Geo& g, const uint8_t* ocls, const int32_t* occ, cons
   k_bin_fill<<<cdiv(nw * 32, 256), 256, 0, s>>>(g, ocls, occ, start, rec, rec_id);
 }
 
+// The same records driven by the pedestrian list, for sparse crowds where
+// reading the whole class grid costs more than the pedestrians: count with
+// atomics (each pedestrian keeps its arrival slot), scan, scatter each
+// pedestrian's su key (row << 5 | column inside the bin) to its slot, then
+// rank: a pedestrian's place in its bin is the number of smaller keys there
+// (keys are unique, one pedestrian per su), which is the row-major order of
+// the grid path.  Work per pedestrian is the size of its bin.
+__device__ __forceinline__ int ped_bin(const Geo& g, int2 q) {
+  return (q.y / kBin) * g.nbx + q.x / kBin;
+}
+
+__global__ void k_binp_count(int n, Geo g, const int2* __restrict__ xy,
+                             const uint8_t* __restrict__ alive, int32_t* __restrict__ count,
+                             int32_t* __restrict__ slot) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n || !alive[p]) return;
+  slot[p] = atomicAdd(&count[ped_bin(g, xy[p])], 1);
+}
+
+__global__ void k_binp_scatter(int n, Geo g, const int2* __restrict__ xy,
+                               const uint8_t* __restrict__ alive, const int32_t* __restrict__ slot,
+                               const int32_t* __restrict__ start, uint32_t* __restrict__ key) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n || !alive[p]) return;
+  const int2 q = xy[p];
+  key[start[ped_bin(g, q)] + slot[p]] = (uint32_t)((q.y % kBin) << 5 | (q.x % kBin));
+}
+
+__global__ void k_binp_rank(int n, Geo g, const int2* __restrict__ xy,
+                            const uint8_t* __restrict__ alive, const uint8_t* __restrict__ heading,
+                            const int32_t* __restrict__ start, const uint32_t* __restrict__ key,
+                            uint32_t* __restrict__ rec, int32_t* __restrict__ rec_id) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n || !alive[p]) return;
+  const int2 q = xy[p];
+  const int b = ped_bin(g, q);
+  const int s = start[b], e = start[b + 1];
+  const int col = q.x % kBin, row = q.y % kBin;
+  const uint32_t mine = (uint32_t)(row << 5 | col);
+  int rank = 0;
+  for (int i = s; i < e; ++i) rank += key[i] < mine;
+  const uint32_t cls = heading[p] > 8 ? 0u : heading[p];
+  rec[s + rank] = (uint32_t)col | ((uint32_t)row << 8) | (cls << 16);
+  rec_id[s + rank] = p;
+}
+
+void launch_bins_from_peds(const Geo& g, int n, const int2* xy, const uint8_t* alive,
+                           const uint8_t* heading, int32_t* count, int32_t* start,
+                           int32_t* scan_tmp, int32_t* slot, uint32_t* key, uint32_t* rec,
+                           int32_t* rec_id, cudaStream_t s) {
+  const int nbins = g.nbx * g.nby;
+  cudaMemsetAsync(count, 0, (size_t)nbins * sizeof(int32_t), s);
+  if (n > 0) k_binp_count<<<cdiv(n, 256), 256, 0, s>>>(n, g, xy, alive, count, slot);
+  launch_scan(count, start, nbins, scan_tmp, s);
+  if (n > 0) {
+    k_binp_scatter<<<cdiv(n, 256), 256, 0, s>>>(n, g, xy, alive, slot, start, key);
+    k_binp_rank<<<cdiv(n, 256), 256, 0, s>>>(n, g, xy, alive, heading, start, key, rec, rec_id);
+  }
+}
+
 __global__ void k_clear_dead(int n, const uint8_t* __restrict__ alive, uint8_t* __restrict__ choice,
                              uint8_t* __restrict__ won) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;

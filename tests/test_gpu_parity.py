@@ -214,6 +214,33 @@ def test_both_gather_footprints_give_the_same_field_and_ticks(name):
         assert e.value.status == sfm.SFM_EINVAL
 
 
+@pytest.mark.parametrize("name", ["room_mixed", "torus", "dense", "tall_r1", "thin_torus",
+                                  "radius41", "no_field"])
+def test_grid_and_pedestrian_list_binning_give_the_same_ticks(name):
+    """Binning by scanning the class grid and binning from the pedestrian
+    list (atomic counts, in-bin rank) produce the same records: fields and
+    ticks are bitwise equal, exits and full bins included."""
+    sc = SCENES[name]()
+    with sfm.Sim(sc) as a, sfm.Sim(sc) as b:
+        a.set_binning("grid")
+        b.set_binning("peds")
+        a.compute_field()
+        b.compute_field()
+        np.testing.assert_array_equal(a.field(), b.field())
+        for t in range(6):
+            a.step(1)
+            b.step(1)
+            np.testing.assert_array_equal(a.field(), b.field(), err_msg=f"tick {t}")
+            np.testing.assert_array_equal(a.decisions()[0], b.decisions()[0])
+            np.testing.assert_array_equal(a.decisions()[1], b.decisions()[1])
+            for x, y in zip(a.peds(), b.peds()):
+                np.testing.assert_array_equal(x, y)
+        assert a.stats()["exited"] == b.stats()["exited"]
+        with pytest.raises(sfm.SfmError) as e:
+            sfm._check(a.ctx, sfm.lib().sfm_set_binning(a.ctx, 3))
+        assert e.value.status == sfm.SFM_EINVAL
+
+
 def test_field_respects_heading_linearity_closed_form():
     """A single pedestrian in an open periodic lattice: the GPU field equals
     the closed form k d^a (1 + gamma cos) to FP32 rounding."""
