@@ -282,10 +282,13 @@ sfm_status sfm_batch_test_missing_ctas(sfm_ctx* ctx, int32_t missing);
 typedef struct sfm_surrogate sfm_surrogate; /* opaque */
 typedef struct sfm_surrogate_cfg {
   int32_t coarsen;     /* s >= 1 */
-  int32_t near_radius; /* rn in [0, r] */
+  int32_t near_radius; /* rn in [0, min(r, 50)] */
   float target_scale;  /* field units per network output unit (> 0) */
   float lr, beta1, beta2, eps; /* Adam */
-  int32_t pad_;
+  float taper_inner;   /* >= 0: the near part's kernel is weighted 1 up to this
+                          Euclidean distance and by a raised cosine down to 0
+                          at rn, leaving a smooth remainder to the network;
+                          >= rn: no taper (hard cut at the Chebyshev window) */
 } sfm_surrogate_cfg;
 int32_t sfm_surrogate_nparams(void);
 sfm_status sfm_surrogate_create(const sfm_surrogate_cfg* cfg, void* stream, sfm_surrogate** out);
@@ -305,12 +308,45 @@ sfm_status sfm_surrogate_grad(sfm_surrogate* sur, int32_t Hin, int32_t Win, cons
 sfm_status sfm_surrogate_train(sfm_surrogate* sur, sfm_ctx* ctx, int32_t iters, float* loss_curve);
 /* surrogate field of ctx's current state into out (W*H floats, host or device) */
 sfm_status sfm_surrogate_field(sfm_surrogate* sur, sfm_ctx* ctx, float* out, int32_t on_device);
-/* On ctx's current state: relative field error sum|F_sur - F| / sum|F - F_static|,
- * the fraction of live pedestrians whose decision changes when taken on
- * F_sur instead of the exact F, and the time of each field (bins included).
- * Overwrites ctx's field and decision buffers. */
-sfm_status sfm_surrogate_eval(sfm_surrogate* sur, sfm_ctx* ctx, double* field_rel_err,
-                              double* flip_rate, double* ms_surrogate, double* ms_exact);
+/* Decisions with the exact field as fallback.  A tick of sfm_surrogate_step
+ * decides every live pedestrian on F_sur; a pedestrian whose energy margin
+ * (second-best minus best candidate) is at most delta (plus a rounding
+ * allowance) is decided again on the exact field at its admissible
+ * candidates, computed bit for bit as the exact gather computes it.  If
+ * F_sur - F varies by less than the margin over a pedestrian's admissible
+ * candidates (max - min), its move equals the exact path's: an error common
+ * to all candidates cancels.  delta starts at +infinity (every pedestrian
+ * falls back: exact moves, no speed-up).
+ * sfm_surrogate_set_delta: delta >= 0 (or +inf) by hand.
+ * sfm_surrogate_calibrate: on ctx's current state, delta = the `quantile`
+ *   (in [0, 1]) over live pedestrians of the spread max - min of F_sur - F
+ *   over their admissible candidates; *delta_out (may be NULL) receives it.
+ *   Overwrites ctx's field buffer.
+ * sfm_surrogate_step: nsteps ticks of ctx (clear, bins, surrogate field,
+ *   decisions with the fallback, vote, commit), asynchronous on ctx's stream.
+ *   Field radius <= 50 (the exact fallback reuses the class-table gather).
+ * sfm_surrogate_counts: totals over all surrogate ticks so far of the
+ *   pedestrians that fell back and of those decided (synchronising). */
+sfm_status sfm_surrogate_set_delta(sfm_surrogate* sur, float delta);
+sfm_status sfm_surrogate_calibrate(sfm_surrogate* sur, sfm_ctx* ctx, double quantile,
+                                   float* delta_out);
+sfm_status sfm_surrogate_step(sfm_surrogate* sur, sfm_ctx* ctx, int32_t nsteps);
+sfm_status sfm_surrogate_counts(sfm_surrogate* sur, int64_t* fallbacks, int64_t* decided);
+/* sfm_surrogate_eval, on ctx's current state (overwrites ctx's field and
+ * decision buffers):
+ *   field_rel_err  sum|F_sur - F| / sum|F - F_static| over the lattice;
+ *   flip_rate      fraction of live pedestrians whose surrogate decision,
+ *                  with the fallback, differs from the exact path's;
+ *   flip_rate_raw  the same without the fallback (decisions on F_sur alone);
+ *   fallback_rate  fraction that fell back;
+ *   ms_surrogate   bins + surrogate field + decisions with the fallback;
+ *   ms_exact       bins + exact field + decisions (CUDA events, ctx stream). */
+typedef struct sfm_surrogate_report {
+  double field_rel_err, flip_rate, flip_rate_raw, fallback_rate, ms_surrogate, ms_exact;
+  float delta;
+  int32_t decided;
+} sfm_surrogate_report;
+sfm_status sfm_surrogate_eval(sfm_surrogate* sur, sfm_ctx* ctx, sfm_surrogate_report* report);
 
 /* ---- Field superposition that allocates nothing ------------------------
  * The paper has no counterpart of this entry point: it serves callers that

@@ -12,8 +12,9 @@ with "valid" cross-correlations, conv(X; W)[o, y, x] = sum_{c, i, j}
 W[o, c, i, j] X[c, y + i, x + j], and the loss L = 0.5 * mean((Y - T)^2).
 Inputs X are per coarse cell of s x s su: [number of pedestrians, sum of
 heading x, sum of heading y] / s^2.  Targets T are the cell averages of the
-exact field minus its near part (contributions within Chebyshev radius rn),
-divided by a fixed scale.  Predictions are returned to su by bilinear
+exact field minus its near part (contributions within Chebyshev radius rn,
+optionally tapered to zero between Euclidean distances r_in and rn so that
+what is left to the network is smooth), divided by a fixed scale.  Predictions are returned to su by bilinear
 interpolation between coarse cell centres.
 
 Plain NumPy: every convolution is a sum over kernel offsets of channel
@@ -87,6 +88,55 @@ def loss_and_grad(params, X, T):
         grads[li] = (dW, db)
         dA = dAin
     return L, grads
+
+
+def taper_weight(d, r_in, rn):
+    """Weight of the near part at Euclidean distance d: 1 up to r_in, a raised
+    cosine down to 0 at rn, 0 beyond; no taper (1 on the whole Chebyshev
+    window) when r_in >= rn."""
+    if r_in >= rn:
+        return 1.0
+    if d <= r_in:
+        return 1.0
+    if d >= rn:
+        return 0.0
+    return 0.5 * (1.0 + np.cos(np.pi * (d - r_in) / (rn - r_in)))
+
+
+def tapered_near_field(W, H, xy, heading, rn, r_in, kP, aP, gamma, periodic_x=0, periodic_y=0,
+                       alive=None):
+    """[H, W]: sum over pedestrians of w(|delta|) K_P(delta; h) over the
+    Chebyshev window 0 < |delta|_inf <= rn, delta = su - pedestrian, with
+    K_P(delta; h) = kP d^aP (1 + gamma h.delta / d) (h the unit heading, zero
+    for heading 0) and w = taper_weight.  Out-of-lattice su are dropped, or
+    wrapped in periodic dimensions."""
+    from math import hypot, sqrt
+    dirs = [(0, 0), (1, 0), (1, 1), (0, 1), (-1, 1), (-1, 0), (-1, -1), (0, -1), (1, -1)]
+    F = np.zeros((H, W))
+    for i in range(len(xy)):
+        if alive is not None and not alive[i]:
+            continue
+        px, py = int(xy[i][0]), int(xy[i][1])
+        hdx, hdy = dirs[int(heading[i])]
+        n = sqrt(hdx * hdx + hdy * hdy)
+        hx, hy = (hdx / n, hdy / n) if n else (0.0, 0.0)
+        for dy in range(-rn, rn + 1):
+            for dx in range(-rn, rn + 1):
+                if dx == 0 and dy == 0:
+                    continue
+                x, y = px + dx, py + dy
+                if periodic_x:
+                    x %= W
+                elif not 0 <= x < W:
+                    continue
+                if periodic_y:
+                    y %= H
+                elif not 0 <= y < H:
+                    continue
+                d = hypot(dx, dy)
+                K = kP * d ** aP * (1.0 + gamma * (hx * dx + hy * dy) / d)
+                F[y, x] += taper_weight(d, r_in, rn) * K
+    return F
 
 
 def coarse_channels(W, H, s, xy, heading, alive=None):

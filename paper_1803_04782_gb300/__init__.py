@@ -37,7 +37,8 @@ EXPORTS = [
     "sfm_batch_autotune", "sfm_batch_test_missing_ctas", "sfm_surrogate_nparams",
     "sfm_surrogate_create", "sfm_surrogate_destroy", "sfm_surrogate_last_error",
     "sfm_surrogate_set_params", "sfm_surrogate_get_params", "sfm_surrogate_grad",
-    "sfm_surrogate_train", "sfm_surrogate_field", "sfm_surrogate_eval",
+    "sfm_surrogate_train", "sfm_surrogate_field", "sfm_surrogate_eval", "sfm_surrogate_set_delta",
+    "sfm_surrogate_calibrate", "sfm_surrogate_step", "sfm_surrogate_counts",
 ]
 
 
@@ -72,7 +73,14 @@ class Stats(C.Structure):
 class SurrogateCfg(C.Structure):
     _fields_ = [("coarsen", C.c_int32), ("near_radius", C.c_int32), ("target_scale", C.c_float),
                 ("lr", C.c_float), ("beta1", C.c_float), ("beta2", C.c_float), ("eps", C.c_float),
-                ("pad_", C.c_int32)]
+                ("taper_inner", C.c_float)]
+
+
+class SurrogateReport(C.Structure):
+    _fields_ = [("field_rel_err", C.c_double), ("flip_rate", C.c_double),
+                ("flip_rate_raw", C.c_double), ("fallback_rate", C.c_double),
+                ("ms_surrogate", C.c_double), ("ms_exact", C.c_double), ("delta", C.c_float),
+                ("decided", C.c_int32)]
 
 
 def lib():
@@ -125,7 +133,11 @@ def lib():
             "sfm_surrogate_grad": (C.c_int, [P, I32, I32, P, P, P, P]),
             "sfm_surrogate_train": (C.c_int, [P, P, I32, P]),
             "sfm_surrogate_field": (C.c_int, [P, P, P, I32]),
-            "sfm_surrogate_eval": (C.c_int, [P, P, P, P, P, P]),
+            "sfm_surrogate_eval": (C.c_int, [P, P, C.POINTER(SurrogateReport)]),
+            "sfm_surrogate_set_delta": (C.c_int, [P, C.c_float]),
+            "sfm_surrogate_calibrate": (C.c_int, [P, P, C.c_double, P]),
+            "sfm_surrogate_step": (C.c_int, [P, P, I32]),
+            "sfm_surrogate_counts": (C.c_int, [P, P, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -576,9 +588,10 @@ class Surrogate:
     BF16 convolutional far field on an s-times coarsened grid."""
 
     def __init__(self, coarsen=8, near_radius=3, target_scale=20.0, lr=1e-3, beta1=0.9,
-                 beta2=0.999, eps=1e-8, stream=None, params=None):
+                 beta2=0.999, eps=1e-8, stream=None, params=None, taper_inner=None):
+        ti = float(near_radius) if taper_inner is None else float(taper_inner)
         self.cfg = SurrogateCfg(int(coarsen), int(near_radius), target_scale, lr, beta1, beta2,
-                                eps, 0)
+                                eps, ti)
         out = C.c_void_p()
         st = lib().sfm_surrogate_create(C.byref(self.cfg), _stream_handle(stream), C.byref(out))
         if st != SFM_OK:
@@ -639,10 +652,30 @@ class Surrogate:
         return out
 
     def eval(self, sim):
-        v = [C.c_double() for _ in range(4)]
-        _scheck(self.h, lib().sfm_surrogate_eval(self.h, sim.ctx, *[C.byref(x) for x in v]))
-        return {"field_rel_err": v[0].value, "flip_rate": v[1].value,
-                "ms_surrogate": v[2].value, "ms_exact": v[3].value}
+        """Surrogate against the exact path on sim's current state (see
+        sfm_surrogate_eval): field error, flip rates with and without the
+        exact fallback, fallback rate, the time of each and delta."""
+        r = SurrogateReport()
+        _scheck(self.h, lib().sfm_surrogate_eval(self.h, sim.ctx, C.byref(r)))
+        return {k: getattr(r, k) for k, _ in SurrogateReport._fields_}
+
+    def set_delta(self, delta):
+        _scheck(self.h, lib().sfm_surrogate_set_delta(self.h, float(delta)))
+
+    def calibrate(self, sim, quantile=0.999):
+        """Set delta to a quantile of the per-pedestrian candidate field error."""
+        d = C.c_float()
+        _scheck(self.h, lib().sfm_surrogate_calibrate(self.h, sim.ctx, float(quantile), C.byref(d)))
+        return float(d.value)
+
+    def step(self, sim, nsteps=1):
+        """nsteps ticks of sim with the surrogate field and the exact fallback."""
+        _scheck(self.h, lib().sfm_surrogate_step(self.h, sim.ctx, int(nsteps)))
+
+    def counts(self):
+        fb, dec = C.c_int64(), C.c_int64()
+        _scheck(self.h, lib().sfm_surrogate_counts(self.h, C.byref(fb), C.byref(dec)))
+        return int(fb.value), int(dec.value)
 
 
 def flatten_params(params):

@@ -183,10 +183,16 @@ __device__ __forceinline__ void add_row_pairs(const float* __restrict__ p, float
     acc[k] = __fadd2_rn(acc[k], make_float2(p[2 * k * S], p[(2 * k + 1) * S]));
 }
 
-template <int SP, int FW, int FH, class Visit>
-__device__ __forceinline__ void walk_footprint(const Geo& g, const int32_t* __restrict__ bin_start,
-                                               const uint32_t* __restrict__ rec, int TS, int2* scr,
-                                               int lane, int x0, int y0, Visit visit) {
+// Visits, in bin-walk order (halo bins row-major, records in bin order), the
+// records within reach (Chebyshev r) of some su of the FW x FH window at
+// (x0, y0): a batch of 32 records is fetched lane-parallel, each lane turns
+// its record (rx, ry relative to (x0, y0), heading class) into an item with
+// make(), the items in reach are compacted into the warp's scratch scr (32
+// int2) and visit() is called on each, in order, by the whole warp.
+template <int FW, int FH, class Make, class Visit>
+__device__ __forceinline__ void walk_records(const Geo& g, const int32_t* __restrict__ bin_start,
+                                             const uint32_t* __restrict__ rec, int2* scr, int lane,
+                                             int x0, int y0, Make make, Visit visit) {
   const int r = g.r;
   const unsigned lt = (1u << lane) - 1u;
   const int xlo = x0 - r, xhi = x0 + FW - 1 + r, ylo = y0 - r, yhi = y0 + FH - 1 + r;
@@ -232,12 +238,7 @@ __device__ __forceinline__ void walk_footprint(const Geo& g, const int32_t* __re
         const int cls = (int)((rc >> 16) & 0xfu);
         // some row of the footprint and some column within the window
         keep = ry >= -r && ry <= FH - 1 + r && rx >= -r && rx <= FW - 1 + r;
-        if (keep) {
-          const int sx = c_csx[cls], sy = c_csy[cls];
-          const int llo = max(0, rx - r), lhi = min(FW - 1, rx + r);
-          item.x = c_ctab[cls] * TS + (r + kFieldPad - sy * ry) * SP + r - sx * rx;
-          item.y = llo | (lhi << 5) | (sx < 0 ? 1024 : 0) | (sy < 0 ? 2048 : 0);
-        }
+        if (keep) item = make(rx, ry, cls);
       }
       const unsigned bal = __ballot_sync(0xffffffffu, keep);
       if (keep) scr[__popc(bal & lt)] = item;
@@ -247,6 +248,21 @@ __device__ __forceinline__ void walk_footprint(const Geo& g, const int32_t* __re
       __syncwarp();
     }
   }
+}
+
+// The footprint gather's walk: items carry the table offset of the
+// pedestrian's class and position, its lane range and mirror flags.
+template <int SP, int FW, int FH, class Visit>
+__device__ __forceinline__ void walk_footprint(const Geo& g, const int32_t* __restrict__ bin_start,
+                                               const uint32_t* __restrict__ rec, int TS, int2* scr,
+                                               int lane, int x0, int y0, Visit visit) {
+  const int r = g.r;
+  walk_records<FW, FH>(g, bin_start, rec, scr, lane, x0, y0, [&](int rx, int ry, int cls) {
+    const int sx = c_csx[cls], sy = c_csy[cls];
+    const int llo = max(0, rx - r), lhi = min(FW - 1, rx + r);
+    return make_int2(c_ctab[cls] * TS + (r + kFieldPad - sy * ry) * SP + r - sx * rx,
+                     llo | (lhi << 5) | (sx < 0 ? 1024 : 0) | (sy < 0 ? 2048 : 0));
+  }, visit);
 }
 
 // Adds the pedestrian field of the 16 x 16 footprint at (x0, y0): lane l owns
@@ -296,12 +312,109 @@ __device__ __forceinline__ void gather_footprint32(const Geo& g, const int32_t* 
   });
 }
 
+// The far part (see FarPart), split into a column part (per lane, once per
+// footprint) and a row part (per row): bilinear weights between the centres
+// of the coarse cells, indices wrapped or clamped.
+struct FarAxis {
+  int i0, i1;  // coarse indices of the two neighbouring centres
+  float t;     // weight of i1
+};
+__device__ __forceinline__ FarAxis far_axis(int v, int s, int n, int periodic) {
+  const float f = (v + 0.5f) / s - 0.5f;
+  int a = (int)floorf(f);
+  FarAxis ax;
+  ax.t = f - a;
+  int b = a + 1;
+  if (periodic) {
+    a = a < 0 ? a + n : (a >= n ? a - n : a);
+    b = b < 0 ? b + n : (b >= n ? b - n : b);
+  } else {
+    a = min(max(a, 0), n - 1);
+    b = min(max(b, 0), n - 1);
+  }
+  ax.i0 = a;
+  ax.i1 = b;
+  return ax;
+}
+__device__ __forceinline__ float far_value(const FarPart& fp, const FarAxis& ay, const FarAxis& ax) {
+  const float* r0 = fp.Y + (size_t)ay.i0 * fp.Wc;
+  const float* r1 = fp.Y + (size_t)ay.i1 * fp.Wc;
+  const float v = (1.f - ay.t) * ((1.f - ax.t) * r0[ax.i0] + ax.t * r0[ax.i1]) +
+                  ay.t * ((1.f - ax.t) * r1[ax.i0] + ax.t * r1[ax.i1]);
+  return fp.scale * v;
+}
+
 // ---------------------------------------------------------------- S3 decide
 // E over the 9 candidates (stay + 8 neighbours), admissible iff inside, not
 // WALL and unoccupied at tick start; the minimum with ties to the smallest
 // class.  F rows: lattice rows [y_lo, y_hi) at buffer row y - y_lo + main_off,
 // lo_row at buffer row 0 and hi_row at hi_off.  own / dirdot: this lattice's
 // 81-entry tables.
+// Admissible candidates (stay, or inside, not WALL and unoccupied at tick
+// start) and the energy E(k) = F(c_k) - K_P(own heading) + guidance; the
+// minimum with ties to the smallest class.  With MARGIN, *margin receives
+// E(second best) - E(best) over the admissible candidates (+inf when only
+// staying is admissible) and *emag (optional) the larger |E| of the two:
+// any field error below margin / 2 at every candidate, less FP32 rounding of
+// energies of that size, leaves the choice unchanged.
+template <bool MARGIN>
+__device__ __forceinline__ int pick_move(const float (&f)[9], const int32_t (&dd)[9],
+                                         const uint8_t (&cl)[9], const uint8_t (&oc)[9],
+                                         const bool (&okx)[3], const bool (&oky)[3], int h, int gl,
+                                         float beta, const float* __restrict__ own,
+                                         const float* __restrict__ dirdot, float* margin,
+                                         float* emag = nullptr) {
+  int best = 0;
+  float bestE = 0.f, second = __int_as_float(0x7f800000);
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    const int xi = move_dx(k) + 1, yi = move_dy(k) + 1;
+    const bool adm = (k == 0) || (okx[xi] && oky[yi] && cl[k] != kWall && oc[k] == 0);
+    const float guide = (gl == 0) ? beta * ((float)(dd[k] - dd[0]) / 5.0f) : -beta * dirdot[gl * 9 + k];
+    const float e = f[k] - own[h * 9 + k] + guide;
+    if (adm && (k == 0 || e < bestE)) {
+      if (MARGIN && k != 0) second = bestE;
+      best = k;
+      bestE = e;
+    } else if (MARGIN && adm && e < second) {
+      second = e;
+    }
+  }
+  if (MARGIN) {
+    *margin = second - bestE;
+    // size of the energies compared, for a rounding allowance
+    if (emag) *emag = fmaxf(fabsf(bestE), second < __int_as_float(0x7f800000) ? fabsf(second) : 0.f);
+  }
+  return best;
+}
+
+// The 3 x 3 neighbourhood of pedestrian p: wrapped or clipped coordinates
+// (an out-of-lattice candidate repeats p's own row or column and is marked
+// inadmissible by okx / oky), and the guidance, cell and occupancy of each
+// candidate.
+__device__ __forceinline__ void candidate_cells(int2 q, const Geo& g, const uint8_t* __restrict__ cell,
+                                                const uint8_t* __restrict__ ocls,
+                                                const int32_t* __restrict__ D, int (&cx)[3],
+                                                int (&ry)[3], bool (&okx)[3], bool (&oky)[3],
+                                                int32_t (&dd)[9], uint8_t (&cl)[9],
+                                                uint8_t (&oc)[9]) {
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    okx[d] = wrap_coord(q.x + d - 1, g.W, g.px, cx[d]);
+    oky[d] = wrap_coord(q.y + d - 1, g.H, g.py, ry[d]);
+    if (!okx[d]) cx[d] = q.x;
+    if (!oky[d]) ry[d] = q.y;
+  }
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    const int xi = move_dx(k) + 1, yi = move_dy(k) + 1;
+    const size_t c = (size_t)ry[yi] * g.W + cx[xi];
+    dd[k] = D[c];
+    cl[k] = cell[c];
+    oc[k] = ocls[(size_t)ry[yi] * g.opitch + cx[xi]];
+  }
+}
+
 __device__ __forceinline__ uint8_t decide_one(
     int p, const Geo& g, const int2* __restrict__ xy, const uint8_t* __restrict__ heading,
     const uint8_t* __restrict__ goal, const uint8_t* __restrict__ cell,
@@ -336,20 +449,7 @@ __device__ __forceinline__ uint8_t decide_one(
     cl[k] = cell[c];
     oc[k] = ocls[(size_t)ry[yi] * g.opitch + cx[xi]];
   }
-  int best = 0;
-  float bestE = 0.f;
-#pragma unroll
-  for (int k = 0; k < 9; ++k) {
-    const int xi = move_dx(k) + 1, yi = move_dy(k) + 1;
-    const bool adm = (k == 0) || (okx[xi] && oky[yi] && cl[k] != kWall && oc[k] == 0);
-    const float guide = (gl == 0) ? beta * ((float)(dd[k] - dd[0]) / 5.0f) : -beta * dirdot[gl * 9 + k];
-    const float e = f[k] - own[h * 9 + k] + guide;
-    if (adm && (k == 0 || e < bestE)) {
-      best = k;
-      bestE = e;
-    }
-  }
-  return (uint8_t)best;
+  return (uint8_t)pick_move<false>(f, dd, cl, oc, okx, oky, h, gl, beta, own, dirdot, nullptr);
 }
 
 // ------------------------------------------------------------------ S4 vote

@@ -87,6 +87,16 @@ struct Geo {
   int opitch;    // row pitch (bytes) of the occupancy-class grid, a multiple of 128
 };
 
+// A far part added by the class-table gather's epilogue (the learned
+// surrogate): F = (Fs + near sum) + scale * Y~, Y~ the bilinear interpolation
+// of an Hc x Wc grid of s x s cells between cell centres (wrapped in periodic
+// dimensions, clamped otherwise).  Y == nullptr: no far part.
+struct FarPart {
+  const float* Y = nullptr;
+  int s = 1, Hc = 0, Wc = 0;
+  float scale = 0.f;
+};
+
 struct Tables {
   const float* T0;      // (2r+1)^2: kP d^aP          (pedestrian, isotropic part)
   const float* TX;      // (2r+1)^2: kP d^aP gamma dx/d
@@ -138,10 +148,13 @@ void launch_clear_dead(int n, const uint8_t* alive, uint8_t* choice, uint8_t* wo
 // the row range, so banded and unbanded passes agree bit for bit.
 void launch_field(const Geo& g, const int32_t* bin_start, const uint32_t* rec, const Tables& tb,
                   const float* Fs, float* out, int out_row0, int store_lo, int store_hi,
-                  Counters* ctr, cudaStream_t s);
+                  Counters* ctr, cudaStream_t s, const FarPart& far = FarPart());
 int class_table_stride(int r);
 size_t class_table_floats(int r);
-void launch_class_tables(int r, const sfm_params& p, float* T, cudaStream_t s);
+// taper_in < r: entries weighted by 1 up to Euclidean distance taper_in and
+// a raised cosine down to 0 at r (the surrogate's near part); default none
+void launch_class_tables(int r, const sfm_params& p, float* T, cudaStream_t s,
+                         double taper_in = 1e30);
 
 // The per-pedestrian stages visit the live pedestrians of bins [b_lo, b_hi)
 // through rec_id (n bounds the launch).  F rows: lattice rows [y_lo, y_hi) at

@@ -650,7 +650,7 @@ static void launch_field_v1(const Geo& g, const int32_t* bin_start, const uint32
 // stride SP lets the 16 reads use immediate offsets.  One CTA of 32 warps per
 // SM loads the tables once for the whole launch.
 
-__global__ void k_class_tables(int r, int SP, double kP, double aP, double gamma,
+__global__ void k_class_tables(int r, int SP, double kP, double aP, double gamma, double taper_in,
                                float* __restrict__ T) {
   const int TR = 2 * r + 1 + 2 * kFieldPad;
   const int n = 4 * TR * SP;
@@ -665,6 +665,10 @@ __global__ void k_class_tables(int r, int SP, double kP, double aP, double gamma
     const double hy = (t == 2) ? 1.0 : (t == 3 ? 0.70710678118654752440 : 0.0);
     const double d = sqrt((double)(dx * dx + dy * dy));
     v = kP * pow(d, aP) * (1.0 + gamma * (hx * dx + hy * dy) / d);
+    // optional taper (surrogate near part): 1 up to taper_in, raised cosine
+    // to 0 at Euclidean distance r
+    if (taper_in < r && d > taper_in)
+      v *= d >= r ? 0.0 : 0.5 * (1.0 + cos(3.14159265358979323846 * (d - taper_in) / (r - taper_in)));
   }
   T[i] = (float)v;
 }
@@ -673,19 +677,19 @@ int class_table_stride(int r) { return class_table_stride_of(r); }
 
 size_t class_table_floats(int r) { return class_table_floats_of(r); }
 
-void launch_class_tables(int r, const sfm_params& p, float* T, cudaStream_t s) {
+void launch_class_tables(int r, const sfm_params& p, float* T, cudaStream_t s, double taper_in) {
   const int sp = class_table_stride(r);
   if (!sp) return;
   const int n = (int)class_table_floats(r);
-  k_class_tables<<<cdiv(n, 256), 256, 0, s>>>(r, sp, p.kP, p.aP, p.gamma, T);
+  k_class_tables<<<cdiv(n, 256), 256, 0, s>>>(r, sp, p.kP, p.aP, p.gamma, taper_in, T);
 }
 
-template <int SP, int SHAPE>
+template <int SP, int SHAPE, bool FAR>
 __global__ void __launch_bounds__(kV2Threads, 1)
     k_field_v2(Geo g, const int32_t* __restrict__ bin_start, const uint32_t* __restrict__ rec,
                const float* __restrict__ CT, const float* __restrict__ Fs,
                float* __restrict__ out, int out_row0, int fy0, int fy1, int store_lo,
-               int store_hi) {
+               int store_hi, FarPart far) {
   extern __shared__ __align__(16) float sm[];
   constexpr int FW = SHAPE ? 32 : 16, FH = 16, NJ = SHAPE ? 16 : 8;
   const int r = g.r;
@@ -709,6 +713,8 @@ __global__ void __launch_bounds__(kV2Threads, 1)
   const int x = SHAPE ? lane : (lane & 15), yl = SHAPE ? 0 : (lane >> 4) * 8;
   for (int f = blockIdx.x * wpb + warp; f < nf; f += tw) {
     const int x0 = (f % nfx) * FW, y0 = (fy0 + f / nfx) * FH;
+    FarAxis fax{};
+    if constexpr (FAR) fax = far_axis(x0 + x, far.s, far.Wc, g.px);
     float2 acc[NJ / 2];
 #pragma unroll
     for (int j = 0; j < NJ / 2; ++j) acc[j] = make_float2(0.f, 0.f);
@@ -721,7 +727,9 @@ __global__ void __launch_bounds__(kV2Threads, 1)
       const int y = y0 + yl + j, xx = x0 + x;
       if (xx < g.W && y < g.H && y >= store_lo && y < store_hi) {
         const size_t c = (size_t)y * g.W + xx;
-        out[(size_t)(y - out_row0) * g.W + xx] = Fs[c] + ((j & 1) ? acc[j >> 1].y : acc[j >> 1].x);
+        float v = Fs[c] + ((j & 1) ? acc[j >> 1].y : acc[j >> 1].x);
+        if constexpr (FAR) v += far_value(far, far_axis(y, far.s, far.Hc, g.py), fax);
+        out[(size_t)(y - out_row0) * g.W + xx] = v;
       }
     }
   }
@@ -729,14 +737,14 @@ __global__ void __launch_bounds__(kV2Threads, 1)
 
 static int g_num_sms = 0;
 
-template <int SP, int SHAPE>
+template <int SP, int SHAPE, bool FAR>
 static void launch_v2(const Geo& g, const int32_t* bin_start, const uint32_t* rec, const float* CT,
                       const float* Fs, float* out, int out_row0, int store_lo, int store_hi,
-                      cudaStream_t s) {
+                      cudaStream_t s, const FarPart& far) {
   constexpr int FW = SHAPE ? 32 : 16, FH = 16;
   const size_t smem = (kTableGuard + class_table_floats(g.r)) * sizeof(float) +
                       kV2Threads / 32 * 32 * sizeof(int2);
-  cudaFuncSetAttribute(k_field_v2<SP, SHAPE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaFuncSetAttribute(k_field_v2<SP, SHAPE, FAR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (!g_num_sms) {
     int dev = 0;
     cudaGetDevice(&dev);
@@ -749,23 +757,27 @@ static void launch_v2(const Geo& g, const int32_t* bin_start, const uint32_t* re
   int blocks = (nf + wpb - 1) / wpb;
   if (blocks > g_num_sms) blocks = g_num_sms;
   if (blocks < 1) blocks = 1;
-  k_field_v2<SP, SHAPE><<<blocks, kV2Threads, smem, s>>>(g, bin_start, rec, CT, Fs, out, out_row0,
-                                                         fy0, fy1, store_lo, store_hi);
+  k_field_v2<SP, SHAPE, FAR><<<blocks, kV2Threads, smem, s>>>(g, bin_start, rec, CT, Fs, out, out_row0,
+                                                         fy0, fy1, store_lo, store_hi, far);
 }
 
 template <int SP>
 static void launch_v2_shape(const Geo& g, const int32_t* bin_start, const uint32_t* rec,
                             const Tables& tb, const float* Fs, float* out, int out_row0,
-                            int store_lo, int store_hi, cudaStream_t s) {
-  if (tb.shape)
-    launch_v2<SP, 1>(g, bin_start, rec, tb.CT, Fs, out, out_row0, store_lo, store_hi, s);
+                            int store_lo, int store_hi, cudaStream_t s, const FarPart& far) {
+  // the far part (surrogate) has its own instantiation, 32 x 16 footprint only,
+  // so the exact gather carries no code for it
+  if (far.Y)
+    launch_v2<SP, 1, true>(g, bin_start, rec, tb.CT, Fs, out, out_row0, store_lo, store_hi, s, far);
+  else if (tb.shape)
+    launch_v2<SP, 1, false>(g, bin_start, rec, tb.CT, Fs, out, out_row0, store_lo, store_hi, s, far);
   else
-    launch_v2<SP, 0>(g, bin_start, rec, tb.CT, Fs, out, out_row0, store_lo, store_hi, s);
+    launch_v2<SP, 0, false>(g, bin_start, rec, tb.CT, Fs, out, out_row0, store_lo, store_hi, s, far);
 }
 
 void launch_field(const Geo& g, const int32_t* bin_start, const uint32_t* rec, const Tables& tb,
                   const float* Fs, float* out, int out_row0, int store_lo, int store_hi,
-                  Counters* ctr, cudaStream_t s) {
+                  Counters* ctr, cudaStream_t s, const FarPart& far) {
   if (store_hi <= store_lo) return;
   const int sp = tb.CT ? class_table_stride(g.r) : 0;
   if (!sp) {
@@ -773,13 +785,13 @@ void launch_field(const Geo& g, const int32_t* bin_start, const uint32_t* rec, c
     return;
   }
   switch (sp) {
-    case 34: launch_v2_shape<34>(g, bin_start, rec, tb, Fs, out, out_row0, store_lo, store_hi, s); break;
-    case 50: launch_v2_shape<50>(g, bin_start, rec, tb, Fs, out, out_row0, store_lo, store_hi, s); break;
-    case 66: launch_v2_shape<66>(g, bin_start, rec, tb, Fs, out, out_row0, store_lo, store_hi, s); break;
-    case 82: launch_v2_shape<82>(g, bin_start, rec, tb, Fs, out, out_row0, store_lo, store_hi, s); break;
-    case 98: launch_v2_shape<98>(g, bin_start, rec, tb, Fs, out, out_row0, store_lo, store_hi, s); break;
-    case 114: launch_v2_shape<114>(g, bin_start, rec, tb, Fs, out, out_row0, store_lo, store_hi, s); break;
-    default: launch_v2_shape<kNarrowStride>(g, bin_start, rec, tb, Fs, out, out_row0, store_lo, store_hi, s); break;
+    case 34: launch_v2_shape<34>(g, bin_start, rec, tb, Fs, out, out_row0, store_lo, store_hi, s, far); break;
+    case 50: launch_v2_shape<50>(g, bin_start, rec, tb, Fs, out, out_row0, store_lo, store_hi, s, far); break;
+    case 66: launch_v2_shape<66>(g, bin_start, rec, tb, Fs, out, out_row0, store_lo, store_hi, s, far); break;
+    case 82: launch_v2_shape<82>(g, bin_start, rec, tb, Fs, out, out_row0, store_lo, store_hi, s, far); break;
+    case 98: launch_v2_shape<98>(g, bin_start, rec, tb, Fs, out, out_row0, store_lo, store_hi, s, far); break;
+    case 114: launch_v2_shape<114>(g, bin_start, rec, tb, Fs, out, out_row0, store_lo, store_hi, s, far); break;
+    default: launch_v2_shape<kNarrowStride>(g, bin_start, rec, tb, Fs, out, out_row0, store_lo, store_hi, s, far); break;
   }
 }
 

@@ -12,6 +12,7 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <algorithm>
 #include <string>
 #include <vector>
 
@@ -202,6 +203,144 @@ __global__ void k_pack_w3(const float* __restrict__ w, bf16* __restrict__ wt) {
   if (i >= 9 * 32 * 32) return;
   const int c = i % 32, o = (i / 32) % 32, kk = i / 1024;
   wt[i] = __float2bfloat16(w[(kk * 32 + c) * 32 + o]);
+}
+
+// ------------------------------------------- tensor-core 5x5, 3 -> 32
+// Layer 1 as an implicit GEMM with K = 75 (ky, kx, c) padded to 80: the CTA
+// stages its 12 x 20-pixel input tile, expands it to a [128 pixel][80] BF16
+// matrix in shared memory (rows padded to 88 elements, 176 bytes, so the
+// ldmatrix row fetches hit distinct banks) and runs 5 k16 steps of
+// m16n8k16 per m16 tile; layout of warps and fragments as k_conv3_tc.
+constexpr int kC1K = 80, kC1Pad = 88;
+static_assert(kTcCols + 4 == 20, "c_im2col assumes 20-pixel input rows");
+// input-tile offset of K entry k = (ky*5 + kx)*3 + c: (ky*20 + kx)*3 + c
+__constant__ int c_im2col[80] = {
+#define C1ROW(ky) (ky * 20 + 0) * 3, (ky * 20 + 0) * 3 + 1, (ky * 20 + 0) * 3 + 2, \
+                  (ky * 20 + 1) * 3, (ky * 20 + 1) * 3 + 1, (ky * 20 + 1) * 3 + 2, \
+                  (ky * 20 + 2) * 3, (ky * 20 + 2) * 3 + 1, (ky * 20 + 2) * 3 + 2, \
+                  (ky * 20 + 3) * 3, (ky * 20 + 3) * 3 + 1, (ky * 20 + 3) * 3 + 2, \
+                  (ky * 20 + 4) * 3, (ky * 20 + 4) * 3 + 1, (ky * 20 + 4) * 3 + 2
+    C1ROW(0), C1ROW(1), C1ROW(2), C1ROW(3), C1ROW(4), 0, 0, 0, 0, 0
+#undef C1ROW
+};
+
+__global__ void __launch_bounds__(128)
+    k_conv1_tc(const bf16* __restrict__ in, int Hin, int Win, const bf16* __restrict__ Wt,
+               const float* __restrict__ b, bf16* __restrict__ out) {
+  constexpr int TH = kTcRows + 4, TW = kTcCols + 4;
+  __shared__ __align__(16) bf16 sX[TH * TW * 3];
+  __shared__ __align__(16) bf16 sA[kTcRows * kTcCols * kC1Pad];
+  __shared__ __align__(16) bf16 sW[32 * kC1Pad];
+  const int Hout = Hin - 4, Wout = Win - 4;
+  const int x0 = blockIdx.x * kTcCols, y0 = blockIdx.y * kTcRows;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int i = tid; i < 32 * kC1K; i += blockDim.x) sW[(i / kC1K) * kC1Pad + i % kC1K] = Wt[i];
+  for (int i = tid; i < TH * TW * 3; i += blockDim.x) {
+    const int c = i % 3, p = i / 3, px = p % TW, py = p / TW;
+    const int gy = y0 + py, gx = x0 + px;
+    sX[i] = (gy < Hin && gx < Win) ? in[((size_t)gy * Win + gx) * 3 + c] : __float2bfloat16(0.f);
+  }
+  __syncthreads();
+  {
+    // thread = output pixel of the tile (128 of them): its row of the
+    // im2col matrix, two K entries per 4-byte store
+    const int p = tid, base = ((p / kTcCols) * TW + p % kTcCols) * 3;
+    __nv_bfloat162* row = reinterpret_cast<__nv_bfloat162*>(sA + p * kC1Pad);
+#pragma unroll 8
+    for (int k = 0; k < kC1K; k += 2) {
+      const bf16 z = __float2bfloat16(0.f);
+      const bf16 a = k < 75 ? sX[base + c_im2col[k]] : z;
+      const bf16 b = k + 1 < 75 ? sX[base + c_im2col[k + 1]] : z;
+      row[k / 2] = __halves2bfloat162(a, b);
+    }
+  }
+  __syncthreads();
+  float acc[2][4][4];
+#pragma unroll
+  for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+    for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) acc[mt][nt][k] = 0.f;
+  const uint32_t sA0 = (uint32_t)__cvta_generic_to_shared(sA);
+  const uint32_t sW0 = (uint32_t)__cvta_generic_to_shared(sW);
+  const int a_row = (lane & 7) + 8 * ((lane >> 3) & 1), a_col = 8 * (lane >> 4);
+  const int b_n = (lane & 7) + 8 * (lane >> 4), b_k = 8 * ((lane >> 3) & 1);
+#pragma unroll
+  for (int kb = 0; kb < kC1K / 16; ++kb) {
+    uint32_t bw[4][2];
+#pragma unroll
+    for (int np = 0; np < 2; ++np)
+      ldsm_x4(sW0 + (uint32_t)(((np * 16 + b_n) * kC1Pad + kb * 16 + b_k) * 2), bw[2 * np][0],
+              bw[2 * np][1], bw[2 * np + 1][0], bw[2 * np + 1][1]);
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt) {
+      const int prow = (2 * warp + mt) * kTcCols + a_row;
+      uint32_t a0, a1, a2, a3;
+      ldsm_x4(sA0 + (uint32_t)((prow * kC1Pad + kb * 16 + a_col) * 2), a0, a1, a2, a3);
+#pragma unroll
+      for (int nt = 0; nt < 4; ++nt) mma_bf16(acc[mt][nt], a0, a1, a2, a3, bw[nt][0], bw[nt][1]);
+    }
+  }
+  const int g = lane >> 2, cp = 2 * (lane & 3);
+#pragma unroll
+  for (int mt = 0; mt < 2; ++mt) {
+    const int y = y0 + 2 * warp + mt;
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+      const int x = x0 + g + 8 * half;
+      if (y >= Hout || x >= Wout) continue;
+      __nv_bfloat162* o = reinterpret_cast<__nv_bfloat162*>(out + ((size_t)y * Wout + x) * 32);
+#pragma unroll
+      for (int nt = 0; nt < 4; ++nt) {
+        const int c = nt * 8 + cp;
+        const float v0 = fmaxf(acc[mt][nt][2 * half] + b[c], 0.f);
+        const float v1 = fmaxf(acc[mt][nt][2 * half + 1] + b[c + 1], 0.f);
+        o[c / 2] = __floats2bfloat162_rn(v0, v1);
+      }
+    }
+  }
+}
+
+// BF16 layer-1 weights [out][80] (k = (ky*5 + kx)*3 + c, zero beyond 75)
+// from the internal [ky][kx][in][out] floats.
+__global__ void k_pack_w1(const float* __restrict__ w, bf16* __restrict__ wt) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 32 * kC1K) return;
+  const int o = i / kC1K, k = i % kC1K;
+  wt[i] = __float2bfloat16(k < 75 ? w[k * 32 + o] : 0.f);
+}
+
+// Layer 4 (3x3, 32 -> 1, no activation): one output pixel per thread, the
+// 9 x 32 inputs as 16-byte loads, FP32 sums in the order (ky, kx, c).
+__global__ void __launch_bounds__(256)
+    k_conv_last(const bf16* __restrict__ in, int Hin, int Win, const float* __restrict__ Wt,
+                const float* __restrict__ b, float* __restrict__ out) {
+  __shared__ float sW[9 * 32];
+  for (int i = threadIdx.x; i < 9 * 32; i += blockDim.x) sW[i] = Wt[i];
+  __syncthreads();
+  const int Hout = Hin - 2, Wout = Win - 2;
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= Hout * Wout) return;
+  const int y = idx / Wout, x = idx % Wout;
+  float acc = b[0];
+#pragma unroll
+  for (int kk = 0; kk < 9; ++kk) {
+    const uint4* px =
+        reinterpret_cast<const uint4*>(in + ((size_t)(y + kk / 3) * Win + (x + kk % 3)) * 32);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const uint4 v = px[q];
+      const uint32_t w4[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w4[e]));
+        acc = fmaf(f.x, sW[kk * 32 + q * 8 + 2 * e], acc);
+        acc = fmaf(f.y, sW[kk * 32 + q * 8 + 2 * e + 1], acc);
+      }
+    }
+  }
+  out[idx] = acc;
 }
 
 // -------------------------------------------------------------- backward
@@ -402,28 +541,6 @@ __global__ void k_targets(const float* __restrict__ F, const float* __restrict__
   T[idx] = (float)(acc / (s * s)) * inv_scale;
 }
 
-// out = Fnear + scale * bilinear(Y) between coarse cell centres.
-__global__ void k_combine(Geo g, const float* __restrict__ Fnear, const float* __restrict__ Y,
-                          int s, int Hc, int Wc, float scale, float* __restrict__ out) {
-  const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-  if (i >= (size_t)g.W * g.H) return;
-  const int y = (int)(i / g.W), x = (int)(i % g.W);
-  const float fy = (y + 0.5f) / s - 0.5f, fx = (x + 0.5f) / s - 0.5f;
-  const int y0 = (int)floorf(fy), x0 = (int)floorf(fx);
-  const float ty = fy - y0, tx = fx - x0;
-  float v = 0.f;
-#pragma unroll
-  for (int a = 0; a < 2; ++a)
-#pragma unroll
-    for (int b = 0; b < 2; ++b) {
-      int yy = y0 + a, xx = x0 + b;
-      if (g.py) yy = (yy + Hc) % Hc; else yy = min(max(yy, 0), Hc - 1);
-      if (g.px) xx = (xx + Wc) % Wc; else xx = min(max(xx, 0), Wc - 1);
-      v += (a ? ty : 1.f - ty) * (b ? tx : 1.f - tx) * Y[(size_t)yy * Wc + xx];
-    }
-  out[i] = Fnear[i] + scale * v;
-}
-
 // number of pedestrians (live, in bin order) whose two decisions differ;
 // sums of |Fa - Fb| and |Fb - Fs| over the lattice (FP64 partials per CTA)
 __global__ void k_diff_choices(const int32_t* __restrict__ rec_id, const int32_t* __restrict__ bin_start,
@@ -464,6 +581,158 @@ __global__ void k_field_err(const float* __restrict__ Fa, const float* __restric
   }
 }
 
+// ------------------------------------- decisions with an exact fallback
+// Decisions on the surrogate field F_sur; a pedestrian whose energy margin
+// (second best - best) is not above delta plus a rounding allowance joins
+// the fallback list and is decided again on the exact field at its
+// candidates.  If the error F_sur - F varies by less than the margin over a
+// pedestrian's admissible candidates, every other candidate's exact energy
+// stays strictly above the surrogate's choice, so the choice is the exact
+// one (ties included).  ref / raw_flips (optional): count decisions that differ from
+// ref before the fallback.
+__device__ __forceinline__ float margin_allowance(float delta, float emag, float fmag) {
+  return delta * 1.0001f + 1e-6f * (emag + fmag);
+}
+
+__global__ void k_sur_decide(const int32_t* __restrict__ rec_id, const int32_t* __restrict__ bin_start,
+                             int nbins, Geo g, const int2* __restrict__ xy,
+                             const uint8_t* __restrict__ heading, const uint8_t* __restrict__ goal,
+                             const uint8_t* __restrict__ cell, const uint8_t* __restrict__ ocls,
+                             const int32_t* __restrict__ D, const float* __restrict__ Fsur,
+                             float beta, const float* __restrict__ own,
+                             const float* __restrict__ dirdot, float delta,
+                             uint8_t* __restrict__ choice, int32_t* __restrict__ flag_list,
+                             int32_t* __restrict__ nflag, const uint8_t* __restrict__ ref,
+                             unsigned long long* __restrict__ raw_flips) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  bool differs = false;
+  if (i < bin_start[nbins]) {
+    const int p = rec_id[i];
+    const int2 q = xy[p];
+    int cx[3], ry[3];
+    bool okx[3], oky[3];
+    int32_t dd[9];
+    uint8_t cl[9], oc[9];
+    candidate_cells(q, g, cell, ocls, D, cx, ry, okx, oky, dd, cl, oc);
+    float f[9], fmag = 0.f;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      f[k] = Fsur[(size_t)ry[move_dy(k) + 1] * g.W + cx[move_dx(k) + 1]];
+      fmag = fmaxf(fmag, fabsf(f[k]));
+    }
+    float margin, emag;
+    const int best = pick_move<true>(f, dd, cl, oc, okx, oky, heading[p], goal[p], beta, own,
+                                     dirdot, &margin, &emag);
+    choice[p] = (uint8_t)best;
+    if (!(margin > margin_allowance(delta, emag, fmag))) flag_list[atomicAdd(nflag, 1)] = p;
+    differs = ref && ref[p] != best;
+  }
+  if (raw_flips) {
+    const unsigned nd = __popc(__ballot_sync(0xffffffffu, differs));
+    if ((threadIdx.x & 31) == 0 && nd) atomicAdd(raw_flips, (unsigned long long)nd);
+  }
+}
+
+// Exact field at the 9 candidates of each listed pedestrian: one warp per
+// pedestrian walks, once, the records in reach of its 3 x 3 candidate block
+// (the walk of a 3 x 3 footprint) and lane k < 9 adds, in walk order, the
+// class-table entry of every record that reaches candidate k: the sums of
+// the exact gather, bit for bit (its other terms are zero pads).  The class
+// tables are staged in shared memory as for the gather (one CTA of 32 warps
+// per SM).  Values of candidates outside the lattice are never read.
+constexpr int kFbThreads = 1024;
+
+__global__ void __launch_bounds__(kFbThreads, 1)
+    k_sur_fallback(const int32_t* __restrict__ flag_list, const int32_t* __restrict__ nflag, Geo g,
+                   const int2* __restrict__ xy, const int32_t* __restrict__ bin_start,
+                   const uint32_t* __restrict__ rec, const float* __restrict__ CT, int SP, int TS,
+                   const float* __restrict__ Fs, float* __restrict__ fex) {
+  extern __shared__ __align__(16) float sm[];
+  float* sT = sm + kTableGuard;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  int2* scr = reinterpret_cast<int2*>(sT + 4 * TS) + w * 32;
+  for (int i = threadIdx.x; i < 4 * TS; i += blockDim.x) sT[i] = CT[i];
+  __syncthreads();
+  const int n = *nflag, r = g.r;
+  const int k = lane < 9 ? lane : 0;
+  const int cdx = move_dx(k) + 1, cdy = move_dy(k) + 1;  // candidate in the 3 x 3 block
+  for (int j = blockIdx.x * nw + w; j < n; j += gridDim.x * nw) {
+    const int2 q = xy[flag_list[j]];
+    float acc = 0.f;
+    walk_records<3, 3>(
+        g, bin_start, rec, scr, lane, q.x - 1, q.y - 1,
+        [](int rx, int ry, int cls) { return make_int2(rx, ry * 16 + cls); },
+        [&](const int2 it) {
+          const int cls = it.y & 15, dx = cdx - it.x, dy = cdy - (it.y >> 4);
+          if (lane < 9 && dx >= -r && dx <= r && dy >= -r && dy <= r)
+            acc += sT[c_ctab[cls] * TS + (r + kFieldPad + c_csy[cls] * dy) * SP + r + c_csx[cls] * dx];
+        });
+    if (lane < 9) {
+      int tx, ty;
+      const bool ok = wrap_coord(q.x + move_dx(k), g.W, g.px, tx) &
+                      wrap_coord(q.y + move_dy(k), g.H, g.py, ty);
+      fex[(size_t)j * 9 + lane] = ok ? Fs[(size_t)ty * g.W + tx] + acc : 0.f;
+    }
+  }
+}
+
+__global__ void k_sur_redecide(const int32_t* __restrict__ flag_list, const int32_t* __restrict__ nflag,
+                               Geo g, const int2* __restrict__ xy,
+                               const uint8_t* __restrict__ heading, const uint8_t* __restrict__ goal,
+                               const uint8_t* __restrict__ cell, const uint8_t* __restrict__ ocls,
+                               const int32_t* __restrict__ D, const float* __restrict__ fex,
+                               float beta, const float* __restrict__ own,
+                               const float* __restrict__ dirdot, uint8_t* __restrict__ choice) {
+  const int n = *nflag;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+    const int p = flag_list[j];
+    int cx[3], ry[3];
+    bool okx[3], oky[3];
+    int32_t dd[9];
+    uint8_t cl[9], oc[9];
+    candidate_cells(xy[p], g, cell, ocls, D, cx, ry, okx, oky, dd, cl, oc);
+    float f[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) f[k] = fex[(size_t)j * 9 + k];
+    choice[p] = (uint8_t)pick_move<false>(f, dd, cl, oc, okx, oky, heading[p], goal[p], beta, own,
+                                          dirdot, nullptr);
+  }
+}
+
+// running totals of listed and decided pedestrians over surrogate ticks
+__global__ void k_count_fallbacks(const int32_t* __restrict__ nflag, const int32_t* __restrict__ nrec,
+                                  unsigned long long* __restrict__ tot) {
+  tot[0] += (unsigned long long)*nflag;
+  tot[1] += (unsigned long long)*nrec;
+}
+
+// per pedestrian (bin order): the spread max - min of Fa - Fb over its
+// admissible candidates, the part of the field error a decision margin has
+// to absorb (an error common to all candidates cancels)
+__global__ void k_sur_err(const int32_t* __restrict__ rec_id, const int32_t* __restrict__ bin_start,
+                          int nbins, Geo g, const int2* __restrict__ xy,
+                          const uint8_t* __restrict__ cell, const uint8_t* __restrict__ ocls,
+                          const float* __restrict__ Fa, const float* __restrict__ Fb,
+                          float* __restrict__ err) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= bin_start[nbins]) return;
+  const int2 q = xy[rec_id[i]];
+  float lo = __int_as_float(0x7f800000), hi = -lo;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    int tx, ty;
+    const bool ok = wrap_coord(q.x + move_dx(k), g.W, g.px, tx) &
+                    wrap_coord(q.y + move_dy(k), g.H, g.py, ty);
+    if (ok && (k == 0 || (cell[(size_t)ty * g.W + tx] != kWall && ocls[(size_t)ty * g.opitch + tx] == 0))) {
+      const size_t c = (size_t)ty * g.W + tx;
+      const float d = Fa[c] - Fb[c];
+      lo = fminf(lo, d);
+      hi = fmaxf(hi, d);
+    }
+  }
+  err[i] = hi - lo;
+}
+
 inline int cdiv(int a, int b) { return (a + b - 1) / b; }
 
 }  // namespace
@@ -475,7 +744,7 @@ struct sfm_surrogate {
   std::string err;
   // parameters (internal layout), BF16-rounded copies, Adam state, gradients
   float *p = nullptr, *pq = nullptr, *m = nullptr, *v = nullptr, *g = nullptr;
-  bf16 *wt2 = nullptr, *wt3 = nullptr;  // layers 2 and 3 packed for the tensor-core kernel
+  bf16 *wt1 = nullptr, *wt2 = nullptr, *wt3 = nullptr;  // packed for the tensor-core kernels
   int adam_t = 0;
   // activations for an image of (Hc + 2 kHalo) x (Wc + 2 kHalo) coarse cells
   int Hc = 0, Wc = 0;
@@ -492,6 +761,15 @@ struct sfm_surrogate {
   int near_r_built = -1;
   double* red = nullptr;
   unsigned long long* cnt = nullptr;
+  // decisions with the exact fallback
+  float delta = __builtin_inff();  // field error bound behind the margin test
+  float* fex = nullptr;            // exact field at the candidates of listed pedestrians
+  int32_t* flag_list = nullptr;
+  int32_t* nflag = nullptr;
+  float* perr = nullptr;           // per-pedestrian candidate error (calibration)
+  int fb_cap = 0;
+  long long fallbacks = 0, decided = 0;  // totals over surrogate ticks (host copies)
+  unsigned long long* fb_dev = nullptr;  // [0] listed, [1] decided, summed on the device
   std::vector<void*> allocs;
 };
 
@@ -625,10 +903,14 @@ void conv3_tc(const bf16* in, int Hin, int Win, const bf16* wt, const float* b, 
 void forward(sfm_surrogate* S, cudaStream_t s) {
   const int Hp = S->Hc + 2 * kHalo, Wp = S->Wc + 2 * kHalo;
   const float* q = S->pq;
-  conv_fwd<3, 32, 5, true>(S->X, Hp, Wp, q + kOffW[0], q + kOffB[0], S->A1, nullptr, s);
+  {
+    dim3 grid(cdiv(Wp - 4, kTcCols), cdiv(Hp - 4, kTcRows));
+    k_conv1_tc<<<grid, 128, 0, s>>>(S->X, Hp, Wp, S->wt1, q + kOffB[0], S->A1);
+  }
   conv3_tc(S->A1, Hp - 4, Wp - 4, S->wt2, q + kOffB[1], S->A2, s);
   conv3_tc(S->A2, Hp - 6, Wp - 6, S->wt3, q + kOffB[2], S->A3, s);
-  conv_fwd<32, 1, 3, false>(S->A3, Hp - 8, Wp - 8, q + kOffW[3], q + kOffB[3], nullptr, S->Y, s);
+  k_conv_last<<<cdiv(S->Hc * S->Wc, 256), 256, 0, s>>>(S->A3, Hp - 8, Wp - 8, q + kOffW[3],
+                                                       q + kOffB[3], S->Y);
 }
 
 // loss and gradients (into S->g) for the image in S->X and targets in S->T
@@ -700,6 +982,8 @@ sfm_status check_ctx(sfm_surrogate* S, sfm_ctx* ctx) {
   if (ctx->geo.W / s < 1 || ctx->geo.H / s < 1) return sfail(S, SFM_EINVAL, "lattice too small");
   if (S->cfg.near_radius > ctx->geo.r)
     return sfail(S, SFM_EINVAL, "near radius larger than the field radius");
+  if (!ctx->CT)
+    return sfail(S, SFM_EINVAL, "field radius beyond the class-table gather (r > 50)");
   return SFM_OK;
 }
 
@@ -719,6 +1003,15 @@ sfm_status ensure_lattice(sfm_surrogate* S, sfm_ctx* ctx) {
     STRY(salloc(S, &S->choice2, (size_t)ctx->cap));
     S->choice_cap = ctx->cap;
   }
+  if (ctx->cap > S->fb_cap) {
+    sfree(S, S->fex);
+    sfree(S, S->flag_list);
+    sfree(S, S->perr);
+    STRY(salloc(S, &S->fex, (size_t)ctx->cap * 9));
+    STRY(salloc(S, &S->flag_list, (size_t)ctx->cap));
+    STRY(salloc(S, &S->perr, (size_t)ctx->cap));
+    S->fb_cap = ctx->cap;
+  }
   const int rn = S->cfg.near_radius;
   if (S->near_r_built != rn || !S->CTnear) {
     sfree(S, S->CTnear);
@@ -726,7 +1019,7 @@ sfm_status ensure_lattice(sfm_surrogate* S, sfm_ctx* ctx) {
     const size_t n = class_table_floats(rn);
     if (n) {
       STRY(salloc(S, &S->CTnear, n));
-      launch_class_tables(rn, ctx->prm, S->CTnear, S->stream);
+      launch_class_tables(rn, ctx->prm, S->CTnear, S->stream, S->cfg.taper_inner);
     }
     S->near_r_built = rn;
   }
@@ -750,18 +1043,60 @@ void coarse_inputs(sfm_surrogate* S, sfm_ctx* ctx) {
                                                             S->Hc, S->Wc, S->X);
 }
 
+// Fsur = (Fs + pedestrian field within rn) + scale * bilinear(Y): the network
+// runs first and the near-field gather adds its interpolated output in its
+// epilogue, so the lattice is written once.  Bins must be current.
 void surrogate_field(sfm_surrogate* S, sfm_ctx* ctx) {
-  ctx_run_bins(ctx);
-  near_field(S, ctx);
   coarse_inputs(S, ctx);
   forward(S, ctx->stream);
-  const size_t nsu = (size_t)ctx->geo.W * ctx->geo.H;
-  k_combine<<<(unsigned)((nsu + 255) / 256), 256, 0, ctx->stream>>>(
-      ctx->geo, S->Fnear, S->Y, S->cfg.coarsen, S->Hc, S->Wc, S->cfg.target_scale, S->Fsur);
+  Geo gn = ctx->geo;
+  gn.r = S->cfg.near_radius;
+  Tables tb = ctx->tables();
+  tb.CT = S->CTnear;
+  FarPart far;
+  far.Y = S->Y;
+  far.s = S->cfg.coarsen;
+  far.Hc = S->Hc;
+  far.Wc = S->Wc;
+  far.scale = S->cfg.target_scale;
+  launch_field(gn, ctx->bin_start, ctx->rec, tb, ctx->Fs, S->Fsur, 0, 0, gn.H, ctx->ctr,
+               ctx->stream, far);
+}
+
+// Decisions of ctx's live pedestrians into `choice` from Fsur, then the
+// exact fallback for the pedestrians within the margin.  ref/raw_flips as
+// k_sur_decide.
+void surrogate_decide(sfm_surrogate* S, sfm_ctx* ctx, uint8_t* choice, const uint8_t* ref,
+                      unsigned long long* raw_flips) {
+  const Geo& g = ctx->geo;
+  const Tables tb = ctx->tables();
+  const int nbins = g.nbx * g.nby;
+  cudaStream_t st = ctx->stream;
+  cudaMemsetAsync(S->nflag, 0, sizeof(int32_t), st);
+  if (ctx->n <= 0) return;
+  k_sur_decide<<<cdiv(ctx->n, 256), 256, 0, st>>>(
+      ctx->rec_id, ctx->bin_start, nbins, g, ctx->xy, ctx->heading, ctx->goal, ctx->cell, ctx->ocls,
+      ctx->D, S->Fsur, ctx->prm.beta, tb.own, tb.dirdot, S->delta, choice, S->flag_list, S->nflag,
+      ref, raw_flips);
+  const int SP = class_table_stride(g.r);
+  const int TS = (2 * g.r + 1 + 2 * kFieldPadRows) * SP;
+  const size_t smem = (kTableGuard + 4 * (size_t)TS) * sizeof(float) +
+                      (size_t)kFbThreads / 32 * 32 * sizeof(int2);
+  cudaFuncSetAttribute(k_sur_fallback, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int dev = 0, nsm = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  k_sur_fallback<<<nsm > 0 ? nsm : 1, kFbThreads, smem, st>>>(S->flag_list, S->nflag, g, ctx->xy,
+                                                              ctx->bin_start, ctx->rec, ctx->CT,
+                                                              SP, TS, ctx->Fs, S->fex);
+  k_sur_redecide<<<cdiv(ctx->n < 152 * 2048 ? ctx->n : 152 * 2048, 256), 256, 0, st>>>(
+      S->flag_list, S->nflag, g, ctx->xy, ctx->heading, ctx->goal, ctx->cell, ctx->ocls, ctx->D,
+      S->fex, ctx->prm.beta, tb.own, tb.dirdot, choice);
 }
 
 void round_params(sfm_surrogate* S) {
   k_round_bf16<<<cdiv(kNParams, 256), 256, 0, S->stream>>>(S->p, S->pq, kNParams);
+  k_pack_w1<<<cdiv(32 * kC1K, 256), 256, 0, S->stream>>>(S->pq + kOffW[0], S->wt1);
   k_pack_w3<<<cdiv(9 * 32 * 32, 256), 256, 0, S->stream>>>(S->pq + kOffW[1], S->wt2);
   k_pack_w3<<<cdiv(9 * 32 * 32, 256), 256, 0, S->stream>>>(S->pq + kOffW[2], S->wt3);
 }
@@ -776,7 +1111,8 @@ sfm_status sfm_surrogate_create(const sfm_surrogate_cfg* cfg, void* stream, sfm_
   if (out) *out = nullptr;
   if (!cfg || !out) return sfail(nullptr, SFM_EINVAL, "NULL argument");
   if (cfg->coarsen < 1 || cfg->coarsen > 64 || cfg->near_radius < 0 ||
-      cfg->near_radius > SFM_MAX_RADIUS || !(cfg->target_scale > 0.f))
+      cfg->near_radius > kMaxTableRadius || !(cfg->target_scale > 0.f) ||
+      !(cfg->taper_inner >= 0.f))
     return sfail(nullptr, SFM_EINVAL, "bad surrogate configuration");
   sfm_surrogate* S = new sfm_surrogate;
   S->cfg = *cfg;
@@ -790,13 +1126,16 @@ sfm_status sfm_surrogate_create(const sfm_surrogate_cfg* cfg, void* stream, sfm_
   if ((st = salloc(S, &S->p, kNParams)) != SFM_OK || (st = salloc(S, &S->pq, kNParams)) != SFM_OK ||
       (st = salloc(S, &S->m, kNParams)) != SFM_OK || (st = salloc(S, &S->v, kNParams)) != SFM_OK ||
       (st = salloc(S, &S->g, kNParams)) != SFM_OK || (st = salloc(S, &S->red, 2 * 1024)) != SFM_OK ||
+      (st = salloc(S, &S->wt1, 32 * kC1K)) != SFM_OK ||
       (st = salloc(S, &S->wt2, 9 * 32 * 32)) != SFM_OK ||
+      (st = salloc(S, &S->fb_dev, 2)) != SFM_OK || (st = salloc(S, &S->nflag, 1)) != SFM_OK ||
       (st = salloc(S, &S->wt3, 9 * 32 * 32)) != SFM_OK ||
-      (st = salloc(S, &S->cnt, 1)) != SFM_OK)
+      (st = salloc(S, &S->cnt, 2)) != SFM_OK)
     return bail(st);
   cudaMemsetAsync(S->p, 0, kNParams * sizeof(float), S->stream);
   cudaMemsetAsync(S->m, 0, kNParams * sizeof(float), S->stream);
   cudaMemsetAsync(S->v, 0, kNParams * sizeof(float), S->stream);
+  cudaMemsetAsync(S->fb_dev, 0, 2 * sizeof(unsigned long long), S->stream);
   round_params(S);
   if (cudaStreamSynchronize(S->stream) != cudaSuccess) {
     S->err = "surrogate set-up failed";
@@ -899,13 +1238,21 @@ sfm_status sfm_surrogate_train(sfm_surrogate* S, sfm_ctx* ctx, int32_t iters, fl
   return SFM_OK;
 }
 
-sfm_status sfm_surrogate_field(sfm_surrogate* S, sfm_ctx* ctx, float* out, int32_t on_device) {
-  if (!S || !out) return SFM_EINVAL;
+// set-up shared by the calls below
+sfm_status surrogate_ready(sfm_surrogate* S, sfm_ctx* ctx) {
+  if (!S) return SFM_EINVAL;
   STRY(check_ctx(S, ctx));
   STRY(ensure_lattice(S, ctx));
   const int s = S->cfg.coarsen;
   STRY(ensure_image(S, ctx->geo.H / s, ctx->geo.W / s));
   S->stream = ctx->stream;
+  return SFM_OK;
+}
+
+sfm_status sfm_surrogate_field(sfm_surrogate* S, sfm_ctx* ctx, float* out, int32_t on_device) {
+  if (!S || !out) return SFM_EINVAL;
+  STRY(surrogate_ready(S, ctx));
+  ctx_run_bins(ctx);
   surrogate_field(S, ctx);
   SCU(cudaMemcpyAsync(out, S->Fsur, S->nsu * sizeof(float),
                       on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ctx->stream));
@@ -914,47 +1261,113 @@ sfm_status sfm_surrogate_field(sfm_surrogate* S, sfm_ctx* ctx, float* out, int32
   return SFM_OK;
 }
 
-sfm_status sfm_surrogate_eval(sfm_surrogate* S, sfm_ctx* ctx, double* field_rel_err,
-                              double* flip_rate, double* ms_surrogate, double* ms_exact) {
-  if (!S) return SFM_EINVAL;
-  STRY(check_ctx(S, ctx));
-  STRY(ensure_lattice(S, ctx));
-  const int s = S->cfg.coarsen;
-  STRY(ensure_image(S, ctx->geo.H / s, ctx->geo.W / s));
-  S->stream = ctx->stream;
+sfm_status sfm_surrogate_set_delta(sfm_surrogate* S, float delta) {
+  if (!S || !(delta >= 0.f)) return SFM_EINVAL;
+  S->delta = delta;
+  return SFM_OK;
+}
+
+sfm_status sfm_surrogate_calibrate(sfm_surrogate* S, sfm_ctx* ctx, double quantile,
+                                   float* delta_out) {
+  if (!(quantile >= 0.0 && quantile <= 1.0)) return sfail(S, SFM_EINVAL, "quantile outside [0, 1]");
+  STRY(surrogate_ready(S, ctx));
   cudaStream_t st = ctx->stream;
+  const Geo& g = ctx->geo;
+  const int nbins = g.nbx * g.nby;
+  ctx_run_bins(ctx);
+  ctx_field_rows(ctx, ctx->F, 0, g.H, 0, false);
+  surrogate_field(S, ctx);
+  if (ctx->n > 0)
+    k_sur_err<<<cdiv(ctx->n, 256), 256, 0, st>>>(ctx->rec_id, ctx->bin_start, nbins, g, ctx->xy,
+                                                 ctx->cell, ctx->ocls, S->Fsur, ctx->F, S->perr);
+  int nrec = 0;
+  SCU(cudaMemcpyAsync(&nrec, ctx->bin_start + nbins, sizeof(int), cudaMemcpyDeviceToHost, st));
+  SCU(cudaStreamSynchronize(st));
+  std::vector<float> e((size_t)nrec);
+  if (nrec > 0) {
+    SCU(cudaMemcpyAsync(e.data(), S->perr, (size_t)nrec * sizeof(float), cudaMemcpyDeviceToHost, st));
+    SCU(cudaStreamSynchronize(st));
+  }
+  SCU(cudaGetLastError());
+  float d = 0.f;
+  if (nrec > 0) {
+    size_t k = (size_t)(quantile * (double)(nrec - 1) + 0.5);
+    if (k >= (size_t)nrec) k = (size_t)nrec - 1;
+    std::nth_element(e.begin(), e.begin() + (long)k, e.end());
+    d = e[k];
+  }
+  S->delta = d;
+  if (delta_out) *delta_out = d;
+  return SFM_OK;
+}
+
+sfm_status sfm_surrogate_step(sfm_surrogate* S, sfm_ctx* ctx, int32_t nsteps) {
+  if (nsteps < 0) return sfail(S, SFM_EINVAL, "nsteps < 0");
+  STRY(surrogate_ready(S, ctx));
+  cudaStream_t st = ctx->stream;
+  const Geo& g = ctx->geo;
+  for (int i = 0; i < nsteps; ++i) {
+    launch_clear_dead(ctx->n, ctx->alive, ctx->choice, ctx->won, st);
+    ctx_run_bins(ctx);
+    surrogate_field(S, ctx);
+    surrogate_decide(S, ctx, ctx->choice, nullptr, nullptr);
+    k_count_fallbacks<<<1, 1, 0, st>>>(S->nflag, ctx->bin_start + g.nbx * g.nby, S->fb_dev);
+    launch_vote(ctx->n, ctx->rec_id, ctx->bin_start, ctx->xy, ctx->choice, ctx->occ, g,
+                ctx->prm.seed, ctx->ctr, ctx->won, st);
+    launch_commit(ctx->n, ctx->rec_id, ctx->bin_start, ctx->xy, ctx->alive, ctx->heading,
+                  ctx->choice, ctx->won, ctx->cell, ctx->occ, ctx->ocls, g, ctx->ctr, st);
+    ++ctx->t;
+  }
+  SCU(cudaGetLastError());
+  return SFM_OK;
+}
+
+sfm_status sfm_surrogate_counts(sfm_surrogate* S, int64_t* fallbacks, int64_t* decided) {
+  if (!S) return SFM_EINVAL;
+  unsigned long long h[2] = {0, 0};
+  SCU(cudaMemcpyAsync(h, S->fb_dev, sizeof(h), cudaMemcpyDeviceToHost, S->stream));
+  SCU(cudaStreamSynchronize(S->stream));
+  if (fallbacks) *fallbacks = (int64_t)h[0];
+  if (decided) *decided = (int64_t)h[1];
+  return SFM_OK;
+}
+
+sfm_status sfm_surrogate_eval(sfm_surrogate* S, sfm_ctx* ctx, sfm_surrogate_report* rep) {
+  if (!rep) return SFM_EINVAL;
+  STRY(surrogate_ready(S, ctx));
+  cudaStream_t st = ctx->stream;
+  const Geo& g = ctx->geo;
+  const Tables tb = ctx->tables();
+  const int nbins = g.nbx * g.nby;
   cudaEvent_t e0, e1, e2;
   SCU(cudaEventCreate(&e0));
   SCU(cudaEventCreate(&e1));
   SCU(cudaEventCreate(&e2));
-  // exact field (bins + gather) and the surrogate field of the same state
+  // exact: bins, field, decisions (into ctx->choice)
   SCU(cudaEventRecord(e0, st));
   ctx_run_bins(ctx);
-  ctx_field_rows(ctx, ctx->F, 0, ctx->geo.H, 0, false);
-  SCU(cudaEventRecord(e1, st));
-  surrogate_field(S, ctx);
-  SCU(cudaEventRecord(e2, st));
-  // decisions on each field
-  const Geo& g = ctx->geo;
-  const Tables tb = ctx->tables();
-  const int nbins = g.nbx * g.nby;
+  ctx_field_rows(ctx, ctx->F, 0, g.H, 0, false);
   launch_decide(ctx->n, ctx->rec_id, ctx->bin_start, 0, nbins, ctx->xy, ctx->heading, ctx->goal,
                 ctx->cell, ctx->ocls, ctx->D, ctx->F, 0, -1, -1, 0, 0, g.H, g, ctx->prm.beta, tb,
                 ctx->choice, st);
-  launch_decide(ctx->n, ctx->rec_id, ctx->bin_start, 0, nbins, ctx->xy, ctx->heading, ctx->goal,
-                ctx->cell, ctx->ocls, ctx->D, S->Fsur, 0, -1, -1, 0, 0, g.H, g, ctx->prm.beta, tb,
-                S->choice2, st);
-  SCU(cudaMemsetAsync(S->cnt, 0, sizeof(unsigned long long), st));
+  SCU(cudaEventRecord(e1, st));
+  // surrogate: bins, field, decisions with the fallback (into choice2)
+  SCU(cudaMemsetAsync(S->cnt, 0, 2 * sizeof(unsigned long long), st));
+  ctx_run_bins(ctx);
+  surrogate_field(S, ctx);
+  surrogate_decide(S, ctx, S->choice2, ctx->choice, S->cnt + 1);
+  SCU(cudaEventRecord(e2, st));
   if (ctx->n > 0)
     k_diff_choices<<<cdiv(ctx->n, 256), 256, 0, st>>>(ctx->rec_id, ctx->bin_start, nbins,
                                                       ctx->choice, S->choice2, S->cnt);
   k_field_err<<<1024, 256, 0, st>>>(S->Fsur, ctx->F, ctx->Fs, S->nsu, S->red);
   std::vector<double> red(2048);
-  unsigned long long cnt = 0;
-  int nrec = 0;
+  unsigned long long cnt[2] = {0, 0};
+  int nrec = 0, nfl = 0;
   SCU(cudaMemcpyAsync(red.data(), S->red, red.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
-  SCU(cudaMemcpyAsync(&cnt, S->cnt, sizeof(cnt), cudaMemcpyDeviceToHost, st));
+  SCU(cudaMemcpyAsync(cnt, S->cnt, sizeof(cnt), cudaMemcpyDeviceToHost, st));
   SCU(cudaMemcpyAsync(&nrec, ctx->bin_start + nbins, sizeof(int), cudaMemcpyDeviceToHost, st));
+  SCU(cudaMemcpyAsync(&nfl, S->nflag, sizeof(int), cudaMemcpyDeviceToHost, st));
   SCU(cudaStreamSynchronize(st));
   SCU(cudaGetLastError());
   double a = 0.0, b = 0.0;
@@ -968,10 +1381,15 @@ sfm_status sfm_surrogate_eval(sfm_surrogate* S, sfm_ctx* ctx, double* field_rel_
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   cudaEventDestroy(e2);
-  if (field_rel_err) *field_rel_err = b > 0 ? a / b : 0.0;
-  if (flip_rate) *flip_rate = nrec > 0 ? (double)cnt / nrec : 0.0;
-  if (ms_surrogate) *ms_surrogate = t_su;
-  if (ms_exact) *ms_exact = t_ex;
+  const double nd = nrec > 0 ? (double)nrec : 1.0;
+  rep->field_rel_err = b > 0 ? a / b : 0.0;
+  rep->flip_rate = (double)cnt[0] / nd;
+  rep->flip_rate_raw = (double)cnt[1] / nd;
+  rep->fallback_rate = (double)nfl / nd;
+  rep->ms_surrogate = t_su;
+  rep->ms_exact = t_ex;
+  rep->delta = S->delta;
+  rep->decided = nrec;
   return SFM_OK;
 }
 

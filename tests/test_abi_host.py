@@ -60,6 +60,23 @@ def test_struct_layouts_match_header(tmp_path):
     assert got == want
 
 
+def test_surrogate_struct_layouts_match_header(tmp_path):
+    prog = tmp_path / "slayout.c"
+    prog.write_text(
+        '#include <stdio.h>\n#include <stddef.h>\n#include "sfm.h"\n'
+        "int main(void){printf(\"%zu %zu %zu %zu %zu\\n\", sizeof(sfm_surrogate_cfg),"
+        " offsetof(sfm_surrogate_cfg, taper_inner), sizeof(sfm_surrogate_report),"
+        " offsetof(sfm_surrogate_report, delta), offsetof(sfm_surrogate_report, decided));"
+        " return 0;}\n")
+    exe = tmp_path / "slayout"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)])
+    got = [int(v) for v in subprocess.check_output([str(exe)]).split()]
+    want = [C.sizeof(sfm.SurrogateCfg), sfm.SurrogateCfg.taper_inner.offset,
+            C.sizeof(sfm.SurrogateReport), sfm.SurrogateReport.delta.offset,
+            sfm.SurrogateReport.decided.offset]
+    assert got == want
+
+
 def test_params_helper_round_trips():
     p = sfm.make_params(r=40, seed=2**64 - 1, hbm_budget_bytes=5 << 30)
     assert p.r == 40 and p.seed == 2**64 - 1 and p.hbm_budget_bytes == 5 << 30

@@ -77,3 +77,32 @@ def test_coarse_channels_cell_average_and_upsampling():
     ramp = np.tile(np.arange(4.0), (3, 1))
     up = S.upsample(ramp, 4, periodic=False)
     np.testing.assert_allclose(up[5, 6:10], (np.arange(6, 10) + 0.5) / 4 - 0.5)
+
+
+def test_untapered_near_field_equals_the_model_field_at_radius_rn():
+    """With r_in >= rn the near part is the model's pedestrian field with the
+    influence radius set to rn (the C oracle, independent code)."""
+    import oracle as O
+    import scenegen as SG
+    sc = SG.random_scene(23, 19, 40, r=4, seed=7, periodic_x=1, exits=("south",),
+                         goal_mode="mixed", heading_mode="random")
+    m = O.model(sc, r=4)
+    occ, bad = O.occupancy(m, sc.cell, sc.xy)
+    assert bad == 0
+    Fp, _ = O.field(m, sc.cell, occ, sc.heading, parts=2)
+    Fn = S.tapered_near_field(sc.W, sc.H, sc.xy, sc.heading, 4, 10.0, m.kP, m.aP, m.gamma,
+                              periodic_x=1, periodic_y=0)
+    np.testing.assert_allclose(Fn, Fp, rtol=1e-12, atol=1e-12)
+
+
+def test_taper_of_a_single_pedestrian():
+    """One pedestrian heading east: full kernel inside r_in, half of it at
+    the taper's midpoint, nothing at or beyond rn."""
+    rn, r_in = 6, 2.0
+    F = S.tapered_near_field(21, 21, [(10, 10)], [1], rn, r_in, 2.0, -0.5, 0.5)
+    K = lambda dx, dy: 2.0 * np.hypot(dx, dy) ** -0.5 * (1 + 0.5 * dx / np.hypot(dx, dy))
+    assert F[10, 12] == pytest.approx(K(2, 0), rel=1e-14)        # d = 2 = r_in
+    assert F[10, 14] == pytest.approx(0.5 * K(4, 0), rel=1e-14)  # d = 4, midpoint
+    assert F[10, 16] == 0.0 and F[16, 16] == 0.0                 # d = 6 and 8.5
+    assert F[13, 13] == pytest.approx(S.taper_weight(np.hypot(3, 3), r_in, rn) * K(3, 3), rel=1e-14)
+    assert 0.0 < S.taper_weight(5.0, r_in, rn) < 0.5 < S.taper_weight(3.0, r_in, rn) < 1.0
