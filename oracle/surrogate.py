@@ -29,12 +29,10 @@ HALO = sum((k - 1) // 2 for _, _, k in LAYERS)                 # 5 cells of cont
 
 
 def init_params(seed: int = 0):
-    """He-style random initialisation (the GPU path receives these values)."""
-    rng = np.random.default_rng(seed)
-    ps = []
-    for cin, cout, k in LAYERS:
-        std = np.sqrt(2.0 / (cin * k * k))
-        ps.append((rng.normal(0.0, std, (cout, cin, k, k)), np.zeros(cout)))
+    """Seeded random initial weights (drawn by the shared input generator)."""
+    import scenegen
+    ps = scenegen.surrogate_init(seed)
+    assert [(W.shape[1], W.shape[0], W.shape[2]) for W, _ in ps] == LAYERS
     return ps
 
 

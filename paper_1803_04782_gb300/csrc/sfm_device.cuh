@@ -319,8 +319,8 @@ struct FarAxis {
   int i0, i1;  // coarse indices of the two neighbouring centres
   float t;     // weight of i1
 };
-__device__ __forceinline__ FarAxis far_axis(int v, int s, int n, int periodic) {
-  const float f = (v + 0.5f) / s - 0.5f;
+__device__ __forceinline__ FarAxis far_axis(int v, float inv_s, int n, int periodic) {
+  const float f = (v + 0.5f) * inv_s - 0.5f;
   int a = (int)floorf(f);
   FarAxis ax;
   ax.t = f - a;

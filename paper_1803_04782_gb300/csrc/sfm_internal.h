@@ -95,6 +95,7 @@ struct FarPart {
   const float* Y = nullptr;
   int s = 1, Hc = 0, Wc = 0;
   float scale = 0.f;
+  float inv_s = 1.f;  // 1 / s
 };
 
 struct Tables {

@@ -714,7 +714,7 @@ __global__ void __launch_bounds__(kV2Threads, 1)
   for (int f = blockIdx.x * wpb + warp; f < nf; f += tw) {
     const int x0 = (f % nfx) * FW, y0 = (fy0 + f / nfx) * FH;
     FarAxis fax{};
-    if constexpr (FAR) fax = far_axis(x0 + x, far.s, far.Wc, g.px);
+    if constexpr (FAR) fax = far_axis(x0 + x, far.inv_s, far.Wc, g.px);
     float2 acc[NJ / 2];
 #pragma unroll
     for (int j = 0; j < NJ / 2; ++j) acc[j] = make_float2(0.f, 0.f);
@@ -728,7 +728,7 @@ __global__ void __launch_bounds__(kV2Threads, 1)
       if (xx < g.W && y < g.H && y >= store_lo && y < store_hi) {
         const size_t c = (size_t)y * g.W + xx;
         float v = Fs[c] + ((j & 1) ? acc[j >> 1].y : acc[j >> 1].x);
-        if constexpr (FAR) v += far_value(far, far_axis(y, far.s, far.Hc, g.py), fax);
+        if constexpr (FAR) v += far_value(far, far_axis(y, far.inv_s, far.Hc, g.py), fax);
         out[(size_t)(y - out_row0) * g.W + xx] = v;
       }
     }

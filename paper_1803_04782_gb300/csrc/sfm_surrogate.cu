@@ -1059,6 +1059,7 @@ void surrogate_field(sfm_surrogate* S, sfm_ctx* ctx) {
   far.Hc = S->Hc;
   far.Wc = S->Wc;
   far.scale = S->cfg.target_scale;
+  far.inv_s = 1.f / (float)S->cfg.coarsen;
   launch_field(gn, ctx->bin_start, ctx->rec, tb, ctx->Fs, S->Fsur, 0, 0, gn.H, ctx->ctr,
                ctx->stream, far);
 }

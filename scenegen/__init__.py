@@ -347,3 +347,18 @@ def config(i: int, **kw):
     if i == 4:
         return batch(**kw)
     raise ValueError(i)
+
+
+SURROGATE_LAYERS = ((3, 32, 5), (32, 32, 3), (32, 32, 3), (32, 1, 3))  # (Cin, Cout, k)
+
+
+def surrogate_init(seed: int = 0):
+    """Seeded initial weights of the field surrogate's 4 layers: [(W [out, in,
+    k, k], b [out]), ...], W normal with standard deviation sqrt(2 / (in k^2)),
+    b zero.  Random inputs only: the network's arithmetic lives elsewhere."""
+    rng = np.random.default_rng(seed)
+    ps = []
+    for cin, cout, k in SURROGATE_LAYERS:
+        std = np.sqrt(2.0 / (cin * k * k))
+        ps.append((rng.normal(0.0, std, (cout, cin, k, k)), np.zeros(cout)))
+    return ps
