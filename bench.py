@@ -294,6 +294,19 @@ def run_gpu(args):
     sim.set_timing(False)
     st1 = sim.stats()
     xy1, h1, a1 = sim.peds()
+    # the same ticks replayed as one CUDA graph each, without per-stage events
+    # (what the stage events cost shows on small lattices); after the timed
+    # region, not part of `value`
+    graph_ticks = max(3, min(args.steps, 20))
+    sim.step(1)
+    torch.cuda.synchronize()
+    g0 = torch.cuda.Event(enable_timing=True)
+    g1 = torch.cuda.Event(enable_timing=True)
+    g0.record(stream)
+    sim.step(graph_ticks)
+    g1.record(stream)
+    torch.cuda.synchronize()
+    graph_ms = g0.elapsed_time(g1) / graph_ticks
     pairs1 = pair_count(sc, xy1, a1)
     alive1 = int(a1.sum())
     launches = st1["kernel_launches"] - launches0
@@ -378,6 +391,7 @@ def run_gpu(args):
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "su_updates_per_s": sc.W * sc.H * args.steps * world / elapsed,
         "stage_ms_per_step": {k: v / max(1, ticks) for k, v in stage_ms.items()},
+        "graph_ms_per_step": graph_ms,
         "roofline": roofline,
         "cpu_baseline": cpu,
         "e2e": e2e,
