@@ -33,10 +33,11 @@ FLOPS_PER_PAIR = 6.0  # three FP32 multiply-adds per (su, pedestrian-in-window) 
 # 16384^2 floor with 4 bands, from a one-pass ncu capture of this benchmark
 # (dram__bytes_read.sum + dram__bytes_write.sum); valid only while the
 # gather's sources hash to the value they had when it was taken.
-GATHER_TRAFFIC = {"sha1": "4176862f2136bb4684d1cd020b7f1d17c6c4abc4", "bands": 4,
-                  "footprint": "32x16", "workload": "floor", "bytes_per_launch": 492866560}
-GATHER_SOURCES = ("paper_1803_04782_gb300/csrc/sfm_device.cuh",
-                  "paper_1803_04782_gb300/csrc/sfm_kernels.cu")
+GATHER_TRAFFIC = {"sha1": "d589993404cd4330f8a617e4d55f651b60adb42a", "bands": 4,
+                  "footprint": "32x16", "workload": "floor", "bytes_per_launch": 492692544}
+GATHER_SOURCES = ("paper_1803_04782_gb300/csrc/sfm_gather.cuh",
+                  "paper_1803_04782_gb300/csrc/sfm_field.cu",
+                  "paper_1803_04782_gb300/csrc/sfm_internal.h")
 
 
 def gather_sources_sha1() -> str:

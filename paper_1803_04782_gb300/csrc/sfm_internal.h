@@ -147,6 +147,10 @@ void launch_clear_dead(int n, const uint8_t* alive, uint8_t* choice, uint8_t* wo
 // Field gather; stores lattice rows y in [store_lo, store_hi) at
 // out[(y - out_row0) * W + x].  Every su is summed in the same order whatever
 // the row range, so banded and unbanded passes agree bit for bit.
+// the three-component gather (radius > 50), called by launch_field
+void launch_field_v1(const Geo& g, const int32_t* bin_start, const uint32_t* rec, const Tables& tb,
+                     const float* Fs, float* out, int out_row0, int store_lo, int store_hi,
+                     Counters* ctr, cudaStream_t s);
 void launch_field(const Geo& g, const int32_t* bin_start, const uint32_t* rec, const Tables& tb,
                   const float* Fs, float* out, int out_row0, int store_lo, int store_hi,
                   Counters* ctr, cudaStream_t s, const FarPart& far = FarPart());

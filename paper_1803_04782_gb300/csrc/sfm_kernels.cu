@@ -6,7 +6,7 @@
 #include <math.h>
 #include <stdint.h>
 
-#include "sfm_device.cuh"
+#include "sfm_gather.cuh"
 #include "sfm_internal.h"
 
 namespace sfm {
@@ -621,7 +621,7 @@ static int field_cap(int r, size_t* smem_out) {
   return cap;
 }
 
-static void launch_field_v1(const Geo& g, const int32_t* bin_start, const uint32_t* rec,
+void launch_field_v1(const Geo& g, const int32_t* bin_start, const uint32_t* rec,
                             const Tables& tb, const float* Fs, float* out, int out_row0,
                             int store_lo, int store_hi, Counters* ctr, cudaStream_t s) {
   const int ty0 = store_lo / kTile, ty1 = (store_hi + kTile - 1) / kTile;
@@ -634,21 +634,6 @@ static void launch_field_v1(const Geo& g, const int32_t* bin_start, const uint32
                                             store_lo, store_hi, cap, ctr);
 }
 
-
-// ---------------------------------------------- S2 (v2): persistent warps
-// One warp owns a 32 x 16 su footprint (lane = column, 16 rows per lane) and
-// walks the bins overlapping the footprint's r-halo in batches of 32
-// records, fetched lane-parallel (coalesced, L1-shared by the neighbouring
-// footprints other warps of the SM work on).  Each lane screens its record,
-// precomputes its table offset and lane range, and the records in reach are
-// compacted into a per-warp shared-memory scratch read back by broadcast.
-// Each (su, pedestrian) pair then costs one shared-memory table read and one
-// FP32 add, because the heading of a pedestrian is one of 9 classes and the
-// kernel of every class is stored precomputed (4 tables, the other 5 classes
-// by x/y mirroring).  Tables carry kFieldPad zero rows above and below the
-// window so the 16 rows of a lane need no row test, and a compile-time row
-// stride SP lets the 16 reads use immediate offsets.  One CTA of 32 warps per
-// SM loads the tables once for the whole launch.
 
 __global__ void k_class_tables(int r, int SP, double kP, double aP, double gamma, double taper_in,
                                float* __restrict__ T) {
@@ -684,117 +669,6 @@ void launch_class_tables(int r, const sfm_params& p, float* T, cudaStream_t s, d
   k_class_tables<<<cdiv(n, 256), 256, 0, s>>>(r, sp, p.kP, p.aP, p.gamma, taper_in, T);
 }
 
-template <int SP, int SHAPE, bool FAR>
-__global__ void __launch_bounds__(kV2Threads, 1)
-    k_field_v2(Geo g, const int32_t* __restrict__ bin_start, const uint32_t* __restrict__ rec,
-               const float* __restrict__ CT, const float* __restrict__ Fs,
-               float* __restrict__ out, int out_row0, int fy0, int fy1, int store_lo,
-               int store_hi, FarPart far) {
-  extern __shared__ __align__(16) float sm[];
-  constexpr int FW = SHAPE ? 32 : 16, FH = 16, NJ = SHAPE ? 16 : 8;
-  const int r = g.r;
-  const int TR = 2 * r + 1 + 2 * kFieldPad, TS = TR * SP;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  float* sT = sm + kTableGuard;
-  // per-warp scratch: the batch's pedestrians in reach of the footprint
-  int2* scr = reinterpret_cast<int2*>(sT + 4 * TS) + warp * 32;
-  {
-    const float2* src = reinterpret_cast<const float2*>(CT);
-    float2* dst = reinterpret_cast<float2*>(sT);
-    for (int i = threadIdx.x; i < 2 * TS; i += blockDim.x) dst[i] = src[i];  // 4*TS floats
-    if (threadIdx.x < kTableGuard) sm[threadIdx.x] = 0.f;
-  }
-  __syncthreads();
-  const int wpb = blockDim.x >> 5;
-  const int tw = gridDim.x * wpb;
-  const int nfx = (g.W + FW - 1) / FW;
-  const int nf = nfx * (fy1 - fy0);
-  // this lane's column and first row inside a footprint
-  const int x = SHAPE ? lane : (lane & 15), yl = SHAPE ? 0 : (lane >> 4) * 8;
-  for (int f = blockIdx.x * wpb + warp; f < nf; f += tw) {
-    const int x0 = (f % nfx) * FW, y0 = (fy0 + f / nfx) * FH;
-    FarAxis fax{};
-    if constexpr (FAR) fax = far_axis(x0 + x, far.inv_s, far.Wc, g.px);
-    float2 acc[NJ / 2];
-#pragma unroll
-    for (int j = 0; j < NJ / 2; ++j) acc[j] = make_float2(0.f, 0.f);
-    if constexpr (SHAPE)
-      gather_footprint32<SP>(g, bin_start, rec, sT, TS, scr, lane, x0, y0, acc);
-    else
-      gather_footprint16<SP>(g, bin_start, rec, sT, TS, scr, lane, x0, y0, acc);
-#pragma unroll
-    for (int j = 0; j < NJ; ++j) {
-      const int y = y0 + yl + j, xx = x0 + x;
-      if (xx < g.W && y < g.H && y >= store_lo && y < store_hi) {
-        const size_t c = (size_t)y * g.W + xx;
-        float v = Fs[c] + ((j & 1) ? acc[j >> 1].y : acc[j >> 1].x);
-        if constexpr (FAR) v += far_value(far, far_axis(y, far.inv_s, far.Hc, g.py), fax);
-        out[(size_t)(y - out_row0) * g.W + xx] = v;
-      }
-    }
-  }
-}
-
-static int g_num_sms = 0;
-
-template <int SP, int SHAPE, bool FAR>
-static void launch_v2(const Geo& g, const int32_t* bin_start, const uint32_t* rec, const float* CT,
-                      const float* Fs, float* out, int out_row0, int store_lo, int store_hi,
-                      cudaStream_t s, const FarPart& far) {
-  constexpr int FW = SHAPE ? 32 : 16, FH = 16;
-  const size_t smem = (kTableGuard + class_table_floats(g.r)) * sizeof(float) +
-                      kV2Threads / 32 * 32 * sizeof(int2);
-  cudaFuncSetAttribute(k_field_v2<SP, SHAPE, FAR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (!g_num_sms) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
-    if (g_num_sms <= 0) g_num_sms = 1;
-  }
-  const int fy0 = store_lo / FH, fy1 = (store_hi + FH - 1) / FH;
-  const int nf = ((g.W + FW - 1) / FW) * (fy1 - fy0);
-  const int wpb = kV2Threads / 32;
-  int blocks = (nf + wpb - 1) / wpb;
-  if (blocks > g_num_sms) blocks = g_num_sms;
-  if (blocks < 1) blocks = 1;
-  k_field_v2<SP, SHAPE, FAR><<<blocks, kV2Threads, smem, s>>>(g, bin_start, rec, CT, Fs, out, out_row0,
-                                                         fy0, fy1, store_lo, store_hi, far);
-}
-
-template <int SP>
-static void launch_v2_shape(const Geo& g, const int32_t* bin_start, const uint32_t* rec,
-                            const Tables& tb, const float* Fs, float* out, int out_row0,
-                            int store_lo, int store_hi, cudaStream_t s, const FarPart& far) {
-  // the far part (surrogate) has its own instantiation, 32 x 16 footprint only,
-  // so the exact gather carries no code for it
-  if (far.Y)
-    launch_v2<SP, 1, true>(g, bin_start, rec, tb.CT, Fs, out, out_row0, store_lo, store_hi, s, far);
-  else if (tb.shape)
-    launch_v2<SP, 1, false>(g, bin_start, rec, tb.CT, Fs, out, out_row0, store_lo, store_hi, s, far);
-  else
-    launch_v2<SP, 0, false>(g, bin_start, rec, tb.CT, Fs, out, out_row0, store_lo, store_hi, s, far);
-}
-
-void launch_field(const Geo& g, const int32_t* bin_start, const uint32_t* rec, const Tables& tb,
-                  const float* Fs, float* out, int out_row0, int store_lo, int store_hi,
-                  Counters* ctr, cudaStream_t s, const FarPart& far) {
-  if (store_hi <= store_lo) return;
-  const int sp = tb.CT ? class_table_stride(g.r) : 0;
-  if (!sp) {
-    launch_field_v1(g, bin_start, rec, tb, Fs, out, out_row0, store_lo, store_hi, ctr, s);
-    return;
-  }
-  switch (sp) {
-    case 34: launch_v2_shape<34>(g, bin_start, rec, tb, Fs, out, out_row0, store_lo, store_hi, s, far); break;
-    case 50: launch_v2_shape<50>(g, bin_start, rec, tb, Fs, out, out_row0, store_lo, store_hi, s, far); break;
-    case 66: launch_v2_shape<66>(g, bin_start, rec, tb, Fs, out, out_row0, store_lo, store_hi, s, far); break;
-    case 82: launch_v2_shape<82>(g, bin_start, rec, tb, Fs, out, out_row0, store_lo, store_hi, s, far); break;
-    case 98: launch_v2_shape<98>(g, bin_start, rec, tb, Fs, out, out_row0, store_lo, store_hi, s, far); break;
-    case 114: launch_v2_shape<114>(g, bin_start, rec, tb, Fs, out, out_row0, store_lo, store_hi, s, far); break;
-    default: launch_v2_shape<kNarrowStride>(g, bin_start, rec, tb, Fs, out, out_row0, store_lo, store_hi, s, far); break;
-  }
-}
-
 // --------------------------------------------------------- S3: decide
 // Per live pedestrian (visited in bin order, so neighbouring threads read
 // neighbouring su): E over the 9 candidates (stay + 8 neighbours), admissible
@@ -808,11 +682,15 @@ __global__ void k_decide(const int32_t* __restrict__ rec_id, const int32_t* __re
                          int lo_row, int hi_row, int hi_off, int y_lo, int y_hi, Geo g,
                          float beta, const float* __restrict__ own,
                          const float* __restrict__ dirdot, uint8_t* __restrict__ choice) {
-  const int i = bin_start[b_lo] + blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= bin_start[b_hi]) return;
-  const int p = rec_id[i];
-  choice[p] = decide_one(p, g, xy, heading, goal, cell, ocls, D, F, main_off, lo_row, hi_row,
-                         hi_off, y_lo, y_hi, beta, own, dirdot);
+  // grid-stride over the records of bins [b_lo, b_hi): a band's launch needs
+  // no more blocks than the GPU holds, whatever its share of the crowd
+  const int end = bin_start[b_hi];
+  for (int i = bin_start[b_lo] + blockIdx.x * blockDim.x + threadIdx.x; i < end;
+       i += gridDim.x * blockDim.x) {
+    const int p = rec_id[i];
+    choice[p] = decide_one(p, g, xy, heading, goal, cell, ocls, D, F, main_off, lo_row, hi_row,
+                           hi_off, y_lo, y_hi, beta, own, dirdot);
+  }
 }
 
 void launch_decide(int n, const int32_t* rec_id, const int32_t* bin_start, int b_lo, int b_hi,
@@ -821,7 +699,15 @@ void launch_decide(int n, const int32_t* rec_id, const int32_t* bin_start, int b
                    int main_off, int lo_row, int hi_row, int hi_off, int y_lo, int y_hi,
                    const Geo& g, float beta, const Tables& tb, uint8_t* choice, cudaStream_t s) {
   if (n <= 0 || b_hi <= b_lo) return;
-  k_decide<<<cdiv(n, 256), 256, 0, s>>>(rec_id, bin_start, b_lo, b_hi, xy, heading, goal, cell,
+  static int max_blocks = 0;
+  if (!max_blocks) {
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    max_blocks = (nsm > 0 ? nsm : 1) * 8;  // 8 blocks of 256 per SM (64 registers each)
+  }
+  const int blocks = cdiv(n, 256) < max_blocks ? cdiv(n, 256) : max_blocks;
+  k_decide<<<blocks, 256, 0, s>>>(rec_id, bin_start, b_lo, b_hi, xy, heading, goal, cell,
                                         ocls, D, F, main_off, lo_row, hi_row, hi_off, y_lo, y_hi,
                                         g, beta, tb.own, tb.dirdot, choice);
 }

@@ -17,7 +17,7 @@
 #include <vector>
 
 #include "sfm_ctx.h"
-#include "sfm_device.cuh"
+#include "sfm_gather.cuh"
 
 using namespace sfm;
 
