@@ -190,10 +190,29 @@ def oracle_sample(sc, D, xy, heading, goal, alive, n_sample, t, seed=0):
     return per_tick, O.threads(), req.size
 
 
+def reduce_over_ranks(dist, seconds, units, device="cpu"):
+    """Whole-job timing over N ranks: the slowest rank's time and the units
+    all ranks processed (replicas: no collective on the data path, only this
+    one after the timed region).  dist None: one rank, values unchanged."""
+    if dist is None:
+        return float(seconds), float(units)
+    import torch
+    t = torch.tensor([float(seconds)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    u = torch.tensor([float(units)], device=device, dtype=torch.float64)
+    dist.all_reduce(u)
+    return float(t.item()), float(u.item())
+
+
+def reference_runs_here() -> bool:
+    """The reference arm (the CPU oracle) runs on rank 0 only; under torchrun
+    the other ranks exit 0 without work."""
+    return int(os.environ.get("RANK", "0")) == 0
+
+
 def run_reference(args):
     """--impl reference: the FP64 oracle on the host cores, bounded samples."""
-    rank = int(os.environ.get("RANK", "0"))
-    if rank != 0:
+    if not reference_runs_here():
         return 0
     import oracle as O
     O.build()
@@ -312,13 +331,7 @@ def run_gpu(args):
     alive1 = int(a1.sum())
     launches = st1["kernel_launches"] - launches0
     ped_steps = 0.5 * (alive0 + alive1) * args.steps
-    if dist is not None:
-        t = torch.tensor([elapsed], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed = float(t.item())
-        p = torch.tensor([ped_steps], device="cuda", dtype=torch.float64)
-        dist.all_reduce(p)
-        ped_steps = float(p.item())
+    elapsed, ped_steps = reduce_over_ranks(dist, elapsed, ped_steps, "cuda")
 
     # roofline of the dominant kernel: the field gather
     field_s = stage_ms["field"] / 1e3
@@ -349,13 +362,7 @@ def run_gpu(args):
         e2e_peds += int(ha.numpy().sum())
     torch.cuda.synchronize()
     e2e_t = time.perf_counter() - t0
-    if dist is not None:
-        t = torch.tensor([e2e_t], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_t = float(t.item())
-        p = torch.tensor([float(e2e_peds)], device="cuda", dtype=torch.float64)
-        dist.all_reduce(p)
-        e2e_peds = float(p.item())
+    e2e_t, e2e_peds = reduce_over_ranks(dist, e2e_t, e2e_peds, "cuda")
     e2e = {"value": e2e_peds / e2e_t, "unit": "ped-steps/s",
            "h2d_bytes_per_step": n * (8 + 1 + 1 + 1), "d2h_bytes_per_step": n * (8 + 1 + 1),
            "steps": e2e_steps}
