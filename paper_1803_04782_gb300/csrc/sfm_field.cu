@@ -52,7 +52,13 @@ __global__ void __launch_bounds__(kV2Threads, 1)
   const int nf = nfx * (fy1 - fy0);
   // this lane's column and first row inside a footprint
   const int x = SHAPE ? lane : (lane & 15), yl = SHAPE ? 0 : (lane >> 4) * 8;
-  for (int f = blockIdx.x * wpb + warp; f < nf; f += tw) {
+  // large lattices: each CTA takes runs of wpb consecutive footprints (its
+  // warps share records through L1); small ones (under 4 footprints per warp
+  // of the whole grid): footprint f goes to CTA f % gridDim.x, so every SM
+  // gets work.  Either way each footprint is computed once, by one warp.
+  // (both walk footprints with the stride of all warps, tw)
+  const int f0 = nf < 4 * tw ? blockIdx.x + gridDim.x * warp : blockIdx.x * wpb + warp;
+  for (int f = f0; f < nf; f += tw) {
     const int x0 = (f % nfx) * FW, y0 = (fy0 + f / nfx) * FH;
     FarAxis fax{};
     if constexpr (FAR) fax = far_axis(x0 + x, far.inv_s, far.Wc, g.px);
@@ -95,7 +101,9 @@ static void launch_v2(const Geo& g, const int32_t* bin_start, const uint32_t* re
   const int fy0 = store_lo / FH, fy1 = (store_hi + FH - 1) / FH;
   const int nf = ((g.W + FW - 1) / FW) * (fy1 - fy0);
   const int wpb = kV2Threads / 32;
-  int blocks = (nf + wpb - 1) / wpb;
+  // under 4 footprints per warp of a full grid the kernel spreads single
+  // footprints over the CTAs, so a full grid (one CTA per SM) has work
+  int blocks = nf < 4 * wpb * g_num_sms ? nf : (nf + wpb - 1) / wpb;
   if (blocks > g_num_sms) blocks = g_num_sms;
   if (blocks < 1) blocks = 1;
   k_field_v2<SP, SHAPE, FAR><<<blocks, kV2Threads, smem, s>>>(g, bin_start, rec, CT, Fs, out, out_row0,
