@@ -83,7 +83,9 @@ def lib():
         L.orc_commit.restype = C.c_int32
         L.orc_commit.argtypes = [M, P, C.c_int32, P, P, P, P, P]
         L.orc_step.restype = C.c_int32
-        L.orc_step.argtypes = [M, P, P, C.c_int64, C.c_int32, P, P, P, P, P, P, P]
+        L.orc_step.argtypes = [M, P, P, C.c_int64, C.c_int32, P, P, P, P, P, P, P, P, P]
+        L.orc_gate_periods.restype = None
+        L.orc_gate_periods.argtypes = [C.c_int64, C.c_int32, P, P, P]
         _lib = L
     return _lib
 
@@ -219,12 +221,29 @@ class State:
         self.alive = np.ones(scene.n, np.uint8)
         self.t = 0
         self.exited = 0
+        # walk periods (None: every pedestrian active every tick)
+        self.period = None
+        self.phase = None
 
     def copy(self):
         s = State.__new__(State)
         s.xy, s.heading, s.goal = self.xy.copy(), self.heading.copy(), self.goal.copy()
         s.alive, s.t, s.exited = self.alive.copy(), self.t, self.exited
+        s.period = None if self.period is None else self.period.copy()
+        s.phase = None if self.phase is None else self.phase.copy()
         return s
+
+
+def gate_periods(t: int, period, phase, choice):
+    """Walk periods: pedestrians with t mod period != phase stay (choice 0).
+    Returns the gated copy of choice."""
+    choice = np.ascontiguousarray(choice, np.uint8).copy()
+    if period is None:
+        return choice
+    period = np.ascontiguousarray(period, np.uint8)
+    phase = np.ascontiguousarray(phase, np.uint8)
+    lib().orc_gate_periods(int(t), choice.shape[0], _p(period), _p(phase), _p(choice))
+    return choice
 
 
 def step(m: Model, cell, D, st: State):
@@ -235,8 +254,11 @@ def step(m: Model, cell, D, st: State):
     occ = np.empty(m.W * m.H, np.int32)
     choice = np.zeros(max(n, 1), np.uint8)
     won = np.zeros(max(n, 1), np.uint8)
+    per = None if st.period is None else np.ascontiguousarray(st.period, np.uint8)
+    pha = None if st.phase is None else np.ascontiguousarray(st.phase, np.uint8)
     left = lib().orc_step(C.byref(m), _p(cell), _p(D), st.t, n, _p(st.xy), _p(st.heading),
-                          _p(st.goal), _p(st.alive), _p(occ), _p(choice), _p(won))
+                          _p(st.goal), _p(st.alive), _p(occ), _p(choice), _p(won), _p(per),
+                          _p(pha))
     st.t += 1
     st.exited += int(left)
     return choice[:n], won[:n]

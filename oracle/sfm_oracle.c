@@ -360,17 +360,33 @@ int32_t orc_commit(const orc_model* m, const uint8_t* cell, int32_t n, int32_t* 
   return left;
 }
 
+/* ---- walk period (Sec. 2) ----
+ * The paper adopts walk periods from its predecessor to vary walking speeds
+ * under v_max = 1 su per tick, without stating the rule.  Reading: pedestrian
+ * p has a period P_p >= 1 and a phase 0 <= phase_p < P_p, and may move only
+ * on ticks t with t mod P_p = phase_p; on other ticks it stays (choice 0), so
+ * it registers nowhere and keeps its su.  P = 1 everywhere is the plain
+ * model.  period == NULL: every pedestrian is active. */
+void orc_gate_periods(int64_t t, int32_t n, const uint8_t* period, const uint8_t* phase,
+                      uint8_t* choice) {
+  if (!period) return;
+  for (int32_t p = 0; p < n; ++p)
+    if (t % (int64_t)period[p] != (int64_t)phase[p]) choice[p] = 0;
+}
+
 /* ---- one full step (Alg. 1): decide all, vote, commit ----
  * D must hold the guidance distances; occ scratch of W*H int32; choice and won
- * receive the per-pedestrian results.  Returns the number that left. */
+ * receive the per-pedestrian results; period/phase as orc_gate_periods (NULL:
+ * all active).  Returns the number that left. */
 int32_t orc_step(const orc_model* m, const uint8_t* cell, const int32_t* D, int64_t t, int32_t n,
                  int32_t* xy, uint8_t* heading, const uint8_t* goal, uint8_t* alive, int32_t* occ,
-                 uint8_t* choice, uint8_t* won) {
+                 uint8_t* choice, uint8_t* won, const uint8_t* period, const uint8_t* phase) {
   orc_occupancy(m, cell, n, xy, alive, occ);
   double* E = (double*)malloc(sizeof(double) * 9 * (size_t)(n > 0 ? n : 1));
   double* T = (double*)malloc(sizeof(double) * 9 * (size_t)(n > 0 ? n : 1));
   uint8_t* adm = (uint8_t*)malloc(9 * (size_t)(n > 0 ? n : 1));
   orc_decide(m, cell, occ, xy, heading, goal, alive, D, NULL, NULL, n, NULL, choice, E, T, adm);
+  orc_gate_periods(t, n, period, phase, choice);
   orc_vote(m, t, n, xy, alive, choice, won);
   int32_t left = orc_commit(m, cell, n, xy, heading, alive, choice, won);
   free(E);

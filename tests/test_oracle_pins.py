@@ -274,6 +274,69 @@ def test_lone_walker_moves_along_its_direction():
         assert tuple(st.xy[0]) == ((3 + t + 1) % W, 3)
 
 
+def test_walk_period_walker_moves_only_on_its_ticks():
+    """Walk period (Sec. 2, reading: moves only on ticks t with t mod P =
+    phase): the lone east-walker above with period 3 and phase 1 advances one
+    su on ticks 1, 4, 7, ... and stays in between, keeping its heading."""
+    W, H = 40, 7
+    cell = np.zeros((H, W), np.uint8)
+    cell[0, :] = SG.WALL
+    cell[H - 1, :] = SG.WALL
+    sc = SG.Scene("walker", W, H, 1, 0, cell, np.array([[3, 3]], np.int32),
+                  np.array([1], np.uint8), np.array([1], np.uint8), SG._params(r=5))
+    m = O.model(sc)
+    st = O.State(sc)
+    st.period = np.array([3], np.uint8)
+    st.phase = np.array([1], np.uint8)
+    D = O.guidance(m, cell)
+    x = 3
+    for t in range(30):
+        ch, won = O.step(m, cell, D, st)
+        if t % 3 == 1:
+            x = (x + 1) % W
+            assert ch[0] == 1 and won[0] == 1
+        else:
+            assert ch[0] == 0 and won[0] == 0
+        assert tuple(st.xy[0]) == (x, 3) and st.heading[0] == 1
+    assert x == 3 + 10
+
+
+def test_walk_periods_of_one_are_the_plain_model_and_gating_is_exact():
+    """All periods 1: the same run as without periods.  Random periods: a
+    pedestrian moves (or wins a vote) only on its own ticks, never registers
+    otherwise, and its moves over T ticks are at most its active ticks."""
+    sc = SG.random_scene(48, 40, 500, r=5, seed=81, obstacles=3, exits=("east",),
+                         goal_mode="mixed", heading_mode="random")
+    m = O.model(sc)
+    D = O.guidance(m, sc.cell)
+    a, b = O.State(sc), O.State(sc)
+    b.period = np.ones(sc.n, np.uint8)
+    b.phase = np.zeros(sc.n, np.uint8)
+    for _ in range(8):
+        ca, wa = O.step(m, sc.cell, D, a)
+        cb, wb = O.step(m, sc.cell, D, b)
+        np.testing.assert_array_equal(ca, cb)
+        np.testing.assert_array_equal(a.xy, b.xy)
+    rng = np.random.default_rng(5)
+    st = O.State(sc)
+    st.period = rng.integers(1, 6, size=sc.n).astype(np.uint8)
+    st.phase = (rng.integers(0, 255, size=sc.n) % st.period).astype(np.uint8)
+    moves = np.zeros(sc.n, int)
+    T = 15
+    for t in range(T):
+        xy0 = st.xy.copy()
+        ch, won = O.step(m, sc.cell, D, st)
+        active = (t % st.period.astype(int)) == st.phase
+        moved = np.any(st.xy != xy0, axis=1)
+        assert not np.any(moved & ~active)
+        assert not np.any((ch > 0) & ~active) and not np.any((won > 0) & ~active)
+        moves += moved
+    n_active = np.array([sum(1 for t in range(T) if t % p == f) for p, f in zip(st.period, st.phase)])
+    assert np.all(moves <= n_active) and moves.sum() > 0
+    gated = O.gate_periods(4, st.period, st.phase, np.full(sc.n, 3, np.uint8))
+    np.testing.assert_array_equal(gated > 0, (4 % st.period.astype(int)) == st.phase)
+
+
 def test_decision_energy_matches_brute_force_field():
     sc = SG.random_scene(21, 19, 45, r=4, seed=71, obstacles=2, goal_mode="mixed",
                          heading_mode="random")
