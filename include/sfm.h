@@ -164,6 +164,18 @@ sfm_status sfm_compute_field(sfm_ctx* ctx);
  * nobody. */
 sfm_status sfm_autotune(sfm_ctx* ctx, int32_t* shape_out);
 
+/* Walk periods (Sec. 2 of the paper, which adopts them to vary walking
+ * speeds under a maximal speed of 1 su per tick): pedestrian p may move only
+ * on ticks t with t mod period[p] == phase[p] (t = the context's tick
+ * counter, see sfm_set_time) and stays on the others, registering nowhere.
+ * period, phase: n bytes each (n of the last sfm_place), host or device per
+ * on_device; 1 <= period, phase < period, else SFM_EINVAL and nothing
+ * changes.  period == NULL switches periods off (every pedestrian active,
+ * the plain model).  Every sfm_place switches them off; call this after it.
+ * Synchronising. */
+sfm_status sfm_set_walk_periods(sfm_ctx* ctx, const uint8_t* period, const uint8_t* phase,
+                                int32_t on_device);
+
 /* How the pedestrians are sorted into bins each tick (the bin records and
  * every result are identical either way): 1 = by scanning the per-su class
  * grid (cost follows the lattice area), 2 = from the pedestrian list with

@@ -33,7 +33,8 @@ EXPORTS = [
     "sfm_set_time", "sfm_step", "sfm_compute_field", "sfm_sync", "sfm_read_field",
     "sfm_compute_field_into", "sfm_read_static_field", "sfm_read_guidance", "sfm_read_peds",
     "sfm_read_decisions", "sfm_stats", "sfm_set_timing", "sfm_stage_times",
-    "sfm_autotune", "sfm_set_field_footprint", "sfm_set_binning", "sfm_field_noalloc", "sfm_batch_create", "sfm_batch_place", "sfm_batch_offsets",
+    "sfm_autotune", "sfm_set_field_footprint", "sfm_set_binning", "sfm_set_walk_periods",
+    "sfm_field_noalloc", "sfm_batch_create", "sfm_batch_place", "sfm_batch_offsets",
     "sfm_batch_autotune", "sfm_batch_test_missing_ctas", "sfm_surrogate_nparams",
     "sfm_surrogate_create", "sfm_surrogate_destroy", "sfm_surrogate_last_error",
     "sfm_surrogate_set_params", "sfm_surrogate_get_params", "sfm_surrogate_grad",
@@ -115,6 +116,7 @@ def lib():
             "sfm_autotune": (C.c_int, [P, P]),
             "sfm_set_field_footprint": (C.c_int, [P, I32]),
             "sfm_set_binning": (C.c_int, [P, I32]),
+            "sfm_set_walk_periods": (C.c_int, [P, P, P, I32]),
             "sfm_stage_times": (C.c_int, [P, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
             "sfm_field_noalloc": (C.c_int, [C.POINTER(Lattice), C.POINTER(Params), I32, P, P, P,
                                             P, P, P]),
@@ -461,6 +463,18 @@ class Sim:
 
     def autotune(self):
         return sfm_autotune(self.ctx)
+
+    def set_walk_periods(self, period=None, phase=None):
+        """Walk periods: pedestrian p moves only on ticks t with t % period[p]
+        == phase[p]; None switches them off.  Reset by every placement."""
+        if period is None:
+            _check(self.ctx, lib().sfm_set_walk_periods(self.ctx, None, None, 0))
+            return
+        self._period = np.ascontiguousarray(period, np.uint8)
+        self._phase = np.ascontiguousarray(phase, np.uint8)
+        _check(self.ctx, lib().sfm_set_walk_periods(
+            self.ctx, self._period.ctypes.data_as(C.c_void_p),
+            self._phase.ctypes.data_as(C.c_void_p), 0))
 
     def set_binning(self, mode: str):
         """"auto", "grid" (scan the class grid) or "peds" (from the pedestrian list)."""

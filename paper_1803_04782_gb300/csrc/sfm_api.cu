@@ -179,7 +179,7 @@ void run_tick(sfm_ctx* c) {
     StageScope sc(c, SFM_STAGE_DECIDE);
     launch_decide(c->n, c->rec_id, c->bin_start, 0, nbins, c->xy, c->heading, c->goal, c->cell,
                   c->ocls, c->D, c->F, 0, -1, -1, 0, 0, g.H, g, c->prm.beta, tb, c->choice,
-                  c->stream);
+                  c->stream, c->walk());
     if (c->n > 0) ++c->launches;
   } else {
     for (int b = 0; b < c->bands; ++b) {
@@ -196,7 +196,7 @@ void run_tick(sfm_ctx* c) {
       launch_decide(c->n, c->rec_id, c->bin_start, (ya / kBin) * g.nbx,
                     ((yb + kBin - 1) / kBin) * g.nbx, c->xy, c->heading, c->goal, c->cell, c->ocls,
                     c->D, c->band_buf, 1, lo, hi, yb - ya + 1, ya, yb, g, c->prm.beta, tb,
-                    c->choice, c->stream);
+                    c->choice, c->stream, c->walk());
       if (c->n > 0) ++c->launches;
     }
   }
@@ -465,6 +465,8 @@ sfm_status sfm_place(sfm_ctx* ctx, int32_t n, const int32_t* xy, const uint8_t* 
     dfree(ctx, ctx->rec_id);
     dfree(ctx, ctx->bin_slot);
     dfree(ctx, ctx->bin_key);
+    dfree(ctx, ctx->period);
+    dfree(ctx, ctx->phase);
     ctx->xy = nullptr;
     ctx->cap = 0;
     TRY(dalloc(ctx, &ctx->xy, (size_t)n));
@@ -477,6 +479,8 @@ sfm_status sfm_place(sfm_ctx* ctx, int32_t n, const int32_t* xy, const uint8_t* 
     TRY(dalloc(ctx, &ctx->rec_id, (size_t)n));
     TRY(dalloc(ctx, &ctx->bin_slot, (size_t)n));
     TRY(dalloc(ctx, &ctx->bin_key, (size_t)n));
+    TRY(dalloc(ctx, &ctx->period, (size_t)n));
+    TRY(dalloc(ctx, &ctx->phase, (size_t)n));
     ctx->cap = n;
   }
   if (ctx->cap == 0) {
@@ -490,9 +494,12 @@ sfm_status sfm_place(sfm_ctx* ctx, int32_t n, const int32_t* xy, const uint8_t* 
     TRY(dalloc(ctx, &ctx->rec_id, 1));
     TRY(dalloc(ctx, &ctx->bin_slot, 1));
     TRY(dalloc(ctx, &ctx->bin_key, 1));
+    TRY(dalloc(ctx, &ctx->period, 1));
+    TRY(dalloc(ctx, &ctx->phase, 1));
     ctx->cap = 1;
   }
   ctx->placed = false;
+  ctx->walk_periods = false;  // a placement starts with every pedestrian active
   ctx->n = n;
   const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   if (n > 0) {
@@ -652,6 +659,37 @@ sfm_status sfm_autotune(sfm_ctx* ctx, int32_t* shape_out) {
   drop_graph(ctx);
   if (shape_out) *shape_out = best_shape;
   return check_flags(ctx);
+}
+
+sfm_status sfm_set_walk_periods(sfm_ctx* ctx, const uint8_t* period, const uint8_t* phase,
+                                int32_t on_device) {
+  if (!ctx) return SFM_EINVAL;
+  if (ctx->batch) return fail(ctx, SFM_EINVAL, "walk periods are per single lattice");
+  if (!ctx->placed) return fail(ctx, SFM_ESTATE, "walk periods need placed pedestrians");
+  drop_graph(ctx);
+  if (!period) {
+    ctx->walk_periods = false;
+    return SFM_OK;
+  }
+  if (!phase) return fail(ctx, SFM_EINVAL, "phase array missing");
+  const int n = ctx->n;
+  std::vector<uint8_t> hp((size_t)n), hf((size_t)n);
+  if (n > 0) {
+    const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost;
+    CU(cudaMemcpy(hp.data(), period, (size_t)n, k));
+    CU(cudaMemcpy(hf.data(), phase, (size_t)n, k));
+  }
+  for (int p = 0; p < n; ++p)
+    if (hp[p] < 1 || hf[p] >= hp[p])
+      return fail(ctx, SFM_EINVAL, "pedestrian %d: period %d, phase %d (need 1 <= period, phase < period)",
+                  p, (int)hp[p], (int)hf[p]);
+  if (n > 0) {
+    CU(cudaMemcpyAsync(ctx->period, hp.data(), (size_t)n, cudaMemcpyHostToDevice, ctx->stream));
+    CU(cudaMemcpyAsync(ctx->phase, hf.data(), (size_t)n, cudaMemcpyHostToDevice, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+  }
+  ctx->walk_periods = true;
+  return SFM_OK;
 }
 
 sfm_status sfm_set_binning(sfm_ctx* ctx, int32_t mode) {

@@ -60,6 +60,8 @@ struct sfm_ctx {
   int n = 0, cap = 0;
   int2* xy = nullptr;
   uint8_t *heading = nullptr, *goal = nullptr, *alive = nullptr, *choice = nullptr, *won = nullptr;
+  uint8_t *period = nullptr, *phase = nullptr;  // walk periods (used when walk_periods)
+  bool walk_periods = false;
   bool placed = false;
   int64_t t = 0;
   // banded mode
@@ -95,6 +97,15 @@ struct sfm_ctx {
     tb.CT = CT;
     tb.shape = field_shape;
     return tb;
+  }
+  sfm::WalkPeriods walk() const {
+    sfm::WalkPeriods wp;
+    if (walk_periods) {
+      wp.period = period;
+      wp.phase = phase;
+      wp.ctr = ctr;
+    }
+    return wp;
   }
 };
 

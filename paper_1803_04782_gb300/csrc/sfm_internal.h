@@ -165,11 +165,21 @@ void launch_class_tables(int r, const sfm_params& p, float* T, cudaStream_t s,
 // through rec_id (n bounds the launch).  F rows: lattice rows [y_lo, y_hi) at
 // buffer row (y - y_lo + main_off), lattice row lo_row at buffer row 0 and
 // hi_row at buffer row hi_off.
+// Walk periods (Sec. 2): pedestrian p may move only on ticks t with
+// t mod period[p] = phase[p] (t = ctr->t, read on the device); period ==
+// nullptr: every pedestrian is active.
+struct WalkPeriods {
+  const uint8_t* period = nullptr;
+  const uint8_t* phase = nullptr;
+  const Counters* ctr = nullptr;
+};
+
 void launch_decide(int n, const int32_t* rec_id, const int32_t* bin_start, int b_lo, int b_hi,
                    const int2* xy, const uint8_t* heading, const uint8_t* goal,
                    const uint8_t* cell, const uint8_t* ocls, const int32_t* D, const float* F,
                    int main_off, int lo_row, int hi_row, int hi_off, int y_lo, int y_hi,
-                   const Geo& g, float beta, const Tables& tb, uint8_t* choice, cudaStream_t s);
+                   const Geo& g, float beta, const Tables& tb, uint8_t* choice, cudaStream_t s,
+                   const WalkPeriods& wp = WalkPeriods());
 void launch_vote(int n, const int32_t* rec_id, const int32_t* bin_start, const int2* xy,
                  const uint8_t* choice, const int32_t* occ, const Geo& g, uint64_t seed,
                  Counters* ctr, uint8_t* won, cudaStream_t s);

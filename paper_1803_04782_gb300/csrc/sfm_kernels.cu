@@ -681,13 +681,19 @@ __global__ void k_decide(const int32_t* __restrict__ rec_id, const int32_t* __re
                          const int32_t* __restrict__ D, const float* __restrict__ F, int main_off,
                          int lo_row, int hi_row, int hi_off, int y_lo, int y_hi, Geo g,
                          float beta, const float* __restrict__ own,
-                         const float* __restrict__ dirdot, uint8_t* __restrict__ choice) {
+                         const float* __restrict__ dirdot, uint8_t* __restrict__ choice,
+                         WalkPeriods wp) {
   // grid-stride over the records of bins [b_lo, b_hi): a band's launch needs
   // no more blocks than the GPU holds, whatever its share of the crowd
   const int end = bin_start[b_hi];
+  const long long t = wp.period ? wp.ctr->t : 0;
   for (int i = bin_start[b_lo] + blockIdx.x * blockDim.x + threadIdx.x; i < end;
        i += gridDim.x * blockDim.x) {
     const int p = rec_id[i];
+    if (wp.period && t % wp.period[p] != wp.phase[p]) {
+      choice[p] = 0;  // not this pedestrian's tick: it stays
+      continue;
+    }
     choice[p] = decide_one(p, g, xy, heading, goal, cell, ocls, D, F, main_off, lo_row, hi_row,
                            hi_off, y_lo, y_hi, beta, own, dirdot);
   }
@@ -697,7 +703,8 @@ void launch_decide(int n, const int32_t* rec_id, const int32_t* bin_start, int b
                    const int2* xy, const uint8_t* heading, const uint8_t* goal,
                    const uint8_t* cell, const uint8_t* ocls, const int32_t* D, const float* F,
                    int main_off, int lo_row, int hi_row, int hi_off, int y_lo, int y_hi,
-                   const Geo& g, float beta, const Tables& tb, uint8_t* choice, cudaStream_t s) {
+                   const Geo& g, float beta, const Tables& tb, uint8_t* choice, cudaStream_t s,
+                   const WalkPeriods& wp) {
   if (n <= 0 || b_hi <= b_lo) return;
   static int max_blocks = 0;
   if (!max_blocks) {
@@ -709,7 +716,7 @@ void launch_decide(int n, const int32_t* rec_id, const int32_t* bin_start, int b
   const int blocks = cdiv(n, 256) < max_blocks ? cdiv(n, 256) : max_blocks;
   k_decide<<<blocks, 256, 0, s>>>(rec_id, bin_start, b_lo, b_hi, xy, heading, goal, cell,
                                         ocls, D, F, main_off, lo_row, hi_row, hi_off, y_lo, y_hi,
-                                        g, beta, tb.own, tb.dirdot, choice);
+                                        g, beta, tb.own, tb.dirdot, choice, wp);
 }
 
 // ------------------------------------------------------------ S4: vote

@@ -603,10 +603,15 @@ __global__ void k_sur_decide(const int32_t* __restrict__ rec_id, const int32_t* 
                              const float* __restrict__ dirdot, float delta,
                              uint8_t* __restrict__ choice, int32_t* __restrict__ flag_list,
                              int32_t* __restrict__ nflag, const uint8_t* __restrict__ ref,
-                             unsigned long long* __restrict__ raw_flips) {
+                             unsigned long long* __restrict__ raw_flips, WalkPeriods wp) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   bool differs = false;
-  if (i < bin_start[nbins]) {
+  const long long t = wp.period ? wp.ctr->t : 0;
+  if (i < bin_start[nbins] && wp.period &&
+      t % wp.period[rec_id[i]] != wp.phase[rec_id[i]]) {
+    choice[rec_id[i]] = 0;  // not this pedestrian's tick (walk period): it stays
+    differs = ref && ref[rec_id[i]] != 0;
+  } else if (i < bin_start[nbins]) {
     const int p = rec_id[i];
     const int2 q = xy[p];
     int cx[3], ry[3];
@@ -1078,7 +1083,7 @@ void surrogate_decide(sfm_surrogate* S, sfm_ctx* ctx, uint8_t* choice, const uin
   k_sur_decide<<<cdiv(ctx->n, 256), 256, 0, st>>>(
       ctx->rec_id, ctx->bin_start, nbins, g, ctx->xy, ctx->heading, ctx->goal, ctx->cell, ctx->ocls,
       ctx->D, S->Fsur, ctx->prm.beta, tb.own, tb.dirdot, S->delta, choice, S->flag_list, S->nflag,
-      ref, raw_flips);
+      ref, raw_flips, ctx->walk());
   const int SP = class_table_stride(g.r);
   const int TS = (2 * g.r + 1 + 2 * kFieldPadRows) * SP;
   const size_t smem = (kTableGuard + 4 * (size_t)TS) * sizeof(float) +
@@ -1350,7 +1355,7 @@ sfm_status sfm_surrogate_eval(sfm_surrogate* S, sfm_ctx* ctx, sfm_surrogate_repo
   ctx_field_rows(ctx, ctx->F, 0, g.H, 0, false);
   launch_decide(ctx->n, ctx->rec_id, ctx->bin_start, 0, nbins, ctx->xy, ctx->heading, ctx->goal,
                 ctx->cell, ctx->ocls, ctx->D, ctx->F, 0, -1, -1, 0, 0, g.H, g, ctx->prm.beta, tb,
-                ctx->choice, st);
+                ctx->choice, st, ctx->walk());
   SCU(cudaEventRecord(e1, st));
   // surrogate: bins, field, decisions with the fallback (into choice2)
   SCU(cudaMemsetAsync(S->cnt, 0, 2 * sizeof(unsigned long long), st));

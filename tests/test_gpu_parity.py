@@ -166,6 +166,48 @@ def test_free_running_room_100x100_r10_50_ticks():
         assert s["exited"] == orc.st.exited
 
 
+@pytest.mark.parametrize("bands", [1, 4])
+def test_walk_periods_free_running_against_the_oracle(bands):
+    """Walk periods (Sec. 2) drawn in 1..5 with random phases on a room of
+    mixed exit-seekers and walkers: the GPU runs 20 ticks on its own, banded
+    or not, and stays identical to the oracle, which gates each pedestrian
+    to its own ticks; inactive pedestrians stay and register nowhere."""
+    sc = SG.random_scene(200, 160, 3000, r=12, seed=131, obstacles=4, exits=("east", "north"),
+                         goal_mode="mixed", heading_mode="random")
+    rng = np.random.default_rng(7)
+    period = rng.integers(1, 6, size=sc.n).astype(np.uint8)
+    phase = (rng.integers(0, 255, size=sc.n) % period).astype(np.uint8)
+    orc = OracleRun(sc)
+    orc.st.period, orc.st.phase = period, phase
+    budget = sfm.band_budget(sc.W, sc.H, 32) if bands > 1 else 0
+    with sfm.Sim(sc, hbm_budget_bytes=budget) as sim:
+        assert (sim.stats()["bands"] > 1) == (bands > 1)
+        sim.set_walk_periods(period, phase)
+        for t in range(20):
+            sim.step(1)
+            Fo, So = orc.field()
+            ch_o, E, T, adm = orc.decide(Ffull=Fo.ravel(), Sfull=So.ravel())
+            active = (t % period.astype(int)) == phase
+            ch_o = O.gate_periods(orc.st.t, period, phase, ch_o)
+            ch_g, won_g = sim.decisions()
+            alive = orc.st.alive.astype(bool)
+            assert not np.any(ch_g[alive & ~active]), f"inactive pedestrian moved at tick {t}"
+            assert compare_choices(ch_g, ch_o, E, T, adm) == 0, f"tie flip at tick {t}"
+            won_o, _ = orc.advance(ch_o)
+            np.testing.assert_array_equal(won_g, won_o)
+            for x, y in zip(sim.peds(), (orc.st.xy, orc.st.heading, orc.st.alive)):
+                np.testing.assert_array_equal(x, y)
+        # switching periods off again is the plain model; bad periods are refused
+        sim.set_walk_periods(None)
+        bad = period.copy()
+        bad[0] = 0
+        with pytest.raises(sfm.SfmError) as e:
+            sim.set_walk_periods(bad, phase)
+        assert e.value.status == sfm.SFM_EINVAL
+        with pytest.raises(sfm.SfmError):
+            sim.set_walk_periods(period, period)  # phase == period
+
+
 @pytest.mark.parametrize("periodic", [0, 1])
 def test_banded_field_is_bitwise_the_unbanded_field(periodic):
     """Divide-and-conquer (Eq. 1): row bands under an HBM budget give exactly
