@@ -634,6 +634,80 @@ def run_surrogate_eval(args):
     return 0
 
 
+def run_paper_sweep(args):
+    """The paper's experiment shapes (Sec. 5) on one GB300: a periodic
+    1000x1000 lattice, density 0.5 (500 000 pedestrians), 8 flow directions.
+    paper-windows: field geometries 7x7 ... 77x77 (Table III, r = 3 ... 38);
+    paper-periods: 7x7 fields with walk periods uniform in [1, P_max],
+    P_max = 1 ... 11 (Table IV).  Each case: autotuned footprint, warm-up,
+    then ticks replayed as CUDA graphs timed with CUDA events, and a second
+    pass with per-stage events for the field time.  The paper's own times
+    (seconds per 1000 ticks, unnamed hardware) are listed beside as context."""
+    import torch
+    import paper_1803_04782_gb300 as sfm
+    import scenegen as SG
+    from paper_1803_04782_gb300 import build as B
+
+    B.build()
+    sfm.lib()
+    stream = torch.cuda.current_stream()
+    if args.workload == "paper-windows":
+        cases = [(r, 1) for r in (3, 10, 17, 24, 31, 38)]
+        paper_s = [62, 317, 738, 1424, 2187, 3238]
+        what = "Table III: field geometry (2r+1)^2, 1000^2 su, density 0.5, 8 directions"
+    else:
+        cases = [(3, p) for p in (1, 3, 5, 7, 9, 11)]
+        paper_s = [62, 64, 64, 63, 62, 62]
+        what = "Table IV: maximal walk period, 1000^2 su, density 0.5, 8 directions, 7x7 fields"
+    ticks = max(5, min(args.steps, 50))
+    rows = []
+    for (r, pmax), ps in zip(cases, paper_s):
+        sc = SG.paper_scene(side=1000, density=0.5, ndir=8, r=r)
+        with sfm.Sim(sc, stream=stream) as sim:
+            fp = sim.autotune()
+            if pmax > 1:
+                per, pha = SG.walk_periods(sc.n, pmax)
+                sim.set_walk_periods(per, pha)
+            sim.step(args.warmup)
+            torch.cuda.synchronize()
+            xy0, _, a0 = sim.peds()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            sim.step(ticks)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / ticks
+            sim.set_timing(True)
+            sim.stage_times()
+            sim.step(ticks)
+            st_ms, nt = sim.stage_times()
+            sim.set_timing(False)
+            pairs = pair_count(sc, xy0, a0)
+            field_ms = st_ms["field"] / max(1, nt)
+            rows.append({"r": r, "window": (2 * r + 1) ** 2, "walk_period_max": pmax,
+                         "footprint": fp, "ms_per_tick": ms,
+                         "ped_steps_per_s": int(a0.sum()) / (ms / 1e3),
+                         "su_updates_per_s": sc.W * sc.H / (ms / 1e3),
+                         "field_ms": field_ms,
+                         "field_tflops": FLOPS_PER_PAIR * pairs / (field_ms / 1e3) / 1e12,
+                         "paper_ms_per_tick": ps, "paper_over_this": ps / ms})
+    area = np.array([row["window"] for row in rows], float)
+    tms = np.array([row["ms_per_tick"] for row in rows])
+    slope, icpt = np.polyfit(area, tms, 1) if len(set(area)) > 1 else (0.0, float(tms.mean()))
+    pred = slope * area + icpt
+    r2 = 1.0 - float(((tms - pred) ** 2).sum() / max(((tms - tms.mean()) ** 2).sum(), 1e-30))
+    line = {"metric": "pedestrian-steps/s", "value": rows[0]["ped_steps_per_s"],
+            "unit": "ped-steps/s", "n_gpus": 1, "steps": ticks, "warmup": args.warmup,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": {"workload": what},
+            "rows": rows,
+            "time_vs_window_area": {"ms_per_window_su": slope, "ms_intercept": icpt,
+                                    "r2": r2 if args.workload == "paper-windows" else None}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -642,7 +716,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="floor",
                     choices=["floor", "floor-small", "corridor", "room", "batch", "batch-small",
-                             "surrogate", "surrogate-eval"])
+                             "surrogate", "surrogate-eval", "paper-windows", "paper-periods"])
     ap.add_argument("--bands", type=int, default=4,
                     help="row bands of the divide-and-conquer field pass (1 = unbanded)")
     ap.add_argument("--e2e-steps", type=int, default=10)
@@ -658,6 +732,8 @@ def main():
         return run_surrogate(args)
     if args.workload == "surrogate-eval":
         return run_surrogate_eval(args)
+    if args.workload.startswith("paper-"):
+        return run_paper_sweep(args)
     return run_gpu(args)
 
 

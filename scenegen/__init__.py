@@ -336,6 +336,32 @@ def training_canvas(side=4096, r=40, tile=128, rho_lo=0.002, rho_hi=0.25, seed=5
                  _params(r=r, seed=seed), 1)
 
 
+FLOW_GOALS = {1: (1,), 2: (1, 5), 4: (1, 3, 5, 7), 8: tuple(range(1, 9))}
+
+
+def paper_scene(side=1000, density=0.5, ndir=8, r=3, seed=11, name="paper") -> Scene:
+    """The paper's experiment shape (Sec. 5): a periodic side x side lattice
+    without walls or exits, round(density * side^2) pedestrians uniform on it,
+    fixed-direction walkers split evenly over `ndir` flow directions (1: east;
+    2: east and west; 4: the axes; 8: every direction), heading = direction."""
+    rng = np.random.default_rng(seed)
+    cell = np.zeros((side, side), np.uint8)
+    n = int(round(density * side * side))
+    xy = place_uniform(rng, np.ones((side, side), bool), n)
+    dirs = np.array(FLOW_GOALS[ndir], np.uint8)
+    goal = dirs[np.arange(n) % len(dirs)]
+    rng.shuffle(goal)
+    return Scene(name, side, side, 1, 1, cell, xy, goal.copy(), goal, _params(r=r))
+
+
+def walk_periods(n, p_max, seed=12):
+    """Walk periods uniform in [1, p_max] and phases uniform in [0, period)."""
+    rng = np.random.default_rng(seed)
+    period = rng.integers(1, p_max + 1, size=n).astype(np.uint8)
+    phase = (rng.integers(0, 1 << 16, size=n) % period).astype(np.uint8)
+    return period, phase
+
+
 def config(i: int, **kw):
     """The five evaluation configurations by number (1-based)."""
     if i == 1:
