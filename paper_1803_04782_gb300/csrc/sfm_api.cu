@@ -513,21 +513,16 @@ sfm_status sfm_place(sfm_ctx* ctx, int32_t n, const int32_t* xy, const uint8_t* 
     CU(cudaMemsetAsync(ctx->choice, 0, n, s));
     CU(cudaMemsetAsync(ctx->won, 0, n, s));
   }
-  // reset per-placement counters and flags, keep the tick counter
-  CU(cudaStreamSynchronize(s));
-  Counters h;
-  CU(cudaMemcpy(&h, ctx->ctr, sizeof(h), cudaMemcpyDeviceToHost));
-  h.moved = 0;
-  h.exited = 0;
-  h.max_registrants = 0;
-  h.err = 0;
-  CU(cudaMemcpy(ctx->ctr, &h, sizeof(h), cudaMemcpyHostToDevice));
+  // reset per-placement counters and flags on the stream, keep the tick counter
+  launch_reset_counters(ctx->ctr, s);
+  ++ctx->launches;
   launch_place_scatter(n, ctx->xy, ctx->heading, ctx->goal, ctx->alive, ctx->cell, g, ctx->occ,
                        ctx->ocls, ctx->ctr, s);
   if (n > 0) ++ctx->launches;
+  Counters h;
+  CU(cudaMemcpyAsync(&h, ctx->ctr, sizeof(h), cudaMemcpyDeviceToHost, s));
   CU(cudaStreamSynchronize(s));
   CU(cudaGetLastError());
-  CU(cudaMemcpy(&h, ctx->ctr, sizeof(h), cudaMemcpyDeviceToHost));
   if (h.err) {
     const uint32_t flags = h.err;
     const size_t nsu = (size_t)g.W * g.H;

@@ -142,6 +142,7 @@ void launch_bins_from_peds(const Geo& g, int n, const int2* xy, const uint8_t* a
                            const uint8_t* heading, int32_t* count, int32_t* start,
                            int32_t* scan_tmp, int32_t* slot, uint32_t* key, uint32_t* rec,
                            int32_t* rec_id, cudaStream_t s);
+void launch_reset_counters(Counters* ctr, cudaStream_t s);
 void launch_clear_dead(int n, const uint8_t* alive, uint8_t* choice, uint8_t* won, cudaStream_t s);
 
 // Field gather; stores lattice rows y in [store_lo, store_hi) at

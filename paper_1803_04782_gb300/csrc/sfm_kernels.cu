@@ -250,6 +250,16 @@ void launch_place_clear(int n, const int2* xy, const uint8_t* alive, const Geo& 
   k_place_clear<<<cdiv(n, 256), 256, 0, s>>>(n, xy, alive, g, occ, ocls);
 }
 
+// per-placement counters and flags back to zero (the tick counter stays)
+__global__ void k_reset_counters(Counters* ctr) {
+  ctr->moved = 0;
+  ctr->exited = 0;
+  ctr->max_registrants = 0;
+  ctr->err = 0;
+}
+
+void launch_reset_counters(Counters* ctr, cudaStream_t s) { k_reset_counters<<<1, 1, 0, s>>>(ctr); }
+
 void launch_place_scatter(int n, const int2* xy, const uint8_t* heading, const uint8_t* goal,
                           const uint8_t* alive, const uint8_t* cell, const Geo& g, int32_t* occ,
                           uint8_t* ocls, Counters* ctr, cudaStream_t s) {
