@@ -77,13 +77,17 @@ def lib():
         L.orc_prio.restype = C.c_uint64
         L.orc_prio.argtypes = [C.c_uint64, C.c_int64, C.c_int64]
         L.orc_decide.restype = None
-        L.orc_decide.argtypes = [M, P, P, P, P, P, P, P, P, P, C.c_int64, P, P, P, P, P]
+        L.orc_decide.argtypes = [M, P, P, P, P, P, P, P, P, P, C.c_int64, P, P, P, P, P, P, P, P]
+        L.orc_cover.restype = C.c_int64
+        L.orc_cover.argtypes = [M, P, C.c_int32, P, P, P, P, P]
+        L.orc_vote_sized.restype = C.c_int32
+        L.orc_vote_sized.argtypes = [M, C.c_int64, C.c_int32, P, P, P, P, P, P]
         L.orc_vote.restype = C.c_int32
         L.orc_vote.argtypes = [M, C.c_int64, C.c_int32, P, P, P, P]
         L.orc_commit.restype = C.c_int32
-        L.orc_commit.argtypes = [M, P, C.c_int32, P, P, P, P, P]
+        L.orc_commit.argtypes = [M, P, C.c_int32, P, P, P, P, P, P, P]
         L.orc_step.restype = C.c_int32
-        L.orc_step.argtypes = [M, P, P, C.c_int64, C.c_int32, P, P, P, P, P, P, P, P, P]
+        L.orc_step.argtypes = [M, P, P, C.c_int64, C.c_int32, P, P, P, P, P, P, P, P, P, P, P]
         L.orc_gate_periods.restype = None
         L.orc_gate_periods.argtypes = [C.c_int64, C.c_int32, P, P, P]
         _lib = L
@@ -171,8 +175,24 @@ def prio(seed: int, t: int, pid: int) -> int:
     return int(lib().orc_prio(seed & (2**64 - 1), t, pid))
 
 
-def decide(m: Model, cell, occ, xy, heading, goal, alive, D, req=None, Ffull=None, Sfull=None):
-    """Decision of the requested pedestrians: (choice, E[.,9], T[.,9], admissible[.,9])."""
+def cover(m: Model, cell, xy, alive, w, h):
+    """Multi-su occupancy: [H, W] int32 holding p on every su of p's w x h
+    rectangle (-1 elsewhere), and the number of placement violations."""
+    cell = np.ascontiguousarray(cell, np.uint8)
+    xy = np.ascontiguousarray(xy, np.int32)
+    alive = None if alive is None else np.ascontiguousarray(alive, np.uint8)
+    w = np.ascontiguousarray(w, np.uint8)
+    h = np.ascontiguousarray(h, np.uint8)
+    cov = np.empty(m.W * m.H, np.int32)
+    bad = lib().orc_cover(C.byref(m), _p(cell), xy.shape[0], _p(xy), _p(alive), _p(w), _p(h),
+                          _p(cov))
+    return cov, int(bad)
+
+
+def decide(m: Model, cell, occ, xy, heading, goal, alive, D, req=None, Ffull=None, Sfull=None,
+           cov=None, w=None, h=None):
+    """Decision of the requested pedestrians: (choice, E[.,9], T[.,9], admissible[.,9]).
+    cov/w/h: multi-su pedestrians (admissibility over the su a move enters)."""
     cell = np.ascontiguousarray(cell, np.uint8)
     occ = np.ascontiguousarray(occ, np.int32)
     xy = np.ascontiguousarray(xy, np.int32)
@@ -189,26 +209,43 @@ def decide(m: Model, cell, occ, xy, heading, goal, alive, D, req=None, Ffull=Non
     E = np.zeros((max(n, 1), 9), np.float64)
     T = np.zeros((max(n, 1), 9), np.float64)
     adm = np.zeros((max(n, 1), 9), np.uint8)
+    if cov is not None:
+        cov = np.ascontiguousarray(cov, np.int32)
+        w = np.ascontiguousarray(w, np.uint8)
+        h = np.ascontiguousarray(h, np.uint8)
     lib().orc_decide(C.byref(m), _p(cell), _p(occ), _p(xy), _p(heading), _p(goal), _p(alive),
-                     _p(D), _p(Ffull), _p(Sfull), n, _p(reqa), _p(choice), _p(E), _p(T), _p(adm))
+                     _p(D), _p(Ffull), _p(Sfull), n, _p(reqa), _p(choice), _p(E), _p(T), _p(adm),
+                     _p(cov), _p(w), _p(h))
     return choice[:n], E[:n], T[:n], adm[:n]
 
 
-def vote(m: Model, t: int, xy, alive, choice):
+def vote(m: Model, t: int, xy, alive, choice, w=None, h=None):
+    """Winners of the tick's moves (w/h: multi-su pedestrians, claims)."""
     xy = np.ascontiguousarray(xy, np.int32)
     alive = np.ascontiguousarray(alive, np.uint8)
     choice = np.ascontiguousarray(choice, np.uint8)
     won = np.zeros(max(xy.shape[0], 1), np.uint8)
-    maxc = lib().orc_vote(C.byref(m), t, xy.shape[0], _p(xy), _p(alive), _p(choice), _p(won))
+    if w is not None:
+        w = np.ascontiguousarray(w, np.uint8)
+        h = np.ascontiguousarray(h, np.uint8)
+        maxc = lib().orc_vote_sized(C.byref(m), t, xy.shape[0], _p(xy), _p(alive), _p(choice),
+                                    _p(w), _p(h), _p(won))
+    else:
+        maxc = lib().orc_vote(C.byref(m), t, xy.shape[0], _p(xy), _p(alive), _p(choice),
+                              _p(won))
     return won[:xy.shape[0]], int(maxc)
 
 
-def commit(m: Model, cell, xy, heading, alive, choice, won):
-    """Apply the moves in place; returns the number of pedestrians that left."""
+def commit(m: Model, cell, xy, heading, alive, choice, won, w=None, h=None):
+    """Apply the moves in place; returns the number of pedestrians that left
+    (w/h: multi-su pedestrians leave when their new rectangle meets an EXIT)."""
     cell = np.ascontiguousarray(cell, np.uint8)
+    if w is not None:
+        w = np.ascontiguousarray(w, np.uint8)
+        h = np.ascontiguousarray(h, np.uint8)
     return int(lib().orc_commit(C.byref(m), _p(cell), xy.shape[0], _p(xy), _p(heading),
                                 _p(alive), _p(np.ascontiguousarray(choice, np.uint8)),
-                                _p(np.ascontiguousarray(won, np.uint8))))
+                                _p(np.ascontiguousarray(won, np.uint8)), _p(w), _p(h)))
 
 
 class State:
@@ -224,6 +261,9 @@ class State:
         # walk periods (None: every pedestrian active every tick)
         self.period = None
         self.phase = None
+        # multi-su pedestrians: odd widths and heights (None: 1 x 1)
+        self.w = None
+        self.h = None
 
     def copy(self):
         s = State.__new__(State)
@@ -231,6 +271,8 @@ class State:
         s.alive, s.t, s.exited = self.alive.copy(), self.t, self.exited
         s.period = None if self.period is None else self.period.copy()
         s.phase = None if self.phase is None else self.phase.copy()
+        s.w = None if self.w is None else self.w.copy()
+        s.h = None if self.h is None else self.h.copy()
         return s
 
 
@@ -256,9 +298,11 @@ def step(m: Model, cell, D, st: State):
     won = np.zeros(max(n, 1), np.uint8)
     per = None if st.period is None else np.ascontiguousarray(st.period, np.uint8)
     pha = None if st.phase is None else np.ascontiguousarray(st.phase, np.uint8)
+    w = None if st.w is None else np.ascontiguousarray(st.w, np.uint8)
+    h = None if st.h is None else np.ascontiguousarray(st.h, np.uint8)
     left = lib().orc_step(C.byref(m), _p(cell), _p(D), st.t, n, _p(st.xy), _p(st.heading),
                           _p(st.goal), _p(st.alive), _p(occ), _p(choice), _p(won), _p(per),
-                          _p(pha))
+                          _p(pha), _p(w), _p(h))
     st.t += 1
     st.exited += int(left)
     return choice[:n], won[:n]

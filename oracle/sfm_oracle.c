@@ -128,6 +128,59 @@ int64_t orc_occupancy(const orc_model* m, const uint8_t* cell, int32_t n, const 
   return bad;
 }
 
+/* ---- multi-su pedestrians (Sec. 2; Table V) ----
+ * Reading: pedestrian p has odd width w_p and height h_p and occupies the
+ * w_p x h_p rectangle R(x_p) of su centred on its centre su x_p (wrapped in
+ * periodic dimensions).  Its field is emitted from the centre (the field
+ * functions above are unchanged and read only centres).  cover[su] = p for
+ * every su of p's rectangle, -1 elsewhere.  Returns the number of violations
+ * (a rectangle leaving a closed lattice, overlapping another or a WALL su,
+ * a centre on a non-FREE su).  w == NULL: every pedestrian is 1 x 1. */
+static int rect_su(const orc_model* m, int cx, int cy, int i, int j, int64_t* out) {
+  int x, y;
+  if (!wrap(cx + i, m->W, m->periodic_x, &x) || !wrap(cy + j, m->H, m->periodic_y, &y)) return 0;
+  *out = (int64_t)y * m->W + x;
+  return 1;
+}
+
+int64_t orc_cover(const orc_model* m, const uint8_t* cell, int32_t n, const int32_t* xy,
+                  const uint8_t* alive, const uint8_t* w, const uint8_t* h, int32_t* cover) {
+  int64_t nsu = (int64_t)m->W * m->H, bad = 0;
+  for (int64_t i = 0; i < nsu; ++i) cover[i] = -1;
+  for (int32_t p = 0; p < n; ++p) {
+    if (alive && !alive[p]) continue;
+    int x = xy[2 * p], y = xy[2 * p + 1];
+    int a = w ? w[p] / 2 : 0, b = h ? h[p] / 2 : 0;
+    if (x < 0 || x >= m->W || y < 0 || y >= m->H) { ++bad; continue; }
+    if (cell && cell[(int64_t)y * m->W + x] != ORC_FREE) ++bad;
+    for (int j = -b; j <= b; ++j)
+      for (int i = -a; i <= a; ++i) {
+        int64_t s;
+        if (!rect_su(m, x, y, i, j, &s)) { ++bad; continue; }
+        if (cover[s] >= 0 || (cell && cell[s] == ORC_WALL)) ++bad;
+        cover[s] = p;
+      }
+  }
+  return bad;
+}
+
+/* The su p newly enters when its centre moves by move class k: R(x + D_k)
+ * minus R(x).  Writes up to w + h - 1 su to out; returns the count, or -1 if
+ * the moved rectangle leaves a closed lattice. */
+static int entered_strip(const orc_model* m, int x, int y, int a, int b, int k, int64_t* out) {
+  int dx = ODX[k], dy = ODY[k], cnt = 0;
+  for (int j = -b; j <= b; ++j)
+    for (int i = -a; i <= a; ++i) {
+      /* (i, j) relative to the new centre; keep it unless it lies in R(x) */
+      int ox = i + dx, oy = j + dy;  /* offset from the old centre */
+      if (ox >= -a && ox <= a && oy >= -b && oy <= b) continue;
+      int64_t s;
+      if (!rect_su(m, x + dx, y + dy, i, j, &s)) return -1;
+      out[cnt++] = s;
+    }
+  return cnt;
+}
+
 /* Field at one su c by direct superposition over its (2r+1)^2 window.
  * parts: bit 0 = WALL and EXIT sources, bit 1 = pedestrians.
  * *f receives the field, *s the sum of the terms' magnitudes. */
@@ -245,7 +298,8 @@ uint64_t orc_prio(uint64_t seed, int64_t t, int64_t id) {
 void orc_decide(const orc_model* m, const uint8_t* cell, const int32_t* occ, const int32_t* xy,
                 const uint8_t* heading, const uint8_t* goal, const uint8_t* alive,
                 const int32_t* D, const double* Ffull, const double* Sfull, int64_t nreq,
-                const int32_t* req, uint8_t* choice, double* E, double* T, uint8_t* adm) {
+                const int32_t* req, uint8_t* choice, double* E, double* T, uint8_t* adm,
+                const int32_t* cover, const uint8_t* w, const uint8_t* h) {
 #pragma omp parallel for schedule(dynamic, 64)
   for (int64_t q = 0; q < nreq; ++q) {
     int32_t p = req ? req[q] : (int32_t)q;
@@ -263,7 +317,17 @@ void orc_decide(const orc_model* m, const uint8_t* cell, const int32_t* occ, con
       if (!wrap(x + ODX[k], m->W, m->periodic_x, &nx)) continue;
       if (!wrap(y + ODY[k], m->H, m->periodic_y, &ny)) continue;
       int64_t c = (int64_t)ny * m->W + nx;
-      if (k > 0 && (cell[c] == ORC_WALL || occ[c] >= 0)) continue;
+      if (k > 0 && !cover && (cell[c] == ORC_WALL || occ[c] >= 0)) continue;
+      if (k > 0 && cover) {
+        /* multi-su: every su the rectangle newly enters is inside, not WALL
+           and not covered by another pedestrian at tick start */
+        int64_t strip[64];
+        int ns = entered_strip(m, x, y, w ? w[p] / 2 : 0, h ? h[p] / 2 : 0, k, strip);
+        int ok = ns > 0;
+        for (int i = 0; ok && i < ns; ++i)
+          if (cell[strip[i]] == ORC_WALL || cover[strip[i]] >= 0) ok = 0;
+        if (!ok) continue;
+      }
       cand[k] = c;
       a[k] = 1;
     }
@@ -338,9 +402,62 @@ int32_t orc_vote(const orc_model* m, int64_t t, int32_t n, const int32_t* xy,
   return maxc;
 }
 
+/* Vote with multi-su pedestrians: a mover claims the su its rectangle newly
+ * enters; it wins iff its (prio, id) is the smallest among the claimants of
+ * every su it claims, i.e. smaller than that of every mover whose claim
+ * intersects its own.  With 1 x 1 pedestrians a claim is the target su and
+ * this is orc_vote.  Returns the most claimants of one su. */
+typedef struct { int64_t su; uint64_t prio; int32_t id; } orc_claim;
+
+static int claim_cmp(const void* a, const void* b) {
+  const orc_claim* x = (const orc_claim*)a;
+  const orc_claim* y = (const orc_claim*)b;
+  if (x->su != y->su) return x->su < y->su ? -1 : 1;
+  if (x->prio != y->prio) return x->prio < y->prio ? -1 : 1;
+  return x->id < y->id ? -1 : (x->id > y->id);
+}
+
+int32_t orc_vote_sized(const orc_model* m, int64_t t, int32_t n, const int32_t* xy,
+                       const uint8_t* alive, const uint8_t* choice, const uint8_t* w,
+                       const uint8_t* h, uint8_t* won) {
+  size_t cap = 16, nc = 0;
+  orc_claim* cl = (orc_claim*)malloc(sizeof(orc_claim) * cap);
+  for (int32_t p = 0; p < n; ++p) {
+    won[p] = 0;
+    if ((alive && !alive[p]) || choice[p] == 0) continue;
+    int64_t strip[64];
+    int ns = entered_strip(m, xy[2 * p], xy[2 * p + 1], w[p] / 2, h[p] / 2, choice[p], strip);
+    if (ns <= 0) continue;
+    won[p] = 1;  /* until a claimant with a smaller (prio, id) shares a su */
+    uint64_t pr = orc_prio(m->seed, t, p);
+    for (int i = 0; i < ns; ++i) {
+      if (nc == cap) {
+        cap *= 2;
+        cl = (orc_claim*)realloc(cl, sizeof(orc_claim) * cap);
+      }
+      cl[nc].su = strip[i];
+      cl[nc].prio = pr;
+      cl[nc].id = p;
+      ++nc;
+    }
+  }
+  qsort(cl, nc, sizeof(orc_claim), claim_cmp);
+  int32_t maxc = 0;
+  for (size_t i = 0; i < nc;) {
+    size_t j = i;
+    while (j < nc && cl[j].su == cl[i].su) ++j;
+    for (size_t q = i + 1; q < j; ++q) won[cl[q].id] = 0;
+    if ((int32_t)(j - i) > maxc) maxc = (int32_t)(j - i);
+    i = j;
+  }
+  free(cl);
+  return maxc;
+}
+
 /* ---- commit (sub-job k-4) ----  returns the number that left via exits */
 int32_t orc_commit(const orc_model* m, const uint8_t* cell, int32_t n, int32_t* xy,
-                   uint8_t* heading, uint8_t* alive, const uint8_t* choice, const uint8_t* won) {
+                   uint8_t* heading, uint8_t* alive, const uint8_t* choice, const uint8_t* won,
+                   const uint8_t* w, const uint8_t* h) {
   int32_t left = 0;
   for (int32_t p = 0; p < n; ++p) {
     if ((alive && !alive[p]) || !won[p]) continue;
@@ -352,7 +469,16 @@ int32_t orc_commit(const orc_model* m, const uint8_t* cell, int32_t n, int32_t* 
     xy[2 * p] = nx;
     xy[2 * p + 1] = ny;
     heading[p] = (uint8_t)k;
-    if (cell[(int64_t)ny * m->W + nx] == ORC_EXIT) {
+    /* it leaves when it steps onto an EXIT su: its centre (1 x 1), or for a
+       multi-su pedestrian any su of its new rectangle */
+    int out = cell[(int64_t)ny * m->W + nx] == ORC_EXIT;
+    const int a = w ? w[p] / 2 : 0, b = h ? h[p] / 2 : 0;
+    for (int j = -b; !out && j <= b; ++j)
+      for (int i = -a; !out && i <= a; ++i) {
+        int64_t s;
+        if (rect_su(m, nx, ny, i, j, &s) && cell[s] == ORC_EXIT) out = 1;
+      }
+    if (out) {
       alive[p] = 0;
       ++left;
     }
@@ -377,18 +503,30 @@ void orc_gate_periods(int64_t t, int32_t n, const uint8_t* period, const uint8_t
 /* ---- one full step (Alg. 1): decide all, vote, commit ----
  * D must hold the guidance distances; occ scratch of W*H int32; choice and won
  * receive the per-pedestrian results; period/phase as orc_gate_periods (NULL:
- * all active).  Returns the number that left. */
+ * all active); w/h the pedestrians' rectangles (NULL: 1 x 1).  Returns the
+ * number that left. */
 int32_t orc_step(const orc_model* m, const uint8_t* cell, const int32_t* D, int64_t t, int32_t n,
                  int32_t* xy, uint8_t* heading, const uint8_t* goal, uint8_t* alive, int32_t* occ,
-                 uint8_t* choice, uint8_t* won, const uint8_t* period, const uint8_t* phase) {
+                 uint8_t* choice, uint8_t* won, const uint8_t* period, const uint8_t* phase,
+                 const uint8_t* w, const uint8_t* h) {
   orc_occupancy(m, cell, n, xy, alive, occ);
   double* E = (double*)malloc(sizeof(double) * 9 * (size_t)(n > 0 ? n : 1));
   double* T = (double*)malloc(sizeof(double) * 9 * (size_t)(n > 0 ? n : 1));
   uint8_t* adm = (uint8_t*)malloc(9 * (size_t)(n > 0 ? n : 1));
-  orc_decide(m, cell, occ, xy, heading, goal, alive, D, NULL, NULL, n, NULL, choice, E, T, adm);
+  int32_t* cover = NULL;
+  if (w) {
+    cover = (int32_t*)malloc(sizeof(int32_t) * (size_t)m->W * m->H);
+    orc_cover(m, cell, n, xy, alive, w, h, cover);
+  }
+  orc_decide(m, cell, occ, xy, heading, goal, alive, D, NULL, NULL, n, NULL, choice, E, T, adm,
+             cover, w, h);
   orc_gate_periods(t, n, period, phase, choice);
-  orc_vote(m, t, n, xy, alive, choice, won);
-  int32_t left = orc_commit(m, cell, n, xy, heading, alive, choice, won);
+  if (w)
+    orc_vote_sized(m, t, n, xy, alive, choice, w, h, won);
+  else
+    orc_vote(m, t, n, xy, alive, choice, won);
+  free(cover);
+  int32_t left = orc_commit(m, cell, n, xy, heading, alive, choice, won, w, h);
   free(E);
   free(T);
   free(adm);

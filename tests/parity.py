@@ -76,13 +76,17 @@ class OracleRun:
 
     def decide(self, req=None, Ffull=None, Sfull=None):
         occ, _ = O.occupancy(self.m, self.sc.cell, self.st.xy, self.st.alive)
+        cov = None
+        if self.st.w is not None:
+            cov, _ = O.cover(self.m, self.sc.cell, self.st.xy, self.st.alive, self.st.w, self.st.h)
         return O.decide(self.m, self.sc.cell, occ, self.st.xy, self.st.heading, self.st.goal,
-                        self.st.alive, self.D, req, Ffull, Sfull)
+                        self.st.alive, self.D, req, Ffull, Sfull, cov, self.st.w, self.st.h)
 
     def advance(self, choice):
-        won, maxc = O.vote(self.m, self.st.t, self.st.xy, self.st.alive, choice)
+        won, maxc = O.vote(self.m, self.st.t, self.st.xy, self.st.alive, choice, self.st.w,
+                           self.st.h)
         left = O.commit(self.m, self.sc.cell, self.st.xy, self.st.heading, self.st.alive,
-                        choice, won)
+                        choice, won, self.st.w, self.st.h)
         self.st.t += 1
         self.st.exited += left
         return won, maxc

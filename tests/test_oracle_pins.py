@@ -337,6 +337,150 @@ def test_walk_periods_of_one_are_the_plain_model_and_gating_is_exact():
     np.testing.assert_array_equal(gated > 0, (4 % st.period.astype(int)) == st.phase)
 
 
+def _rect(W, H, px, py, x, y, w, h):
+    """su of the w x h rectangle centred on (x, y), or None if it leaves a
+    closed lattice (plain Python sets: an independent restatement)."""
+    out = set()
+    x, y, w, h = int(x), int(y), int(w), int(h)
+    for j in range(-(h // 2), h // 2 + 1):
+        for i in range(-(w // 2), w // 2 + 1):
+            u, v = x + i, y + j
+            if px:
+                u %= W
+            elif not 0 <= u < W:
+                return None
+            if py:
+                v %= H
+            elif not 0 <= v < H:
+                return None
+            out.add((u, v))
+    return out
+
+
+def test_sized_pedestrians_of_one_su_are_the_plain_model():
+    sc = SG.random_scene(48, 40, 500, r=5, seed=82, obstacles=3, exits=("east",),
+                         goal_mode="mixed", heading_mode="random")
+    m = O.model(sc)
+    D = O.guidance(m, sc.cell)
+    a, b = O.State(sc), O.State(sc)
+    b.w = np.ones(sc.n, np.uint8)
+    b.h = np.ones(sc.n, np.uint8)
+    for _ in range(8):
+        ca, wa = O.step(m, sc.cell, D, a)
+        cb, wb = O.step(m, sc.cell, D, b)
+        np.testing.assert_array_equal(ca, cb)
+        np.testing.assert_array_equal(wa, wb)
+        np.testing.assert_array_equal(a.xy, b.xy)
+
+
+def test_wide_pedestrian_walks_open_space_and_is_stopped_by_a_narrow_gap():
+    """Multi-su pedestrians (Sec. 2): a 3x3 east-walker crosses an open
+    corridor like a 1x1 one, but a 2-su gap in a wall lets only the 1x1 one
+    through."""
+    W, H = 40, 9
+    cell = np.zeros((H, W), np.uint8)
+    cell[0, :] = SG.WALL
+    cell[H - 1, :] = SG.WALL
+    cell[1:H - 1, 20] = SG.WALL
+    cell[4:6, 20] = SG.FREE                       # gap: rows 4 and 5
+    for size, passes in ((1, True), (3, False)):
+        # strong guidance, so the walls' repulsion does not stop the walkers
+        sc = SG.Scene("gap", W, H, 0, 0, cell, np.array([[5, 4]], np.int32),
+                      np.array([1], np.uint8), np.array([1], np.uint8), SG._params(r=4, beta=20.0))
+        m = O.model(sc)
+        st = O.State(sc)
+        st.w = np.array([size], np.uint8)
+        st.h = np.array([size], np.uint8)
+        D = O.guidance(m, cell)
+        for t in range(30):
+            O.step(m, cell, D, st)
+            rect = _rect(W, H, 0, 0, st.xy[0, 0], st.xy[0, 1], size, size)
+            assert rect is not None and all(cell[v, u] != SG.WALL for u, v in rect)
+        assert (st.xy[0, 0] > 20) == passes, (size, st.xy[0])
+        if not passes:
+            assert st.xy[0, 0] == 18                # its east edge stops at x = 19
+
+
+def test_sized_vote_against_a_pairwise_restatement():
+    """One tick of a crowd of 1x1 and 3x3 pedestrians: winners claim disjoint
+    strips of free su, and every losing mover shares a claimed su with a
+    mover of smaller (priority, id) -- checked pair by pair with Python sets."""
+    sc = SG.random_scene(40, 36, 120, r=4, seed=83, ring=False, periodic_x=1, exits=(),
+                         goal_mode="fixed", heading_mode="random")
+    rng = np.random.default_rng(9)
+    size = np.where(rng.random(sc.n) < 0.5, 3, 1).astype(np.uint8)
+    # drop pedestrians whose rectangles overlap, keep a valid placement
+    m = O.model(sc)
+    keep, taken = [], set()
+    for p in range(sc.n):
+        rc = _rect(sc.W, sc.H, 1, 0, sc.xy[p, 0], sc.xy[p, 1], size[p], size[p])
+        if rc is None or rc & taken or any(sc.cell[v, u] == SG.WALL for u, v in rc):
+            continue
+        keep.append(p)
+        taken |= rc
+    xy, goal, head, size = sc.xy[keep], sc.goal[keep], sc.heading[keep], size[keep]
+    n = len(keep)
+    alive = np.ones(n, np.uint8)
+    cov, bad = O.cover(m, sc.cell, xy, alive, size, size)
+    assert bad == 0
+    occ, _ = O.occupancy(m, sc.cell, xy, alive)
+    D = O.guidance(m, sc.cell)
+    ch, E, T, adm = O.decide(m, sc.cell, occ, xy, head, goal, alive, D, cov=cov, w=size, h=size)
+    t = 5
+    won, _ = O.vote(m, t, xy, alive, ch, size, size)
+    strip = {}
+    for p in range(n):
+        if ch[p] == 0:
+            continue
+        old = _rect(sc.W, sc.H, 1, 0, xy[p, 0], xy[p, 1], size[p], size[p])
+        new = _rect(sc.W, sc.H, 1, 0, xy[p, 0] + SG.DIRS[ch[p]][0], xy[p, 1] + SG.DIRS[ch[p]][1],
+                    size[p], size[p])
+        strip[p] = new - old
+        assert strip[p] and not any(cov[v * sc.W + u] >= 0 for u, v in strip[p])
+    key = {p: (O.prio(m.seed, t, p), p) for p in strip}
+    for p in strip:
+        rivals = [q for q in strip if q != p and strip[q] & strip[p]]
+        assert bool(won[p]) == all(key[p] < key[q] for q in rivals), p
+    winners = [p for p in strip if won[p]]
+    for i, p in enumerate(winners):
+        for q in winners[i + 1:]:
+            assert not strip[p] & strip[q]
+    assert sum(won) > 0 and sum(won) < len(strip)
+
+
+def test_sized_run_keeps_rectangles_disjoint_and_off_walls():
+    sc = SG.random_scene(64, 56, 400, r=5, seed=84, obstacles=3, exits=("east", "west"),
+                         exit_len=12, goal_mode="mixed", heading_mode="random")
+    rng = np.random.default_rng(10)
+    m = O.model(sc)
+    size = rng.choice(np.array([1, 3, 5], np.uint8), size=sc.n, p=[0.6, 0.3, 0.1])
+    keep, taken = [], set()
+    for p in range(sc.n):
+        rc = _rect(sc.W, sc.H, 0, 0, sc.xy[p, 0], sc.xy[p, 1], size[p], size[p])
+        if rc is None or rc & taken or any(sc.cell[v, u] == SG.WALL for u, v in rc):
+            continue
+        keep.append(p)
+        taken |= rc
+    sub = SG.Scene("sized", sc.W, sc.H, 0, 0, sc.cell, sc.xy[keep], sc.heading[keep],
+                   sc.goal[keep], sc.params)
+    st = O.State(sub)
+    st.w = size[keep].copy()
+    st.h = size[keep].copy()
+    D = O.guidance(m, sc.cell)
+    moved = 0
+    for _ in range(60):
+        xy0 = st.xy.copy()
+        O.step(m, sc.cell, D, st)
+        cov, bad = O.cover(m, sc.cell, st.xy, st.alive, st.w, st.h)
+        assert bad == 0
+        assert st.alive.sum() + st.exited == sub.n
+        moved += int(np.any(st.xy != xy0, axis=1).sum())
+    assert moved > 0 and st.exited > 0
+    # wide pedestrians leave too: through an exit they step onto
+    gone = (st.alive == 0)
+    assert np.any(gone & (st.w > 1)), "no multi-su pedestrian left"
+
+
 def test_decision_energy_matches_brute_force_field():
     sc = SG.random_scene(21, 19, 45, r=4, seed=71, obstacles=2, goal_mode="mixed",
                          heading_mode="random")
