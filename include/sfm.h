@@ -164,6 +164,22 @@ sfm_status sfm_compute_field(sfm_ctx* ctx);
  * nobody. */
 sfm_status sfm_autotune(sfm_ctx* ctx, int32_t* shape_out);
 
+/* Multi-su pedestrians (Sec. 2 of the paper; its Table V): as sfm_place, plus
+ * width[n] and height[n] (host or device per on_device): odd sides in
+ * [1, 15].  Pedestrian p occupies the width x height rectangle of su centred
+ * on xy[p] (wrapped in periodic dimensions; a periodic extent must be at
+ * least 2 * side + 3); only the centre emits its field.  A move is
+ * admissible iff every su the rectangle newly enters is inside, not WALL and
+ * not covered by another pedestrian at tick start; a mover claims those su
+ * and wins iff its (priority, id) is the smallest among the movers whose
+ * claims meet its own; it leaves when its new rectangle meets an EXIT su.
+ * Rectangles must not overlap each other or WALL su, and centres must be on
+ * FREE su (else SFM_ECONFLICT, nothing placed).  A later sfm_place returns to
+ * 1 x 1 pedestrians.  Not supported by the surrogate or the batch. */
+sfm_status sfm_place_sized(sfm_ctx* ctx, int32_t n, const int32_t* xy, const uint8_t* heading,
+                           const uint8_t* goal, const uint8_t* alive, const uint8_t* width,
+                           const uint8_t* height, int32_t on_device);
+
 /* Walk periods (Sec. 2 of the paper, which adopts them to vary walking
  * speeds under a maximal speed of 1 su per tick): pedestrian p may move only
  * on ticks t with t mod period[p] == phase[p] (t = the context's tick

@@ -34,7 +34,7 @@ EXPORTS = [
     "sfm_compute_field_into", "sfm_read_static_field", "sfm_read_guidance", "sfm_read_peds",
     "sfm_read_decisions", "sfm_stats", "sfm_set_timing", "sfm_stage_times",
     "sfm_autotune", "sfm_set_field_footprint", "sfm_set_binning", "sfm_set_walk_periods",
-    "sfm_field_noalloc", "sfm_batch_create", "sfm_batch_place", "sfm_batch_offsets",
+    "sfm_place_sized", "sfm_field_noalloc", "sfm_batch_create", "sfm_batch_place", "sfm_batch_offsets",
     "sfm_batch_autotune", "sfm_batch_test_missing_ctas", "sfm_surrogate_nparams",
     "sfm_surrogate_create", "sfm_surrogate_destroy", "sfm_surrogate_last_error",
     "sfm_surrogate_set_params", "sfm_surrogate_get_params", "sfm_surrogate_grad",
@@ -117,6 +117,7 @@ def lib():
             "sfm_set_field_footprint": (C.c_int, [P, I32]),
             "sfm_set_binning": (C.c_int, [P, I32]),
             "sfm_set_walk_periods": (C.c_int, [P, P, P, I32]),
+            "sfm_place_sized": (C.c_int, [P, I32, P, P, P, P, P, P, I32]),
             "sfm_stage_times": (C.c_int, [P, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
             "sfm_field_noalloc": (C.c_int, [C.POINTER(Lattice), C.POINTER(Params), I32, P, P, P,
                                             P, P, P]),
@@ -463,6 +464,15 @@ class Sim:
 
     def autotune(self):
         return sfm_autotune(self.ctx)
+
+    def place_sized(self, xy, heading, goal, alive, width, height):
+        """Place multi-su pedestrians (odd width x height rectangles)."""
+        keep = [np.ascontiguousarray(xy, np.int32), np.ascontiguousarray(heading, np.uint8),
+                np.ascontiguousarray(goal, np.uint8), np.ascontiguousarray(alive, np.uint8),
+                np.ascontiguousarray(width, np.uint8), np.ascontiguousarray(height, np.uint8)]
+        self.n = int(keep[0].shape[0])
+        _check(self.ctx, lib().sfm_place_sized(self.ctx, self.n,
+                                               *[k.ctypes.data_as(C.c_void_p) for k in keep], 0))
 
     def set_walk_periods(self, period=None, phase=None):
         """Walk periods: pedestrian p moves only on ticks t with t % period[p]

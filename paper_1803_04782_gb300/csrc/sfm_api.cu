@@ -6,6 +6,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <string>
 #include <vector>
 
@@ -179,7 +180,7 @@ void run_tick(sfm_ctx* c) {
     StageScope sc(c, SFM_STAGE_DECIDE);
     launch_decide(c->n, c->rec_id, c->bin_start, 0, nbins, c->xy, c->heading, c->goal, c->cell,
                   c->ocls, c->D, c->F, 0, -1, -1, 0, 0, g.H, g, c->prm.beta, tb, c->choice,
-                  c->stream, c->walk());
+                  c->stream, c->walk(), c->sizes(), c->occ);
     if (c->n > 0) ++c->launches;
   } else {
     for (int b = 0; b < c->bands; ++b) {
@@ -196,19 +197,19 @@ void run_tick(sfm_ctx* c) {
       launch_decide(c->n, c->rec_id, c->bin_start, (ya / kBin) * g.nbx,
                     ((yb + kBin - 1) / kBin) * g.nbx, c->xy, c->heading, c->goal, c->cell, c->ocls,
                     c->D, c->band_buf, 1, lo, hi, yb - ya + 1, ya, yb, g, c->prm.beta, tb,
-                    c->choice, c->stream, c->walk());
+                    c->choice, c->stream, c->walk(), c->sizes(), c->occ);
       if (c->n > 0) ++c->launches;
     }
   }
   {
     StageScope sc(c, SFM_STAGE_VOTE);
     launch_vote(c->n, c->rec_id, c->bin_start, c->xy, c->choice, c->occ, g, c->prm.seed, c->ctr,
-                c->won, c->stream);
+                c->won, c->stream, c->sizes());
     if (c->n > 0) ++c->launches;
   }
   StageScope sc(c, SFM_STAGE_COMMIT);
   launch_commit(c->n, c->rec_id, c->bin_start, c->xy, c->alive, c->heading, c->choice, c->won,
-                c->cell, c->occ, c->ocls, g, c->ctr, c->stream);
+                c->cell, c->occ, c->ocls, g, c->ctr, c->stream, c->sizes());
   ++c->launches;
 }
 
@@ -441,16 +442,55 @@ void sfm_destroy(sfm_ctx* ctx) {
   delete ctx;
 }
 
+static sfm_status place_impl(sfm_ctx* ctx, int32_t n, const int32_t* xy, const uint8_t* heading,
+                             const uint8_t* goal, const uint8_t* alive, const uint8_t* w,
+                             const uint8_t* h, int32_t on_device);
+
 sfm_status sfm_place(sfm_ctx* ctx, int32_t n, const int32_t* xy, const uint8_t* heading,
                      const uint8_t* goal, const uint8_t* alive, int32_t on_device) {
+  return place_impl(ctx, n, xy, heading, goal, alive, nullptr, nullptr, on_device);
+}
+
+sfm_status sfm_place_sized(sfm_ctx* ctx, int32_t n, const int32_t* xy, const uint8_t* heading,
+                           const uint8_t* goal, const uint8_t* alive, const uint8_t* width,
+                           const uint8_t* height, int32_t on_device) {
+  if (!width || !height) return fail(ctx, SFM_EINVAL, "width and height arrays are required");
+  return place_impl(ctx, n, xy, heading, goal, alive, width, height, on_device);
+}
+
+static sfm_status place_impl(sfm_ctx* ctx, int32_t n, const int32_t* xy, const uint8_t* heading,
+                             const uint8_t* goal, const uint8_t* alive, const uint8_t* w,
+                             const uint8_t* h, int32_t on_device) {
   if (!ctx) return SFM_EINVAL;
   if (ctx->batch) return fail(ctx, SFM_ESTATE, "a batch is placed with sfm_batch_place");
   drop_graph(ctx);
   if (n < 0 || (n > 0 && !xy)) return fail(ctx, SFM_EINVAL, "bad pedestrian arrays");
+  // multi-su pedestrians: odd sides in [1, kMaxPedSide]; a periodic extent of
+  // at least 2 * side + 3, so minimum-image offsets stay unambiguous
+  std::vector<uint8_t> hw, hh;
+  if (w) {
+    hw.resize((size_t)n);
+    hh.resize((size_t)n);
+    if (n > 0) {
+      const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost;
+      CU(cudaMemcpy(hw.data(), w, (size_t)n, k));
+      CU(cudaMemcpy(hh.data(), h, (size_t)n, k));
+    }
+    int mw = 1, mh = 1;
+    for (int p = 0; p < n; ++p) {
+      if (!(hw[p] & 1) || !(hh[p] & 1) || hw[p] > kMaxPedSide || hh[p] > kMaxPedSide)
+        return fail(ctx, SFM_EINVAL, "pedestrian %d: size %dx%d (odd sides, at most %d)", p,
+                    (int)hw[p], (int)hh[p], kMaxPedSide);
+      mw = std::max(mw, (int)hw[p]);
+      mh = std::max(mh, (int)hh[p]);
+    }
+    if ((ctx->geo.px && ctx->geo.W < 2 * mw + 3) || (ctx->geo.py && ctx->geo.H < 2 * mh + 3))
+      return fail(ctx, SFM_EINVAL, "periodic extent below 2 * pedestrian side + 3");
+  }
   cudaStream_t s = ctx->stream;
   const Geo& g = ctx->geo;
   if (ctx->placed && ctx->n > 0) {
-    launch_place_clear(ctx->n, ctx->xy, ctx->alive, g, ctx->occ, ctx->ocls, s);
+    launch_place_clear(ctx->n, ctx->xy, ctx->alive, g, ctx->occ, ctx->ocls, s, ctx->sizes());
     ++ctx->launches;
   }
   if (n > ctx->cap) {
@@ -467,6 +507,8 @@ sfm_status sfm_place(sfm_ctx* ctx, int32_t n, const int32_t* xy, const uint8_t* 
     dfree(ctx, ctx->bin_key);
     dfree(ctx, ctx->period);
     dfree(ctx, ctx->phase);
+    dfree(ctx, ctx->pw);
+    dfree(ctx, ctx->ph);
     ctx->xy = nullptr;
     ctx->cap = 0;
     TRY(dalloc(ctx, &ctx->xy, (size_t)n));
@@ -481,6 +523,8 @@ sfm_status sfm_place(sfm_ctx* ctx, int32_t n, const int32_t* xy, const uint8_t* 
     TRY(dalloc(ctx, &ctx->bin_key, (size_t)n));
     TRY(dalloc(ctx, &ctx->period, (size_t)n));
     TRY(dalloc(ctx, &ctx->phase, (size_t)n));
+    TRY(dalloc(ctx, &ctx->pw, (size_t)n));
+    TRY(dalloc(ctx, &ctx->ph, (size_t)n));
     ctx->cap = n;
   }
   if (ctx->cap == 0) {
@@ -496,6 +540,8 @@ sfm_status sfm_place(sfm_ctx* ctx, int32_t n, const int32_t* xy, const uint8_t* 
     TRY(dalloc(ctx, &ctx->bin_key, 1));
     TRY(dalloc(ctx, &ctx->period, 1));
     TRY(dalloc(ctx, &ctx->phase, 1));
+    TRY(dalloc(ctx, &ctx->pw, 1));
+    TRY(dalloc(ctx, &ctx->ph, 1));
     ctx->cap = 1;
   }
   ctx->placed = false;
@@ -512,24 +558,30 @@ sfm_status sfm_place(sfm_ctx* ctx, int32_t n, const int32_t* xy, const uint8_t* 
     else CU(cudaMemsetAsync(ctx->alive, 1, n, s));
     CU(cudaMemsetAsync(ctx->choice, 0, n, s));
     CU(cudaMemsetAsync(ctx->won, 0, n, s));
+    if (w) {
+      CU(cudaMemcpyAsync(ctx->pw, hw.data(), n, cudaMemcpyHostToDevice, s));
+      CU(cudaMemcpyAsync(ctx->ph, hh.data(), n, cudaMemcpyHostToDevice, s));
+    }
   }
+  ctx->sized = w != nullptr;
   // reset per-placement counters and flags on the stream, keep the tick counter
   launch_reset_counters(ctx->ctr, s);
   ++ctx->launches;
   launch_place_scatter(n, ctx->xy, ctx->heading, ctx->goal, ctx->alive, ctx->cell, g, ctx->occ,
-                       ctx->ocls, ctx->ctr, s);
+                       ctx->ocls, ctx->ctr, s, ctx->sizes());
   if (n > 0) ++ctx->launches;
-  Counters h;
-  CU(cudaMemcpyAsync(&h, ctx->ctr, sizeof(h), cudaMemcpyDeviceToHost, s));
+  Counters hc;
+  CU(cudaMemcpyAsync(&hc, ctx->ctr, sizeof(hc), cudaMemcpyDeviceToHost, s));
   CU(cudaStreamSynchronize(s));
   CU(cudaGetLastError());
-  if (h.err) {
-    const uint32_t flags = h.err;
+  if (hc.err) {
+    const uint32_t flags = hc.err;
     const size_t nsu = (size_t)g.W * g.H;
     cudaMemsetAsync(ctx->occ, 0xff, nsu * sizeof(int32_t), s);
     cudaMemsetAsync(ctx->ocls, 0, (size_t)g.opitch * g.H, s);
-    h.err = 0;
-    cudaMemcpyAsync(ctx->ctr, &h, sizeof(h), cudaMemcpyHostToDevice, s);
+    ctx->sized = false;
+    hc.err = 0;
+    cudaMemcpyAsync(ctx->ctr, &hc, sizeof(hc), cudaMemcpyHostToDevice, s);
     cudaStreamSynchronize(s);
     return fail(ctx, (flags & kErrPlaceRange) ? SFM_EINVAL : SFM_ECONFLICT,
                 "placement rejected: overlapping pedestrians, a pedestrian on a WALL/EXIT su, "

@@ -62,6 +62,8 @@ struct sfm_ctx {
   uint8_t *heading = nullptr, *goal = nullptr, *alive = nullptr, *choice = nullptr, *won = nullptr;
   uint8_t *period = nullptr, *phase = nullptr;  // walk periods (used when walk_periods)
   bool walk_periods = false;
+  uint8_t *pw = nullptr, *ph = nullptr;  // multi-su pedestrians' widths / heights (when sized)
+  bool sized = false;
   bool placed = false;
   int64_t t = 0;
   // banded mode
@@ -97,6 +99,14 @@ struct sfm_ctx {
     tb.CT = CT;
     tb.shape = field_shape;
     return tb;
+  }
+  sfm::Sizes sizes() const {
+    sfm::Sizes sz;
+    if (sized) {
+      sz.w = pw;
+      sz.h = ph;
+    }
+    return sz;
   }
   sfm::WalkPeriods walk() const {
     sfm::WalkPeriods wp;

@@ -122,6 +122,53 @@ __device__ __forceinline__ void bin_fill_group(const Geo& g, const uint8_t* __re
   }
 }
 
+// ----------------------------------------------------- multi-su pedestrians
+// su (cx + i, cy + j), wrapped in periodic dimensions; false if it leaves a
+// closed lattice.
+__device__ __forceinline__ bool rect_su(const Geo& g, int cx, int cy, int i, int j, size_t& s) {
+  int x, y;
+  if (!(wrap_coord(cx + i, g.W, g.px, x) & wrap_coord(cy + j, g.H, g.py, y))) return false;
+  s = (size_t)y * g.W + x;
+  return true;
+}
+
+// Every su that the rectangle of half sides (a, b) centred on (x, y) newly
+// enters when its centre moves by class k is inside, not WALL and not
+// covered by a pedestrian (occ < 0) at tick start.
+__device__ __forceinline__ bool strip_free(const Geo& g, const uint8_t* __restrict__ cell,
+                                           const int32_t* __restrict__ occ, int x, int y, int a,
+                                           int b, int k) {
+  const int dx = move_dx(k), dy = move_dy(k);
+  for (int j = -b; j <= b; ++j)
+    for (int i = -a; i <= a; ++i) {
+      const int ox = i + dx, oy = j + dy;  // offset from the old centre
+      if (ox >= -a && ox <= a && oy >= -b && oy <= b) continue;
+      size_t s;
+      if (!rect_su(g, x, y, ox, oy, s)) return false;
+      if (cell[s] == kWall || occ[s] >= 0) return false;
+    }
+  return true;
+}
+
+// Offset d along a dimension of n su: the minimum image when periodic.
+__device__ __forceinline__ int image_offset(int d, int n, int periodic) {
+  if (!periodic) return d;
+  d %= n;
+  if (d > n / 2) d -= n;
+  if (d < -(n / 2)) d += n;
+  return d;
+}
+
+// su (sx, sy) is one that pedestrian q (centre (qx, qy), half sides a, b)
+// newly enters with move k.
+__device__ __forceinline__ bool in_entered(const Geo& g, int sx, int sy, int qx, int qy, int a, int b,
+                                           int k) {
+  const int ox = image_offset(sx - qx, g.W, g.px), oy = image_offset(sy - qy, g.H, g.py);
+  const bool in_old = ox >= -a && ox <= a && oy >= -b && oy <= b;
+  const int nx = ox - move_dx(k), ny = oy - move_dy(k);
+  return !in_old && nx >= -a && nx <= a && ny >= -b && ny <= b;
+}
+
 // ---------------------------------------------------------------- S3 decide
 // E over the 9 candidates (stay + 8 neighbours), admissible iff inside, not
 // WALL and unoccupied at tick start; the minimum with ties to the smallest
@@ -198,7 +245,9 @@ __device__ __forceinline__ uint8_t decide_one(
     const uint8_t* __restrict__ goal, const uint8_t* __restrict__ cell,
     const uint8_t* __restrict__ ocls, const int32_t* __restrict__ D, const float* __restrict__ F,
     int main_off, int lo_row, int hi_row, int hi_off, int y_lo, int y_hi, float beta,
-    const float* __restrict__ own, const float* __restrict__ dirdot) {
+    const float* __restrict__ own, const float* __restrict__ dirdot,
+    const uint8_t* __restrict__ pw = nullptr, const uint8_t* __restrict__ ph = nullptr,
+    const int32_t* __restrict__ occ = nullptr) {
   const int2 q = xy[p];
   const int h = heading[p], gl = goal[p];
   // the 3 x 3 neighbourhood (wrapped or clipped); every load is issued
@@ -226,6 +275,16 @@ __device__ __forceinline__ uint8_t decide_one(
     dd[k] = D[c];
     cl[k] = cell[c];
     oc[k] = ocls[(size_t)ry[yi] * g.opitch + cx[xi]];
+  }
+  if (pw) {
+    // multi-su pedestrian: a move is admissible iff the su its rectangle
+    // newly enters are free (walls included in the test)
+    const int a = pw[p] >> 1, b = ph[p] >> 1;
+#pragma unroll
+    for (int k = 1; k < 9; ++k) {
+      oc[k] = strip_free(g, cell, occ, q.x, q.y, a, b, k) ? 0 : 1;
+      cl[k] = kFree;
+    }
   }
   return (uint8_t)pick_move<false>(f, dd, cl, oc, okx, oky, h, gl, beta, own, dirdot, nullptr);
 }
@@ -299,6 +358,108 @@ __device__ __forceinline__ void commit_one(int p, const Geo& g, int2* __restrict
     left = true;
   } else {
     occ[c1] = p;
+    ocls[(size_t)ty * g.opitch + tx] = (uint8_t)(1 + k);
+  }
+  xy[p] = make_int2(tx, ty);
+  heading[p] = (uint8_t)k;
+  moved = true;
+}
+
+// Vote of a multi-su pedestrian: it claims the su its rectangle newly
+// enters and wins iff its (priority, id) is smaller than that of every other
+// mover claiming one of them.  A rival claiming su s covers a su next to s,
+// so the 8 neighbours of each claimed su hold every rival's id.  Returns the
+// most claimants of one su.
+__device__ __forceinline__ int vote_one_sized(int p, const Geo& g, const int2* __restrict__ xy,
+                                              const uint8_t* __restrict__ choice,
+                                              const int32_t* __restrict__ occ,
+                                              const uint8_t* __restrict__ pw,
+                                              const uint8_t* __restrict__ ph, uint64_t seed,
+                                              long long t, uint8_t* __restrict__ won) {
+  const int k = choice[p];
+  if (k == 0) {
+    won[p] = 0;
+    return 0;
+  }
+  const int2 q = xy[p];
+  const int a = pw[p] >> 1, b = ph[p] >> 1, dx = move_dx(k), dy = move_dy(k);
+  const uint64_t st = splitmix_nth(seed, (uint64_t)t + 1);
+  const uint64_t mine = splitmix_nth(st, (uint64_t)p + 1);
+  bool win = true;
+  int regs = 1;
+  for (int j = -b; j <= b; ++j)
+    for (int i = -a; i <= a; ++i) {
+      const int ox = i + dx, oy = j + dy;
+      if (ox >= -a && ox <= a && oy >= -b && oy <= b) continue;  // not newly entered
+      int sx, sy;
+      if (!(wrap_coord(q.x + ox, g.W, g.px, sx) & wrap_coord(q.y + oy, g.H, g.py, sy))) continue;
+      int seen[8], ns = 0;
+      for (int e = 1; e <= 8; ++e) {
+        int nx, ny;
+        if (!(wrap_coord(sx + move_dx(e), g.W, g.px, nx) & wrap_coord(sy + move_dy(e), g.H, g.py, ny)))
+          continue;
+        const int o = occ[(size_t)ny * g.W + nx];
+        if (o < 0 || o == p) continue;
+        bool dup = false;
+        for (int u = 0; u < ns; ++u) dup |= seen[u] == o;
+        if (dup || choice[o] == 0) continue;
+        const int2 qo = xy[o];
+        if (!in_entered(g, sx, sy, qo.x, qo.y, pw[o] >> 1, ph[o] >> 1, choice[o])) continue;
+        seen[ns++] = o;
+        const uint64_t po = splitmix_nth(st, (uint64_t)o + 1);
+        if (po < mine || (po == mine && o < p)) win = false;
+      }
+      regs = max(regs, ns + 1);
+    }
+  won[p] = win ? 1 : 0;
+  return regs;
+}
+
+// Commit of a multi-su pedestrian: the su it leaves behind are freed and the
+// su it enters take its id (claims of winners are disjoint and were free, so
+// no two threads write one su); a winner whose new rectangle meets an EXIT su
+// leaves and frees its whole rectangle.
+__device__ __forceinline__ void commit_one_sized(int p, const Geo& g, int2* __restrict__ xy,
+                                                 uint8_t* __restrict__ alive,
+                                                 uint8_t* __restrict__ heading,
+                                                 const uint8_t* __restrict__ choice,
+                                                 const uint8_t* __restrict__ won,
+                                                 const uint8_t* __restrict__ cell,
+                                                 int32_t* __restrict__ occ,
+                                                 uint8_t* __restrict__ ocls,
+                                                 const uint8_t* __restrict__ pw,
+                                                 const uint8_t* __restrict__ ph, bool& moved,
+                                                 bool& left) {
+  moved = false;
+  left = false;
+  if (!won[p]) return;
+  const int k = choice[p];
+  const int2 q = xy[p];
+  const int a = pw[p] >> 1, b = ph[p] >> 1, dx = move_dx(k), dy = move_dy(k);
+  int tx, ty;
+  wrap_coord(q.x + dx, g.W, g.px, tx);
+  wrap_coord(q.y + dy, g.H, g.py, ty);
+  bool out = false;
+  for (int j = -b; j <= b && !out; ++j)
+    for (int i = -a; i <= a && !out; ++i) {
+      size_t s;
+      if (rect_su(g, tx, ty, i, j, s) && cell[s] == kExit) out = true;
+    }
+  for (int j = -b; j <= b; ++j)
+    for (int i = -a; i <= a; ++i) {
+      size_t s;
+      const int ni = i - dx, nj = j - dy;  // offset of this old su from the new centre
+      const bool kept = ni >= -a && ni <= a && nj >= -b && nj <= b;
+      if ((out || !kept) && rect_su(g, q.x, q.y, i, j, s)) occ[s] = -1;
+      const int ei = i + dx, ej = j + dy;  // offset of a new su from the old centre
+      const bool entered = !(ei >= -a && ei <= a && ej >= -b && ej <= b);
+      if (!out && entered && rect_su(g, q.x, q.y, ei, ej, s)) occ[s] = p;
+    }
+  ocls[(size_t)q.y * g.opitch + q.x] = 0;
+  if (out) {
+    alive[p] = 0;
+    left = true;
+  } else {
     ocls[(size_t)ty * g.opitch + tx] = (uint8_t)(1 + k);
   }
   xy[p] = make_int2(tx, ty);

@@ -79,6 +79,15 @@ struct Counters {
   long long t;  // tick counter read by the vote and advanced by the commit
 };
 
+// Multi-su pedestrians (Sec. 2): pedestrian p occupies the w[p] x h[p]
+// rectangle (odd sides) centred on its centre su; occ holds p on every su of
+// it.  w == nullptr: every pedestrian is 1 x 1 (the plain model).
+struct Sizes {
+  const uint8_t* w = nullptr;
+  const uint8_t* h = nullptr;
+};
+constexpr int kMaxPedSide = 15;  // largest width / height of a pedestrian
+
 // Geometry and model constants passed by value to every kernel.
 struct Geo {
   int W, H, px, py;
@@ -125,10 +134,10 @@ void launch_guidance_round(const Geo& g, const uint8_t* cell, int32_t* D, const 
                            uint8_t* act_out, int* changed, cudaStream_t s);
 
 void launch_place_clear(int n, const int2* xy, const uint8_t* alive, const Geo& g, int32_t* occ,
-                        uint8_t* ocls, cudaStream_t s);
+                        uint8_t* ocls, cudaStream_t s, const Sizes& sz = Sizes());
 void launch_place_scatter(int n, const int2* xy, const uint8_t* heading, const uint8_t* goal,
                           const uint8_t* alive, const uint8_t* cell, const Geo& g, int32_t* occ,
-                          uint8_t* ocls, Counters* ctr, cudaStream_t s);
+                          uint8_t* ocls, Counters* ctr, cudaStream_t s, const Sizes& sz = Sizes());
 
 void launch_bin_count(const Geo& g, const uint8_t* ocls, int32_t* count, cudaStream_t s);
 void launch_scan(const int32_t* in, int32_t* out, int n, int32_t* block_tmp, cudaStream_t s);
@@ -180,13 +189,14 @@ void launch_decide(int n, const int32_t* rec_id, const int32_t* bin_start, int b
                    const uint8_t* cell, const uint8_t* ocls, const int32_t* D, const float* F,
                    int main_off, int lo_row, int hi_row, int hi_off, int y_lo, int y_hi,
                    const Geo& g, float beta, const Tables& tb, uint8_t* choice, cudaStream_t s,
-                   const WalkPeriods& wp = WalkPeriods());
+                   const WalkPeriods& wp = WalkPeriods(), const Sizes& sz = Sizes(),
+                   const int32_t* occ = nullptr);
 void launch_vote(int n, const int32_t* rec_id, const int32_t* bin_start, const int2* xy,
                  const uint8_t* choice, const int32_t* occ, const Geo& g, uint64_t seed,
-                 Counters* ctr, uint8_t* won, cudaStream_t s);
+                 Counters* ctr, uint8_t* won, cudaStream_t s, const Sizes& sz = Sizes());
 void launch_commit(int n, const int32_t* rec_id, const int32_t* bin_start, int2* xy,
                    uint8_t* alive, uint8_t* heading, const uint8_t* choice, const uint8_t* won,
                    const uint8_t* cell, int32_t* occ, uint8_t* ocls, const Geo& g, Counters* ctr,
-                   cudaStream_t s);
+                   cudaStream_t s, const Sizes& sz = Sizes());
 
 }  // namespace sfm

@@ -213,11 +213,17 @@ void launch_guidance_round(const Geo& g, const uint8_t* cell, int32_t* D, const 
 
 // ------------------------------------------------------------- placement
 __global__ void k_place_clear(int n, const int2* __restrict__ xy, const uint8_t* __restrict__ alive,
-                              Geo g, int32_t* __restrict__ occ, uint8_t* __restrict__ ocls) {
+                              Geo g, int32_t* __restrict__ occ, uint8_t* __restrict__ ocls,
+                              Sizes sz) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= n || !alive[p]) return;
   const int2 q = xy[p];
-  occ[(size_t)q.y * g.W + q.x] = -1;
+  const int a = sz.w ? sz.w[p] >> 1 : 0, b = sz.w ? sz.h[p] >> 1 : 0;
+  for (int j = -b; j <= b; ++j)
+    for (int i = -a; i <= a; ++i) {
+      size_t s;
+      if (rect_su(g, q.x, q.y, i, j, s)) occ[s] = -1;
+    }
   ocls[(size_t)q.y * g.opitch + q.x] = 0;
 }
 
@@ -225,7 +231,7 @@ __global__ void k_place_scatter(int n, const int2* __restrict__ xy,
                                 const uint8_t* __restrict__ heading,
                                 const uint8_t* __restrict__ goal, const uint8_t* __restrict__ alive,
                                 const uint8_t* __restrict__ cell, Geo g, int32_t* __restrict__ occ,
-                                uint8_t* __restrict__ ocls, Counters* ctr) {
+                                uint8_t* __restrict__ ocls, Counters* ctr, Sizes sz) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= n) return;
   if (heading[p] > 8 || goal[p] > 8) atomicOr(&ctr->err, kErrPlaceRange);
@@ -237,17 +243,25 @@ __global__ void k_place_scatter(int n, const int2* __restrict__ xy,
   }
   const size_t c = (size_t)q.y * g.W + q.x;
   if (cell[c] != kFree) atomicOr(&ctr->err, kErrPlaceConflict);
-  if (atomicCAS(&occ[c], -1, p) != -1) {
-    atomicOr(&ctr->err, kErrPlaceConflict);
-    return;
-  }
+  // the rectangle (1 x 1 without sizes): inside, off walls, on nobody else
+  const int a = sz.w ? sz.w[p] >> 1 : 0, b = sz.w ? sz.h[p] >> 1 : 0;
+  for (int j = -b; j <= b; ++j)
+    for (int i = -a; i <= a; ++i) {
+      size_t s;
+      if (!rect_su(g, q.x, q.y, i, j, s)) {
+        atomicOr(&ctr->err, kErrPlaceConflict);
+        continue;
+      }
+      if (cell[s] == kWall || atomicCAS(&occ[s], -1, p) != -1)
+        atomicOr(&ctr->err, kErrPlaceConflict);
+    }
   ocls[(size_t)q.y * g.opitch + q.x] = (uint8_t)(1 + (heading[p] > 8 ? 0 : heading[p]));
 }
 
 void launch_place_clear(int n, const int2* xy, const uint8_t* alive, const Geo& g, int32_t* occ,
-                        uint8_t* ocls, cudaStream_t s) {
+                        uint8_t* ocls, cudaStream_t s, const Sizes& sz) {
   if (n <= 0) return;
-  k_place_clear<<<cdiv(n, 256), 256, 0, s>>>(n, xy, alive, g, occ, ocls);
+  k_place_clear<<<cdiv(n, 256), 256, 0, s>>>(n, xy, alive, g, occ, ocls, sz);
 }
 
 // per-placement counters and flags back to zero (the tick counter stays)
@@ -262,10 +276,10 @@ void launch_reset_counters(Counters* ctr, cudaStream_t s) { k_reset_counters<<<1
 
 void launch_place_scatter(int n, const int2* xy, const uint8_t* heading, const uint8_t* goal,
                           const uint8_t* alive, const uint8_t* cell, const Geo& g, int32_t* occ,
-                          uint8_t* ocls, Counters* ctr, cudaStream_t s) {
+                          uint8_t* ocls, Counters* ctr, cudaStream_t s, const Sizes& sz) {
   if (n <= 0) return;
   k_place_scatter<<<cdiv(n, 256), 256, 0, s>>>(n, xy, heading, goal, alive, cell, g, occ, ocls,
-                                               ctr);
+                                               ctr, sz);
 }
 
 // --------------------------------------------------------- S1: binning
@@ -692,7 +706,7 @@ __global__ void k_decide(const int32_t* __restrict__ rec_id, const int32_t* __re
                          int lo_row, int hi_row, int hi_off, int y_lo, int y_hi, Geo g,
                          float beta, const float* __restrict__ own,
                          const float* __restrict__ dirdot, uint8_t* __restrict__ choice,
-                         WalkPeriods wp) {
+                         WalkPeriods wp, Sizes sz, const int32_t* __restrict__ occ) {
   // grid-stride over the records of bins [b_lo, b_hi): a band's launch needs
   // no more blocks than the GPU holds, whatever its share of the crowd
   const int end = bin_start[b_hi];
@@ -705,7 +719,7 @@ __global__ void k_decide(const int32_t* __restrict__ rec_id, const int32_t* __re
       continue;
     }
     choice[p] = decide_one(p, g, xy, heading, goal, cell, ocls, D, F, main_off, lo_row, hi_row,
-                           hi_off, y_lo, y_hi, beta, own, dirdot);
+                           hi_off, y_lo, y_hi, beta, own, dirdot, sz.w, sz.h, occ);
   }
 }
 
@@ -714,7 +728,7 @@ void launch_decide(int n, const int32_t* rec_id, const int32_t* bin_start, int b
                    const uint8_t* cell, const uint8_t* ocls, const int32_t* D, const float* F,
                    int main_off, int lo_row, int hi_row, int hi_off, int y_lo, int y_hi,
                    const Geo& g, float beta, const Tables& tb, uint8_t* choice, cudaStream_t s,
-                   const WalkPeriods& wp) {
+                   const WalkPeriods& wp, const Sizes& sz, const int32_t* occ) {
   if (n <= 0 || b_hi <= b_lo) return;
   static int max_blocks = 0;
   if (!max_blocks) {
@@ -726,7 +740,7 @@ void launch_decide(int n, const int32_t* rec_id, const int32_t* bin_start, int b
   const int blocks = cdiv(n, 256) < max_blocks ? cdiv(n, 256) : max_blocks;
   k_decide<<<blocks, 256, 0, s>>>(rec_id, bin_start, b_lo, b_hi, xy, heading, goal, cell,
                                         ocls, D, F, main_off, lo_row, hi_row, hi_off, y_lo, y_hi,
-                                        g, beta, tb.own, tb.dirdot, choice, wp);
+                                        g, beta, tb.own, tb.dirdot, choice, wp, sz, occ);
 }
 
 // ------------------------------------------------------------ S4: vote
@@ -734,20 +748,21 @@ void launch_decide(int n, const int32_t* rec_id, const int32_t* bin_start, int b
 __global__ void k_vote(const int32_t* __restrict__ rec_id, const int32_t* __restrict__ bin_start,
                        int nbins, const int2* __restrict__ xy, const uint8_t* __restrict__ choice,
                        const int32_t* __restrict__ occ, Geo g, uint64_t seed, Counters* ctr,
-                       uint8_t* __restrict__ won) {
+                       uint8_t* __restrict__ won, Sizes sz) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= bin_start[nbins]) return;
-  const int regs = vote_one(rec_id[i], 0, g, xy, choice, occ, seed, ctr->t, won);
+  const int regs = sz.w ? vote_one_sized(rec_id[i], g, xy, choice, occ, sz.w, sz.h, seed, ctr->t, won)
+                        : vote_one(rec_id[i], 0, g, xy, choice, occ, seed, ctr->t, won);
   if (regs > 2) atomicMax(&ctr->max_registrants, regs);
   if (regs > 8) atomicOr(&ctr->err, kErrEnroll);
 }
 
 void launch_vote(int n, const int32_t* rec_id, const int32_t* bin_start, const int2* xy,
                  const uint8_t* choice, const int32_t* occ, const Geo& g, uint64_t seed,
-                 Counters* ctr, uint8_t* won, cudaStream_t s) {
+                 Counters* ctr, uint8_t* won, cudaStream_t s, const Sizes& sz) {
   if (n <= 0) return;
   k_vote<<<cdiv(n, 256), 256, 0, s>>>(rec_id, bin_start, g.nbx * g.nby, xy, choice, occ, g, seed,
-                                      ctr, won);
+                                      ctr, won, sz);
 }
 
 // ---------------------------------------------------------- S5: commit
@@ -756,11 +771,16 @@ __global__ void k_commit(const int32_t* __restrict__ rec_id, const int32_t* __re
                          uint8_t* __restrict__ heading, const uint8_t* __restrict__ choice,
                          const uint8_t* __restrict__ won, const uint8_t* __restrict__ cell,
                          int32_t* __restrict__ occ, uint8_t* __restrict__ ocls, Geo g,
-                         Counters* ctr) {
+                         Counters* ctr, Sizes sz) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   bool moved = false, left = false;
-  if (i < bin_start[nbins])
-    commit_one(rec_id[i], g, xy, alive, heading, choice, won, cell, occ, ocls, moved, left);
+  if (i < bin_start[nbins]) {
+    if (sz.w)
+      commit_one_sized(rec_id[i], g, xy, alive, heading, choice, won, cell, occ, ocls, sz.w, sz.h,
+                       moved, left);
+    else
+      commit_one(rec_id[i], g, xy, alive, heading, choice, won, cell, occ, ocls, moved, left);
+  }
   const unsigned nm = __popc(__ballot_sync(0xffffffffu, moved));
   const unsigned nl = __popc(__ballot_sync(0xffffffffu, left));
   if ((threadIdx.x & 31) == 0) {
@@ -773,10 +793,10 @@ __global__ void k_commit(const int32_t* __restrict__ rec_id, const int32_t* __re
 void launch_commit(int n, const int32_t* rec_id, const int32_t* bin_start, int2* xy,
                    uint8_t* alive, uint8_t* heading, const uint8_t* choice, const uint8_t* won,
                    const uint8_t* cell, int32_t* occ, uint8_t* ocls, const Geo& g, Counters* ctr,
-                   cudaStream_t s) {
+                   cudaStream_t s, const Sizes& sz) {
   const int blocks = n > 0 ? cdiv(n, 256) : 1;
   k_commit<<<blocks, 256, 0, s>>>(rec_id, bin_start, g.nbx * g.nby, xy, alive, heading, choice,
-                                  won, cell, occ, ocls, g, ctr);
+                                  won, cell, occ, ocls, g, ctr, sz);
 }
 
 }  // namespace sfm

@@ -989,6 +989,7 @@ sfm_status check_ctx(sfm_surrogate* S, sfm_ctx* ctx) {
     return sfail(S, SFM_EINVAL, "near radius larger than the field radius");
   if (!ctx->CT)
     return sfail(S, SFM_EINVAL, "field radius beyond the class-table gather (r > 50)");
+  if (ctx->sized) return sfail(S, SFM_EINVAL, "multi-su pedestrians are not supported here");
   return SFM_OK;
 }
 

@@ -90,3 +90,43 @@ class OracleRun:
         self.st.t += 1
         self.st.exited += left
         return won, maxc
+
+
+def rect_cells(W, H, px, py, x, y, w, h):
+    """su of the w x h rectangle centred on (x, y); None if it leaves a closed
+    lattice."""
+    out = set()
+    x, y, w, h = int(x), int(y), int(w), int(h)
+    for j in range(-(h // 2), h // 2 + 1):
+        for i in range(-(w // 2), w // 2 + 1):
+            u, v = x + i, y + j
+            if px:
+                u %= W
+            elif not 0 <= u < W:
+                return None
+            if py:
+                v %= H
+            elif not 0 <= v < H:
+                return None
+            out.add((u, v))
+    return out
+
+
+def sized_subset(sc, size):
+    """The scene's pedestrians whose size x size rectangles fit: inside, off
+    walls, centre on a FREE su, no overlap with an earlier one.  Returns a
+    scene of those pedestrians and their sizes."""
+    import scenegen as SG
+    keep, taken = [], set()
+    for p in range(sc.n):
+        rc = rect_cells(sc.W, sc.H, sc.periodic_x, sc.periodic_y, sc.xy[p, 0], sc.xy[p, 1],
+                        size[p], size[p])
+        if rc is None or rc & taken or any(sc.cell[v, u] == SG.WALL for u, v in rc):
+            continue
+        if sc.cell[sc.xy[p, 1], sc.xy[p, 0]] != SG.FREE:
+            continue
+        keep.append(p)
+        taken |= rc
+    sub = SG.Scene(sc.name + "-sized", sc.W, sc.H, sc.periodic_x, sc.periodic_y, sc.cell,
+                   sc.xy[keep].copy(), sc.heading[keep].copy(), sc.goal[keep].copy(), sc.params)
+    return sub, np.ascontiguousarray(size[keep], np.uint8)

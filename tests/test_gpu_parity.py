@@ -12,7 +12,7 @@ import oracle as O
 import paper_1803_04782_gb300 as sfm
 import scenegen as SG
 from paper_1803_04782_gb300 import build as B
-from parity import OracleRun, assert_field, compare_choices
+from parity import OracleRun, assert_field, compare_choices, sized_subset
 
 pytestmark = pytest.mark.gpu
 
@@ -206,6 +206,67 @@ def test_walk_periods_free_running_against_the_oracle(bands):
         assert e.value.status == sfm.SFM_EINVAL
         with pytest.raises(sfm.SfmError):
             sim.set_walk_periods(period, period)  # phase == period
+
+
+@pytest.mark.parametrize("bands,periodic", [(1, 0), (4, 0), (1, 1)])
+def test_multi_su_pedestrians_free_running_against_the_oracle(bands, periodic):
+    """Multi-su pedestrians (Sec. 2, Table V): 1x1, 3x3 and 5x5 rectangles in
+    one crowd run 25 ticks on their own, banded or not, closed with exits or
+    on a torus, identical to the oracle (admissibility over the entered
+    strip, claims in the vote, exits through any su of the rectangle)."""
+    sc = SG.random_scene(160, 128, 2600, r=10, seed=141, obstacles=0 if periodic else 3,
+                         periodic_x=periodic, periodic_y=periodic, ring=not periodic,
+                         exits=() if periodic else ("east", "west"), exit_len=14,
+                         goal_mode="mixed" if not periodic else "fixed", heading_mode="random")
+    rng = np.random.default_rng(11)
+    size = rng.choice(np.array([1, 3, 5], np.uint8), size=sc.n, p=[0.6, 0.3, 0.1])
+    sub, size = sized_subset(sc, size)
+    assert (size == 5).sum() > 10 and (size == 3).sum() > 50
+    orc = OracleRun(sub)
+    orc.st.w, orc.st.h = size, size
+    budget = sfm.band_budget(sub.W, sub.H, 32) if bands > 1 else 0
+    with sfm.Sim(sub, place=False, hbm_budget_bytes=budget) as sim:
+        sim.place_sized(sub.xy, sub.heading, sub.goal, np.ones(sub.n, np.uint8), size, size)
+        for t in range(25):
+            sim.step(1)
+            Fo, So = orc.field()
+            ch_o, E, T, adm = orc.decide(Ffull=Fo.ravel(), Sfull=So.ravel())
+            ch_g, won_g = sim.decisions()
+            assert compare_choices(ch_g, ch_o, E, T, adm) == 0, f"tie flip at tick {t}"
+            won_o, maxc = orc.advance(ch_o)
+            assert maxc <= 8
+            np.testing.assert_array_equal(won_g, won_o, err_msg=f"tick {t}")
+            for x, y in zip(sim.peds(), (orc.st.xy, orc.st.heading, orc.st.alive)):
+                np.testing.assert_array_equal(x, y)
+        st = sim.stats()
+        assert st["error_flags"] == 0 and st["exited"] == orc.st.exited
+        if not periodic:
+            assert np.any((orc.st.alive == 0) & (size > 1)), "no multi-su pedestrian left"
+
+
+def test_multi_su_placement_errors():
+    sc = SG.random_scene(60, 50, 40, r=4, seed=142, exits=("east",))
+    sub, size = sized_subset(sc, np.full(sc.n, 3, np.uint8))
+    one = np.ones(sub.n, np.uint8)
+    with sfm.Sim(sub, place=False) as sim:
+        bad = size.copy()
+        bad[0] = 2
+        with pytest.raises(sfm.SfmError) as e:
+            sim.place_sized(sub.xy, sub.heading, sub.goal, one, bad, size)
+        assert e.value.status == sfm.SFM_EINVAL
+        xy = sub.xy.copy()
+        xy[1] = xy[0] + np.array([2, 0], np.int32)   # rectangles overlap
+        with pytest.raises(sfm.SfmError) as e:
+            sim.place_sized(xy, sub.heading, sub.goal, one, size, size)
+        assert e.value.status == sfm.SFM_ECONFLICT
+        xy = sub.xy.copy()
+        xy[0] = (1, 1)                                # rectangle on the wall ring
+        with pytest.raises(sfm.SfmError) as e:
+            sim.place_sized(xy, sub.heading, sub.goal, one, size, size)
+        assert e.value.status == sfm.SFM_ECONFLICT
+        sim.place_sized(sub.xy, sub.heading, sub.goal, one, size, size)
+        sim.step(3)
+        assert sim.stats()["error_flags"] == 0
 
 
 @pytest.mark.parametrize("periodic", [0, 1])
