@@ -651,6 +651,8 @@ def run_paper_sweep(args):
     B.build()
     sfm.lib()
     stream = torch.cuda.current_stream()
+    if args.workload == "paper-sizes":
+        return run_paper_sizes(args)
     if args.workload == "paper-windows":
         cases = [(r, 1) for r in (3, 10, 17, 24, 31, 38)]
         paper_s = [62, 317, 738, 1424, 2187, 3238]
@@ -708,6 +710,62 @@ def run_paper_sweep(args):
     return 0
 
 
+def run_paper_sizes(args):
+    """Table V's shape: pedestrian geometry g x g (g = 1 ... 11) on a periodic
+    1000^2 lattice covering half its area (500 000 / g^2 pedestrians), field
+    window 7g x 7g, crossed with maximal walk periods 1 ... 11; graph-replayed
+    ticks timed with CUDA events.  The paper's seconds per 1000 ticks are
+    given beside (context only)."""
+    import torch
+    import paper_1803_04782_gb300 as sfm
+    import scenegen as SG
+    from paper_1803_04782_gb300 import build as B
+
+    B.build()
+    sfm.lib()
+    stream = torch.cuda.current_stream()
+    paper = {1: [63.5, 63.9, 64.0, 63.8, 63.7, 63.9], 3: [264.6, 261.7, 264.1, 262.9, 262.2, 261.8],
+             5: [213.5, 202.0, 204.6, 201.3, 200.1, 200.8], 7: [207.7, 197.1, 195.5, 193.9, 194.5, 193.8],
+             9: [197.6, 186.9, 184.4, 182.0, 184.2, 182.1], 11: [201.5, 192.5, 191.2, 191.6, 190.5, 189.6]}
+    ticks = max(5, min(args.steps, 30))
+    rows = []
+    for g in (1, 3, 5, 7, 9, 11):
+        sc, size = SG.paper_sized_scene(g=g)
+        with sfm.Sim(sc, stream=stream, place=False) as sim:
+            sim.place_sized(sc.xy, sc.heading, sc.goal, np.ones(sc.n, np.uint8), size, size)
+            fp = sim.autotune()
+            for pi, pmax in enumerate((1, 3, 5, 7, 9, 11)):
+                if pmax > 1:
+                    per, pha = SG.walk_periods(sc.n, pmax)
+                    sim.set_walk_periods(per, pha)
+                else:
+                    sim.set_walk_periods(None)
+                sim.step(args.warmup)
+                torch.cuda.synchronize()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                sim.step(ticks)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1) / ticks
+                alive = sim.stats()["alive"]
+                rows.append({"ped_side": g, "peds": sc.n, "window": (7 * g) ** 2,
+                             "walk_period_max": pmax, "footprint": fp, "ms_per_tick": ms,
+                             "ped_steps_per_s": alive / (ms / 1e3),
+                             "paper_ms_per_tick": paper[g][pi],
+                             "paper_over_this": paper[g][pi] / ms})
+    line = {"metric": "pedestrian-steps/s", "value": rows[0]["ped_steps_per_s"],
+            "unit": "ped-steps/s", "n_gpus": 1, "steps": ticks, "warmup": args.warmup,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "Table V: pedestrian geometry x maximal walk period, 1000^2 su, "
+                                   "half the area covered, 8 directions, fields 7g x 7g"},
+            "rows": rows}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -716,7 +774,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="floor",
                     choices=["floor", "floor-small", "corridor", "room", "batch", "batch-small",
-                             "surrogate", "surrogate-eval", "paper-windows", "paper-periods"])
+                             "surrogate", "surrogate-eval", "paper-windows", "paper-periods",
+                             "paper-sizes"])
     ap.add_argument("--bands", type=int, default=4,
                     help="row bands of the divide-and-conquer field pass (1 = unbanded)")
     ap.add_argument("--e2e-steps", type=int, default=10)

@@ -354,6 +354,25 @@ def paper_scene(side=1000, density=0.5, ndir=8, r=3, seed=11, name="paper") -> S
     return Scene(name, side, side, 1, 1, cell, xy, goal.copy(), goal, _params(r=r))
 
 
+def paper_sized_scene(g=3, side=1000, density=0.5, ndir=8, seed=13, name="paper-sized"):
+    """Table V's shape: g x g pedestrians (g odd) on a periodic side x side
+    lattice covering `density` of its area, i.e. round(density * side^2 / g^2)
+    pedestrians, field window 7g x 7g (r = (7g - 1) / 2).  Centres are the
+    centres of randomly chosen cells of a g x g block tiling, so rectangles
+    never overlap.  Returns (scene, sizes)."""
+    rng = np.random.default_rng(seed)
+    nb = side // g
+    n = int(round(density * side * side / (g * g)))
+    pick = rng.choice(nb * nb, size=n, replace=False)
+    xy = np.stack([(pick % nb) * g + g // 2, (pick // nb) * g + g // 2], axis=1).astype(np.int32)
+    dirs = np.array(FLOW_GOALS[ndir], np.uint8)
+    goal = dirs[np.arange(n) % len(dirs)]
+    rng.shuffle(goal)
+    cell = np.zeros((side, side), np.uint8)
+    sc = Scene(name, side, side, 1, 1, cell, xy, goal.copy(), goal, _params(r=(7 * g - 1) // 2))
+    return sc, np.full(n, g, np.uint8)
+
+
 def walk_periods(n, p_max, seed=12):
     """Walk periods uniform in [1, p_max] and phases uniform in [0, period)."""
     rng = np.random.default_rng(seed)
