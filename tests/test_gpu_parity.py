@@ -292,10 +292,10 @@ def test_banded_field_is_bitwise_the_unbanded_field(periodic):
 
 
 @pytest.mark.parametrize("name", ["room_mixed", "torus", "thin_torus", "wide_radius", "radius41",
-                                  "radius47"])
+                                  "radius47", "dense", "tall_r1"])
 def test_both_gather_footprints_give_the_same_field_and_ticks(name):
-    """The 16x16 and 32x16 warp footprints add each su's terms in the same
-    order: fields and ticks are bitwise equal, with and without the tuner."""
+    """The 16x16 and 32x16 footprints add each su's terms in the same order:
+    fields and ticks are bitwise equal, and equal to the autotuner's choice."""
     sc = SCENES[name]()
     with sfm.Sim(sc) as a, sfm.Sim(sc) as b, sfm.Sim(sc) as c:
         a.set_footprint("16x16")
@@ -309,6 +309,7 @@ def test_both_gather_footprints_give_the_same_field_and_ticks(name):
             for s in (a, b, c):
                 s.step(1)
             for s in (b, c):
+                np.testing.assert_array_equal(a.field(), s.field())
                 np.testing.assert_array_equal(a.decisions()[0], s.decisions()[0])
                 for x, y in zip(a.peds(), s.peds()):
                     np.testing.assert_array_equal(x, y)
