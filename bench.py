@@ -318,7 +318,7 @@ def run_gpu(args):
     # (what the stage events cost shows on small lattices); after the timed
     # region, not part of `value`
     graph_ticks = max(3, min(args.steps, 20))
-    sim.step(1)
+    sim.step(graph_ticks)  # builds (once) the graphs the timed call replays
     torch.cuda.synchronize()
     g0 = torch.cuda.Event(enable_timing=True)
     g1 = torch.cuda.Event(enable_timing=True)
@@ -670,7 +670,7 @@ def run_paper_sweep(args):
             if pmax > 1:
                 per, pha = SG.walk_periods(sc.n, pmax)
                 sim.set_walk_periods(per, pha)
-            sim.step(args.warmup)
+            sim.step(max(args.warmup, 9))  # also builds the 8-tick graph
             torch.cuda.synchronize()
             xy0, _, a0 = sim.peds()
             e0 = torch.cuda.Event(enable_timing=True)
@@ -740,7 +740,7 @@ def run_paper_sizes(args):
                     sim.set_walk_periods(per, pha)
                 else:
                     sim.set_walk_periods(None)
-                sim.step(args.warmup)
+                sim.step(max(args.warmup, 9))  # also builds the 8-tick graph
                 torch.cuda.synchronize()
                 e0 = torch.cuda.Event(enable_timing=True)
                 e1 = torch.cuda.Event(enable_timing=True)

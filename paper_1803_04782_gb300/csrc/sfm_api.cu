@@ -216,11 +216,18 @@ void run_tick(sfm_ctx* c) {
 void drop_graph(sfm_ctx* c) {
   if (c->tick_graph) cudaGraphExecDestroy(c->tick_graph);
   c->tick_graph = nullptr;
+  if (c->block_graph) cudaGraphExecDestroy(c->block_graph);
+  c->block_graph = nullptr;
   c->direct_ticks = 0;
 }
 
 // Capture one tick (all its launches, on a private stream) into a graph.
-cudaError_t build_tick_graph(sfm_ctx* c) {
+// Runs of at least this many ticks replay one graph holding that many ticks
+// (fewer launches for small lattices, where launching dominates).
+constexpr int kBlockTicks = 8;
+
+// Capture `ticks` ticks (all their launches, on a private stream) into a graph.
+cudaError_t build_tick_graph(sfm_ctx* c, int ticks, cudaGraphExec_t* exec, int64_t* launches) {
   cudaStream_t cs;
   cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
   if (e != cudaSuccess) return e;
@@ -230,17 +237,17 @@ cudaError_t build_tick_graph(sfm_ctx* c) {
   c->stream = cs;
   e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
-    run_tick(c);
+    for (int i = 0; i < ticks; ++i) run_tick(c);
     const cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
     e = e2;
   }
   c->stream = saved;
-  c->graph_launches = c->launches - l0;
+  *launches = c->launches - l0;
   c->launches = l0;
-  if (e == cudaSuccess) e = cudaGraphInstantiate(&c->tick_graph, graph, 0);
+  if (e == cudaSuccess) e = cudaGraphInstantiate(exec, graph, 0);
   if (graph) cudaGraphDestroy(graph);
   cudaStreamDestroy(cs);
-  if (e != cudaSuccess) c->tick_graph = nullptr;
+  if (e != cudaSuccess) *exec = nullptr;
   return e;
 }
 
@@ -605,24 +612,32 @@ sfm_status sfm_step(sfm_ctx* ctx, int32_t nsteps) {
   if (nsteps < 0) return fail(ctx, SFM_EINVAL, "nsteps < 0");
   if (ctx->batch) return batch_tick(ctx, nsteps, 0);
   if (!ctx->placed) return fail(ctx, SFM_ESTATE, "sfm_step before a successful sfm_place");
-  for (int i = 0; i < nsteps; ++i) {
+  for (int i = 0; i < nsteps;) {
     // timed ticks launch stage by stage (events between stages); otherwise the
-    // first tick after placement runs directly and the rest replay its graph
+    // first tick after placement runs directly and the rest replay graphs: of
+    // kBlockTicks ticks while that many remain, else of one tick
     if (ctx->timing || ctx->direct_ticks < 1) {
       run_tick(ctx);
       ++ctx->direct_ticks;
-    } else {
-      if (!ctx->tick_graph) {
-        const cudaError_t ge = build_tick_graph(ctx);
-        if (ge != cudaSuccess) {
-          cudaGetLastError();
-          return fail(ctx, SFM_ECUDA, "tick graph: %s", cudaGetErrorString(ge));
-        }
-      }
-      CU(cudaGraphLaunch(ctx->tick_graph, ctx->stream));
-      ctx->launches += ctx->graph_launches;
+      ++ctx->t;
+      ++i;
+      continue;
     }
-    ++ctx->t;
+    const bool block = nsteps - i >= kBlockTicks;
+    cudaGraphExec_t* exec = block ? &ctx->block_graph : &ctx->tick_graph;
+    int64_t* nl = block ? &ctx->block_launches : &ctx->graph_launches;
+    if (!*exec) {
+      const cudaError_t ge = build_tick_graph(ctx, block ? kBlockTicks : 1, exec, nl);
+      if (ge != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, SFM_ECUDA, "tick graph: %s", cudaGetErrorString(ge));
+      }
+    }
+    CU(cudaGraphLaunch(*exec, ctx->stream));
+    ctx->launches += *nl;
+    const int done = block ? kBlockTicks : 1;
+    ctx->t += done;
+    i += done;
   }
   if (ctx->timing) ctx->timed_ticks += nsteps;
   CU(cudaGetLastError());

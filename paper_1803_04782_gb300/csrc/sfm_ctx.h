@@ -82,6 +82,8 @@ struct sfm_ctx {
   // one tick captured as a CUDA graph (single lattice, untimed ticks)
   cudaGraphExec_t tick_graph = nullptr;
   int64_t graph_launches = 0;  // kernels in one replay of tick_graph
+  cudaGraphExec_t block_graph = nullptr;  // kBlockTicks ticks in one graph
+  int64_t block_launches = 0;
   int64_t direct_ticks = 0;    // ticks launched stage by stage since placement
   // batch of independent lattices (nullptr for a single lattice)
   sfm::BatchState* batch = nullptr;

@@ -345,6 +345,34 @@ def test_grid_and_pedestrian_list_binning_give_the_same_ticks(name):
         assert e.value.status == sfm.SFM_EINVAL
 
 
+@pytest.mark.parametrize("variant", ["plain", "periods", "sized"])
+def test_many_ticks_in_one_call_equal_single_ticks(variant):
+    """step(20) replays graphs of 8 ticks and of 1 tick; the trajectory equals
+    20 calls of step(1), with walk periods (gated on the device's tick
+    counter) and with multi-su pedestrians."""
+    sc = SG.random_scene(200, 160, 3000, r=9, seed=151, obstacles=3, exits=("east",),
+                         goal_mode="mixed", heading_mode="random")
+    size = None
+    if variant == "sized":
+        rng = np.random.default_rng(3)
+        sc, size = sized_subset(sc, rng.choice(np.array([1, 3], np.uint8), size=sc.n))
+    with sfm.Sim(sc, place=size is None) as a, sfm.Sim(sc, place=size is None) as b:
+        if size is not None:
+            for s in (a, b):
+                s.place_sized(sc.xy, sc.heading, sc.goal, np.ones(sc.n, np.uint8), size, size)
+        if variant == "periods":
+            per, pha = SG.walk_periods(sc.n, 4)
+            for s in (a, b):
+                s.set_walk_periods(per, pha)
+        for _ in range(20):
+            a.step(1)
+        b.step(20)
+        for x, y in zip(a.peds(), b.peds()):
+            np.testing.assert_array_equal(x, y)
+        assert a.stats()["exited"] == b.stats()["exited"]
+        assert b.stats()["error_flags"] == 0
+
+
 def test_field_respects_heading_linearity_closed_form():
     """A single pedestrian in an open periodic lattice: the GPU field equals
     the closed form k d^a (1 + gamma cos) to FP32 rounding."""
