@@ -1,5 +1,6 @@
 // sfm_internal.h -- device data layout and kernel launchers shared by the
-// C-ABI host code (sfm_api.cu) and the kernels (sfm_kernels.cu).
+// C-ABI host code (sfm_api.cu) and the kernels (sfm_kernels.cu, sfm_field.cu,
+// sfm_batch.cu, sfm_surrogate.cu, sfm_noalloc.cu).
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -11,8 +12,8 @@ namespace sfm {
 constexpr int kFree = 0, kWall = 1, kExit = 2;
 constexpr int32_t kDInf = 1 << 23;  // guidance distance of unreachable / WALL su
 
-// Field gather tiling: a CTA owns a 32 x 32 su tile; warp w owns rows
-// 4w..4w+3 of it, lane l owns column l.
+// Three-component field gather (radius > 50): a CTA owns a 32 x 32 su tile;
+// warp w owns rows 4w..4w+3 of it, lane l owns column l.
 constexpr int kTile = 32;
 constexpr int kFieldThreads = 256;
 constexpr int kRowsPerThread = kTile / (kFieldThreads / 32);  // 4

@@ -485,8 +485,10 @@ void launch_scan(const int32_t* in, int32_t* out, int n, int32_t* block_tmp, cud
   k_scan_final<<<nb, kScanThreads, 0, s>>>(in, n, block_tmp, out);
 }
 
-// ------------------------------------------------------ S2: field gather
-// Each CTA owns a 32 x 32 su tile.  The pedestrians of the bins that overlap
+// ------------------------------------ S2: field gather for radius > 50
+// Used where the heading-class tables would not fit in shared memory (the
+// class-table gather in sfm_field.cu covers radius <= 50).  Each CTA owns a
+// 32 x 32 su tile.  The pedestrians of the bins that overlap
 // the tile's r-halo are staged in shared memory in chunks of at most `cap`
 // records (the bounded multi-step sum of Alg. 3 / Eq. 1: the per-su sum is
 // split into a fixed number of partial passes), every lane accumulates the
