@@ -164,6 +164,19 @@ sfm_status sfm_compute_field(sfm_ctx* ctx);
  * nobody. */
 sfm_status sfm_autotune(sfm_ctx* ctx, int32_t* shape_out);
 
+/* Checkpoint and resume.  sfm_snapshot writes the context's dynamic state
+ * (tick counter, exit and move counters, every pedestrian's position,
+ * heading, goal and alive flag, and its walk period and size when set) into
+ * buf, a caller-owned host buffer of *len bytes; buf == NULL only stores the
+ * size needed in *len (a buffer too small is SFM_EINVAL, *len = size
+ * needed).  sfm_restore places that state in a context created with the same
+ * lattice, cells and model parameters (lattice size, boundaries, radius and
+ * the parameters are checked; SFM_EINVAL otherwise, the context unchanged);
+ * the run then continues bit for bit as the snapshotted one would.  The
+ * format is this library's (little-endian, versioned).  Both synchronise. */
+sfm_status sfm_snapshot(sfm_ctx* ctx, void* buf, size_t* len);
+sfm_status sfm_restore(sfm_ctx* ctx, const void* buf, size_t len);
+
 /* Multi-su pedestrians (Sec. 2 of the paper; its Table V): as sfm_place, plus
  * width[n] and height[n] (host or device per on_device): odd sides in
  * [1, 15].  Pedestrian p occupies the width x height rectangle of su centred

@@ -34,7 +34,7 @@ EXPORTS = [
     "sfm_compute_field_into", "sfm_read_static_field", "sfm_read_guidance", "sfm_read_peds",
     "sfm_read_decisions", "sfm_stats", "sfm_set_timing", "sfm_stage_times",
     "sfm_autotune", "sfm_set_field_footprint", "sfm_set_binning", "sfm_set_walk_periods",
-    "sfm_place_sized", "sfm_field_noalloc", "sfm_batch_create", "sfm_batch_place", "sfm_batch_offsets",
+    "sfm_place_sized", "sfm_snapshot", "sfm_restore", "sfm_field_noalloc", "sfm_batch_create", "sfm_batch_place", "sfm_batch_offsets",
     "sfm_batch_autotune", "sfm_batch_test_missing_ctas", "sfm_surrogate_nparams",
     "sfm_surrogate_create", "sfm_surrogate_destroy", "sfm_surrogate_last_error",
     "sfm_surrogate_set_params", "sfm_surrogate_get_params", "sfm_surrogate_grad",
@@ -118,6 +118,8 @@ def lib():
             "sfm_set_binning": (C.c_int, [P, I32]),
             "sfm_set_walk_periods": (C.c_int, [P, P, P, I32]),
             "sfm_place_sized": (C.c_int, [P, I32, P, P, P, P, P, P, I32]),
+            "sfm_snapshot": (C.c_int, [P, P, C.POINTER(C.c_size_t)]),
+            "sfm_restore": (C.c_int, [P, P, C.c_size_t]),
             "sfm_stage_times": (C.c_int, [P, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
             "sfm_field_noalloc": (C.c_int, [C.POINTER(Lattice), C.POINTER(Params), I32, P, P, P,
                                             P, P, P]),
@@ -464,6 +466,20 @@ class Sim:
 
     def autotune(self):
         return sfm_autotune(self.ctx)
+
+    def snapshot(self) -> bytes:
+        """The context's dynamic state as bytes (see sfm_snapshot)."""
+        n = C.c_size_t(0)
+        _check(self.ctx, lib().sfm_snapshot(self.ctx, None, C.byref(n)))
+        buf = C.create_string_buffer(n.value)
+        _check(self.ctx, lib().sfm_snapshot(self.ctx, buf, C.byref(n)))
+        return buf.raw[:n.value]
+
+    def restore(self, snap: bytes):
+        """Continue from a snapshot of a context on the same lattice."""
+        buf = C.create_string_buffer(bytes(snap), len(snap))
+        _check(self.ctx, lib().sfm_restore(self.ctx, buf, len(snap)))
+        self.n = int(np.frombuffer(bytes(snap)[56:64], np.int64)[0])  # header field n
 
     def place_sized(self, xy, heading, goal, alive, width, height):
         """Place multi-su pedestrians (odd width x height rectangles)."""

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdarg.h>
 #include <stdio.h>
+#include <stdint.h>
 #include <string.h>
 
 #include <algorithm>
@@ -813,6 +814,156 @@ sfm_status sfm_read_peds(sfm_ctx* ctx, int32_t* xy, uint8_t* heading, uint8_t* a
     if (alive) CU(cudaMemcpyAsync(alive, ctx->alive, n, kind, ctx->stream));
   }
   return check_flags(ctx);
+}
+
+// ---------------------------------------------------------- checkpoints
+namespace {
+
+struct SnapHeader {
+  char magic[8];
+  uint32_t version, flags;  // flags: 1 walk periods, 2 multi-su sizes
+  int32_t W, H, px, py, r, pad_;
+  uint64_t params_fp;  // fingerprint of the model parameters
+  int64_t t, n;
+  uint64_t exited, moved;
+};
+constexpr char kSnapMagic[8] = {'S', 'F', 'M', 'S', 'N', 'A', 'P', '1'};
+constexpr uint32_t kSnapPeriods = 1u, kSnapSizes = 2u;
+
+// FNV-1a over the parameters that decide a trajectory (not the HBM budget)
+uint64_t params_fingerprint(const sfm_params& p) {
+  uint64_t h = 1469598103934665603ull;
+  auto mix = [&h](const void* d, size_t n) {
+    const unsigned char* b = static_cast<const unsigned char*>(d);
+    for (size_t i = 0; i < n; ++i) h = (h ^ b[i]) * 1099511628211ull;
+  };
+  mix(&p.r, sizeof p.r);
+  mix(&p.kP, sizeof p.kP);
+  mix(&p.aP, sizeof p.aP);
+  mix(&p.gamma, sizeof p.gamma);
+  mix(&p.kO, sizeof p.kO);
+  mix(&p.aO, sizeof p.aO);
+  mix(&p.kE, sizeof p.kE);
+  mix(&p.aE, sizeof p.aE);
+  mix(&p.beta, sizeof p.beta);
+  mix(&p.seed, sizeof p.seed);
+  return h;
+}
+
+size_t snap_bytes(int64_t n, uint32_t flags) {
+  size_t per = 8 + 3;  // xy, heading, goal, alive
+  if (flags & kSnapPeriods) per += 2;
+  if (flags & kSnapSizes) per += 2;
+  return sizeof(SnapHeader) + (size_t)n * per;
+}
+
+}  // namespace
+
+sfm_status sfm_snapshot(sfm_ctx* ctx, void* buf, size_t* len) {
+  if (!ctx || !len) return SFM_EINVAL;
+  if (ctx->batch) return fail(ctx, SFM_EINVAL, "snapshots are per single lattice");
+  if (!ctx->placed) return fail(ctx, SFM_ESTATE, "nothing placed");
+  const uint32_t flags = (ctx->walk_periods ? kSnapPeriods : 0u) | (ctx->sized ? kSnapSizes : 0u);
+  const int64_t n = ctx->n;
+  const size_t need = snap_bytes(n, flags);
+  if (!buf) {
+    *len = need;
+    return SFM_OK;
+  }
+  if (*len < need) {
+    *len = need;
+    return fail(ctx, SFM_EINVAL, "snapshot buffer of %zu bytes, %zu needed", *len, need);
+  }
+  CU(cudaStreamSynchronize(ctx->stream));
+  Counters hc;
+  CU(cudaMemcpy(&hc, ctx->ctr, sizeof(hc), cudaMemcpyDeviceToHost));
+  SnapHeader hd{};
+  memcpy(hd.magic, kSnapMagic, 8);
+  hd.version = 1;
+  hd.flags = flags;
+  hd.W = ctx->geo.W;
+  hd.H = ctx->geo.H;
+  hd.px = ctx->geo.px;
+  hd.py = ctx->geo.py;
+  hd.r = ctx->geo.r;
+  hd.params_fp = params_fingerprint(ctx->prm);
+  hd.t = hc.t;
+  hd.n = n;
+  hd.exited = hc.exited;
+  hd.moved = hc.moved;
+  unsigned char* o = static_cast<unsigned char*>(buf);
+  memcpy(o, &hd, sizeof hd);
+  o += sizeof hd;
+  auto take = [&](const void* src, size_t bytes) -> cudaError_t {
+    const cudaError_t e = bytes ? cudaMemcpy(o, src, bytes, cudaMemcpyDeviceToHost) : cudaSuccess;
+    o += bytes;
+    return e;
+  };
+  CU(take(ctx->xy, (size_t)n * 8));
+  CU(take(ctx->heading, (size_t)n));
+  CU(take(ctx->goal, (size_t)n));
+  CU(take(ctx->alive, (size_t)n));
+  if (flags & kSnapPeriods) {
+    CU(take(ctx->period, (size_t)n));
+    CU(take(ctx->phase, (size_t)n));
+  }
+  if (flags & kSnapSizes) {
+    CU(take(ctx->pw, (size_t)n));
+    CU(take(ctx->ph, (size_t)n));
+  }
+  *len = need;
+  return SFM_OK;
+}
+
+sfm_status sfm_restore(sfm_ctx* ctx, const void* buf, size_t len) {
+  if (!ctx || !buf) return SFM_EINVAL;
+  if (ctx->batch) return fail(ctx, SFM_EINVAL, "snapshots are per single lattice");
+  SnapHeader hd;
+  if (len < sizeof hd) return fail(ctx, SFM_EINVAL, "snapshot shorter than its header");
+  memcpy(&hd, buf, sizeof hd);
+  if (memcmp(hd.magic, kSnapMagic, 8) != 0 || hd.version != 1)
+    return fail(ctx, SFM_EINVAL, "not a snapshot of this library (magic or version)");
+  if (hd.n < 0 || hd.n > INT32_MAX || (hd.flags & ~(kSnapPeriods | kSnapSizes)) ||
+      len != snap_bytes(hd.n, hd.flags))
+    return fail(ctx, SFM_EINVAL, "snapshot length or flags do not match its header");
+  if (hd.W != ctx->geo.W || hd.H != ctx->geo.H || hd.px != ctx->geo.px || hd.py != ctx->geo.py ||
+      hd.r != ctx->geo.r || hd.params_fp != params_fingerprint(ctx->prm))
+    return fail(ctx, SFM_EINVAL, "snapshot of another lattice or other model parameters");
+  const unsigned char* in = static_cast<const unsigned char*>(buf) + sizeof hd;
+  const int32_t n = (int32_t)hd.n;
+  const int32_t* xy = reinterpret_cast<const int32_t*>(in);
+  const uint8_t* heading = in + (size_t)n * 8;
+  const uint8_t* goal = heading + n;
+  const uint8_t* alive = goal + n;
+  const uint8_t* extra = alive + n;
+  const uint8_t *period = nullptr, *phase = nullptr, *w = nullptr, *h = nullptr;
+  if (hd.flags & kSnapPeriods) {
+    period = extra;
+    phase = extra + n;
+    extra += 2 * (size_t)n;
+  }
+  if (hd.flags & kSnapSizes) {
+    w = extra;
+    h = extra + n;
+  }
+  // xy may be unaligned inside the buffer: copy to aligned storage
+  std::vector<int32_t> xya((size_t)n * 2);
+  if (n) memcpy(xya.data(), xy, (size_t)n * 8);
+  sfm_status st = place_impl(ctx, n, xya.data(), heading, goal, alive, w, h, 0);
+  if (st != SFM_OK) return st;
+  if (period) {
+    st = sfm_set_walk_periods(ctx, period, phase, 0);
+    if (st != SFM_OK) return st;
+  }
+  CU(cudaStreamSynchronize(ctx->stream));
+  Counters hc;
+  CU(cudaMemcpy(&hc, ctx->ctr, sizeof(hc), cudaMemcpyDeviceToHost));
+  hc.t = hd.t;
+  hc.exited = hd.exited;
+  hc.moved = hd.moved;
+  CU(cudaMemcpy(ctx->ctr, &hc, sizeof(hc), cudaMemcpyHostToDevice));
+  ctx->t = hd.t;
+  return SFM_OK;
 }
 
 sfm_status sfm_read_decisions(sfm_ctx* ctx, uint8_t* choice, uint8_t* won, int32_t on_device) {

@@ -106,3 +106,10 @@ def test_resident_bytes_and_band_budget():
     lat = sfm.Lattice(16384, 16384, 0, 0)
     assert sfm.sfm_resident_bytes(lat) == 16384 * 16384 * 14
     assert sfm.band_budget(16384, 16384, 4096) == 16384 * 16384 * 14 + 4 * 16384 * 4098
+
+
+def test_snapshot_calls_reject_null_without_a_gpu():
+    import ctypes as C
+    n = C.c_size_t(0)
+    assert sfm.lib().sfm_snapshot(None, None, C.byref(n)) == sfm.SFM_EINVAL
+    assert sfm.lib().sfm_restore(None, None, 0) == sfm.SFM_EINVAL

@@ -373,6 +373,48 @@ def test_many_ticks_in_one_call_equal_single_ticks(variant):
         assert b.stats()["error_flags"] == 0
 
 
+@pytest.mark.parametrize("variant", ["plain", "periods", "sized"])
+def test_snapshot_restore_continues_bit_for_bit(variant):
+    """Checkpoint and resume: a snapshot taken after 7 ticks, restored into a
+    fresh context on the same lattice, continues exactly as the original run
+    (positions, headings, exits, tick counter); snapshots of other lattices
+    or parameters, and damaged buffers, are refused."""
+    sc = SG.random_scene(180, 150, 2500, r=8, seed=161, obstacles=3, exits=("west",),
+                         goal_mode="mixed", heading_mode="random")
+    size = None
+    if variant == "sized":
+        sc, size = sized_subset(sc, np.random.default_rng(4).choice(np.array([1, 3], np.uint8),
+                                                                     size=sc.n))
+    with sfm.Sim(sc, place=size is None) as a, sfm.Sim(sc, place=False) as b:
+        if size is not None:
+            a.place_sized(sc.xy, sc.heading, sc.goal, np.ones(sc.n, np.uint8), size, size)
+        if variant == "periods":
+            a.set_walk_periods(*SG.walk_periods(sc.n, 5))
+        a.step(7)
+        snap = a.snapshot()
+        a.step(12)
+        b.restore(snap)
+        assert b.stats()["t"] == 7
+        b.step(12)
+        for x, y in zip(a.peds(), b.peds()):
+            np.testing.assert_array_equal(x, y)
+        sa, sb = a.stats(), b.stats()
+        assert (sa["t"], sa["exited"], sa["alive"]) == (sb["t"], sb["exited"], sb["alive"])
+        for bad in (snap[:-1], b"XXXXXXXX" + snap[8:]):
+            with pytest.raises(sfm.SfmError) as e:
+                b.restore(bad)
+            assert e.value.status == sfm.SFM_EINVAL
+    other = SG.random_scene(180, 151, 10, r=8, seed=162)
+    with sfm.Sim(other, place=False) as c:
+        with pytest.raises(sfm.SfmError) as e:
+            c.restore(snap)
+        assert e.value.status == sfm.SFM_EINVAL
+    with sfm.Sim(sc, place=False, beta=2.0) as d:
+        with pytest.raises(sfm.SfmError) as e:
+            d.restore(snap)
+        assert e.value.status == sfm.SFM_EINVAL
+
+
 def test_field_respects_heading_linearity_closed_form():
     """A single pedestrian in an open periodic lattice: the GPU field equals
     the closed form k d^a (1 + gamma cos) to FP32 rounding."""
