@@ -113,3 +113,18 @@ def test_snapshot_calls_reject_null_without_a_gpu():
     n = C.c_size_t(0)
     assert sfm.lib().sfm_snapshot(None, None, C.byref(n)) == sfm.SFM_EINVAL
     assert sfm.lib().sfm_restore(None, None, 0) == sfm.SFM_EINVAL
+
+
+def test_create_refuses_a_budget_too_small_before_allocating():
+    """Failure injection on the host: an HBM budget below the resident arrays,
+    or leaving room for fewer than 32 field rows, is SFM_EBUDGET."""
+    import numpy as np
+    cell = np.zeros((200, 300), np.uint8)
+    L = sfm.Lattice(300, 200, 0, 0)
+    resident = sfm.sfm_resident_bytes(L)
+    for budget, msg in ((resident - 1, "resident arrays"),
+                        (resident + 4 * 300 * 20, "fewer than 32 field rows")):
+        with pytest.raises(sfm.SfmError) as e:
+            sfm.sfm_create(L, cell, sfm.make_params(r=3, hbm_budget_bytes=budget))
+        assert e.value.status == sfm.SFM_EBUDGET
+        assert msg in str(e.value)
