@@ -343,7 +343,11 @@ def run_gpu(args):
                 "traffic_unit": "bytes per launch",
                 "kernel": "k_field_v2", "field_ms_per_step": 1e3 * field_s / args.steps,
                 "pairs_per_step": pairs,
-                "peak_basis": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz (max clock)"}
+                "peak_basis": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz (max clock)",
+                # the gather's binding resource: one 128-byte shared-memory
+                # wavefront (32 table words) per clock per SM, one word a pair
+                "smem_pair_frac": pairs * args.steps / field_s / (SMS * 32 * SM_MAX_MHZ * 1e6),
+                "smem_basis": "pairs/s over 152 SMs x 32 table words x 2070 MHz"}
 
     # end to end through the C ABI with host buffers
     e2e_steps = min(args.steps, args.e2e_steps)
