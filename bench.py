@@ -556,7 +556,7 @@ def run_surrogate(args):
         ev = sorted(evs, key=lambda e: e["ms_surrogate"])[1]
         out = {"delta": d, **{k: ev[k] for k in ("field_rel_err", "flip_rate", "flip_rate_raw",
                                                  "fallback_rate", "ms_surrogate", "ms_exact",
-                                                 "decided")}}
+                                                 "ms_surrogate_field", "decided")}}
         if timed:
             n = max(3, min(args.steps, 10))
             out["ms_tick_surrogate"] = tick_ms(lambda k: sur.step(sim, k), n)
@@ -614,7 +614,8 @@ def run_surrogate(args):
 
 
 def run_surrogate_eval(args):
-    """One surrogate evaluation on the 16384^2 floor with the seeded
+    """One surrogate evaluation on the 16384^2 floor (4096^2 for
+    surrogate-eval-small, the case for counter captures) with the seeded
     (untrained) network, s = 8, r_n = 3: calibrate delta (99.9th percentile)
     and judge twice; prints the second report (the case the surrogate's
     launch-list profile covers)."""
@@ -626,7 +627,7 @@ def run_surrogate_eval(args):
     B.build()
     sfm.lib()
     stream = torch.cuda.current_stream()
-    sc, desc = workload("floor")
+    sc, desc = workload("floor-small" if args.workload.endswith("small") else "floor")
     with sfm.Sim(sc, stream=stream) as sim, \
             sfm.Surrogate(coarsen=8, near_radius=3, params=sfm.flatten_params(SG.surrogate_init(0)),
                           stream=stream) as sur:
@@ -778,7 +779,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="floor",
                     choices=["floor", "floor-small", "corridor", "room", "batch", "batch-small",
-                             "surrogate", "surrogate-eval", "paper-windows", "paper-periods",
+                             "surrogate", "surrogate-eval", "surrogate-eval-small", "paper-windows", "paper-periods",
                              "paper-sizes"])
     ap.add_argument("--bands", type=int, default=4,
                     help="row bands of the divide-and-conquer field pass (1 = unbanded)")
@@ -793,7 +794,7 @@ def main():
         return run_batch(args)
     if args.workload == "surrogate":
         return run_surrogate(args)
-    if args.workload == "surrogate-eval":
+    if args.workload in ("surrogate-eval", "surrogate-eval-small"):
         return run_surrogate_eval(args)
     if args.workload.startswith("paper-"):
         return run_paper_sweep(args)

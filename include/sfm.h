@@ -48,7 +48,7 @@
 extern "C" {
 #endif
 
-#define SFM_ABI_VERSION 2
+#define SFM_ABI_VERSION 3
 #define SFM_MAX_RADIUS 64
 #define SFM_NSTAGES 6
 
@@ -350,7 +350,10 @@ sfm_status sfm_surrogate_train(sfm_surrogate* sur, sfm_ctx* ctx, int32_t iters, 
 /* surrogate field of ctx's current state into out (W*H floats, host or device) */
 sfm_status sfm_surrogate_field(sfm_surrogate* sur, sfm_ctx* ctx, float* out, int32_t on_device);
 /* Decisions with the exact field as fallback.  A tick of sfm_surrogate_step
- * decides every live pedestrian on F_sur; a pedestrian whose energy margin
+ * runs the network on the tick's coarse inputs and decides every live
+ * pedestrian on F_sur composed at its 9 candidates (the values the lattice
+ * pass of sfm_surrogate_field writes there, up to FP32 rounding; the fine
+ * lattice itself is not written); a pedestrian whose energy margin
  * (second-best minus best candidate) is at most delta (plus a rounding
  * allowance) is decided again on the exact field at its admissible
  * candidates, computed bit for bit as the exact gather computes it.  If
@@ -363,8 +366,8 @@ sfm_status sfm_surrogate_field(sfm_surrogate* sur, sfm_ctx* ctx, float* out, int
  *   (in [0, 1]) over live pedestrians of the spread max - min of F_sur - F
  *   over their admissible candidates; *delta_out (may be NULL) receives it.
  *   Overwrites ctx's field buffer.
- * sfm_surrogate_step: nsteps ticks of ctx (clear, bins, surrogate field,
- *   decisions with the fallback, vote, commit), asynchronous on ctx's stream.
+ * sfm_surrogate_step: nsteps ticks of ctx (clear, bins, network, decisions
+ *   with the fallback, vote, commit), asynchronous on ctx's stream.
  *   Field radius <= 50 (the exact fallback reuses the class-table gather).
  * sfm_surrogate_counts: totals over all surrogate ticks so far of the
  *   pedestrians that fell back and of those decided (synchronising). */
@@ -380,10 +383,14 @@ sfm_status sfm_surrogate_counts(sfm_surrogate* sur, int64_t* fallbacks, int64_t*
  *                  with the fallback, differs from the exact path's;
  *   flip_rate_raw  the same without the fallback (decisions on F_sur alone);
  *   fallback_rate  fraction that fell back;
- *   ms_surrogate   bins + surrogate field + decisions with the fallback;
- *   ms_exact       bins + exact field + decisions (CUDA events, ctx stream). */
+ *   ms_surrogate   bins + network + decisions with the fallback (the
+ *                  decision part of a surrogate tick);
+ *   ms_exact       bins + exact field + decisions (CUDA events, ctx stream);
+ *   ms_surrogate_field  network + the lattice pass of sfm_surrogate_field
+ *                  (the surrogate field of every su; its field_rel_err). */
 typedef struct sfm_surrogate_report {
-  double field_rel_err, flip_rate, flip_rate_raw, fallback_rate, ms_surrogate, ms_exact;
+  double field_rel_err, flip_rate, flip_rate_raw, fallback_rate, ms_surrogate, ms_exact,
+      ms_surrogate_field;
   float delta;
   int32_t decided;
 } sfm_surrogate_report;

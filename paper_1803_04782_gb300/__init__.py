@@ -80,8 +80,8 @@ class SurrogateCfg(C.Structure):
 class SurrogateReport(C.Structure):
     _fields_ = [("field_rel_err", C.c_double), ("flip_rate", C.c_double),
                 ("flip_rate_raw", C.c_double), ("fallback_rate", C.c_double),
-                ("ms_surrogate", C.c_double), ("ms_exact", C.c_double), ("delta", C.c_float),
-                ("decided", C.c_int32)]
+                ("ms_surrogate", C.c_double), ("ms_exact", C.c_double),
+                ("ms_surrogate_field", C.c_double), ("delta", C.c_float), ("decided", C.c_int32)]
 
 
 def lib():

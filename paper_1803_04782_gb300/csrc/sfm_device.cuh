@@ -16,10 +16,36 @@ static __constant__ int c_dx[9] = {0, 1, 1, 0, -1, -1, -1, 0, 1};
 static __constant__ int c_dy[9] = {0, 0, 1, 1, 1, 0, -1, -1, -1};
 static __constant__ int c_opp[9] = {0, 5, 6, 7, 8, 1, 2, 3, 4};
 // heading class -> (stored table, x sign, y sign): tables 0 none, 1 E, 2 N,
-// 3 NE; x/y mirrors give W, S, NW, SW, SE
-static __constant__ int c_ctab[9] = {0, 1, 3, 2, 3, 1, 3, 2, 3};
-static __constant__ int c_csx[9] = {1, 1, 1, 1, -1, -1, -1, 1, 1};
-static __constant__ int c_csy[9] = {1, 1, 1, 1, 1, 1, -1, -1, -1};
+// 3 NE; x/y mirrors give W, S, NW, SW, SE.  Two bits per class in two
+// immediate constants (the table; x mirrored | y mirrored << 1), so a class
+// that differs from lane to lane costs no serialised constant-memory read.
+constexpr unsigned kClassTab = 0x3B7B4u, kClassMirror = 0x2B500u;
+__host__ __device__ __forceinline__ constexpr int class_table(int c) {
+  return (int)(kClassTab >> (2 * c)) & 3;
+}
+__host__ __device__ __forceinline__ constexpr int class_sx(int c) {
+  return ((kClassMirror >> (2 * c)) & 1u) ? -1 : 1;
+}
+__host__ __device__ __forceinline__ constexpr int class_sy(int c) {
+  return ((kClassMirror >> (2 * c)) & 2u) ? -1 : 1;
+}
+static_assert(class_table(0) == 0 && class_table(1) == 1 && class_table(2) == 3 &&
+                  class_table(3) == 2 && class_table(4) == 3 && class_table(5) == 1 &&
+                  class_table(6) == 3 && class_table(7) == 2 && class_table(8) == 3,
+              "heading class tables");
+static_assert(class_sx(0) + class_sx(1) + class_sx(2) + class_sx(3) == 4 && class_sx(4) == -1 &&
+                  class_sx(5) == -1 && class_sx(6) == -1 && class_sx(7) == 1 && class_sx(8) == 1,
+              "heading class x mirrors");
+static_assert(class_sy(0) + class_sy(1) + class_sy(2) + class_sy(3) + class_sy(4) + class_sy(5) == 6 &&
+                  class_sy(6) == -1 && class_sy(7) == -1 && class_sy(8) == -1,
+              "heading class y mirrors");
+// the same in constant memory (the footprint gather decodes a batch's records
+// with these; its register allocation is tuned with them)
+#define SFM_CLASS_ROW(f) {f(0), f(1), f(2), f(3), f(4), f(5), f(6), f(7), f(8)}
+static __constant__ int c_ctab[9] = SFM_CLASS_ROW(class_table);
+static __constant__ int c_csx[9] = SFM_CLASS_ROW(class_sx);
+static __constant__ int c_csy[9] = SFM_CLASS_ROW(class_sy);
+#undef SFM_CLASS_ROW
 
 constexpr int kFieldPad = kFieldPadRows;
 

@@ -25,7 +25,90 @@ namespace sfm {
 // a range test, and the compile-time row stride SP turns the 16 reads into
 // immediate offsets.  F = Fs + sum (+ the far part when FAR) is written once.
 
-template <int SP, int SHAPE, bool FAR>
+// Store of a 32 x 16 footprint column with the surrogate's far part: F =
+// Fs + near sum + scale * bilinear(Y).  The 16 rows of a footprint need the
+// coarse rows a(y0) .. a(y0 + 15) + 1; when these are at most 4 (coarsening
+// >= 8), each lane blends its two coarse columns once per coarse row (8
+// independent loads) and every row interpolates between two of those; else
+// the far part is evaluated row by row.
+template <int NJ, int S>
+__device__ __forceinline__ void far_epilogue(const Geo& g, const FarPart& far, const FarAxis& fax,
+                                             const float* __restrict__ Fs, float* __restrict__ out,
+                                             int out_row0, int store_lo, int store_hi, int xx,
+                                             int y0, const float2 (&acc)[NJ / 2]) {
+  const float is = far.inv_s;
+  const int a0 = (int)floorf((y0 + 0.5f) * is - 0.5f);
+  const int a1 = (int)floorf((y0 + NJ - 1 + 0.5f) * is - 0.5f);
+  const bool col = xx < g.W;  // fax is only valid for columns inside the lattice
+  float v[NJ];
+#pragma unroll
+  for (int j = 0; j < NJ; ++j) {
+    const int y = y0 + j;
+    v[j] = (col && y < g.H) ? Fs[(size_t)y * g.W + xx] + ((j & 1) ? acc[j >> 1].y : acc[j >> 1].x)
+                            : 0.f;
+  }
+  if constexpr (S == 8 && NJ == 16) {
+    // coarsening 8, rows y0 .. y0 + 15 with y0 a multiple of 16: row j lies
+    // at (y0 + j + 0.5) / 8 - 0.5 = y0 / 8 + (j - 3.5) / 8, so its coarse rows
+    // are a0 + m_j, a0 + m_j + 1 (a0 = y0 / 8 - 1, m_j = 0, 1, 2 for j < 4,
+    // < 12, < 16) with weight t_j = (j + 4.5) / 8 - m_j of the second: the
+    // values the general formula gives, exactly (all are multiples of 1/16)
+    float h[4];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      int k = y0 / 8 - 1 + m;
+      if (g.py) {
+        k %= far.Hc;
+        if (k < 0) k += far.Hc;
+      } else {
+        k = min(max(k, 0), far.Hc - 1);
+      }
+      const float* row = far.Y + (size_t)k * far.Wc;
+      h[m] = col ? (1.f - fax.t) * row[fax.i0] + fax.t * row[fax.i1] : 0.f;
+    }
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      const int m = j < 4 ? 0 : (j < 12 ? 1 : 2);
+      const float t = (j + 4.5f) * 0.125f - (float)m;
+      v[j] += far.scale * ((1.f - t) * h[m] + t * h[m + 1]);
+    }
+  } else if (a1 - a0 <= 2) {
+    float h[4];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      // coarse row a0 + m, wrapped (periodic) or clamped as far_axis does
+      int k = a0 + m;
+      if (g.py) {
+        k %= far.Hc;
+        if (k < 0) k += far.Hc;
+      } else {
+        k = min(max(k, 0), far.Hc - 1);
+      }
+      const float* row = far.Y + (size_t)k * far.Wc;
+      h[m] = col ? (1.f - fax.t) * row[fax.i0] + fax.t * row[fax.i1] : 0.f;
+    }
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) {
+      const float f = (y0 + j + 0.5f) * is - 0.5f;
+      const float a = floorf(f), t = f - a;
+      const int m = (int)a - a0;
+      const float h0 = m == 0 ? h[0] : (m == 1 ? h[1] : h[2]);
+      const float h1 = m == 0 ? h[1] : (m == 1 ? h[2] : h[3]);
+      v[j] += far.scale * ((1.f - t) * h0 + t * h1);
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < NJ; ++j)
+      if (col && y0 + j < g.H) v[j] += far_value(far, far_axis(y0 + j, is, far.Hc, g.py), fax);
+  }
+#pragma unroll
+  for (int j = 0; j < NJ; ++j) {
+    const int y = y0 + j;
+    if (xx < g.W && y < g.H && y >= store_lo && y < store_hi) out[(size_t)(y - out_row0) * g.W + xx] = v[j];
+  }
+}
+
+template <int SP, int SHAPE, int FAR>
 __global__ void __launch_bounds__(kV2Threads, 1)
     k_field_v2(Geo g, const int32_t* __restrict__ bin_start, const uint32_t* __restrict__ rec,
                const float* __restrict__ CT, const float* __restrict__ Fs,
@@ -58,8 +141,19 @@ __global__ void __launch_bounds__(kV2Threads, 1)
   // gets work.  Either way each footprint is computed once, by one warp.
   // (both walk footprints with the stride of all warps, tw)
   const int f0 = nf < 4 * tw ? blockIdx.x + gridDim.x * warp : blockIdx.x * wpb + warp;
+  // with the far part (little gather work per footprint) the static-field
+  // lines of a footprint (one per row) are fetched into L2 one footprint
+  // ahead, so the store's reads of Fs do not wait on HBM
+  auto prefetch_fs = [&](int f) {
+    if (FAR && f < nf && lane < FH) {
+      const int px0 = (f % nfx) * FW, py = (fy0 + f / nfx) * FH + lane;
+      if (py < g.H) asm volatile("prefetch.global.L2 [%0];" ::"l"(Fs + (size_t)py * g.W + px0));
+    }
+  };
+  prefetch_fs(f0);
   for (int f = f0; f < nf; f += tw) {
     const int x0 = (f % nfx) * FW, y0 = (fy0 + f / nfx) * FH;
+    prefetch_fs(f + tw);
     FarAxis fax{};
     if constexpr (FAR) fax = far_axis(x0 + x, far.inv_s, far.Wc, g.px);
     float2 acc[NJ / 2];
@@ -69,14 +163,16 @@ __global__ void __launch_bounds__(kV2Threads, 1)
       gather_footprint32<SP>(g, bin_start, rec, sT, TS, scr, lane, x0, y0, acc);
     else
       gather_footprint16<SP>(g, bin_start, rec, sT, TS, scr, lane, x0, y0, acc);
+    if constexpr (FAR) {
+      far_epilogue<NJ, FAR>(g, far, fax, Fs, out, out_row0, store_lo, store_hi, x0 + x, y0, acc);
+    } else {
 #pragma unroll
-    for (int j = 0; j < NJ; ++j) {
-      const int y = y0 + yl + j, xx = x0 + x;
-      if (xx < g.W && y < g.H && y >= store_lo && y < store_hi) {
-        const size_t c = (size_t)y * g.W + xx;
-        float v = Fs[c] + ((j & 1) ? acc[j >> 1].y : acc[j >> 1].x);
-        if constexpr (FAR) v += far_value(far, far_axis(y, far.inv_s, far.Hc, g.py), fax);
-        out[(size_t)(y - out_row0) * g.W + xx] = v;
+      for (int j = 0; j < NJ; ++j) {
+        const int y = y0 + yl + j, xx = x0 + x;
+        if (xx < g.W && y < g.H && y >= store_lo && y < store_hi) {
+          const size_t c = (size_t)y * g.W + xx;
+          out[(size_t)(y - out_row0) * g.W + xx] = Fs[c] + ((j & 1) ? acc[j >> 1].y : acc[j >> 1].x);
+        }
       }
     }
   }
@@ -84,7 +180,7 @@ __global__ void __launch_bounds__(kV2Threads, 1)
 
 static int g_num_sms = 0;
 
-template <int SP, int SHAPE, bool FAR>
+template <int SP, int SHAPE, int FAR>
 static void launch_v2(const Geo& g, const int32_t* bin_start, const uint32_t* rec, const float* CT,
                       const float* Fs, float* out, int out_row0, int store_lo, int store_hi,
                       cudaStream_t s, const FarPart& far) {
@@ -114,14 +210,17 @@ template <int SP>
 static void launch_v2_shape(const Geo& g, const int32_t* bin_start, const uint32_t* rec,
                             const Tables& tb, const float* Fs, float* out, int out_row0,
                             int store_lo, int store_hi, cudaStream_t s, const FarPart& far) {
-  // the far part (surrogate) has its own instantiation, 32 x 16 footprint only,
-  // so the exact gather carries no code for it
-  if (far.Y)
-    launch_v2<SP, 1, true>(g, bin_start, rec, tb.CT, Fs, out, out_row0, store_lo, store_hi, s, far);
+  // the far part (surrogate) has its own instantiations, 32 x 16 footprint
+  // only (one for coarsening 8, one for any), so the exact gather carries no
+  // code for it
+  if (far.Y && far.s == 8)
+    launch_v2<SP, 1, 8>(g, bin_start, rec, tb.CT, Fs, out, out_row0, store_lo, store_hi, s, far);
+  else if (far.Y)
+    launch_v2<SP, 1, 1>(g, bin_start, rec, tb.CT, Fs, out, out_row0, store_lo, store_hi, s, far);
   else if (tb.shape)
-    launch_v2<SP, 1, false>(g, bin_start, rec, tb.CT, Fs, out, out_row0, store_lo, store_hi, s, far);
+    launch_v2<SP, 1, 0>(g, bin_start, rec, tb.CT, Fs, out, out_row0, store_lo, store_hi, s, far);
   else
-    launch_v2<SP, 0, false>(g, bin_start, rec, tb.CT, Fs, out, out_row0, store_lo, store_hi, s, far);
+    launch_v2<SP, 0, 0>(g, bin_start, rec, tb.CT, Fs, out, out_row0, store_lo, store_hi, s, far);
 }
 
 void launch_field(const Geo& g, const int32_t* bin_start, const uint32_t* rec, const Tables& tb,

@@ -75,10 +75,12 @@ __device__ __forceinline__ void add_row_pairs(const float* __restrict__ p, float
 // its record (rx, ry relative to (x0, y0), heading class) into an item with
 // make(), the items in reach are compacted into the warp's scratch scr (32
 // int2) and visit() is called on each, in order, by the whole warp.
-template <int FW, int FH, class Make, class Visit>
-__device__ __forceinline__ void walk_records(const Geo& g, const int32_t* __restrict__ bin_start,
-                                             const uint32_t* __restrict__ rec, int2* scr, int lane,
-                                             int x0, int y0, Make make, Visit visit) {
+// The window's extent FW x FH is a run-time value here (walk_records below
+// fixes it at compile time for the footprints).
+template <class Make, class Visit>
+__device__ __forceinline__ void walk_records_box(const Geo& g, const int32_t* __restrict__ bin_start,
+                                                 const uint32_t* __restrict__ rec, int2* scr, int lane,
+                                                 int x0, int y0, int FW, int FH, Make make, Visit visit) {
   const int r = g.r;
   const unsigned lt = (1u << lane) - 1u;
   const int xlo = x0 - r, xhi = x0 + FW - 1 + r, ylo = y0 - r, yhi = y0 + FH - 1 + r;
@@ -134,6 +136,13 @@ __device__ __forceinline__ void walk_records(const Geo& g, const int32_t* __rest
       __syncwarp();
     }
   }
+}
+
+template <int FW, int FH, class Make, class Visit>
+__device__ __forceinline__ void walk_records(const Geo& g, const int32_t* __restrict__ bin_start,
+                                             const uint32_t* __restrict__ rec, int2* scr, int lane,
+                                             int x0, int y0, Make make, Visit visit) {
+  walk_records_box(g, bin_start, rec, scr, lane, x0, y0, FW, FH, make, visit);
 }
 
 // The footprint gather's walk: items carry the table offset of the

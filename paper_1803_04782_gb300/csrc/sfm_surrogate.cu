@@ -8,6 +8,7 @@
 // (sfm_surrogate_eval: field error and decision flip rate).
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
+#include <limits.h>
 #include <math.h>
 #include <stdint.h>
 #include <string.h>
@@ -96,7 +97,10 @@ __global__ void __launch_bounds__(kTile* kTile)
 // kernel offsets x 2 blocks of 16 input channels.  The input tile (10 x 18
 // pixels) and the weights sit in shared memory channel-last with rows padded
 // to 40 channels (80 bytes), which keeps the ldmatrix row fetches free of
-// bank conflicts.  Weights in shared memory: [ky][kx][out][in], BF16.
+// bank conflicts.  Weights in shared memory: [ky][kx][out][in], BF16.  The
+// CTAs are persistent (4 per SM): each loads the weights once and takes the
+// tiles with the grid's stride, copying the next tile's input with cp.async
+// into the second of two buffers while it computes the current one.
 constexpr int kTcRows = 8, kTcCols = 16, kTcPad = 40;
 
 __device__ __forceinline__ void ldsm_x4(uint32_t addr, uint32_t& r0, uint32_t& r1, uint32_t& r2,
@@ -115,85 +119,117 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], uint32_t a0, uint32_t a1
       : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
 }
 
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;\n" ::); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::); }
+
+constexpr int kC3In = (kTcRows + 2) * (kTcCols + 2) * kTcPad;  // input tile, BF16 elements
+constexpr int kC3W = 9 * 32 * kTcPad;                           // weights, BF16 elements
+constexpr size_t kC3Smem = (size_t)(kC3W + 2 * kC3In) * 2;
+constexpr int kC3CtasPerSm = 4;
+
 __global__ void __launch_bounds__(128)
     k_conv3_tc(const bf16* __restrict__ in, int Hin, int Win, const bf16* __restrict__ Wt,
                const float* __restrict__ b, bf16* __restrict__ out) {
-  __shared__ __align__(16) bf16 sIn[(kTcRows + 2) * (kTcCols + 2) * kTcPad];
-  __shared__ __align__(16) bf16 sW[9 * 32 * kTcPad];
+  extern __shared__ __align__(16) bf16 sm3[];
+  bf16* sW = sm3;
   const int Hout = Hin - 2, Wout = Win - 2;
-  const int x0 = blockIdx.x * kTcCols, y0 = blockIdx.y * kTcRows;
+  const int ntx = (Wout + kTcCols - 1) / kTcCols, ntiles = ntx * ((Hout + kTcRows - 1) / kTcRows);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  // weights: 9 x 32 rows of 32 channels (4 chunks of 16 bytes each)
+  const uint32_t sW0 = (uint32_t)__cvta_generic_to_shared(sW);
+  const uint32_t sIn0 = sW0 + (uint32_t)kC3W * 2;
+  // weights: 9 x 32 rows of 32 channels (4 chunks of 16 bytes each), once per CTA
   for (int i = tid; i < 9 * 32 * 4; i += blockDim.x) {
     const int q = i & 3, row = i >> 2;
-    *reinterpret_cast<uint4*>(sW + row * kTcPad + q * 8) =
-        *reinterpret_cast<const uint4*>(Wt + row * 32 + q * 8);
+    cp_async16(sW0 + (uint32_t)(row * kTcPad + q * 8) * 2, Wt + row * 32 + q * 8);
   }
-  // input tile with a 1-pixel halo on the right and bottom (valid conv)
-  for (int i = tid; i < (kTcRows + 2) * (kTcCols + 2) * 4; i += blockDim.x) {
-    const int q = i & 3, p = i >> 2, px = p % (kTcCols + 2), py = p / (kTcCols + 2);
-    const int gy = y0 + py, gx = x0 + px;
-    uint4 v = make_uint4(0, 0, 0, 0);
-    if (gy < Hin && gx < Win) v = *reinterpret_cast<const uint4*>(in + ((size_t)gy * Win + gx) * 32 + q * 8);
-    *reinterpret_cast<uint4*>(sIn + p * kTcPad + q * 8) = v;
-  }
-  __syncthreads();
-  float acc[2][4][4];
-#pragma unroll
-  for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-    for (int nt = 0; nt < 4; ++nt)
-#pragma unroll
-      for (int k = 0; k < 4; ++k) acc[mt][nt][k] = 0.f;
-  const uint32_t sIn0 = (uint32_t)__cvta_generic_to_shared(sIn);
-  const uint32_t sW0 = (uint32_t)__cvta_generic_to_shared(sW);
+  // input tile t (with a 1-pixel halo on the right and bottom) into buffer bi;
+  // pixels outside the image are zeros
+  auto fetch = [&](int t, int bi) {
+    const int x0 = (t % ntx) * kTcCols, y0 = (t / ntx) * kTcRows;
+    const uint32_t base = sIn0 + (uint32_t)(bi * kC3In) * 2;
+    for (int i = tid; i < (kTcRows + 2) * (kTcCols + 2) * 4; i += blockDim.x) {
+      const int q = i & 3, p = i >> 2, px = p % (kTcCols + 2), py = p / (kTcCols + 2);
+      const int gy = y0 + py, gx = x0 + px;
+      const uint32_t dst = base + (uint32_t)(p * kTcPad + q * 8) * 2;
+      if (gy < Hin && gx < Win)
+        cp_async16(dst, in + ((size_t)gy * Win + gx) * 32 + q * 8);
+      else
+        asm volatile("st.shared.v4.u32 [%0], {%1, %1, %1, %1};\n" ::"r"(dst), "r"(0));
+    }
+  };
+  int t = blockIdx.x, bi = 0;
+  if (t < ntiles) fetch(t, 0);
+  cp_async_commit();
   // ldmatrix lane roles: A rows (pixels) and column halves; B rows (out channels)
   const int a_row = (lane & 7) + 8 * ((lane >> 3) & 1), a_col = 8 * (lane >> 4);
   const int b_n = (lane & 7) + 8 * (lane >> 4), b_k = 8 * ((lane >> 3) & 1);
-#pragma unroll 1
-  for (int kk = 0; kk < 9; ++kk) {
-    const int ky = kk / 3, kx = kk % 3;
-#pragma unroll
-    for (int kb = 0; kb < 2; ++kb) {
-      uint32_t bw[4][2];
-#pragma unroll
-      for (int np = 0; np < 2; ++np) {
-        const uint32_t addr =
-            sW0 + (uint32_t)(((kk * 32 + np * 16 + b_n) * kTcPad + kb * 16 + b_k) * 2);
-        ldsm_x4(addr, bw[2 * np][0], bw[2 * np][1], bw[2 * np + 1][0], bw[2 * np + 1][1]);
-      }
-#pragma unroll
-      for (int mt = 0; mt < 2; ++mt) {
-        const int py = 2 * warp + mt + ky, px = a_row + kx;
-        const uint32_t addr =
-            sIn0 + (uint32_t)(((py * (kTcCols + 2) + px) * kTcPad + kb * 16 + a_col) * 2);
-        uint32_t a0, a1, a2, a3;
-        ldsm_x4(addr, a0, a1, a2, a3);
-#pragma unroll
-        for (int nt = 0; nt < 4; ++nt) mma_bf16(acc[mt][nt], a0, a1, a2, a3, bw[nt][0], bw[nt][1]);
-      }
-    }
-  }
-  // epilogue: bias, ReLU, BF16; accumulator (row g = lane/4 and g+8, column
-  // pair 2*(lane%4)) of each m16 x n8 tile
   const int g = lane >> 2, cp = 2 * (lane & 3);
+  for (; t < ntiles; t += gridDim.x, bi ^= 1) {
+    // the next tile's copies run while this one is computed
+    if (t + (int)gridDim.x < ntiles) fetch(t + gridDim.x, bi ^ 1);
+    cp_async_commit();
+    cp_async_wait_prev();
+    __syncthreads();
+    const uint32_t sIn = sIn0 + (uint32_t)(bi * kC3In) * 2;
+    float acc[2][4][4];
 #pragma unroll
-  for (int mt = 0; mt < 2; ++mt) {
-    const int y = y0 + 2 * warp + mt;
+    for (int mt = 0; mt < 2; ++mt)
 #pragma unroll
-    for (int half = 0; half < 2; ++half) {
-      const int x = x0 + g + 8 * half;
-      if (y >= Hout || x >= Wout) continue;
-      __nv_bfloat162* o = reinterpret_cast<__nv_bfloat162*>(out + ((size_t)y * Wout + x) * 32);
+      for (int nt = 0; nt < 4; ++nt)
 #pragma unroll
-      for (int nt = 0; nt < 4; ++nt) {
-        const int c = nt * 8 + cp;
-        const float v0 = fmaxf(acc[mt][nt][2 * half] + b[c], 0.f);
-        const float v1 = fmaxf(acc[mt][nt][2 * half + 1] + b[c + 1], 0.f);
-        o[c / 2] = __floats2bfloat162_rn(v0, v1);
+        for (int k = 0; k < 4; ++k) acc[mt][nt][k] = 0.f;
+#pragma unroll 1
+    for (int kk = 0; kk < 9; ++kk) {
+      const int ky = kk / 3, kx = kk % 3;
+#pragma unroll
+      for (int kb = 0; kb < 2; ++kb) {
+        uint32_t bw[4][2];
+#pragma unroll
+        for (int np = 0; np < 2; ++np) {
+          const uint32_t addr =
+              sW0 + (uint32_t)(((kk * 32 + np * 16 + b_n) * kTcPad + kb * 16 + b_k) * 2);
+          ldsm_x4(addr, bw[2 * np][0], bw[2 * np][1], bw[2 * np + 1][0], bw[2 * np + 1][1]);
+        }
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt) {
+          const int py = 2 * warp + mt + ky, px = a_row + kx;
+          const uint32_t addr =
+              sIn + (uint32_t)(((py * (kTcCols + 2) + px) * kTcPad + kb * 16 + a_col) * 2);
+          uint32_t a0, a1, a2, a3;
+          ldsm_x4(addr, a0, a1, a2, a3);
+#pragma unroll
+          for (int nt = 0; nt < 4; ++nt) mma_bf16(acc[mt][nt], a0, a1, a2, a3, bw[nt][0], bw[nt][1]);
+        }
       }
     }
+    // epilogue: bias, ReLU, BF16; accumulator (row g = lane/4 and g+8, column
+    // pair 2*(lane%4)) of each m16 x n8 tile
+    const int x0 = (t % ntx) * kTcCols, y0 = (t / ntx) * kTcRows;
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt) {
+      const int y = y0 + 2 * warp + mt;
+#pragma unroll
+      for (int half = 0; half < 2; ++half) {
+        const int x = x0 + g + 8 * half;
+        if (y >= Hout || x >= Wout) continue;
+        __nv_bfloat162* o = reinterpret_cast<__nv_bfloat162*>(out + ((size_t)y * Wout + x) * 32);
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt) {
+          const int c = nt * 8 + cp;
+          const float v0 = fmaxf(acc[mt][nt][2 * half] + b[c], 0.f);
+          const float v1 = fmaxf(acc[mt][nt][2 * half + 1] + b[c + 1], 0.f);
+          o[c / 2] = __floats2bfloat162_rn(v0, v1);
+        }
+      }
+    }
+    // every warp is done with this buffer before it is refilled
+    __syncthreads();
   }
+  cp_async_wait_all();
 }
 
 // BF16 weights of a 3x3 32->32 layer for the tensor-core kernel:
@@ -210,7 +246,9 @@ __global__ void k_pack_w3(const float* __restrict__ w, bf16* __restrict__ wt) {
 // stages its 12 x 20-pixel input tile, expands it to a [128 pixel][80] BF16
 // matrix in shared memory (rows padded to 88 elements, 176 bytes, so the
 // ldmatrix row fetches hit distinct banks) and runs 5 k16 steps of
-// m16n8k16 per m16 tile; layout of warps and fragments as k_conv3_tc.
+// m16n8k16 per m16 tile; layout of warps and fragments as k_conv3_tc, and
+// persistent CTAs as there (the next tile's input is prefetched into
+// registers).
 constexpr int kC1K = 80, kC1Pad = 88;
 static_assert(kTcCols + 4 == 20, "c_im2col assumes 20-pixel input rows");
 // input-tile offset of K entry k = (ky*5 + kx)*3 + c: (ky*20 + kx)*3 + c
@@ -224,6 +262,10 @@ __constant__ int c_im2col[80] = {
 #undef C1ROW
 };
 
+constexpr int kC1CtasPerSm = 6;
+constexpr int kC1TileElems = (kTcRows + 4) * (kTcCols + 4) * 3;  // input tile, BF16 elements
+constexpr int kC1PerThread = (kC1TileElems + 127) / 128;
+
 __global__ void __launch_bounds__(128)
     k_conv1_tc(const bf16* __restrict__ in, int Hin, int Win, const bf16* __restrict__ Wt,
                const float* __restrict__ b, bf16* __restrict__ out) {
@@ -232,73 +274,92 @@ __global__ void __launch_bounds__(128)
   __shared__ __align__(16) bf16 sA[kTcRows * kTcCols * kC1Pad];
   __shared__ __align__(16) bf16 sW[32 * kC1Pad];
   const int Hout = Hin - 4, Wout = Win - 4;
-  const int x0 = blockIdx.x * kTcCols, y0 = blockIdx.y * kTcRows;
+  const int ntx = (Wout + kTcCols - 1) / kTcCols, ntiles = ntx * ((Hout + kTcRows - 1) / kTcRows);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (int i = tid; i < 32 * kC1K; i += blockDim.x) sW[(i / kC1K) * kC1Pad + i % kC1K] = Wt[i];
-  for (int i = tid; i < TH * TW * 3; i += blockDim.x) {
-    const int c = i % 3, p = i / 3, px = p % TW, py = p / TW;
-    const int gy = y0 + py, gx = x0 + px;
-    sX[i] = (gy < Hin && gx < Win) ? in[((size_t)gy * Win + gx) * 3 + c] : __float2bfloat16(0.f);
-  }
-  __syncthreads();
-  {
-    // thread = output pixel of the tile (128 of them): its row of the
-    // im2col matrix, two K entries per 4-byte store
-    const int p = tid, base = ((p / kTcCols) * TW + p % kTcCols) * 3;
-    __nv_bfloat162* row = reinterpret_cast<__nv_bfloat162*>(sA + p * kC1Pad);
-#pragma unroll 8
-    for (int k = 0; k < kC1K; k += 2) {
-      const bf16 z = __float2bfloat16(0.f);
-      const bf16 a = k < 75 ? sX[base + c_im2col[k]] : z;
-      const bf16 b = k + 1 < 75 ? sX[base + c_im2col[k + 1]] : z;
-      row[k / 2] = __halves2bfloat162(a, b);
+  // persistent CTAs take the tiles with the grid's stride; the next tile's
+  // input elements are loaded into registers while the current one is computed
+  bf16 pre[kC1PerThread];
+  auto fetch = [&](int t) {
+    const int x0 = (t % ntx) * kTcCols, y0 = (t / ntx) * kTcRows;
+#pragma unroll
+    for (int u = 0; u < kC1PerThread; ++u) {
+      const int i = tid + 128 * u;
+      const int c = i % 3, p = i / 3, px = p % TW, py = p / TW;
+      const int gy = y0 + py, gx = x0 + px;
+      pre[u] = (i < kC1TileElems && gy < Hin && gx < Win) ? in[((size_t)gy * Win + gx) * 3 + c]
+                                                         : __float2bfloat16(0.f);
     }
-  }
-  __syncthreads();
-  float acc[2][4][4];
-#pragma unroll
-  for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-    for (int nt = 0; nt < 4; ++nt)
-#pragma unroll
-      for (int k = 0; k < 4; ++k) acc[mt][nt][k] = 0.f;
+  };
+  if ((int)blockIdx.x < ntiles) fetch(blockIdx.x);
   const uint32_t sA0 = (uint32_t)__cvta_generic_to_shared(sA);
   const uint32_t sW0 = (uint32_t)__cvta_generic_to_shared(sW);
   const int a_row = (lane & 7) + 8 * ((lane >> 3) & 1), a_col = 8 * (lane >> 4);
   const int b_n = (lane & 7) + 8 * (lane >> 4), b_k = 8 * ((lane >> 3) & 1);
-#pragma unroll
-  for (int kb = 0; kb < kC1K / 16; ++kb) {
-    uint32_t bw[4][2];
-#pragma unroll
-    for (int np = 0; np < 2; ++np)
-      ldsm_x4(sW0 + (uint32_t)(((np * 16 + b_n) * kC1Pad + kb * 16 + b_k) * 2), bw[2 * np][0],
-              bw[2 * np][1], bw[2 * np + 1][0], bw[2 * np + 1][1]);
-#pragma unroll
-    for (int mt = 0; mt < 2; ++mt) {
-      const int prow = (2 * warp + mt) * kTcCols + a_row;
-      uint32_t a0, a1, a2, a3;
-      ldsm_x4(sA0 + (uint32_t)((prow * kC1Pad + kb * 16 + a_col) * 2), a0, a1, a2, a3);
-#pragma unroll
-      for (int nt = 0; nt < 4; ++nt) mma_bf16(acc[mt][nt], a0, a1, a2, a3, bw[nt][0], bw[nt][1]);
-    }
-  }
   const int g = lane >> 2, cp = 2 * (lane & 3);
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
 #pragma unroll
-  for (int mt = 0; mt < 2; ++mt) {
-    const int y = y0 + 2 * warp + mt;
-#pragma unroll
-    for (int half = 0; half < 2; ++half) {
-      const int x = x0 + g + 8 * half;
-      if (y >= Hout || x >= Wout) continue;
-      __nv_bfloat162* o = reinterpret_cast<__nv_bfloat162*>(out + ((size_t)y * Wout + x) * 32);
-#pragma unroll
-      for (int nt = 0; nt < 4; ++nt) {
-        const int c = nt * 8 + cp;
-        const float v0 = fmaxf(acc[mt][nt][2 * half] + b[c], 0.f);
-        const float v1 = fmaxf(acc[mt][nt][2 * half + 1] + b[c + 1], 0.f);
-        o[c / 2] = __floats2bfloat162_rn(v0, v1);
+    for (int u = 0; u < kC1PerThread; ++u)
+      if (tid + 128 * u < kC1TileElems) sX[tid + 128 * u] = pre[u];
+    __syncthreads();
+    if (t + (int)gridDim.x < ntiles) fetch(t + gridDim.x);
+    {
+      // thread = output pixel of the tile (128 of them): its row of the
+      // im2col matrix, two K entries per 4-byte store
+      const int p = tid, base = ((p / kTcCols) * TW + p % kTcCols) * 3;
+      __nv_bfloat162* row = reinterpret_cast<__nv_bfloat162*>(sA + p * kC1Pad);
+#pragma unroll 8
+      for (int k = 0; k < kC1K; k += 2) {
+        const bf16 z = __float2bfloat16(0.f);
+        const bf16 a = k < 75 ? sX[base + c_im2col[k]] : z;
+        const bf16 bb = k + 1 < 75 ? sX[base + c_im2col[k + 1]] : z;
+        row[k / 2] = __halves2bfloat162(a, bb);
       }
     }
+    __syncthreads();
+    float acc[2][4][4];
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+      for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) acc[mt][nt][k] = 0.f;
+#pragma unroll
+    for (int kb = 0; kb < kC1K / 16; ++kb) {
+      uint32_t bw[4][2];
+#pragma unroll
+      for (int np = 0; np < 2; ++np)
+        ldsm_x4(sW0 + (uint32_t)(((np * 16 + b_n) * kC1Pad + kb * 16 + b_k) * 2), bw[2 * np][0],
+                bw[2 * np][1], bw[2 * np + 1][0], bw[2 * np + 1][1]);
+#pragma unroll
+      for (int mt = 0; mt < 2; ++mt) {
+        const int prow = (2 * warp + mt) * kTcCols + a_row;
+        uint32_t a0, a1, a2, a3;
+        ldsm_x4(sA0 + (uint32_t)((prow * kC1Pad + kb * 16 + a_col) * 2), a0, a1, a2, a3);
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt) mma_bf16(acc[mt][nt], a0, a1, a2, a3, bw[nt][0], bw[nt][1]);
+      }
+    }
+    const int x0 = (t % ntx) * kTcCols, y0 = (t / ntx) * kTcRows;
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt) {
+      const int y = y0 + 2 * warp + mt;
+#pragma unroll
+      for (int half = 0; half < 2; ++half) {
+        const int x = x0 + g + 8 * half;
+        if (y >= Hout || x >= Wout) continue;
+        __nv_bfloat162* o = reinterpret_cast<__nv_bfloat162*>(out + ((size_t)y * Wout + x) * 32);
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt) {
+          const int c = nt * 8 + cp;
+          const float v0 = fmaxf(acc[mt][nt][2 * half] + b[c], 0.f);
+          const float v1 = fmaxf(acc[mt][nt][2 * half + 1] + b[c + 1], 0.f);
+          o[c / 2] = __floats2bfloat162_rn(v0, v1);
+        }
+      }
+    }
+    // sX and sA are rewritten by the next tile
+    __syncthreads();
   }
 }
 
@@ -311,36 +372,70 @@ __global__ void k_pack_w1(const float* __restrict__ w, bf16* __restrict__ wt) {
   wt[i] = __float2bfloat16(k < 75 ? w[k * 32 + o] : 0.f);
 }
 
-// Layer 4 (3x3, 32 -> 1, no activation): one output pixel per thread, the
-// 9 x 32 inputs as 16-byte loads, FP32 sums in the order (ky, kx, c).
-__global__ void __launch_bounds__(256)
+// Layer 4 (3x3, 32 -> 1, no activation), FP32 sums in the order (ky, kx, c).
+// A CTA of 128 threads computes an 8 x 32 output tile: the 10 x 34-pixel
+// input tile is staged in shared memory with pixel rows padded to 40
+// channels (80 bytes, so 8 threads reading 16 bytes at consecutive pixels hit
+// distinct banks), and each thread computes 2 outputs of one column, reusing
+// one kernel offset's 32 weights from registers for both; 27 KB a CTA lets 8
+// CTAs share an SM, whose tile loads overlap the others' sums.
+constexpr int kL4Rows = 8, kL4Cols = 32, kL4Pad = 40, kL4Per = kL4Rows / 4;
+constexpr size_t kL4Smem = (size_t)(kL4Rows + 2) * (kL4Cols + 2) * kL4Pad * 2;
+
+__global__ void __launch_bounds__(128)
     k_conv_last(const bf16* __restrict__ in, int Hin, int Win, const float* __restrict__ Wt,
                 const float* __restrict__ b, float* __restrict__ out) {
-  __shared__ float sW[9 * 32];
-  for (int i = threadIdx.x; i < 9 * 32; i += blockDim.x) sW[i] = Wt[i];
-  __syncthreads();
+  extern __shared__ __align__(16) bf16 sIn4[];
+  __shared__ __align__(16) float sW[9 * 32];
+  constexpr int TW = kL4Cols + 2, TH = kL4Rows + 2;
   const int Hout = Hin - 2, Wout = Win - 2;
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= Hout * Wout) return;
-  const int y = idx / Wout, x = idx % Wout;
-  float acc = b[0];
+  const int x0 = blockIdx.x * kL4Cols, y0 = blockIdx.y * kL4Rows, tid = threadIdx.x;
+  for (int i = tid; i < 9 * 32; i += blockDim.x) sW[i] = Wt[i];
+  for (int i = tid; i < TH * TW * 4; i += blockDim.x) {
+    const int q = i & 3, p = i >> 2, px = p % TW, py = p / TW;
+    const int gy = y0 + py, gx = x0 + px;
+    uint4 v = make_uint4(0, 0, 0, 0);
+    if (gy < Hin && gx < Win) v = *reinterpret_cast<const uint4*>(in + ((size_t)gy * Win + gx) * 32 + q * 8);
+    *reinterpret_cast<uint4*>(sIn4 + p * kL4Pad + q * 8) = v;
+  }
+  __syncthreads();
+  const int tx = tid & 31, ty = (tid >> 5) * kL4Per;
+  float acc[kL4Per];
 #pragma unroll
+  for (int j = 0; j < kL4Per; ++j) acc[j] = b[0];
+#pragma unroll 1
   for (int kk = 0; kk < 9; ++kk) {
-    const uint4* px =
-        reinterpret_cast<const uint4*>(in + ((size_t)(y + kk / 3) * Win + (x + kk % 3)) * 32);
+    const int ky = kk / 3, kx = kk % 3;
+    float w[32];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const uint4 v = px[q];
-      const uint32_t w4[4] = {v.x, v.y, v.z, v.w};
+    for (int c = 0; c < 32; c += 4) {
+      const float4 t = *reinterpret_cast<const float4*>(sW + kk * 32 + c);
+      w[c] = t.x;
+      w[c + 1] = t.y;
+      w[c + 2] = t.z;
+      w[c + 3] = t.w;
+    }
 #pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w4[e]));
-        acc = fmaf(f.x, sW[kk * 32 + q * 8 + 2 * e], acc);
-        acc = fmaf(f.y, sW[kk * 32 + q * 8 + 2 * e + 1], acc);
+    for (int j = 0; j < kL4Per; ++j) {
+      const uint4* px = reinterpret_cast<const uint4*>(sIn4 + ((ty + j + ky) * TW + tx + kx) * kL4Pad);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const uint4 v = px[q];
+        const uint32_t w4[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w4[e]));
+          acc[j] = fmaf(f.x, w[q * 8 + 2 * e], acc[j]);
+          acc[j] = fmaf(f.y, w[q * 8 + 2 * e + 1], acc[j]);
+        }
       }
     }
   }
-  out[idx] = acc;
+#pragma unroll
+  for (int j = 0; j < kL4Per; ++j) {
+    const int y = y0 + ty + j, x = x0 + tx;
+    if (y < Hout && x < Wout) out[(size_t)y * Wout + x] = acc[j];
+  }
 }
 
 // -------------------------------------------------------------- backward
@@ -506,7 +601,45 @@ __global__ void k_coarse_in(Geo g, const uint8_t* __restrict__ ocls, int s, int 
   if (cj < 0 || cj >= Wc) {
     if (g.px) cj = (cj + Wc) % Wc; else ok = false;
   }
-  if (ok) {
+  if (ok && s == 8) {
+    // the cell's 8 rows of 8 bytes, all loads in flight at once
+    uint2 w[8];
+#pragma unroll
+    for (int dy = 0; dy < 8; ++dy)
+      w[dy] = *reinterpret_cast<const uint2*>(ocls + (size_t)(ci * 8 + dy) * g.opitch + cj * 8);
+#pragma unroll
+    for (int dy = 0; dy < 8; ++dy) {
+      if (!(w[dy].x | w[dy].y)) continue;
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        const int v = (int)(((e < 4 ? w[dy].x : w[dy].y) >> (8 * (e & 3))) & 0xffu);
+        if (v) {
+          n += 1.f;
+          hx += c_hx[v - 1];
+          hy += c_hy[v - 1];
+        }
+      }
+    }
+  } else if (ok && (s & 7) == 0) {
+    // 8 bytes of a cell row per load (the grid's pitch is a multiple of 128);
+    // empty words are skipped, the others summed byte by byte in row order
+    for (int dy = 0; dy < s; ++dy) {
+      const uint2* row = reinterpret_cast<const uint2*>(ocls + (size_t)(ci * s + dy) * g.opitch + cj * s);
+      for (int dw = 0; dw < s / 8; ++dw) {
+        const uint2 w = row[dw];
+        if (!(w.x | w.y)) continue;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          const int v = (int)(((e < 4 ? w.x : w.y) >> (8 * (e & 3))) & 0xffu);
+          if (v) {
+            n += 1.f;
+            hx += c_hx[v - 1];
+            hy += c_hy[v - 1];
+          }
+        }
+      }
+    }
+  } else if (ok) {
     for (int dy = 0; dy < s; ++dy) {
       const uint8_t* row = ocls + (size_t)(ci * s + dy) * g.opitch + cj * s;
       for (int dx = 0; dx < s; ++dx) {
@@ -594,15 +727,80 @@ __device__ __forceinline__ float margin_allowance(float delta, float emag, float
   return delta * 1.0001f + 1e-6f * (emag + fmag);
 }
 
+// The surrogate field at the 9 candidates of the pedestrian at q from its
+// parts, as the lattice pass composes it: (Fs + near sum) + scale *
+// bilinear(Y).  The near sum walks the records within reach (rn) of the 3 x 3
+// block in the gather's order (halo bins row-major, records in bin order),
+// so it holds the lattice pass's terms in its order.
+struct NearPart {
+  const float* CT;  // near-field class tables (global memory), radius rn
+  int rn, SP, TS;
+};
+
+__device__ __forceinline__ void surrogate_at_candidates(
+    const Geo& g, int2 q, const int (&cx)[3], const int (&ry)[3], const int32_t* __restrict__ bin_start,
+    const uint32_t* __restrict__ rec, const float* __restrict__ Fs, const NearPart& np,
+    const FarPart& far, float (&f)[9]) {
+  float acc[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) acc[k] = 0.f;
+  const int rn = np.rn;
+  if (rn > 0) {
+    const int x0 = q.x - 1, y0 = q.y - 1;
+    const int xlo = x0 - rn, xhi = x0 + 2 + rn, ylo = y0 - rn, yhi = y0 + 2 + rn;
+    const int nxl = halo_count(xlo, xhi, g.W, g.px), nyl = halo_count(ylo, yhi, g.H, g.py);
+    for (int ey = 0; ey < nyl; ++ey) {
+      int by, yoff;
+      halo_entry(ey, ylo, yhi, g.H, g.py, y0, by, yoff);
+      for (int ex = 0; ex < nxl; ++ex) {
+        int bx, xoff;
+        halo_entry(ex, xlo, xhi, g.W, g.px, x0, bx, xoff);
+        const int id = by * g.nbx + bx;
+        const int s1 = bin_start[id + 1];
+        for (int i = bin_start[id]; i < s1; ++i) {
+          const uint32_t rc = rec[i];
+          const int rx = xoff + (int)(rc & 0xffu), rry = yoff + (int)((rc >> 8) & 0xffu);
+          if (rx < -rn || rx > 2 + rn || rry < -rn || rry > 2 + rn) continue;
+          const int cls = (int)((rc >> 16) & 0xfu);
+          const int sx = class_sx(cls), sy = class_sy(cls);
+          const float* p = np.CT + class_table(cls) * np.TS + (rn + kFieldPad - sy * rry) * np.SP + rn - sx * rx;
+#pragma unroll
+          for (int k = 0; k < 9; ++k) {
+            const int ccx = move_dx(k) + 1, ccy = move_dy(k) + 1;
+            if (ccx - rx >= -rn && ccx - rx <= rn && ccy - rry >= -rn && ccy - rry <= rn)
+              acc[k] += __ldg(p + sy * ccy * np.SP + sx * ccx);
+          }
+        }
+      }
+    }
+  }
+  FarAxis fx[3], fy[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    fx[d] = far_axis(cx[d], far.inv_s, far.Wc, g.px);
+    fy[d] = far_axis(ry[d], far.inv_s, far.Hc, g.py);
+  }
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    const int xi = move_dx(k) + 1, yi = move_dy(k) + 1;
+    f[k] = (Fs[(size_t)ry[yi] * g.W + cx[xi]] + acc[k]) + far_value(far, fy[yi], fx[xi]);
+  }
+}
+
+// CAND: the surrogate field is composed at the candidates (no lattice pass);
+// else it is read from Fsur.
+template <bool CAND>
 __global__ void k_sur_decide(const int32_t* __restrict__ rec_id, const int32_t* __restrict__ bin_start,
                              int nbins, Geo g, const int2* __restrict__ xy,
                              const uint8_t* __restrict__ heading, const uint8_t* __restrict__ goal,
                              const uint8_t* __restrict__ cell, const uint8_t* __restrict__ ocls,
                              const int32_t* __restrict__ D, const float* __restrict__ Fsur,
-                             float beta, const float* __restrict__ own,
+                             const uint32_t* __restrict__ rec, const float* __restrict__ Fs,
+                             NearPart np, FarPart far, float beta, const float* __restrict__ own,
                              const float* __restrict__ dirdot, float delta,
                              uint8_t* __restrict__ choice, int32_t* __restrict__ flag_list,
-                             int32_t* __restrict__ nflag, const uint8_t* __restrict__ ref,
+                             int32_t* __restrict__ nflag, uint8_t* __restrict__ fb_flag,
+                             const uint8_t* __restrict__ ref,
                              unsigned long long* __restrict__ raw_flips, WalkPeriods wp) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   bool differs = false;
@@ -610,6 +808,7 @@ __global__ void k_sur_decide(const int32_t* __restrict__ rec_id, const int32_t* 
   if (i < bin_start[nbins] && wp.period &&
       t % wp.period[rec_id[i]] != wp.phase[rec_id[i]]) {
     choice[rec_id[i]] = 0;  // not this pedestrian's tick (walk period): it stays
+    fb_flag[i] = 0;
     differs = ref && ref[rec_id[i]] != 0;
   } else if (i < bin_start[nbins]) {
     const int p = rec_id[i];
@@ -620,16 +819,21 @@ __global__ void k_sur_decide(const int32_t* __restrict__ rec_id, const int32_t* 
     uint8_t cl[9], oc[9];
     candidate_cells(q, g, cell, ocls, D, cx, ry, okx, oky, dd, cl, oc);
     float f[9], fmag = 0.f;
+    if constexpr (CAND) {
+      surrogate_at_candidates(g, q, cx, ry, bin_start, rec, Fs, np, far, f);
+    } else {
 #pragma unroll
-    for (int k = 0; k < 9; ++k) {
-      f[k] = Fsur[(size_t)ry[move_dy(k) + 1] * g.W + cx[move_dx(k) + 1]];
-      fmag = fmaxf(fmag, fabsf(f[k]));
+      for (int k = 0; k < 9; ++k) f[k] = Fsur[(size_t)ry[move_dy(k) + 1] * g.W + cx[move_dx(k) + 1]];
     }
+#pragma unroll
+    for (int k = 0; k < 9; ++k) fmag = fmaxf(fmag, fabsf(f[k]));
     float margin, emag;
     const int best = pick_move<true>(f, dd, cl, oc, okx, oky, heading[p], goal[p], beta, own,
                                      dirdot, &margin, &emag);
     choice[p] = (uint8_t)best;
-    if (!(margin > margin_allowance(delta, emag, fmag))) flag_list[atomicAdd(nflag, 1)] = p;
+    const bool fl = !(margin > margin_allowance(delta, emag, fmag));
+    fb_flag[i] = fl;
+    if (fl) flag_list[atomicAdd(nflag, 1)] = i;
     differs = ref && ref[p] != best;
   }
   if (raw_flips) {
@@ -638,18 +842,26 @@ __global__ void k_sur_decide(const int32_t* __restrict__ rec_id, const int32_t* 
   }
 }
 
-// Exact field at the 9 candidates of each listed pedestrian: one warp per
-// pedestrian walks, once, the records in reach of its 3 x 3 candidate block
-// (the walk of a 3 x 3 footprint) and lane k < 9 adds, in walk order, the
-// class-table entry of every record that reaches candidate k: the sums of
-// the exact gather, bit for bit (its other terms are zero pads).  The class
-// tables are staged in shared memory as for the gather (one CTA of 32 warps
-// per SM).  Values of candidates outside the lattice are never read.
+// Exact field at the 9 candidates of each listed pedestrian.  A warp takes
+// 32 consecutive records in bin order (fb_flag marks the listed ones) and,
+// for each run of them in one bin row, walks once the records in reach of
+// the run's bounding box of candidate blocks, in the gather's order (halo
+// bins row-major, records in bin order); each lane adds, for every record
+// that reaches one of its pedestrian's candidates, the record's class-table
+// entry into that candidate's sum.  Every pedestrian's halo entries are a
+// subsequence of the box's, in the same order, so each sum holds the exact
+// gather's terms in its order, bit for bit (its other terms are zero pads).
+// With a wide table stride an out-of-reach candidate reads a zero pad, so
+// only NARROW tests each candidate.  The class tables are staged in shared
+// memory as for the gather (one CTA of 1024 threads per SM); fex is indexed
+// by the record's slot.  Values of candidates outside the lattice are never
+// read.
 constexpr int kFbThreads = 1024;
 
+template <bool NARROW>
 __global__ void __launch_bounds__(kFbThreads, 1)
-    k_sur_fallback(const int32_t* __restrict__ flag_list, const int32_t* __restrict__ nflag, Geo g,
-                   const int2* __restrict__ xy, const int32_t* __restrict__ bin_start,
+    k_sur_fallback(const uint8_t* __restrict__ fb_flag, const int32_t* __restrict__ rec_id, int nbins,
+                   Geo g, const int2* __restrict__ xy, const int32_t* __restrict__ bin_start,
                    const uint32_t* __restrict__ rec, const float* __restrict__ CT, int SP, int TS,
                    const float* __restrict__ Fs, float* __restrict__ fex) {
   extern __shared__ __align__(16) float sm[];
@@ -658,31 +870,65 @@ __global__ void __launch_bounds__(kFbThreads, 1)
   int2* scr = reinterpret_cast<int2*>(sT + 4 * TS) + w * 32;
   for (int i = threadIdx.x; i < 4 * TS; i += blockDim.x) sT[i] = CT[i];
   __syncthreads();
-  const int n = *nflag, r = g.r;
-  const int k = lane < 9 ? lane : 0;
-  const int cdx = move_dx(k) + 1, cdy = move_dy(k) + 1;  // candidate in the 3 x 3 block
-  for (int j = blockIdx.x * nw + w; j < n; j += gridDim.x * nw) {
-    const int2 q = xy[flag_list[j]];
-    float acc = 0.f;
-    walk_records<3, 3>(
-        g, bin_start, rec, scr, lane, q.x - 1, q.y - 1,
-        [](int rx, int ry, int cls) { return make_int2(rx, ry * 16 + cls); },
-        [&](const int2 it) {
-          const int cls = it.y & 15, dx = cdx - it.x, dy = cdy - (it.y >> 4);
-          if (lane < 9 && dx >= -r && dx <= r && dy >= -r && dy <= r)
-            acc += sT[c_ctab[cls] * TS + (r + kFieldPad + c_csy[cls] * dy) * SP + r + c_csx[cls] * dx];
-        });
-    if (lane < 9) {
-      int tx, ty;
-      const bool ok = wrap_coord(q.x + move_dx(k), g.W, g.px, tx) &
-                      wrap_coord(q.y + move_dy(k), g.H, g.py, ty);
-      fex[(size_t)j * 9 + lane] = ok ? Fs[(size_t)ty * g.W + tx] + acc : 0.f;
+  const int nrec = bin_start[nbins], r = g.r;
+  const int nchunks = (nrec + 31) / 32;
+  for (int c = blockIdx.x * nw + w; c < nchunks; c += gridDim.x * nw) {
+    const int i = c * 32 + lane;
+    const bool fl = i < nrec && fb_flag[i] != 0;
+    unsigned todo = __ballot_sync(0xffffffffu, fl);
+    if (!todo) continue;
+    const int2 q = fl ? xy[rec_id[i]] : make_int2(0, 0);
+    const int brow = q.y / kBin;
+    float acc[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) acc[k] = 0.f;
+    while (todo) {
+      // the listed lanes of the first remaining bin row (bin order keeps them contiguous)
+      const int row = __shfl_sync(0xffffffffu, brow, __ffs(todo) - 1);
+      const bool mine = ((todo >> lane) & 1u) && brow == row;
+      todo &= ~__ballot_sync(0xffffffffu, mine);
+      const int xmin = __reduce_min_sync(0xffffffffu, mine ? q.x : INT_MAX);
+      const int xmax = __reduce_max_sync(0xffffffffu, mine ? q.x : INT_MIN);
+      const int ymin = __reduce_min_sync(0xffffffffu, mine ? q.y : INT_MAX);
+      const int ymax = __reduce_max_sync(0xffffffffu, mine ? q.y : INT_MIN);
+      // box of the candidate blocks, and this lane's block origin inside it
+      const int x0 = xmin - 1, y0 = ymin - 1, ox = q.x - xmin, oy = q.y - ymin;
+      walk_records_box(
+          g, bin_start, rec, scr, lane, x0, y0, xmax - xmin + 3, ymax - ymin + 3,
+          [](int rx, int ry, int cls) { return make_int2(rx, ry * 16 + cls); },
+          [&](const int2 it) {
+            const int rx = it.x - ox, ry = (it.y >> 4) - oy, cls = it.y & 15;
+            if (mine && rx >= -r && rx <= 2 + r && ry >= -r && ry <= 2 + r) {
+              const int sx = class_sx(cls), sy = class_sy(cls);
+              // entry of candidate (cx, cy): offset (cx - rx, cy - ry) from the record
+              const float* p =
+                  sT + class_table(cls) * TS + (r + kFieldPad - sy * ry) * SP + r - sx * rx;
+#pragma unroll
+              for (int k = 0; k < 9; ++k) {
+                const int cx = move_dx(k) + 1, cy = move_dy(k) + 1;
+                if (!NARROW || (cx - rx >= -r && cx - rx <= r && cy - ry >= -r && cy - ry <= r))
+                  acc[k] += p[sy * cy * SP + sx * cx];
+              }
+            }
+          });
+    }
+    if (fl) {
+#pragma unroll
+      for (int k = 0; k < 9; ++k) {
+        int tx, ty;
+        const bool ok = wrap_coord(q.x + move_dx(k), g.W, g.px, tx) &
+                        wrap_coord(q.y + move_dy(k), g.H, g.py, ty);
+        fex[(size_t)i * 9 + k] = ok ? Fs[(size_t)ty * g.W + tx] + acc[k] : 0.f;
+      }
     }
   }
 }
 
+// The listed pedestrians decided again on the exact candidate field (fex,
+// indexed by slot), with the exact path's energy.  (A separate kernel: done
+// inside the fallback, the decision's scattered loads stall its few warps.)
 __global__ void k_sur_redecide(const int32_t* __restrict__ flag_list, const int32_t* __restrict__ nflag,
-                               Geo g, const int2* __restrict__ xy,
+                               const int32_t* __restrict__ rec_id, Geo g, const int2* __restrict__ xy,
                                const uint8_t* __restrict__ heading, const uint8_t* __restrict__ goal,
                                const uint8_t* __restrict__ cell, const uint8_t* __restrict__ ocls,
                                const int32_t* __restrict__ D, const float* __restrict__ fex,
@@ -690,7 +936,7 @@ __global__ void k_sur_redecide(const int32_t* __restrict__ flag_list, const int3
                                const float* __restrict__ dirdot, uint8_t* __restrict__ choice) {
   const int n = *nflag;
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
-    const int p = flag_list[j];
+    const int i = flag_list[j], p = rec_id[i];
     int cx[3], ry[3];
     bool okx[3], oky[3];
     int32_t dd[9];
@@ -698,7 +944,7 @@ __global__ void k_sur_redecide(const int32_t* __restrict__ flag_list, const int3
     candidate_cells(xy[p], g, cell, ocls, D, cx, ry, okx, oky, dd, cl, oc);
     float f[9];
 #pragma unroll
-    for (int k = 0; k < 9; ++k) f[k] = fex[(size_t)j * 9 + k];
+    for (int k = 0; k < 9; ++k) f[k] = fex[(size_t)i * 9 + k];
     choice[p] = (uint8_t)pick_move<false>(f, dd, cl, oc, okx, oky, heading[p], goal[p], beta, own,
                                           dirdot, nullptr);
   }
@@ -768,9 +1014,10 @@ struct sfm_surrogate {
   unsigned long long* cnt = nullptr;
   // decisions with the exact fallback
   float delta = __builtin_inff();  // field error bound behind the margin test
-  float* fex = nullptr;            // exact field at the candidates of listed pedestrians
-  int32_t* flag_list = nullptr;
+  float* fex = nullptr;            // exact field at the candidates, by slot
+  int32_t* flag_list = nullptr;    // slots (bin order) of the listed pedestrians
   int32_t* nflag = nullptr;
+  uint8_t* fb_flag = nullptr;      // per slot: listed or not
   float* perr = nullptr;           // per-pedestrian candidate error (calibration)
   int fb_cap = 0;
   long long fallbacks = 0, decided = 0;  // totals over surrogate ticks (host copies)
@@ -899,8 +1146,17 @@ sfm_status conv_dw(sfm_surrogate* S, const bf16* in, const float* dA, const bf16
 
 void conv3_tc(const bf16* in, int Hin, int Win, const bf16* wt, const float* b, bf16* out,
               cudaStream_t s) {
-  dim3 grid(cdiv(Win - 2, kTcCols), cdiv(Hin - 2, kTcRows));
-  k_conv3_tc<<<grid, 128, 0, s>>>(in, Hin, Win, wt, b, out);
+  static int nsm = 0;
+  if (!nsm) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (nsm <= 0) nsm = 1;
+  }
+  const int ntiles = cdiv(Win - 2, kTcCols) * cdiv(Hin - 2, kTcRows);
+  cudaFuncSetAttribute(k_conv3_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kC3Smem);
+  const int grid = std::max(1, std::min(ntiles, nsm * kC3CtasPerSm));
+  k_conv3_tc<<<grid, 128, kC3Smem, s>>>(in, Hin, Win, wt, b, out);
 }
 
 // forward of the whole padded image currently in S->X (layers 2 and 3 on the
@@ -909,13 +1165,18 @@ void forward(sfm_surrogate* S, cudaStream_t s) {
   const int Hp = S->Hc + 2 * kHalo, Wp = S->Wc + 2 * kHalo;
   const float* q = S->pq;
   {
-    dim3 grid(cdiv(Wp - 4, kTcCols), cdiv(Hp - 4, kTcRows));
+    int dev = 0, nsm = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const int ntiles = cdiv(Wp - 4, kTcCols) * cdiv(Hp - 4, kTcRows);
+    const int grid = std::max(1, std::min(ntiles, std::max(nsm, 1) * kC1CtasPerSm));
     k_conv1_tc<<<grid, 128, 0, s>>>(S->X, Hp, Wp, S->wt1, q + kOffB[0], S->A1);
   }
   conv3_tc(S->A1, Hp - 4, Wp - 4, S->wt2, q + kOffB[1], S->A2, s);
   conv3_tc(S->A2, Hp - 6, Wp - 6, S->wt3, q + kOffB[2], S->A3, s);
-  k_conv_last<<<cdiv(S->Hc * S->Wc, 256), 256, 0, s>>>(S->A3, Hp - 8, Wp - 8, q + kOffW[3],
-                                                       q + kOffB[3], S->Y);
+  cudaFuncSetAttribute(k_conv_last, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kL4Smem);
+  k_conv_last<<<dim3(cdiv(S->Wc, kL4Cols), cdiv(S->Hc, kL4Rows)), 128, kL4Smem, s>>>(
+      S->A3, Hp - 8, Wp - 8, q + kOffW[3], q + kOffB[3], S->Y);
 }
 
 // loss and gradients (into S->g) for the image in S->X and targets in S->T
@@ -1012,9 +1273,11 @@ sfm_status ensure_lattice(sfm_surrogate* S, sfm_ctx* ctx) {
   if (ctx->cap > S->fb_cap) {
     sfree(S, S->fex);
     sfree(S, S->flag_list);
+    sfree(S, S->fb_flag);
     sfree(S, S->perr);
     STRY(salloc(S, &S->fex, (size_t)ctx->cap * 9));
     STRY(salloc(S, &S->flag_list, (size_t)ctx->cap));
+    STRY(salloc(S, &S->fb_flag, (size_t)ctx->cap));
     STRY(salloc(S, &S->perr, (size_t)ctx->cap));
     S->fb_cap = ctx->cap;
   }
@@ -1049,16 +1312,7 @@ void coarse_inputs(sfm_surrogate* S, sfm_ctx* ctx) {
                                                             S->Hc, S->Wc, S->X);
 }
 
-// Fsur = (Fs + pedestrian field within rn) + scale * bilinear(Y): the network
-// runs first and the near-field gather adds its interpolated output in its
-// epilogue, so the lattice is written once.  Bins must be current.
-void surrogate_field(sfm_surrogate* S, sfm_ctx* ctx) {
-  coarse_inputs(S, ctx);
-  forward(S, ctx->stream);
-  Geo gn = ctx->geo;
-  gn.r = S->cfg.near_radius;
-  Tables tb = ctx->tables();
-  tb.CT = S->CTnear;
+FarPart far_part(const sfm_surrogate* S) {
   FarPart far;
   far.Y = S->Y;
   far.s = S->cfg.coarsen;
@@ -1066,39 +1320,68 @@ void surrogate_field(sfm_surrogate* S, sfm_ctx* ctx) {
   far.Wc = S->Wc;
   far.scale = S->cfg.target_scale;
   far.inv_s = 1.f / (float)S->cfg.coarsen;
-  launch_field(gn, ctx->bin_start, ctx->rec, tb, ctx->Fs, S->Fsur, 0, 0, gn.H, ctx->ctr,
-               ctx->stream, far);
+  return far;
 }
 
-// Decisions of ctx's live pedestrians into `choice` from Fsur, then the
-// exact fallback for the pedestrians within the margin.  ref/raw_flips as
-// k_sur_decide.
+// The network's output Y (the far part on the coarse grid) for ctx's current
+// state.  Bins must be current.
+void surrogate_far(sfm_surrogate* S, sfm_ctx* ctx) {
+  coarse_inputs(S, ctx);
+  forward(S, ctx->stream);
+}
+
+// Fsur = (Fs + pedestrian field within rn) + scale * bilinear(Y) over the
+// whole lattice: the network runs first and the near-field gather adds its
+// interpolated output in its epilogue, so the lattice is written once.  Bins
+// must be current.
+void surrogate_field(sfm_surrogate* S, sfm_ctx* ctx) {
+  surrogate_far(S, ctx);
+  Geo gn = ctx->geo;
+  gn.r = S->cfg.near_radius;
+  Tables tb = ctx->tables();
+  tb.CT = S->CTnear;
+  launch_field(gn, ctx->bin_start, ctx->rec, tb, ctx->Fs, S->Fsur, 0, 0, gn.H, ctx->ctr,
+               ctx->stream, far_part(S));
+}
+
+// Decisions of ctx's live pedestrians into `choice` on the surrogate field,
+// then the exact fallback for the pedestrians within the margin.  cand: the
+// surrogate field is composed at each pedestrian's candidates from Y (which
+// surrogate_far must have computed) and the near tables; else it is read
+// from Fsur (surrogate_field).  ref/raw_flips as k_sur_decide.
 void surrogate_decide(sfm_surrogate* S, sfm_ctx* ctx, uint8_t* choice, const uint8_t* ref,
-                      unsigned long long* raw_flips) {
+                      unsigned long long* raw_flips, bool cand) {
   const Geo& g = ctx->geo;
   const Tables tb = ctx->tables();
   const int nbins = g.nbx * g.nby;
   cudaStream_t st = ctx->stream;
   cudaMemsetAsync(S->nflag, 0, sizeof(int32_t), st);
   if (ctx->n <= 0) return;
-  k_sur_decide<<<cdiv(ctx->n, 256), 256, 0, st>>>(
+  NearPart np;
+  np.CT = S->CTnear;
+  np.rn = S->cfg.near_radius;
+  np.SP = class_table_stride(np.rn);
+  np.TS = (2 * np.rn + 1 + 2 * kFieldPadRows) * np.SP;
+  auto dk = cand ? k_sur_decide<true> : k_sur_decide<false>;
+  dk<<<cdiv(ctx->n, 256), 256, 0, st>>>(
       ctx->rec_id, ctx->bin_start, nbins, g, ctx->xy, ctx->heading, ctx->goal, ctx->cell, ctx->ocls,
-      ctx->D, S->Fsur, ctx->prm.beta, tb.own, tb.dirdot, S->delta, choice, S->flag_list, S->nflag,
-      ref, raw_flips, ctx->walk());
+      ctx->D, S->Fsur, ctx->rec, ctx->Fs, np, far_part(S), ctx->prm.beta, tb.own, tb.dirdot,
+      S->delta, choice, S->flag_list, S->nflag, S->fb_flag, ref, raw_flips, ctx->walk());
   const int SP = class_table_stride(g.r);
   const int TS = (2 * g.r + 1 + 2 * kFieldPadRows) * SP;
   const size_t smem = (kTableGuard + 4 * (size_t)TS) * sizeof(float) +
                       (size_t)kFbThreads / 32 * 32 * sizeof(int2);
-  cudaFuncSetAttribute(k_sur_fallback, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  auto fb = SP == kNarrowStride ? k_sur_fallback<true> : k_sur_fallback<false>;
+  cudaFuncSetAttribute(fb, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int dev = 0, nsm = 1;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  k_sur_fallback<<<nsm > 0 ? nsm : 1, kFbThreads, smem, st>>>(S->flag_list, S->nflag, g, ctx->xy,
-                                                              ctx->bin_start, ctx->rec, ctx->CT,
-                                                              SP, TS, ctx->Fs, S->fex);
+  fb<<<nsm > 0 ? nsm : 1, kFbThreads, smem, st>>>(S->fb_flag, ctx->rec_id, nbins, g, ctx->xy,
+                                                  ctx->bin_start, ctx->rec, ctx->CT, SP, TS, ctx->Fs,
+                                                  S->fex);
   k_sur_redecide<<<cdiv(ctx->n < 152 * 2048 ? ctx->n : 152 * 2048, 256), 256, 0, st>>>(
-      S->flag_list, S->nflag, g, ctx->xy, ctx->heading, ctx->goal, ctx->cell, ctx->ocls, ctx->D,
-      S->fex, ctx->prm.beta, tb.own, tb.dirdot, choice);
+      S->flag_list, S->nflag, ctx->rec_id, g, ctx->xy, ctx->heading, ctx->goal, ctx->cell, ctx->ocls,
+      ctx->D, S->fex, ctx->prm.beta, tb.own, tb.dirdot, choice);
 }
 
 void round_params(sfm_surrogate* S) {
@@ -1316,8 +1599,8 @@ sfm_status sfm_surrogate_step(sfm_surrogate* S, sfm_ctx* ctx, int32_t nsteps) {
   for (int i = 0; i < nsteps; ++i) {
     launch_clear_dead(ctx->n, ctx->alive, ctx->choice, ctx->won, st);
     ctx_run_bins(ctx);
-    surrogate_field(S, ctx);
-    surrogate_decide(S, ctx, ctx->choice, nullptr, nullptr);
+    surrogate_far(S, ctx);
+    surrogate_decide(S, ctx, ctx->choice, nullptr, nullptr, true);
     k_count_fallbacks<<<1, 1, 0, st>>>(S->nflag, ctx->bin_start + g.nbx * g.nby, S->fb_dev);
     launch_vote(ctx->n, ctx->rec_id, ctx->bin_start, ctx->xy, ctx->choice, ctx->occ, g,
                 ctx->prm.seed, ctx->ctr, ctx->won, st);
@@ -1346,10 +1629,11 @@ sfm_status sfm_surrogate_eval(sfm_surrogate* S, sfm_ctx* ctx, sfm_surrogate_repo
   const Geo& g = ctx->geo;
   const Tables tb = ctx->tables();
   const int nbins = g.nbx * g.nby;
-  cudaEvent_t e0, e1, e2;
+  cudaEvent_t e0, e1, e2, e3;
   SCU(cudaEventCreate(&e0));
   SCU(cudaEventCreate(&e1));
   SCU(cudaEventCreate(&e2));
+  SCU(cudaEventCreate(&e3));
   // exact: bins, field, decisions (into ctx->choice)
   SCU(cudaEventRecord(e0, st));
   ctx_run_bins(ctx);
@@ -1358,12 +1642,17 @@ sfm_status sfm_surrogate_eval(sfm_surrogate* S, sfm_ctx* ctx, sfm_surrogate_repo
                 ctx->cell, ctx->ocls, ctx->D, ctx->F, 0, -1, -1, 0, 0, g.H, g, ctx->prm.beta, tb,
                 ctx->choice, st, ctx->walk());
   SCU(cudaEventRecord(e1, st));
-  // surrogate: bins, field, decisions with the fallback (into choice2)
+  // surrogate tick's decisions: bins, network, decisions on the surrogate
+  // field at the candidates with the fallback (into choice2)
   SCU(cudaMemsetAsync(S->cnt, 0, 2 * sizeof(unsigned long long), st));
+  SCU(cudaEventRecord(e1, st));
   ctx_run_bins(ctx);
-  surrogate_field(S, ctx);
-  surrogate_decide(S, ctx, S->choice2, ctx->choice, S->cnt + 1);
+  surrogate_far(S, ctx);
+  surrogate_decide(S, ctx, S->choice2, ctx->choice, S->cnt + 1, true);
   SCU(cudaEventRecord(e2, st));
+  // the surrogate field over the whole lattice (network and lattice pass)
+  surrogate_field(S, ctx);
+  SCU(cudaEventRecord(e3, st));
   if (ctx->n > 0)
     k_diff_choices<<<cdiv(ctx->n, 256), 256, 0, st>>>(ctx->rec_id, ctx->bin_start, nbins,
                                                       ctx->choice, S->choice2, S->cnt);
@@ -1382,12 +1671,14 @@ sfm_status sfm_surrogate_eval(sfm_surrogate* S, sfm_ctx* ctx, sfm_surrogate_repo
     a += red[2 * i];
     b += red[2 * i + 1];
   }
-  float t_ex = 0.f, t_su = 0.f;
+  float t_ex = 0.f, t_su = 0.f, t_sf = 0.f;
   cudaEventElapsedTime(&t_ex, e0, e1);
   cudaEventElapsedTime(&t_su, e1, e2);
+  cudaEventElapsedTime(&t_sf, e2, e3);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   cudaEventDestroy(e2);
+  cudaEventDestroy(e3);
   const double nd = nrec > 0 ? (double)nrec : 1.0;
   rep->field_rel_err = b > 0 ? a / b : 0.0;
   rep->flip_rate = (double)cnt[0] / nd;
@@ -1395,6 +1686,7 @@ sfm_status sfm_surrogate_eval(sfm_surrogate* S, sfm_ctx* ctx, sfm_surrogate_repo
   rep->fallback_rate = (double)nfl / nd;
   rep->ms_surrogate = t_su;
   rep->ms_exact = t_ex;
+  rep->ms_surrogate_field = t_sf;
   rep->delta = S->delta;
   rep->decided = nrec;
   return SFM_OK;
