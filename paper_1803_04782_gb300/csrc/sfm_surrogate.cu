@@ -110,6 +110,12 @@ __device__ __forceinline__ void ldsm_x4(uint32_t addr, uint32_t& r0, uint32_t& r
                : "r"(addr));
 }
 
+__device__ __forceinline__ void ldsm_x2(uint32_t addr, uint32_t& r0, uint32_t& r1) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];\n"
+               : "=r"(r0), "=r"(r1)
+               : "r"(addr));
+}
+
 __device__ __forceinline__ void mma_bf16(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2,
                                          uint32_t a3, uint32_t b0, uint32_t b1) {
   asm volatile(
@@ -131,9 +137,13 @@ constexpr int kC3W = 9 * 32 * kTcPad;                           // weights, BF16
 constexpr size_t kC3Smem = (size_t)(kC3W + 2 * kC3In) * 2;
 constexpr int kC3CtasPerSm = 4;
 
+// NT n8 tiles of output channels: 4 (32 -> 32, ReLU, BF16 out) or 1 for
+// layer 4 (32 -> 1: weights of output 0 in row 0 of the n8 tile, rows 1-7
+// zero; no activation, FP32 out in yout).
+template <int NT>
 __global__ void __launch_bounds__(128)
     k_conv3_tc(const bf16* __restrict__ in, int Hin, int Win, const bf16* __restrict__ Wt,
-               const float* __restrict__ b, bf16* __restrict__ out) {
+               const float* __restrict__ b, bf16* __restrict__ out, float* __restrict__ yout) {
   extern __shared__ __align__(16) bf16 sm3[];
   bf16* sW = sm3;
   const int Hout = Hin - 2, Wout = Win - 2;
@@ -141,8 +151,8 @@ __global__ void __launch_bounds__(128)
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint32_t sW0 = (uint32_t)__cvta_generic_to_shared(sW);
   const uint32_t sIn0 = sW0 + (uint32_t)kC3W * 2;
-  // weights: 9 x 32 rows of 32 channels (4 chunks of 16 bytes each), once per CTA
-  for (int i = tid; i < 9 * 32 * 4; i += blockDim.x) {
+  // weights: 9 x 8 NT rows of 32 channels (4 chunks of 16 bytes each), once per CTA
+  for (int i = tid; i < 9 * 8 * NT * 4; i += blockDim.x) {
     const int q = i & 3, row = i >> 2;
     cp_async16(sW0 + (uint32_t)(row * kTcPad + q * 8) * 2, Wt + row * 32 + q * 8);
   }
@@ -175,24 +185,31 @@ __global__ void __launch_bounds__(128)
     cp_async_wait_prev();
     __syncthreads();
     const uint32_t sIn = sIn0 + (uint32_t)(bi * kC3In) * 2;
-    float acc[2][4][4];
+    float acc[2][NT][4];
 #pragma unroll
     for (int mt = 0; mt < 2; ++mt)
 #pragma unroll
-      for (int nt = 0; nt < 4; ++nt)
+      for (int nt = 0; nt < NT; ++nt)
 #pragma unroll
         for (int k = 0; k < 4; ++k) acc[mt][nt][k] = 0.f;
-#pragma unroll 1
+#pragma unroll
     for (int kk = 0; kk < 9; ++kk) {
       const int ky = kk / 3, kx = kk % 3;
 #pragma unroll
       for (int kb = 0; kb < 2; ++kb) {
-        uint32_t bw[4][2];
+        uint32_t bw[NT][2];
+        if constexpr (NT == 4) {
 #pragma unroll
-        for (int np = 0; np < 2; ++np) {
+          for (int np = 0; np < 2; ++np) {
+            const uint32_t addr =
+                sW0 + (uint32_t)(((kk * 32 + np * 16 + b_n) * kTcPad + kb * 16 + b_k) * 2);
+            ldsm_x4(addr, bw[2 * np][0], bw[2 * np][1], bw[2 * np + 1][0], bw[2 * np + 1][1]);
+          }
+        } else {
+          // one n8 tile: lanes 0-15 address rows (lane & 7) at k offset 8 (lane >> 3)
           const uint32_t addr =
-              sW0 + (uint32_t)(((kk * 32 + np * 16 + b_n) * kTcPad + kb * 16 + b_k) * 2);
-          ldsm_x4(addr, bw[2 * np][0], bw[2 * np][1], bw[2 * np + 1][0], bw[2 * np + 1][1]);
+              sW0 + (uint32_t)(((kk * 8 + (lane & 7)) * kTcPad + kb * 16 + 8 * ((lane >> 3) & 1)) * 2);
+          ldsm_x2(addr, bw[0][0], bw[0][1]);
         }
 #pragma unroll
         for (int mt = 0; mt < 2; ++mt) {
@@ -202,12 +219,13 @@ __global__ void __launch_bounds__(128)
           uint32_t a0, a1, a2, a3;
           ldsm_x4(addr, a0, a1, a2, a3);
 #pragma unroll
-          for (int nt = 0; nt < 4; ++nt) mma_bf16(acc[mt][nt], a0, a1, a2, a3, bw[nt][0], bw[nt][1]);
+          for (int nt = 0; nt < NT; ++nt) mma_bf16(acc[mt][nt], a0, a1, a2, a3, bw[nt][0], bw[nt][1]);
         }
       }
     }
-    // epilogue: bias, ReLU, BF16; accumulator (row g = lane/4 and g+8, column
-    // pair 2*(lane%4)) of each m16 x n8 tile
+    // epilogue: accumulator (row g = lane/4 and g+8, column pair 2*(lane%4))
+    // of each m16 x n8 tile; bias, then ReLU and BF16 (NT 4) or channel 0 in
+    // FP32 (NT 1)
     const int x0 = (t % ntx) * kTcCols, y0 = (t / ntx) * kTcRows;
 #pragma unroll
     for (int mt = 0; mt < 2; ++mt) {
@@ -216,13 +234,17 @@ __global__ void __launch_bounds__(128)
       for (int half = 0; half < 2; ++half) {
         const int x = x0 + g + 8 * half;
         if (y >= Hout || x >= Wout) continue;
-        __nv_bfloat162* o = reinterpret_cast<__nv_bfloat162*>(out + ((size_t)y * Wout + x) * 32);
+        if constexpr (NT == 1) {
+          if (cp == 0) yout[(size_t)y * Wout + x] = acc[mt][0][2 * half] + b[0];
+        } else {
+          __nv_bfloat162* o = reinterpret_cast<__nv_bfloat162*>(out + ((size_t)y * Wout + x) * 32);
 #pragma unroll
-        for (int nt = 0; nt < 4; ++nt) {
-          const int c = nt * 8 + cp;
-          const float v0 = fmaxf(acc[mt][nt][2 * half] + b[c], 0.f);
-          const float v1 = fmaxf(acc[mt][nt][2 * half + 1] + b[c + 1], 0.f);
-          o[c / 2] = __floats2bfloat162_rn(v0, v1);
+          for (int nt = 0; nt < NT; ++nt) {
+            const int c = nt * 8 + cp;
+            const float v0 = fmaxf(acc[mt][nt][2 * half] + b[c], 0.f);
+            const float v1 = fmaxf(acc[mt][nt][2 * half + 1] + b[c + 1], 0.f);
+            o[c / 2] = __floats2bfloat162_rn(v0, v1);
+          }
         }
       }
     }
@@ -241,42 +263,44 @@ __global__ void k_pack_w3(const float* __restrict__ w, bf16* __restrict__ wt) {
   wt[i] = __float2bfloat16(w[(kk * 32 + c) * 32 + o]);
 }
 
-// ------------------------------------------- tensor-core 5x5, 3 -> 32
-// Layer 1 as an implicit GEMM with K = 75 (ky, kx, c) padded to 80: the CTA
-// stages its 12 x 20-pixel input tile, expands it to a [128 pixel][80] BF16
-// matrix in shared memory (rows padded to 88 elements, 176 bytes, so the
-// ldmatrix row fetches hit distinct banks) and runs 5 k16 steps of
-// m16n8k16 per m16 tile; layout of warps and fragments as k_conv3_tc, and
-// persistent CTAs as there (the next tile's input is prefetched into
-// registers).
-constexpr int kC1K = 80, kC1Pad = 88;
-static_assert(kTcCols + 4 == 20, "c_im2col assumes 20-pixel input rows");
-// input-tile offset of K entry k = (ky*5 + kx)*3 + c: (ky*20 + kx)*3 + c
-__constant__ int c_im2col[80] = {
-#define C1ROW(ky) (ky * 20 + 0) * 3, (ky * 20 + 0) * 3 + 1, (ky * 20 + 0) * 3 + 2, \
-                  (ky * 20 + 1) * 3, (ky * 20 + 1) * 3 + 1, (ky * 20 + 1) * 3 + 2, \
-                  (ky * 20 + 2) * 3, (ky * 20 + 2) * 3 + 1, (ky * 20 + 2) * 3 + 2, \
-                  (ky * 20 + 3) * 3, (ky * 20 + 3) * 3 + 1, (ky * 20 + 3) * 3 + 2, \
-                  (ky * 20 + 4) * 3, (ky * 20 + 4) * 3 + 1, (ky * 20 + 4) * 3 + 2
-    C1ROW(0), C1ROW(1), C1ROW(2), C1ROW(3), C1ROW(4), 0, 0, 0, 0, 0
-#undef C1ROW
-};
+// BF16 weights of layer 4 (3x3, 32 -> 1) as one n8 tile: [ky][kx][8][in],
+// row 0 the output's weights, rows 1-7 zero.
+__global__ void k_pack_w4(const float* __restrict__ w, bf16* __restrict__ wt) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 9 * 8 * 32) return;
+  const int c = i % 32, o = (i / 32) % 8, kk = i / 256;
+  wt[i] = __float2bfloat16(o == 0 ? w[kk * 32 + c] : 0.f);
+}
 
+// ------------------------------------------- tensor-core 5x5, 3 -> 32
+// Layer 1 as an implicit GEMM, one k16 step per kernel row ky: the K entries
+// of row ky are (kx, c), 15 of them plus a zero, which for output pixel px
+// are the 15 consecutive input elements from pixel px of input row py + ky
+// (channel-last).  The CTA stages its 12 x 20-pixel input tile, expands each
+// of its 12 x 16 (row, pixel) starts to such a 16-element run (rows padded
+// to 24 elements, 48 bytes, so the ldmatrix row fetches hit distinct banks;
+// a 5x expansion where a full im2col is 25x) and runs 5 k16 steps of
+// m16n8k16 per m16 tile with A rows from row py + ky of the runs; layout of
+// warps and fragments as k_conv3_tc, and persistent CTAs as there (the next
+// tile's input is prefetched into registers).  Weights: [ky][out][16].
+constexpr int kC1K = 80, kC1Run = 24;
 constexpr int kC1CtasPerSm = 6;
 constexpr int kC1TileElems = (kTcRows + 4) * (kTcCols + 4) * 3;  // input tile, BF16 elements
 constexpr int kC1PerThread = (kC1TileElems + 127) / 128;
+constexpr int kC1Starts = (kTcRows + 4) * kTcCols;               // (row, pixel) run starts
+static_assert(kC1TileElems % 2 == 0, "the input tile is read as 32-bit words");
 
 __global__ void __launch_bounds__(128)
     k_conv1_tc(const bf16* __restrict__ in, int Hin, int Win, const bf16* __restrict__ Wt,
                const float* __restrict__ b, bf16* __restrict__ out) {
   constexpr int TH = kTcRows + 4, TW = kTcCols + 4;
   __shared__ __align__(16) bf16 sX[TH * TW * 3];
-  __shared__ __align__(16) bf16 sA[kTcRows * kTcCols * kC1Pad];
-  __shared__ __align__(16) bf16 sW[32 * kC1Pad];
+  __shared__ __align__(16) bf16 sR[kC1Starts * kC1Run];
+  __shared__ __align__(16) bf16 sW[5 * 32 * kC1Run];
   const int Hout = Hin - 4, Wout = Win - 4;
   const int ntx = (Wout + kTcCols - 1) / kTcCols, ntiles = ntx * ((Hout + kTcRows - 1) / kTcRows);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  for (int i = tid; i < 32 * kC1K; i += blockDim.x) sW[(i / kC1K) * kC1Pad + i % kC1K] = Wt[i];
+  for (int i = tid; i < 5 * 32 * 16; i += blockDim.x) sW[(i / 16) * kC1Run + i % 16] = Wt[i];
   // persistent CTAs take the tiles with the grid's stride; the next tile's
   // input elements are loaded into registers while the current one is computed
   bf16 pre[kC1PerThread];
@@ -292,8 +316,9 @@ __global__ void __launch_bounds__(128)
     }
   };
   if ((int)blockIdx.x < ntiles) fetch(blockIdx.x);
-  const uint32_t sA0 = (uint32_t)__cvta_generic_to_shared(sA);
+  const uint32_t sR0 = (uint32_t)__cvta_generic_to_shared(sR);
   const uint32_t sW0 = (uint32_t)__cvta_generic_to_shared(sW);
+  const uint32_t* sXw = reinterpret_cast<const uint32_t*>(sX);
   const int a_row = (lane & 7) + 8 * ((lane >> 3) & 1), a_col = 8 * (lane >> 4);
   const int b_n = (lane & 7) + 8 * (lane >> 4), b_k = 8 * ((lane >> 3) & 1);
   const int g = lane >> 2, cp = 2 * (lane & 3);
@@ -303,18 +328,27 @@ __global__ void __launch_bounds__(128)
       if (tid + 128 * u < kC1TileElems) sX[tid + 128 * u] = pre[u];
     __syncthreads();
     if (t + (int)gridDim.x < ntiles) fetch(t + gridDim.x);
-    {
-      // thread = output pixel of the tile (128 of them): its row of the
-      // im2col matrix, two K entries per 4-byte store
-      const int p = tid, base = ((p / kTcCols) * TW + p % kTcCols) * 3;
-      __nv_bfloat162* row = reinterpret_cast<__nv_bfloat162*>(sA + p * kC1Pad);
-#pragma unroll 8
-      for (int k = 0; k < kC1K; k += 2) {
-        const bf16 z = __float2bfloat16(0.f);
-        const bf16 a = k < 75 ? sX[base + c_im2col[k]] : z;
-        const bf16 bb = k + 1 < 75 ? sX[base + c_im2col[k + 1]] : z;
-        row[k / 2] = __halves2bfloat162(a, bb);
+    // runs: start (py, px) holds input elements e0 .. e0 + 14, e0 = (py TW + px) 3,
+    // and a zero; read as the 8 words from e0 rounded down to even
+    for (int j = tid; j < kC1Starts; j += blockDim.x) {
+      const int py = j / kTcCols, px = j % kTcCols;
+      const int e0 = (py * TW + px) * 3, w0 = e0 >> 1;
+      uint32_t w[9];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) w[k] = sXw[w0 + k];
+      w[8] = 0u;
+      uint32_t o[8];
+      if (e0 & 1) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) o[k] = __byte_perm(w[k], w[k + 1], 0x5432);
+      } else {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) o[k] = w[k];
       }
+      o[7] &= 0x0000ffffu;  // the 16th entry is zero
+      uint4* dst = reinterpret_cast<uint4*>(sR + j * kC1Run);
+      dst[0] = make_uint4(o[0], o[1], o[2], o[3]);
+      dst[1] = make_uint4(o[4], o[5], o[6], o[7]);
     }
     __syncthreads();
     float acc[2][4][4];
@@ -325,17 +359,17 @@ __global__ void __launch_bounds__(128)
 #pragma unroll
         for (int k = 0; k < 4; ++k) acc[mt][nt][k] = 0.f;
 #pragma unroll
-    for (int kb = 0; kb < kC1K / 16; ++kb) {
+    for (int ky = 0; ky < 5; ++ky) {
       uint32_t bw[4][2];
 #pragma unroll
       for (int np = 0; np < 2; ++np)
-        ldsm_x4(sW0 + (uint32_t)(((np * 16 + b_n) * kC1Pad + kb * 16 + b_k) * 2), bw[2 * np][0],
+        ldsm_x4(sW0 + (uint32_t)(((ky * 32 + np * 16 + b_n) * kC1Run + b_k) * 2), bw[2 * np][0],
                 bw[2 * np][1], bw[2 * np + 1][0], bw[2 * np + 1][1]);
 #pragma unroll
       for (int mt = 0; mt < 2; ++mt) {
-        const int prow = (2 * warp + mt) * kTcCols + a_row;
+        const int prow = (2 * warp + mt + ky) * kTcCols + a_row;
         uint32_t a0, a1, a2, a3;
-        ldsm_x4(sA0 + (uint32_t)((prow * kC1Pad + kb * 16 + a_col) * 2), a0, a1, a2, a3);
+        ldsm_x4(sR0 + (uint32_t)((prow * kC1Run + a_col) * 2), a0, a1, a2, a3);
 #pragma unroll
         for (int nt = 0; nt < 4; ++nt) mma_bf16(acc[mt][nt], a0, a1, a2, a3, bw[nt][0], bw[nt][1]);
       }
@@ -358,84 +392,18 @@ __global__ void __launch_bounds__(128)
         }
       }
     }
-    // sX and sA are rewritten by the next tile
+    // sX and sR are rewritten by the next tile
     __syncthreads();
   }
 }
 
-// BF16 layer-1 weights [out][80] (k = (ky*5 + kx)*3 + c, zero beyond 75)
-// from the internal [ky][kx][in][out] floats.
+// BF16 layer-1 weights [ky][out][16] (entry kk = kx*3 + c, zero at 15) from
+// the internal [ky][kx][in][out] floats.
 __global__ void k_pack_w1(const float* __restrict__ w, bf16* __restrict__ wt) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= 32 * kC1K) return;
-  const int o = i / kC1K, k = i % kC1K;
-  wt[i] = __float2bfloat16(k < 75 ? w[k * 32 + o] : 0.f);
-}
-
-// Layer 4 (3x3, 32 -> 1, no activation), FP32 sums in the order (ky, kx, c).
-// A CTA of 128 threads computes an 8 x 32 output tile: the 10 x 34-pixel
-// input tile is staged in shared memory with pixel rows padded to 40
-// channels (80 bytes, so 8 threads reading 16 bytes at consecutive pixels hit
-// distinct banks), and each thread computes 2 outputs of one column, reusing
-// one kernel offset's 32 weights from registers for both; 27 KB a CTA lets 8
-// CTAs share an SM, whose tile loads overlap the others' sums.
-constexpr int kL4Rows = 8, kL4Cols = 32, kL4Pad = 40, kL4Per = kL4Rows / 4;
-constexpr size_t kL4Smem = (size_t)(kL4Rows + 2) * (kL4Cols + 2) * kL4Pad * 2;
-
-__global__ void __launch_bounds__(128)
-    k_conv_last(const bf16* __restrict__ in, int Hin, int Win, const float* __restrict__ Wt,
-                const float* __restrict__ b, float* __restrict__ out) {
-  extern __shared__ __align__(16) bf16 sIn4[];
-  __shared__ __align__(16) float sW[9 * 32];
-  constexpr int TW = kL4Cols + 2, TH = kL4Rows + 2;
-  const int Hout = Hin - 2, Wout = Win - 2;
-  const int x0 = blockIdx.x * kL4Cols, y0 = blockIdx.y * kL4Rows, tid = threadIdx.x;
-  for (int i = tid; i < 9 * 32; i += blockDim.x) sW[i] = Wt[i];
-  for (int i = tid; i < TH * TW * 4; i += blockDim.x) {
-    const int q = i & 3, p = i >> 2, px = p % TW, py = p / TW;
-    const int gy = y0 + py, gx = x0 + px;
-    uint4 v = make_uint4(0, 0, 0, 0);
-    if (gy < Hin && gx < Win) v = *reinterpret_cast<const uint4*>(in + ((size_t)gy * Win + gx) * 32 + q * 8);
-    *reinterpret_cast<uint4*>(sIn4 + p * kL4Pad + q * 8) = v;
-  }
-  __syncthreads();
-  const int tx = tid & 31, ty = (tid >> 5) * kL4Per;
-  float acc[kL4Per];
-#pragma unroll
-  for (int j = 0; j < kL4Per; ++j) acc[j] = b[0];
-#pragma unroll 1
-  for (int kk = 0; kk < 9; ++kk) {
-    const int ky = kk / 3, kx = kk % 3;
-    float w[32];
-#pragma unroll
-    for (int c = 0; c < 32; c += 4) {
-      const float4 t = *reinterpret_cast<const float4*>(sW + kk * 32 + c);
-      w[c] = t.x;
-      w[c + 1] = t.y;
-      w[c + 2] = t.z;
-      w[c + 3] = t.w;
-    }
-#pragma unroll
-    for (int j = 0; j < kL4Per; ++j) {
-      const uint4* px = reinterpret_cast<const uint4*>(sIn4 + ((ty + j + ky) * TW + tx + kx) * kL4Pad);
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const uint4 v = px[q];
-        const uint32_t w4[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w4[e]));
-          acc[j] = fmaf(f.x, w[q * 8 + 2 * e], acc[j]);
-          acc[j] = fmaf(f.y, w[q * 8 + 2 * e + 1], acc[j]);
-        }
-      }
-    }
-  }
-#pragma unroll
-  for (int j = 0; j < kL4Per; ++j) {
-    const int y = y0 + ty + j, x = x0 + tx;
-    if (y < Hout && x < Wout) out[(size_t)y * Wout + x] = acc[j];
-  }
+  if (i >= 5 * 32 * 16) return;
+  const int kk = i % 16, o = (i / 16) % 32, ky = i / 512;
+  wt[i] = __float2bfloat16(kk < 15 ? w[(ky * 15 + kk) * 32 + o] : 0.f);
 }
 
 // -------------------------------------------------------------- backward
@@ -800,6 +768,7 @@ __global__ void k_sur_decide(const int32_t* __restrict__ rec_id, const int32_t* 
                              const float* __restrict__ dirdot, float delta,
                              uint8_t* __restrict__ choice, int32_t* __restrict__ flag_list,
                              int32_t* __restrict__ nflag, uint8_t* __restrict__ fb_flag,
+                             int32_t* __restrict__ fb_dd, uint32_t* __restrict__ fb_info,
                              const uint8_t* __restrict__ ref,
                              unsigned long long* __restrict__ raw_flips, WalkPeriods wp) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -833,7 +802,19 @@ __global__ void k_sur_decide(const int32_t* __restrict__ rec_id, const int32_t* 
     choice[p] = (uint8_t)best;
     const bool fl = !(margin > margin_allowance(delta, emag, fmag));
     fb_flag[i] = fl;
-    if (fl) flag_list[atomicAdd(nflag, 1)] = i;
+    if (fl) {
+      flag_list[atomicAdd(nflag, 1)] = i;
+      // what the fallback's decision needs besides the field: guidance
+      // distances, admissible candidates, heading and goal
+      uint32_t mask = 0;
+#pragma unroll
+      for (int k = 0; k < 9; ++k) {
+        fb_dd[(size_t)i * 9 + k] = dd[k];
+        const int xi = move_dx(k) + 1, yi = move_dy(k) + 1;
+        if (k == 0 || (okx[xi] && oky[yi] && cl[k] != kWall && oc[k] == 0)) mask |= 1u << k;
+      }
+      fb_info[i] = mask | (uint32_t)heading[p] << 9 | (uint32_t)goal[p] << 16;
+    }
     differs = ref && ref[p] != best;
   }
   if (raw_flips) {
@@ -853,9 +834,11 @@ __global__ void k_sur_decide(const int32_t* __restrict__ rec_id, const int32_t* 
 // gather's terms in its order, bit for bit (its other terms are zero pads).
 // With a wide table stride an out-of-reach candidate reads a zero pad, so
 // only NARROW tests each candidate.  The class tables are staged in shared
-// memory as for the gather (one CTA of 1024 threads per SM); fex is indexed
-// by the record's slot.  Values of candidates outside the lattice are never
-// read.
+// memory as for the gather (one CTA of 1024 threads per SM).  Each listed
+// pedestrian is then decided again with the exact path's energy on these
+// values, from the guidance distances, admissibility, heading and goal that
+// k_sur_decide stored for its slot (values of candidates outside the lattice
+// are never used).
 constexpr int kFbThreads = 1024;
 
 template <bool NARROW>
@@ -863,7 +846,9 @@ __global__ void __launch_bounds__(kFbThreads, 1)
     k_sur_fallback(const uint8_t* __restrict__ fb_flag, const int32_t* __restrict__ rec_id, int nbins,
                    Geo g, const int2* __restrict__ xy, const int32_t* __restrict__ bin_start,
                    const uint32_t* __restrict__ rec, const float* __restrict__ CT, int SP, int TS,
-                   const float* __restrict__ Fs, float* __restrict__ fex) {
+                   const float* __restrict__ Fs, const int32_t* __restrict__ fb_dd,
+                   const uint32_t* __restrict__ fb_info, float beta, const float* __restrict__ own,
+                   const float* __restrict__ dirdot, uint8_t* __restrict__ choice) {
   extern __shared__ __align__(16) float sm[];
   float* sT = sm + kTableGuard;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -913,40 +898,27 @@ __global__ void __launch_bounds__(kFbThreads, 1)
           });
     }
     if (fl) {
+      // the decision again on the exact candidate field, by the exact path's
+      // energy (pick_move) from what k_sur_decide stored for this slot
+      const uint32_t info = fb_info[i];
+      float f[9];
+      int32_t dd[9];
+      uint8_t cl[9], oc[9];
 #pragma unroll
       for (int k = 0; k < 9; ++k) {
         int tx, ty;
         const bool ok = wrap_coord(q.x + move_dx(k), g.W, g.px, tx) &
                         wrap_coord(q.y + move_dy(k), g.H, g.py, ty);
-        fex[(size_t)i * 9 + k] = ok ? Fs[(size_t)ty * g.W + tx] + acc[k] : 0.f;
+        f[k] = ok ? Fs[(size_t)ty * g.W + tx] + acc[k] : 0.f;
+        dd[k] = fb_dd[(size_t)i * 9 + k];
+        cl[k] = 0;
+        oc[k] = (info >> k) & 1u ? 0 : 1;  // admissible iff its mask bit is set
       }
+      const bool ok3[3] = {true, true, true};
+      choice[rec_id[i]] = (uint8_t)pick_move<false>(f, dd, cl, oc, ok3, ok3, (int)((info >> 9) & 15u),
+                                                    (int)((info >> 16) & 255u), beta, own, dirdot,
+                                                    nullptr);
     }
-  }
-}
-
-// The listed pedestrians decided again on the exact candidate field (fex,
-// indexed by slot), with the exact path's energy.  (A separate kernel: done
-// inside the fallback, the decision's scattered loads stall its few warps.)
-__global__ void k_sur_redecide(const int32_t* __restrict__ flag_list, const int32_t* __restrict__ nflag,
-                               const int32_t* __restrict__ rec_id, Geo g, const int2* __restrict__ xy,
-                               const uint8_t* __restrict__ heading, const uint8_t* __restrict__ goal,
-                               const uint8_t* __restrict__ cell, const uint8_t* __restrict__ ocls,
-                               const int32_t* __restrict__ D, const float* __restrict__ fex,
-                               float beta, const float* __restrict__ own,
-                               const float* __restrict__ dirdot, uint8_t* __restrict__ choice) {
-  const int n = *nflag;
-  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
-    const int i = flag_list[j], p = rec_id[i];
-    int cx[3], ry[3];
-    bool okx[3], oky[3];
-    int32_t dd[9];
-    uint8_t cl[9], oc[9];
-    candidate_cells(xy[p], g, cell, ocls, D, cx, ry, okx, oky, dd, cl, oc);
-    float f[9];
-#pragma unroll
-    for (int k = 0; k < 9; ++k) f[k] = fex[(size_t)i * 9 + k];
-    choice[p] = (uint8_t)pick_move<false>(f, dd, cl, oc, okx, oky, heading[p], goal[p], beta, own,
-                                          dirdot, nullptr);
   }
 }
 
@@ -995,7 +967,7 @@ struct sfm_surrogate {
   std::string err;
   // parameters (internal layout), BF16-rounded copies, Adam state, gradients
   float *p = nullptr, *pq = nullptr, *m = nullptr, *v = nullptr, *g = nullptr;
-  bf16 *wt1 = nullptr, *wt2 = nullptr, *wt3 = nullptr;  // packed for the tensor-core kernels
+  bf16 *wt1 = nullptr, *wt2 = nullptr, *wt3 = nullptr, *wt4 = nullptr;  // for the tensor cores
   int adam_t = 0;
   // activations for an image of (Hc + 2 kHalo) x (Wc + 2 kHalo) coarse cells
   int Hc = 0, Wc = 0;
@@ -1014,7 +986,8 @@ struct sfm_surrogate {
   unsigned long long* cnt = nullptr;
   // decisions with the exact fallback
   float delta = __builtin_inff();  // field error bound behind the margin test
-  float* fex = nullptr;            // exact field at the candidates, by slot
+  int32_t* fb_dd = nullptr;        // per listed slot: guidance distances D at the 9 candidates
+  uint32_t* fb_info = nullptr;     // per listed slot: admissible mask | heading << 9 | goal << 16
   int32_t* flag_list = nullptr;    // slots (bin order) of the listed pedestrians
   int32_t* nflag = nullptr;
   uint8_t* fb_flag = nullptr;      // per slot: listed or not
@@ -1144,8 +1117,10 @@ sfm_status conv_dw(sfm_surrogate* S, const bf16* in, const float* dA, const bf16
   return SFM_OK;
 }
 
+// 3x3 layer on the tensor cores: 32 -> 32 into out (BF16), or with yout
+// the 32 -> 1 last layer into yout (FP32; wt packed by k_pack_w4)
 void conv3_tc(const bf16* in, int Hin, int Win, const bf16* wt, const float* b, bf16* out,
-              cudaStream_t s) {
+              cudaStream_t s, float* yout = nullptr) {
   static int nsm = 0;
   if (!nsm) {
     int dev = 0;
@@ -1154,13 +1129,18 @@ void conv3_tc(const bf16* in, int Hin, int Win, const bf16* wt, const float* b, 
     if (nsm <= 0) nsm = 1;
   }
   const int ntiles = cdiv(Win - 2, kTcCols) * cdiv(Hin - 2, kTcRows);
-  cudaFuncSetAttribute(k_conv3_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kC3Smem);
   const int grid = std::max(1, std::min(ntiles, nsm * kC3CtasPerSm));
-  k_conv3_tc<<<grid, 128, kC3Smem, s>>>(in, Hin, Win, wt, b, out);
+  if (yout) {
+    cudaFuncSetAttribute(k_conv3_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kC3Smem);
+    k_conv3_tc<1><<<grid, 128, kC3Smem, s>>>(in, Hin, Win, wt, b, nullptr, yout);
+  } else {
+    cudaFuncSetAttribute(k_conv3_tc<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kC3Smem);
+    k_conv3_tc<4><<<grid, 128, kC3Smem, s>>>(in, Hin, Win, wt, b, out, nullptr);
+  }
 }
 
-// forward of the whole padded image currently in S->X (layers 2 and 3 on the
-// tensor cores, 1 and 4 on the FP32 pipes)
+// forward of the whole padded image currently in S->X (all four layers on
+// the tensor cores, FP32 accumulation)
 void forward(sfm_surrogate* S, cudaStream_t s) {
   const int Hp = S->Hc + 2 * kHalo, Wp = S->Wc + 2 * kHalo;
   const float* q = S->pq;
@@ -1174,9 +1154,7 @@ void forward(sfm_surrogate* S, cudaStream_t s) {
   }
   conv3_tc(S->A1, Hp - 4, Wp - 4, S->wt2, q + kOffB[1], S->A2, s);
   conv3_tc(S->A2, Hp - 6, Wp - 6, S->wt3, q + kOffB[2], S->A3, s);
-  cudaFuncSetAttribute(k_conv_last, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kL4Smem);
-  k_conv_last<<<dim3(cdiv(S->Wc, kL4Cols), cdiv(S->Hc, kL4Rows)), 128, kL4Smem, s>>>(
-      S->A3, Hp - 8, Wp - 8, q + kOffW[3], q + kOffB[3], S->Y);
+  conv3_tc(S->A3, Hp - 8, Wp - 8, S->wt4, q + kOffB[3], nullptr, s, S->Y);
 }
 
 // loss and gradients (into S->g) for the image in S->X and targets in S->T
@@ -1271,11 +1249,13 @@ sfm_status ensure_lattice(sfm_surrogate* S, sfm_ctx* ctx) {
     S->choice_cap = ctx->cap;
   }
   if (ctx->cap > S->fb_cap) {
-    sfree(S, S->fex);
+    sfree(S, S->fb_dd);
+    sfree(S, S->fb_info);
     sfree(S, S->flag_list);
     sfree(S, S->fb_flag);
     sfree(S, S->perr);
-    STRY(salloc(S, &S->fex, (size_t)ctx->cap * 9));
+    STRY(salloc(S, &S->fb_dd, (size_t)ctx->cap * 9));
+    STRY(salloc(S, &S->fb_info, (size_t)ctx->cap));
     STRY(salloc(S, &S->flag_list, (size_t)ctx->cap));
     STRY(salloc(S, &S->fb_flag, (size_t)ctx->cap));
     STRY(salloc(S, &S->perr, (size_t)ctx->cap));
@@ -1366,7 +1346,8 @@ void surrogate_decide(sfm_surrogate* S, sfm_ctx* ctx, uint8_t* choice, const uin
   dk<<<cdiv(ctx->n, 256), 256, 0, st>>>(
       ctx->rec_id, ctx->bin_start, nbins, g, ctx->xy, ctx->heading, ctx->goal, ctx->cell, ctx->ocls,
       ctx->D, S->Fsur, ctx->rec, ctx->Fs, np, far_part(S), ctx->prm.beta, tb.own, tb.dirdot,
-      S->delta, choice, S->flag_list, S->nflag, S->fb_flag, ref, raw_flips, ctx->walk());
+      S->delta, choice, S->flag_list, S->nflag, S->fb_flag, S->fb_dd, S->fb_info, ref, raw_flips,
+      ctx->walk());
   const int SP = class_table_stride(g.r);
   const int TS = (2 * g.r + 1 + 2 * kFieldPadRows) * SP;
   const size_t smem = (kTableGuard + 4 * (size_t)TS) * sizeof(float) +
@@ -1376,19 +1357,17 @@ void surrogate_decide(sfm_surrogate* S, sfm_ctx* ctx, uint8_t* choice, const uin
   int dev = 0, nsm = 1;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  fb<<<nsm > 0 ? nsm : 1, kFbThreads, smem, st>>>(S->fb_flag, ctx->rec_id, nbins, g, ctx->xy,
-                                                  ctx->bin_start, ctx->rec, ctx->CT, SP, TS, ctx->Fs,
-                                                  S->fex);
-  k_sur_redecide<<<cdiv(ctx->n < 152 * 2048 ? ctx->n : 152 * 2048, 256), 256, 0, st>>>(
-      S->flag_list, S->nflag, ctx->rec_id, g, ctx->xy, ctx->heading, ctx->goal, ctx->cell, ctx->ocls,
-      ctx->D, S->fex, ctx->prm.beta, tb.own, tb.dirdot, choice);
+  fb<<<nsm > 0 ? nsm : 1, kFbThreads, smem, st>>>(
+      S->fb_flag, ctx->rec_id, nbins, g, ctx->xy, ctx->bin_start, ctx->rec, ctx->CT, SP, TS, ctx->Fs,
+      S->fb_dd, S->fb_info, ctx->prm.beta, tb.own, tb.dirdot, choice);
 }
 
 void round_params(sfm_surrogate* S) {
   k_round_bf16<<<cdiv(kNParams, 256), 256, 0, S->stream>>>(S->p, S->pq, kNParams);
-  k_pack_w1<<<cdiv(32 * kC1K, 256), 256, 0, S->stream>>>(S->pq + kOffW[0], S->wt1);
+  k_pack_w1<<<cdiv(5 * 32 * 16, 256), 256, 0, S->stream>>>(S->pq + kOffW[0], S->wt1);
   k_pack_w3<<<cdiv(9 * 32 * 32, 256), 256, 0, S->stream>>>(S->pq + kOffW[1], S->wt2);
   k_pack_w3<<<cdiv(9 * 32 * 32, 256), 256, 0, S->stream>>>(S->pq + kOffW[2], S->wt3);
+  k_pack_w4<<<cdiv(9 * 8 * 32, 256), 256, 0, S->stream>>>(S->pq + kOffW[3], S->wt4);
 }
 
 }  // namespace
@@ -1420,6 +1399,7 @@ sfm_status sfm_surrogate_create(const sfm_surrogate_cfg* cfg, void* stream, sfm_
       (st = salloc(S, &S->wt2, 9 * 32 * 32)) != SFM_OK ||
       (st = salloc(S, &S->fb_dev, 2)) != SFM_OK || (st = salloc(S, &S->nflag, 1)) != SFM_OK ||
       (st = salloc(S, &S->wt3, 9 * 32 * 32)) != SFM_OK ||
+      (st = salloc(S, &S->wt4, 9 * 8 * 32)) != SFM_OK ||
       (st = salloc(S, &S->cnt, 2)) != SFM_OK)
     return bail(st);
   cudaMemsetAsync(S->p, 0, kNParams * sizeof(float), S->stream);
