@@ -782,7 +782,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="floor",
-                    choices=["floor", "floor-small", "corridor", "room", "batch", "batch-small",
+                    choices=["floor", "floor-small", "floor-mid", "corridor", "room", "batch",
+                             "batch-small",
                              "surrogate", "surrogate-eval", "surrogate-eval-small", "surrogate-eval-mid",
                              "paper-windows", "paper-periods",
                              "paper-sizes"])

@@ -132,22 +132,25 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 __device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;\n" ::); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::); }
 
-constexpr int kC3In = (kTcRows + 2) * (kTcCols + 2) * kTcPad;  // input tile, BF16 elements
-constexpr int kC3W = 9 * 32 * kTcPad;                           // weights, BF16 elements
-constexpr size_t kC3Smem = (size_t)(kC3W + 2 * kC3In) * 2;
-constexpr int kC3CtasPerSm = 4;
+// input tile of a CTA computing 4 MT output rows, and the shared memory of
+// weights plus two input buffers (BF16 elements / bytes)
+__host__ __device__ constexpr int conv3_in_elems(int MT) { return (4 * MT + 2) * (kTcCols + 2) * kTcPad; }
+constexpr int kC3W = 9 * 32 * kTcPad;
+constexpr size_t conv3_smem(int MT) { return (size_t)(kC3W + 2 * conv3_in_elems(MT)) * 2; }
 
 // NT n8 tiles of output channels: 4 (32 -> 32, ReLU, BF16 out) or 1 for
 // layer 4 (32 -> 1: weights of output 0 in row 0 of the n8 tile, rows 1-7
-// zero; no activation, FP32 out in yout).
-template <int NT>
-__global__ void __launch_bounds__(128)
+// zero; no activation, FP32 out in yout).  MT m16 tiles (output rows) per
+// warp: a CTA computes 4 MT rows x 16 pixels.
+template <int NT, int MT>
+__global__ void __launch_bounds__(128, MT == 4 ? 3 : 4)
     k_conv3_tc(const bf16* __restrict__ in, int Hin, int Win, const bf16* __restrict__ Wt,
                const float* __restrict__ b, bf16* __restrict__ out, float* __restrict__ yout) {
   extern __shared__ __align__(16) bf16 sm3[];
   bf16* sW = sm3;
   const int Hout = Hin - 2, Wout = Win - 2;
-  const int ntx = (Wout + kTcCols - 1) / kTcCols, ntiles = ntx * ((Hout + kTcRows - 1) / kTcRows);
+  constexpr int R = 4 * MT, IN = conv3_in_elems(MT);
+  const int ntx = (Wout + kTcCols - 1) / kTcCols, ntiles = ntx * ((Hout + R - 1) / R);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint32_t sW0 = (uint32_t)__cvta_generic_to_shared(sW);
   const uint32_t sIn0 = sW0 + (uint32_t)kC3W * 2;
@@ -159,9 +162,9 @@ __global__ void __launch_bounds__(128)
   // input tile t (with a 1-pixel halo on the right and bottom) into buffer bi;
   // pixels outside the image are zeros
   auto fetch = [&](int t, int bi) {
-    const int x0 = (t % ntx) * kTcCols, y0 = (t / ntx) * kTcRows;
-    const uint32_t base = sIn0 + (uint32_t)(bi * kC3In) * 2;
-    for (int i = tid; i < (kTcRows + 2) * (kTcCols + 2) * 4; i += blockDim.x) {
+    const int x0 = (t % ntx) * kTcCols, y0 = (t / ntx) * R;
+    const uint32_t base = sIn0 + (uint32_t)(bi * IN) * 2;
+    for (int i = tid; i < (R + 2) * (kTcCols + 2) * 4; i += blockDim.x) {
       const int q = i & 3, p = i >> 2, px = p % (kTcCols + 2), py = p / (kTcCols + 2);
       const int gy = y0 + py, gx = x0 + px;
       const uint32_t dst = base + (uint32_t)(p * kTcPad + q * 8) * 2;
@@ -184,10 +187,10 @@ __global__ void __launch_bounds__(128)
     cp_async_commit();
     cp_async_wait_prev();
     __syncthreads();
-    const uint32_t sIn = sIn0 + (uint32_t)(bi * kC3In) * 2;
-    float acc[2][NT][4];
+    const uint32_t sIn = sIn0 + (uint32_t)(bi * IN) * 2;
+    float acc[MT][NT][4];
 #pragma unroll
-    for (int mt = 0; mt < 2; ++mt)
+    for (int mt = 0; mt < MT; ++mt)
 #pragma unroll
       for (int nt = 0; nt < NT; ++nt)
 #pragma unroll
@@ -212,8 +215,8 @@ __global__ void __launch_bounds__(128)
           ldsm_x2(addr, bw[0][0], bw[0][1]);
         }
 #pragma unroll
-        for (int mt = 0; mt < 2; ++mt) {
-          const int py = 2 * warp + mt + ky, px = a_row + kx;
+        for (int mt = 0; mt < MT; ++mt) {
+          const int py = MT * warp + mt + ky, px = a_row + kx;
           const uint32_t addr =
               sIn + (uint32_t)(((py * (kTcCols + 2) + px) * kTcPad + kb * 16 + a_col) * 2);
           uint32_t a0, a1, a2, a3;
@@ -226,10 +229,10 @@ __global__ void __launch_bounds__(128)
     // epilogue: accumulator (row g = lane/4 and g+8, column pair 2*(lane%4))
     // of each m16 x n8 tile; bias, then ReLU and BF16 (NT 4) or channel 0 in
     // FP32 (NT 1)
-    const int x0 = (t % ntx) * kTcCols, y0 = (t / ntx) * kTcRows;
+    const int x0 = (t % ntx) * kTcCols, y0 = (t / ntx) * R;
 #pragma unroll
-    for (int mt = 0; mt < 2; ++mt) {
-      const int y = y0 + 2 * warp + mt;
+    for (int mt = 0; mt < MT; ++mt) {
+      const int y = y0 + MT * warp + mt;
 #pragma unroll
       for (int half = 0; half < 2; ++half) {
         const int x = x0 + g + 8 * half;
@@ -626,6 +629,46 @@ __global__ void k_coarse_in(Geo g, const uint8_t* __restrict__ ocls, int s, int 
   X[(size_t)idx * 3 + 2] = __float2bfloat16(hy * inv);
 }
 
+// The same inputs from the binned records, for coarsenings that divide the
+// bin side: a cell lies inside one bin, whose records are in row-major order,
+// so the cell's pedestrians are summed in the order of the grid scan above.
+// Reads the bins' records (a few MB) instead of the whole class grid.
+__global__ void k_coarse_in_rec(Geo g, const int32_t* __restrict__ bin_start,
+                                const uint32_t* __restrict__ rec, int s, int Hc, int Wc,
+                                bf16* __restrict__ X) {
+  const int Wp = Wc + 2 * kHalo, Hp = Hc + 2 * kHalo;
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= Wp * Hp) return;
+  int ci = idx / Wp - kHalo, cj = idx % Wp - kHalo;
+  float n = 0.f, hx = 0.f, hy = 0.f;
+  bool ok = true;
+  if (ci < 0 || ci >= Hc) {
+    if (g.py) ci = (ci + Hc) % Hc; else ok = false;
+  }
+  if (cj < 0 || cj >= Wc) {
+    if (g.px) cj = (cj + Wc) % Wc; else ok = false;
+  }
+  if (ok) {
+    const int x0 = cj * s, y0 = ci * s;
+    const int b = (y0 / kBin) * g.nbx + x0 / kBin;
+    const uint32_t cx0 = (uint32_t)(x0 % kBin), cy0 = (uint32_t)(y0 % kBin);
+    const int e = bin_start[b + 1];
+    for (int k = bin_start[b]; k < e; ++k) {
+      const uint32_t rc = rec[k];
+      if ((rc & 0xffu) - cx0 < (uint32_t)s && ((rc >> 8) & 0xffu) - cy0 < (uint32_t)s) {
+        const int cls = (int)((rc >> 16) & 0xfu);
+        n += 1.f;
+        hx += c_hx[cls];
+        hy += c_hy[cls];
+      }
+    }
+  }
+  const float inv = 1.f / (float)(s * s);
+  X[(size_t)idx * 3 + 0] = __float2bfloat16(n * inv);
+  X[(size_t)idx * 3 + 1] = __float2bfloat16(hx * inv);
+  X[(size_t)idx * 3 + 2] = __float2bfloat16(hy * inv);
+}
+
 // T[i][j] = mean over the cell of (F - Fnear) / scale: the far part of the
 // exact field (Fnear holds the static field plus the near pedestrian part).
 __global__ void k_targets(const float* __restrict__ F, const float* __restrict__ Fnear, int W,
@@ -833,7 +876,9 @@ __global__ void k_sur_decide(const int32_t* __restrict__ rec_id, const int32_t* 
 // subsequence of the box's, in the same order, so each sum holds the exact
 // gather's terms in its order, bit for bit (its other terms are zero pads).
 // With a wide table stride an out-of-reach candidate reads a zero pad, so
-// only NARROW tests each candidate.  The class tables are staged in shared
+// only the narrow stride tests each candidate; the stride is a template
+// parameter and each record's mirror signs pick one of four unrolled reads
+// with immediate offsets (warp-uniform: every lane visits the same record).  The class tables are staged in shared
 // memory as for the gather (one CTA of 1024 threads per SM).  Each listed
 // pedestrian is then decided again with the exact path's energy on these
 // values, from the guidance distances, admissibility, heading and goal that
@@ -841,11 +886,21 @@ __global__ void k_sur_decide(const int32_t* __restrict__ rec_id, const int32_t* 
 // are never used).
 constexpr int kFbThreads = 1024;
 
-template <bool NARROW>
+// acc[k] += the class-table entry of candidate k = (cx, cy) at p + SY cy SP
+// + SX cx (compile-time offsets; out-of-reach candidates read zero pads)
+template <int SP, int SX, int SY>
+__device__ __forceinline__ void add_candidates(const float* __restrict__ p, float (&acc)[9]) {
+#pragma unroll
+  for (int k = 0; k < 9; ++k) acc[k] += p[SY * (move_dy(k) + 1) * SP + SX * (move_dx(k) + 1)];
+}
+
+constexpr int kFbRunBins = 8;  // widest run of bins whose pedestrians share one walk
+
+template <int SP>
 __global__ void __launch_bounds__(kFbThreads, 1)
     k_sur_fallback(const uint8_t* __restrict__ fb_flag, const int32_t* __restrict__ rec_id, int nbins,
                    Geo g, const int2* __restrict__ xy, const int32_t* __restrict__ bin_start,
-                   const uint32_t* __restrict__ rec, const float* __restrict__ CT, int SP, int TS,
+                   const uint32_t* __restrict__ rec, const float* __restrict__ CT, int TS,
                    const float* __restrict__ Fs, const int32_t* __restrict__ fb_dd,
                    const uint32_t* __restrict__ fb_info, float beta, const float* __restrict__ own,
                    const float* __restrict__ dirdot, uint8_t* __restrict__ choice) {
@@ -863,36 +918,59 @@ __global__ void __launch_bounds__(kFbThreads, 1)
     unsigned todo = __ballot_sync(0xffffffffu, fl);
     if (!todo) continue;
     const int2 q = fl ? xy[rec_id[i]] : make_int2(0, 0);
-    const int brow = q.y / kBin;
+    const int brow = q.y / kBin, bcol = q.x / kBin;
     float acc[9];
 #pragma unroll
     for (int k = 0; k < 9; ++k) acc[k] = 0.f;
     while (todo) {
-      // the listed lanes of the first remaining bin row (bin order keeps them contiguous)
-      const int row = __shfl_sync(0xffffffffu, brow, __ffs(todo) - 1);
-      const bool mine = ((todo >> lane) & 1u) && brow == row;
+      // the listed lanes of the first remaining bin row within kFbRunBins bins
+      // of its first listed lane (bin order keeps them contiguous)
+      const int lead = __ffs(todo) - 1;
+      const int row = __shfl_sync(0xffffffffu, brow, lead), col0 = __shfl_sync(0xffffffffu, bcol, lead);
+      const bool mine = ((todo >> lane) & 1u) && brow == row && bcol - col0 < kFbRunBins;
       todo &= ~__ballot_sync(0xffffffffu, mine);
       const int xmin = __reduce_min_sync(0xffffffffu, mine ? q.x : INT_MAX);
       const int xmax = __reduce_max_sync(0xffffffffu, mine ? q.x : INT_MIN);
       const int ymin = __reduce_min_sync(0xffffffffu, mine ? q.y : INT_MAX);
       const int ymax = __reduce_max_sync(0xffffffffu, mine ? q.y : INT_MIN);
-      // box of the candidate blocks, and this lane's block origin inside it
+      // box of the candidate blocks (at most 8 bins + 2 su wide, a bin + 2
+      // high), this lane's block origin inside it, and the lane's part of a
+      // table address (for mirror signs sx, sy: sy oy SP + sx ox)
       const int x0 = xmin - 1, y0 = ymin - 1, ox = q.x - xmin, oy = q.y - ymin;
+      const int lox = ox - r, loy = oy - r, span = 2 * r + 2;
+      // item: x = the record's part of a table address (class table, row and
+      // column of candidate (0, 0)), y = its box coordinates + 64 (11 bits
+      // each) and its mirror bits
       walk_records_box(
           g, bin_start, rec, scr, lane, x0, y0, xmax - xmin + 3, ymax - ymin + 3,
-          [](int rx, int ry, int cls) { return make_int2(rx, ry * 16 + cls); },
+          [&](int rx, int ry, int cls) {
+            const int sx = class_sx(cls), sy = class_sy(cls);
+            return make_int2(class_table(cls) * TS + (r + kFieldPad - sy * ry) * SP + r - sx * rx,
+                             (rx + 64) | (ry + 64) << 11 | (sx < 0 ? 1 : 0) << 22 |
+                                 (sy < 0 ? 1 : 0) << 23);
+          },
           [&](const int2 it) {
-            const int rx = it.x - ox, ry = (it.y >> 4) - oy, cls = it.y & 15;
-            if (mine && rx >= -r && rx <= 2 + r && ry >= -r && ry <= 2 + r) {
-              const int sx = class_sx(cls), sy = class_sy(cls);
-              // entry of candidate (cx, cy): offset (cx - rx, cy - ry) from the record
-              const float* p =
-                  sT + class_table(cls) * TS + (r + kFieldPad - sy * ry) * SP + r - sx * rx;
+            const int rxu = (it.y & 2047) - 64, ryu = ((it.y >> 11) & 2047) - 64;
+            if (mine && (unsigned)(rxu - lox) <= (unsigned)span && (unsigned)(ryu - loy) <= (unsigned)span) {
+              const int m = (it.y >> 22) & 3;
+              const float* p = sT + it.x + ((m & 2) ? -oy * SP : oy * SP) + ((m & 1) ? -ox : ox);
+              if constexpr (SP == kNarrowStride) {
+                // narrow stride: fewer than 2 zero columns, so test each candidate
+                const int rx = rxu - ox, ry = ryu - oy, sx = (m & 1) ? -1 : 1, sy = (m & 2) ? -1 : 1;
 #pragma unroll
-              for (int k = 0; k < 9; ++k) {
-                const int cx = move_dx(k) + 1, cy = move_dy(k) + 1;
-                if (!NARROW || (cx - rx >= -r && cx - rx <= r && cy - ry >= -r && cy - ry <= r))
-                  acc[k] += p[sy * cy * SP + sx * cx];
+                for (int k = 0; k < 9; ++k) {
+                  const int cx = move_dx(k) + 1, cy = move_dy(k) + 1;
+                  if (cx - rx >= -r && cx - rx <= r && cy - ry >= -r && cy - ry <= r)
+                    acc[k] += p[sy * cy * SP + sx * cx];
+                }
+              } else if (m == 0) {
+                add_candidates<SP, 1, 1>(p, acc);
+              } else if (m == 1) {
+                add_candidates<SP, -1, 1>(p, acc);
+              } else if (m == 2) {
+                add_candidates<SP, 1, -1>(p, acc);
+              } else {
+                add_candidates<SP, -1, -1>(p, acc);
               }
             }
           });
@@ -1128,14 +1206,21 @@ void conv3_tc(const bf16* in, int Hin, int Win, const bf16* wt, const float* b, 
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     if (nsm <= 0) nsm = 1;
   }
-  const int ntiles = cdiv(Win - 2, kTcCols) * cdiv(Hin - 2, kTcRows);
-  const int grid = std::max(1, std::min(ntiles, nsm * kC3CtasPerSm));
+  // 32 -> 32: 4 m16 tiles a warp (16 rows a CTA, 3 CTAs an SM); 32 -> 1: 2
+  // (8 rows, 4 CTAs)
+  constexpr int MT4 = 4, MT1 = 2;
   if (yout) {
-    cudaFuncSetAttribute(k_conv3_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kC3Smem);
-    k_conv3_tc<1><<<grid, 128, kC3Smem, s>>>(in, Hin, Win, wt, b, nullptr, yout);
+    const int ntiles = cdiv(Win - 2, kTcCols) * cdiv(Hin - 2, 4 * MT1);
+    const int grid = std::max(1, std::min(ntiles, nsm * 4));
+    cudaFuncSetAttribute(k_conv3_tc<1, MT1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)conv3_smem(MT1));
+    k_conv3_tc<1, MT1><<<grid, 128, conv3_smem(MT1), s>>>(in, Hin, Win, wt, b, nullptr, yout);
   } else {
-    cudaFuncSetAttribute(k_conv3_tc<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kC3Smem);
-    k_conv3_tc<4><<<grid, 128, kC3Smem, s>>>(in, Hin, Win, wt, b, out, nullptr);
+    const int ntiles = cdiv(Win - 2, kTcCols) * cdiv(Hin - 2, 4 * MT4);
+    const int grid = std::max(1, std::min(ntiles, nsm * 3));
+    cudaFuncSetAttribute(k_conv3_tc<4, MT4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)conv3_smem(MT4));
+    k_conv3_tc<4, MT4><<<grid, 128, conv3_smem(MT4), s>>>(in, Hin, Win, wt, b, out, nullptr);
   }
 }
 
@@ -1286,10 +1371,15 @@ void near_field(sfm_surrogate* S, sfm_ctx* ctx) {
                ctx->stream);
 }
 
+// the network's inputs for ctx's current state (bins must be current)
 void coarse_inputs(sfm_surrogate* S, sfm_ctx* ctx) {
   const int Hp = S->Hc + 2 * kHalo, Wp = S->Wc + 2 * kHalo;
-  k_coarse_in<<<cdiv(Hp * Wp, 256), 256, 0, ctx->stream>>>(ctx->geo, ctx->ocls, S->cfg.coarsen,
-                                                            S->Hc, S->Wc, S->X);
+  if (kBin % S->cfg.coarsen == 0)
+    k_coarse_in_rec<<<cdiv(Hp * Wp, 256), 256, 0, ctx->stream>>>(
+        ctx->geo, ctx->bin_start, ctx->rec, S->cfg.coarsen, S->Hc, S->Wc, S->X);
+  else
+    k_coarse_in<<<cdiv(Hp * Wp, 256), 256, 0, ctx->stream>>>(ctx->geo, ctx->ocls, S->cfg.coarsen,
+                                                              S->Hc, S->Wc, S->X);
 }
 
 FarPart far_part(const sfm_surrogate* S) {
@@ -1352,13 +1442,24 @@ void surrogate_decide(sfm_surrogate* S, sfm_ctx* ctx, uint8_t* choice, const uin
   const int TS = (2 * g.r + 1 + 2 * kFieldPadRows) * SP;
   const size_t smem = (kTableGuard + 4 * (size_t)TS) * sizeof(float) +
                       (size_t)kFbThreads / 32 * 32 * sizeof(int2);
-  auto fb = SP == kNarrowStride ? k_sur_fallback<true> : k_sur_fallback<false>;
+  void (*fb)(const uint8_t*, const int32_t*, int, Geo, const int2*, const int32_t*, const uint32_t*,
+             const float*, int, const float*, const int32_t*, const uint32_t*, float, const float*,
+             const float*, uint8_t*);
+  switch (SP) {
+    case 34: fb = k_sur_fallback<34>; break;
+    case 50: fb = k_sur_fallback<50>; break;
+    case 66: fb = k_sur_fallback<66>; break;
+    case 82: fb = k_sur_fallback<82>; break;
+    case 98: fb = k_sur_fallback<98>; break;
+    case 114: fb = k_sur_fallback<114>; break;
+    default: fb = k_sur_fallback<kNarrowStride>; break;
+  }
   cudaFuncSetAttribute(fb, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int dev = 0, nsm = 1;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   fb<<<nsm > 0 ? nsm : 1, kFbThreads, smem, st>>>(
-      S->fb_flag, ctx->rec_id, nbins, g, ctx->xy, ctx->bin_start, ctx->rec, ctx->CT, SP, TS, ctx->Fs,
+      S->fb_flag, ctx->rec_id, nbins, g, ctx->xy, ctx->bin_start, ctx->rec, ctx->CT, TS, ctx->Fs,
       S->fb_dd, S->fb_info, ctx->prm.beta, tb.own, tb.dirdot, choice);
 }
 
