@@ -343,6 +343,15 @@ sfm_status sfm_surrogate_get_params(sfm_surrogate* sur, float* params);
  * mean((Y-T)^2) and its gradients (host, nparams floats, public order). */
 sfm_status sfm_surrogate_grad(sfm_surrogate* sur, int32_t Hin, int32_t Win, const float* X,
                               const float* T, float* loss, float* grads);
+/* Forward pass alone on a given input: X as for sfm_surrogate_grad, Y (host,
+ * [Hin-10][Win-10]) the network's output.  tcgen05 != 0: the 3x3 32 -> 32
+ * layers on the tcgen05 kernel, 0: on the mma.sync kernel that every other
+ * surrogate call uses (it is the faster of the two at 32 channels).
+ * SFM_ETIMEOUT: a tcgen05 convolution's bounded wait ran out; from then on
+ * the surrogate runs those layers on mma.sync (every synchronising
+ * surrogate call reports such a timeout once). */
+sfm_status sfm_surrogate_forward(sfm_surrogate* sur, int32_t Hin, int32_t Win, const float* X,
+                                 float* Y, int32_t tcgen05);
 /* iters training steps on ctx: each takes the exact field of ctx's current
  * state, one Adam step on the whole coarse lattice, then ticks ctx once so
  * the next step sees a new crowd.  loss_curve: iters floats (host) or NULL. */

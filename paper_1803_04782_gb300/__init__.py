@@ -38,6 +38,7 @@ EXPORTS = [
     "sfm_batch_autotune", "sfm_batch_test_missing_ctas", "sfm_surrogate_nparams",
     "sfm_surrogate_create", "sfm_surrogate_destroy", "sfm_surrogate_last_error",
     "sfm_surrogate_set_params", "sfm_surrogate_get_params", "sfm_surrogate_grad",
+    "sfm_surrogate_forward",
     "sfm_surrogate_train", "sfm_surrogate_field", "sfm_surrogate_eval", "sfm_surrogate_set_delta",
     "sfm_surrogate_calibrate", "sfm_surrogate_step", "sfm_surrogate_counts",
 ]
@@ -139,6 +140,7 @@ def lib():
             "sfm_surrogate_train": (C.c_int, [P, P, I32, P]),
             "sfm_surrogate_field": (C.c_int, [P, P, P, I32]),
             "sfm_surrogate_eval": (C.c_int, [P, P, C.POINTER(SurrogateReport)]),
+            "sfm_surrogate_forward": (C.c_int, [P, I32, I32, P, P, I32]),
             "sfm_surrogate_set_delta": (C.c_int, [P, C.c_float]),
             "sfm_surrogate_calibrate": (C.c_int, [P, P, C.c_double, P]),
             "sfm_surrogate_step": (C.c_int, [P, P, I32]),
@@ -679,6 +681,17 @@ class Surrogate:
                                                  T.ctypes.data_as(C.c_void_p), C.byref(loss),
                                                  g.ctypes.data_as(C.c_void_p)))
         return float(loss.value), g
+
+    def forward(self, X, tcgen05=True):
+        """The network's output for a channel-planar input X [3][Hin][Win]
+        (rounded to BF16), with the 3x3 32 -> 32 layers on the tcgen05 kernel
+        or (tcgen05=False) on the mma.sync kernel the surrogate's ticks use."""
+        X = np.ascontiguousarray(X, np.float32)
+        Y = np.empty((X.shape[1] - 10, X.shape[2] - 10), np.float32)
+        _scheck(self.h, lib().sfm_surrogate_forward(self.h, X.shape[1], X.shape[2],
+                                                    X.ctypes.data_as(C.c_void_p),
+                                                    Y.ctypes.data_as(C.c_void_p), int(bool(tcgen05))))
+        return Y
 
     def train(self, sim, iters):
         curve = np.zeros(int(iters), np.float32)

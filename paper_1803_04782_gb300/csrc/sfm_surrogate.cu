@@ -257,6 +257,224 @@ __global__ void __launch_bounds__(128, MT == 4 ? 3 : 4)
   cp_async_wait_all();
 }
 
+// ------------------------------- 5th-generation tensor cores: 3x3, 32 -> 32
+// The 32 -> 32 layers as an implicit GEMM on tcgen05: a CTA computes 2
+// output rows x 128 pixels; each row is one M = 128, N = 32 accumulator in
+// TMEM (2 x 32 columns), summed over K = 9 kernel offsets x 2 blocks of 16
+// channels by 18 MMAs (BF16 operands from shared memory, FP32 accumulation).
+// Operands sit in the no-swizzle K-major core-matrix layout (8 rows x 16
+// bytes each): the input tile as [input row][channel group of 8][pixel][8
+// channels], so the A operand of kernel offset (ky, kx) for output row j
+// starts at input row j + ky, pixel kx (K-adjacent core matrices 130 x 16
+// bytes apart, M-adjacent ones 128 bytes); the weights as [ky kx][block of
+// 16][half][out][8 in].  One thread issues the MMAs and commits them to an
+// mbarrier; the four warps then read their 32 TMEM lanes (pixels) and store
+// bias + ReLU in BF16.  Persistent CTAs walk the tiles with the grid's
+// stride: 4 per SM with one input buffer each (kUmStages 1), or 2 per SM that
+// copy the next tile's input with cp.async into a second buffer while the
+// current one is multiplied and stored (kUmStages 2).  Every wait is
+// bounded: on a timeout the kernel raises an error flag, frees its TMEM and
+// returns.  Measured on the 16384^2 floor's 2054^2 images: 235 us a layer
+// (one buffer, 4 CTAs), 267 us (two buffers, 2 CTAs) against 207 us for the
+// mma.sync kernel, with the tensor pipe 13-14 % busy: with N = 32 an MMA is
+// small and each tile's copy, MMAs and store run one after another in a CTA,
+// so the layers stay on mma.sync unless a caller asks for this kernel.  (A
+// warp-specialised pipeline -- copy warp, MMA warp, store warps over a ring
+// of buffers and two accumulators -- is what it would take to win.)
+constexpr int kUmRows = 2, kUmCols = 128, kUmInPx = kUmCols + 2, kUmInRows = kUmRows + 2;
+constexpr int kUmA = kUmInRows * 4 * kUmInPx * 16;  // bytes of one input tile buffer
+constexpr int kUmB = 9 * 2 * 2 * 32 * 16;           // bytes of the weights
+constexpr int kUmTmemCols = 64;                     // kUmRows x 32, a power of 2 >= 32
+constexpr int kUmStages = 1;                                       // input buffers a CTA
+constexpr size_t kUmSmem = (size_t)kUmStages * kUmA + kUmB + 16;  // + mbarrier and TMEM address
+constexpr int kUmCtasPerSm = kUmStages == 1 ? 4 : 2;
+constexpr uint32_t kUmIdesc =                             // kind::f16 instruction descriptor
+    (1u << 4) |                                           // D: FP32
+    (1u << 7) | (1u << 10) |                              // A, B: BF16 (both K-major)
+    ((uint32_t)(32 >> 3) << 17) |                         // N = 32
+    ((uint32_t)(128 >> 4) << 24);                         // M = 128
+static_assert(kUmA % 16 == 0 && kUmB % 16 == 0, "operands must stay 16-byte aligned");
+static_assert(kUmRows * 32 <= kUmTmemCols, "accumulators exceed the TMEM allocation");
+
+// shared-memory matrix descriptor, no swizzle: start, K-direction (leading)
+// and M/N-direction (stride) byte offsets between core matrices
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)(lbo >> 4) << 16) |
+         ((uint64_t)(sbo >> 4) << 32) | (1ull << 46);
+}
+
+__device__ __forceinline__ void umma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                         uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
+
+// bounded wait for the mbarrier phase `parity`; false on a timeout
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
+  for (int it = 0; it < (1 << 22); ++it) {
+    uint32_t done = 0;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(done)
+        : "r"(mbar), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+// 16-byte copy into shared memory, or 16 zero bytes when !valid
+__device__ __forceinline__ void cp_async16_or_zero(uint32_t dst, const void* src, bool valid) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src),
+               "r"(valid ? 16 : 0));
+}
+
+__global__ void __launch_bounds__(128, kUmCtasPerSm)
+    k_conv3_umma(const bf16* __restrict__ in, int Hin, int Win, const bf16* __restrict__ Wu,
+                 const float* __restrict__ b, bf16* __restrict__ out, int* __restrict__ err) {
+  extern __shared__ __align__(128) uint8_t smu[];
+  const uint32_t sA0 = (uint32_t)__cvta_generic_to_shared(smu);
+  const uint32_t sB = sA0 + kUmStages * kUmA, mbar = sB + kUmB, tslot = mbar + 8;
+  const int Hout = Hin - 2, Wout = Win - 2;
+  const int ntx = (Wout + kUmCols - 1) / kUmCols, ntiles = ntx * ((Hout + kUmRows - 1) / kUmRows);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  // weights once per CTA (already in the core-matrix layout, 16-byte chunks)
+  for (int i = tid; i < kUmB / 16; i += blockDim.x)
+    reinterpret_cast<uint4*>(smu + kUmStages * kUmA)[i] = reinterpret_cast<const uint4*>(Wu)[i];
+  if (tid == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mbar));
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(tslot),
+                 "r"(kUmTmemCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::);
+  }
+  // input tile t into buffer bi: chunk (row, pixel, group) of 8 channels ->
+  // [row][group][pixel], zeros outside the image
+  auto fetch = [&](int t, int bi) {
+    const int x0 = (t % ntx) * kUmCols, y0 = (t / ntx) * kUmRows;
+    const uint32_t base = sA0 + (uint32_t)(bi * kUmA);
+    for (int i = tid; i < kUmInRows * kUmInPx * 4; i += blockDim.x) {
+      const int cg = i & 3, px = (i >> 2) % kUmInPx, r = (i >> 2) / kUmInPx;
+      const int gy = y0 + r, gx = x0 + px;
+      const bool v = gy < Hin && gx < Win;
+      cp_async16_or_zero(base + (uint32_t)(((r * 4 + cg) * kUmInPx + px) * 16),
+                         v ? in + ((size_t)gy * Win + gx) * 32 + cg * 8 : in, v);
+    }
+  };
+  int t = blockIdx.x, bi = 0;
+  if (kUmStages == 2 && t < ntiles) fetch(t, 0);
+  cp_async_commit();
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  uint32_t tmem;
+  asm volatile("ld.shared.u32 %0, [%1];\n" : "=r"(tmem) : "r"(tslot));
+  uint32_t phase = 0;
+  bool failed = false;
+  for (; t < ntiles; t += gridDim.x, bi ^= (kUmStages - 1)) {
+    if (kUmStages == 2) {
+      // the next tile's copies run while this one is multiplied and stored
+      if (t + (int)gridDim.x < ntiles) fetch(t + gridDim.x, bi ^ 1);
+      cp_async_commit();
+      cp_async_wait_prev();
+    } else {
+      fetch(t, 0);
+      cp_async_commit();
+      cp_async_wait_all();
+    }
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+      const uint32_t sA = sA0 + (uint32_t)(bi * kUmA);
+#pragma unroll 1
+      for (int j = 0; j < kUmRows; ++j)
+#pragma unroll 1
+        for (int kk = 0; kk < 9; ++kk) {
+          const int ky = kk / 3, kx = kk % 3;
+#pragma unroll
+          for (int kb = 0; kb < 2; ++kb) {
+            const uint64_t ad =
+                umma_desc(sA + (uint32_t)((((j + ky) * 4 + 2 * kb) * kUmInPx + kx) * 16), kUmInPx * 16, 128);
+            const uint64_t bd = umma_desc(sB + (uint32_t)((kk * 2 + kb) * 1024), 512, 128);
+            umma_f16(tmem + (uint32_t)(j * 32), ad, bd, kUmIdesc, (kk | kb) != 0);
+          }
+        }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(mbar)
+                   : "memory");
+    }
+    // one decision for the whole CTA, so every warp leaves the loop together
+    const bool ok = __syncthreads_and(mbar_wait(mbar, phase) ? 1 : 0) != 0;
+    phase ^= 1u;
+    if (!ok) {
+      failed = true;
+      break;
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    // epilogue: warp w holds TMEM lanes 32w .. 32w + 31 (pixels), row j in
+    // columns 32j .. 32j + 31 (channels)
+    const int x0 = (t % ntx) * kUmCols, y0 = (t / ntx) * kUmRows;
+    const int px = x0 + 32 * warp + lane;
+#pragma unroll 1
+    for (int j = 0; j < kUmRows; ++j) {
+      uint32_t v[32];
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+          "%11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, "
+          "%28, %29, %30, %31}, [%32];\n"
+          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+            "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+            "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]),
+            "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]),
+            "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+          : "r"(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(j * 32)));
+      asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+      const int y = y0 + j;
+      if (px < Wout && y < Hout) {
+        uint32_t o[16];
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+          const float a0 = fmaxf(__uint_as_float(v[2 * c]) + b[2 * c], 0.f);
+          const float a1 = fmaxf(__uint_as_float(v[2 * c + 1]) + b[2 * c + 1], 0.f);
+          const __nv_bfloat162 h = __floats2bfloat162_rn(a0, a1);
+          o[c] = *reinterpret_cast<const uint32_t*>(&h);
+        }
+        uint4* dst = reinterpret_cast<uint4*>(out + ((size_t)y * Wout + px) * 32);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) dst[q] = make_uint4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]);
+      }
+    }
+    // all TMEM reads done before the next tile's MMAs overwrite the accumulators
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+  }
+  cp_async_wait_all();
+  if (failed && tid == 0) atomicExch(err, 1);
+  // (after a timeout the MMAs in flight are waited for once more, bounded)
+  if (failed) mbar_wait(mbar, phase ^ 1u);
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kUmTmemCols));
+}
+
+// BF16 weights of a 3x3 32->32 layer in the tcgen05 operand layout:
+// [ky kx][block of 16 inputs][half][out][8 inputs], from the internal
+// [ky][kx][in][out] floats.
+__global__ void k_pack_wum(const float* __restrict__ w, bf16* __restrict__ wt) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 9 * 32 * 32) return;
+  const int e = i % 8, o = (i / 8) % 32, h = (i / 256) % 2, kb = (i / 512) % 2, kk = i / 1024;
+  const int c = kb * 16 + h * 8 + e;
+  wt[i] = __float2bfloat16(w[(kk * 32 + c) * 32 + o]);
+}
+
 // BF16 weights of a 3x3 32->32 layer for the tensor-core kernel:
 // [ky][kx][out][in] from the internal [ky][kx][in][out] floats.
 __global__ void k_pack_w3(const float* __restrict__ w, bf16* __restrict__ wt) {
@@ -1046,6 +1264,9 @@ struct sfm_surrogate {
   // parameters (internal layout), BF16-rounded copies, Adam state, gradients
   float *p = nullptr, *pq = nullptr, *m = nullptr, *v = nullptr, *g = nullptr;
   bf16 *wt1 = nullptr, *wt2 = nullptr, *wt3 = nullptr, *wt4 = nullptr;  // for the tensor cores
+  bf16 *wu2 = nullptr, *wu3 = nullptr;  // layers 2 and 3 in the tcgen05 operand layout
+  int* umma_err = nullptr;              // set by a tcgen05 convolution that timed out
+  bool use_umma = false;                // layers 2 and 3 on tcgen05 (else mma.sync, faster here)
   int adam_t = 0;
   // activations for an image of (Hc + 2 kHalo) x (Wc + 2 kHalo) coarse cells
   int Hc = 0, Wc = 0;
@@ -1224,8 +1445,25 @@ void conv3_tc(const bf16* in, int Hin, int Win, const bf16* wt, const float* b, 
   }
 }
 
+// 3x3 32 -> 32 layer on tcgen05 (persistent CTAs, 2 an SM)
+void conv3_umma(const bf16* in, int Hin, int Win, const bf16* wu, const float* b, bf16* out,
+                int* err, cudaStream_t s) {
+  static int nsm = 0;
+  if (!nsm) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (nsm <= 0) nsm = 1;
+  }
+  const int ntiles = cdiv(Win - 2, kUmCols) * cdiv(Hin - 2, kUmRows);
+  const int grid = std::max(1, std::min(ntiles, nsm * kUmCtasPerSm));
+  cudaFuncSetAttribute(k_conv3_umma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kUmSmem);
+  k_conv3_umma<<<grid, 128, kUmSmem, s>>>(in, Hin, Win, wu, b, out, err);
+}
+
 // forward of the whole padded image currently in S->X (all four layers on
-// the tensor cores, FP32 accumulation)
+// the tensor cores, FP32 accumulation; layers 2 and 3 on tcgen05 when
+// use_umma is on)
 void forward(sfm_surrogate* S, cudaStream_t s) {
   const int Hp = S->Hc + 2 * kHalo, Wp = S->Wc + 2 * kHalo;
   const float* q = S->pq;
@@ -1237,8 +1475,13 @@ void forward(sfm_surrogate* S, cudaStream_t s) {
     const int grid = std::max(1, std::min(ntiles, std::max(nsm, 1) * kC1CtasPerSm));
     k_conv1_tc<<<grid, 128, 0, s>>>(S->X, Hp, Wp, S->wt1, q + kOffB[0], S->A1);
   }
-  conv3_tc(S->A1, Hp - 4, Wp - 4, S->wt2, q + kOffB[1], S->A2, s);
-  conv3_tc(S->A2, Hp - 6, Wp - 6, S->wt3, q + kOffB[2], S->A3, s);
+  if (S->use_umma) {
+    conv3_umma(S->A1, Hp - 4, Wp - 4, S->wu2, q + kOffB[1], S->A2, S->umma_err, s);
+    conv3_umma(S->A2, Hp - 6, Wp - 6, S->wu3, q + kOffB[2], S->A3, S->umma_err, s);
+  } else {
+    conv3_tc(S->A1, Hp - 4, Wp - 4, S->wt2, q + kOffB[1], S->A2, s);
+    conv3_tc(S->A2, Hp - 6, Wp - 6, S->wt3, q + kOffB[2], S->A3, s);
+  }
   conv3_tc(S->A3, Hp - 8, Wp - 8, S->wt4, q + kOffB[3], nullptr, s, S->Y);
 }
 
@@ -1469,6 +1712,32 @@ void round_params(sfm_surrogate* S) {
   k_pack_w3<<<cdiv(9 * 32 * 32, 256), 256, 0, S->stream>>>(S->pq + kOffW[1], S->wt2);
   k_pack_w3<<<cdiv(9 * 32 * 32, 256), 256, 0, S->stream>>>(S->pq + kOffW[2], S->wt3);
   k_pack_w4<<<cdiv(9 * 8 * 32, 256), 256, 0, S->stream>>>(S->pq + kOffW[3], S->wt4);
+  k_pack_wum<<<cdiv(9 * 32 * 32, 256), 256, 0, S->stream>>>(S->pq + kOffW[1], S->wu2);
+  k_pack_wum<<<cdiv(9 * 32 * 32, 256), 256, 0, S->stream>>>(S->pq + kOffW[2], S->wu3);
+}
+
+// Status of the tcgen05 convolutions (synchronising): a timeout switches
+// layers 2 and 3 to the mma.sync kernel for good and is reported once.
+sfm_status umma_check(sfm_surrogate* S) {
+  int h = 0;
+  SCU(cudaMemcpyAsync(&h, S->umma_err, sizeof(int), cudaMemcpyDeviceToHost, S->stream));
+  SCU(cudaStreamSynchronize(S->stream));
+  if (h) {
+    S->use_umma = false;
+    SCU(cudaMemsetAsync(S->umma_err, 0, sizeof(int), S->stream));
+    return sfail(S, SFM_ETIMEOUT, "a tcgen05 convolution timed out; layers 2-3 now run on mma.sync");
+  }
+  return SFM_OK;
+}
+
+// channel-planar FP32 image [3][Hin][Win] (host) into S->X (channel-last BF16)
+sfm_status upload_image(sfm_surrogate* S, int Hin, int Win, const float* X) {
+  std::vector<bf16> hx((size_t)Hin * Win * 3);
+  for (int c = 0; c < 3; ++c)
+    for (int i = 0; i < Hin * Win; ++i) hx[(size_t)i * 3 + c] = __float2bfloat16(X[(size_t)c * Hin * Win + i]);
+  SCU(cudaMemcpyAsync(S->X, hx.data(), hx.size() * sizeof(bf16), cudaMemcpyHostToDevice, S->stream));
+  SCU(cudaStreamSynchronize(S->stream));
+  return SFM_OK;
 }
 
 }  // namespace
@@ -1476,6 +1745,23 @@ void round_params(sfm_surrogate* S) {
 extern "C" {
 
 int32_t sfm_surrogate_nparams(void) { return kNParams; }
+
+sfm_status sfm_surrogate_forward(sfm_surrogate* S, int32_t Hin, int32_t Win, const float* X,
+                                 float* Y, int32_t tcgen05) {
+  if (!S || !X || !Y) return SFM_EINVAL;
+  if (Hin <= 2 * kHalo || Win <= 2 * kHalo) return sfail(S, SFM_EINVAL, "image too small");
+  const int Hc = Hin - 2 * kHalo, Wc = Win - 2 * kHalo;
+  STRY(ensure_image(S, Hc, Wc));
+  STRY(upload_image(S, Hin, Win, X));
+  const bool saved = S->use_umma;
+  S->use_umma = saved && tcgen05 != 0;
+  forward(S, S->stream);
+  S->use_umma = saved;
+  SCU(cudaMemcpyAsync(Y, S->Y, (size_t)Hc * Wc * sizeof(float), cudaMemcpyDeviceToHost, S->stream));
+  SCU(cudaStreamSynchronize(S->stream));
+  SCU(cudaGetLastError());
+  return umma_check(S);
+}
 
 sfm_status sfm_surrogate_create(const sfm_surrogate_cfg* cfg, void* stream, sfm_surrogate** out) {
   if (out) *out = nullptr;
@@ -1501,12 +1787,16 @@ sfm_status sfm_surrogate_create(const sfm_surrogate_cfg* cfg, void* stream, sfm_
       (st = salloc(S, &S->fb_dev, 2)) != SFM_OK || (st = salloc(S, &S->nflag, 1)) != SFM_OK ||
       (st = salloc(S, &S->wt3, 9 * 32 * 32)) != SFM_OK ||
       (st = salloc(S, &S->wt4, 9 * 8 * 32)) != SFM_OK ||
+      (st = salloc(S, &S->wu2, 9 * 32 * 32)) != SFM_OK ||
+      (st = salloc(S, &S->wu3, 9 * 32 * 32)) != SFM_OK ||
+      (st = salloc(S, &S->umma_err, 1)) != SFM_OK ||
       (st = salloc(S, &S->cnt, 2)) != SFM_OK)
     return bail(st);
   cudaMemsetAsync(S->p, 0, kNParams * sizeof(float), S->stream);
   cudaMemsetAsync(S->m, 0, kNParams * sizeof(float), S->stream);
   cudaMemsetAsync(S->v, 0, kNParams * sizeof(float), S->stream);
   cudaMemsetAsync(S->fb_dev, 0, 2 * sizeof(unsigned long long), S->stream);
+  cudaMemsetAsync(S->umma_err, 0, sizeof(int), S->stream);
   round_params(S);
   if (cudaStreamSynchronize(S->stream) != cudaSuccess) {
     S->err = "surrogate set-up failed";
@@ -1553,11 +1843,7 @@ sfm_status sfm_surrogate_grad(sfm_surrogate* S, int32_t Hin, int32_t Win, const 
   if (Hin <= 2 * kHalo || Win <= 2 * kHalo) return sfail(S, SFM_EINVAL, "image too small");
   const int Hc = Hin - 2 * kHalo, Wc = Win - 2 * kHalo;
   STRY(ensure_image(S, Hc, Wc));
-  // X given channel-planar [3][Hin][Win]; the network reads channel-last BF16
-  std::vector<bf16> hx((size_t)Hin * Win * 3);
-  for (int c = 0; c < 3; ++c)
-    for (int i = 0; i < Hin * Win; ++i) hx[(size_t)i * 3 + c] = __float2bfloat16(X[(size_t)c * Hin * Win + i]);
-  SCU(cudaMemcpyAsync(S->X, hx.data(), hx.size() * sizeof(bf16), cudaMemcpyHostToDevice, S->stream));
+  STRY(upload_image(S, Hin, Win, X));
   SCU(cudaMemcpyAsync(S->T, T, (size_t)Hc * Wc * sizeof(float), cudaMemcpyHostToDevice, S->stream));
   forward(S, S->stream);
   STRY(backward(S, loss, S->stream));
@@ -1568,7 +1854,7 @@ sfm_status sfm_surrogate_grad(sfm_surrogate* S, int32_t Hin, int32_t Win, const 
     to_public(in.data(), grads);
   }
   SCU(cudaStreamSynchronize(S->stream));
-  return SFM_OK;
+  return umma_check(S);
 }
 
 sfm_status sfm_surrogate_train(sfm_surrogate* S, sfm_ctx* ctx, int32_t iters, float* loss_curve) {
@@ -1606,7 +1892,7 @@ sfm_status sfm_surrogate_train(sfm_surrogate* S, sfm_ctx* ctx, int32_t iters, fl
   }
   SCU(cudaStreamSynchronize(st));
   SCU(cudaGetLastError());
-  return SFM_OK;
+  return umma_check(S);
 }
 
 // set-up shared by the calls below
@@ -1629,7 +1915,7 @@ sfm_status sfm_surrogate_field(sfm_surrogate* S, sfm_ctx* ctx, float* out, int32
                       on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ctx->stream));
   SCU(cudaStreamSynchronize(ctx->stream));
   SCU(cudaGetLastError());
-  return SFM_OK;
+  return umma_check(S);
 }
 
 sfm_status sfm_surrogate_set_delta(sfm_surrogate* S, float delta) {
@@ -1669,7 +1955,7 @@ sfm_status sfm_surrogate_calibrate(sfm_surrogate* S, sfm_ctx* ctx, double quanti
   }
   S->delta = d;
   if (delta_out) *delta_out = d;
-  return SFM_OK;
+  return umma_check(S);
 }
 
 sfm_status sfm_surrogate_step(sfm_surrogate* S, sfm_ctx* ctx, int32_t nsteps) {
@@ -1700,7 +1986,7 @@ sfm_status sfm_surrogate_counts(sfm_surrogate* S, int64_t* fallbacks, int64_t* d
   SCU(cudaStreamSynchronize(S->stream));
   if (fallbacks) *fallbacks = (int64_t)h[0];
   if (decided) *decided = (int64_t)h[1];
-  return SFM_OK;
+  return umma_check(S);
 }
 
 sfm_status sfm_surrogate_eval(sfm_surrogate* S, sfm_ctx* ctx, sfm_surrogate_report* rep) {
@@ -1770,7 +2056,7 @@ sfm_status sfm_surrogate_eval(sfm_surrogate* S, sfm_ctx* ctx, sfm_surrogate_repo
   rep->ms_surrogate_field = t_sf;
   rep->delta = S->delta;
   rep->decided = nrec;
-  return SFM_OK;
+  return umma_check(S);
 }
 
 }  // extern "C"

@@ -35,6 +35,28 @@ def _rounded_params(seed=0, scale=1.0):
     return [(bf16(W * scale), bf16(b)) for W, b in ps]
 
 
+@pytest.mark.parametrize("shape", [(30, 34), (157, 333)])
+def test_tcgen05_layers_match_the_mma_sync_layers_and_the_oracle(shape):
+    """The 3x3 32 -> 32 layers on tcgen05 against the same layers on mma.sync
+    (both sum in FP32 and round the activations to BF16, in different orders,
+    so a hidden activation may differ by one BF16 rounding), and the network's
+    output against the FP64 oracle from the same BF16 inputs and weights; the
+    larger image has ragged tiles in both directions."""
+    rng = np.random.default_rng(21)
+    params = _rounded_params(5, scale=0.5)
+    X = bf16(rng.random((3,) + shape) * 0.3)
+    with sfm.Surrogate(params=sfm.flatten_params(params)) as s:
+        Yu = s.forward(X, tcgen05=True)
+        Ym = s.forward(X, tcgen05=False)
+    Yo, _ = OS.forward(params, X)
+    assert Yu.shape == Ym.shape == Yo.shape
+    scale = float(np.abs(Yo).max())
+    assert scale > 0
+    assert float(np.abs(Yu - Ym).max()) <= 2e-2 * scale
+    for Y in (Yu, Ym):
+        assert np.linalg.norm(Y - Yo) / np.linalg.norm(Yo) <= 2e-2
+
+
 def test_gradients_match_the_oracle_within_bf16_bound():
     rng = np.random.default_rng(11)
     params = _rounded_params(3)
