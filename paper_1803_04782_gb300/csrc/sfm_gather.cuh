@@ -131,8 +131,16 @@ __device__ __forceinline__ void walk_records_box(const Geo& g, const int32_t* __
       const unsigned bal = __ballot_sync(0xffffffffu, keep);
       if (keep) scr[__popc(bal & lt)] = item;
       __syncwarp();
+      // two items per shared-memory read (one broadcast of 16 bytes; scr is
+      // 16-byte aligned and j even)
       const int m = __popc(bal);
-      for (int j = 0; j < m; ++j) visit(scr[j]);
+      int j = 0;
+      for (; j + 1 < m; j += 2) {
+        const int4 two = *reinterpret_cast<const int4*>(scr + j);
+        visit(make_int2(two.x, two.y));
+        visit(make_int2(two.z, two.w));
+      }
+      if (j < m) visit(scr[j]);
       __syncwarp();
     }
   }
