@@ -138,6 +138,38 @@ def test_infinite_delta_falls_back_everywhere_and_reproduces_the_exact_ticks(i):
         assert a.stats()["exited"] == b.stats()["exited"]
 
 
+def test_tick_decisions_on_the_candidate_composition_match_the_lattice_surrogate_field():
+    """A surrogate tick composes F_sur at each pedestrian's candidates instead
+    of over the lattice.  With delta = 0 (only margins within FP32 rounding
+    fall back) its decisions equal the oracle's decisions on the lattice
+    surrogate field of sfm_surrogate_field, wherever the oracle's best two
+    energies are apart by more than FP32 rounding."""
+    sc = SG.random_scene(400, 320, 6000, r=20, seed=131, obstacles=5, exits=("east",),
+                         goal_mode="mixed", heading_mode="random")
+    init = sfm.flatten_params(_rounded_params(5))
+    with sfm.Sim(sc) as sim, sfm.Surrogate(coarsen=8, near_radius=3, params=init) as sur:
+        sim.step(2)
+        xy, hd, al = sim.peds()
+        F = sur.field(sim).astype(np.float64)
+        D = sim.guidance()
+        m = O.model(sc)
+        occ, bad = O.occupancy(m, sc.cell, xy, al)
+        assert bad == 0
+        ch_o, E, _, adm = O.decide(m, sc.cell, occ, xy, hd, sc.goal, al, D, Ffull=F,
+                                   Sfull=np.abs(F))
+        sur.set_delta(0.0)
+        sur.step(sim, 1)
+        ch, _ = sim.decisions()
+    live = al.astype(bool)
+    Ea = np.where(adm.astype(bool), E, np.inf)
+    two = np.sort(Ea, axis=1)[:, :2]
+    with np.errstate(invalid="ignore"):  # dead pedestrians: no admissible candidate
+        margin = two[:, 1] - two[:, 0]
+    clear = live & (margin > 1e-5 * (np.abs(two[:, 0]) + 1.0))
+    assert clear.sum() > 0.9 * live.sum()
+    np.testing.assert_array_equal(ch[clear], ch_o[clear])
+
+
 def test_calibrated_delta_meets_the_flip_target_and_zero_delta_only_ties():
     """A calibrated delta (99th percentile of the candidate error spread) keeps
     the decision flip rate within 0.1% while part of the crowd is decided on
