@@ -243,12 +243,10 @@ __device__ __forceinline__ int pick_move(const float (&f)[9], const int32_t (&dd
 // (an out-of-lattice candidate repeats p's own row or column and is marked
 // inadmissible by okx / oky), and the guidance, cell and occupancy of each
 // candidate.
-__device__ __forceinline__ void candidate_cells(int2 q, const Geo& g, const uint8_t* __restrict__ cell,
-                                                const uint8_t* __restrict__ ocls,
-                                                const int32_t* __restrict__ D, int (&cx)[3],
-                                                int (&ry)[3], bool (&okx)[3], bool (&oky)[3],
-                                                int32_t (&dd)[9], uint8_t (&cl)[9],
-                                                uint8_t (&oc)[9]) {
+// The 3 x 3 candidate block of a pedestrian at q: columns and rows wrapped
+// (periodic) or clamped to q (outside, ok false) ...
+__device__ __forceinline__ void candidate_coords(int2 q, const Geo& g, int (&cx)[3], int (&ry)[3],
+                                                 bool (&okx)[3], bool (&oky)[3]) {
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     okx[d] = wrap_coord(q.x + d - 1, g.W, g.px, cx[d]);
@@ -256,6 +254,14 @@ __device__ __forceinline__ void candidate_cells(int2 q, const Geo& g, const uint
     if (!okx[d]) cx[d] = q.x;
     if (!oky[d]) ry[d] = q.y;
   }
+}
+
+// ... and the guidance distance, cell type and occupancy class there
+__device__ __forceinline__ void candidate_loads(const Geo& g, const uint8_t* __restrict__ cell,
+                                                const uint8_t* __restrict__ ocls,
+                                                const int32_t* __restrict__ D, const int (&cx)[3],
+                                                const int (&ry)[3], int32_t (&dd)[9],
+                                                uint8_t (&cl)[9], uint8_t (&oc)[9]) {
 #pragma unroll
   for (int k = 0; k < 9; ++k) {
     const int xi = move_dx(k) + 1, yi = move_dy(k) + 1;
@@ -264,6 +270,16 @@ __device__ __forceinline__ void candidate_cells(int2 q, const Geo& g, const uint
     cl[k] = cell[c];
     oc[k] = ocls[(size_t)ry[yi] * g.opitch + cx[xi]];
   }
+}
+
+__device__ __forceinline__ void candidate_cells(int2 q, const Geo& g, const uint8_t* __restrict__ cell,
+                                                const uint8_t* __restrict__ ocls,
+                                                const int32_t* __restrict__ D, int (&cx)[3],
+                                                int (&ry)[3], bool (&okx)[3], bool (&oky)[3],
+                                                int32_t (&dd)[9], uint8_t (&cl)[9],
+                                                uint8_t (&oc)[9]) {
+  candidate_coords(q, g, cx, ry, okx, oky);
+  candidate_loads(g, cell, ocls, D, cx, ry, dd, cl, oc);
 }
 
 __device__ __forceinline__ uint8_t decide_one(

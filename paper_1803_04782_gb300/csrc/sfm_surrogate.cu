@@ -1045,16 +1045,20 @@ __global__ void k_sur_decide(const int32_t* __restrict__ rec_id, const int32_t* 
     const int2 q = xy[p];
     int cx[3], ry[3];
     bool okx[3], oky[3];
-    int32_t dd[9];
-    uint8_t cl[9], oc[9];
-    candidate_cells(q, g, cell, ocls, D, cx, ry, okx, oky, dd, cl, oc);
+    candidate_coords(q, g, cx, ry, okx, oky);
     float f[9], fmag = 0.f;
     if constexpr (CAND) {
       surrogate_at_candidates(g, q, cx, ry, bin_start, rec, Fs, np, far, f);
+      // the candidates' other data are loaded after the field is composed
+      // (fewer values live across the near walk)
+      asm volatile("" ::: "memory");
     } else {
 #pragma unroll
       for (int k = 0; k < 9; ++k) f[k] = Fsur[(size_t)ry[move_dy(k) + 1] * g.W + cx[move_dx(k) + 1]];
     }
+    int32_t dd[9];
+    uint8_t cl[9], oc[9];
+    candidate_loads(g, cell, ocls, D, cx, ry, dd, cl, oc);
 #pragma unroll
     for (int k = 0; k < 9; ++k) fmag = fmaxf(fmag, fabsf(f[k]));
     float margin, emag;
