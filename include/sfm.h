@@ -345,8 +345,8 @@ sfm_status sfm_surrogate_grad(sfm_surrogate* sur, int32_t Hin, int32_t Win, cons
                               const float* T, float* loss, float* grads);
 /* Forward pass alone on a given input: X as for sfm_surrogate_grad, Y (host,
  * [Hin-10][Win-10]) the network's output.  tcgen05 != 0: the 3x3 32 -> 32
- * layers on the tcgen05 kernel, 0: on the mma.sync kernel that every other
- * surrogate call uses (it is the faster of the two at 32 channels).
+ * layers on the tcgen05 kernel that every other surrogate call uses, 0: on
+ * the mma.sync kernel (a check of the first against the second).
  * SFM_ETIMEOUT: a tcgen05 convolution's bounded wait ran out; from then on
  * the surrogate runs those layers on mma.sync (every synchronising
  * surrogate call reports such a timeout once). */

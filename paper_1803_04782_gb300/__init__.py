@@ -685,7 +685,7 @@ class Surrogate:
     def forward(self, X, tcgen05=True):
         """The network's output for a channel-planar input X [3][Hin][Win]
         (rounded to BF16), with the 3x3 32 -> 32 layers on the tcgen05 kernel
-        or (tcgen05=False) on the mma.sync kernel the surrogate's ticks use."""
+        the surrogate's ticks use, or (tcgen05=False) on the mma.sync kernel."""
         X = np.ascontiguousarray(X, np.float32)
         Y = np.empty((X.shape[1] - 10, X.shape[2] - 10), np.float32)
         _scheck(self.h, lib().sfm_surrogate_forward(self.h, X.shape[1], X.shape[2],

@@ -6,6 +6,7 @@
 // accumulation; trained on the GPU by the kernels below (forward, backward,
 // Adam) on fields the exact path computes; the exact path stays the judge
 // (sfm_surrogate_eval: field error and decision flip rate).
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <limits.h>
@@ -258,43 +259,50 @@ __global__ void __launch_bounds__(128, MT == 4 ? 3 : 4)
 }
 
 // ------------------------------- 5th-generation tensor cores: 3x3, 32 -> 32
-// The 32 -> 32 layers as an implicit GEMM on tcgen05: a CTA computes 2
-// output rows x 128 pixels; each row is one M = 128, N = 32 accumulator in
-// TMEM (2 x 32 columns), summed over K = 9 kernel offsets x 2 blocks of 16
-// channels by 18 MMAs (BF16 operands from shared memory, FP32 accumulation).
-// Operands sit in the no-swizzle K-major core-matrix layout (8 rows x 16
-// bytes each): the input tile as [input row][channel group of 8][pixel][8
-// channels], so the A operand of kernel offset (ky, kx) for output row j
-// starts at input row j + ky, pixel kx (K-adjacent core matrices 130 x 16
-// bytes apart, M-adjacent ones 128 bytes); the weights as [ky kx][block of
-// 16][half][out][8 in].  One thread issues the MMAs and commits them to an
-// mbarrier; the four warps then read their 32 TMEM lanes (pixels) and store
-// bias + ReLU in BF16.  Persistent CTAs walk the tiles with the grid's
-// stride: 4 per SM with one input buffer each (kUmStages 1), or 2 per SM that
-// copy the next tile's input with cp.async into a second buffer while the
-// current one is multiplied and stored (kUmStages 2).  Every wait is
-// bounded: on a timeout the kernel raises an error flag, frees its TMEM and
-// returns.  Measured on the 16384^2 floor's 2054^2 images: 235 us a layer
-// (one buffer, 4 CTAs), 267 us (two buffers, 2 CTAs) against 207 us for the
-// mma.sync kernel, with the tensor pipe 13-14 % busy: with N = 32 an MMA is
-// small and each tile's copy, MMAs and store run one after another in a CTA,
-// so the layers stay on mma.sync unless a caller asks for this kernel.  (A
-// warp-specialised pipeline -- copy warp, MMA warp, store warps over a ring
-// of buffers and two accumulators -- is what it would take to win.)
-constexpr int kUmRows = 2, kUmCols = 128, kUmInPx = kUmCols + 2, kUmInRows = kUmRows + 2;
-constexpr int kUmA = kUmInRows * 4 * kUmInPx * 16;  // bytes of one input tile buffer
+// The 32 -> 32 layers as an implicit GEMM on tcgen05.  A tile is 4 output
+// rows x 128 pixels; each row is one M = 128, N = 32 accumulator in TMEM,
+// summed over K = 9 kernel offsets x 2 blocks of 16 channels by 18 MMAs
+// (BF16 operands from shared memory, FP32 accumulation), issued with the
+// rows interleaved so that consecutive MMAs write different accumulators.  Operands sit in the
+// no-swizzle K-major core-matrix layout (8 rows x 16 bytes each): the input
+// tile as [input row][channel group of 8][pixel][8 channels], so the A
+// operand of kernel offset (ky, kx) for output row j starts at input row
+// j + ky, pixel kx (K-adjacent core matrices one 2080-byte plane apart,
+// M-adjacent ones 128 bytes); the weights as [ky kx][block of 16][half][out]
+// [8 in].  One persistent CTA an SM, warp-specialised:
+//   warp 0 (one lane): TMA copies of each tile's 4 input rows (a box of 8
+//     channels x 130 pixels x 4 channel groups each, zeros outside the
+//     image) into a ring of kWsStages buffers;
+//   warp 1 (one lane): the MMAs of a tile into one of two TMEM accumulators;
+//     tcgen05.commit frees the input buffer and hands the accumulator on;
+//   warps 2-5: read their 32 TMEM lanes (pixels) of the accumulator two
+//     rows at a time, store bias + ReLU in BF16, then free it.
+// Copies, MMAs and stores of different tiles overlap.  Every wait is
+// bounded: on a timeout a role stops, the kernel raises an error flag, frees
+// its TMEM and returns.  Measured on the 16384^2 floor's 2054^2 images: 175
+// us a layer against 207 us for the mma.sync kernel; what bounds it is the
+// TMA path (each pixel's 64 bytes arrive as four 16-byte pieces, 3.4x the
+// input in L2 -> SM bytes) with the tensor pipe about 20 % busy.
+constexpr int kUmRows = 4, kUmCols = 128, kUmInPx = kUmCols + 2, kUmInRows = kUmRows + 2;
+// one (input row, channel group) plane: 130 pixels x 16 bytes; the 4 planes
+// of an input row (8320 bytes, a multiple of 128) come from one TMA copy
+constexpr int kUmPlane = kUmInPx * 16;
+constexpr int kUmRowBytes = 4 * kUmPlane;
+constexpr int kUmA = kUmInRows * kUmRowBytes;       // bytes of one input tile buffer
 constexpr int kUmB = 9 * 2 * 2 * 32 * 16;           // bytes of the weights
-constexpr int kUmTmemCols = 64;                     // kUmRows x 32, a power of 2 >= 32
-constexpr int kUmStages = 1;                                       // input buffers a CTA
-constexpr size_t kUmSmem = (size_t)kUmStages * kUmA + kUmB + 16;  // + mbarrier and TMEM address
-constexpr int kUmCtasPerSm = kUmStages == 1 ? 4 : 2;
-constexpr uint32_t kUmIdesc =                             // kind::f16 instruction descriptor
-    (1u << 4) |                                           // D: FP32
-    (1u << 7) | (1u << 10) |                              // A, B: BF16 (both K-major)
-    ((uint32_t)(32 >> 3) << 17) |                         // N = 32
-    ((uint32_t)(128 >> 4) << 24);                         // M = 128
-static_assert(kUmA % 16 == 0 && kUmB % 16 == 0, "operands must stay 16-byte aligned");
-static_assert(kUmRows * 32 <= kUmTmemCols, "accumulators exceed the TMEM allocation");
+constexpr int kWsStages = 4, kWsThreads = 192;
+constexpr int kUmTmemCols = 256;                    // 2 accumulators x kUmRows x 32 columns
+constexpr size_t kUmSmem = (size_t)kWsStages * kUmA + kUmB + (2 * kWsStages + 4) * 8 + 16;
+constexpr uint32_t kUmTx = (uint32_t)(kUmInRows * 4 * kUmInPx * 16);  // TMA bytes a tile
+constexpr uint32_t kUmIdesc =                       // kind::f16 instruction descriptor
+    (1u << 4) |                                     // D: FP32
+    (1u << 7) | (1u << 10) |                        // A, B: BF16 (both K-major)
+    ((uint32_t)(32 >> 3) << 17) |                   // N = 32
+    ((uint32_t)(128 >> 4) << 24);                   // M = 128
+static_assert(kUmRowBytes % 128 == 0 && kUmA % 128 == 0 && kUmB % 16 == 0,
+              "TMA destinations and operands must stay aligned");
+static_assert(2 * kUmRows * 32 <= kUmTmemCols, "accumulators exceed the TMEM allocation");
+static_assert((kUmPlane >> 4) < (1 << 14), "plane stride must fit a descriptor offset");
 
 // shared-memory matrix descriptor, no swizzle: start, K-direction (leading)
 // and M/N-direction (stride) byte offsets between core matrices
@@ -310,6 +318,11 @@ __device__ __forceinline__ void umma_f16(uint32_t d_tmem, uint64_t adesc, uint64
       "setp.ne.b32 p, %4, 0;\n\t"
       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
       "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void umma_commit(uint32_t mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(mbar)
+               : "memory");
 }
 
 // bounded wait for the mbarrier phase `parity`; false on a timeout
@@ -328,139 +341,176 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
   return false;
 }
 
-// 16-byte copy into shared memory, or 16 zero bytes when !valid
-__device__ __forceinline__ void cp_async16_or_zero(uint32_t dst, const void* src, bool valid) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src),
-               "r"(valid ? 16 : 0));
-}
-
-__global__ void __launch_bounds__(128, kUmCtasPerSm)
-    k_conv3_umma(const bf16* __restrict__ in, int Hin, int Win, const bf16* __restrict__ Wu,
-                 const float* __restrict__ b, bf16* __restrict__ out, int* __restrict__ err) {
+__global__ void __launch_bounds__(kWsThreads, 1)
+    k_conv3_umma(const __grid_constant__ CUtensorMap tmap, int Hin, int Win,
+                 const bf16* __restrict__ Wu, const float* __restrict__ b, bf16* __restrict__ out,
+                 int* __restrict__ err) {
   extern __shared__ __align__(128) uint8_t smu[];
   const uint32_t sA0 = (uint32_t)__cvta_generic_to_shared(smu);
-  const uint32_t sB = sA0 + kUmStages * kUmA, mbar = sB + kUmB, tslot = mbar + 8;
+  const uint32_t sB = sA0 + kWsStages * kUmA, bar = sB + kUmB;
+  // mbarriers: full[s], empty[s] (input ring), accf[a], acce[a] (accumulators)
+  const uint32_t tslot = bar + (2 * kWsStages + 4) * 8;
+  auto full = [&](int st) { return bar + 8 * st; };
+  auto empty = [&](int st) { return bar + 8 * (kWsStages + st); };
+  auto accf = [&](int ac) { return bar + 8 * (2 * kWsStages + ac); };
+  auto acce = [&](int ac) { return bar + 8 * (2 * kWsStages + 2 + ac); };
   const int Hout = Hin - 2, Wout = Win - 2;
   const int ntx = (Wout + kUmCols - 1) / kUmCols, ntiles = ntx * ((Hout + kUmRows - 1) / kUmRows);
+  const int my = ntiles > (int)blockIdx.x ? (ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x : 0;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   // weights once per CTA (already in the core-matrix layout, 16-byte chunks)
   for (int i = tid; i < kUmB / 16; i += blockDim.x)
-    reinterpret_cast<uint4*>(smu + kUmStages * kUmA)[i] = reinterpret_cast<const uint4*>(Wu)[i];
-  if (tid == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mbar));
-  if (warp == 0) {
+    reinterpret_cast<uint4*>(smu + kWsStages * kUmA)[i] = reinterpret_cast<const uint4*>(Wu)[i];
+  if (tid == 0) {
+    for (int st = 0; st < kWsStages; ++st) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(full(st)));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(empty(st)));
+    }
+    for (int ac = 0; ac < 2; ++ac) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(accf(ac)));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;\n" ::"r"(acce(ac)));
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(tslot),
                  "r"(kUmTmemCols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::);
   }
-  // input tile t into buffer bi: chunk (row, pixel, group) of 8 channels ->
-  // [row][group][pixel], zeros outside the image
-  auto fetch = [&](int t, int bi) {
-    const int x0 = (t % ntx) * kUmCols, y0 = (t / ntx) * kUmRows;
-    const uint32_t base = sA0 + (uint32_t)(bi * kUmA);
-    for (int i = tid; i < kUmInRows * kUmInPx * 4; i += blockDim.x) {
-      const int cg = i & 3, px = (i >> 2) % kUmInPx, r = (i >> 2) / kUmInPx;
-      const int gy = y0 + r, gx = x0 + px;
-      const bool v = gy < Hin && gx < Win;
-      cp_async16_or_zero(base + (uint32_t)(((r * 4 + cg) * kUmInPx + px) * 16),
-                         v ? in + ((size_t)gy * Win + gx) * 32 + cg * 8 : in, v);
-    }
-  };
-  int t = blockIdx.x, bi = 0;
-  if (kUmStages == 2 && t < ntiles) fetch(t, 0);
-  cp_async_commit();
   asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
   uint32_t tmem;
   asm volatile("ld.shared.u32 %0, [%1];\n" : "=r"(tmem) : "r"(tslot));
-  uint32_t phase = 0;
   bool failed = false;
-  for (; t < ntiles; t += gridDim.x, bi ^= (kUmStages - 1)) {
-    if (kUmStages == 2) {
-      // the next tile's copies run while this one is multiplied and stored
-      if (t + (int)gridDim.x < ntiles) fetch(t + gridDim.x, bi ^ 1);
-      cp_async_commit();
-      cp_async_wait_prev();
-    } else {
-      fetch(t, 0);
-      cp_async_commit();
-      cp_async_wait_all();
-    }
-    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-    __syncthreads();
-    if (tid == 0) {
-      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-      const uint32_t sA = sA0 + (uint32_t)(bi * kUmA);
-#pragma unroll 1
-      for (int j = 0; j < kUmRows; ++j)
-#pragma unroll 1
-        for (int kk = 0; kk < 9; ++kk) {
-          const int ky = kk / 3, kx = kk % 3;
-#pragma unroll
-          for (int kb = 0; kb < 2; ++kb) {
-            const uint64_t ad =
-                umma_desc(sA + (uint32_t)((((j + ky) * 4 + 2 * kb) * kUmInPx + kx) * 16), kUmInPx * 16, 128);
-            const uint64_t bd = umma_desc(sB + (uint32_t)((kk * 2 + kb) * 1024), 512, 128);
-            umma_f16(tmem + (uint32_t)(j * 32), ad, bd, kUmIdesc, (kk | kb) != 0);
-          }
+  if (warp == 0) {
+    // producer: TMA copies into the ring
+    if (lane == 0) {
+      for (int it = 0; it < my; ++it) {
+        const int t = blockIdx.x + it * gridDim.x, st = it % kWsStages;
+        const uint32_t ph = (uint32_t)(it / kWsStages) & 1u;
+        if (!mbar_wait(empty(st), ph ^ 1u)) {
+          failed = true;
+          break;
         }
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(mbar)
-                   : "memory");
-    }
-    // one decision for the whole CTA, so every warp leaves the loop together
-    const bool ok = __syncthreads_and(mbar_wait(mbar, phase) ? 1 : 0) != 0;
-    phase ^= 1u;
-    if (!ok) {
-      failed = true;
-      break;
-    }
-    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-    // epilogue: warp w holds TMEM lanes 32w .. 32w + 31 (pixels), row j in
-    // columns 32j .. 32j + 31 (channels)
-    const int x0 = (t % ntx) * kUmCols, y0 = (t / ntx) * kUmRows;
-    const int px = x0 + 32 * warp + lane;
-#pragma unroll 1
-    for (int j = 0; j < kUmRows; ++j) {
-      uint32_t v[32];
-      asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
-          "%11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, "
-          "%28, %29, %30, %31}, [%32];\n"
-          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
-            "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
-            "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]),
-            "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]),
-            "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-          : "r"(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(j * 32)));
-      asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-      const int y = y0 + j;
-      if (px < Wout && y < Hout) {
-        uint32_t o[16];
-#pragma unroll
-        for (int c = 0; c < 16; ++c) {
-          const float a0 = fmaxf(__uint_as_float(v[2 * c]) + b[2 * c], 0.f);
-          const float a1 = fmaxf(__uint_as_float(v[2 * c + 1]) + b[2 * c + 1], 0.f);
-          const __nv_bfloat162 h = __floats2bfloat162_rn(a0, a1);
-          o[c] = *reinterpret_cast<const uint32_t*>(&h);
-        }
-        uint4* dst = reinterpret_cast<uint4*>(out + ((size_t)y * Wout + px) * 32);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) dst[q] = make_uint4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]);
+        const int x0 = (t % ntx) * kUmCols, y0 = (t / ntx) * kUmRows;
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(full(st)), "r"(kUmTx)
+                     : "memory");
+        const uint32_t base = sA0 + (uint32_t)(st * kUmA);
+        for (int r = 0; r < kUmInRows; ++r)
+          asm volatile(
+              "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, "
+              "%4, %5}], [%6];\n" ::"r"(base + (uint32_t)(r * kUmRowBytes)),
+              "l"(reinterpret_cast<uint64_t>(&tmap)), "r"(0), "r"(x0), "r"(0), "r"(y0 + r), "r"(full(st))
+              : "memory");
       }
     }
-    // all TMEM reads done before the next tile's MMAs overwrite the accumulators
-    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-    __syncthreads();
+    __syncwarp();
+  } else if (warp == 1) {
+    // MMA issue
+    if (lane == 0) {
+      for (int it = 0; it < my; ++it) {
+        const int st = it % kWsStages, ac = it & 1;
+        const uint32_t ph = (uint32_t)(it / kWsStages) & 1u, pa = (uint32_t)(it >> 1) & 1u;
+        if (!mbar_wait(full(st), ph) || !mbar_wait(acce(ac), pa ^ 1u)) {
+          failed = true;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        // the rows' accumulations interleaved: consecutive MMAs write
+        // different accumulators; every descriptor is a base plus a
+        // compile-time offset (addresses stay below 256 KB, so the 14-bit
+        // start field takes the sum without a carry)
+        const uint64_t a0 = umma_desc(sA0 + (uint32_t)(st * kUmA), kUmPlane, 128);
+        const uint64_t b0 = umma_desc(sB, 512, 128);
+        const uint32_t d0 = tmem + (uint32_t)(ac * kUmRows * 32);
+#pragma unroll
+        for (int kk = 0; kk < 9; ++kk) {
+#pragma unroll
+          for (int kb = 0; kb < 2; ++kb) {
+            const uint64_t bd = b0 + (uint64_t)(((kk * 2 + kb) * 1024) >> 4);
+#pragma unroll
+            for (int j = 0; j < kUmRows; ++j) {
+              const uint64_t ad =
+                  a0 + (uint64_t)(((j + kk / 3) * kUmRowBytes + 2 * kb * kUmPlane + (kk % 3) * 16) >> 4);
+              umma_f16(d0 + (uint32_t)(j * 32), ad, bd, kUmIdesc, (kk | kb) != 0);
+            }
+          }
+        }
+        umma_commit(empty(st));
+        umma_commit(accf(ac));
+      }
+    }
+    __syncwarp();
+  } else {
+    // stores: warp w reads TMEM lanes 32 (w % 4) .. + 31 (pixels)
+    const int sp = warp & 3;
+    float bias[32];
+#pragma unroll
+    for (int c = 0; c < 32; ++c) bias[c] = b[c];
+    for (int it = 0; it < my; ++it) {
+      const int t = blockIdx.x + it * gridDim.x, ac = it & 1;
+      const uint32_t pa = (uint32_t)(it >> 1) & 1u;
+      if (!__all_sync(0xffffffffu, mbar_wait(accf(ac), pa))) {
+        failed = true;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+      const int x0 = (t % ntx) * kUmCols, y0 = (t / ntx) * kUmRows;
+      const int px = x0 + 32 * sp + lane;
+      // the rows two at a time (64 values in registers), then the accumulator is freed
+#pragma unroll 1
+      for (int j0 = 0; j0 < kUmRows; j0 += 2) {
+        uint32_t v[2][32];
+#pragma unroll
+        for (int jj = 0; jj < 2; ++jj)
+          asm volatile(
+              "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+              "%11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, "
+              "%28, %29, %30, %31}, [%32];\n"
+              : "=r"(v[jj][0]), "=r"(v[jj][1]), "=r"(v[jj][2]), "=r"(v[jj][3]), "=r"(v[jj][4]),
+                "=r"(v[jj][5]), "=r"(v[jj][6]), "=r"(v[jj][7]), "=r"(v[jj][8]), "=r"(v[jj][9]),
+                "=r"(v[jj][10]), "=r"(v[jj][11]), "=r"(v[jj][12]), "=r"(v[jj][13]), "=r"(v[jj][14]),
+                "=r"(v[jj][15]), "=r"(v[jj][16]), "=r"(v[jj][17]), "=r"(v[jj][18]), "=r"(v[jj][19]),
+                "=r"(v[jj][20]), "=r"(v[jj][21]), "=r"(v[jj][22]), "=r"(v[jj][23]), "=r"(v[jj][24]),
+                "=r"(v[jj][25]), "=r"(v[jj][26]), "=r"(v[jj][27]), "=r"(v[jj][28]), "=r"(v[jj][29]),
+                "=r"(v[jj][30]), "=r"(v[jj][31])
+              : "r"(tmem + ((uint32_t)(32 * sp) << 16) + (uint32_t)((ac * kUmRows + j0 + jj) * 32)));
+        asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+        for (int jj = 0; jj < 2; ++jj) {
+          const int y = y0 + j0 + jj;
+          if (px < Wout && y < Hout) {
+            uint32_t o[16];
+#pragma unroll
+            for (int c = 0; c < 16; ++c) {
+              const float a0 = fmaxf(__uint_as_float(v[jj][2 * c]) + bias[2 * c], 0.f);
+              const float a1 = fmaxf(__uint_as_float(v[jj][2 * c + 1]) + bias[2 * c + 1], 0.f);
+              const __nv_bfloat162 h = __floats2bfloat162_rn(a0, a1);
+              o[c] = *reinterpret_cast<const uint32_t*>(&h);
+            }
+            uint4* dst = reinterpret_cast<uint4*>(out + ((size_t)y * Wout + px) * 32);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) dst[q] = make_uint4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]);
+          }
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(acce(ac)) : "memory");
+    }
   }
-  cp_async_wait_all();
-  if (failed && tid == 0) atomicExch(err, 1);
-  // (after a timeout the MMAs in flight are waited for once more, bounded)
-  if (failed) mbar_wait(mbar, phase ^ 1u);
+  if (failed) atomicExch(err, 1);
+  // every role has stopped (all waits are bounded); after a failure the
+  // copies and MMAs still in flight are waited for, bounded, before TMEM is freed
+  if (__syncthreads_or(failed ? 1 : 0) && tid == 0) {
+    for (int st = 0; st < kWsStages; ++st) mbar_wait(empty(st), 0);
+  }
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-  if (warp == 0)
+  if (warp == 1)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kUmTmemCols));
 }
 
@@ -1270,7 +1320,7 @@ struct sfm_surrogate {
   bf16 *wt1 = nullptr, *wt2 = nullptr, *wt3 = nullptr, *wt4 = nullptr;  // for the tensor cores
   bf16 *wu2 = nullptr, *wu3 = nullptr;  // layers 2 and 3 in the tcgen05 operand layout
   int* umma_err = nullptr;              // set by a tcgen05 convolution that timed out
-  bool use_umma = false;                // layers 2 and 3 on tcgen05 (else mma.sync, faster here)
+  bool use_umma = true;                 // layers 2 and 3 on tcgen05 (else mma.sync)
   int adam_t = 0;
   // activations for an image of (Hc + 2 kHalo) x (Wc + 2 kHalo) coarse cells
   int Hc = 0, Wc = 0;
@@ -1449,8 +1499,28 @@ void conv3_tc(const bf16* in, int Hin, int Win, const bf16* wt, const float* b, 
   }
 }
 
-// 3x3 32 -> 32 layer on tcgen05 (persistent CTAs, 2 an SM)
-void conv3_umma(const bf16* in, int Hin, int Win, const bf16* wu, const float* b, bf16* out,
+// cuTensorMapEncodeTiled from the driver (the library links the runtime only)
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_tiled() {
+  static EncodeTiledFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
+}
+
+// 3x3 32 -> 32 layer on tcgen05 (one warp-specialised CTA an SM); false when
+// the tensor map cannot be made (the caller uses the mma.sync kernel)
+bool conv3_umma(const bf16* in, int Hin, int Win, const bf16* wu, const float* b, bf16* out,
                 int* err, cudaStream_t s) {
   static int nsm = 0;
   if (!nsm) {
@@ -1459,10 +1529,25 @@ void conv3_umma(const bf16* in, int Hin, int Win, const bf16* wu, const float* b
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     if (nsm <= 0) nsm = 1;
   }
+  EncodeTiledFn enc = encode_tiled();
+  if (!enc) return false;
+  // the input [Hin][Win][32] BF16 seen as [row][channel group][pixel][8
+  // channels] (strides: pixel 64 bytes, group 16, row Win x 64): one box of
+  // 8 channels x 130 pixels x 4 groups x 1 row lands as the 4 planes of a row
+  alignas(64) CUtensorMap tm;
+  const cuuint64_t dims[4] = {8, (cuuint64_t)Win, 4, (cuuint64_t)Hin};
+  const cuuint64_t strides[3] = {64, 16, (cuuint64_t)Win * 64};
+  const cuuint32_t box[4] = {8, (cuuint32_t)kUmInPx, 4, 1};
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  if (enc(&tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<bf16*>(in), dims, strides, box, estr,
+          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return false;
   const int ntiles = cdiv(Win - 2, kUmCols) * cdiv(Hin - 2, kUmRows);
-  const int grid = std::max(1, std::min(ntiles, nsm * kUmCtasPerSm));
+  const int grid = std::max(1, std::min(ntiles, nsm));
   cudaFuncSetAttribute(k_conv3_umma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kUmSmem);
-  k_conv3_umma<<<grid, 128, kUmSmem, s>>>(in, Hin, Win, wu, b, out, err);
+  k_conv3_umma<<<grid, kWsThreads, kUmSmem, s>>>(tm, Hin, Win, wu, b, out, err);
+  return true;
 }
 
 // forward of the whole padded image currently in S->X (all four layers on
@@ -1479,13 +1564,10 @@ void forward(sfm_surrogate* S, cudaStream_t s) {
     const int grid = std::max(1, std::min(ntiles, std::max(nsm, 1) * kC1CtasPerSm));
     k_conv1_tc<<<grid, 128, 0, s>>>(S->X, Hp, Wp, S->wt1, q + kOffB[0], S->A1);
   }
-  if (S->use_umma) {
-    conv3_umma(S->A1, Hp - 4, Wp - 4, S->wu2, q + kOffB[1], S->A2, S->umma_err, s);
-    conv3_umma(S->A2, Hp - 6, Wp - 6, S->wu3, q + kOffB[2], S->A3, S->umma_err, s);
-  } else {
+  if (!(S->use_umma && conv3_umma(S->A1, Hp - 4, Wp - 4, S->wu2, q + kOffB[1], S->A2, S->umma_err, s)))
     conv3_tc(S->A1, Hp - 4, Wp - 4, S->wt2, q + kOffB[1], S->A2, s);
+  if (!(S->use_umma && conv3_umma(S->A2, Hp - 6, Wp - 6, S->wu3, q + kOffB[2], S->A3, S->umma_err, s)))
     conv3_tc(S->A2, Hp - 6, Wp - 6, S->wt3, q + kOffB[2], S->A3, s);
-  }
   conv3_tc(S->A3, Hp - 8, Wp - 8, S->wt4, q + kOffB[3], nullptr, s, S->Y);
 }
 
