@@ -263,52 +263,57 @@ __global__ void __launch_bounds__(128, MT == 4 ? 3 : 4)
 // rows x 128 pixels; each row is one M = 128, N = 32 accumulator in TMEM,
 // summed over K = 9 kernel offsets x 2 blocks of 16 channels by 18 MMAs
 // (BF16 operands from shared memory, FP32 accumulation), issued with the
-// rows interleaved so that consecutive MMAs write different accumulators.  Operands sit in the
-// no-swizzle K-major core-matrix layout (8 rows x 16 bytes each): the input
-// tile as [input row][channel group of 8][pixel][8 channels], so the A
-// operand of kernel offset (ky, kx) for output row j starts at input row
-// j + ky, pixel kx (K-adjacent core matrices one 2080-byte plane apart,
-// M-adjacent ones 128 bytes); the weights as [ky kx][block of 16][half][out]
-// [8 in].  One persistent CTA an SM, warp-specialised:
-//   warp 0 (one lane): TMA copies of each tile's 4 input rows (a box of 8
-//     channels x 130 pixels x 4 channel groups each, zeros outside the
-//     image) into a ring of kWsStages buffers;
-//   warp 1 (one lane): the MMAs of a tile into one of two TMEM accumulators;
-//     tcgen05.commit frees the input buffer and hands the accumulator on;
-//   warps 2-5: read their 32 TMEM lanes (pixels) of the accumulator two
-//     rows at a time, store bias + ReLU in BF16, then free it.
+// rows interleaved so that consecutive MMAs write different accumulators.
+// An input row (130 pixels x all 32 channels, 64 bytes a pixel) arrives in
+// one TMA copy with the 64-byte swizzle, which is the K-major SWIZZLE_64B
+// operand layout (a pixel is a row of 64 bytes, 8-row groups 512 bytes
+// apart): the A operand of kernel offset (ky, kx) and channel block kb for
+// output row j starts at input row j + ky, pixel kx, byte 32 kb (the
+// swizzle follows the absolute shared-memory address, so the shifts need no
+// base offset).  The weights use the no-swizzle layout [ky kx][block of 16]
+// [half][out][8 in].  One persistent CTA an SM, warp-specialised:
+//   warp 0 (one lane): TMA copies of each tile's 6 input rows (zeros outside
+//     the image) into a ring of kWsStages buffers;
+//   warp 1 (one lane): the MMAs of a tile into one of two TMEM accumulator
+//     sets; tcgen05.commit frees the input buffer and hands the set on;
+//   warps 2-5: read their 32 TMEM lanes (pixels) of the set two rows at a
+//     time, store bias + ReLU in BF16, then free it.
 // Copies, MMAs and stores of different tiles overlap.  Every wait is
 // bounded: on a timeout a role stops, the kernel raises an error flag, frees
-// its TMEM and returns.  Measured on the 16384^2 floor's 2054^2 images: 175
-// us a layer against 207 us for the mma.sync kernel; what bounds it is the
-// TMA path (each pixel's 64 bytes arrive as four 16-byte pieces, 3.4x the
-// input in L2 -> SM bytes) with the tensor pipe about 20 % busy.
+// its TMEM and returns.  Measured on the 16384^2 floor's 2054^2 images: 140
+// us a layer against 207 us for the mma.sync kernel.
 constexpr int kUmRows = 4, kUmCols = 128, kUmInPx = kUmCols + 2, kUmInRows = kUmRows + 2;
-// one (input row, channel group) plane: 130 pixels x 16 bytes; the 4 planes
-// of an input row (8320 bytes, a multiple of 128) come from one TMA copy
-constexpr int kUmPlane = kUmInPx * 16;
-constexpr int kUmRowBytes = 4 * kUmPlane;
+// one input row: 130 pixels x 64 bytes (all 32 channels), one TMA copy with
+// the 64-byte swizzle, in a 512-byte aligned slot
+constexpr int kUmRowBytes = (kUmInPx * 64 + 511) / 512 * 512;
 constexpr int kUmA = kUmInRows * kUmRowBytes;       // bytes of one input tile buffer
 constexpr int kUmB = 9 * 2 * 2 * 32 * 16;           // bytes of the weights
 constexpr int kWsStages = 4, kWsThreads = 192;
 constexpr int kUmTmemCols = 256;                    // 2 accumulators x kUmRows x 32 columns
-constexpr size_t kUmSmem = (size_t)kWsStages * kUmA + kUmB + (2 * kWsStages + 4) * 8 + 16;
-constexpr uint32_t kUmTx = (uint32_t)(kUmInRows * 4 * kUmInPx * 16);  // TMA bytes a tile
+constexpr size_t kUmSmem = (size_t)kWsStages * kUmA + kUmB + (2 * kWsStages + 4) * 8 + 16 + 512;
+constexpr uint32_t kUmTx = (uint32_t)(kUmInRows * kUmInPx * 64);  // TMA bytes a tile
 constexpr uint32_t kUmIdesc =                       // kind::f16 instruction descriptor
     (1u << 4) |                                     // D: FP32
     (1u << 7) | (1u << 10) |                        // A, B: BF16 (both K-major)
     ((uint32_t)(32 >> 3) << 17) |                   // N = 32
     ((uint32_t)(128 >> 4) << 24);                   // M = 128
-static_assert(kUmRowBytes % 128 == 0 && kUmA % 128 == 0 && kUmB % 16 == 0,
+static_assert(kUmRowBytes % 512 == 0 && kUmA % 512 == 0 && kUmB % 16 == 0,
               "TMA destinations and operands must stay aligned");
 static_assert(2 * kUmRows * 32 <= kUmTmemCols, "accumulators exceed the TMEM allocation");
-static_assert((kUmPlane >> 4) < (1 << 14), "plane stride must fit a descriptor offset");
+static_assert(kUmSmem <= 227 * 1024, "shared memory of the tcgen05 convolution");
 
 // shared-memory matrix descriptor, no swizzle: start, K-direction (leading)
 // and M/N-direction (stride) byte offsets between core matrices
 __device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
   return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)(lbo >> 4) << 16) |
          ((uint64_t)(sbo >> 4) << 32) | (1ull << 46);
+}
+
+// the same with the 64-byte swizzle (K-major rows of 64 bytes, 8-row groups
+// 512 bytes apart; the leading offset is unused)
+__device__ __forceinline__ uint64_t umma_desc_sw64(uint32_t saddr) {
+  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | (1ull << 16) | ((uint64_t)(512 >> 4) << 32) |
+         (1ull << 46) | (4ull << 61);
 }
 
 __device__ __forceinline__ void umma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
@@ -345,8 +350,11 @@ __global__ void __launch_bounds__(kWsThreads, 1)
     k_conv3_umma(const __grid_constant__ CUtensorMap tmap, int Hin, int Win,
                  const bf16* __restrict__ Wu, const float* __restrict__ b, bf16* __restrict__ out,
                  int* __restrict__ err) {
-  extern __shared__ __align__(128) uint8_t smu[];
-  const uint32_t sA0 = (uint32_t)__cvta_generic_to_shared(smu);
+  extern __shared__ __align__(1024) uint8_t smu_raw[];
+  // the swizzled buffers start on a 512-byte boundary (512 bytes allocated spare)
+  const uint32_t raw = (uint32_t)__cvta_generic_to_shared(smu_raw);
+  const uint32_t sA0 = (raw + 511u) & ~511u;
+  uint8_t* smu = smu_raw + (sA0 - raw);
   const uint32_t sB = sA0 + kWsStages * kUmA, bar = sB + kUmB;
   // mbarriers: full[s], empty[s] (input ring), accf[a], acce[a] (accumulators)
   const uint32_t tslot = bar + (2 * kWsStages + 4) * 8;
@@ -400,9 +408,9 @@ __global__ void __launch_bounds__(kWsThreads, 1)
         const uint32_t base = sA0 + (uint32_t)(st * kUmA);
         for (int r = 0; r < kUmInRows; ++r)
           asm volatile(
-              "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, "
-              "%4, %5}], [%6];\n" ::"r"(base + (uint32_t)(r * kUmRowBytes)),
-              "l"(reinterpret_cast<uint64_t>(&tmap)), "r"(0), "r"(x0), "r"(0), "r"(y0 + r), "r"(full(st))
+              "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, "
+              "%4}], [%5];\n" ::"r"(base + (uint32_t)(r * kUmRowBytes)),
+              "l"(reinterpret_cast<uint64_t>(&tmap)), "r"(0), "r"(x0), "r"(y0 + r), "r"(full(st))
               : "memory");
       }
     }
@@ -422,7 +430,7 @@ __global__ void __launch_bounds__(kWsThreads, 1)
         // different accumulators; every descriptor is a base plus a
         // compile-time offset (addresses stay below 256 KB, so the 14-bit
         // start field takes the sum without a carry)
-        const uint64_t a0 = umma_desc(sA0 + (uint32_t)(st * kUmA), kUmPlane, 128);
+        const uint64_t a0 = umma_desc_sw64(sA0 + (uint32_t)(st * kUmA));
         const uint64_t b0 = umma_desc(sB, 512, 128);
         const uint32_t d0 = tmem + (uint32_t)(ac * kUmRows * 32);
 #pragma unroll
@@ -433,7 +441,7 @@ __global__ void __launch_bounds__(kWsThreads, 1)
 #pragma unroll
             for (int j = 0; j < kUmRows; ++j) {
               const uint64_t ad =
-                  a0 + (uint64_t)(((j + kk / 3) * kUmRowBytes + 2 * kb * kUmPlane + (kk % 3) * 16) >> 4);
+                  a0 + (uint64_t)(((j + kk / 3) * kUmRowBytes + (kk % 3) * 64 + kb * 32) >> 4);
               umma_f16(d0 + (uint32_t)(j * 32), ad, bd, kUmIdesc, (kk | kb) != 0);
             }
           }
@@ -1535,12 +1543,12 @@ bool conv3_umma(const bf16* in, int Hin, int Win, const bf16* wu, const float* b
   // channels] (strides: pixel 64 bytes, group 16, row Win x 64): one box of
   // 8 channels x 130 pixels x 4 groups x 1 row lands as the 4 planes of a row
   alignas(64) CUtensorMap tm;
-  const cuuint64_t dims[4] = {8, (cuuint64_t)Win, 4, (cuuint64_t)Hin};
-  const cuuint64_t strides[3] = {64, 16, (cuuint64_t)Win * 64};
-  const cuuint32_t box[4] = {8, (cuuint32_t)kUmInPx, 4, 1};
-  const cuuint32_t estr[4] = {1, 1, 1, 1};
-  if (enc(&tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<bf16*>(in), dims, strides, box, estr,
-          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+  const cuuint64_t dims[3] = {32, (cuuint64_t)Win, (cuuint64_t)Hin};
+  const cuuint64_t strides[2] = {64, (cuuint64_t)Win * 64};
+  const cuuint32_t box[3] = {32, (cuuint32_t)kUmInPx, 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  if (enc(&tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<bf16*>(in), dims, strides, box, estr,
+          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
     return false;
   const int ntiles = cdiv(Win - 2, kUmCols) * cdiv(Hin - 2, kUmRows);
