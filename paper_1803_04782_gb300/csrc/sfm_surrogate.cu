@@ -276,11 +276,12 @@ __global__ void __launch_bounds__(128, MT == 4 ? 3 : 4)
 //     the image) into a ring of kWsStages buffers;
 //   warp 1 (one lane): the MMAs of a tile into one of two TMEM accumulator
 //     sets; tcgen05.commit frees the input buffer and hands the set on;
-//   warps 2-5: read their 32 TMEM lanes (pixels) of the set two rows at a
-//     time, store bias + ReLU in BF16, then free it.
+//   warps 2-9: each reads its 32 TMEM lanes (pixels) of two of the set's
+//     rows (two warps share a lane quarter), stores bias + ReLU in BF16, then
+//     frees its part of the set.
 // Copies, MMAs and stores of different tiles overlap.  Every wait is
 // bounded: on a timeout a role stops, the kernel raises an error flag, frees
-// its TMEM and returns.  Measured on the 16384^2 floor's 2054^2 images: 140
+// its TMEM and returns.  Measured on the 16384^2 floor's 2054^2 images: 133
 // us a layer against 207 us for the mma.sync kernel.
 constexpr int kUmRows = 4, kUmCols = 128, kUmInPx = kUmCols + 2, kUmInRows = kUmRows + 2;
 // one input row: 130 pixels x 64 bytes (all 32 channels), one TMA copy with
@@ -288,7 +289,7 @@ constexpr int kUmRows = 4, kUmCols = 128, kUmInPx = kUmCols + 2, kUmInRows = kUm
 constexpr int kUmRowBytes = (kUmInPx * 64 + 511) / 512 * 512;
 constexpr int kUmA = kUmInRows * kUmRowBytes;       // bytes of one input tile buffer
 constexpr int kUmB = 9 * 2 * 2 * 32 * 16;           // bytes of the weights
-constexpr int kWsStages = 4, kWsThreads = 192;
+constexpr int kWsStages = 4, kWsThreads = 320;  // warps 0, 1 and 8 store warps
 constexpr int kUmTmemCols = 256;                    // 2 accumulators x kUmRows x 32 columns
 constexpr size_t kUmSmem = (size_t)kWsStages * kUmA + kUmB + (2 * kWsStages + 4) * 8 + 16 + 512;
 constexpr uint32_t kUmTx = (uint32_t)(kUmInRows * kUmInPx * 64);  // TMA bytes a tile
@@ -376,7 +377,7 @@ __global__ void __launch_bounds__(kWsThreads, 1)
     }
     for (int ac = 0; ac < 2; ++ac) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(accf(ac)));
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;\n" ::"r"(acce(ac)));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 8;\n" ::"r"(acce(ac)));
     }
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
@@ -452,8 +453,9 @@ __global__ void __launch_bounds__(kWsThreads, 1)
     }
     __syncwarp();
   } else {
-    // stores: warp w reads TMEM lanes 32 (w % 4) .. + 31 (pixels)
-    const int sp = warp & 3;
+    // stores: warp w reads TMEM lanes 32 (w % 4) .. + 31 (pixels) of rows
+    // jh, jh + 2 (two warps share a lane quarter)
+    const int sp = warp & 3, jh = (warp - 2) >> 2;
     float bias[32];
 #pragma unroll
     for (int c = 0; c < 32; ++c) bias[c] = b[c];
@@ -467,9 +469,9 @@ __global__ void __launch_bounds__(kWsThreads, 1)
       asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
       const int x0 = (t % ntx) * kUmCols, y0 = (t / ntx) * kUmRows;
       const int px = x0 + 32 * sp + lane;
-      // the rows two at a time (64 values in registers), then the accumulator is freed
-#pragma unroll 1
-      for (int j0 = 0; j0 < kUmRows; j0 += 2) {
+      // this warp's two rows (64 values in registers), then its part of the
+      // accumulator set is freed
+      {
         uint32_t v[2][32];
 #pragma unroll
         for (int jj = 0; jj < 2; ++jj)
@@ -484,11 +486,11 @@ __global__ void __launch_bounds__(kWsThreads, 1)
                 "=r"(v[jj][20]), "=r"(v[jj][21]), "=r"(v[jj][22]), "=r"(v[jj][23]), "=r"(v[jj][24]),
                 "=r"(v[jj][25]), "=r"(v[jj][26]), "=r"(v[jj][27]), "=r"(v[jj][28]), "=r"(v[jj][29]),
                 "=r"(v[jj][30]), "=r"(v[jj][31])
-              : "r"(tmem + ((uint32_t)(32 * sp) << 16) + (uint32_t)((ac * kUmRows + j0 + jj) * 32)));
+              : "r"(tmem + ((uint32_t)(32 * sp) << 16) + (uint32_t)((ac * kUmRows + jh + 2 * jj) * 32)));
         asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
 #pragma unroll
         for (int jj = 0; jj < 2; ++jj) {
-          const int y = y0 + j0 + jj;
+          const int y = y0 + jh + 2 * jj;
           if (px < Wout && y < Hout) {
             uint32_t o[16];
 #pragma unroll
