@@ -43,65 +43,19 @@ constexpr int kOffB[4] = {kNW1, kNW1 + kL1o + kNW2, kNW1 + kL1o + 2 * kNW2 + kLh
 constexpr int kTile = 16;  // output pixels per CTA side
 static_assert(kNParams == 3 * 32 * 25 + 32 + 2 * (32 * 32 * 9 + 32) + 32 * 9 + 1, "params");
 
-// --------------------------------------------------------------- forward
-// out[y][x][o] = act(b[o] + sum_{ky,kx,c} W[ky][kx][c][o] * in[y+ky][x+kx][c])
-// ("valid" cross-correlation, channel-last tensors, FP32 accumulation).
-template <int CIN, int COUT, int K, bool RELU>
-__global__ void __launch_bounds__(kTile* kTile)
-    k_conv_fwd(const bf16* __restrict__ in, int Hin, int Win, const float* __restrict__ Wt,
-               const float* __restrict__ b, bf16* __restrict__ out_bf, float* __restrict__ out_f) {
-  constexpr int TI = kTile + K - 1;
-  extern __shared__ __align__(16) float sm[];
-  float* sW = sm;                        // K*K*CIN*COUT
-  float* sIn = sm + K * K * CIN * COUT;  // TI*TI*CIN
-  const int Hout = Hin - K + 1, Wout = Win - K + 1;
-  const int x0 = blockIdx.x * kTile, y0 = blockIdx.y * kTile;
-  const int tid = threadIdx.x;
-  for (int i = tid; i < K * K * CIN * COUT; i += blockDim.x) sW[i] = Wt[i];
-  for (int i = tid; i < TI * TI * CIN; i += blockDim.x) {
-    const int c = i % CIN, p = i / CIN, px = p % TI, py = p / TI;
-    const int gy = y0 + py, gx = x0 + px;
-    sIn[i] = (gy < Hin && gx < Win) ? __bfloat162float(in[((size_t)gy * Win + gx) * CIN + c]) : 0.f;
-  }
-  __syncthreads();
-  const int tx = tid % kTile, ty = tid / kTile;
-  const int y = y0 + ty, x = x0 + tx;
-  float acc[COUT];
-#pragma unroll
-  for (int o = 0; o < COUT; ++o) acc[o] = b[o];
-  for (int ky = 0; ky < K; ++ky)
-    for (int kx = 0; kx < K; ++kx) {
-      const float* xin = sIn + ((ty + ky) * TI + (tx + kx)) * CIN;
-      const float* w = sW + (ky * K + kx) * CIN * COUT;
-#pragma unroll 4
-      for (int c = 0; c < CIN; ++c) {
-        const float v = xin[c];
-#pragma unroll
-        for (int o = 0; o < COUT; ++o) acc[o] = fmaf(v, w[c * COUT + o], acc[o]);
-      }
-    }
-  if (y >= Hout || x >= Wout) return;
-  const size_t base = ((size_t)y * Wout + x) * COUT;
-#pragma unroll
-  for (int o = 0; o < COUT; ++o) {
-    const float v = RELU ? fmaxf(acc[o], 0.f) : acc[o];
-    if (out_bf) out_bf[base + o] = __float2bfloat16(v);
-    if (out_f) out_f[base + o] = v;
-  }
-}
-
-
-// ------------------------------------------- tensor-core 3x3, 32 -> 32
-// Implicit GEMM on mma.sync m16n8k16 (BF16 operands, FP32 accumulators): a
-// CTA computes 8 x 16 output pixels x 32 channels; warp w owns output rows
-// 2w and 2w+1 (one m16 tile each) and all four n8 tiles.  K runs over the 9
-// kernel offsets x 2 blocks of 16 input channels.  The input tile (10 x 18
-// pixels) and the weights sit in shared memory channel-last with rows padded
-// to 40 channels (80 bytes), which keeps the ldmatrix row fetches free of
-// bank conflicts.  Weights in shared memory: [ky][kx][out][in], BF16.  The
-// CTAs are persistent (4 per SM): each loads the weights once and takes the
-// tiles with the grid's stride, copying the next tile's input with cp.async
-// into the second of two buffers while it computes the current one.
+// ------------------------------------------- tensor-core 3x3 (mma.sync)
+// Implicit GEMM on mma.sync m16n8k16 (BF16 operands, FP32 accumulators) for
+// the 32 -> 1 last layer, and for the 32 -> 32 layers when the tcgen05
+// kernel below is not used: a CTA computes 4 MT output rows x 16 pixels;
+// warp w owns rows MT w .. MT w + MT - 1 (one m16 tile each) and the NT n8
+// tiles of output channels.  K runs over the 9 kernel offsets x 2 blocks of
+// 16 input channels.  The input tile and the weights sit in shared memory
+// channel-last with rows padded to 40 channels (80 bytes), which keeps the
+// ldmatrix row fetches free of bank conflicts.  Weights in shared memory:
+// [ky][kx][out][in], BF16.  The CTAs are persistent: each loads the weights
+// once and takes the tiles with the grid's stride, copying the next tile's
+// input with cp.async into the second of two buffers while it computes the
+// current one.  (Layer 1 uses the 8 x 16 tiles of kTcRows.)
 constexpr int kTcRows = 8, kTcCols = 16, kTcPad = 40;
 
 __device__ __forceinline__ void ldsm_x4(uint32_t addr, uint32_t& r0, uint32_t& r1, uint32_t& r2,
@@ -1427,27 +1381,12 @@ sfm_status ensure_image(sfm_surrogate* S, int Hc, int Wc) {
 }
 
 template <int CIN, int COUT, int K>
-size_t fwd_smem() {
-  return ((size_t)K * K * CIN * COUT + (size_t)(kTile + K - 1) * (kTile + K - 1) * CIN) * 4;
-}
-template <int CIN, int COUT, int K>
 size_t dx_smem() {
   return ((size_t)K * K * CIN * COUT + (size_t)(kTile + K - 1) * (kTile + K - 1) * COUT) * 4;
 }
 template <int CIN, int COUT, int K>
 size_t dw_smem() {
   return ((size_t)(kTile + K - 1) * (kTile + K - 1) * CIN + (size_t)kTile * kTile * COUT) * 4;
-}
-
-template <int CIN, int COUT, int K, bool RELU>
-void conv_fwd(const bf16* in, int Hin, int Win, const float* W, const float* b, bf16* out_bf,
-              float* out_f, cudaStream_t s) {
-  const size_t sm = fwd_smem<CIN, COUT, K>();
-  cudaFuncSetAttribute(k_conv_fwd<CIN, COUT, K, RELU>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)sm);
-  const int Ho = Hin - K + 1, Wo = Win - K + 1;
-  dim3 grid(cdiv(Wo, kTile), cdiv(Ho, kTile));
-  k_conv_fwd<CIN, COUT, K, RELU><<<grid, kTile * kTile, sm, s>>>(in, Hin, Win, W, b, out_bf, out_f);
 }
 
 template <int CIN, int COUT, int K, bool RELU>
