@@ -113,7 +113,7 @@ __global__ void __launch_bounds__(kV2Threads, 1)
     k_field_v2(Geo g, const int32_t* __restrict__ bin_start, const uint32_t* __restrict__ rec,
                const float* __restrict__ CT, const float* __restrict__ Fs,
                float* __restrict__ out, int out_row0, int fy0, int fy1, int store_lo,
-               int store_hi, FarPart far) {
+               int store_hi, FarPart far, unsigned int* __restrict__ tickets) {
   extern __shared__ __align__(16) float sm[];
   constexpr int FW = SHAPE ? 32 : 16, FH = 16, NJ = SHAPE ? 16 : 8;
   const int r = g.r;
@@ -135,25 +135,33 @@ __global__ void __launch_bounds__(kV2Threads, 1)
   const int nf = nfx * (fy1 - fy0);
   // this lane's column and first row inside a footprint
   const int x = SHAPE ? lane : (lane & 15), yl = SHAPE ? 0 : (lane >> 4) * 8;
-  // large lattices: each CTA takes runs of wpb consecutive footprints (its
-  // warps share records through L1); small ones (under 4 footprints per warp
-  // of the whole grid): footprint f goes to CTA f % gridDim.x, so every SM
-  // gets work.  Either way each footprint is computed once, by one warp.
-  // (both walk footprints with the stride of all warps, tw)
-  const int f0 = nf < 4 * tw ? blockIdx.x + gridDim.x * warp : blockIdx.x * wpb + warp;
+  // Schedule.  The first footprints go out in rounds of tw, one per warp: a
+  // round of a large lattice gives each CTA a run of wpb consecutive
+  // footprints (its warps share records through L1); a partial round, or
+  // every round of a lattice under 4 footprints per warp of the whole grid,
+  // deals footprint base + i to CTA i % gridDim.x, so it spreads over every
+  // SM.  With a ticket counter only whole rounds covering about 4/5 of the
+  // footprints are dealt so; a warp then takes the rest one at a time, in
+  // the order of tickets it draws, so SMs whose share of the crowd was light
+  // do more of them and all finish together.  Either way each footprint is
+  // computed once, by one warp.
+  const bool spread_all = nf < 4 * tw;
+  const int nstat = tickets ? (int)((4LL * nf / 5) / tw) * tw : nf;
+  auto footprint = [&](int base) {
+    return spread_all || nf - base < tw ? base + blockIdx.x + gridDim.x * warp
+                                        : base + blockIdx.x * wpb + warp;
+  };
   // with the far part (little gather work per footprint) the static-field
-  // lines of a footprint (one per row) are fetched into L2 one footprint
-  // ahead, so the store's reads of Fs do not wait on HBM
+  // lines of a footprint (one per row) are fetched into L2 before its
+  // gather, so the store's reads of Fs do not wait on HBM
   auto prefetch_fs = [&](int f) {
     if (FAR && f < nf && lane < FH) {
       const int px0 = (f % nfx) * FW, py = (fy0 + f / nfx) * FH + lane;
       if (py < g.H) asm volatile("prefetch.global.L2 [%0];" ::"l"(Fs + (size_t)py * g.W + px0));
     }
   };
-  prefetch_fs(f0);
-  for (int f = f0; f < nf; f += tw) {
+  auto visit = [&](int f) {
     const int x0 = (f % nfx) * FW, y0 = (fy0 + f / nfx) * FH;
-    prefetch_fs(f + tw);
     FarAxis fax{};
     if constexpr (FAR) fax = far_axis(x0 + x, far.inv_s, far.Wc, g.px);
     float2 acc[NJ / 2];
@@ -175,6 +183,43 @@ __global__ void __launch_bounds__(kV2Threads, 1)
         }
       }
     }
+  };
+  // one loop over both parts, so the footprint's code is inlined once; lane
+  // 0 draws a warp's next ticket while the warp works on the current one
+  unsigned int t = 0;
+  int base = 0, f;
+  if (nstat > 0) {
+    f = footprint(0);
+  } else {
+    if (lane == 0) t = atomicAdd(tickets, 1u);
+    f = nstat + (int)__shfl_sync(0xffffffffu, t, 0);
+  }
+  prefetch_fs(f);
+  while (f < nf) {  // f >= nf: a partial round had none left, or the tickets ran out
+    int fn = nf;
+    if (base + tw < nstat) {
+      base += tw;
+      fn = footprint(base);
+    } else if (tickets) {
+      if (lane == 0) t = atomicAdd(tickets, 1u);
+      fn = -1;
+    }
+    if (fn >= 0) prefetch_fs(fn);
+    visit(f);
+    f = fn >= 0 ? fn : nstat + (int)__shfl_sync(0xffffffffu, t, 0);
+    if (fn < 0) prefetch_fs(f);
+  }
+  if (!tickets) return;
+  // the last CTA out puts the counter back to zero for the next launch:
+  // every warp of every CTA has drawn its final ticket before its CTA counts
+  // itself done
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(tickets + 1, 1u) == gridDim.x - 1) {
+      atomicExch(tickets, 0u);
+      atomicExch(tickets + 1, 0u);
+    }
   }
 }
 
@@ -183,7 +228,7 @@ static int g_num_sms = 0;
 template <int SP, int SHAPE, int FAR>
 static void launch_v2(const Geo& g, const int32_t* bin_start, const uint32_t* rec, const float* CT,
                       const float* Fs, float* out, int out_row0, int store_lo, int store_hi,
-                      cudaStream_t s, const FarPart& far) {
+                      cudaStream_t s, const FarPart& far, unsigned int* tickets) {
   constexpr int FW = SHAPE ? 32 : 16, FH = 16;
   const size_t smem = (kTableGuard + class_table_floats(g.r)) * sizeof(float) +
                       kV2Threads / 32 * 32 * sizeof(int2);
@@ -203,24 +248,26 @@ static void launch_v2(const Geo& g, const int32_t* bin_start, const uint32_t* re
   if (blocks > g_num_sms) blocks = g_num_sms;
   if (blocks < 1) blocks = 1;
   k_field_v2<SP, SHAPE, FAR><<<blocks, kV2Threads, smem, s>>>(g, bin_start, rec, CT, Fs, out, out_row0,
-                                                         fy0, fy1, store_lo, store_hi, far);
+                                                         fy0, fy1, store_lo, store_hi, far,
+                                                         tickets);
 }
 
 template <int SP>
 static void launch_v2_shape(const Geo& g, const int32_t* bin_start, const uint32_t* rec,
                             const Tables& tb, const float* Fs, float* out, int out_row0,
-                            int store_lo, int store_hi, cudaStream_t s, const FarPart& far) {
+                            int store_lo, int store_hi, cudaStream_t s, const FarPart& far,
+                            unsigned int* tickets) {
   // the far part (surrogate) has its own instantiations, 32 x 16 footprint
   // only (one for coarsening 8, one for any), so the exact gather carries no
   // code for it
   if (far.Y && far.s == 8)
-    launch_v2<SP, 1, 8>(g, bin_start, rec, tb.CT, Fs, out, out_row0, store_lo, store_hi, s, far);
+    launch_v2<SP, 1, 8>(g, bin_start, rec, tb.CT, Fs, out, out_row0, store_lo, store_hi, s, far, tickets);
   else if (far.Y)
-    launch_v2<SP, 1, 1>(g, bin_start, rec, tb.CT, Fs, out, out_row0, store_lo, store_hi, s, far);
+    launch_v2<SP, 1, 1>(g, bin_start, rec, tb.CT, Fs, out, out_row0, store_lo, store_hi, s, far, tickets);
   else if (tb.shape)
-    launch_v2<SP, 1, 0>(g, bin_start, rec, tb.CT, Fs, out, out_row0, store_lo, store_hi, s, far);
+    launch_v2<SP, 1, 0>(g, bin_start, rec, tb.CT, Fs, out, out_row0, store_lo, store_hi, s, far, tickets);
   else
-    launch_v2<SP, 0, 0>(g, bin_start, rec, tb.CT, Fs, out, out_row0, store_lo, store_hi, s, far);
+    launch_v2<SP, 0, 0>(g, bin_start, rec, tb.CT, Fs, out, out_row0, store_lo, store_hi, s, far, tickets);
 }
 
 void launch_field(const Geo& g, const int32_t* bin_start, const uint32_t* rec, const Tables& tb,
@@ -232,14 +279,19 @@ void launch_field(const Geo& g, const int32_t* bin_start, const uint32_t* rec, c
     launch_field_v1(g, bin_start, rec, tb, Fs, out, out_row0, store_lo, store_hi, ctr, s);
     return;
   }
+  // the context's footprint ticket counter (no counter: a static schedule).
+  // The far-part gather keeps the static one: its footprints cost about the
+  // same everywhere (a 7 x 7 window and the epilogue), and they are so short
+  // that one ticket each would queue on the counter.
+  unsigned int* tickets = ctr && !far.Y ? ctr->field_tickets : nullptr;
   switch (sp) {
-    case 34: launch_v2_shape<34>(g, bin_start, rec, tb, Fs, out, out_row0, store_lo, store_hi, s, far); break;
-    case 50: launch_v2_shape<50>(g, bin_start, rec, tb, Fs, out, out_row0, store_lo, store_hi, s, far); break;
-    case 66: launch_v2_shape<66>(g, bin_start, rec, tb, Fs, out, out_row0, store_lo, store_hi, s, far); break;
-    case 82: launch_v2_shape<82>(g, bin_start, rec, tb, Fs, out, out_row0, store_lo, store_hi, s, far); break;
-    case 98: launch_v2_shape<98>(g, bin_start, rec, tb, Fs, out, out_row0, store_lo, store_hi, s, far); break;
-    case 114: launch_v2_shape<114>(g, bin_start, rec, tb, Fs, out, out_row0, store_lo, store_hi, s, far); break;
-    default: launch_v2_shape<kNarrowStride>(g, bin_start, rec, tb, Fs, out, out_row0, store_lo, store_hi, s, far); break;
+    case 34: launch_v2_shape<34>(g, bin_start, rec, tb, Fs, out, out_row0, store_lo, store_hi, s, far, tickets); break;
+    case 50: launch_v2_shape<50>(g, bin_start, rec, tb, Fs, out, out_row0, store_lo, store_hi, s, far, tickets); break;
+    case 66: launch_v2_shape<66>(g, bin_start, rec, tb, Fs, out, out_row0, store_lo, store_hi, s, far, tickets); break;
+    case 82: launch_v2_shape<82>(g, bin_start, rec, tb, Fs, out, out_row0, store_lo, store_hi, s, far, tickets); break;
+    case 98: launch_v2_shape<98>(g, bin_start, rec, tb, Fs, out, out_row0, store_lo, store_hi, s, far, tickets); break;
+    case 114: launch_v2_shape<114>(g, bin_start, rec, tb, Fs, out, out_row0, store_lo, store_hi, s, far, tickets); break;
+    default: launch_v2_shape<kNarrowStride>(g, bin_start, rec, tb, Fs, out, out_row0, store_lo, store_hi, s, far, tickets); break;
   }
 }
 

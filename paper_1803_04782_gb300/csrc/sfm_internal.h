@@ -78,6 +78,10 @@ struct Counters {
   int max_registrants;
   uint32_t err;
   long long t;  // tick counter read by the vote and advanced by the commit
+  // the class-table gather's footprint tickets: next ticket, CTAs done; zero
+  // between launches (the launch's last CTA puts them back), so launches
+  // sharing one context's counters run one at a time, in stream order
+  unsigned int field_tickets[2];
 };
 
 // Multi-su pedestrians (Sec. 2): pedestrian p occupies the w[p] x h[p]
