@@ -29,6 +29,11 @@ sys.path.insert(0, ROOT)
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 FLOPS_PER_PAIR = 6.0  # three FP32 multiply-adds per (su, pedestrian-in-window) pair
+# stage events on every 9th tick of the timed region: an event record costs a
+# few microseconds of GPU time (the stream drains before it), so recording all
+# stages of every tick would add about 7 % to a floor tick; the 8 ticks in
+# between fill one untimed 8-tick graph
+TIMING_EVERY = 9
 # DRAM bytes (read + write) per banded launch of the field gather on the
 # 16384^2 floor with 4 bands, from a one-pass ncu capture of this benchmark
 # (dram__bytes_read.sum + dram__bytes_write.sum); valid only while the
@@ -283,7 +288,9 @@ def run_gpu(args):
         if dist is not None:
             dist.barrier()
 
-    # warm-up
+    # warm-up with the stage sampling on, so its first replayed tick builds
+    # every graph the timed region replays (untimed and timed)
+    sim.set_timing(TIMING_EVERY)
     sim.step(args.warmup)
     sim.sync()
     xy0, h0, a0 = sim.peds()
@@ -291,8 +298,10 @@ def run_gpu(args):
     alive0 = int(a0.sum())
     launches0 = sim.stats()["kernel_launches"]
 
-    # timed region: K ticks, stage events on the library's stream
-    sim.set_timing(True)
+    # timed region: K ticks replayed as graphs; every TIMING_EVERY-th of them
+    # (the first included) replays the one-tick graph whose stage events are
+    # event record nodes on the library's stream
+    sim.set_timing(TIMING_EVERY)
     sim.stage_times()  # reset
     uuid = None
     try:
@@ -317,9 +326,9 @@ def run_gpu(args):
     sim.set_timing(False)
     st1 = sim.stats()
     xy1, h1, a1 = sim.peds()
-    # the same ticks replayed as one CUDA graph each, without per-stage events
-    # (what the stage events cost shows on small lattices); after the timed
-    # region, not part of `value`
+    # the same ticks replayed as untimed graphs (8 ticks each while that many
+    # remain) without stage events: what the event nodes cost shows on small
+    # lattices; after the timed region, not part of `value`
     graph_ticks = max(3, min(args.steps, 20))
     sim.step(graph_ticks)  # builds (once) the graphs the timed call replays
     torch.cuda.synchronize()
@@ -337,14 +346,15 @@ def run_gpu(args):
     elapsed, ped_steps = reduce_over_ranks(dist, elapsed, ped_steps, "cuda")
 
     # roofline of the dominant kernel: the field gather
-    field_s = stage_ms["field"] / 1e3
+    field_s = stage_ms["field"] / 1e3  # over the `ticks` timed ticks
     pairs = 0.5 * (pairs0 + pairs1)
-    achieved = FLOPS_PER_PAIR * pairs * args.steps / field_s / 1e12
+    achieved = FLOPS_PER_PAIR * pairs * ticks / field_s / 1e12
     peak = SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": gather_traffic(args.workload, st1["bands"], footprint),
                 "traffic_unit": "bytes per launch",
-                "kernel": "k_field_v2", "field_ms_per_step": 1e3 * field_s / args.steps,
+                "kernel": "k_field_v2", "field_ms_per_step": 1e3 * field_s / ticks,
+                "timed_ticks": ticks,
                 "pairs_per_step": pairs,
                 "peak_basis": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz (max clock)",
                 # the gather's binding resource: one 128-byte shared-memory
@@ -406,6 +416,8 @@ def run_gpu(args):
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "su_updates_per_s": sc.W * sc.H * args.steps * world / elapsed,
         "stage_ms_per_step": {k: v / max(1, ticks) for k, v in stage_ms.items()},
+        "stage_timing": f"CUDA events around each stage of every {TIMING_EVERY}th tick of the "
+                        f"timed region ({ticks} of {args.steps} ticks)",
         "graph_ms_per_step": graph_ms,
         "roofline": roofline,
         "cpu_baseline": cpu,

@@ -248,12 +248,20 @@ sfm_status sfm_read_decisions(sfm_ctx* ctx, uint8_t* choice, uint8_t* won, int32
 /* Counters (synchronising). */
 sfm_status sfm_stats(sfm_ctx* ctx, sfm_stats_t* out);
 
-/* Per-stage timing: when enabled, sfm_step launches stage by stage and
- * records CUDA events around each stage on the context's stream. */
-sfm_status sfm_set_timing(sfm_ctx* ctx, int32_t enable);
+/* Per-stage timing.  every = 0: off; every = k >= 1: sfm_step records CUDA
+ * events around each stage of every k-th tick (the first tick after this call
+ * is one), on the context's stream.  Every record waits for the stream's
+ * work before it and the next launch waits for it, so it costs a few
+ * microseconds of GPU time; sampling (k > 1) keeps that out of most ticks.
+ * After the first tick following a placement (launched stage by stage), a
+ * timed tick replays a one-tick CUDA graph whose event record nodes are
+ * pointed at fresh events before the replay; untimed ticks replay the
+ * untimed graphs.  A batch context times every tick (one event pair around
+ * its graph) whatever k is.  every < 0: SFM_EINVAL. */
+sfm_status sfm_set_timing(sfm_ctx* ctx, int32_t every);
 
 /* Accumulated milliseconds per stage (SFM_NSTAGES doubles) and the number
- * of ticks they cover since the last call; resets the accumulators.
+ * of timed ticks they cover since the last call; resets the accumulators.
  * Synchronising. */
 sfm_status sfm_stage_times(sfm_ctx* ctx, double* ms, int64_t* ticks);
 

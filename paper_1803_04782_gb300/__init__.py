@@ -288,8 +288,9 @@ def sfm_autotune(ctx) -> str:
     return "32x16" if v.value else "16x16"
 
 
-def sfm_set_timing(ctx, enable: bool) -> None:
-    _check(ctx, lib().sfm_set_timing(ctx, 1 if enable else 0))
+def sfm_set_timing(ctx, every) -> None:
+    """every: False / 0 off, True / 1 every tick, k > 1 every k-th tick."""
+    _check(ctx, lib().sfm_set_timing(ctx, int(every)))
 
 
 def sfm_stage_times(ctx):
@@ -511,8 +512,9 @@ class Sim:
     def set_footprint(self, shape: str):
         _check(self.ctx, lib().sfm_set_field_footprint(self.ctx, {"16x16": 0, "32x16": 1}[shape]))
 
-    def set_timing(self, on=True):
-        sfm_set_timing(self.ctx, on)
+    def set_timing(self, every=True):
+        """Stage events on every ``every``-th tick (True: every tick; False: off)."""
+        sfm_set_timing(self.ctx, every)
 
     def stage_times(self):
         return sfm_stage_times(self.ctx)
@@ -611,8 +613,9 @@ class Batch:
     def stats(self):
         return sfm_stats(self.ctx)
 
-    def set_timing(self, on=True):
-        sfm_set_timing(self.ctx, on)
+    def set_timing(self, every=True):
+        """Stage events on every ``every``-th tick (True: every tick; False: off)."""
+        sfm_set_timing(self.ctx, every)
 
     def stage_times(self):
         return sfm_stage_times(self.ctx)

@@ -87,15 +87,22 @@ struct StageScope {
   StageScope(sfm_ctx* c_, int s_) : c(c_), stage(s_) {
     if (c->timing) {
       a = pool_get(c);
-      cudaEventRecord(a, c->stream);
+      record(a);
     }
   }
   ~StageScope() {
     if (c->timing) {
       cudaEvent_t b = pool_get(c);
-      cudaEventRecord(b, c->stream);
+      record(b);
       c->recs.push_back({stage, a, b});
     }
+  }
+  // under the capture of the timed tick graph an event becomes a record node
+  void record(cudaEvent_t e) {
+    if (c->capturing_timed)
+      cudaEventRecordWithFlags(e, c->stream, cudaEventRecordExternal);
+    else
+      cudaEventRecord(e, c->stream);
   }
 };
 
@@ -219,6 +226,13 @@ void drop_graph(sfm_ctx* c) {
   c->tick_graph = nullptr;
   if (c->block_graph) cudaGraphExecDestroy(c->block_graph);
   c->block_graph = nullptr;
+  if (c->timed_graph) cudaGraphExecDestroy(c->timed_graph);
+  c->timed_graph = nullptr;
+  if (c->timed_tmpl) cudaGraphDestroy(c->timed_tmpl);
+  c->timed_tmpl = nullptr;
+  c->timed_nodes.clear();
+  for (cudaEvent_t e : c->timed_placeholders) cudaEventDestroy(e);
+  c->timed_placeholders.clear();
   c->direct_ticks = 0;
 }
 
@@ -250,6 +264,113 @@ cudaError_t build_tick_graph(sfm_ctx* c, int ticks, cudaGraphExec_t* exec, int64
   cudaStreamDestroy(cs);
   if (e != cudaSuccess) *exec = nullptr;
   return e;
+}
+
+// Capture one tick with its stage events as event record nodes (the timed
+// tick graph), and find each stage's pair of nodes.
+cudaError_t build_timed_graph(sfm_ctx* c) {
+  cudaStream_t cs;
+  cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return e;
+  cudaStream_t saved = c->stream;
+  const int64_t l0 = c->launches;
+  const size_t r0 = c->recs.size();
+  cudaGraph_t graph = nullptr;
+  c->stream = cs;
+  c->capturing_timed = true;
+  e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    run_tick(c);
+    e = cudaStreamEndCapture(cs, &graph);
+  }
+  c->capturing_timed = false;
+  c->stream = saved;
+  c->timed_launches = c->launches - l0;
+  c->launches = l0;
+  // the capture's events stay with the graph (its nodes name them until the
+  // first replay points them elsewhere)
+  std::vector<sfm_ctx::Rec> cap(c->recs.begin() + (long)r0, c->recs.end());
+  c->recs.resize(r0);
+  for (const auto& r : cap) {
+    c->timed_placeholders.push_back(r.a);
+    c->timed_placeholders.push_back(r.b);
+  }
+  if (e == cudaSuccess) {
+    size_t nn = 0;
+    e = cudaGraphGetNodes(graph, nullptr, &nn);
+    std::vector<cudaGraphNode_t> nodes(nn);
+    if (e == cudaSuccess && nn) e = cudaGraphGetNodes(graph, nodes.data(), &nn);
+    std::vector<std::pair<cudaEvent_t, cudaGraphNode_t>> ev;
+    for (size_t i = 0; e == cudaSuccess && i < nn; ++i) {
+      cudaGraphNodeType t;
+      e = cudaGraphNodeGetType(nodes[i], &t);
+      cudaEvent_t x = nullptr;
+      if (e == cudaSuccess && t == cudaGraphNodeTypeEventRecord) {
+        e = cudaGraphEventRecordNodeGetEvent(nodes[i], &x);
+        ev.push_back({x, nodes[i]});
+      }
+    }
+    auto node_of = [&](cudaEvent_t x) -> cudaGraphNode_t {
+      for (const auto& p : ev)
+        if (p.first == x) return p.second;
+      return nullptr;
+    };
+    for (const auto& r : cap) {
+      const cudaGraphNode_t na = node_of(r.a), nb = node_of(r.b);
+      if (!na || !nb) {
+        if (e == cudaSuccess) e = cudaErrorInvalidValue;
+        break;
+      }
+      c->timed_nodes.push_back({r.stage, na, nb});
+    }
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&c->timed_graph, graph, 0);
+  if (e == cudaSuccess) {
+    c->timed_tmpl = graph;
+  } else {
+    if (graph) cudaGraphDestroy(graph);
+    c->timed_graph = nullptr;
+    c->timed_nodes.clear();
+  }
+  cudaStreamDestroy(cs);
+  return e;
+}
+
+// Every graph sfm_step replays, built together the first time one is needed
+// after a placement: the one-tick and kBlockTicks-tick graphs and, with
+// timing on, the timed one-tick graph; so no capture happens in the middle
+// of a run of replays that someone is timing.
+sfm_status ensure_graphs(sfm_ctx* c) {
+  const bool saved = c->timing;
+  cudaError_t e = cudaSuccess;
+  c->timing = false;
+  if (!c->tick_graph) e = build_tick_graph(c, 1, &c->tick_graph, &c->graph_launches);
+  if (e == cudaSuccess && !c->block_graph)
+    e = build_tick_graph(c, kBlockTicks, &c->block_graph, &c->block_launches);
+  c->timing = true;
+  if (e == cudaSuccess && c->timing_every > 0 && !c->timed_graph) e = build_timed_graph(c);
+  c->timing = saved;
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, SFM_ECUDA, "tick graph: %s", cudaGetErrorString(e));
+  }
+  return SFM_OK;
+}
+
+// One replay of the timed tick graph, its stage nodes on fresh events.
+cudaError_t replay_timed_tick(sfm_ctx* c) {
+  for (const auto& n : c->timed_nodes) {
+    const cudaEvent_t a = pool_get(c), b = pool_get(c);
+    cudaError_t e = cudaGraphExecEventRecordNodeSetEvent(c->timed_graph, n.a, a);
+    if (e == cudaSuccess) e = cudaGraphExecEventRecordNodeSetEvent(c->timed_graph, n.b, b);
+    if (e != cudaSuccess) {
+      c->pool.push_back(a);
+      c->pool.push_back(b);
+      return e;
+    }
+    c->recs.push_back({n.stage, a, b});
+  }
+  return cudaGraphLaunch(c->timed_graph, c->stream);
 }
 
 sfm_status copy_out(sfm_ctx* ctx, void* dst, const void* src, size_t bytes, int on_device) {
@@ -613,34 +734,56 @@ sfm_status sfm_step(sfm_ctx* ctx, int32_t nsteps) {
   if (nsteps < 0) return fail(ctx, SFM_EINVAL, "nsteps < 0");
   if (ctx->batch) return batch_tick(ctx, nsteps, 0);
   if (!ctx->placed) return fail(ctx, SFM_ESTATE, "sfm_step before a successful sfm_place");
+  const int every = ctx->timing_every;
+  // after `done` ticks: the phase of the timing sample
+  auto advance = [&](int done) {
+    if (every > 0) ctx->timing_phase = (ctx->timing_phase + done) % every;
+  };
+  struct Restore {  // whatever happens, the flag means "timing on" again
+    sfm_ctx* c;
+    ~Restore() { c->timing = c->timing_every > 0; }
+  } restore{ctx};
   for (int i = 0; i < nsteps;) {
-    // timed ticks launch stage by stage (events between stages); otherwise the
-    // first tick after placement runs directly and the rest replay graphs: of
-    // kBlockTicks ticks while that many remain, else of one tick
-    if (ctx->timing || ctx->direct_ticks < 1) {
+    // Timed ticks (every `every`-th) record stage events.  The first tick
+    // after placement runs directly (stage by stage); the rest replay graphs:
+    // a timed tick its own graph, with event record nodes between the stages;
+    // untimed ticks kBlockTicks ticks at a time while that many remain before
+    // the end or the next timed tick, else one.
+    const bool timed = every > 0 && ctx->timing_phase == 0;
+    ctx->timing = timed;
+    if (ctx->direct_ticks < 1) {
       run_tick(ctx);
       ++ctx->direct_ticks;
       ++ctx->t;
       ++i;
+      if (timed) ++ctx->timed_ticks;
+      advance(1);
       continue;
     }
-    const bool block = nsteps - i >= kBlockTicks;
+    if (timed) {
+      if (!ctx->timed_graph) TRY(ensure_graphs(ctx));
+      const cudaError_t re = replay_timed_tick(ctx);
+      if (re != cudaSuccess) return fail(ctx, SFM_ECUDA, "timed tick: %s", cudaGetErrorString(re));
+      ctx->launches += ctx->timed_launches;
+      ++ctx->t;
+      ++i;
+      ++ctx->timed_ticks;
+      advance(1);
+      continue;
+    }
+    int room = nsteps - i;
+    if (every > 0 && every - ctx->timing_phase < room) room = (int)(every - ctx->timing_phase);
+    const bool block = room >= kBlockTicks;
     cudaGraphExec_t* exec = block ? &ctx->block_graph : &ctx->tick_graph;
     int64_t* nl = block ? &ctx->block_launches : &ctx->graph_launches;
-    if (!*exec) {
-      const cudaError_t ge = build_tick_graph(ctx, block ? kBlockTicks : 1, exec, nl);
-      if (ge != cudaSuccess) {
-        cudaGetLastError();
-        return fail(ctx, SFM_ECUDA, "tick graph: %s", cudaGetErrorString(ge));
-      }
-    }
+    if (!*exec) TRY(ensure_graphs(ctx));
     CU(cudaGraphLaunch(*exec, ctx->stream));
     ctx->launches += *nl;
     const int done = block ? kBlockTicks : 1;
     ctx->t += done;
     i += done;
+    advance(done);
   }
-  if (ctx->timing) ctx->timed_ticks += nsteps;
   CU(cudaGetLastError());
   return SFM_OK;
 }
@@ -1003,9 +1146,12 @@ sfm_status sfm_stats(sfm_ctx* ctx, sfm_stats_t* out) {
   return SFM_OK;
 }
 
-sfm_status sfm_set_timing(sfm_ctx* ctx, int32_t enable) {
+sfm_status sfm_set_timing(sfm_ctx* ctx, int32_t every) {
   if (!ctx) return SFM_EINVAL;
-  ctx->timing = enable != 0;
+  if (every < 0) return fail(ctx, SFM_EINVAL, "timing period %d < 0", every);
+  ctx->timing_every = every;
+  ctx->timing_phase = 0;
+  ctx->timing = every > 0;
   return SFM_OK;
 }
 

@@ -70,8 +70,11 @@ struct sfm_ctx {
   int bands = 1;
   int band_rows = 0;  // lattice rows per band (multiple of the tile height)
   float* band_buf = nullptr;
-  // timing
+  // timing: stage events on every timing_every-th tick (0: none); `timing`
+  // says whether the tick being launched records them
   bool timing = false;
+  int timing_every = 0;
+  int64_t timing_phase = 0;  // ticks since the last timed one, mod timing_every
   struct Rec {
     int stage;
     cudaEvent_t a, b;
@@ -79,6 +82,18 @@ struct sfm_ctx {
   std::vector<Rec> recs;
   std::vector<cudaEvent_t> pool;
   int64_t timed_ticks = 0;
+  // one timed tick captured as a CUDA graph whose stage events are event
+  // record nodes; before each replay the nodes are pointed at fresh events
+  struct TimedNode {
+    int stage;
+    cudaGraphNode_t a, b;
+  };
+  bool capturing_timed = false;  // StageScope records capture-external events
+  cudaGraph_t timed_tmpl = nullptr;  // kept: the event nodes belong to it
+  cudaGraphExec_t timed_graph = nullptr;
+  int64_t timed_launches = 0;
+  std::vector<TimedNode> timed_nodes;
+  std::vector<cudaEvent_t> timed_placeholders;  // events recorded during the capture
   // one tick captured as a CUDA graph (single lattice, untimed ticks)
   cudaGraphExec_t tick_graph = nullptr;
   int64_t graph_launches = 0;  // kernels in one replay of tick_graph

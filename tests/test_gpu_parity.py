@@ -373,6 +373,48 @@ def test_many_ticks_in_one_call_equal_single_ticks(variant):
         assert b.stats()["error_flags"] == 0
 
 
+@pytest.mark.parametrize("banded,every", [(False, 1), (True, 1), (False, 4), (True, 9)])
+def test_timed_ticks_replay_the_same_ticks(banded, every):
+    """With stage timing on, timed ticks after the first replay a one-tick
+    graph whose stage events are event record nodes, re-pointed before each
+    replay; with every = k > 1 only every k-th tick is timed and the others
+    replay the untimed graphs.  The trajectory equals untimed stepping, each
+    stage reports time for every timed tick, the stages fit inside the whole
+    tick, and a placement drops the timed graph (the next timed ticks follow
+    the new crowd)."""
+    sc = SG.random_scene(200, 160, 3000, r=9, seed=152, obstacles=3, exits=("east",),
+                         goal_mode="mixed", heading_mode="random")
+    budget = sfm.band_budget(sc.W, sc.H, 64) if banded else 0
+    with sfm.Sim(sc, hbm_budget_bytes=budget) as a, sfm.Sim(sc, hbm_budget_bytes=budget) as b:
+        assert (a.stats()["bands"] > 1) == banded
+        a.step(12)
+        b.set_timing(every)
+        b.stage_times()
+        b.step(5)
+        b.step(7)
+        ms, ticks = b.stage_times()
+        assert ticks == -(-12 // every)
+        for x, y in zip(a.peds(), b.peds()):
+            np.testing.assert_array_equal(x, y)
+        for k in ("bin", "field", "decide", "vote", "commit", "step"):
+            assert ms[k] > 0.0, k
+        parts = sum(ms[k] for k in ("bin", "field", "decide", "vote", "commit"))
+        assert parts <= ms["step"] * 1.0001
+        # a new placement: the timed graph is rebuilt for the new crowd
+        for s in (a, b):
+            s.place(sc.xy[: sc.n // 2], sc.heading[: sc.n // 2], sc.goal[: sc.n // 2])
+        b.set_timing(every)  # the next tick is a timed one
+        a.step(4)
+        b.step(4)
+        for x, y in zip(a.peds(), b.peds()):
+            np.testing.assert_array_equal(x, y)
+        assert b.stage_times()[1] == -(-4 // every)
+        assert b.stats()["error_flags"] == 0
+        with pytest.raises(sfm.SfmError) as e:
+            b.set_timing(-1)
+        assert e.value.status == sfm.SFM_EINVAL
+
+
 @pytest.mark.parametrize("variant", ["plain", "periods", "sized"])
 def test_snapshot_restore_continues_bit_for_bit(variant):
     """Checkpoint and resume: a snapshot taken after 7 ticks, restored into a
