@@ -359,7 +359,7 @@ def run_gpu(args):
                 "peak_basis": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz (max clock)",
                 # the gather's binding resource: one 128-byte shared-memory
                 # wavefront (32 table words) per clock per SM, one word a pair
-                "smem_pair_frac": pairs * args.steps / field_s / (SMS * 32 * SM_MAX_MHZ * 1e6),
+                "smem_pair_frac": pairs * ticks / field_s / (SMS * 32 * SM_MAX_MHZ * 1e6),
                 "smem_basis": "pairs/s over 152 SMs x 32 table words x 2070 MHz"}
 
     # end to end through the C ABI with host buffers
@@ -376,7 +376,7 @@ def run_gpu(args):
         sfm.sfm_place(sim.ctx, hx, hh, hg, ha)
         sfm.sfm_step(sim.ctx, 1)
         sfm.sfm_read_peds(sim.ctx, hx, hh, ha)
-        e2e_peds += int(ha.numpy().sum())
+        e2e_peds += int(np.count_nonzero(ha.numpy()))
     torch.cuda.synchronize()
     e2e_t = time.perf_counter() - t0
     e2e_t, e2e_peds = reduce_over_ranks(dist, e2e_t, e2e_peds, "cuda")

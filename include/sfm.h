@@ -143,7 +143,11 @@ const char* sfm_last_error(const sfm_ctx* ctx);
  * goal: n classes, 0 = exit-seeker, 1..8 = fixed desired direction (NULL = 0);
  * alive: n flags (NULL = all alive).  Validates on the device and returns
  * SFM_ECONFLICT if two live pedestrians share a su or one sits on a WALL or
- * EXIT su or off-lattice.  Synchronising. */
+ * EXIT su or off-lattice.  Synchronising.  A placement of as many
+ * pedestrians as the previous one, with the same sizing and no walk periods
+ * set, keeps the captured tick graphs (a place / step / read loop replays
+ * them); any other placement drops them and its first tick runs stage by
+ * stage. */
 sfm_status sfm_place(sfm_ctx* ctx, int32_t n, const int32_t* xy, const uint8_t* heading,
                      const uint8_t* goal, const uint8_t* alive, int32_t on_device);
 

@@ -592,7 +592,13 @@ static sfm_status place_impl(sfm_ctx* ctx, int32_t n, const int32_t* xy, const u
                              const uint8_t* h, int32_t on_device) {
   if (!ctx) return SFM_EINVAL;
   if (ctx->batch) return fail(ctx, SFM_ESTATE, "a batch is placed with sfm_batch_place");
-  drop_graph(ctx);
+  // The tick graphs hold the pedestrian count and array pointers as launch
+  // parameters; they stay valid for a new placement of as many pedestrians
+  // into the same arrays with the same options (no walk periods, the same
+  // sizing), so a place / step / read loop keeps replaying them.
+  const bool keep_graphs = ctx->placed && n == ctx->n && n <= ctx->cap && !ctx->walk_periods &&
+                           (w != nullptr) == ctx->sized;
+  if (!keep_graphs) drop_graph(ctx);
   if (n < 0 || (n > 0 && !xy)) return fail(ctx, SFM_EINVAL, "bad pedestrian arrays");
   // multi-su pedestrians: odd sides in [1, kMaxPedSide]; a periodic extent of
   // at least 2 * side + 3, so minimum-image offsets stay unambiguous
@@ -704,6 +710,7 @@ static sfm_status place_impl(sfm_ctx* ctx, int32_t n, const int32_t* xy, const u
   CU(cudaStreamSynchronize(s));
   CU(cudaGetLastError());
   if (hc.err) {
+    drop_graph(ctx);
     const uint32_t flags = hc.err;
     const size_t nsu = (size_t)g.W * g.H;
     cudaMemsetAsync(ctx->occ, 0xff, nsu * sizeof(int32_t), s);

@@ -415,6 +415,46 @@ def test_timed_ticks_replay_the_same_ticks(banded, every):
         assert e.value.status == sfm.SFM_EINVAL
 
 
+@pytest.mark.parametrize("variant", ["plain", "sized", "periods"])
+def test_place_step_read_loop_equals_plain_ticks(variant):
+    """The end-to-end loop (place the crowd read back, step one tick, read)
+    keeps the tick graphs across placements of as many pedestrians into the
+    same arrays, and follows the trajectory of plain ticks.  With walk periods
+    a placement turns them off, so that loop drops its graphs and is compared
+    with ticks whose periods are cleared the same way."""
+    sc = SG.random_scene(200, 160, 3000, r=9, seed=153, obstacles=3, exits=("east",),
+                         goal_mode="mixed", heading_mode="random")
+    size = None
+    if variant == "sized":
+        rng = np.random.default_rng(5)
+        sc, size = sized_subset(sc, rng.choice(np.array([1, 3], np.uint8), size=sc.n))
+    with sfm.Sim(sc, place=size is None) as a, sfm.Sim(sc, place=size is None) as b:
+        def put(s, xy, h, alive):
+            if size is None:
+                s.place(xy, h, sc.goal, alive)
+            else:
+                s.place_sized(xy, h, sc.goal, alive, size, size)
+        if size is not None:
+            for s in (a, b):
+                put(s, sc.xy, sc.heading, np.ones(sc.n, np.uint8))
+        a.step(3)
+        b.step(3)  # builds b's graphs
+        for tick in range(8):
+            if variant == "periods" and tick == 4:
+                per, pha = SG.walk_periods(sc.n, 3)
+                for s in (a, b):
+                    s.set_walk_periods(per, pha)
+            xy, h, alive = b.peds()
+            put(b, xy, h, alive)
+            if variant == "periods" and tick >= 4:
+                put(a, *a.peds())  # a placement clears the walk periods on both
+            a.step(1)
+            b.step(1)
+            for x, y in zip(a.peds(), b.peds()):
+                np.testing.assert_array_equal(x, y)
+        assert b.stats()["error_flags"] == 0
+
+
 @pytest.mark.parametrize("variant", ["plain", "periods", "sized"])
 def test_snapshot_restore_continues_bit_for_bit(variant):
     """Checkpoint and resume: a snapshot taken after 7 ticks, restored into a
