@@ -950,7 +950,16 @@ sfm_status sfm_read_static_field(sfm_ctx* ctx, float* dst, int32_t on_device) {
 
 sfm_status sfm_read_guidance(sfm_ctx* ctx, int32_t* dst, int32_t on_device) {
   if (!ctx || !dst) return SFM_EINVAL;
-  return copy_out(ctx, dst, ctx->D, (size_t)ctx->nsu_total * sizeof(int32_t), on_device);
+  const size_t n = (size_t)ctx->nsu_total;
+  if (on_device) {
+    CU(cudaMemcpyAsync(dst, ctx->D, n * sizeof(int32_t), cudaMemcpyDeviceToDevice, ctx->stream));
+    launch_guidance_export(dst, n, ctx->stream);  // WALL su: kDWall -> kDInf
+    return check_flags(ctx);
+  }
+  TRY(copy_out(ctx, dst, ctx->D, n * sizeof(int32_t), 0));
+  for (size_t i = 0; i < n; ++i)
+    if (dst[i] == kDWall) dst[i] = kDInf;
+  return SFM_OK;
 }
 
 sfm_status sfm_read_peds(sfm_ctx* ctx, int32_t* xy, uint8_t* heading, uint8_t* alive,

@@ -210,7 +210,7 @@ __device__ __forceinline__ bool in_entered(const Geo& g, int sx, int sy, int qx,
 // energies of that size, leaves the choice unchanged.
 template <bool MARGIN>
 __device__ __forceinline__ int pick_move(const float (&f)[9], const int32_t (&dd)[9],
-                                         const uint8_t (&cl)[9], const uint8_t (&oc)[9],
+                                         const uint8_t (&oc)[9],
                                          const bool (&okx)[3], const bool (&oky)[3], int h, int gl,
                                          float beta, const float* __restrict__ own,
                                          const float* __restrict__ dirdot, float* margin,
@@ -220,7 +220,8 @@ __device__ __forceinline__ int pick_move(const float (&f)[9], const int32_t (&dd
 #pragma unroll
   for (int k = 0; k < 9; ++k) {
     const int xi = move_dx(k) + 1, yi = move_dy(k) + 1;
-    const bool adm = (k == 0) || (okx[xi] && oky[yi] && cl[k] != kWall && oc[k] == 0);
+    // a WALL su carries kDWall in the guidance array
+    const bool adm = (k == 0) || (okx[xi] && oky[yi] && dd[k] != kDWall && oc[k] == 0);
     const float guide = (gl == 0) ? beta * ((float)(dd[k] - dd[0]) / 5.0f) : -beta * dirdot[gl * 9 + k];
     const float e = f[k] - own[h * 9 + k] + guide;
     if (adm && (k == 0 || e < bestE)) {
@@ -239,12 +240,9 @@ __device__ __forceinline__ int pick_move(const float (&f)[9], const int32_t (&dd
   return best;
 }
 
-// The 3 x 3 neighbourhood of pedestrian p: wrapped or clipped coordinates
-// (an out-of-lattice candidate repeats p's own row or column and is marked
-// inadmissible by okx / oky), and the guidance, cell and occupancy of each
-// candidate.
 // The 3 x 3 candidate block of a pedestrian at q: columns and rows wrapped
-// (periodic) or clamped to q (outside, ok false) ...
+// (periodic) or clamped to q (an out-of-lattice candidate repeats q's own
+// row or column and is marked inadmissible by okx / oky) ...
 __device__ __forceinline__ void candidate_coords(int2 q, const Geo& g, int (&cx)[3], int (&ry)[3],
                                                  bool (&okx)[3], bool (&oky)[3]) {
 #pragma unroll
@@ -256,30 +254,18 @@ __device__ __forceinline__ void candidate_coords(int2 q, const Geo& g, int (&cx)
   }
 }
 
-// ... and the guidance distance, cell type and occupancy class there
-__device__ __forceinline__ void candidate_loads(const Geo& g, const uint8_t* __restrict__ cell,
-                                                const uint8_t* __restrict__ ocls,
+// ... and the guidance distance and occupancy class there (a WALL su is
+// recognised by its guidance value kDWall, so the cell grid is not read)
+__device__ __forceinline__ void candidate_loads(const Geo& g, const uint8_t* __restrict__ ocls,
                                                 const int32_t* __restrict__ D, const int (&cx)[3],
                                                 const int (&ry)[3], int32_t (&dd)[9],
-                                                uint8_t (&cl)[9], uint8_t (&oc)[9]) {
+                                                uint8_t (&oc)[9]) {
 #pragma unroll
   for (int k = 0; k < 9; ++k) {
     const int xi = move_dx(k) + 1, yi = move_dy(k) + 1;
-    const size_t c = (size_t)ry[yi] * g.W + cx[xi];
-    dd[k] = D[c];
-    cl[k] = cell[c];
+    dd[k] = D[(size_t)ry[yi] * g.W + cx[xi]];
     oc[k] = ocls[(size_t)ry[yi] * g.opitch + cx[xi]];
   }
-}
-
-__device__ __forceinline__ void candidate_cells(int2 q, const Geo& g, const uint8_t* __restrict__ cell,
-                                                const uint8_t* __restrict__ ocls,
-                                                const int32_t* __restrict__ D, int (&cx)[3],
-                                                int (&ry)[3], bool (&okx)[3], bool (&oky)[3],
-                                                int32_t (&dd)[9], uint8_t (&cl)[9],
-                                                uint8_t (&oc)[9]) {
-  candidate_coords(q, g, cx, ry, okx, oky);
-  candidate_loads(g, cell, ocls, D, cx, ry, dd, cl, oc);
 }
 
 __device__ __forceinline__ uint8_t decide_one(
@@ -308,14 +294,12 @@ __device__ __forceinline__ uint8_t decide_one(
   }
   float f[9];
   int32_t dd[9];
-  uint8_t cl[9], oc[9];
+  uint8_t oc[9];
 #pragma unroll
   for (int k = 0; k < 9; ++k) {
     const int xi = move_dx(k) + 1, yi = move_dy(k) + 1;
-    const size_t c = (size_t)ry[yi] * g.W + cx[xi];
     f[k] = F[(size_t)fr[yi] * g.W + cx[xi]];
-    dd[k] = D[c];
-    cl[k] = cell[c];
+    dd[k] = D[(size_t)ry[yi] * g.W + cx[xi]];  // kDWall on WALL su: no cell read
     oc[k] = ocls[(size_t)ry[yi] * g.opitch + cx[xi]];
   }
   if (pw) {
@@ -323,12 +307,9 @@ __device__ __forceinline__ uint8_t decide_one(
     // newly enters are free (walls included in the test)
     const int a = pw[p] >> 1, b = ph[p] >> 1;
 #pragma unroll
-    for (int k = 1; k < 9; ++k) {
-      oc[k] = strip_free(g, cell, occ, q.x, q.y, a, b, k) ? 0 : 1;
-      cl[k] = kFree;
-    }
+    for (int k = 1; k < 9; ++k) oc[k] = strip_free(g, cell, occ, q.x, q.y, a, b, k) ? 0 : 1;
   }
-  return (uint8_t)pick_move<false>(f, dd, cl, oc, okx, oky, h, gl, beta, own, dirdot, nullptr);
+  return (uint8_t)pick_move<false>(f, dd, oc, okx, oky, h, gl, beta, own, dirdot, nullptr);
 }
 
 // ------------------------------------------------------------------ S4 vote

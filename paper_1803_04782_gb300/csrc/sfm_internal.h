@@ -10,7 +10,10 @@
 namespace sfm {
 
 constexpr int kFree = 0, kWall = 1, kExit = 2;
-constexpr int32_t kDInf = 1 << 23;  // guidance distance of unreachable / WALL su
+constexpr int32_t kDInf = 1 << 23;  // guidance distance of unreachable su (and WALL su, as exported)
+// the guidance array's value on WALL su inside the library: it marks the su
+// inadmissible, so a decision needs no read of the cell grid; exported as kDInf
+constexpr int32_t kDWall = kDInf + 1;
 
 // Three-component field gather (radius > 50): a CTA owns a 32 x 32 su tile;
 // warp w owns rows 4w..4w+3 of it, lane l owns column l.
@@ -135,6 +138,7 @@ void launch_static_field(const Geo& g, const uint8_t* cell, const Tables& tb, fl
                          cudaStream_t s);
 // One relaxation round of the guidance distances; returns via *changed.
 void launch_guidance_init(const Geo& g, const uint8_t* cell, int32_t* D, cudaStream_t s);
+void launch_guidance_export(int32_t* D, size_t n, cudaStream_t s);
 void launch_guidance_round(const Geo& g, const uint8_t* cell, int32_t* D, const uint8_t* act_in,
                            uint8_t* act_out, int* changed, cudaStream_t s);
 

@@ -127,7 +127,8 @@ void launch_static_field(const Geo& g, const uint8_t* cell, const Tables& tb, fl
 }
 
 // --------------------------------------------------------------- guidance
-// Chamfer (5, 7) geodesic distance to the nearest EXIT through non-WALL su,
+// Chamfer (5, 7) geodesic distance to the nearest EXIT through non-WALL su
+// (kDInf where none is reachable, kDWall on WALL su),
 // solved as the fixed point of D(c) = min_k D(c + Delta_k) + w_k by tile-local
 // relaxation in shared memory; a tile is revisited only when it or a
 // neighbour changed in the previous round.  The fixed point is unique, so the
@@ -136,7 +137,14 @@ __global__ void k_guidance_init(Geo g, const uint8_t* __restrict__ cell, int32_t
   const size_t n = (size_t)g.W * g.H;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
        i += (size_t)gridDim.x * blockDim.x)
-    D[i] = (cell[i] == kExit) ? 0 : kDInf;
+    D[i] = cell[i] == kExit ? 0 : (cell[i] == kWall ? kDWall : kDInf);
+}
+
+// the exported form: WALL su read kDInf, like unreachable ones
+__global__ void k_guidance_export(int32_t* __restrict__ D, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x)
+    if (D[i] == kDWall) D[i] = kDInf;
 }
 
 __global__ void __launch_bounds__(1024)
@@ -203,6 +211,13 @@ void launch_guidance_init(const Geo& g, const uint8_t* cell, int32_t* D, cudaStr
   int blocks = (int)((n + 255) / 256);
   if (blocks > 152 * 64) blocks = 152 * 64;
   k_guidance_init<<<blocks, 256, 0, s>>>(g, cell, D);
+}
+
+void launch_guidance_export(int32_t* D, size_t n, cudaStream_t s) {
+  if (!n) return;
+  int blocks = (int)((n + 255) / 256);
+  if (blocks > 152 * 64) blocks = 152 * 64;
+  k_guidance_export<<<blocks, 256, 0, s>>>(D, n);
 }
 
 void launch_guidance_round(const Geo& g, const uint8_t* cell, int32_t* D, const uint8_t* act_in,
@@ -700,7 +715,7 @@ void launch_class_tables(int r, const sfm_params& p, float* T, cudaStream_t s, d
 // neighbouring su): E over the 9 candidates (stay + 8 neighbours), admissible
 // iff inside, not WALL and unoccupied at tick start; select of the minimum
 // with ties to the smallest class.
-__global__ void k_decide(const int32_t* __restrict__ rec_id, const int32_t* __restrict__ bin_start,
+__global__ void __launch_bounds__(256, 4) k_decide(const int32_t* __restrict__ rec_id, const int32_t* __restrict__ bin_start,
                          int b_lo, int b_hi, const int2* __restrict__ xy,
                          const uint8_t* __restrict__ heading, const uint8_t* __restrict__ goal,
                          const uint8_t* __restrict__ cell, const uint8_t* __restrict__ ocls,
@@ -737,7 +752,7 @@ void launch_decide(int n, const int32_t* rec_id, const int32_t* bin_start, int b
     int dev = 0, nsm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    max_blocks = (nsm > 0 ? nsm : 1) * 8;  // 8 blocks of 256 per SM (64 registers each)
+    max_blocks = (nsm > 0 ? nsm : 1) * 8;  // two rounds of the 4 blocks of 256 an SM holds (64 registers)
   }
   const int blocks = cdiv(n, 256) < max_blocks ? cdiv(n, 256) : max_blocks;
   k_decide<<<blocks, 256, 0, s>>>(rec_id, bin_start, b_lo, b_hi, xy, heading, goal, cell,

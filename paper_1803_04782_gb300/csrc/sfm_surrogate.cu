@@ -1071,12 +1071,12 @@ __global__ void k_sur_decide(const int32_t* __restrict__ rec_id, const int32_t* 
       for (int k = 0; k < 9; ++k) f[k] = Fsur[(size_t)ry[move_dy(k) + 1] * g.W + cx[move_dx(k) + 1]];
     }
     int32_t dd[9];
-    uint8_t cl[9], oc[9];
-    candidate_loads(g, cell, ocls, D, cx, ry, dd, cl, oc);
+    uint8_t oc[9];
+    candidate_loads(g, ocls, D, cx, ry, dd, oc);
 #pragma unroll
     for (int k = 0; k < 9; ++k) fmag = fmaxf(fmag, fabsf(f[k]));
     float margin, emag;
-    const int best = pick_move<true>(f, dd, cl, oc, okx, oky, heading[p], goal[p], beta, own,
+    const int best = pick_move<true>(f, dd, oc, okx, oky, heading[p], goal[p], beta, own,
                                      dirdot, &margin, &emag);
     choice[p] = (uint8_t)best;
     const bool fl = !(margin > margin_allowance(delta, emag, fmag));
@@ -1090,7 +1090,7 @@ __global__ void k_sur_decide(const int32_t* __restrict__ rec_id, const int32_t* 
       for (int k = 0; k < 9; ++k) {
         fb_dd[(size_t)i * 9 + k] = dd[k];
         const int xi = move_dx(k) + 1, yi = move_dy(k) + 1;
-        if (k == 0 || (okx[xi] && oky[yi] && cl[k] != kWall && oc[k] == 0)) mask |= 1u << k;
+        if (k == 0 || (okx[xi] && oky[yi] && dd[k] != kDWall && oc[k] == 0)) mask |= 1u << k;
       }
       fb_info[i] = mask | (uint32_t)heading[p] << 9 | (uint32_t)goal[p] << 16;
     }
@@ -1217,7 +1217,7 @@ __global__ void __launch_bounds__(kFbThreads, 1)
       const uint32_t info = fb_info[i];
       float f[9];
       int32_t dd[9];
-      uint8_t cl[9], oc[9];
+      uint8_t oc[9];
 #pragma unroll
       for (int k = 0; k < 9; ++k) {
         int tx, ty;
@@ -1225,11 +1225,10 @@ __global__ void __launch_bounds__(kFbThreads, 1)
                         wrap_coord(q.y + move_dy(k), g.H, g.py, ty);
         f[k] = ok ? Fs[(size_t)ty * g.W + tx] + acc[k] : 0.f;
         dd[k] = fb_dd[(size_t)i * 9 + k];
-        cl[k] = 0;
         oc[k] = (info >> k) & 1u ? 0 : 1;  // admissible iff its mask bit is set
       }
       const bool ok3[3] = {true, true, true};
-      choice[rec_id[i]] = (uint8_t)pick_move<false>(f, dd, cl, oc, ok3, ok3, (int)((info >> 9) & 15u),
+      choice[rec_id[i]] = (uint8_t)pick_move<false>(f, dd, oc, ok3, ok3, (int)((info >> 9) & 15u),
                                                     (int)((info >> 16) & 255u), beta, own, dirdot,
                                                     nullptr);
     }
