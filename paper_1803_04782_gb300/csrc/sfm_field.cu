@@ -247,6 +247,10 @@ static void launch_v2(const Geo& g, const int32_t* bin_start, const uint32_t* re
   int blocks = nf < 4 * wpb * g_num_sms ? nf : (nf + wpb - 1) / wpb;
   if (blocks > g_num_sms) blocks = g_num_sms;
   if (blocks < 1) blocks = 1;
+  // tickets only where there are whole rounds to rebalance (4 footprints per
+  // warp or more); a small lattice keeps the static deal, without the
+  // counter's atomics at the start and end of the launch
+  if (nf < 4 * wpb * blocks) tickets = nullptr;
   k_field_v2<SP, SHAPE, FAR><<<blocks, kV2Threads, smem, s>>>(g, bin_start, rec, CT, Fs, out, out_row0,
                                                          fy0, fy1, store_lo, store_hi, far,
                                                          tickets);
@@ -282,7 +286,8 @@ void launch_field(const Geo& g, const int32_t* bin_start, const uint32_t* rec, c
   // the context's footprint ticket counter (no counter: a static schedule).
   // The far-part gather keeps the static one: its footprints cost about the
   // same everywhere (a 7 x 7 window and the epilogue), and they are so short
-  // that one ticket each would queue on the counter.
+  // that one ticket each would queue on the counter.  So do lattices under 4
+  // footprints per warp (launch_v2).
   unsigned int* tickets = ctr && !far.Y ? ctr->field_tickets : nullptr;
   switch (sp) {
     case 34: launch_v2_shape<34>(g, bin_start, rec, tb, Fs, out, out_row0, store_lo, store_hi, s, far, tickets); break;
