@@ -12,7 +12,8 @@ sampled pedestrians (every one next to a band edge among them), teacher-forced
 from the GPU's state at the start of the tick, and, exactly and for the whole
 crowd, the vote and commit that the GPU's choices lead to.  Guidance is
 compared on every su.  The corridor is small enough for the whole field and
-every decision.
+every decision.  The learned surrogate is judged on the full floor as the
+bench runs it.
 """
 import numpy as np
 import pytest
@@ -174,3 +175,36 @@ def test_batch_of_256_rooms_full_size_tick_against_the_oracle():
             assert flips <= 3, f"scene {i}: {flips} tie flips"
             _check_vote_and_commit(m, sc, t, xy, hd, al, chs[i], wons[i],
                                    (after[0][i], after[1][i], after[2][i]))
+
+
+def test_surrogate_on_the_full_floor_meets_the_flip_target():
+    """The learned surrogate as bench.py runs it: trained on the GPU for 150
+    steps on the 4096^2 canvas, its margin bound calibrated on the 16384^2
+    floor (99.9th percentile), then judged there by the exact path after 3
+    more ticks.  With the exact fallback at most 0.1 % of the decisions may
+    differ from the exact ones, part of the crowd must be decided on the
+    surrogate alone, and the network must leave a smaller field error than
+    the near part without it."""
+    init = sfm.flatten_params(SG.surrogate_init(0))
+    canvas = SG.training_canvas(side=4096, r=40, seed=500)
+    with sfm.Sim(canvas) as tsim, \
+            sfm.Surrogate(coarsen=8, near_radius=3, target_scale=20.0, lr=2e-3, params=init) as sur:
+        curve = sur.train(tsim, 150)
+        trained = sur.get_params()
+    assert curve[-10:].mean() < 0.5 * curve[:3].mean()
+    sc, _ = bench.workload("floor")
+    with sfm.Sim(sc) as fsim:
+        fsim.step(5)
+        live = int(fsim.stats()["alive"])
+        evs = {}
+        for name, params in (("net", trained), ("near_only", 0 * init)):
+            with sfm.Surrogate(coarsen=8, near_radius=3, target_scale=20.0, params=params) as sur:
+                d = sur.calibrate(fsim, 0.999)
+                assert 0.0 < d < np.inf
+                fsim.step(3)
+                evs[name] = sur.eval(fsim)
+    ev = evs["net"]
+    assert ev["decided"] >= 0.99 * live, ev
+    assert ev["flip_rate"] <= 1e-3, ev
+    assert ev["fallback_rate"] < 1.0, ev
+    assert ev["field_rel_err"] < 0.5 * evs["near_only"]["field_rel_err"], evs
