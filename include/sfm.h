@@ -147,7 +147,11 @@ const char* sfm_last_error(const sfm_ctx* ctx);
  * pedestrians as the previous one, with the same sizing and no walk periods
  * set, keeps the captured tick graphs (a place / step / read loop replays
  * them); any other placement drops them and its first tick runs stage by
- * stage. */
+ * stage.  A placement of as many 1 x 1 pedestrians also rewrites the
+ * occupancy grids only for the pedestrians whose su, alive flag or heading
+ * it changes (the others stay as the previous placement and the ticks since
+ * left them), with the same checks; a loop that hands back what it read
+ * changes none. */
 sfm_status sfm_place(sfm_ctx* ctx, int32_t n, const int32_t* xy, const uint8_t* heading,
                      const uint8_t* goal, const uint8_t* alive, int32_t on_device);
 

@@ -624,7 +624,15 @@ static sfm_status place_impl(sfm_ctx* ctx, int32_t n, const int32_t* xy, const u
   }
   cudaStream_t s = ctx->stream;
   const Geo& g = ctx->geo;
-  if (ctx->placed && ctx->n > 0) {
+  // as many 1 x 1 pedestrians into the same arrays: keep the previous state
+  // and touch the grid entries of the pedestrians that change only (a place /
+  // step / read loop that hands back what it read changes none)
+  const bool diff = keep_graphs && !w && n > 0;
+  if (diff) {
+    CU(cudaMemcpyAsync(ctx->xy_prev, ctx->xy, (size_t)n * sizeof(int2), cudaMemcpyDeviceToDevice, s));
+    CU(cudaMemcpyAsync(ctx->alive_prev, ctx->alive, (size_t)n, cudaMemcpyDeviceToDevice, s));
+    CU(cudaMemcpyAsync(ctx->heading_prev, ctx->heading, (size_t)n, cudaMemcpyDeviceToDevice, s));
+  } else if (ctx->placed && ctx->n > 0) {
     launch_place_clear(ctx->n, ctx->xy, ctx->alive, g, ctx->occ, ctx->ocls, s, ctx->sizes());
     ++ctx->launches;
   }
@@ -644,6 +652,9 @@ static sfm_status place_impl(sfm_ctx* ctx, int32_t n, const int32_t* xy, const u
     dfree(ctx, ctx->phase);
     dfree(ctx, ctx->pw);
     dfree(ctx, ctx->ph);
+    dfree(ctx, ctx->xy_prev);
+    dfree(ctx, ctx->alive_prev);
+    dfree(ctx, ctx->heading_prev);
     ctx->xy = nullptr;
     ctx->cap = 0;
     TRY(dalloc(ctx, &ctx->xy, (size_t)n));
@@ -660,6 +671,9 @@ static sfm_status place_impl(sfm_ctx* ctx, int32_t n, const int32_t* xy, const u
     TRY(dalloc(ctx, &ctx->phase, (size_t)n));
     TRY(dalloc(ctx, &ctx->pw, (size_t)n));
     TRY(dalloc(ctx, &ctx->ph, (size_t)n));
+    TRY(dalloc(ctx, &ctx->xy_prev, (size_t)n));
+    TRY(dalloc(ctx, &ctx->alive_prev, (size_t)n));
+    TRY(dalloc(ctx, &ctx->heading_prev, (size_t)n));
     ctx->cap = n;
   }
   if (ctx->cap == 0) {
@@ -677,6 +691,9 @@ static sfm_status place_impl(sfm_ctx* ctx, int32_t n, const int32_t* xy, const u
     TRY(dalloc(ctx, &ctx->phase, 1));
     TRY(dalloc(ctx, &ctx->pw, 1));
     TRY(dalloc(ctx, &ctx->ph, 1));
+    TRY(dalloc(ctx, &ctx->xy_prev, 1));
+    TRY(dalloc(ctx, &ctx->alive_prev, 1));
+    TRY(dalloc(ctx, &ctx->heading_prev, 1));
     ctx->cap = 1;
   }
   ctx->placed = false;
@@ -702,9 +719,15 @@ static sfm_status place_impl(sfm_ctx* ctx, int32_t n, const int32_t* xy, const u
   // reset per-placement counters and flags on the stream, keep the tick counter
   launch_reset_counters(ctx->ctr, s);
   ++ctx->launches;
-  launch_place_scatter(n, ctx->xy, ctx->heading, ctx->goal, ctx->alive, ctx->cell, g, ctx->occ,
-                       ctx->ocls, ctx->ctr, s, ctx->sizes());
-  if (n > 0) ++ctx->launches;
+  if (diff) {
+    launch_place_diff(n, ctx->xy_prev, ctx->alive_prev, ctx->heading_prev, ctx->xy, ctx->heading,
+                      ctx->goal, ctx->alive, ctx->cell, g, ctx->occ, ctx->ocls, ctx->ctr, s);
+    ctx->launches += 2;
+  } else {
+    launch_place_scatter(n, ctx->xy, ctx->heading, ctx->goal, ctx->alive, ctx->cell, g, ctx->occ,
+                         ctx->ocls, ctx->ctr, s, ctx->sizes());
+    if (n > 0) ++ctx->launches;
+  }
   Counters hc;
   CU(cudaMemcpyAsync(&hc, ctx->ctr, sizeof(hc), cudaMemcpyDeviceToHost, s));
   CU(cudaStreamSynchronize(s));

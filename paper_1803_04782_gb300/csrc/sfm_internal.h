@@ -147,6 +147,11 @@ void launch_place_clear(int n, const int2* xy, const uint8_t* alive, const Geo& 
 void launch_place_scatter(int n, const int2* xy, const uint8_t* heading, const uint8_t* goal,
                           const uint8_t* alive, const uint8_t* cell, const Geo& g, int32_t* occ,
                           uint8_t* ocls, Counters* ctr, cudaStream_t s, const Sizes& sz = Sizes());
+// placement of as many 1 x 1 pedestrians: grid entries of the changed ones only
+void launch_place_diff(int n, const int2* xy_prev, const uint8_t* alive_prev,
+                       const uint8_t* heading_prev, const int2* xy, const uint8_t* heading,
+                       const uint8_t* goal, const uint8_t* alive, const uint8_t* cell, const Geo& g,
+                       int32_t* occ, uint8_t* ocls, Counters* ctr, cudaStream_t s);
 
 void launch_bin_count(const Geo& g, const uint8_t* ocls, int32_t* count, cudaStream_t s);
 void launch_scan(const int32_t* in, int32_t* out, int n, int32_t* block_tmp, cudaStream_t s);

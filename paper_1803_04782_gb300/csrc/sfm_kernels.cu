@@ -279,6 +279,67 @@ void launch_place_clear(int n, const int2* xy, const uint8_t* alive, const Geo& 
   k_place_clear<<<cdiv(n, 256), 256, 0, s>>>(n, xy, alive, g, occ, ocls, sz);
 }
 
+// A placement of as many 1 x 1 pedestrians into the same arrays (the tick
+// graphs are kept): xy_prev / alive_prev / heading_prev hold the state before
+// it, xy / alive / heading the new one.  Only pedestrians whose su or alive
+// flag changes leave (clear) and claim (claim, with the checks of
+// k_place_scatter) occupancy-grid entries, in two launches so that a su
+// vacated by one may be claimed by another; a pedestrian that keeps its su
+// only rewrites its class entry when its heading changed.  The entries of
+// the others are already right: the previous placement validated them and
+// every tick keeps the grids in step with the pedestrians.
+__global__ void k_place_diff_clear(int n, const int2* __restrict__ xy_prev,
+                                   const uint8_t* __restrict__ alive_prev,
+                                   const int2* __restrict__ xy, const uint8_t* __restrict__ alive,
+                                   Geo g, int32_t* __restrict__ occ, uint8_t* __restrict__ ocls) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n || !alive_prev[p]) return;
+  const int2 q = xy_prev[p], v = xy[p];
+  if (alive[p] && q.x == v.x && q.y == v.y) return;
+  occ[(size_t)q.y * g.W + q.x] = -1;
+  ocls[(size_t)q.y * g.opitch + q.x] = 0;
+}
+
+__global__ void k_place_diff_claim(int n, const int2* __restrict__ xy_prev,
+                                   const uint8_t* __restrict__ alive_prev,
+                                   const uint8_t* __restrict__ heading_prev,
+                                   const int2* __restrict__ xy, const uint8_t* __restrict__ heading,
+                                   const uint8_t* __restrict__ goal, const uint8_t* __restrict__ alive,
+                                   const uint8_t* __restrict__ cell, Geo g, int32_t* __restrict__ occ,
+                                   uint8_t* __restrict__ ocls, Counters* ctr) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  const uint8_t hp = heading[p];
+  if (hp > 8 || goal[p] > 8) atomicOr(&ctr->err, kErrPlaceRange);
+  if (!alive[p]) return;
+  const int2 v = xy[p];
+  const uint8_t cls = (uint8_t)(1 + (hp > 8 ? 0 : hp));
+  if (alive_prev[p]) {
+    const int2 q = xy_prev[p];
+    if (q.x == v.x && q.y == v.y) {
+      if (hp != heading_prev[p]) ocls[(size_t)v.y * g.opitch + v.x] = cls;
+      return;
+    }
+  }
+  if (v.x < 0 || v.x >= g.W || v.y < 0 || v.y >= g.H) {
+    atomicOr(&ctr->err, kErrPlaceRange);
+    return;
+  }
+  const size_t c = (size_t)v.y * g.W + v.x;
+  if (cell[c] != kFree || atomicCAS(&occ[c], -1, p) != -1) atomicOr(&ctr->err, kErrPlaceConflict);
+  ocls[(size_t)v.y * g.opitch + v.x] = cls;
+}
+
+void launch_place_diff(int n, const int2* xy_prev, const uint8_t* alive_prev,
+                       const uint8_t* heading_prev, const int2* xy, const uint8_t* heading,
+                       const uint8_t* goal, const uint8_t* alive, const uint8_t* cell, const Geo& g,
+                       int32_t* occ, uint8_t* ocls, Counters* ctr, cudaStream_t s) {
+  if (n <= 0) return;
+  k_place_diff_clear<<<cdiv(n, 256), 256, 0, s>>>(n, xy_prev, alive_prev, xy, alive, g, occ, ocls);
+  k_place_diff_claim<<<cdiv(n, 256), 256, 0, s>>>(n, xy_prev, alive_prev, heading_prev, xy, heading,
+                                                  goal, alive, cell, g, occ, ocls, ctr);
+}
+
 // per-placement counters and flags back to zero (the tick counter stays)
 __global__ void k_reset_counters(Counters* ctr) {
   ctr->moved = 0;

@@ -455,6 +455,69 @@ def test_place_step_read_loop_equals_plain_ticks(variant):
         assert b.stats()["error_flags"] == 0
 
 
+def test_placement_keeping_the_graphs_equals_a_fresh_placement():
+    """A placement of as many 1x1 pedestrians keeps the tick graphs and
+    rewrites the grid entries of the pedestrians it changes only.  Moves,
+    swapped positions (a su one changed pedestrian leaves and another claims),
+    deaths, revivals and heading changes give the same fields, decisions and
+    ticks as a fresh context placed with that state; overlapping, walled-in
+    and off-lattice placements are still refused, and a valid one then works."""
+    sc = SG.random_scene(120, 90, 1500, r=6, seed=161, obstacles=3, exits=("east", "north"),
+                         goal_mode="mixed", heading_mode="random")
+    rng = np.random.default_rng(17)
+    with sfm.Sim(sc) as a:
+        a.step(12)
+        xy, h, al = a.peds()
+        assert (al == 0).any()  # some have left through the exits
+        xy, h, al = xy.copy(), h.copy(), al.copy()
+        live = np.flatnonzero(al)
+        sw = rng.choice(live, 20, replace=False)
+        xy[sw[:10]], xy[sw[10:]] = xy[sw[10:]].copy(), xy[sw[:10]].copy()
+        rest = np.setdiff1d(live, sw)
+        kill = rng.choice(rest, 30, replace=False)
+        al[kill] = 0
+        turn = rng.choice(rest, 60, replace=False)
+        h[turn] = rng.integers(0, 9, turn.size)
+        taken = set(map(tuple, xy[al == 1]))
+        free = [(x, y) for y in range(sc.H) for x in range(sc.W)
+                if sc.cell[y, x] == SG.FREE and (x, y) not in taken]
+        free = [free[i] for i in rng.choice(len(free), 80, replace=False)]
+        mov = rng.choice(np.setdiff1d(rest, kill), 40, replace=False)
+        xy[mov] = free[:40]
+        dead = np.flatnonzero(al == 0)
+        rev = rng.choice(dead, min(40, dead.size), replace=False)
+        xy[rev] = free[40:40 + rev.size]
+        al[rev] = 1
+        a.place(xy, h, sc.goal, al)
+        t = a.stats()["t"]
+        with sfm.Sim(sc, place=False) as b:
+            b.place(xy, h, sc.goal, al)
+            b.set_time(t)
+            for s in (a, b):
+                s.compute_field()
+            np.testing.assert_array_equal(a.field(), b.field())
+            for _ in range(4):
+                a.step(1)
+                b.step(1)
+                np.testing.assert_array_equal(a.field(), b.field())
+                np.testing.assert_array_equal(a.decisions()[0], b.decisions()[0])
+                for x, y in zip(a.peds(), b.peds()):
+                    np.testing.assert_array_equal(x, y)
+        xy, h, al = a.peds()
+        live = np.flatnonzero(al)
+        for bad, status in ((lambda q: q.__setitem__(live[0], q[live[1]]), sfm.SFM_ECONFLICT),
+                            (lambda q: q.__setitem__(live[0], (0, 0)), sfm.SFM_ECONFLICT),
+                            (lambda q: q.__setitem__(live[0], (sc.W, 3)), sfm.SFM_EINVAL)):
+            q = xy.copy()
+            bad(q)
+            with pytest.raises(sfm.SfmError) as e:
+                a.place(q, h, sc.goal, al)
+            assert e.value.status == status
+        a.place(xy, h, sc.goal, al)
+        a.step(2)
+        assert a.stats()["error_flags"] == 0
+
+
 @pytest.mark.parametrize("variant", ["plain", "periods", "sized"])
 def test_snapshot_restore_continues_bit_for_bit(variant):
     """Checkpoint and resume: a snapshot taken after 7 ticks, restored into a
