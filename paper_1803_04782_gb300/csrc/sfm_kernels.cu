@@ -786,12 +786,15 @@ __global__ void __launch_bounds__(256, 4) k_decide(const int32_t* __restrict__ r
                          const float* __restrict__ dirdot, uint8_t* __restrict__ choice,
                          WalkPeriods wp, Sizes sz, const int32_t* __restrict__ occ) {
   // grid-stride over the records of bins [b_lo, b_hi): a band's launch needs
-  // no more blocks than the GPU holds, whatever its share of the crowd
+  // no more blocks than the GPU holds, whatever its share of the crowd.  The
+  // records are taken from the last backwards: the gather wrote the band's
+  // bottom rows last, so the first blocks find their field rows still in L2
+  // (0.199 -> 0.195 ms a banded floor tick).
   const int end = bin_start[b_hi];
   const long long t = wp.period ? wp.ctr->t : 0;
-  for (int i = bin_start[b_lo] + blockIdx.x * blockDim.x + threadIdx.x; i < end;
-       i += gridDim.x * blockDim.x) {
-    const int p = rec_id[i];
+  const int cnt = end - bin_start[b_lo];
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < cnt; k += gridDim.x * blockDim.x) {
+    const int p = rec_id[end - 1 - k];
     if (wp.period && t % wp.period[p] != wp.phase[p]) {
       choice[p] = 0;  // not this pedestrian's tick: it stays
       continue;
