@@ -151,7 +151,10 @@ const char* sfm_last_error(const sfm_ctx* ctx);
  * occupancy grids only for the pedestrians whose su, alive flag or heading
  * it changes (the others stay as the previous placement and the ticks since
  * left them), with the same checks; a loop that hands back what it read
- * changes none. */
+ * changes none.  When every array given is device memory or pinned host
+ * memory mapped into the device's address space (cudaHostAlloc,
+ * cudaMallocHost, cudaHostRegister), such a placement reads them in place,
+ * without copies; pageable host memory is copied in. */
 sfm_status sfm_place(sfm_ctx* ctx, int32_t n, const int32_t* xy, const uint8_t* heading,
                      const uint8_t* goal, const uint8_t* alive, int32_t on_device);
 
@@ -245,7 +248,10 @@ sfm_status sfm_read_static_field(sfm_ctx* ctx, float* dst, int32_t on_device);
 sfm_status sfm_read_guidance(sfm_ctx* ctx, int32_t* dst, int32_t on_device);
 
 /* Pedestrian state: xy (n pairs), heading classes, alive flags (each may be
- * NULL to skip). */
+ * NULL to skip).  on_device: the buffers are device memory (copied device to
+ * device); otherwise host memory: pinned host buffers mapped into the
+ * device's address space are written in place by one launch, pageable ones
+ * are copied out.  Synchronising. */
 sfm_status sfm_read_peds(sfm_ctx* ctx, int32_t* xy, uint8_t* heading, uint8_t* alive,
                          int32_t on_device);
 

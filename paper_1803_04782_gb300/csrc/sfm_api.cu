@@ -373,6 +373,21 @@ cudaError_t replay_timed_tick(sfm_ctx* c) {
   return cudaGraphLaunch(c->timed_graph, c->stream);
 }
 
+// Address under which the device reads or writes a caller's buffer in place:
+// the pointer itself for device memory, the mapped address of pinned host
+// memory (cudaHostAlloc / cudaMallocHost / cudaHostRegister with unified
+// addressing); NULL for pageable host memory, which is copied instead.
+void* device_view(const void* p, int on_device) {
+  if (!p) return nullptr;
+  if (on_device) return const_cast<void*>(p);
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();  // an unknown pointer: not an error of this context
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 sfm_status copy_out(sfm_ctx* ctx, void* dst, const void* src, size_t bytes, int on_device) {
   CU(cudaMemcpyAsync(dst, src, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                      ctx->stream));
@@ -624,14 +639,29 @@ static sfm_status place_impl(sfm_ctx* ctx, int32_t n, const int32_t* xy, const u
   }
   cudaStream_t s = ctx->stream;
   const Geo& g = ctx->geo;
-  // as many 1 x 1 pedestrians into the same arrays: keep the previous state
-  // and touch the grid entries of the pedestrians that change only (a place /
-  // step / read loop that hands back what it read changes none)
+  // as many 1 x 1 pedestrians into the same arrays: touch the grid entries of
+  // the pedestrians that change only (a place / step / read loop that hands
+  // back what it read changes none).  Buffers the device can read in place
+  // (device memory, mapped pinned host memory) are read by the placement
+  // kernels themselves; otherwise the previous state is kept and the new one
+  // copied in.
   const bool diff = keep_graphs && !w && n > 0;
+  const int2* src_xy = nullptr;
+  const uint8_t *src_h = nullptr, *src_g = nullptr, *src_a = nullptr;
+  bool direct = false;
   if (diff) {
-    CU(cudaMemcpyAsync(ctx->xy_prev, ctx->xy, (size_t)n * sizeof(int2), cudaMemcpyDeviceToDevice, s));
-    CU(cudaMemcpyAsync(ctx->alive_prev, ctx->alive, (size_t)n, cudaMemcpyDeviceToDevice, s));
-    CU(cudaMemcpyAsync(ctx->heading_prev, ctx->heading, (size_t)n, cudaMemcpyDeviceToDevice, s));
+    src_xy = static_cast<const int2*>(device_view(xy, on_device));
+    src_h = static_cast<const uint8_t*>(device_view(heading, on_device));
+    src_g = static_cast<const uint8_t*>(device_view(goal, on_device));
+    src_a = static_cast<const uint8_t*>(device_view(alive, on_device));
+    direct = src_xy && (!heading || src_h) && (!goal || src_g) && (!alive || src_a);
+  }
+  if (direct) {
+    // nothing to copy: the staging launch reads the caller's buffers
+  } else if (diff) {
+    CU(cudaMemcpyAsync(ctx->pl_xy, ctx->xy, (size_t)n * sizeof(int2), cudaMemcpyDeviceToDevice, s));
+    CU(cudaMemcpyAsync(ctx->pl_alive, ctx->alive, (size_t)n, cudaMemcpyDeviceToDevice, s));
+    CU(cudaMemcpyAsync(ctx->pl_heading, ctx->heading, (size_t)n, cudaMemcpyDeviceToDevice, s));
   } else if (ctx->placed && ctx->n > 0) {
     launch_place_clear(ctx->n, ctx->xy, ctx->alive, g, ctx->occ, ctx->ocls, s, ctx->sizes());
     ++ctx->launches;
@@ -652,9 +682,10 @@ static sfm_status place_impl(sfm_ctx* ctx, int32_t n, const int32_t* xy, const u
     dfree(ctx, ctx->phase);
     dfree(ctx, ctx->pw);
     dfree(ctx, ctx->ph);
-    dfree(ctx, ctx->xy_prev);
-    dfree(ctx, ctx->alive_prev);
-    dfree(ctx, ctx->heading_prev);
+    dfree(ctx, ctx->pl_xy);
+    dfree(ctx, ctx->pl_alive);
+    dfree(ctx, ctx->pl_heading);
+    dfree(ctx, ctx->pl_goal);
     ctx->xy = nullptr;
     ctx->cap = 0;
     TRY(dalloc(ctx, &ctx->xy, (size_t)n));
@@ -671,9 +702,10 @@ static sfm_status place_impl(sfm_ctx* ctx, int32_t n, const int32_t* xy, const u
     TRY(dalloc(ctx, &ctx->phase, (size_t)n));
     TRY(dalloc(ctx, &ctx->pw, (size_t)n));
     TRY(dalloc(ctx, &ctx->ph, (size_t)n));
-    TRY(dalloc(ctx, &ctx->xy_prev, (size_t)n));
-    TRY(dalloc(ctx, &ctx->alive_prev, (size_t)n));
-    TRY(dalloc(ctx, &ctx->heading_prev, (size_t)n));
+    TRY(dalloc(ctx, &ctx->pl_xy, (size_t)n));
+    TRY(dalloc(ctx, &ctx->pl_alive, (size_t)n));
+    TRY(dalloc(ctx, &ctx->pl_heading, (size_t)n));
+    TRY(dalloc(ctx, &ctx->pl_goal, (size_t)n));
     ctx->cap = n;
   }
   if (ctx->cap == 0) {
@@ -691,16 +723,17 @@ static sfm_status place_impl(sfm_ctx* ctx, int32_t n, const int32_t* xy, const u
     TRY(dalloc(ctx, &ctx->phase, 1));
     TRY(dalloc(ctx, &ctx->pw, 1));
     TRY(dalloc(ctx, &ctx->ph, 1));
-    TRY(dalloc(ctx, &ctx->xy_prev, 1));
-    TRY(dalloc(ctx, &ctx->alive_prev, 1));
-    TRY(dalloc(ctx, &ctx->heading_prev, 1));
+    TRY(dalloc(ctx, &ctx->pl_xy, 1));
+    TRY(dalloc(ctx, &ctx->pl_alive, 1));
+    TRY(dalloc(ctx, &ctx->pl_heading, 1));
+    TRY(dalloc(ctx, &ctx->pl_goal, 1));
     ctx->cap = 1;
   }
   ctx->placed = false;
   ctx->walk_periods = false;  // a placement starts with every pedestrian active
   ctx->n = n;
   const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-  if (n > 0) {
+  if (n > 0 && !direct) {
     CU(cudaMemcpyAsync(ctx->xy, xy, (size_t)n * sizeof(int2), kind, s));
     if (heading) CU(cudaMemcpyAsync(ctx->heading, heading, n, kind, s));
     else CU(cudaMemsetAsync(ctx->heading, 0, n, s));
@@ -719,8 +752,13 @@ static sfm_status place_impl(sfm_ctx* ctx, int32_t n, const int32_t* xy, const u
   // reset per-placement counters and flags on the stream, keep the tick counter
   launch_reset_counters(ctx->ctr, s);
   ++ctx->launches;
-  if (diff) {
-    launch_place_diff(n, ctx->xy_prev, ctx->alive_prev, ctx->heading_prev, ctx->xy, ctx->heading,
+  if (direct) {
+    launch_place_direct(n, src_xy, src_h, src_g, src_a, ctx->pl_xy, ctx->pl_heading, ctx->pl_goal,
+                        ctx->pl_alive, ctx->xy, ctx->heading, ctx->goal, ctx->alive, ctx->choice,
+                        ctx->won, ctx->cell, g, ctx->occ, ctx->ocls, ctx->ctr, s);
+    ctx->launches += 2;
+  } else if (diff) {
+    launch_place_diff(n, ctx->pl_xy, ctx->pl_alive, ctx->pl_heading, ctx->xy, ctx->heading,
                       ctx->goal, ctx->alive, ctx->cell, g, ctx->occ, ctx->ocls, ctx->ctr, s);
     ctx->launches += 2;
   } else {
@@ -990,7 +1028,15 @@ sfm_status sfm_read_peds(sfm_ctx* ctx, int32_t* xy, uint8_t* heading, uint8_t* a
   if (!ctx) return SFM_EINVAL;
   const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
   const size_t n = (size_t)ctx->n;
-  if (n) {
+  // pinned host buffers are written in place by one launch, without copies
+  void* dxy = on_device ? nullptr : device_view(xy, 0);
+  void* dh = on_device ? nullptr : device_view(heading, 0);
+  void* da = on_device ? nullptr : device_view(alive, 0);
+  if (n && (xy || heading || alive) && (!xy || dxy) && (!heading || dh) && (!alive || da)) {
+    launch_read_peds((int)n, ctx->xy, ctx->heading, ctx->alive, static_cast<int2*>(dxy),
+                     static_cast<uint8_t*>(dh), static_cast<uint8_t*>(da), ctx->stream);
+    ++ctx->launches;
+  } else if (n) {
     if (xy) CU(cudaMemcpyAsync(xy, ctx->xy, n * sizeof(int2), kind, ctx->stream));
     if (heading) CU(cudaMemcpyAsync(heading, ctx->heading, n, kind, ctx->stream));
     if (alive) CU(cudaMemcpyAsync(alive, ctx->alive, n, kind, ctx->stream));

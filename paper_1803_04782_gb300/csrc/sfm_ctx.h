@@ -63,9 +63,10 @@ struct sfm_ctx {
   uint8_t *period = nullptr, *phase = nullptr;  // walk periods (used when walk_periods)
   bool walk_periods = false;
   uint8_t *pw = nullptr, *ph = nullptr;  // multi-su pedestrians' widths / heights (when sized)
-  // the state before a placement that keeps the tick graphs (place_impl)
-  int2* xy_prev = nullptr;
-  uint8_t *alive_prev = nullptr, *heading_prev = nullptr;
+  // placement scratch (place_impl): the state before a placement that keeps
+  // the tick graphs, or the new state staged from the caller's buffers
+  int2* pl_xy = nullptr;
+  uint8_t *pl_alive = nullptr, *pl_heading = nullptr, *pl_goal = nullptr;
   bool sized = false;
   bool placed = false;
   int64_t t = 0;

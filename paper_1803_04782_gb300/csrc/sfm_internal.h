@@ -148,6 +148,15 @@ void launch_place_scatter(int n, const int2* xy, const uint8_t* heading, const u
                           const uint8_t* alive, const uint8_t* cell, const Geo& g, int32_t* occ,
                           uint8_t* ocls, Counters* ctr, cudaStream_t s, const Sizes& sz = Sizes());
 // placement of as many 1 x 1 pedestrians: grid entries of the changed ones only
+// (from the previous state kept in *_prev, or read in place from the caller's
+// device-visible buffers and staged in st_*)
+void launch_place_direct(int n, const int2* src_xy, const uint8_t* src_h, const uint8_t* src_g,
+                         const uint8_t* src_a, int2* st_xy, uint8_t* st_h, uint8_t* st_g,
+                         uint8_t* st_a, int2* xy, uint8_t* heading, uint8_t* goal, uint8_t* alive,
+                         uint8_t* choice, uint8_t* won, const uint8_t* cell, const Geo& g,
+                         int32_t* occ, uint8_t* ocls, Counters* ctr, cudaStream_t s);
+void launch_read_peds(int n, const int2* xy, const uint8_t* heading, const uint8_t* alive, int2* dxy,
+                      uint8_t* dh, uint8_t* da, cudaStream_t s);
 void launch_place_diff(int n, const int2* xy_prev, const uint8_t* alive_prev,
                        const uint8_t* heading_prev, const int2* xy, const uint8_t* heading,
                        const uint8_t* goal, const uint8_t* alive, const uint8_t* cell, const Geo& g,

@@ -330,6 +330,104 @@ __global__ void k_place_diff_claim(int n, const int2* __restrict__ xy_prev,
   ocls[(size_t)v.y * g.opitch + v.x] = cls;
 }
 
+// The same placement read in place from the caller's buffers (device memory
+// or pinned host memory mapped into the device's address space; a NULL
+// heading, goal or alive array stands for 0, 0, 1): the first launch stages
+// the new state in st_* and clears the su of the pedestrians that leave
+// theirs; the second claims the su of those that take a new one (the checks
+// of k_place_scatter), rewrites the class entry of those that turn in place,
+// and installs the new state with cleared decisions.
+__global__ void k_place_direct_stage(int n, const int2* __restrict__ src_xy,
+                                     const uint8_t* __restrict__ src_h,
+                                     const uint8_t* __restrict__ src_g,
+                                     const uint8_t* __restrict__ src_a, int2* __restrict__ st_xy,
+                                     uint8_t* __restrict__ st_h, uint8_t* __restrict__ st_g,
+                                     uint8_t* __restrict__ st_a, const int2* __restrict__ xy,
+                                     const uint8_t* __restrict__ alive, Geo g,
+                                     int32_t* __restrict__ occ, uint8_t* __restrict__ ocls) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  const int2 v = src_xy[p];
+  const uint8_t a = src_a ? src_a[p] : 1;
+  st_xy[p] = v;
+  st_h[p] = src_h ? src_h[p] : 0;
+  st_g[p] = src_g ? src_g[p] : 0;
+  st_a[p] = a;
+  if (!alive[p]) return;
+  const int2 q = xy[p];
+  if (a && q.x == v.x && q.y == v.y) return;
+  occ[(size_t)q.y * g.W + q.x] = -1;
+  ocls[(size_t)q.y * g.opitch + q.x] = 0;
+}
+
+__global__ void k_place_direct_claim(int n, const int2* __restrict__ st_xy,
+                                     const uint8_t* __restrict__ st_h,
+                                     const uint8_t* __restrict__ st_g,
+                                     const uint8_t* __restrict__ st_a, int2* __restrict__ xy,
+                                     uint8_t* __restrict__ heading, uint8_t* __restrict__ goal,
+                                     uint8_t* __restrict__ alive, uint8_t* __restrict__ choice,
+                                     uint8_t* __restrict__ won, const uint8_t* __restrict__ cell,
+                                     Geo g, int32_t* __restrict__ occ, uint8_t* __restrict__ ocls,
+                                     Counters* ctr) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  const int2 v = st_xy[p], q = xy[p];
+  const uint8_t hp = st_h[p], gp = st_g[p], ap = st_a[p], a_old = alive[p], h_old = heading[p];
+  xy[p] = v;
+  heading[p] = hp;
+  goal[p] = gp;
+  alive[p] = ap;
+  choice[p] = 0;
+  won[p] = 0;
+  if (hp > 8 || gp > 8) atomicOr(&ctr->err, kErrPlaceRange);
+  if (!ap) return;
+  const uint8_t cls = (uint8_t)(1 + (hp > 8 ? 0 : hp));
+  if (a_old && q.x == v.x && q.y == v.y) {
+    if (hp != h_old) ocls[(size_t)v.y * g.opitch + v.x] = cls;
+    return;
+  }
+  if (v.x < 0 || v.x >= g.W || v.y < 0 || v.y >= g.H) {
+    atomicOr(&ctr->err, kErrPlaceRange);
+    return;
+  }
+  const size_t c = (size_t)v.y * g.W + v.x;
+  if (cell[c] != kFree || atomicCAS(&occ[c], -1, p) != -1) atomicOr(&ctr->err, kErrPlaceConflict);
+  ocls[(size_t)v.y * g.opitch + v.x] = cls;
+}
+
+void launch_place_direct(int n, const int2* src_xy, const uint8_t* src_h, const uint8_t* src_g,
+                         const uint8_t* src_a, int2* st_xy, uint8_t* st_h, uint8_t* st_g,
+                         uint8_t* st_a, int2* xy, uint8_t* heading, uint8_t* goal, uint8_t* alive,
+                         uint8_t* choice, uint8_t* won, const uint8_t* cell, const Geo& g,
+                         int32_t* occ, uint8_t* ocls, Counters* ctr, cudaStream_t s) {
+  if (n <= 0) return;
+  // one pedestrian a thread: many small reads in flight move pinned host
+  // buffers faster than fewer, wider ones (measured: 4 a thread with 16-byte
+  // accesses slowed the read-back from 0.078 to 0.126 ms for 10^6)
+  k_place_direct_stage<<<cdiv(n, 256), 256, 0, s>>>(n, src_xy, src_h, src_g, src_a, st_xy, st_h, st_g,
+                                                    st_a, xy, alive, g, occ, ocls);
+  k_place_direct_claim<<<cdiv(n, 256), 256, 0, s>>>(n, st_xy, st_h, st_g, st_a, xy, heading, goal,
+                                                    alive, choice, won, cell, g, occ, ocls, ctr);
+}
+
+// Pedestrian state written in place into the caller's buffers (any may be
+// NULL; device memory or mapped pinned host memory), one pedestrian a thread.
+__global__ void k_read_peds(int n, const int2* __restrict__ xy, const uint8_t* __restrict__ heading,
+                            const uint8_t* __restrict__ alive, int2* __restrict__ dxy,
+                            uint8_t* __restrict__ dh, uint8_t* __restrict__ da) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  if (dxy) dxy[p] = xy[p];
+  if (dh) dh[p] = heading[p];
+  if (da) da[p] = alive[p];
+}
+
+void launch_read_peds(int n, const int2* xy, const uint8_t* heading, const uint8_t* alive, int2* dxy,
+                      uint8_t* dh, uint8_t* da, cudaStream_t s) {
+  if (n <= 0) return;
+  k_read_peds<<<cdiv(n, 256), 256, 0, s>>>(n, xy, heading, alive, dxy, dh, da);
+}
+
 void launch_place_diff(int n, const int2* xy_prev, const uint8_t* alive_prev,
                        const uint8_t* heading_prev, const int2* xy, const uint8_t* heading,
                        const uint8_t* goal, const uint8_t* alive, const uint8_t* cell, const Geo& g,

@@ -415,7 +415,7 @@ def test_timed_ticks_replay_the_same_ticks(banded, every):
         assert e.value.status == sfm.SFM_EINVAL
 
 
-@pytest.mark.parametrize("variant", ["plain", "sized", "periods"])
+@pytest.mark.parametrize("variant", ["plain", "sized", "periods", "pinned"])
 def test_place_step_read_loop_equals_plain_ticks(variant):
     """The end-to-end loop (place the crowd read back, step one tick, read)
     keeps the tick graphs across placements of as many pedestrians into the
@@ -439,11 +439,22 @@ def test_place_step_read_loop_equals_plain_ticks(variant):
                 put(s, sc.xy, sc.heading, np.ones(sc.n, np.uint8))
         a.step(3)
         b.step(3)  # builds b's graphs
+        if variant == "pinned":  # placed and read in place through pinned buffers (n = 3000 = 0 mod 4)
+            xy0, h0, a0 = b.peds()
+            hx, hh, hg, ha = _arrays_as("pinned", xy0, h0, sc.goal, a0)
         for tick in range(8):
             if variant == "periods" and tick == 4:
                 per, pha = SG.walk_periods(sc.n, 3)
                 for s in (a, b):
                     s.set_walk_periods(per, pha)
+            if variant == "pinned":
+                sfm.sfm_place(b.ctx, hx, hh, hg, ha)
+                a.step(1)
+                b.step(1)
+                sfm.sfm_read_peds(b.ctx, hx, hh, ha)
+                for x, y in zip(a.peds(), (hx, hh, ha)):
+                    np.testing.assert_array_equal(x, y.numpy())
+                continue
             xy, h, alive = b.peds()
             put(b, xy, h, alive)
             if variant == "periods" and tick >= 4:
@@ -455,15 +466,37 @@ def test_place_step_read_loop_equals_plain_ticks(variant):
         assert b.stats()["error_flags"] == 0
 
 
-def test_placement_keeping_the_graphs_equals_a_fresh_placement():
+def _arrays_as(kind, *arrays):
+    """NumPy arrays (pageable host memory), or torch tensors in pinned host
+    memory or on the GPU: the placement reads the last two in place.
+    "pinned_unaligned": pinned tensors one element into their allocation, so
+    that no buffer is aligned for the wide accesses."""
+    if kind == "numpy":
+        return [np.ascontiguousarray(a) for a in arrays]
+    import torch
+    ts = [torch.from_numpy(np.ascontiguousarray(a)) for a in arrays]
+    if kind == "pinned_unaligned":
+        out = []
+        for t in ts:
+            big = torch.empty((t.shape[0] + 1,) + tuple(t.shape[1:]), dtype=t.dtype).pin_memory()
+            big[1:] = t
+            out.append(big[1:])
+        return out
+    return [t.pin_memory() if kind == "pinned" else t.cuda() for t in ts]
+
+
+@pytest.mark.parametrize("src", ["numpy", "pinned", "pinned_unaligned", "device"])
+def test_placement_keeping_the_graphs_equals_a_fresh_placement(src):
     """A placement of as many 1x1 pedestrians keeps the tick graphs and
-    rewrites the grid entries of the pedestrians it changes only.  Moves,
-    swapped positions (a su one changed pedestrian leaves and another claims),
-    deaths, revivals and heading changes give the same fields, decisions and
-    ticks as a fresh context placed with that state; overlapping, walled-in
-    and off-lattice placements are still refused, and a valid one then works."""
-    sc = SG.random_scene(120, 90, 1500, r=6, seed=161, obstacles=3, exits=("east", "north"),
-                         goal_mode="mixed", heading_mode="random")
+    rewrites the grid entries of the pedestrians it changes only, whether it
+    copies pageable host arrays or reads pinned host or device buffers in
+    place.  Moves, swapped positions (a su one changed pedestrian leaves and
+    another claims), deaths, revivals and heading changes give the same
+    fields, decisions and ticks as a fresh context placed with that state;
+    overlapping, walled-in and off-lattice placements are still refused, and a
+    valid one then works."""
+    sc = SG.random_scene(120, 90, 1501, r=6, seed=161, obstacles=3, exits=("east", "north"),
+                         goal_mode="mixed", heading_mode="random")  # n = 1 (mod 4): a ragged quad
     rng = np.random.default_rng(17)
     with sfm.Sim(sc) as a:
         a.step(12)
@@ -488,7 +521,7 @@ def test_placement_keeping_the_graphs_equals_a_fresh_placement():
         rev = rng.choice(dead, min(40, dead.size), replace=False)
         xy[rev] = free[40:40 + rev.size]
         al[rev] = 1
-        a.place(xy, h, sc.goal, al)
+        a.place(*_arrays_as(src, xy, h, sc.goal, al))
         t = a.stats()["t"]
         with sfm.Sim(sc, place=False) as b:
             b.place(xy, h, sc.goal, al)
@@ -511,9 +544,10 @@ def test_placement_keeping_the_graphs_equals_a_fresh_placement():
             q = xy.copy()
             bad(q)
             with pytest.raises(sfm.SfmError) as e:
-                a.place(q, h, sc.goal, al)
+                a.place(*_arrays_as(src, q, h, sc.goal, al))
             assert e.value.status == status
-        a.place(xy, h, sc.goal, al)
+            a.place(xy, h, sc.goal, al)  # a valid placement after the refused one
+            a.place(*_arrays_as(src, xy, h, sc.goal, al))  # keeps the graphs again
         a.step(2)
         assert a.stats()["error_flags"] == 0
 
