@@ -280,24 +280,52 @@ void launch_place_clear(int n, const int2* xy, const uint8_t* alive, const Geo& 
 }
 
 // A placement of as many 1 x 1 pedestrians into the same arrays (the tick
-// graphs are kept): xy_prev / alive_prev / heading_prev hold the state before
-// it, xy / alive / heading the new one.  Only pedestrians whose su or alive
-// flag changes leave (clear) and claim (claim, with the checks of
-// k_place_scatter) occupancy-grid entries, in two launches so that a su
-// vacated by one may be claimed by another; a pedestrian that keeps its su
-// only rewrites its class entry when its heading changed.  The entries of
-// the others are already right: the previous placement validated them and
-// every tick keeps the grids in step with the pedestrians.
+// graphs are kept).  Only pedestrians whose su or alive flag changes leave
+// (leave_su) and claim (claim_su, with the checks of k_place_scatter)
+// occupancy-grid entries, in two launches so that a su vacated by one may be
+// claimed by another; a pedestrian that keeps its su only rewrites its class
+// entry when its heading changed.  The entries of the others are already
+// right: the previous placement validated them and every tick keeps the grids
+// in step with the pedestrians.
+
+// Pedestrian p, alive at q before the placement, is placed at v (alive: a):
+// frees q unless it stays there.
+__device__ __forceinline__ void leave_su(int2 q, int2 v, uint8_t a, const Geo& g,
+                                         int32_t* __restrict__ occ, uint8_t* __restrict__ ocls) {
+  if (a && q.x == v.x && q.y == v.y) return;
+  occ[(size_t)q.y * g.W + q.x] = -1;
+  ocls[(size_t)q.y * g.opitch + q.x] = 0;
+}
+
+// Live pedestrian p placed at v with heading hp; before the placement it was
+// at q (if a_old) with heading h_old.
+__device__ __forceinline__ void claim_su(int p, int2 v, uint8_t hp, bool a_old, int2 q,
+                                         uint8_t h_old, const uint8_t* __restrict__ cell,
+                                         const Geo& g, int32_t* __restrict__ occ,
+                                         uint8_t* __restrict__ ocls, Counters* ctr) {
+  const uint8_t cls = (uint8_t)(1 + (hp > 8 ? 0 : hp));
+  if (a_old && q.x == v.x && q.y == v.y) {
+    if (hp != h_old) ocls[(size_t)v.y * g.opitch + v.x] = cls;
+    return;
+  }
+  if (v.x < 0 || v.x >= g.W || v.y < 0 || v.y >= g.H) {
+    atomicOr(&ctr->err, kErrPlaceRange);
+    return;
+  }
+  const size_t c = (size_t)v.y * g.W + v.x;
+  if (cell[c] != kFree || atomicCAS(&occ[c], -1, p) != -1) atomicOr(&ctr->err, kErrPlaceConflict);
+  ocls[(size_t)v.y * g.opitch + v.x] = cls;
+}
+
+// From copies: xy_prev / alive_prev / heading_prev hold the state before the
+// placement, xy / heading / goal / alive the new one.
 __global__ void k_place_diff_clear(int n, const int2* __restrict__ xy_prev,
                                    const uint8_t* __restrict__ alive_prev,
                                    const int2* __restrict__ xy, const uint8_t* __restrict__ alive,
                                    Geo g, int32_t* __restrict__ occ, uint8_t* __restrict__ ocls) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= n || !alive_prev[p]) return;
-  const int2 q = xy_prev[p], v = xy[p];
-  if (alive[p] && q.x == v.x && q.y == v.y) return;
-  occ[(size_t)q.y * g.W + q.x] = -1;
-  ocls[(size_t)q.y * g.opitch + q.x] = 0;
+  leave_su(xy_prev[p], xy[p], alive[p], g, occ, ocls);
 }
 
 __global__ void k_place_diff_claim(int n, const int2* __restrict__ xy_prev,
@@ -312,22 +340,7 @@ __global__ void k_place_diff_claim(int n, const int2* __restrict__ xy_prev,
   const uint8_t hp = heading[p];
   if (hp > 8 || goal[p] > 8) atomicOr(&ctr->err, kErrPlaceRange);
   if (!alive[p]) return;
-  const int2 v = xy[p];
-  const uint8_t cls = (uint8_t)(1 + (hp > 8 ? 0 : hp));
-  if (alive_prev[p]) {
-    const int2 q = xy_prev[p];
-    if (q.x == v.x && q.y == v.y) {
-      if (hp != heading_prev[p]) ocls[(size_t)v.y * g.opitch + v.x] = cls;
-      return;
-    }
-  }
-  if (v.x < 0 || v.x >= g.W || v.y < 0 || v.y >= g.H) {
-    atomicOr(&ctr->err, kErrPlaceRange);
-    return;
-  }
-  const size_t c = (size_t)v.y * g.W + v.x;
-  if (cell[c] != kFree || atomicCAS(&occ[c], -1, p) != -1) atomicOr(&ctr->err, kErrPlaceConflict);
-  ocls[(size_t)v.y * g.opitch + v.x] = cls;
+  claim_su(p, xy[p], hp, alive_prev[p] != 0, xy_prev[p], heading_prev[p], cell, g, occ, ocls, ctr);
 }
 
 // The same placement read in place from the caller's buffers (device memory
@@ -353,11 +366,7 @@ __global__ void k_place_direct_stage(int n, const int2* __restrict__ src_xy,
   st_h[p] = src_h ? src_h[p] : 0;
   st_g[p] = src_g ? src_g[p] : 0;
   st_a[p] = a;
-  if (!alive[p]) return;
-  const int2 q = xy[p];
-  if (a && q.x == v.x && q.y == v.y) return;
-  occ[(size_t)q.y * g.W + q.x] = -1;
-  ocls[(size_t)q.y * g.opitch + q.x] = 0;
+  if (alive[p]) leave_su(xy[p], v, a, g, occ, ocls);
 }
 
 __global__ void k_place_direct_claim(int n, const int2* __restrict__ st_xy,
@@ -380,19 +389,7 @@ __global__ void k_place_direct_claim(int n, const int2* __restrict__ st_xy,
   choice[p] = 0;
   won[p] = 0;
   if (hp > 8 || gp > 8) atomicOr(&ctr->err, kErrPlaceRange);
-  if (!ap) return;
-  const uint8_t cls = (uint8_t)(1 + (hp > 8 ? 0 : hp));
-  if (a_old && q.x == v.x && q.y == v.y) {
-    if (hp != h_old) ocls[(size_t)v.y * g.opitch + v.x] = cls;
-    return;
-  }
-  if (v.x < 0 || v.x >= g.W || v.y < 0 || v.y >= g.H) {
-    atomicOr(&ctr->err, kErrPlaceRange);
-    return;
-  }
-  const size_t c = (size_t)v.y * g.W + v.x;
-  if (cell[c] != kFree || atomicCAS(&occ[c], -1, p) != -1) atomicOr(&ctr->err, kErrPlaceConflict);
-  ocls[(size_t)v.y * g.opitch + v.x] = cls;
+  if (ap) claim_su(p, v, hp, a_old != 0, q, h_old, cell, g, occ, ocls, ctr);
 }
 
 void launch_place_direct(int n, const int2* src_xy, const uint8_t* src_h, const uint8_t* src_g,
