@@ -84,6 +84,13 @@ def workload(name: str):
     return sc, desc
 
 
+def default_bands(workload: str) -> int:
+    """Row bands of the field pass when --bands is not given: the floor's
+    divide-and-conquer blocking is part of its workload (at least 4 bands);
+    the corridor's and the room's fields (0.8 MB and 40 KB) are not banded."""
+    return 4 if workload.startswith("floor") else 1
+
+
 def band_budget(sc, bands: int) -> int:
     """HBM budget that leaves room for about H/bands field rows."""
     import paper_1803_04782_gb300 as sfm
@@ -276,7 +283,7 @@ def run_gpu(args):
     sfm.lib()
 
     sc, desc = workload(args.workload)
-    bands = args.bands
+    bands = args.bands if args.bands is not None else default_bands(args.workload)
     budget = band_budget(sc, bands)
     stream = torch.cuda.current_stream()
     sim = sfm.Sim(sc, stream=stream, hbm_budget_bytes=budget)
@@ -807,7 +814,7 @@ def main():
                              "surrogate", "surrogate-eval", "surrogate-eval-small", "surrogate-eval-mid",
                              "paper-windows", "paper-periods",
                              "paper-sizes"])
-    ap.add_argument("--bands", type=int, default=4,
+    ap.add_argument("--bands", type=int, default=None,
                     help="row bands of the divide-and-conquer field pass (1 = unbanded)")
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--footprint", default="auto", choices=["auto", "16x16", "32x16"],

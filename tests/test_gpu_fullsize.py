@@ -1,10 +1,10 @@
 """CUDA path vs FP64 oracle at the benchmark's full sizes (GPU).
 
 The workloads and the launch configuration are the ones bench.py times: the
-16384 x 16384 floor (10^6 exit-seekers, r = 40) and the 1000 x 200 corridor
-(20 000 walkers, r = 20), each with the bench's band budget (4 row bands),
-the autotuned footprint and graph-replayed ticks with stage events on every
-9th tick; and the batch of 256 uneven rooms stepped by one persistent launch
+16384 x 16384 floor (10^6 exit-seekers, r = 40) in 4 row bands and the
+1000 x 200 corridor (20 000 walkers, r = 20) unbanded, as the bench's band
+budget sets them, each with the autotuned footprint and graph-replayed ticks
+with stage events on every 9th tick; and the batch of 256 uneven rooms stepped by one persistent launch
 per tick.  The oracle cannot redo a whole 16384^2 lattice in seconds, so on
 the floor and the batch it checks what it can compute one output at a time:
 the field at sampled su (every band-edge row among them), the decisions of
@@ -39,7 +39,7 @@ def _built():
 def _bench_sim(name):
     """A context in the configuration bench.py times for workload `name`."""
     sc, _ = bench.workload(name)
-    sim = sfm.Sim(sc, hbm_budget_bytes=bench.band_budget(sc, 4))
+    sim = sfm.Sim(sc, hbm_budget_bytes=bench.band_budget(sc, bench.default_bands(name)))
     sim.autotune()
     sim.set_timing(bench.TIMING_EVERY)
     sim.step(WARM_TICKS)
@@ -114,7 +114,7 @@ def test_corridor_full_size_ticks_against_the_oracle():
     sc, sim = _bench_sim("corridor")
     with sim:
         st = sim.stats()
-        assert st["bands"] >= 4 and st["n"] == 20000
+        assert st["bands"] == 1 and st["n"] == 20000
         m = O.model(sc)
         D = O.guidance(m, sc.cell)
         flips = 0
