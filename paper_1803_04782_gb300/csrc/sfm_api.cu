@@ -157,16 +157,18 @@ bool bins_from_peds(const sfm_ctx* c) {
 void run_bins(sfm_ctx* c) {
   StageScope sc(c, SFM_STAGE_BIN);
   const Geo& g = c->geo;
+  // the bin scan: three passes, or one when a block covers every bin
+  const int scan_launches = scan_tmp_elems(g.nbx * g.nby) == 1 ? 1 : 3;
   if (bins_from_peds(c)) {
     launch_bins_from_peds(g, c->n, c->xy, c->alive, c->heading, c->bin_count, c->bin_start,
                           c->scan_tmp, c->bin_slot, c->bin_key, c->rec, c->rec_id, c->stream);
-    c->launches += c->n > 0 ? 6 : 3;  // count, three scan passes, scatter, rank
+    c->launches += (c->n > 0 ? 3 : 0) + scan_launches;  // count, scan, scatter, rank
     return;
   }
   launch_bin_count(g, c->ocls, c->bin_count, c->stream);
   launch_scan(c->bin_count, c->bin_start, g.nbx * g.nby, c->scan_tmp, c->stream);
   launch_bin_fill(g, c->ocls, c->occ, c->bin_start, c->rec, c->rec_id, c->stream);
-  c->launches += 5;  // count, three scan passes, fill
+  c->launches += 2 + scan_launches;  // count, scan, fill
 }
 
 void run_tick(sfm_ctx* c) {

@@ -562,7 +562,8 @@ void launch_clear_dead(int n, const uint8_t* alive, uint8_t* choice, uint8_t* wo
 
 // ------------------------------------------------------------------ scan
 // Exclusive prefix sum of n int32 into out[0..n] (out[n] = total), three
-// passes: per-block totals, a single-block scan of the totals, final.
+// passes: per-block totals, a single-block scan of the totals, final; one
+// pass (the final one, from offset 0) when a block covers all n.
 constexpr int kScanThreads = 1024, kScanItems = 4, kScanChunk = kScanThreads * kScanItems;
 
 __device__ int block_exclusive_scan(int v, int* sWarp, int& total) {
@@ -638,7 +639,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_final(const int32_t* __re
     s += v[k];
   }
   int total;
-  int e = block_exclusive_scan(s, sWarp, total) + offs[blockIdx.x];
+  int e = block_exclusive_scan(s, sWarp, total) + (offs ? offs[blockIdx.x] : 0);
 #pragma unroll
   for (int k = 0; k < kScanItems; ++k) {
     if (i0 + k < n) out[i0 + k] = e;
@@ -651,6 +652,10 @@ int scan_tmp_elems(int n) { return cdiv(n > 0 ? n : 1, kScanChunk); }
 
 void launch_scan(const int32_t* in, int32_t* out, int n, int32_t* block_tmp, cudaStream_t s) {
   const int nb = scan_tmp_elems(n);
+  if (nb == 1) {  // small lattices: one launch instead of three
+    k_scan_final<<<1, kScanThreads, 0, s>>>(in, n, nullptr, out);
+    return;
+  }
   k_scan_totals<<<nb, kScanThreads, 0, s>>>(in, n, block_tmp);
   k_scan_top<<<1, kScanThreads, 0, s>>>(block_tmp, nb);
   k_scan_final<<<nb, kScanThreads, 0, s>>>(in, n, block_tmp, out);
