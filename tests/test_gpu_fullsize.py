@@ -36,13 +36,14 @@ def _built():
     sfm.lib()
 
 
-def _bench_sim(name):
+def _bench_sim(name, warm=WARM_TICKS):
     """A context in the configuration bench.py times for workload `name`."""
     sc, _ = bench.workload(name)
     sim = sfm.Sim(sc, hbm_budget_bytes=bench.band_budget(sc, bench.default_bands(name)))
     sim.autotune()
     sim.set_timing(bench.TIMING_EVERY)
-    sim.step(WARM_TICKS)
+    if warm:
+        sim.step(warm)
     sim.sync()
     return sc, sim
 
@@ -66,8 +67,10 @@ def _edge_rows(H, rows_per_band):
     return np.array(sorted(v for v in e if 0 <= v < H))
 
 
-def test_floor_16384_full_size_tick_against_the_oracle():
-    sc, sim = _bench_sim("floor")
+def test_floor_16384_full_size_ticks_against_the_oracle():
+    """Checked at ticks 0 (run stage by stage, the first after the
+    placement), 6 and 60 (replayed from graphs)."""
+    sc, sim = _bench_sim("floor", warm=0)
     with sim:
         st = sim.stats()
         assert st["bands"] >= 4 and st["n"] == 1_000_000
@@ -76,38 +79,44 @@ def test_floor_16384_full_size_tick_against_the_oracle():
         m = O.model(sc)
         D = O.guidance(m, sc.cell)
         np.testing.assert_array_equal(sim.guidance(), D)
-        xy, hd, al = sim.peds()
-        t = st["t"]
-        assert t == WARM_TICKS
-        F = sim.field_banded()  # the field of this state, band by band
-        occ, bad = O.occupancy(m, sc.cell, xy, al)
-        assert bad == 0
-        # sampled su: uniform, every band-edge row (and the lattice's first and
-        # last rows) at random columns, and EXIT su
         rng = np.random.default_rng(31)
         W, H = sc.W, sc.H
         edges = _edge_rows(H, band_rows)
-        req = [rng.integers(0, W * H, 16384),
-               (edges[:, None] * W + rng.integers(0, W, (edges.size, 512))).ravel(),
-               rng.choice(np.flatnonzero(sc.cell.ravel() == SG.EXIT), 512, replace=False)]
-        req = np.unique(np.concatenate(req)).astype(np.int64)
-        Fo, So = O.field(m, sc.cell, occ, hd, 3, req)
-        assert_field(F.ravel()[req], Fo, So, "floor field (sampled su)")
-        # one graph-replayed tick from this state
-        sim.step(1)
-        ch, won = sim.decisions()
-        after = sim.peds()
-        live = np.flatnonzero(al)
-        near_edge = live[np.isin(xy[live, 1], edges)]
-        peds = np.unique(np.concatenate([rng.choice(live, 20000, replace=False), near_edge]))
-        peds = peds.astype(np.int32)
-        ch_o, E, T, adm = O.decide(m, sc.cell, occ, xy, hd, sc.goal, al, D, peds)
-        flips = compare_choices(ch[peds], ch_o, E, T, adm)
-        assert flips <= 3, f"{flips} tie flips in {peds.size} sampled decisions"
-        _check_vote_and_commit(m, sc, t, xy, hd, al, ch, won, after)
-        s = sim.stats()
-        assert s["error_flags"] == 0 and s["max_registrants"] <= 8
-        assert s["alive"] + s["exited"] == sc.n
+        exits = np.flatnonzero(sc.cell.ravel() == SG.EXIT)
+        done = 0
+        for tick in (0, WARM_TICKS, 60):
+            if tick > done:
+                sim.step(tick - done)
+            xy, hd, al = sim.peds()
+            t = sim.stats()["t"]
+            assert t == tick
+            F = sim.field_banded()  # the field of this state, band by band
+            occ, bad = O.occupancy(m, sc.cell, xy, al)
+            assert bad == 0
+            # sampled su: uniform, every band-edge row (and the lattice's first
+            # and last rows) at random columns, and EXIT su
+            req = [rng.integers(0, W * H, 16384),
+                   (edges[:, None] * W + rng.integers(0, W, (edges.size, 512))).ravel(),
+                   rng.choice(exits, 512, replace=False)]
+            req = np.unique(np.concatenate(req)).astype(np.int64)
+            Fo, So = O.field(m, sc.cell, occ, hd, 3, req)
+            assert_field(F.ravel()[req], Fo, So, f"floor field at tick {tick} (sampled su)")
+            # one tick from this state
+            sim.step(1)
+            done = tick + 1
+            ch, won = sim.decisions()
+            after = sim.peds()
+            live = np.flatnonzero(al)
+            near_edge = live[np.isin(xy[live, 1], edges)]
+            peds = np.unique(np.concatenate([rng.choice(live, 20000, replace=False), near_edge]))
+            peds = peds.astype(np.int32)
+            ch_o, E, T, adm = O.decide(m, sc.cell, occ, xy, hd, sc.goal, al, D, peds)
+            flips = compare_choices(ch[peds], ch_o, E, T, adm)
+            assert flips <= 3, f"tick {tick}: {flips} tie flips in {peds.size} sampled decisions"
+            _check_vote_and_commit(m, sc, t, xy, hd, al, ch, won, after)
+            s = sim.stats()
+            assert s["error_flags"] == 0 and s["max_registrants"] <= 8
+            assert s["alive"] + s["exited"] == sc.n
 
 
 def test_corridor_full_size_ticks_against_the_oracle():
