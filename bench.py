@@ -27,8 +27,13 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
-SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
-FLOPS_PER_PAIR = 6.0  # three FP32 multiply-adds per (su, pedestrian-in-window) pair
+FP32_LANES = 128      # FP32 lanes per SM (Blackwell)
+SMEM_WORDS = 32       # shared-memory banks per SM: one 4-byte word each per clock
+NOMINAL_SM_MHZ = 2070.0
+# algorithmic work of one (su, pedestrian-in-window) pair in the 3-channel
+# kernel-table formulation: three FP32 multiply-adds; the class-table gather
+# executes one FP32 add per pair instead
+FLOPS_PER_PAIR = 6.0
 # stage events on every 9th tick of the timed region: an event record costs a
 # few microseconds of GPU time (the stream drains before it), so recording all
 # stages of every tick would add about 7 % to a floor tick; the 8 ticks in
@@ -181,12 +186,57 @@ def peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
+def sm_count(torch, dev) -> int:
+    """Streaming multiprocessors of the device (its attribute, not a constant)."""
+    return int(torch.cuda.get_device_properties(dev).multi_processor_count)
+
+
+def max_sm_mhz(clk, pk):
+    """The maximum SM clock: as nvidia-smi reported it during the timed
+    region, else the measured peaks file's, else the nominal 2070."""
+    if clk.get("sm_max_mhz"):
+        return float(clk["sm_max_mhz"]), "nvidia-smi clocks.max.sm during the run"
+    if pk.get("sm_max_mhz"):
+        return float(pk["sm_max_mhz"]), "MEASURED_PEAKS.json sm_max_mhz"
+    return NOMINAL_SM_MHZ, "nominal maximum"
+
+
+def gather_roofline(pairs, field_s, nsm, mhz, mhz_src, kernel, traffic=None):
+    """Roofline of the class-table field gather for `pairs` (su, pedestrian)
+    pairs computed in `field_s` seconds.  Each pair costs one table word read
+    from shared memory, and the shared-memory pipe (32 banks x 4 bytes per
+    clock per SM) is the resource that binds it; the survey's algorithmic
+    FP32 figure (6 flops per pair) and the FP32 actually executed (1 add per
+    pair) are given beside it."""
+    words = pairs / field_s
+    smem_peak = nsm * SMEM_WORDS * mhz * 1e6
+    fp32_peak = nsm * FP32_LANES * 2 * mhz * 1e6
+    return {"bound": "smem", "achieved": words / 1e12, "peak": smem_peak / 1e12,
+            "unit": "T table words/s (shared memory, one 4-byte word per pair)",
+            "frac": words / smem_peak, "traffic": traffic, "traffic_unit": "bytes per launch",
+            "kernel": kernel, "field_ms_per_step": 1e3 * field_s, "pairs_per_step": pairs,
+            "peak_basis": f"{nsm} SMs (device attribute) x {SMEM_WORDS} banks x 4 B per clock "
+                          f"x {mhz:.0f} MHz ({mhz_src}); derived from unit counts, not measured",
+            "algorithmic_fp32": {"flops_per_pair": FLOPS_PER_PAIR,
+                                 "achieved_tflops": FLOPS_PER_PAIR * words / 1e12,
+                                 "peak_tflops": fp32_peak / 1e12,
+                                 "frac": FLOPS_PER_PAIR * words / fp32_peak,
+                                 "basis": "3 FP32 multiply-adds per pair of the 3-channel table "
+                                          "formulation (algorithmic work, not executed)"},
+            "fp32_executed": {"flops_per_pair": 1.0, "achieved_tflops": words / 1e12,
+                              "frac": words / fp32_peak,
+                              "basis": "the gather adds one precomputed class-table word per pair"}}
+
+
 # ------------------------------------------------------------------ oracle
 def oracle_sample(sc, D, xy, heading, goal, alive, n_sample, t, seed=0):
-    """Time the oracle's tick on a bounded sample: the decision of n_sample
-    random pedestrians (field evaluated at their 9 candidates, as the oracle's
-    tick does) scaled to all live pedestrians, plus the vote and commit of the
-    whole crowd.  Returns (estimated seconds per tick, threads)."""
+    """One bounded sample of the oracle's tick, timed as it runs: n_sample
+    random live pedestrians decide (the oracle evaluates the field by direct
+    superposition at their 9 candidates only; it never builds the lattice
+    field the GPU path writes), then vote and commit, every other pedestrian
+    staying for this sample.  The state arrays are advanced in place.
+    Returns (seconds spent, threads, pedestrians decided, live pedestrians,
+    seconds of the decisions alone)."""
     import oracle as O
     m = O.model(sc)
     occ, _ = O.occupancy(m, sc.cell, xy, alive)
@@ -201,8 +251,21 @@ def oracle_sample(sc, D, xy, heading, goal, alive, n_sample, t, seed=0):
     won, _ = O.vote(m, t, xy, alive, choice)
     O.commit(m, sc.cell, xy, heading, alive, choice, won)
     t2 = time.perf_counter()
-    per_tick = (t1 - t0) * (live.size / max(1, req.size)) + (t2 - t1)
-    return per_tick, O.threads(), req.size
+    return t2 - t0, O.threads(), int(req.size), int(live.size), t1 - t0
+
+
+def oracle_sample_desc(n_sample):
+    return (f"per step: {n_sample} random live pedestrians decide (the oracle evaluates the "
+            f"field by direct FP64 superposition at their 9 candidates only, not on the "
+            f"lattice), vote and commit; the rest of the crowd stays for that step")
+
+
+def workload_config(args, sc, desc):
+    """The workload's description, identical in both arms."""
+    return {"workload": desc, "W": sc.W, "H": sc.H, "n": sc.n, "r": int(sc.params["r"]),
+            "bands": args.bands if args.bands is not None else default_bands(args.workload),
+            "l2": "inputs larger than L2 (the field alone is 4*W*H bytes)"
+            if sc.W * sc.H * 4 > 129e6 else "inputs smaller than L2"}
 
 
 def reduce_over_ranks(dist, seconds, units, device="cpu"):
@@ -239,23 +302,35 @@ def run_reference(args):
     n_sample = args.ref_sample
     for w in range(args.warmup):
         oracle_sample(sc, D, xy, heading, goal, alive, n_sample, w)
-    est = []
-    peds = []
+    secs, dec_secs, decided, lives = [], [], [], []
+    thr = 0
     for k in range(args.steps):
-        s, thr, ns = oracle_sample(sc, D, xy, heading, goal, alive, n_sample, args.warmup + k)
-        est.append(s)
-        peds.append(int(alive.sum()))
-    tot = sum(est)
-    value = sum(peds) / tot
+        s, thr, ns, nl, sd = oracle_sample(sc, D, xy, heading, goal, alive, n_sample,
+                                           args.warmup + k)
+        secs.append(s)
+        dec_secs.append(sd)
+        decided.append(ns)
+        lives.append(nl)
+    tot = sum(secs)
+    # value: pedestrian-steps the oracle actually advanced per second it ran
+    value = sum(decided) / tot
+    frac = sum(decided) / max(1, sum(lives))
     line = {
         "impl": "reference", "metric": "pedestrian-steps/s", "value": value,
         "unit": "ped-steps/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": desc, "W": sc.W, "H": sc.H, "n": sc.n, "r": int(sc.params["r"])},
+        "config": workload_config(args, sc, desc),
+        "parallelism": "CPU oracle, rank 0 only",
         "cpu_baseline": {"value": value, "unit": "ped-steps/s", "cores": thr, "kind": "oracle",
-                         "sample": f"per tick: decision of {n_sample} random live pedestrians "
-                                   f"scaled to the live crowd, plus vote and commit of all"},
+                         "sample": oracle_sample_desc(n_sample),
+                         "sample_peds_per_step": n_sample,
+                         "sample_fraction_of_live_crowd": frac,
+                         "seconds_timed": tot,
+                         "seconds_deciding": sum(dec_secs)},
+        # what a whole tick of the live crowd would take at the sample's
+        # decision rate: an extrapolation, not a measurement
+        "full_tick_s_extrapolated": (sum(dec_secs) / frac + (tot - sum(dec_secs))) / args.steps,
         "e2e": {"value": value, "unit": "ped-steps/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -281,6 +356,7 @@ def run_gpu(args):
     torch.cuda.set_device(local)
     B.build()
     sfm.lib()
+    nsm = sm_count(torch, local)
 
     sc, desc = workload(args.workload)
     bands = args.bands if args.bands is not None else default_bands(args.workload)
@@ -307,7 +383,8 @@ def run_gpu(args):
     xy0, h0, a0 = sim.peds()
     pairs0 = pair_count(sc, xy0, a0)
     alive0 = int(a0.sum())
-    launches0 = sim.stats()["kernel_launches"]
+    stw = sim.stats()
+    launches0 = stw["kernel_launches"]
 
     # timed region: K ticks replayed as graphs; every TIMING_EVERY-th of them
     # (the first included) replays the one-tick graph whose stage events are
@@ -353,25 +430,20 @@ def run_gpu(args):
     pairs1 = pair_count(sc, xy1, a1)
     alive1 = int(a1.sum())
     launches = st1["kernel_launches"] - launches0
+    # decisions of the timed ticks and the near ties among them
+    decided = st1["decided"] - stw["decided"]
+    near_ties = st1["near_ties"] - stw["near_ties"]
     ped_steps = 0.5 * (alive0 + alive1) * args.steps
     elapsed, ped_steps = reduce_over_ranks(dist, elapsed, ped_steps, "cuda")
 
     # roofline of the dominant kernel: the field gather
+    pk, pk_src = peaks()
+    mhz, mhz_src = max_sm_mhz(clk, pk)
     field_s = stage_ms["field"] / 1e3  # over the `ticks` timed ticks
     pairs = 0.5 * (pairs0 + pairs1)
-    achieved = FLOPS_PER_PAIR * pairs * ticks / field_s / 1e12
-    peak = SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": gather_traffic(args.workload, st1["bands"], footprint),
-                "traffic_unit": "bytes per launch",
-                "kernel": "k_field_v2", "field_ms_per_step": 1e3 * field_s / ticks,
-                "timed_ticks": ticks,
-                "pairs_per_step": pairs,
-                "peak_basis": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz (max clock)",
-                # the gather's binding resource: one 128-byte shared-memory
-                # wavefront (32 table words) per clock per SM, one word a pair
-                "smem_pair_frac": pairs * ticks / field_s / (SMS * 32 * SM_MAX_MHZ * 1e6),
-                "smem_basis": "pairs/s over 152 SMs x 32 table words x 2070 MHz"}
+    roofline = gather_roofline(pairs, field_s / ticks, nsm, mhz, mhz_src, "k_field_v2",
+                               gather_traffic(args.workload, st1["bands"], footprint))
+    roofline["timed_ticks"] = ticks
 
     # end to end through the C ABI with host buffers
     e2e_steps = min(args.steps, args.e2e_steps)
@@ -410,24 +482,27 @@ def run_gpu(args):
         O.build()
         m = O.model(sc)
         D = O.guidance(m, sc.cell)
-        s, thr, ns = oracle_sample(sc, D, xy1.copy(), h1.copy(), sc.goal.copy(), a1.copy(),
-                                   args.ref_sample, 0)
-        cpu = {"value": alive1 / s, "unit": "ped-steps/s", "cores": thr, "kind": "oracle",
-               "sample": f"decision of {ns} random live pedestrians of this workload (field at "
-                         f"their 9 candidates), scaled to {alive1}, plus vote+commit of all"}
-    pk, pk_src = peaks()
+        s, thr, ns, nl, sd = oracle_sample(sc, D, xy1.copy(), h1.copy(), sc.goal.copy(),
+                                           a1.copy(), args.ref_sample, 0)
+        cpu = {"value": ns / s, "unit": "ped-steps/s", "cores": thr, "kind": "oracle",
+               "sample": oracle_sample_desc(args.ref_sample) + " (one step)",
+               "sample_peds": ns, "sample_fraction_of_live_crowd": ns / max(1, nl),
+               "seconds_timed": s, "seconds_deciding": sd,
+               "full_tick_s_extrapolated": sd * nl / max(1, ns) + (s - sd)}
     line = {
         "metric": "pedestrian-steps/s", "value": ped_steps / elapsed, "unit": "ped-steps/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": desc, "W": sc.W, "H": sc.H, "n": n, "r": int(sc.params["r"]),
-                   "bands": st1["bands"], "hbm_budget_bytes": budget,
-                   "field_footprint": footprint,
-                   "l2": "inputs larger than L2 (the field alone is 4*W*H bytes)"
-                   if sc.W * sc.H * 4 > 129e6 else "inputs smaller than L2",
-                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "config": workload_config(args, sc, desc),
+        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+        "bands": st1["bands"], "hbm_budget_bytes": budget, "field_footprint": footprint,
+        "sms": nsm,
         "su_updates_per_s": sc.W * sc.H * args.steps * world / elapsed,
+        "decisions": {"timed_ticks_decided": decided, "near_ties": near_ties,
+                      "near_tie_rate": near_ties / max(1, decided),
+                      "rule": "best and second-best admissible energies within 1e-5 of "
+                              "|F| + |own| + |guidance| (FP32, counted by the decision kernel)"},
         "stage_ms_per_step": {k: v / max(1, ticks) for k, v in stage_ms.items()},
         "stage_timing": f"CUDA events around each stage of every {TIMING_EVERY}th tick of the "
                         f"timed region ({ticks} of {args.steps} ticks)",
@@ -526,8 +601,8 @@ def run_batch(args):
         s.close()
     plain_value = plain_alive * plain_steps / plain_t
 
-    peak = SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
-    achieved = FLOPS_PER_PAIR * pairs / field_s / 1e12
+    pk, _ = peaks()
+    mhz, mhz_src = max_sm_mhz(clk, pk)
     line = {
         "metric": "pedestrian-steps/s", "value": value, "unit": "ped-steps/s", "n_gpus": 1,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps,
@@ -540,9 +615,8 @@ def run_batch(args):
         "plain_exact_path": {"value": plain_value, "unit": "ped-steps/s",
                              "how": f"{nsc} contexts stepped one after another, {plain_steps} ticks"},
         "speedup_vs_plain": value / plain_value,
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None, "kernel": "k_tick_batch (field only)",
-                     "field_ms": 1e3 * field_s, "pairs_per_step": pairs},
+        "roofline": gather_roofline(pairs, field_s, sm_count(torch, torch.cuda.current_device()),
+                                    mhz, mhz_src, "k_tick_batch (field only)"),
         "cpu_baseline": None, "e2e": None, "clocks": clk, "gpu_launches": int(launches),
     }
     print(json.dumps(line), flush=True)

@@ -48,7 +48,7 @@
 extern "C" {
 #endif
 
-#define SFM_ABI_VERSION 3
+#define SFM_ABI_VERSION 4
 #define SFM_MAX_RADIUS 64
 #define SFM_NSTAGES 6
 
@@ -101,6 +101,13 @@ typedef struct sfm_stats_t {
   int32_t pad_;
   int64_t device_bytes;    /* device memory held by the context */
   int64_t kernel_launches; /* kernels this context has launched since creation */
+  int64_t decided;         /* decisions (k-2) taken since placement */
+  int64_t near_ties;       /* of those, decisions whose best and second-best
+                              admissible energies E_a <= E_b satisfy
+                              E_b - E_a <= 1e-5 (M_a + M_b), M = |F| + |own
+                              field term| + |guidance term| of the candidate:
+                              near ties, which a field rounded otherwise may
+                              break either way (counted, not an error) */
 } sfm_stats_t;
 
 /* Stage indices for sfm_stage_times. */
@@ -122,7 +129,10 @@ int32_t sfm_abi_version(void);
  * field bands of `rows` rows (rounded down to a multiple of 32). */
 uint64_t sfm_resident_bytes(const sfm_lattice* lat);
 
-/* Create a context for one lattice.  cell: W*H bytes, 0 FREE, 1 WALL,
+/* Create a context for one lattice: the discrete space of Sec. 2 (space
+ * units, su, with static openings and obstacles whose omnidirectional fields
+ * Sec. 2 names), set up once before the loop of Alg. 1 (Sec. 3.1).
+ * cell: W*H bytes, 0 FREE, 1 WALL,
  * 2 EXIT (host or device per cell_on_device).  Computes the kernel tables,
  * the static field of WALL and EXIT su and the guidance distances on the
  * device (once per scene).  stream: a cudaStream_t or NULL.  On failure *out
@@ -138,7 +148,11 @@ void sfm_destroy(sfm_ctx* ctx);
  * on this thread).  Never NULL; valid until the next call on ctx. */
 const char* sfm_last_error(const sfm_ctx* ctx);
 
-/* (Re)place n pedestrians, replacing any previous set (the step counter is
+/* Place the crowd that the loop of Alg. 1 (Sec. 3.1) advances: pedestrians
+ * of 1 x 1 su with walk period 1, as in the experiments of Sec. 5 (the
+ * sized and periodic variants of Sec. 2 are sfm_place_sized and
+ * sfm_set_walk_periods).
+ * (Re)place n pedestrians, replacing any previous set (the step counter is
  * kept).  xy: n pairs (x, y) int32; heading: n classes 0..8 (NULL = 0);
  * goal: n classes, 0 = exit-seeker, 1..8 = fixed desired direction (NULL = 0);
  * alive: n flags (NULL = all alive).  Validates on the device and returns
@@ -161,7 +175,10 @@ sfm_status sfm_place(sfm_ctx* ctx, int32_t n, const int32_t* xy, const uint8_t* 
 /* Set the tick counter used by the election hash. */
 sfm_status sfm_set_time(sfm_ctx* ctx, int64_t t);
 
-/* Advance nsteps ticks (asynchronous on the context's stream). */
+/* Advance nsteps ticks: nsteps passes of the while loop of Alg. 1 (Sec.
+ * 3.1), each k-1 (bins), k-5's superposition computed first as a gather of
+ * the tick-start field, k-2 (9-candidate choice), k-3 (election) and k-4
+ * (move commit, exits).  Asynchronous on the context's stream. */
 sfm_status sfm_step(sfm_ctx* ctx, int32_t nsteps);
 
 /* Compute the field of the current state into the field buffer without
@@ -231,7 +248,10 @@ sfm_status sfm_set_field_footprint(sfm_ctx* ctx, int32_t shape);
 /* Wait for the context's stream and report device-side errors. */
 sfm_status sfm_sync(sfm_ctx* ctx);
 
-/* W*H floats: the field at the start of the last tick (or of the last
+/* The superposed field that k-5 of Alg. 1 (Sec. 3.1) maintains: the sum of
+ * the five field kinds of Sec. 2 (here static openings and obstacles plus
+ * the merged pedestrian kernel) at every su.
+ * W*H floats: the field at the start of the last tick (or of the last
  * sfm_compute_field).  SFM_ESTATE in banded mode, where no full-lattice field
  * is resident: use sfm_compute_field_into instead. */
 sfm_status sfm_read_field(sfm_ctx* ctx, float* dst, int32_t on_device);
@@ -247,7 +267,10 @@ sfm_status sfm_read_static_field(sfm_ctx* ctx, float* dst, int32_t on_device);
  * step; 1<<23 where no exit is reachable or on WALL su). */
 sfm_status sfm_read_guidance(sfm_ctx* ctx, int32_t* dst, int32_t on_device);
 
-/* Pedestrian state: xy (n pairs), heading classes, alive flags (each may be
+/* The positions k-4 of Alg. 1 (Sec. 3.1) commits, the headings that orient
+ * the directional fields of Sec. 2, and whether each pedestrian is still on
+ * the lattice (leaving through openings, Sec. 4.2's task no. 11).
+ * Pedestrian state: xy (n pairs), heading classes, alive flags (each may be
  * NULL to skip).  on_device: the buffers are device memory (copied device to
  * device); otherwise host memory: pinned host buffers mapped into the
  * device's address space are written in place by one launch, pageable ones
@@ -259,7 +282,11 @@ sfm_status sfm_read_peds(sfm_ctx* ctx, int32_t* xy, uint8_t* heading, uint8_t* a
  * (1 = moved) per pedestrian (each may be NULL). */
 sfm_status sfm_read_decisions(sfm_ctx* ctx, uint8_t* choice, uint8_t* won, int32_t on_device);
 
-/* Counters (synchronising). */
+/* Counters of the loop of Alg. 1 (Sec. 3.1): the tick t, pedestrians still
+ * on the lattice and those that left through openings (Sec. 4.2, task no.
+ * 11), committed moves (k-4), the largest enrollment of one su (k-3; at most
+ * 8 by the enrollment container of Sec. 3.1, item s-2) and the near-tie
+ * decisions of k-2.  Synchronising. */
 sfm_status sfm_stats(sfm_ctx* ctx, sfm_stats_t* out);
 
 /* Per-stage timing.  every = 0: off; every = k >= 1: sfm_step records CUDA
@@ -407,6 +434,13 @@ sfm_status sfm_surrogate_calibrate(sfm_surrogate* sur, sfm_ctx* ctx, double quan
                                    float* delta_out);
 sfm_status sfm_surrogate_step(sfm_surrogate* sur, sfm_ctx* ctx, int32_t nsteps);
 sfm_status sfm_surrogate_counts(sfm_surrogate* sur, int64_t* fallbacks, int64_t* decided);
+/* Test hook of the bounded waits of the tcgen05 convolution: the next
+ * layer-2 launch stops issuing its input copies after `after` tiles per CTA,
+ * so its MMA and store warps' waits run out (about a second); the launch
+ * then waits for the copies and MMAs it did issue, frees its tensor memory
+ * and returns, and the next synchronising surrogate call reports
+ * SFM_ETIMEOUT and switches layers 2-3 to mma.sync.  after < 0: SFM_EINVAL. */
+sfm_status sfm_surrogate_test_stop_copies(sfm_surrogate* sur, int32_t after);
 /* sfm_surrogate_eval, on ctx's current state (overwrites ctx's field and
  * decision buffers):
  *   field_rel_err  sum|F_sur - F| / sum|F - F_static| over the lattice;

@@ -77,7 +77,7 @@ def lib():
         L.orc_prio.restype = C.c_uint64
         L.orc_prio.argtypes = [C.c_uint64, C.c_int64, C.c_int64]
         L.orc_decide.restype = None
-        L.orc_decide.argtypes = [M, P, P, P, P, P, P, P, P, P, C.c_int64, P, P, P, P, P, P, P, P]
+        L.orc_decide.argtypes = [M, P, P, P, P, P, P, P, P, P, C.c_int64, P, P, P, P, P, P, P, P, P]
         L.orc_cover.restype = C.c_int64
         L.orc_cover.argtypes = [M, P, C.c_int32, P, P, P, P, P]
         L.orc_vote_sized.restype = C.c_int32
@@ -190,8 +190,10 @@ def cover(m: Model, cell, xy, alive, w, h):
 
 
 def decide(m: Model, cell, occ, xy, heading, goal, alive, D, req=None, Ffull=None, Sfull=None,
-           cov=None, w=None, h=None):
-    """Decision of the requested pedestrians: (choice, E[.,9], T[.,9], admissible[.,9]).
+           cov=None, w=None, h=None, magnitudes=False):
+    """Decision of the requested pedestrians: (choice, E[.,9], T[.,9], admissible[.,9]),
+    and with magnitudes=True also Mag[.,9] = |F| + |own| + |guidance| per
+    candidate (the scale of a near tie, see near_ties).
     cov/w/h: multi-su pedestrians (admissibility over the su a move enters)."""
     cell = np.ascontiguousarray(cell, np.uint8)
     occ = np.ascontiguousarray(occ, np.int32)
@@ -209,14 +211,45 @@ def decide(m: Model, cell, occ, xy, heading, goal, alive, D, req=None, Ffull=Non
     E = np.zeros((max(n, 1), 9), np.float64)
     T = np.zeros((max(n, 1), 9), np.float64)
     adm = np.zeros((max(n, 1), 9), np.uint8)
+    Mag = np.zeros((max(n, 1), 9), np.float64) if magnitudes else None
     if cov is not None:
         cov = np.ascontiguousarray(cov, np.int32)
         w = np.ascontiguousarray(w, np.uint8)
         h = np.ascontiguousarray(h, np.uint8)
     lib().orc_decide(C.byref(m), _p(cell), _p(occ), _p(xy), _p(heading), _p(goal), _p(alive),
                      _p(D), _p(Ffull), _p(Sfull), n, _p(reqa), _p(choice), _p(E), _p(T), _p(adm),
-                     _p(cov), _p(w), _p(h))
+                     _p(cov), _p(w), _p(h), _p(Mag))
+    if magnitudes:
+        return choice[:n], E[:n], T[:n], adm[:n], Mag[:n]
     return choice[:n], E[:n], T[:n], adm[:n]
+
+
+def best_two(E, adm):
+    """Per pedestrian: the smallest admissible energy (ties to the smallest
+    class), the candidate index holding it, and the next one in that order
+    (index -1 when only one candidate is admissible)."""
+    n = E.shape[0]
+    Ea = np.where(adm == 1, E, np.inf)
+    # stable sort by energy: equal energies keep the class order
+    order = np.argsort(Ea, axis=1, kind="stable")
+    b = order[:, 0]
+    s = order[:, 1]
+    has2 = np.isfinite(Ea[np.arange(n), s])
+    return b, np.where(has2, s, -1)
+
+
+def near_ties(E, Mag, adm, rtol=1e-5):
+    """Boolean per pedestrian: its best and second-best admissible energies
+    E_a <= E_b satisfy E_b - E_a <= rtol (Mag_a + Mag_b), the near-tie rule
+    the library counts (a field rounded otherwise may break such a choice
+    either way).  A pedestrian with one admissible candidate has none."""
+    n = E.shape[0]
+    b, s = best_two(E, adm)
+    ok = s >= 0
+    i = np.arange(n)
+    sj = np.where(ok, s, 0)
+    gap = E[i, sj] - E[i, b]
+    return ok & (gap <= rtol * (Mag[i, b] + Mag[i, sj]))
 
 
 def vote(m: Model, t: int, xy, alive, choice, w=None, h=None):

@@ -293,20 +293,29 @@ uint64_t orc_prio(uint64_t seed, int64_t t, int64_t id) {
 /* ---- decision (sub-job k-2) ----
  * For each requested pedestrian: E[9], the tolerance scale T[9] (sum of the
  * magnitudes of every term entering E), admissibility, and the choice.
+ * Mag (optional, 9 per pedestrian): the magnitude of the energy's three
+ * parts, |F(c_k)| + |own-field term| + |guidance term|, the scale of a near
+ * tie (two admissible energies within 1e-5 of it).
  * Ffull/Sfull: optional full-lattice field and magnitude (row-major); when
  * NULL the field is evaluated at the candidates directly. */
 void orc_decide(const orc_model* m, const uint8_t* cell, const int32_t* occ, const int32_t* xy,
                 const uint8_t* heading, const uint8_t* goal, const uint8_t* alive,
                 const int32_t* D, const double* Ffull, const double* Sfull, int64_t nreq,
                 const int32_t* req, uint8_t* choice, double* E, double* T, uint8_t* adm,
-                const int32_t* cover, const uint8_t* w, const uint8_t* h) {
+                const int32_t* cover, const uint8_t* w, const uint8_t* h, double* Mag) {
 #pragma omp parallel for schedule(dynamic, 64)
   for (int64_t q = 0; q < nreq; ++q) {
     int32_t p = req ? req[q] : (int32_t)q;
     double* e = E + 9 * q;
     double* tt = T + 9 * q;
+    double* mg = Mag ? Mag + 9 * q : NULL;
     uint8_t* a = adm + 9 * q;
-    for (int k = 0; k < 9; ++k) { e[k] = INFINITY; tt[k] = 0.0; a[k] = 0; }
+    for (int k = 0; k < 9; ++k) {
+      e[k] = INFINITY;
+      tt[k] = 0.0;
+      a[k] = 0;
+      if (mg) mg[k] = 0.0;
+    }
     if (alive && !alive[p]) { choice[q] = 0; continue; }
     int x = xy[2 * p], y = xy[2 * p + 1];
     int64_t c0 = (int64_t)y * m->W + x;
@@ -354,6 +363,7 @@ void orc_decide(const orc_model* m, const uint8_t* cell, const int32_t* occ, con
         g = -m->beta * (ODX[k] * gx + ODY[k] * gy);
       e[k] = fv[k] - own + g;
       tt[k] = sv[k] + fabs(own) + fabs(g);
+      if (mg) mg[k] = fabs(fv[k]) + fabs(own) + fabs(g);
       if (best < 0 || e[k] < e[best]) best = k;
     }
     choice[q] = (uint8_t)(best < 0 ? 0 : best);
@@ -519,7 +529,7 @@ int32_t orc_step(const orc_model* m, const uint8_t* cell, const int32_t* D, int6
     orc_cover(m, cell, n, xy, alive, w, h, cover);
   }
   orc_decide(m, cell, occ, xy, heading, goal, alive, D, NULL, NULL, n, NULL, choice, E, T, adm,
-             cover, w, h);
+             cover, w, h, NULL);
   orc_gate_periods(t, n, period, phase, choice);
   if (w)
     orc_vote_sized(m, t, n, xy, alive, choice, w, h, won);

@@ -41,6 +41,7 @@ EXPORTS = [
     "sfm_surrogate_forward",
     "sfm_surrogate_train", "sfm_surrogate_field", "sfm_surrogate_eval", "sfm_surrogate_set_delta",
     "sfm_surrogate_calibrate", "sfm_surrogate_step", "sfm_surrogate_counts",
+    "sfm_surrogate_test_stop_copies",
 ]
 
 
@@ -66,7 +67,8 @@ class Stats(C.Structure):
     _fields_ = [("t", C.c_int64), ("n", C.c_int64), ("alive", C.c_int64), ("exited", C.c_int64),
                 ("moved_total", C.c_int64), ("max_registrants", C.c_int32),
                 ("bands", C.c_int32), ("error_flags", C.c_uint32), ("pad_", C.c_int32),
-                ("device_bytes", C.c_int64), ("kernel_launches", C.c_int64)]
+                ("device_bytes", C.c_int64), ("kernel_launches", C.c_int64),
+                ("decided", C.c_int64), ("near_ties", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad_"}
@@ -145,6 +147,7 @@ def lib():
             "sfm_surrogate_calibrate": (C.c_int, [P, P, C.c_double, P]),
             "sfm_surrogate_step": (C.c_int, [P, P, I32]),
             "sfm_surrogate_counts": (C.c_int, [P, P, P]),
+            "sfm_surrogate_test_stop_copies": (C.c_int, [P, I32]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -354,11 +357,41 @@ def sfm_field_noalloc(lat: Lattice, prm: Params, xy, heading, alive, base, field
                       stream=None) -> int:
     """Field superposition into ``field`` (device) without any device
     allocation; returns the sfm_status code (0 = SFM_OK).  For callers that
-    cannot allocate device memory while they run; see include/sfm.h."""
-    n = 0 if xy is None else int(xy.shape[0])
-    return int(lib().sfm_field_noalloc(C.byref(lat), C.byref(prm), n, _ptr(xy)[0],
-                                       _ptr(heading)[0], _ptr(alive)[0], _ptr(base)[0],
-                                       _ptr(field)[0], _stream_handle(stream)))
+    cannot allocate device memory while they run; see include/sfm.h.
+
+    Every array must be a contiguous CUDA tensor: xy int32 of shape (n, 2),
+    heading and alive uint8 of n elements (or None), base and field float32
+    of W*H elements each.  Anything else raises ValueError before the C call
+    (the C function takes bare device pointers and cannot check them)."""
+    W, H = int(lat.W), int(lat.H)
+
+    def dev_tensor(name, a, dtype, numel=None, shape=None):
+        if a is None:
+            return None
+        if not hasattr(a, "data_ptr") or not getattr(a, "is_cuda", False):
+            raise ValueError(f"sfm_field_noalloc: {name} must be a CUDA tensor")
+        if str(a.dtype) != f"torch.{dtype}":
+            raise ValueError(f"sfm_field_noalloc: {name} must be {dtype}, got {a.dtype}")
+        if not a.is_contiguous():
+            raise ValueError(f"sfm_field_noalloc: {name} must be contiguous")
+        if shape is not None and tuple(a.shape) != shape:
+            raise ValueError(f"sfm_field_noalloc: {name} must have shape {shape}, got "
+                             f"{tuple(a.shape)}")
+        if numel is not None and a.numel() != numel:
+            raise ValueError(f"sfm_field_noalloc: {name} must hold {numel} elements, got "
+                             f"{a.numel()}")
+        return C.c_void_p(a.data_ptr())
+
+    if xy is None or base is None or field is None:
+        raise ValueError("sfm_field_noalloc: xy, base and field are required")
+    n = int(xy.shape[0]) if len(xy.shape) else -1
+    pxy = dev_tensor("xy", xy, "int32", shape=(n, 2))
+    ph = dev_tensor("heading", heading, "uint8", numel=n)
+    pa = dev_tensor("alive", alive, "uint8", numel=n)
+    pb = dev_tensor("base", base, "float32", numel=W * H)
+    pf = dev_tensor("field", field, "float32", numel=W * H)
+    return int(lib().sfm_field_noalloc(C.byref(lat), C.byref(prm), n, pxy, ph, pa, pb, pf,
+                                       _stream_handle(stream)))
 
 
 # ------------------------------------------------------------------ wrapper
@@ -727,6 +760,11 @@ class Surrogate:
     def step(self, sim, nsteps=1):
         """nsteps ticks of sim with the surrogate field and the exact fallback."""
         _scheck(self.h, lib().sfm_surrogate_step(self.h, sim.ctx, int(nsteps)))
+
+    def test_stop_copies(self, after):
+        """Test hook: the next tcgen05 layer-2 launch stops issuing copies
+        after `after` tiles per CTA, so its bounded waits run out."""
+        _scheck(self.h, lib().sfm_surrogate_test_stop_copies(self.h, int(after)))
 
     def counts(self):
         fb, dec = C.c_int64(), C.c_int64()

@@ -190,7 +190,7 @@ void run_tick(sfm_ctx* c) {
     StageScope sc(c, SFM_STAGE_DECIDE);
     launch_decide(c->n, c->rec_id, c->bin_start, 0, nbins, c->xy, c->heading, c->goal, c->cell,
                   c->ocls, c->D, c->F, 0, -1, -1, 0, 0, g.H, g, c->prm.beta, tb, c->choice,
-                  c->stream, c->walk(), c->sizes(), c->occ);
+                  c->stream, c->walk(), c->sizes(), c->occ, c->ctr);
     if (c->n > 0) ++c->launches;
   } else {
     for (int b = 0; b < c->bands; ++b) {
@@ -207,7 +207,7 @@ void run_tick(sfm_ctx* c) {
       launch_decide(c->n, c->rec_id, c->bin_start, (ya / kBin) * g.nbx,
                     ((yb + kBin - 1) / kBin) * g.nbx, c->xy, c->heading, c->goal, c->cell, c->ocls,
                     c->D, c->band_buf, 1, lo, hi, yb - ya + 1, ya, yb, g, c->prm.beta, tb,
-                    c->choice, c->stream, c->walk(), c->sizes(), c->occ);
+                    c->choice, c->stream, c->walk(), c->sizes(), c->occ, c->ctr);
       if (c->n > 0) ++c->launches;
     }
   }
@@ -1222,6 +1222,8 @@ sfm_status sfm_stats(sfm_ctx* ctx, sfm_stats_t* out) {
   out->error_flags = h.err;
   out->device_bytes = ctx->device_bytes;
   out->kernel_launches = ctx->launches;
+  out->decided = (int64_t)h.decided;
+  out->near_ties = (int64_t)h.near_ties;
   // alive = placed live pedestrians minus those that left since placement
   int64_t alive0 = 0;
   if (ctx->n) {

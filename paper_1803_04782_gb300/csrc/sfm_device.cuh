@@ -207,16 +207,22 @@ __device__ __forceinline__ bool in_entered(const Geo& g, int sx, int sy, int qx,
 // E(second best) - E(best) over the admissible candidates (+inf when only
 // staying is admissible) and *emag (optional) the larger |E| of the two:
 // any field error below margin / 2 at every candidate, less FP32 rounding of
-// energies of that size, leaves the choice unchanged.
-template <bool MARGIN>
+// energies of that size, leaves the choice unchanged.  With TIE, *tie
+// receives whether the second-best admissible energy lies within 1e-5 of
+// the best, relative to the two candidates' energy magnitudes |F| + |own| +
+// |guidance| (a near tie: a field rounded otherwise may break it the other
+// way).
+template <bool MARGIN, bool TIE = false>
 __device__ __forceinline__ int pick_move(const float (&f)[9], const int32_t (&dd)[9],
                                          const uint8_t (&oc)[9],
                                          const bool (&okx)[3], const bool (&oky)[3], int h, int gl,
                                          float beta, const float* __restrict__ own,
                                          const float* __restrict__ dirdot, float* margin,
-                                         float* emag = nullptr) {
+                                         float* emag = nullptr, bool* tie = nullptr) {
+  constexpr bool SECOND = MARGIN || TIE;
   int best = 0;
   float bestE = 0.f, second = __int_as_float(0x7f800000);
+  float bestM = 0.f, secondM = 0.f;
 #pragma unroll
   for (int k = 0; k < 9; ++k) {
     const int xi = move_dx(k) + 1, yi = move_dy(k) + 1;
@@ -224,14 +230,22 @@ __device__ __forceinline__ int pick_move(const float (&f)[9], const int32_t (&dd
     const bool adm = (k == 0) || (okx[xi] && oky[yi] && dd[k] != kDWall && oc[k] == 0);
     const float guide = (gl == 0) ? beta * ((float)(dd[k] - dd[0]) / 5.0f) : -beta * dirdot[gl * 9 + k];
     const float e = f[k] - own[h * 9 + k] + guide;
+    const float mag = TIE ? fabsf(f[k]) + fabsf(own[h * 9 + k]) + fabsf(guide) : 0.f;
     if (adm && (k == 0 || e < bestE)) {
-      if (MARGIN && k != 0) second = bestE;
+      if (SECOND && k != 0) {
+        second = bestE;
+        secondM = bestM;
+      }
       best = k;
       bestE = e;
-    } else if (MARGIN && adm && e < second) {
+      bestM = mag;
+    } else if (SECOND && adm && e < second) {
       second = e;
+      secondM = mag;
     }
   }
+  if (TIE)
+    *tie = second < __int_as_float(0x7f800000) && second - bestE <= 1e-5f * (bestM + secondM);
   if (MARGIN) {
     *margin = second - bestE;
     // size of the energies compared, for a rounding allowance
@@ -268,6 +282,7 @@ __device__ __forceinline__ void candidate_loads(const Geo& g, const uint8_t* __r
   }
 }
 
+template <bool TIE = false>
 __device__ __forceinline__ uint8_t decide_one(
     int p, const Geo& g, const int2* __restrict__ xy, const uint8_t* __restrict__ heading,
     const uint8_t* __restrict__ goal, const uint8_t* __restrict__ cell,
@@ -275,7 +290,7 @@ __device__ __forceinline__ uint8_t decide_one(
     int main_off, int lo_row, int hi_row, int hi_off, int y_lo, int y_hi, float beta,
     const float* __restrict__ own, const float* __restrict__ dirdot,
     const uint8_t* __restrict__ pw = nullptr, const uint8_t* __restrict__ ph = nullptr,
-    const int32_t* __restrict__ occ = nullptr) {
+    const int32_t* __restrict__ occ = nullptr, bool* tie = nullptr) {
   const int2 q = xy[p];
   const int h = heading[p], gl = goal[p];
   // the 3 x 3 neighbourhood (wrapped or clipped); every load is issued
@@ -309,7 +324,8 @@ __device__ __forceinline__ uint8_t decide_one(
 #pragma unroll
     for (int k = 1; k < 9; ++k) oc[k] = strip_free(g, cell, occ, q.x, q.y, a, b, k) ? 0 : 1;
   }
-  return (uint8_t)pick_move<false>(f, dd, oc, okx, oky, h, gl, beta, own, dirdot, nullptr);
+  return (uint8_t)pick_move<false, TIE>(f, dd, oc, okx, oky, h, gl, beta, own, dirdot, nullptr,
+                                       nullptr, tie);
 }
 
 // ------------------------------------------------------------------ S4 vote

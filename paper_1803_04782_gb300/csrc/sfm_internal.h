@@ -85,6 +85,11 @@ struct Counters {
   // between launches (the launch's last CTA puts them back), so launches
   // sharing one context's counters run one at a time, in stream order
   unsigned int field_tickets[2];
+  // decisions taken since the placement, and those among them whose best
+  // and second-best admissible energies lie within 1e-5 of their magnitude
+  // (near ties, which a differently rounded field may break the other way)
+  unsigned long long decided;
+  unsigned long long near_ties;
 };
 
 // Multi-su pedestrians (Sec. 2): pedestrian p occupies the w[p] x h[p]
@@ -207,13 +212,15 @@ struct WalkPeriods {
   const Counters* ctr = nullptr;
 };
 
+// streaming multiprocessors of the current device (its attribute, cached)
+int device_sm_count();
 void launch_decide(int n, const int32_t* rec_id, const int32_t* bin_start, int b_lo, int b_hi,
                    const int2* xy, const uint8_t* heading, const uint8_t* goal,
                    const uint8_t* cell, const uint8_t* ocls, const int32_t* D, const float* F,
                    int main_off, int lo_row, int hi_row, int hi_off, int y_lo, int y_hi,
                    const Geo& g, float beta, const Tables& tb, uint8_t* choice, cudaStream_t s,
                    const WalkPeriods& wp = WalkPeriods(), const Sizes& sz = Sizes(),
-                   const int32_t* occ = nullptr);
+                   const int32_t* occ = nullptr, Counters* ctr = nullptr);
 void launch_vote(int n, const int32_t* rec_id, const int32_t* bin_start, const int2* xy,
                  const uint8_t* choice, const int32_t* occ, const Geo& g, uint64_t seed,
                  Counters* ctr, uint8_t* won, cudaStream_t s, const Sizes& sz = Sizes());

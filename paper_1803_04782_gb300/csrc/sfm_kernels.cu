@@ -206,17 +206,30 @@ __global__ void __launch_bounds__(1024)
   }
 }
 
+int device_sm_count() {
+  static int cached[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
+  if (!cached[dev]) {
+    int n = 0;
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    cached[dev] = n > 0 ? n : 1;
+  }
+  return cached[dev];
+}
+
 void launch_guidance_init(const Geo& g, const uint8_t* cell, int32_t* D, cudaStream_t s) {
   const size_t n = (size_t)g.W * g.H;
   int blocks = (int)((n + 255) / 256);
-  if (blocks > 152 * 64) blocks = 152 * 64;
+  // grid-stride: at most 64 blocks of 256 per SM
+  if (blocks > device_sm_count() * 64) blocks = device_sm_count() * 64;
   k_guidance_init<<<blocks, 256, 0, s>>>(g, cell, D);
 }
 
 void launch_guidance_export(int32_t* D, size_t n, cudaStream_t s) {
   if (!n) return;
   int blocks = (int)((n + 255) / 256);
-  if (blocks > 152 * 64) blocks = 152 * 64;
+  if (blocks > device_sm_count() * 64) blocks = device_sm_count() * 64;
   k_guidance_export<<<blocks, 256, 0, s>>>(D, n);
 }
 
@@ -441,6 +454,8 @@ __global__ void k_reset_counters(Counters* ctr) {
   ctr->exited = 0;
   ctr->max_registrants = 0;
   ctr->err = 0;
+  ctr->decided = 0;
+  ctr->near_ties = 0;
 }
 
 void launch_reset_counters(Counters* ctr, cudaStream_t s) { k_reset_counters<<<1, 1, 0, s>>>(ctr); }
@@ -884,7 +899,8 @@ __global__ void __launch_bounds__(256, 4) k_decide(const int32_t* __restrict__ r
                          int lo_row, int hi_row, int hi_off, int y_lo, int y_hi, Geo g,
                          float beta, const float* __restrict__ own,
                          const float* __restrict__ dirdot, uint8_t* __restrict__ choice,
-                         WalkPeriods wp, Sizes sz, const int32_t* __restrict__ occ) {
+                         WalkPeriods wp, Sizes sz, const int32_t* __restrict__ occ,
+                         Counters* __restrict__ ctr) {
   // grid-stride over the records of bins [b_lo, b_hi): a band's launch needs
   // no more blocks than the GPU holds, whatever its share of the crowd.  The
   // records are taken from the last backwards: the gather wrote the band's
@@ -893,14 +909,26 @@ __global__ void __launch_bounds__(256, 4) k_decide(const int32_t* __restrict__ r
   const int end = bin_start[b_hi];
   const long long t = wp.period ? wp.ctr->t : 0;
   const int cnt = end - bin_start[b_lo];
+  unsigned decided = 0, ties = 0;
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < cnt; k += gridDim.x * blockDim.x) {
     const int p = rec_id[end - 1 - k];
     if (wp.period && t % wp.period[p] != wp.phase[p]) {
       choice[p] = 0;  // not this pedestrian's tick: it stays
       continue;
     }
-    choice[p] = decide_one(p, g, xy, heading, goal, cell, ocls, D, F, main_off, lo_row, hi_row,
-                           hi_off, y_lo, y_hi, beta, own, dirdot, sz.w, sz.h, occ);
+    bool tie = false;
+    choice[p] = decide_one<true>(p, g, xy, heading, goal, cell, ocls, D, F, main_off, lo_row,
+                                 hi_row, hi_off, y_lo, y_hi, beta, own, dirdot, sz.w, sz.h, occ,
+                                 &tie);
+    ++decided;
+    ties += tie ? 1u : 0u;
+  }
+  // decisions and near ties, one atomic per warp
+  decided = __reduce_add_sync(0xffffffffu, decided);
+  ties = __reduce_add_sync(0xffffffffu, ties);
+  if (ctr && (threadIdx.x & 31) == 0 && decided) {
+    atomicAdd(&ctr->decided, (unsigned long long)decided);
+    if (ties) atomicAdd(&ctr->near_ties, (unsigned long long)ties);
   }
 }
 
@@ -909,7 +937,8 @@ void launch_decide(int n, const int32_t* rec_id, const int32_t* bin_start, int b
                    const uint8_t* cell, const uint8_t* ocls, const int32_t* D, const float* F,
                    int main_off, int lo_row, int hi_row, int hi_off, int y_lo, int y_hi,
                    const Geo& g, float beta, const Tables& tb, uint8_t* choice, cudaStream_t s,
-                   const WalkPeriods& wp, const Sizes& sz, const int32_t* occ) {
+                   const WalkPeriods& wp, const Sizes& sz, const int32_t* occ,
+                   Counters* ctr) {
   if (n <= 0 || b_hi <= b_lo) return;
   static int max_blocks = 0;
   if (!max_blocks) {
@@ -921,7 +950,7 @@ void launch_decide(int n, const int32_t* rec_id, const int32_t* bin_start, int b
   const int blocks = cdiv(n, 256) < max_blocks ? cdiv(n, 256) : max_blocks;
   k_decide<<<blocks, 256, 0, s>>>(rec_id, bin_start, b_lo, b_hi, xy, heading, goal, cell,
                                         ocls, D, F, main_off, lo_row, hi_row, hi_off, y_lo, y_hi,
-                                        g, beta, tb.own, tb.dirdot, choice, wp, sz, occ);
+                                        g, beta, tb.own, tb.dirdot, choice, wp, sz, occ, ctr);
 }
 
 // ------------------------------------------------------------ S4: vote

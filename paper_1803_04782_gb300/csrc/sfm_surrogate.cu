@@ -285,9 +285,13 @@ __device__ __forceinline__ void umma_commit(uint32_t mbar) {
                : "memory");
 }
 
-// bounded wait for the mbarrier phase `parity`; false on a timeout
+// bounded wait for the mbarrier phase `parity`; false on a timeout.  The
+// bound is about one second of the global timer (checked every 256 tries,
+// each of which may suspend the thread for a short, system-defined time),
+// with an iteration cap behind it.
 __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
-  for (int it = 0; it < (1 << 22); ++it) {
+  uint64_t t0 = 0;
+  for (int it = 0; it < (1 << 24); ++it) {
     uint32_t done = 0;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
@@ -297,6 +301,14 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
         : "r"(mbar), "r"(parity)
         : "memory");
     if (done) return true;
+    if ((it & 255) == 255) {
+      uint64_t now;
+      asm volatile("mov.u64 %0, %%globaltimer;\n" : "=l"(now));
+      if (t0 == 0)
+        t0 = now;
+      else if (now - t0 > 1000000000ull)
+        return false;
+    }
   }
   return false;
 }
@@ -304,7 +316,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
 __global__ void __launch_bounds__(kWsThreads, 1)
     k_conv3_umma(const __grid_constant__ CUtensorMap tmap, int Hin, int Win,
                  const bf16* __restrict__ Wu, const float* __restrict__ b, bf16* __restrict__ out,
-                 int* __restrict__ err) {
+                 int* __restrict__ err, int stop_after) {
   extern __shared__ __align__(1024) uint8_t smu_raw[];
   // the swizzled buffers start on a 512-byte boundary (512 bytes allocated spare)
   const uint32_t raw = (uint32_t)__cvta_generic_to_shared(smu_raw);
@@ -313,6 +325,10 @@ __global__ void __launch_bounds__(kWsThreads, 1)
   const uint32_t sB = sA0 + kWsStages * kUmA, bar = sB + kUmB;
   // mbarriers: full[s], empty[s] (input ring), accf[a], acce[a] (accumulators)
   const uint32_t tslot = bar + (2 * kWsStages + 4) * 8;
+  // after the TMEM address: the last iteration whose copies the producer
+  // issued and the last one whose MMAs were committed (-1: none), which the
+  // drain after a failed wait needs
+  volatile int* last_issued = reinterpret_cast<volatile int*>(smu + (tslot - sA0) + 4);
   auto full = [&](int st) { return bar + 8 * st; };
   auto empty = [&](int st) { return bar + 8 * (kWsStages + st); };
   auto accf = [&](int ac) { return bar + 8 * (2 * kWsStages + ac); };
@@ -325,6 +341,8 @@ __global__ void __launch_bounds__(kWsThreads, 1)
   for (int i = tid; i < kUmB / 16; i += blockDim.x)
     reinterpret_cast<uint4*>(smu + kWsStages * kUmA)[i] = reinterpret_cast<const uint4*>(Wu)[i];
   if (tid == 0) {
+    last_issued[0] = -1;
+    last_issued[1] = -1;
     for (int st = 0; st < kWsStages; ++st) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(full(st)));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(empty(st)));
@@ -353,6 +371,8 @@ __global__ void __launch_bounds__(kWsThreads, 1)
       for (int it = 0; it < my; ++it) {
         const int t = blockIdx.x + it * gridDim.x, st = it % kWsStages;
         const uint32_t ph = (uint32_t)(it / kWsStages) & 1u;
+        // test hook: stop issuing, so that the consumers' waits run out
+        if (stop_after >= 0 && it >= stop_after) break;
         if (!mbar_wait(empty(st), ph ^ 1u)) {
           failed = true;
           break;
@@ -367,6 +387,7 @@ __global__ void __launch_bounds__(kWsThreads, 1)
               "%4}], [%5];\n" ::"r"(base + (uint32_t)(r * kUmRowBytes)),
               "l"(reinterpret_cast<uint64_t>(&tmap)), "r"(0), "r"(x0), "r"(y0 + r), "r"(full(st))
               : "memory");
+        last_issued[0] = it;
       }
     }
     __syncwarp();
@@ -403,6 +424,7 @@ __global__ void __launch_bounds__(kWsThreads, 1)
         }
         umma_commit(empty(st));
         umma_commit(accf(ac));
+        last_issued[1] = it;
       }
     }
     __syncwarp();
@@ -466,10 +488,21 @@ __global__ void __launch_bounds__(kWsThreads, 1)
     }
   }
   if (failed) atomicExch(err, 1);
-  // every role has stopped (all waits are bounded); after a failure the
-  // copies and MMAs still in flight are waited for, bounded, before TMEM is freed
+  // Every role has stopped (all waits are bounded).  After a failure the
+  // copies and MMAs still in flight are waited for, bounded, before TMEM is
+  // freed and the CTA exits: for each ring stage the phase of full(st) that
+  // the last copies issued into it complete (iteration i lands phase
+  // i / stages of stage i % stages), and the phase of the accumulator
+  // barrier that the last commit completes (a tcgen05.commit tracks every
+  // MMA this thread issued before it).
   if (__syncthreads_or(failed ? 1 : 0) && tid == 0) {
-    for (int st = 0; st < kWsStages; ++st) mbar_wait(empty(st), 0);
+    const int li = last_issued[0], lm = last_issued[1];
+    for (int st = 0; st < kWsStages; ++st) {
+      if (li < st) continue;
+      const int i = li - (li - st) % kWsStages;
+      mbar_wait(full(st), (uint32_t)(i / kWsStages) & 1u);
+    }
+    if (lm >= 0) mbar_wait(accf(lm & 1), (uint32_t)(lm >> 1) & 1u);
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();
@@ -1284,6 +1317,7 @@ struct sfm_surrogate {
   bf16 *wu2 = nullptr, *wu3 = nullptr;  // layers 2 and 3 in the tcgen05 operand layout
   int* umma_err = nullptr;              // set by a tcgen05 convolution that timed out
   bool use_umma = true;                 // layers 2 and 3 on tcgen05 (else mma.sync)
+  int test_stop_copies = -1;            // test hook: the next layer-2 launch stops issuing copies
   int adam_t = 0;
   // activations for an image of (Hc + 2 kHalo) x (Wc + 2 kHalo) coarse cells
   int Hc = 0, Wc = 0;
@@ -1469,7 +1503,7 @@ EncodeTiledFn encode_tiled() {
 // 3x3 32 -> 32 layer on tcgen05 (one warp-specialised CTA an SM); false when
 // the tensor map cannot be made (the caller uses the mma.sync kernel)
 bool conv3_umma(const bf16* in, int Hin, int Win, const bf16* wu, const float* b, bf16* out,
-                int* err, cudaStream_t s) {
+                int* err, cudaStream_t s, int stop_after) {
   static int nsm = 0;
   if (!nsm) {
     int dev = 0;
@@ -1494,7 +1528,7 @@ bool conv3_umma(const bf16* in, int Hin, int Win, const bf16* wu, const float* b
   const int ntiles = cdiv(Win - 2, kUmCols) * cdiv(Hin - 2, kUmRows);
   const int grid = std::max(1, std::min(ntiles, nsm));
   cudaFuncSetAttribute(k_conv3_umma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kUmSmem);
-  k_conv3_umma<<<grid, kWsThreads, kUmSmem, s>>>(tm, Hin, Win, wu, b, out, err);
+  k_conv3_umma<<<grid, kWsThreads, kUmSmem, s>>>(tm, Hin, Win, wu, b, out, err, stop_after);
   return true;
 }
 
@@ -1512,9 +1546,11 @@ void forward(sfm_surrogate* S, cudaStream_t s) {
     const int grid = std::max(1, std::min(ntiles, std::max(nsm, 1) * kC1CtasPerSm));
     k_conv1_tc<<<grid, 128, 0, s>>>(S->X, Hp, Wp, S->wt1, q + kOffB[0], S->A1);
   }
-  if (!(S->use_umma && conv3_umma(S->A1, Hp - 4, Wp - 4, S->wu2, q + kOffB[1], S->A2, S->umma_err, s)))
+  const int stop = S->test_stop_copies;
+  S->test_stop_copies = -1;
+  if (!(S->use_umma && conv3_umma(S->A1, Hp - 4, Wp - 4, S->wu2, q + kOffB[1], S->A2, S->umma_err, s, stop)))
     conv3_tc(S->A1, Hp - 4, Wp - 4, S->wt2, q + kOffB[1], S->A2, s);
-  if (!(S->use_umma && conv3_umma(S->A2, Hp - 6, Wp - 6, S->wu3, q + kOffB[2], S->A3, S->umma_err, s)))
+  if (!(S->use_umma && conv3_umma(S->A2, Hp - 6, Wp - 6, S->wu3, q + kOffB[2], S->A3, S->umma_err, s, -1)))
     conv3_tc(S->A2, Hp - 6, Wp - 6, S->wt3, q + kOffB[2], S->A3, s);
   conv3_tc(S->A3, Hp - 8, Wp - 8, S->wt4, q + kOffB[3], nullptr, s, S->Y);
 }
@@ -2010,6 +2046,12 @@ sfm_status sfm_surrogate_step(sfm_surrogate* S, sfm_ctx* ctx, int32_t nsteps) {
     ++ctx->t;
   }
   SCU(cudaGetLastError());
+  return SFM_OK;
+}
+
+sfm_status sfm_surrogate_test_stop_copies(sfm_surrogate* S, int32_t after) {
+  if (!S || after < 0) return SFM_EINVAL;
+  S->test_stop_copies = after;
   return SFM_OK;
 }
 

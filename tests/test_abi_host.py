@@ -40,7 +40,7 @@ def test_library_exports_every_declared_entry_point(libpath):
 
 def test_binding_loads_and_reports_version(libpath):
     assert sfm.lib() is not None
-    assert sfm.sfm_abi_version() == 3
+    assert sfm.sfm_abi_version() == 4
 
 
 def test_struct_layouts_match_header(tmp_path):

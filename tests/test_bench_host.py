@@ -52,3 +52,41 @@ def test_default_bands_and_band_budget():
     assert bench.band_budget(sc, 1) == 0
     b4, b2 = bench.band_budget(sc, 4), bench.band_budget(sc, 2)
     assert 0 < b4 <= b2  # more bands: smaller band buffers, a smaller budget
+
+
+def test_gather_roofline_arithmetic():
+    """One table word per pair against 32 words per clock per SM; the
+    algorithmic FP32 figure is 6 flops per pair, the executed one 1."""
+    r = bench.gather_roofline(pairs=1.0e9, field_s=1e-3, nsm=100, mhz=2000.0, mhz_src="test",
+                              kernel="k")
+    assert r["bound"] == "smem"
+    assert abs(r["achieved"] - 1.0) < 1e-12                 # 1e12 words/s
+    assert abs(r["peak"] - 100 * 32 * 2000e6 / 1e12) < 1e-12
+    assert abs(r["frac"] - 1e12 / (100 * 32 * 2e9)) < 1e-12
+    a = r["algorithmic_fp32"]
+    assert abs(a["achieved_tflops"] - 6.0) < 1e-12
+    assert abs(a["frac"] - 6e12 / (100 * 128 * 2 * 2e9)) < 1e-12
+    assert abs(r["fp32_executed"]["frac"] - a["frac"] / 6) < 1e-15
+
+
+def test_reference_arm_reports_the_time_it_spent_and_the_same_config(capsys):
+    """The oracle arm's ms_per_step is time actually spent on its sampled
+    steps (it fits in the wall time of the run) and its config equals the
+    one the GPU arm prints for the same workload."""
+    import argparse
+    import json
+    import time
+
+    args = argparse.Namespace(workload="room", steps=2, warmup=3, ref_sample=50, gpus=1,
+                              bands=None)
+    t0 = time.perf_counter()
+    assert bench.run_reference(args) == 0
+    wall = time.perf_counter() - t0
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["impl"] == "reference"
+    assert line["ms_per_step"] * args.steps / 1e3 <= wall
+    cb = line["cpu_baseline"]
+    assert cb["seconds_timed"] <= wall
+    assert abs(line["value"] - 50 * args.steps / cb["seconds_timed"]) < 1e-6 * line["value"]
+    sc, desc = bench.workload("room")
+    assert line["config"] == bench.workload_config(args, sc, desc)

@@ -143,6 +143,51 @@ def test_oracle_forced_ticks(name):
     assert flips <= max(3, 0.02 * decisions), f"{flips} tie flips in {decisions} decisions"
 
 
+@pytest.mark.parametrize("which", ["paper_r1", "paper_r3_4dir", "room", "tall_r1"])
+def test_near_tie_counter_matches_the_oracle(which):
+    """The decision kernel's near-tie counter (sfm_stats: decisions whose two
+    best admissible energies lie within 1e-5 of their magnitude |F| + |own|
+    + |guidance|) against the oracle's count by the same rule in FP64, on the
+    same state.  The GPU's energies differ from the oracle's by at most the
+    tie tolerance 1e-5 T (T: sum of term magnitudes), so a pedestrian whose
+    oracle gap lies within that of the threshold may be counted either way;
+    every other one must be counted exactly as the oracle counts it."""
+    sc = {"paper_r1": lambda: SG.paper_scene(side=120, density=0.5, ndir=8, r=1, seed=41),
+          "paper_r3_4dir": lambda: SG.paper_scene(side=150, density=0.3, ndir=4, r=3, seed=42),
+          "room": SG.room, "tall_r1": _tall_r1}[which]()
+    orc = OracleRun(sc)
+    with sfm.Sim(sc) as sim:
+        for _ in range(3):
+            st = orc.st
+            sim.place(st.xy, st.heading, st.goal, st.alive)
+            sim.set_time(st.t)
+            sim.step(1)
+            stats = sim.stats()
+            Fo, So = orc.field()
+            occ, _ = O.occupancy(orc.m, sc.cell, st.xy, st.alive)
+            ch_o, E, T, adm, Mag = O.decide(orc.m, sc.cell, occ, st.xy, st.heading, st.goal,
+                                            st.alive, orc.D, None, Fo.ravel(), So.ravel(),
+                                            magnitudes=True)
+            live = st.alive.astype(bool)
+            assert stats["decided"] == int(live.sum())
+            b, s2 = O.best_two(E, adm)
+            i = np.arange(len(b))
+            ok = live & (s2 >= 0)
+            sj = np.where(s2 >= 0, s2, 0)
+            gap = E[i, sj] - E[i, b]
+            thr = 1e-5 * (Mag[i, b] + Mag[i, sj])
+            band = 1e-5 * (T[i, b] + T[i, sj])
+            lo = int((ok & (gap <= thr - band)).sum())
+            hi = int((ok & (gap <= thr + band)).sum())
+            exact = int((ok & O.near_ties(E, Mag, adm)).sum())
+            assert lo <= stats["near_ties"] <= hi, (lo, exact, hi, stats["near_ties"])
+            ch_g, _ = sim.decisions()
+            compare_choices(ch_g, ch_o, E, T, adm)
+            orc.advance(ch_o)
+        if which == "paper_r1":
+            assert stats["near_ties"] > 0   # equal term multisets make exact ties at r = 1
+
+
 def test_free_running_room_100x100_r10_50_ticks():
     """The 100x100 room with 200 exit-seekers, radius 10, 50 ticks: the GPU
     runs on its own and must stay identical to the oracle's run."""

@@ -57,6 +57,30 @@ def test_tcgen05_layers_match_the_mma_sync_layers_and_the_oracle(shape):
         assert np.linalg.norm(Y - Yo) / np.linalg.norm(Yo) <= 2e-2
 
 
+@pytest.mark.parametrize("after", [0, 1])
+def test_tcgen05_wait_that_runs_out_reports_timeout_and_falls_back(after):
+    """A tcgen05 launch whose producer stops issuing copies (a test hook, no
+    fault): its MMA and store warps' bounded waits run out, the launch drains
+    what it issued and frees its tensor memory, the call reports
+    SFM_ETIMEOUT, and later calls run the layers on mma.sync with the same
+    result as before."""
+    rng = np.random.default_rng(22)
+    params = _rounded_params(6, scale=0.5)
+    X = bf16(rng.random((3, 157, 333)) * 0.3)
+    with sfm.Surrogate(params=sfm.flatten_params(params)) as s:
+        Ym = s.forward(X, tcgen05=False)
+        s.test_stop_copies(after)
+        with pytest.raises(sfm.SfmError) as e:
+            s.forward(X, tcgen05=True)
+        assert e.value.status == sfm.SFM_ETIMEOUT
+        Y2 = s.forward(X, tcgen05=True)   # now on mma.sync
+        assert np.array_equal(Y2, Ym)
+    # the device is still usable for a fresh surrogate on tcgen05
+    with sfm.Surrogate(params=sfm.flatten_params(params)) as s:
+        Yu = s.forward(X, tcgen05=True)
+    assert float(np.abs(Yu - Ym).max()) <= 2e-2 * float(np.abs(Ym).max())
+
+
 def test_gradients_match_the_oracle_within_bf16_bound():
     rng = np.random.default_rng(11)
     params = _rounded_params(3)

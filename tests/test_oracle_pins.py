@@ -256,6 +256,60 @@ def test_fixed_direction_tie_goes_to_smallest_class():
     assert ch[0] == 2
 
 
+def test_near_tie_count_finds_the_exact_tie_of_the_blocked_east_move():
+    """The blocked east move leaves NE and SE with equal energies (-1 each,
+    an exact tie): the near-tie rule counts it; best is the smaller class."""
+    W, H = 9, 9
+    cell = np.zeros((H, W), np.uint8)
+    cell[4, 5] = SG.WALL
+    sc = SG.Scene("tie", W, H, 0, 0, cell, np.array([[4, 4]], np.int32),
+                  np.zeros(1, np.uint8), np.array([1], np.uint8), SG._params(r=0))
+    m = O.model(sc)
+    occ, _ = O.occupancy(m, cell, sc.xy)
+    ch, E, T, adm, Mag = O.decide(m, cell, occ, sc.xy, sc.heading, sc.goal,
+                                  np.ones(1, np.uint8), np.zeros((H, W), np.int32),
+                                  magnitudes=True)
+    b, s2 = O.best_two(E, adm)
+    assert (b[0], s2[0]) == (2, 8) and ch[0] == 2
+    # r = 0: no field, no own term; the magnitude is the guidance term alone
+    assert Mag[0, 2] == Mag[0, 8] == 1.0
+    assert O.near_ties(E, Mag, adm).tolist() == [True]
+
+
+def test_near_tie_count_finds_mirror_ties_and_no_others():
+    """A pedestrian on the mirror axis of a symmetric closed room, walking
+    north with the north su walled: NE and NW are mirror images, so their
+    FP64 energies agree up to summation order (a near tie); the lone walker
+    of an empty corridor has a clear best move (no near tie)."""
+    W, H = 11, 11
+    cell = np.zeros((H, W), np.uint8)
+    cell[0, :] = cell[-1, :] = cell[:, 0] = cell[:, -1] = SG.WALL
+    cell[6, 5] = SG.WALL                                   # north of (5, 5)
+    sc = SG.Scene("mirror", W, H, 0, 0, cell, np.array([[5, 5]], np.int32),
+                  np.zeros(1, np.uint8), np.array([3], np.uint8), SG._params(r=3))
+    m = O.model(sc)
+    occ, _ = O.occupancy(m, cell, sc.xy)
+    ch, E, T, adm, Mag = O.decide(m, cell, occ, sc.xy, sc.heading, sc.goal,
+                                  np.ones(1, np.uint8), O.guidance(m, cell), magnitudes=True)
+    b, s2 = O.best_two(E, adm)
+    assert {int(b[0]), int(s2[0])} == {2, 4}               # NE and NW
+    assert abs(E[0, 2] - E[0, 4]) <= 1e-12 * Mag[0, 2]
+    assert O.near_ties(E, Mag, adm).tolist() == [True]
+    # the corridor walker of the next test: east beats NE / SE by the wall
+    # field's difference, far above 1e-5 of the energies
+    Wc, Hc = 40, 7
+    cc = np.zeros((Hc, Wc), np.uint8)
+    cc[0, :] = cc[Hc - 1, :] = SG.WALL
+    sw = SG.Scene("walker", Wc, Hc, 1, 0, cc, np.array([[3, 3]], np.int32),
+                  np.array([1], np.uint8), np.array([1], np.uint8), SG._params(r=5))
+    mw = O.model(sw)
+    occ, _ = O.occupancy(mw, cc, sw.xy)
+    ch, E, T, adm, Mag = O.decide(mw, cc, occ, sw.xy, sw.heading, sw.goal,
+                                  np.ones(1, np.uint8), O.guidance(mw, cc), magnitudes=True)
+    assert ch[0] == 1
+    assert O.near_ties(E, Mag, adm).tolist() == [False]
+
+
 def test_lone_walker_moves_along_its_direction():
     """Own-field removal: a lone pedestrian heading east in an empty periodic
     corridor steps east every tick (its own field would otherwise block it)."""
