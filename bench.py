@@ -43,11 +43,13 @@ TIMING_EVERY = 9
 # 16384^2 floor with 4 bands, from a one-pass ncu capture of this benchmark
 # (dram__bytes_read.sum + dram__bytes_write.sum); valid only while the
 # gather's sources hash to the value they had when it was taken.
-GATHER_TRAFFIC = {"sha1": "6d95dfe21aa6f4a5c5cf9cfdf24320647d53c76e", "bands": 4,
-                  "footprint": "32x16", "workload": "floor", "bytes_per_launch": 493003136}
+GATHER_TRAFFIC = {"sha1": "fafef7e8cebb75d743dcf92cbba7e2ca2e817429", "bands": 4,
+                  "footprint": "32x32r", "workload": "floor", "bytes_per_launch": 492857728}
 GATHER_SOURCES = ("paper_1803_04782_gb300/csrc/sfm_gather.cuh",
-                  "paper_1803_04782_gb300/csrc/sfm_field.cu",
+                  "paper_1803_04782_gb300/csrc/sfm_field3.cu",
                   "paper_1803_04782_gb300/csrc/sfm_internal.h")
+# the gather kernel of each footprint
+GATHER_KERNEL = {"16x16": "k_field_v2", "32x16": "k_field_v2", "32x32r": "k_field_v3"}
 
 
 def gather_sources_sha1() -> str:
@@ -441,7 +443,8 @@ def run_gpu(args):
     mhz, mhz_src = max_sm_mhz(clk, pk)
     field_s = stage_ms["field"] / 1e3  # over the `ticks` timed ticks
     pairs = 0.5 * (pairs0 + pairs1)
-    roofline = gather_roofline(pairs, field_s / ticks, nsm, mhz, mhz_src, "k_field_v2",
+    roofline = gather_roofline(pairs, field_s / ticks, nsm, mhz, mhz_src,
+                               GATHER_KERNEL.get(footprint, "k_field"),
                                gather_traffic(args.workload, st1["bands"], footprint))
     roofline["timed_ticks"] = ticks
 
@@ -891,7 +894,7 @@ def main():
     ap.add_argument("--bands", type=int, default=None,
                     help="row bands of the divide-and-conquer field pass (1 = unbanded)")
     ap.add_argument("--e2e-steps", type=int, default=10)
-    ap.add_argument("--footprint", default="auto", choices=["auto", "16x16", "32x16"],
+    ap.add_argument("--footprint", default="auto", choices=["auto", "16x16", "32x16", "32x32r"],
                     help="field gather footprint: autotuned, or fixed")
     ap.add_argument("--ref-sample", type=int, default=100000)
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -185,11 +185,11 @@ sfm_status sfm_step(sfm_ctx* ctx, int32_t nsteps);
  * moving anybody (bins + gather only).  Asynchronous. */
 sfm_status sfm_compute_field(sfm_ctx* ctx);
 
-/* Times the field gather of the current state with each of its two warp
- * footprints (16 x 16 and 32 x 16 su) and keeps the faster for this context
- * (the choice survives later placements).  *shape_out (may be NULL): 0 or 1.
- * The fields computed are identical either way.  Synchronising; moves
- * nobody. */
+/* Times the field gather of the current state with each of its warp
+ * footprints (see sfm_set_field_footprint) and keeps the fastest for this
+ * context (the choice survives later placements).  *shape_out (may be
+ * NULL): 0..3.  The fields computed are identical either way.
+ * Synchronising; moves nobody. */
 sfm_status sfm_autotune(sfm_ctx* ctx, int32_t* shape_out);
 
 /* Checkpoint and resume.  sfm_snapshot writes the context's dynamic state
@@ -241,8 +241,11 @@ sfm_status sfm_set_walk_periods(sfm_ctx* ctx, const uint8_t* period, const uint8
 sfm_status sfm_set_binning(sfm_ctx* ctx, int32_t mode);
 
 /* Sets the warp footprint of the field gather by hand: 0 = 16 x 16 su,
- * 1 = 32 x 16 su; anything else is SFM_EINVAL.  Ignored (but accepted) when
- * the interaction radius exceeds the class-table gather (r > 50). */
+ * 1 = 32 x 16 su (every pedestrian visit reads all 16 rows), 2 = 32 x 32 su
+ * on the row-trimmed gather (a visit reads only the 8-row blocks the window
+ * reaches; radius 1..40, beyond which 2 runs as 1).  Anything else is
+ * SFM_EINVAL.  Ignored (but accepted) when the interaction radius exceeds
+ * the class-table gather (r > 50). */
 sfm_status sfm_set_field_footprint(sfm_ctx* ctx, int32_t shape);
 
 /* Wait for the context's stream and report device-side errors. */

@@ -248,8 +248,9 @@ def near_ties(E, Mag, adm, rtol=1e-5):
     ok = s >= 0
     i = np.arange(n)
     sj = np.where(ok, s, 0)
-    gap = E[i, sj] - E[i, b]
-    return ok & (gap <= rtol * (Mag[i, b] + Mag[i, sj]))
+    with np.errstate(invalid="ignore"):   # dead pedestrians: inf - inf
+        gap = E[i, sj] - E[i, b]
+        return ok & (gap <= rtol * (Mag[i, b] + Mag[i, sj]))
 
 
 def vote(m: Model, t: int, xy, alive, choice, w=None, h=None):

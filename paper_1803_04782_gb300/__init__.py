@@ -284,11 +284,15 @@ def sfm_stats(ctx) -> dict:
     return s.as_dict()
 
 
+# sfm_set_field_footprint shapes 0..2; "r": the row-trimmed gather
+FOOTPRINTS = ("16x16", "32x16", "32x32r")
+
+
 def sfm_autotune(ctx) -> str:
-    """Pick the faster warp footprint of the field gather for this context."""
+    """Pick the fastest warp footprint of the field gather for this context."""
     v = C.c_int32()
     _check(ctx, lib().sfm_autotune(ctx, C.byref(v)))
-    return "32x16" if v.value else "16x16"
+    return FOOTPRINTS[v.value]
 
 
 def sfm_set_timing(ctx, every) -> None:
@@ -543,7 +547,7 @@ class Sim:
         _check(self.ctx, lib().sfm_set_binning(self.ctx, {"auto": 0, "grid": 1, "peds": 2}[mode]))
 
     def set_footprint(self, shape: str):
-        _check(self.ctx, lib().sfm_set_field_footprint(self.ctx, {"16x16": 0, "32x16": 1}[shape]))
+        _check(self.ctx, lib().sfm_set_field_footprint(self.ctx, FOOTPRINTS.index(shape)))
 
     def set_timing(self, every=True):
         """Stage events on every ``every``-th tick (True: every tick; False: off)."""

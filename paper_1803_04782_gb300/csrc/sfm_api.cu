@@ -539,6 +539,7 @@ sfm_status sfm_create(const sfm_lattice* lat, const uint8_t* cell, int32_t cell_
   ALLOC(ctx->dirdot, 81);
   ALLOC(ctx->hvec, 9);
   if (class_table_floats(g.r)) ALLOC(ctx->CT, class_table_floats(g.r));
+  if (field3_table_floats(g.r)) ALLOC(ctx->CT3, field3_table_floats(g.r));
   ALLOC(ctx->bin_count, (size_t)nbins);
   ALLOC(ctx->bin_start, (size_t)nbins + 1);
   ALLOC(ctx->scan_tmp, (size_t)scan_tmp_elems(nbins));
@@ -558,6 +559,7 @@ sfm_status sfm_create(const sfm_lattice* lat, const uint8_t* cell, int32_t cell_
   launch_tables(g.r, ctx->prm, ctx->T0, ctx->TX, ctx->TY, ctx->KO, ctx->KE, ctx->own, ctx->dirdot,
                 ctx->hvec, s);
   if (ctx->CT) launch_class_tables(g.r, ctx->prm, ctx->CT, s);
+  if (ctx->CT3) launch_class_tables3(g.r, ctx->prm, ctx->CT3, s);
   launch_static_field(g, ctx->cell, ctx->tables(), ctx->Fs, s);
 
   {
@@ -912,7 +914,8 @@ sfm_status sfm_autotune(sfm_ctx* ctx, int32_t* shape_out) {
   run_bins(ctx);
   float best = 1e30f;
   int best_shape = ctx->field_shape;
-  for (int shape : {0, 1}) {
+  for (int shape : {kShape16x16, kShape32x16, kShape32x32}) {
+    if (shape >= kShape32x32 && !(ctx->CT3 && field3_shape_ok(shape, g.r))) continue;
     ctx->field_shape = shape;
     float tot = 0.f;
     for (int rep = 0; rep < 3; ++rep) {
@@ -982,7 +985,8 @@ sfm_status sfm_set_binning(sfm_ctx* ctx, int32_t mode) {
 sfm_status sfm_set_field_footprint(sfm_ctx* ctx, int32_t shape) {
   if (!ctx) return SFM_EINVAL;
   if (ctx->batch) return fail(ctx, SFM_EINVAL, "a batch tunes its footprints per radius class");
-  if (shape != 0 && shape != 1) return fail(ctx, SFM_EINVAL, "footprint must be 0 or 1");
+  if (shape < kShape16x16 || shape > kShape32x32)
+    return fail(ctx, SFM_EINVAL, "footprint must be 0, 1 or 2");
   if (ctx->field_shape != shape) {
     ctx->field_shape = shape;
     drop_graph(ctx);

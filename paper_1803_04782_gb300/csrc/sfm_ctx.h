@@ -47,6 +47,7 @@ struct sfm_ctx {
   float *own = nullptr, *dirdot = nullptr;
   float2* hvec = nullptr;
   float* CT = nullptr;  // heading-class tables of the v2 gather
+  float* CT3 = nullptr;  // the same in the row-trimmed gather's layout (radius 1..48)
   int field_shape = 0;  // footprint of the class-table gather (0: 16x16, 1: 32x16)
   // bins
   int32_t *bin_count = nullptr, *bin_start = nullptr, *scan_tmp = nullptr;
@@ -118,6 +119,7 @@ struct sfm_ctx {
     tb.dirdot = dirdot;
     tb.hvec = hvec;
     tb.CT = CT;
+    tb.CT3 = CT3;
     tb.shape = field_shape;
     return tb;
   }

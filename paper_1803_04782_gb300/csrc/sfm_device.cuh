@@ -49,6 +49,27 @@ static __constant__ int c_csy[9] = SFM_CLASS_ROW(class_sy);
 
 constexpr int kFieldPad = kFieldPadRows;
 
+// Entry (dx, dy) of stored heading-class table t (0 none, 1 E, 2 N, 3 NE):
+// K_P((dx, dy); h_t) = kP d^aP (1 + gamma h_t . (dx, dy) / d) for 0 <
+// max(|dx|, |dy|) <= r, else 0; evaluated in FP64 (and rounded to FP32 by
+// the caller) so that every table layout holds the same values.  taper_in <
+// r: weighted by 1 up to Euclidean distance taper_in and a raised cosine
+// down to 0 at r (the surrogate's near part).
+__device__ __forceinline__ double class_kernel_value(int t, int dx, int dy, int r, double kP,
+                                                     double aP, double gamma, double taper_in) {
+  const int adx = dx < 0 ? -dx : dx, ady = dy < 0 ? -dy : dy;
+  double v = 0.0;
+  if (adx <= r && ady <= r && (adx | ady) != 0) {
+    const double hx = (t == 1) ? 1.0 : (t == 3 ? 0.70710678118654752440 : 0.0);
+    const double hy = (t == 2) ? 1.0 : (t == 3 ? 0.70710678118654752440 : 0.0);
+    const double d = sqrt((double)(dx * dx + dy * dy));
+    v = kP * pow(d, aP) * (1.0 + gamma * (hx * dx + hy * dy) / d);
+    if (taper_in < r && d > taper_in)
+      v *= d >= r ? 0.0 : 0.5 * (1.0 + cos(3.14159265358979323846 * (d - taper_in) / (r - taper_in)));
+  }
+  return v;
+}
+
 // the same move offsets as compile-time functions, so unrolled loops index
 // register arrays with constants
 __host__ __device__ __forceinline__ constexpr int move_dx(int k) {

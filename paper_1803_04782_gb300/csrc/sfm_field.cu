@@ -268,7 +268,7 @@ static void launch_v2_shape(const Geo& g, const int32_t* bin_start, const uint32
     launch_v2<SP, 1, 8>(g, bin_start, rec, tb.CT, Fs, out, out_row0, store_lo, store_hi, s, far, tickets);
   else if (far.Y)
     launch_v2<SP, 1, 1>(g, bin_start, rec, tb.CT, Fs, out, out_row0, store_lo, store_hi, s, far, tickets);
-  else if (tb.shape)
+  else if (tb.shape != kShape16x16)  // the row-trimmed shape where that gather is off
     launch_v2<SP, 1, 0>(g, bin_start, rec, tb.CT, Fs, out, out_row0, store_lo, store_hi, s, far, tickets);
   else
     launch_v2<SP, 0, 0>(g, bin_start, rec, tb.CT, Fs, out, out_row0, store_lo, store_hi, s, far, tickets);
@@ -289,6 +289,9 @@ void launch_field(const Geo& g, const int32_t* bin_start, const uint32_t* rec, c
   // that one ticket each would queue on the counter.  So do lattices under 4
   // footprints per warp (launch_v2).
   unsigned int* tickets = ctr && !far.Y ? ctr->field_tickets : nullptr;
+  if (!far.Y && launch_field_v3(g, bin_start, rec, tb, Fs, out, out_row0, store_lo, store_hi,
+                                tickets, s))
+    return;
   switch (sp) {
     case 34: launch_v2_shape<34>(g, bin_start, rec, tb, Fs, out, out_row0, store_lo, store_hi, s, far, tickets); break;
     case 50: launch_v2_shape<50>(g, bin_start, rec, tb, Fs, out, out_row0, store_lo, store_hi, s, far, tickets); break;

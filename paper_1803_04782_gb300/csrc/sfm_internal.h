@@ -66,6 +66,37 @@ static_assert((kTableGuard + max_class_table_floats(kMaxTableRadius)) * 4 +
                       kV2Threads / 32 * 32 * 8 <= 227 * 1024 - 1024,
               "class tables exceed shared memory");
 
+// Row-trimmed class-table gather (sfm_field3.cu): 32 x 32 su footprints,
+// lane = column, blocks of 8 rows.  Seven zero rows above
+// and below each window (a visit reads whole blocks) and at least 31 zero
+// columns after each row; the row stride is one of a few compile-time
+// classes.  Radius 1..40.
+constexpr int kField3PadRows = 7;
+constexpr int kShape16x16 = 0, kShape32x16 = 1, kShape32x32 = 2;
+constexpr int field3_stride(int r) {
+  // >= 2r + 32: zero columns for 32 lanes
+  if (r < 1 || r > 40) return 0;
+  for (int sp = 48; sp <= 112; sp += 32)
+    if (sp >= 2 * r + 32) return sp;
+  return 0;
+}
+constexpr size_t field3_table_floats(int r) {
+  return field3_stride(r) ? (size_t)4 * (2 * r + 1 + 2 * kField3PadRows) * field3_stride(r) : 0;
+}
+constexpr size_t max_field3_table_floats() {
+  size_t m = 0;
+  for (int r = 0; r <= kMaxTableRadius; ++r)
+    m = field3_table_floats(r) > m ? field3_table_floats(r) : m;
+  return m;
+}
+static_assert((kTableGuard + max_field3_table_floats()) * 4 + kV2Threads / 32 * 32 * 8 <=
+                  227 * 1024,
+              "row-trimmed gather tables exceed shared memory");
+// the row-trimmed footprint `shape` can run at radius r
+constexpr bool field3_shape_ok(int shape, int r) {
+  return field3_stride(r) != 0 && shape == kShape32x32;
+}
+
 // device error flags (sticky until read by a synchronising call)
 enum : uint32_t {
   kErrPlaceConflict = 1u,  // two pedestrians on one su, or on a WALL/EXIT su
@@ -130,11 +161,14 @@ struct Tables {
   const float* dirdot;  // [9 goal][9 move]: Delta_move . u_goal
   const float2* hvec;   // [9]: unit heading vectors
   const float* CT;      // 4 padded heading-class tables of the v2 gather (or NULL)
-  int shape = 0;        // class-table gather footprint: 0 = 16 x 16 su, 1 = 32 x 16 su
+  const float* CT3 = nullptr;  // the same in the row-trimmed gather's layout (or NULL)
+  int shape = 0;        // class-table gather footprint: kShape16x16 .. kShape32x32
 };
 
 // footprint of the class-table gather used when none has been tuned
-inline int default_field_shape(int r) { return r > 30 ? 1 : 0; }
+inline int default_field_shape(int r) {
+  return r > 30 ? (field3_stride(r) ? kShape32x32 : kShape32x16) : kShape16x16;
+}
 
 // ---- launchers (sfm_kernels.cu) ----
 void launch_tables(int r, const sfm_params& p, float* T0, float* TX, float* TY, float* KO,
@@ -198,6 +232,12 @@ size_t class_table_floats(int r);
 // a raised cosine down to 0 at r (the surrogate's near part); default none
 void launch_class_tables(int r, const sfm_params& p, float* T, cudaStream_t s,
                          double taper_in = 1e30);
+// the row-trimmed gather (sfm_field3.cu): false (nothing launched) when the
+// radius, the tables or the footprint do not select it
+bool launch_field_v3(const Geo& g, const int32_t* bin_start, const uint32_t* rec,
+                     const Tables& tb, const float* Fs, float* out, int out_row0, int store_lo,
+                     int store_hi, unsigned int* tickets, cudaStream_t s);
+void launch_class_tables3(int r, const sfm_params& p, float* T, cudaStream_t s);
 
 // The per-pedestrian stages visit the live pedestrians of bins [b_lo, b_hi)
 // through rec_id (n bounds the launch).  F rows: lattice rows [y_lo, y_hi) at

@@ -860,19 +860,7 @@ __global__ void k_class_tables(int r, int SP, double kP, double aP, double gamma
   if (i >= n) return;
   const int t = i / (TR * SP), rem = i % (TR * SP);
   const int dy = rem / SP - (r + kFieldPad), dx = rem % SP - r;
-  const int adx = dx < 0 ? -dx : dx, ady = dy < 0 ? -dy : dy;
-  double v = 0.0;
-  if (adx <= r && ady <= r && (adx | ady) != 0) {
-    const double hx = (t == 1) ? 1.0 : (t == 3 ? 0.70710678118654752440 : 0.0);
-    const double hy = (t == 2) ? 1.0 : (t == 3 ? 0.70710678118654752440 : 0.0);
-    const double d = sqrt((double)(dx * dx + dy * dy));
-    v = kP * pow(d, aP) * (1.0 + gamma * (hx * dx + hy * dy) / d);
-    // optional taper (surrogate near part): 1 up to taper_in, raised cosine
-    // to 0 at Euclidean distance r
-    if (taper_in < r && d > taper_in)
-      v *= d >= r ? 0.0 : 0.5 * (1.0 + cos(3.14159265358979323846 * (d - taper_in) / (r - taper_in)));
-  }
-  T[i] = (float)v;
+  T[i] = (float)class_kernel_value(t, dx, dy, r, kP, aP, gamma, taper_in);
 }
 
 int class_table_stride(int r) { return class_table_stride_of(r); }

@@ -1680,6 +1680,7 @@ void near_field(sfm_surrogate* S, sfm_ctx* ctx) {
   gn.r = S->cfg.near_radius;
   Tables tb = ctx->tables();
   tb.CT = S->CTnear;
+  tb.CT3 = nullptr;  // the near part runs on the 16-row gathers and their tables
   launch_field(gn, ctx->bin_start, ctx->rec, tb, ctx->Fs, S->Fnear, 0, 0, gn.H, ctx->ctr,
                ctx->stream);
 }
@@ -1723,6 +1724,7 @@ void surrogate_field(sfm_surrogate* S, sfm_ctx* ctx) {
   gn.r = S->cfg.near_radius;
   Tables tb = ctx->tables();
   tb.CT = S->CTnear;
+  tb.CT3 = nullptr;  // the near part runs on the 16-row gathers and their tables
   launch_field(gn, ctx->bin_start, ctx->rec, tb, ctx->Fs, S->Fsur, 0, 0, gn.H, ctx->ctr,
                ctx->stream, far_part(S));
 }

@@ -93,9 +93,22 @@ def _radius53():
                            goal_mode="mixed", heading_mode="random")
 
 
+def _radius8():
+    # smallest radius of the row-trimmed 32 x 16 footprint (2r + 1 = 17 rows)
+    return SG.random_scene(131, 97, 900, r=8, seed=115, obstacles=2, exits=("east", "south"),
+                           goal_mode="mixed", heading_mode="random")
+
+
+def _radius16():
+    # smallest radius of the row-trimmed 32 x 32 footprint (2r + 1 = 33 rows)
+    return SG.random_scene(150, 113, 1100, r=16, seed=116, periodic_y=1, exits=("west",),
+                           goal_mode="mixed", heading_mode="random")
+
+
 SCENES = {f.__name__[1:]: f for f in (_room_mixed, _corridor_periodic, _torus, _no_field,
                                       _tall_r1, _tiny, _dense, _wide_radius, _thin_torus,
-                                      _radius41, _radius47, _radius50, _radius53)}
+                                      _radius41, _radius47, _radius50, _radius53, _radius8,
+                                      _radius16)}
 
 
 @pytest.mark.parametrize("name", list(SCENES))
@@ -174,11 +187,12 @@ def test_near_tie_counter_matches_the_oracle(which):
             i = np.arange(len(b))
             ok = live & (s2 >= 0)
             sj = np.where(s2 >= 0, s2, 0)
-            gap = E[i, sj] - E[i, b]
-            thr = 1e-5 * (Mag[i, b] + Mag[i, sj])
-            band = 1e-5 * (T[i, b] + T[i, sj])
-            lo = int((ok & (gap <= thr - band)).sum())
-            hi = int((ok & (gap <= thr + band)).sum())
+            with np.errstate(invalid="ignore"):   # dead pedestrians: inf - inf
+                gap = E[i, sj] - E[i, b]
+                thr = 1e-5 * (Mag[i, b] + Mag[i, sj])
+                band = 1e-5 * (T[i, b] + T[i, sj])
+                lo = int((ok & (gap <= thr - band)).sum())
+                hi = int((ok & (gap <= thr + band)).sum())
             exact = int((ok & O.near_ties(E, Mag, adm)).sum())
             assert lo <= stats["near_ties"] <= hi, (lo, exact, hi, stats["near_ties"])
             ch_g, _ = sim.decisions()
@@ -314,15 +328,19 @@ def test_multi_su_placement_errors():
         assert sim.stats()["error_flags"] == 0
 
 
-@pytest.mark.parametrize("periodic", [0, 1])
-def test_banded_field_is_bitwise_the_unbanded_field(periodic):
+@pytest.mark.parametrize("periodic,footprint,r", [(0, "32x16", 7), (1, "16x16", 7),
+                                                  (0, "32x32r", 20), (1, "32x32r", 16),
+                                                  (1, "32x32r", 9)])
+def test_banded_field_is_bitwise_the_unbanded_field(periodic, footprint, r):
     """Divide-and-conquer (Eq. 1): row bands under an HBM budget give exactly
-    the unbanded field and the same ticks."""
-    sc = SG.random_scene(300, 260, 5000, r=7, seed=111, periodic_x=periodic, periodic_y=periodic,
+    the unbanded field and the same ticks, whatever the footprint (the band
+    halo rows fall inside footprints)."""
+    sc = SG.random_scene(300, 260, 5000, r=r, seed=111, periodic_x=periodic, periodic_y=periodic,
                          ring=not periodic, exits=() if periodic else ("east",),
                          goal_mode="mixed", heading_mode="random")
     budget = sfm.band_budget(sc.W, sc.H, 64)
     with sfm.Sim(sc) as a, sfm.Sim(sc, hbm_budget_bytes=budget) as b:
+        b.set_footprint(footprint)
         assert b.stats()["bands"] >= 4
         a.compute_field()
         np.testing.assert_array_equal(a.field(), b.field_banded())
@@ -337,30 +355,38 @@ def test_banded_field_is_bitwise_the_unbanded_field(periodic):
 
 
 @pytest.mark.parametrize("name", ["room_mixed", "torus", "thin_torus", "wide_radius", "radius41",
-                                  "radius47", "dense", "tall_r1"])
-def test_both_gather_footprints_give_the_same_field_and_ticks(name):
-    """The 16x16 and 32x16 footprints add each su's terms in the same order:
-    fields and ticks are bitwise equal, and equal to the autotuner's choice."""
+                                  "radius47", "radius50", "dense", "tall_r1", "corridor_periodic",
+                                  "tiny", "radius8", "radius16"])
+def test_all_gather_footprints_give_the_same_field_and_ticks(name):
+    """The 16x16 and 32x16 footprints and the row-trimmed 32x32 and 32x16
+    ones add each su's terms in the same order: fields and ticks are bitwise
+    equal, and equal to the autotuner's choice (where the radius is below
+    their range the row-trimmed shapes run as the 32x16 gather)."""
     sc = SCENES[name]()
-    with sfm.Sim(sc) as a, sfm.Sim(sc) as b, sfm.Sim(sc) as c:
-        a.set_footprint("16x16")
-        b.set_footprint("32x16")
-        assert c.autotune() in ("16x16", "32x16")
-        for s in (a, b, c):
+    sims = [sfm.Sim(sc) for _ in range(len(sfm.FOOTPRINTS) + 1)]
+    try:
+        for s, fp in zip(sims, sfm.FOOTPRINTS):
+            s.set_footprint(fp)
+        assert sims[-1].autotune() in sfm.FOOTPRINTS
+        for s in sims:
             s.compute_field()
-        np.testing.assert_array_equal(a.field(), b.field())
-        np.testing.assert_array_equal(a.field(), c.field())
+        a = sims[0]
+        for s in sims[1:]:
+            np.testing.assert_array_equal(a.field(), s.field())
         for _ in range(3):
-            for s in (a, b, c):
+            for s in sims:
                 s.step(1)
-            for s in (b, c):
+            for s in sims[1:]:
                 np.testing.assert_array_equal(a.field(), s.field())
                 np.testing.assert_array_equal(a.decisions()[0], s.decisions()[0])
                 for x, y in zip(a.peds(), s.peds()):
                     np.testing.assert_array_equal(x, y)
         with pytest.raises(sfm.SfmError) as e:
-            sfm._check(a.ctx, sfm.lib().sfm_set_field_footprint(a.ctx, 2))
+            sfm._check(a.ctx, sfm.lib().sfm_set_field_footprint(a.ctx, len(sfm.FOOTPRINTS)))
         assert e.value.status == sfm.SFM_EINVAL
+    finally:
+        for s in sims:
+            s.close()
 
 
 @pytest.mark.parametrize("name", ["room_mixed", "torus", "dense", "tall_r1", "thin_torus",

@@ -66,7 +66,9 @@ def test_tcgen05_wait_that_runs_out_reports_timeout_and_falls_back(after):
     result as before."""
     rng = np.random.default_rng(22)
     params = _rounded_params(6, scale=0.5)
-    X = bf16(rng.random((3, 157, 333)) * 0.3)
+    # 394 x 394 layer-2 outputs: 396 tiles of 4 x 128, at least two per CTA
+    # on 152 SMs, so after = 1 stops every CTA with tiles left
+    X = bf16(rng.random((3, 400, 400)) * 0.3)
     with sfm.Surrogate(params=sfm.flatten_params(params)) as s:
         Ym = s.forward(X, tcgen05=False)
         s.test_stop_copies(after)
