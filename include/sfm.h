@@ -420,8 +420,10 @@ sfm_status sfm_surrogate_field(sfm_surrogate* sur, sfm_ctx* ctx, float* out, int
  * candidates, computed bit for bit as the exact gather computes it.  If
  * F_sur - F varies by less than the margin over a pedestrian's admissible
  * candidates (max - min), its move equals the exact path's: an error common
- * to all candidates cancels.  delta starts at +infinity (every pedestrian
- * falls back: exact moves, no speed-up).
+ * to all candidates cancels.  delta starts at +infinity: every pedestrian
+ * falls back, and such a tick runs neither the network nor the surrogate
+ * composition -- it is the exact tick with the field computed at each
+ * pedestrian's 9 candidates only (moves equal to sfm_step's bit for bit).
  * sfm_surrogate_set_delta: delta >= 0 (or +inf) by hand.
  * sfm_surrogate_calibrate: on ctx's current state, delta = the `quantile`
  *   (in [0, 1]) over live pedestrians of the spread max - min of F_sur - F

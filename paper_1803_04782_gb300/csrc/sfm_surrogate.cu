@@ -1268,6 +1268,47 @@ __global__ void __launch_bounds__(kFbThreads, 1)
   }
 }
 
+// Every pedestrian listed for the exact candidate field (delta = +inf): per
+// record slot i (bin order) the flag, and the guidance distances,
+// admissible candidates, heading and goal k_sur_fallback decides from; no
+// surrogate field is composed.  Walk-period idle pedestrians stay.
+__global__ void k_list_all(const int32_t* __restrict__ rec_id, const int32_t* __restrict__ bin_start,
+                           int nbins, Geo g, const int2* __restrict__ xy,
+                           const uint8_t* __restrict__ heading, const uint8_t* __restrict__ goal,
+                           const uint8_t* __restrict__ ocls, const int32_t* __restrict__ D,
+                           uint8_t* __restrict__ choice, int32_t* __restrict__ nflag,
+                           uint8_t* __restrict__ fb_flag, int32_t* __restrict__ fb_dd,
+                           uint32_t* __restrict__ fb_info, WalkPeriods wp) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  bool listed = false;
+  if (i < bin_start[nbins]) {
+    const int p = rec_id[i];
+    const long long t = wp.period ? wp.ctr->t : 0;
+    if (wp.period && t % wp.period[p] != wp.phase[p]) {
+      choice[p] = 0;  // not this pedestrian's tick (walk period): it stays
+    } else {
+      int cx[3], ry[3];
+      bool okx[3], oky[3];
+      candidate_coords(xy[p], g, cx, ry, okx, oky);
+      int32_t dd[9];
+      uint8_t oc[9];
+      candidate_loads(g, ocls, D, cx, ry, dd, oc);
+      uint32_t mask = 0;
+#pragma unroll
+      for (int k = 0; k < 9; ++k) {
+        fb_dd[(size_t)i * 9 + k] = dd[k];
+        const int xi = move_dx(k) + 1, yi = move_dy(k) + 1;
+        if (k == 0 || (okx[xi] && oky[yi] && dd[k] != kDWall && oc[k] == 0)) mask |= 1u << k;
+      }
+      fb_info[i] = mask | (uint32_t)heading[p] << 9 | (uint32_t)goal[p] << 16;
+      listed = true;
+    }
+    fb_flag[i] = listed;
+  }
+  const unsigned nl = __popc(__ballot_sync(0xffffffffu, listed));
+  if ((threadIdx.x & 31) == 0 && nl) atomicAdd(nflag, (int32_t)nl);
+}
+
 // running totals of listed and decided pedestrians over surrogate ticks
 __global__ void k_count_fallbacks(const int32_t* __restrict__ nflag, const int32_t* __restrict__ nrec,
                                   unsigned long long* __restrict__ tot) {
@@ -1734,6 +1775,10 @@ void surrogate_field(sfm_surrogate* S, sfm_ctx* ctx) {
 // surrogate field is composed at each pedestrian's candidates from Y (which
 // surrogate_far must have computed) and the near tables; else it is read
 // from Fsur (surrogate_field).  ref/raw_flips as k_sur_decide.
+// The exact candidate field and decision of every listed pedestrian
+// (k_sur_fallback on the context's class tables).
+void surrogate_fallback(sfm_surrogate* S, sfm_ctx* ctx, uint8_t* choice);
+
 void surrogate_decide(sfm_surrogate* S, sfm_ctx* ctx, uint8_t* choice, const uint8_t* ref,
                       unsigned long long* raw_flips, bool cand) {
   const Geo& g = ctx->geo;
@@ -1742,6 +1787,17 @@ void surrogate_decide(sfm_surrogate* S, sfm_ctx* ctx, uint8_t* choice, const uin
   cudaStream_t st = ctx->stream;
   cudaMemsetAsync(S->nflag, 0, sizeof(int32_t), st);
   if (ctx->n <= 0) return;
+  if (cand && std::isinf(S->delta) && !ref) {
+    // delta = +inf: every pedestrian falls back, so neither the network's
+    // output nor the surrogate composition is needed -- the exact tick with
+    // the field computed at the candidates only
+    k_list_all<<<cdiv(ctx->n, 256), 256, 0, st>>>(ctx->rec_id, ctx->bin_start, nbins, g, ctx->xy,
+                                                  ctx->heading, ctx->goal, ctx->ocls, ctx->D, choice,
+                                                  S->nflag, S->fb_flag, S->fb_dd, S->fb_info,
+                                                  ctx->walk());
+    surrogate_fallback(S, ctx, choice);
+    return;
+  }
   NearPart np;
   np.CT = S->CTnear;
   np.rn = S->cfg.near_radius;
@@ -1753,6 +1809,14 @@ void surrogate_decide(sfm_surrogate* S, sfm_ctx* ctx, uint8_t* choice, const uin
       ctx->D, S->Fsur, ctx->rec, ctx->Fs, np, far_part(S), ctx->prm.beta, tb.own, tb.dirdot,
       S->delta, choice, S->flag_list, S->nflag, S->fb_flag, S->fb_dd, S->fb_info, ref, raw_flips,
       ctx->walk());
+  surrogate_fallback(S, ctx, choice);
+}
+
+void surrogate_fallback(sfm_surrogate* S, sfm_ctx* ctx, uint8_t* choice) {
+  const Geo& g = ctx->geo;
+  const Tables tb = ctx->tables();
+  const int nbins = g.nbx * g.nby;
+  cudaStream_t st = ctx->stream;
   const int SP = class_table_stride(g.r);
   const int TS = (2 * g.r + 1 + 2 * kFieldPadRows) * SP;
   const size_t smem = (kTableGuard + 4 * (size_t)TS) * sizeof(float) +
@@ -2038,7 +2102,7 @@ sfm_status sfm_surrogate_step(sfm_surrogate* S, sfm_ctx* ctx, int32_t nsteps) {
   for (int i = 0; i < nsteps; ++i) {
     launch_clear_dead(ctx->n, ctx->alive, ctx->choice, ctx->won, st);
     ctx_run_bins(ctx);
-    surrogate_far(S, ctx);
+    if (!std::isinf(S->delta)) surrogate_far(S, ctx);  // delta = +inf: no network (exact tick)
     surrogate_decide(S, ctx, ctx->choice, nullptr, nullptr, true);
     k_count_fallbacks<<<1, 1, 0, st>>>(S->nflag, ctx->bin_start + g.nbx * g.nby, S->fb_dev);
     launch_vote(ctx->n, ctx->rec_id, ctx->bin_start, ctx->xy, ctx->choice, ctx->occ, g,

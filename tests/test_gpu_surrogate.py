@@ -144,15 +144,28 @@ def _fallback_scenes():
     ]
 
 
-@pytest.mark.parametrize("i", range(4))
+@pytest.mark.parametrize("i", range(6))
 def test_infinite_delta_falls_back_everywhere_and_reproduces_the_exact_ticks(i):
-    """With delta = +inf every pedestrian is decided on the exact field at its
-    candidates, computed by the warp fallback in the exact gather's order:
-    the trajectory equals the exact path's bit for bit."""
-    sc = _fallback_scenes()[i]
+    """With delta = +inf neither the network nor the surrogate composition
+    runs: every pedestrian is decided on the exact field at its 9 candidates
+    only, computed by the warp fallback in the exact gather's order (the
+    exact candidate-only tick).  The trajectory equals the lattice path's bit
+    for bit, on small scenes, with walk periods, and on the 4096^2 floor at
+    the benchmark's density and radius."""
+    if i < 4:
+        sc = _fallback_scenes()[i]
+    elif i == 4:
+        sc = SG.random_scene(300, 260, 6000, r=20, seed=133, obstacles=4, exits=("east", "north"),
+                             goal_mode="mixed", heading_mode="random")
+    else:
+        sc = SG.floor(side=4096, n=62500, exit_len=64)
     init = sfm.flatten_params(_rounded_params(2))
     with sfm.Sim(sc) as a, sfm.Sim(sc) as b, \
             sfm.Surrogate(coarsen=4, near_radius=3, params=init) as sur:
+        if i == 4:
+            per, pha = SG.walk_periods(sc.n, 4)
+            a.set_walk_periods(per, pha)
+            b.set_walk_periods(per, pha)
         for t in range(4):
             a.step(1)
             sur.step(b, 1)
@@ -160,7 +173,10 @@ def test_infinite_delta_falls_back_everywhere_and_reproduces_the_exact_ticks(i):
             for x, y in zip(a.peds(), b.peds()):
                 np.testing.assert_array_equal(x, y)
         fb, dec = sur.counts()
-        assert fb == dec > 0
+        if i == 4:   # walk periods: only the pedestrians whose tick it is decide
+            assert 0 < fb < dec
+        else:
+            assert fb == dec > 0
         assert a.stats()["exited"] == b.stats()["exited"]
 
 
