@@ -233,6 +233,29 @@ sfm_status sfm_place_sized(sfm_ctx* ctx, int32_t n, const int32_t* xy, const uin
 sfm_status sfm_set_walk_periods(sfm_ctx* ctx, const uint8_t* period, const uint8_t* phase,
                                 int32_t on_device);
 
+/* Pedestrian numbers for the election (k-3 of Alg. 1, Sec. 3.1): by default
+ * pedestrian p of the last placement draws its priority as number p (the
+ * SplitMix64 output indexed by (seed, tick, p)) and wins ties by the smaller
+ * p.  A context that holds one row band of a larger lattice, with its
+ * neighbours' pedestrians near the band edges as ghosts (the row-band
+ * decomposition across devices; the divide-and-conquer idea of Sec. 3.3),
+ * sets each pedestrian's number in the whole lattice here so that its
+ * elections match the whole lattice's.  ids: n int32 (n of the last
+ * sfm_place), distinct and >= 0, host or device per on_device; NULL goes
+ * back to the indices.  Every sfm_place goes back to the indices; call this
+ * after it.  Not for multi-su pedestrians (SFM_EINVAL).  Synchronising. */
+sfm_status sfm_set_ids(sfm_ctx* ctx, const int32_t* ids, int32_t on_device);
+
+/* Replace the guidance distances (the 5-7 chamfer distances to the nearest
+ * exit that exit-seekers follow) by D: W*H int32 in [0, 2^23], host or
+ * device per on_device, 2^23 meaning unreachable; WALL su are marked as
+ * walls whatever D holds there.  For a context that is one row band of a
+ * larger lattice, whose distances run through the other bands: pass the
+ * whole lattice's distances for the band's rows (sfm_read_guidance of a
+ * context over the whole lattice gives them).  Synchronising; SFM_EINVAL for
+ * values out of range (nothing changed). */
+sfm_status sfm_set_guidance(sfm_ctx* ctx, const int32_t* D, int32_t on_device);
+
 /* How the pedestrians are sorted into bins each tick (the bin records and
  * every result are identical either way): 1 = by scanning the per-su class
  * grid (cost follows the lattice area), 2 = from the pedestrian list with

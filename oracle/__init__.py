@@ -84,6 +84,8 @@ def lib():
         L.orc_vote_sized.argtypes = [M, C.c_int64, C.c_int32, P, P, P, P, P, P]
         L.orc_vote.restype = C.c_int32
         L.orc_vote.argtypes = [M, C.c_int64, C.c_int32, P, P, P, P]
+        L.orc_vote_numbered.restype = C.c_int32
+        L.orc_vote_numbered.argtypes = [M, C.c_int64, C.c_int32, P, P, P, P, P]
         L.orc_commit.restype = C.c_int32
         L.orc_commit.argtypes = [M, P, C.c_int32, P, P, P, P, P, P, P]
         L.orc_step.restype = C.c_int32
@@ -253,8 +255,9 @@ def near_ties(E, Mag, adm, rtol=1e-5):
         return ok & (gap <= rtol * (Mag[i, b] + Mag[i, sj]))
 
 
-def vote(m: Model, t: int, xy, alive, choice, w=None, h=None):
-    """Winners of the tick's moves (w/h: multi-su pedestrians, claims)."""
+def vote(m: Model, t: int, xy, alive, choice, w=None, h=None, ids=None):
+    """Winners of the tick's moves (w/h: multi-su pedestrians, claims; ids:
+    the pedestrians' numbers for their priorities, default their indices)."""
     xy = np.ascontiguousarray(xy, np.int32)
     alive = np.ascontiguousarray(alive, np.uint8)
     choice = np.ascontiguousarray(choice, np.uint8)
@@ -264,6 +267,10 @@ def vote(m: Model, t: int, xy, alive, choice, w=None, h=None):
         h = np.ascontiguousarray(h, np.uint8)
         maxc = lib().orc_vote_sized(C.byref(m), t, xy.shape[0], _p(xy), _p(alive), _p(choice),
                                     _p(w), _p(h), _p(won))
+    elif ids is not None:
+        ids = np.ascontiguousarray(ids, np.int32)
+        maxc = lib().orc_vote_numbered(C.byref(m), t, xy.shape[0], _p(xy), _p(alive),
+                                       _p(choice), _p(ids), _p(won))
     else:
         maxc = lib().orc_vote(C.byref(m), t, xy.shape[0], _p(xy), _p(alive), _p(choice),
                               _p(won))

@@ -371,7 +371,7 @@ void orc_decide(const orc_model* m, const uint8_t* cell, const int32_t* occ, con
 }
 
 /* ---- vote (sub-job k-3) ---- */
-typedef struct { int64_t target; uint64_t prio; int32_t id; } orc_reg;
+typedef struct { int64_t target; uint64_t prio; int32_t id, p; } orc_reg;
 
 static int reg_cmp(const void* a, const void* b) {
   const orc_reg* x = (const orc_reg*)a;
@@ -382,9 +382,13 @@ static int reg_cmp(const void* a, const void* b) {
 }
 
 /* won[p] = 1 for the winner of each contested su; returns the number of
- * registrants of the most contested su (the enrollment bound says <= 8). */
-int32_t orc_vote(const orc_model* m, int64_t t, int32_t n, const int32_t* xy,
-                 const uint8_t* alive, const uint8_t* choice, uint8_t* won) {
+ * registrants of the most contested su (the enrollment bound says <= 8).
+ * Pedestrian p is numbered ids[p] (its priority and tie-break), or p when
+ * ids is NULL: a lattice that is one band of a larger one numbers its
+ * pedestrians, ghosts included, as the larger lattice does. */
+int32_t orc_vote_numbered(const orc_model* m, int64_t t, int32_t n, const int32_t* xy,
+                          const uint8_t* alive, const uint8_t* choice, const int32_t* ids,
+                          uint8_t* won) {
   orc_reg* regs = (orc_reg*)malloc(sizeof(orc_reg) * (size_t)(n > 0 ? n : 1));
   int32_t nr = 0;
   for (int32_t p = 0; p < n; ++p) {
@@ -395,8 +399,9 @@ int32_t orc_vote(const orc_model* m, int64_t t, int32_t n, const int32_t* xy,
         !wrap(xy[2 * p + 1] + ODY[choice[p]], m->H, m->periodic_y, &ny))
       continue; /* an off-lattice target is never admissible */
     regs[nr].target = (int64_t)ny * m->W + nx;
-    regs[nr].prio = orc_prio(m->seed, t, p);
-    regs[nr].id = p;
+    regs[nr].prio = orc_prio(m->seed, t, ids ? ids[p] : p);
+    regs[nr].id = ids ? ids[p] : p;
+    regs[nr].p = p;
     ++nr;
   }
   qsort(regs, (size_t)nr, sizeof(orc_reg), reg_cmp);
@@ -404,12 +409,17 @@ int32_t orc_vote(const orc_model* m, int64_t t, int32_t n, const int32_t* xy,
   for (int32_t i = 0; i < nr;) {
     int32_t j = i;
     while (j < nr && regs[j].target == regs[i].target) ++j;
-    won[regs[i].id] = 1;
+    won[regs[i].p] = 1;
     if (j - i > maxc) maxc = j - i;
     i = j;
   }
   free(regs);
   return maxc;
+}
+
+int32_t orc_vote(const orc_model* m, int64_t t, int32_t n, const int32_t* xy,
+                 const uint8_t* alive, const uint8_t* choice, uint8_t* won) {
+  return orc_vote_numbered(m, t, n, xy, alive, choice, NULL, won);
 }
 
 /* Vote with multi-su pedestrians: a mover claims the su its rectangle newly

@@ -34,7 +34,7 @@ EXPORTS = [
     "sfm_compute_field_into", "sfm_read_static_field", "sfm_read_guidance", "sfm_read_peds",
     "sfm_read_decisions", "sfm_stats", "sfm_set_timing", "sfm_stage_times",
     "sfm_autotune", "sfm_set_field_footprint", "sfm_set_binning", "sfm_set_walk_periods",
-    "sfm_place_sized", "sfm_snapshot", "sfm_restore", "sfm_field_noalloc", "sfm_batch_create", "sfm_batch_place", "sfm_batch_offsets",
+    "sfm_place_sized", "sfm_snapshot", "sfm_restore", "sfm_set_ids", "sfm_set_guidance", "sfm_field_noalloc", "sfm_batch_create", "sfm_batch_place", "sfm_batch_offsets",
     "sfm_batch_autotune", "sfm_batch_test_missing_ctas", "sfm_surrogate_nparams",
     "sfm_surrogate_create", "sfm_surrogate_destroy", "sfm_surrogate_last_error",
     "sfm_surrogate_set_params", "sfm_surrogate_get_params", "sfm_surrogate_grad",
@@ -120,6 +120,8 @@ def lib():
             "sfm_set_field_footprint": (C.c_int, [P, I32]),
             "sfm_set_binning": (C.c_int, [P, I32]),
             "sfm_set_walk_periods": (C.c_int, [P, P, P, I32]),
+            "sfm_set_ids": (C.c_int, [P, P, I32]),
+            "sfm_set_guidance": (C.c_int, [P, P, I32]),
             "sfm_place_sized": (C.c_int, [P, I32, P, P, P, P, P, P, I32]),
             "sfm_snapshot": (C.c_int, [P, P, C.POINTER(C.c_size_t)]),
             "sfm_restore": (C.c_int, [P, P, C.c_size_t]),
@@ -541,6 +543,21 @@ class Sim:
         _check(self.ctx, lib().sfm_set_walk_periods(
             self.ctx, self._period.ctypes.data_as(C.c_void_p),
             self._phase.ctypes.data_as(C.c_void_p), 0))
+
+    def set_ids(self, ids=None):
+        """The pedestrians' numbers for the election (sfm_set_ids); None: the
+        indices.  Reset by every placement."""
+        if ids is None:
+            _check(self.ctx, lib().sfm_set_ids(self.ctx, None, 0))
+            return
+        ids = np.ascontiguousarray(ids, np.int32)
+        _check(self.ctx, lib().sfm_set_ids(self.ctx, ids.ctypes.data_as(C.c_void_p), 0))
+
+    def set_guidance(self, D):
+        """Replace the guidance distances (sfm_set_guidance), H x W int32."""
+        D = np.ascontiguousarray(D, np.int32)
+        assert D.size == self.W * self.H
+        _check(self.ctx, lib().sfm_set_guidance(self.ctx, D.ctypes.data_as(C.c_void_p), 0))
 
     def set_binning(self, mode: str):
         """"auto", "grid" (scan the class grid) or "peds" (from the pedestrian list)."""

@@ -214,7 +214,7 @@ void run_tick(sfm_ctx* c) {
   {
     StageScope sc(c, SFM_STAGE_VOTE);
     launch_vote(c->n, c->rec_id, c->bin_start, c->xy, c->choice, c->occ, g, c->prm.seed, c->ctr,
-                c->won, c->stream, c->sizes());
+                c->won, c->stream, c->sizes(), c->ids());
     if (c->n > 0) ++c->launches;
   }
   StageScope sc(c, SFM_STAGE_COMMIT);
@@ -616,7 +616,7 @@ static sfm_status place_impl(sfm_ctx* ctx, int32_t n, const int32_t* xy, const u
   // into the same arrays with the same options (no walk periods, the same
   // sizing), so a place / step / read loop keeps replaying them.
   const bool keep_graphs = ctx->placed && n == ctx->n && n <= ctx->cap && !ctx->walk_periods &&
-                           (w != nullptr) == ctx->sized;
+                           !ctx->has_ids && (w != nullptr) == ctx->sized;
   if (!keep_graphs) drop_graph(ctx);
   if (n < 0 || (n > 0 && !xy)) return fail(ctx, SFM_EINVAL, "bad pedestrian arrays");
   // multi-su pedestrians: odd sides in [1, kMaxPedSide]; a periodic extent of
@@ -684,6 +684,7 @@ static sfm_status place_impl(sfm_ctx* ctx, int32_t n, const int32_t* xy, const u
     dfree(ctx, ctx->bin_key);
     dfree(ctx, ctx->period);
     dfree(ctx, ctx->phase);
+    dfree(ctx, ctx->gid);
     dfree(ctx, ctx->pw);
     dfree(ctx, ctx->ph);
     dfree(ctx, ctx->pl_xy);
@@ -704,6 +705,7 @@ static sfm_status place_impl(sfm_ctx* ctx, int32_t n, const int32_t* xy, const u
     TRY(dalloc(ctx, &ctx->bin_key, (size_t)n));
     TRY(dalloc(ctx, &ctx->period, (size_t)n));
     TRY(dalloc(ctx, &ctx->phase, (size_t)n));
+    TRY(dalloc(ctx, &ctx->gid, (size_t)n));
     TRY(dalloc(ctx, &ctx->pw, (size_t)n));
     TRY(dalloc(ctx, &ctx->ph, (size_t)n));
     TRY(dalloc(ctx, &ctx->pl_xy, (size_t)n));
@@ -725,6 +727,7 @@ static sfm_status place_impl(sfm_ctx* ctx, int32_t n, const int32_t* xy, const u
     TRY(dalloc(ctx, &ctx->bin_key, 1));
     TRY(dalloc(ctx, &ctx->period, 1));
     TRY(dalloc(ctx, &ctx->phase, 1));
+    TRY(dalloc(ctx, &ctx->gid, 1));
     TRY(dalloc(ctx, &ctx->pw, 1));
     TRY(dalloc(ctx, &ctx->ph, 1));
     TRY(dalloc(ctx, &ctx->pl_xy, 1));
@@ -735,6 +738,7 @@ static sfm_status place_impl(sfm_ctx* ctx, int32_t n, const int32_t* xy, const u
   }
   ctx->placed = false;
   ctx->walk_periods = false;  // a placement starts with every pedestrian active
+  ctx->has_ids = false;       // and numbers its pedestrians by index
   ctx->n = n;
   const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   if (n > 0 && !direct) {
@@ -969,6 +973,55 @@ sfm_status sfm_set_walk_periods(sfm_ctx* ctx, const uint8_t* period, const uint8
   }
   ctx->walk_periods = true;
   return SFM_OK;
+}
+
+sfm_status sfm_set_ids(sfm_ctx* ctx, const int32_t* ids, int32_t on_device) {
+  if (!ctx) return SFM_EINVAL;
+  if (ctx->batch) return fail(ctx, SFM_EINVAL, "pedestrian numbers are per single lattice");
+  if (!ctx->placed) return fail(ctx, SFM_ESTATE, "pedestrian numbers need placed pedestrians");
+  if (ctx->sized) return fail(ctx, SFM_EINVAL, "pedestrian numbers with multi-su pedestrians");
+  drop_graph(ctx);
+  if (!ids) {
+    ctx->has_ids = false;
+    return SFM_OK;
+  }
+  const int n = ctx->n;
+  std::vector<int32_t> h((size_t)n);
+  if (n > 0)
+    CU(cudaMemcpy(h.data(), ids, (size_t)n * sizeof(int32_t),
+                  on_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost));
+  {
+    std::vector<int32_t> sorted(h);
+    std::sort(sorted.begin(), sorted.end());
+    for (int p = 0; p < n; ++p) {
+      if (sorted[p] < 0) return fail(ctx, SFM_EINVAL, "pedestrian number %d < 0", sorted[p]);
+      if (p && sorted[p] == sorted[p - 1])
+        return fail(ctx, SFM_EINVAL, "pedestrian number %d given twice", sorted[p]);
+    }
+  }
+  if (n > 0) {
+    CU(cudaMemcpyAsync(ctx->gid, h.data(), (size_t)n * sizeof(int32_t), cudaMemcpyHostToDevice,
+                       ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+  }
+  ctx->has_ids = true;
+  return SFM_OK;
+}
+
+sfm_status sfm_set_guidance(sfm_ctx* ctx, const int32_t* D, int32_t on_device) {
+  if (!ctx || !D) return SFM_EINVAL;
+  if (ctx->batch) return fail(ctx, SFM_EINVAL, "guidance is set per single lattice");
+  const size_t n = (size_t)ctx->geo.W * ctx->geo.H;
+  std::vector<int32_t> h(n);
+  CU(cudaMemcpy(h.data(), D, n * sizeof(int32_t),
+                on_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost));
+  for (size_t i = 0; i < n; ++i)
+    if (h[i] < 0 || h[i] > kDInf)
+      return fail(ctx, SFM_EINVAL, "guidance value %d at su %zu outside [0, 2^23]", h[i], i);
+  CU(cudaMemcpyAsync(ctx->D, h.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->stream));
+  launch_guidance_import(ctx->cell, ctx->D, n, ctx->stream);  // WALL su: kDWall
+  ++ctx->launches;
+  return check_flags(ctx);
 }
 
 sfm_status sfm_set_binning(sfm_ctx* ctx, int32_t mode) {

@@ -63,6 +63,8 @@ struct sfm_ctx {
   uint8_t *heading = nullptr, *goal = nullptr, *alive = nullptr, *choice = nullptr, *won = nullptr;
   uint8_t *period = nullptr, *phase = nullptr;  // walk periods (used when walk_periods)
   bool walk_periods = false;
+  int32_t* gid = nullptr;  // caller's pedestrian numbers for the election (used when has_ids)
+  bool has_ids = false;
   uint8_t *pw = nullptr, *ph = nullptr;  // multi-su pedestrians' widths / heights (when sized)
   // placement scratch (place_impl): the state before a placement that keeps
   // the tick graphs, or the new state staged from the caller's buffers
@@ -131,6 +133,7 @@ struct sfm_ctx {
     }
     return sz;
   }
+  const int32_t* ids() const { return has_ids ? gid : nullptr; }
   sfm::WalkPeriods walk() const {
     sfm::WalkPeriods wp;
     if (walk_periods) {

@@ -354,13 +354,16 @@ __device__ __forceinline__ uint8_t decide_one(
 // the target's 8 neighbours whose choice points at it) has a smaller
 // (priority, id).  Atomic-free: each mover reads the <= 8 competitors.  occ
 // holds pedestrian indices; ped_off is the lattice's first index, so the
-// priority is indexed by the pedestrian's number within its lattice.
-// Returns the registrant count of the target (0 for a stay).
+// priority is indexed by the pedestrian's number within its lattice, or by
+// gid[p] when the caller numbered the pedestrians itself (a lattice that is
+// one band of a larger one).  Returns the registrant count of the target (0
+// for a stay).
 __device__ __forceinline__ int vote_one(int p, int ped_off, const Geo& g,
                                         const int2* __restrict__ xy,
                                         const uint8_t* __restrict__ choice,
                                         const int32_t* __restrict__ occ, uint64_t seed,
-                                        long long t, uint8_t* __restrict__ won) {
+                                        long long t, uint8_t* __restrict__ won,
+                                        const int32_t* __restrict__ gid = nullptr) {
   const int k = choice[p];
   if (k == 0) {
     won[p] = 0;
@@ -371,7 +374,8 @@ __device__ __forceinline__ int vote_one(int p, int ped_off, const Geo& g,
   wrap_coord(q.x + c_dx[k], g.W, g.px, tx);
   wrap_coord(q.y + c_dy[k], g.H, g.py, ty);
   const uint64_t st = splitmix_nth(seed, (uint64_t)t + 1);
-  const uint64_t mine = splitmix_nth(st, (uint64_t)(p - ped_off) + 1);
+  const long long idp = gid ? (long long)gid[p] : (long long)(p - ped_off);
+  const uint64_t mine = splitmix_nth(st, (uint64_t)idp + 1);
   bool win = true;
   int regs = 1;
 #pragma unroll
@@ -383,8 +387,9 @@ __device__ __forceinline__ int vote_one(int p, int ped_off, const Geo& g,
     if (o < 0 || o == p) continue;
     if (choice[o] != c_opp[j]) continue;  // its move does not point at the target
     ++regs;
-    const uint64_t po = splitmix_nth(st, (uint64_t)(o - ped_off) + 1);
-    if (po < mine || (po == mine && o < p)) win = false;
+    const long long ido = gid ? (long long)gid[o] : (long long)(o - ped_off);
+    const uint64_t po = splitmix_nth(st, (uint64_t)ido + 1);
+    if (po < mine || (po == mine && ido < idp)) win = false;
   }
   won[p] = win ? 1 : 0;
   return regs;

@@ -178,6 +178,7 @@ void launch_static_field(const Geo& g, const uint8_t* cell, const Tables& tb, fl
 // One relaxation round of the guidance distances; returns via *changed.
 void launch_guidance_init(const Geo& g, const uint8_t* cell, int32_t* D, cudaStream_t s);
 void launch_guidance_export(int32_t* D, size_t n, cudaStream_t s);
+void launch_guidance_import(const uint8_t* cell, int32_t* D, size_t n, cudaStream_t s);
 void launch_guidance_round(const Geo& g, const uint8_t* cell, int32_t* D, const uint8_t* act_in,
                            uint8_t* act_out, int* changed, cudaStream_t s);
 
@@ -263,7 +264,8 @@ void launch_decide(int n, const int32_t* rec_id, const int32_t* bin_start, int b
                    const int32_t* occ = nullptr, Counters* ctr = nullptr);
 void launch_vote(int n, const int32_t* rec_id, const int32_t* bin_start, const int2* xy,
                  const uint8_t* choice, const int32_t* occ, const Geo& g, uint64_t seed,
-                 Counters* ctr, uint8_t* won, cudaStream_t s, const Sizes& sz = Sizes());
+                 Counters* ctr, uint8_t* won, cudaStream_t s, const Sizes& sz = Sizes(),
+                 const int32_t* gid = nullptr);
 void launch_commit(int n, const int32_t* rec_id, const int32_t* bin_start, int2* xy,
                    uint8_t* alive, uint8_t* heading, const uint8_t* choice, const uint8_t* won,
                    const uint8_t* cell, int32_t* occ, uint8_t* ocls, const Geo& g, Counters* ctr,

@@ -147,6 +147,13 @@ __global__ void k_guidance_export(int32_t* __restrict__ D, size_t n) {
     if (D[i] == kDWall) D[i] = kDInf;
 }
 
+// the imported form: WALL su carry kDWall whatever the caller gave there
+__global__ void k_guidance_import(const uint8_t* __restrict__ cell, int32_t* __restrict__ D, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x)
+    if (cell[i] == kWall) D[i] = kDWall;
+}
+
 __global__ void __launch_bounds__(1024)
     k_guidance_round(Geo g, const uint8_t* __restrict__ cell, int32_t* __restrict__ D,
                      const uint8_t* __restrict__ act_in, uint8_t* __restrict__ act_out,
@@ -231,6 +238,13 @@ void launch_guidance_export(int32_t* D, size_t n, cudaStream_t s) {
   int blocks = (int)((n + 255) / 256);
   if (blocks > device_sm_count() * 64) blocks = device_sm_count() * 64;
   k_guidance_export<<<blocks, 256, 0, s>>>(D, n);
+}
+
+void launch_guidance_import(const uint8_t* cell, int32_t* D, size_t n, cudaStream_t s) {
+  if (!n) return;
+  int blocks = (int)((n + 255) / 256);
+  if (blocks > device_sm_count() * 64) blocks = device_sm_count() * 64;
+  k_guidance_import<<<blocks, 256, 0, s>>>(cell, D, n);
 }
 
 void launch_guidance_round(const Geo& g, const uint8_t* cell, int32_t* D, const uint8_t* act_in,
@@ -946,21 +960,22 @@ void launch_decide(int n, const int32_t* rec_id, const int32_t* bin_start, int b
 __global__ void k_vote(const int32_t* __restrict__ rec_id, const int32_t* __restrict__ bin_start,
                        int nbins, const int2* __restrict__ xy, const uint8_t* __restrict__ choice,
                        const int32_t* __restrict__ occ, Geo g, uint64_t seed, Counters* ctr,
-                       uint8_t* __restrict__ won, Sizes sz) {
+                       uint8_t* __restrict__ won, Sizes sz, const int32_t* __restrict__ gid) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= bin_start[nbins]) return;
   const int regs = sz.w ? vote_one_sized(rec_id[i], g, xy, choice, occ, sz.w, sz.h, seed, ctr->t, won)
-                        : vote_one(rec_id[i], 0, g, xy, choice, occ, seed, ctr->t, won);
+                        : vote_one(rec_id[i], 0, g, xy, choice, occ, seed, ctr->t, won, gid);
   if (regs > 2) atomicMax(&ctr->max_registrants, regs);
   if (regs > 8) atomicOr(&ctr->err, kErrEnroll);
 }
 
 void launch_vote(int n, const int32_t* rec_id, const int32_t* bin_start, const int2* xy,
                  const uint8_t* choice, const int32_t* occ, const Geo& g, uint64_t seed,
-                 Counters* ctr, uint8_t* won, cudaStream_t s, const Sizes& sz) {
+                 Counters* ctr, uint8_t* won, cudaStream_t s, const Sizes& sz,
+                 const int32_t* gid) {
   if (n <= 0) return;
   k_vote<<<cdiv(n, 256), 256, 0, s>>>(rec_id, bin_start, g.nbx * g.nby, xy, choice, occ, g, seed,
-                                      ctr, won, sz);
+                                      ctr, won, sz, gid);
 }
 
 // ---------------------------------------------------------- S5: commit

@@ -2106,7 +2106,7 @@ sfm_status sfm_surrogate_step(sfm_surrogate* S, sfm_ctx* ctx, int32_t nsteps) {
     surrogate_decide(S, ctx, ctx->choice, nullptr, nullptr, true);
     k_count_fallbacks<<<1, 1, 0, st>>>(S->nflag, ctx->bin_start + g.nbx * g.nby, S->fb_dev);
     launch_vote(ctx->n, ctx->rec_id, ctx->bin_start, ctx->xy, ctx->choice, ctx->occ, g,
-                ctx->prm.seed, ctx->ctr, ctx->won, st);
+                ctx->prm.seed, ctx->ctr, ctx->won, st, Sizes(), ctx->ids());
     launch_commit(ctx->n, ctx->rec_id, ctx->bin_start, ctx->xy, ctx->alive, ctx->heading,
                   ctx->choice, ctx->won, ctx->cell, ctx->occ, ctx->ocls, g, ctx->ctr, st);
     ++ctx->t;

@@ -638,3 +638,27 @@ def test_full_run_invariants(maker):
         assert st.alive.sum() == sc.n                       # periodic: nobody leaves
     else:
         assert st.exited > 0                                # someone reached the exit
+
+
+def test_numbered_vote_follows_the_numbers_not_the_array_order():
+    """The election with caller-given numbers (a band's ghosts keep their
+    whole-lattice numbers): shuffling the pedestrian arrays and numbering
+    each pedestrian by its old index gives the same winners as the plain
+    vote on the original order; numbering by the identity is the plain vote."""
+    sc = SG.random_scene(60, 50, 900, r=3, seed=77, exits=("east",), heading_mode="random")
+    m = O.model(sc)
+    st = O.State(sc)
+    D = O.guidance(m, sc.cell)
+    occ, _ = O.occupancy(m, sc.cell, st.xy, st.alive)
+    ch, _, _, _ = O.decide(m, sc.cell, occ, st.xy, st.heading, st.goal, st.alive, D)
+    assert (ch > 0).sum() > 100
+    won, maxc = O.vote(m, 5, st.xy, st.alive, ch)
+    assert maxc >= 2                                   # contested su exist
+    won_id, _ = O.vote(m, 5, st.xy, st.alive, ch, ids=np.arange(sc.n))
+    np.testing.assert_array_equal(won_id, won)
+    perm = np.random.default_rng(3).permutation(sc.n)
+    won_p, _ = O.vote(m, 5, st.xy[perm], st.alive[perm], ch[perm], ids=perm)
+    np.testing.assert_array_equal(won_p, won[perm])
+    # other numbers change the priorities, so some contest changes hands
+    won_s, _ = O.vote(m, 5, st.xy, st.alive, ch, ids=np.arange(sc.n) + 1000)
+    assert not np.array_equal(won_s, won)
