@@ -803,6 +803,8 @@ def run_paper_sweep(args):
     stream = torch.cuda.current_stream()
     if args.workload == "paper-sizes":
         return run_paper_sizes(args)
+    if args.workload == "paper-sweep":
+        return run_paper_grid(args)
     if args.workload == "paper-windows":
         cases = [(r, 1) for r in (3, 10, 17, 24, 31, 38)]
         paper_s = [62, 317, 738, 1424, 2187, 3238]
@@ -856,6 +858,68 @@ def run_paper_sweep(args):
             "rows": rows,
             "time_vs_window_area": {"ms_per_window_su": slope, "ms_intercept": icpt,
                                     "r2": r2 if args.workload == "paper-windows" else None}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_paper_grid(args):
+    """The paper's 360-combination sweep (Sec. 5): periodic lattices of side
+    100, 200, ..., 1000 su, densities 0.1 ... 0.9, uni-, bi-, 4- and
+    8-directional flows of fixed-direction walkers, 7x7 fields (r = 3), 1x1
+    pedestrians, walk period 1.  One JSON line per combination (graph-
+    replayed ticks timed with CUDA events after warm-up), then a summary
+    line with, per flow count, the least-squares fit of the tick time to the
+    number of pedestrians.  The paper plots its speed-ups for these
+    combinations (its Figs. 3-6, unnamed hardware) but prints no times."""
+    import torch
+    import paper_1803_04782_gb300 as sfm
+    import scenegen as SG
+    from paper_1803_04782_gb300 import build as B
+
+    B.build()
+    sfm.lib()
+    stream = torch.cuda.current_stream()
+    ticks = max(5, min(args.steps, 20))
+    rows = []
+    for side in range(100, 1001, 100):
+        for di, rho in enumerate([0.1 * k for k in range(1, 10)]):
+            for nd in (1, 2, 4, 8):
+                sc = SG.paper_scene(side=side, density=round(rho, 1), ndir=nd, r=3,
+                                    seed=1000 + side + 10 * di + nd)
+                with sfm.Sim(sc, stream=stream) as sim:
+                    sim.step(max(args.warmup, 9))  # also builds the 8-tick graph
+                    torch.cuda.synchronize()
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    sim.step(ticks)
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    ms = e0.elapsed_time(e1) / ticks
+                row = {"side": side, "density": round(rho, 1), "directions": nd, "peds": sc.n,
+                       "ms_per_tick": ms, "ped_steps_per_s": sc.n / (ms / 1e3),
+                       "su_updates_per_s": side * side / (ms / 1e3)}
+                rows.append(row)
+                print(json.dumps({"metric": "pedestrian-steps/s", "value": row["ped_steps_per_s"],
+                                  "unit": "ped-steps/s", "config": {"workload": "paper sweep cell",
+                                                                    **row}}), flush=True)
+    fits = {}
+    for nd in (1, 2, 4, 8):
+        sel = [rw for rw in rows if rw["directions"] == nd]
+        n = np.array([rw["peds"] for rw in sel], float)
+        t = np.array([rw["ms_per_tick"] for rw in sel])
+        slope, icpt = np.polyfit(n, t, 1)
+        pred = slope * n + icpt
+        r2 = 1.0 - float(((t - pred) ** 2).sum() / max(((t - t.mean()) ** 2).sum(), 1e-30))
+        fits[str(nd)] = {"ms_per_million_peds": slope * 1e6, "ms_intercept": icpt, "r2": r2,
+                         "ms_min": float(t.min()), "ms_max": float(t.max())}
+    line = {"metric": "pedestrian-steps/s", "value": float(np.median([rw["ped_steps_per_s"] for rw in rows])),
+            "unit": "ped-steps/s (median over the 360 combinations)", "n_gpus": 1, "steps": ticks,
+            "warmup": args.warmup, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "paper sweep: sides 100-1000 x densities 0.1-0.9 x 1/2/4/8 "
+                                   "flows, periodic, 7x7 fields", "combinations": len(rows)},
+            "time_vs_pedestrians": fits}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -927,7 +991,7 @@ def main():
                              "batch-small",
                              "surrogate", "surrogate-eval", "surrogate-eval-small", "surrogate-eval-mid",
                              "paper-windows", "paper-periods",
-                             "paper-sizes"])
+                             "paper-sizes", "paper-sweep"])
     ap.add_argument("--bands", type=int, default=None,
                     help="row bands of the divide-and-conquer field pass (1 = unbanded)")
     ap.add_argument("--e2e-steps", type=int, default=10)

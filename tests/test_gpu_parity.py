@@ -202,6 +202,41 @@ def test_near_tie_counter_matches_the_oracle(which):
             assert stats["near_ties"] > 0   # equal term multisets make exact ties at r = 1
 
 
+@pytest.mark.parametrize("r,ndir,density", [(3, 8, 0.5), (38, 4, 0.5), (3, 1, 0.9)])
+def test_paper_shaped_scenes_oracle_forced(r, ndir, density):
+    """The paper's experiment shape (Sec. 5: periodic lattice, no walls or
+    exits, fixed-direction walkers in 1/2/4/8 flows, 1x1 pedestrians, walk
+    period 1) at the ends of Table III's field geometries (7x7, r = 3, and
+    77x77, r = 38) and the densest cell of the 360-combination sweep: the
+    whole field and every decision against the oracle, each tick restarted
+    from the oracle's state; votes and commits exact when no tie flipped."""
+    side = 96 if r == 3 else 160
+    sc = SG.paper_scene(side=side, density=density, ndir=ndir, r=r, seed=40 + r + ndir)
+    orc = OracleRun(sc)
+    flips = decisions = 0
+    with sfm.Sim(sc) as sim:
+        for _ in range(3):
+            st = orc.st
+            sim.place(st.xy, st.heading, st.goal, st.alive)
+            sim.set_time(st.t)
+            sim.step(1)
+            Fo, So = orc.field()
+            assert_field(sim.field(), Fo, So)
+            ch_o, E, T, adm = orc.decide(Ffull=Fo.ravel(), Sfull=So.ravel())
+            ch_g, won_g = sim.decisions()
+            f = compare_choices(ch_g, ch_o, E, T, adm)
+            xy_g, h_g, a_g = sim.peds()
+            won_o, maxc = orc.advance(ch_o)
+            assert maxc <= 8
+            if f == 0:
+                np.testing.assert_array_equal(won_g, won_o)
+                np.testing.assert_array_equal(xy_g, orc.st.xy)
+                np.testing.assert_array_equal(h_g, orc.st.heading)
+            flips += f
+            decisions += int(st.alive.sum())
+    assert flips <= max(3, 0.02 * decisions), f"{flips} tie flips in {decisions} decisions"
+
+
 def test_free_running_room_100x100_r10_50_ticks():
     """The 100x100 room with 200 exit-seekers, radius 10, 50 ticks: the GPU
     runs on its own and must stay identical to the oracle's run."""
