@@ -256,6 +256,25 @@ def oracle_sample(sc, D, xy, heading, goal, alive, n_sample, t, seed=0):
     return t2 - t0, O.threads(), int(req.size), int(live.size), t1 - t0
 
 
+def host_cpu() -> str:
+    """The host CPU's model name as lscpu reports it (else /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu part")):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
 def oracle_sample_desc(n_sample):
     return (f"per step: {n_sample} random live pedestrians decide (the oracle evaluates the "
             f"field by direct FP64 superposition at their 9 candidates only, not on the "
@@ -325,6 +344,7 @@ def run_reference(args):
         "config": workload_config(args, sc, desc),
         "parallelism": "CPU oracle, rank 0 only",
         "cpu_baseline": {"value": value, "unit": "ped-steps/s", "cores": thr, "kind": "oracle",
+                         "cpu_model": host_cpu(),
                          "sample": oracle_sample_desc(n_sample),
                          "sample_peds_per_step": n_sample,
                          "sample_fraction_of_live_crowd": frac,
@@ -488,6 +508,7 @@ def run_gpu(args):
         s, thr, ns, nl, sd = oracle_sample(sc, D, xy1.copy(), h1.copy(), sc.goal.copy(),
                                            a1.copy(), args.ref_sample, 0)
         cpu = {"value": ns / s, "unit": "ped-steps/s", "cores": thr, "kind": "oracle",
+               "cpu_model": host_cpu(),
                "sample": oracle_sample_desc(args.ref_sample) + " (one step)",
                "sample_peds": ns, "sample_fraction_of_live_crowd": ns / max(1, nl),
                "seconds_timed": s, "seconds_deciding": sd,
