@@ -107,11 +107,15 @@ __global__ void __launch_bounds__(kV2Threads, 1)
                            mask | (sx < 0 ? 0x10000 : 0) | (sy < 0 ? 0x20000 : 0));
         },
         [&](const int2 it) {
-          const float* p = sT + it.x + ((it.y & 0x10000) ? -lane : lane);
-          if (it.y & 0x20000)
-            add_blocks<-SP, NB, NG>(p, (uint32_t)it.y, acc);
+          // the item is the same in every lane; its OR over the warp is a
+          // value the compiler knows to be warp-uniform, so the block and
+          // mirror tests below are uniform branches
+          const uint32_t u = __reduce_or_sync(0xffffffffu, (uint32_t)it.y);
+          const float* p = sT + it.x + ((u & 0x10000) ? -lane : lane);
+          if (u & 0x20000)
+            add_blocks<-SP, NB, NG>(p, u, acc);
           else
-            add_blocks<SP, NB, NG>(p, (uint32_t)it.y, acc);
+            add_blocks<SP, NB, NG>(p, u, acc);
         });
     const int xx = x0 + lane;
 #pragma unroll
