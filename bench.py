@@ -604,26 +604,34 @@ def run_batch(args):
     ped_steps = 0.5 * (alive0 + alive1) * args.steps
     value = ped_steps / elapsed
 
-    # the plain exact path: each scene in its own context, one after another
-    # (each context's footprint autotuned like the batch's)
+    # the plain exact path: each scene in its own context (footprint
+    # autotuned like the batch's), (a) on one stream, one context after
+    # another, and (b) spread over 16 streams so that different contexts'
+    # kernels may run at the same time
     plain_steps = max(3, min(args.steps, 10))
-    sims = [sfm.Sim(s, stream=stream) for s in scenes]
-    for s in sims:
-        s.autotune()
-    # two warm-up ticks each: the first runs stage by stage, the second builds
-    # every graph the timed ticks replay (no capture inside the timed region)
-    for s in sims:
-        s.step(2)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for s in sims:
-        s.step(plain_steps)
-    torch.cuda.synchronize()
-    plain_t = time.perf_counter() - t0
-    plain_alive = sum(s.stats()["alive"] for s in sims)
-    for s in sims:
-        s.close()
-    plain_value = plain_alive * plain_steps / plain_t
+
+    def plain_path(nstreams):
+        streams = [stream] if nstreams == 1 else [torch.cuda.Stream() for _ in range(nstreams)]
+        sims = [sfm.Sim(s, stream=streams[i % nstreams]) for i, s in enumerate(scenes)]
+        for s in sims:
+            s.autotune()
+        # two warm-up ticks each: the first runs stage by stage, the second
+        # builds every graph the timed ticks replay (no capture in the timing)
+        for s in sims:
+            s.step(2)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for s in sims:
+            s.step(plain_steps)
+        torch.cuda.synchronize()
+        t = time.perf_counter() - t0
+        alive = sum(s.stats()["alive"] for s in sims)
+        for s in sims:
+            s.close()
+        return alive * plain_steps / t
+
+    plain_value = plain_path(1)
+    plain_value_mt = plain_path(16)
 
     pk, _ = peaks()
     mhz, mhz_src = max_sm_mhz(clk, pk)
@@ -637,8 +645,13 @@ def run_batch(args):
                    "l2": "inputs larger than L2", "parallelism": "single GPU"},
         "su_updates_per_s": su * args.steps / elapsed,
         "plain_exact_path": {"value": plain_value, "unit": "ped-steps/s",
-                             "how": f"{nsc} contexts stepped one after another, {plain_steps} ticks"},
+                             "how": f"{nsc} contexts stepped one after another on one stream, "
+                                    f"{plain_steps} ticks"},
+        "plain_exact_path_16_streams": {"value": plain_value_mt, "unit": "ped-steps/s",
+                                        "how": f"{nsc} contexts on 16 streams (round robin), "
+                                               f"{plain_steps} ticks, launched back to back"},
         "speedup_vs_plain": value / plain_value,
+        "speedup_vs_plain_16_streams": value / plain_value_mt,
         "roofline": gather_roofline(pairs, field_s, sm_count(torch, torch.cuda.current_device()),
                                     mhz, mhz_src, "k_tick_batch (field only)"),
         "cpu_baseline": None, "e2e": None, "clocks": clk, "gpu_launches": int(launches),
