@@ -360,6 +360,89 @@ def run_reference(args):
     return 0
 
 
+# ------------------------------------------------------------ secondary
+def tick_rate(torch, sim, stream, ticks, timing_every=TIMING_EVERY):
+    """Graph-replayed ticks of a placed, warmed-up context: ms per tick over
+    `ticks` (CUDA events on its stream, stage events every `timing_every`-th
+    tick) and the field ms per timed tick."""
+    sim.set_timing(timing_every)
+    sim.stage_times()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sim.step(ticks)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    st, nt = sim.stage_times()
+    sim.set_timing(False)
+    return e0.elapsed_time(e1) / ticks, st["field"] / max(1, nt)
+
+
+def secondary_measurements(torch, sfm, stream, nsm, mhz, mhz_src, ticks=20):
+    """The other configurations, measured in the same run as the headline so
+    that their numbers come from the same box and clock: the 1000x200
+    corridor and the 100x100 room (autotuned, unbanded), the batch of 256
+    rooms (one persistent launch per tick, autotuned), and the floor's exact
+    tick with the field at each pedestrian's 9 candidates only (unbanded; the
+    surrogate entry point with delta = +inf, which runs no network) beside
+    its lattice tick."""
+    import scenegen as SG
+    out = {}
+    for name in ("corridor", "room"):
+        sc, desc = workload(name)
+        with sfm.Sim(sc, stream=stream) as sim:
+            fp = sim.autotune()
+            sim.set_timing(TIMING_EVERY)
+            sim.step(10)
+            xy0, _, a0 = sim.peds()
+            ms, fms = tick_rate(torch, sim, stream, ticks)
+            pairs = pair_count(sc, xy0, a0)
+            out[name] = {"workload": desc, "ped_steps_per_s": int(a0.sum()) / (ms / 1e3),
+                         "ms_per_tick": ms, "field_ms": fms, "footprint": fp,
+                         "roofline": gather_roofline(pairs, fms / 1e3, nsm, mhz, mhz_src,
+                                                     GATHER_KERNEL.get(fp, "k_field"))}
+    scenes = SG.batch(nscenes=256)
+    with sfm.Batch(scenes, stream=stream) as bt:
+        bt.autotune()
+        bt.step(5)
+        bt.sync()
+        _, _, al = bt.peds()
+        alive0 = sum(int(a.sum()) for a in al)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        bt.step(5)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 5
+    out["batch"] = {"workload": "batch of 256 rooms: side U[64,2048], density U[0.05,0.4], "
+                                "radius U[5,30], 1-4 exits", "ped_steps_per_s": alive0 / (ms / 1e3),
+                    "ms_per_tick": ms}
+    sc, desc = workload("floor")
+    with sfm.Sim(sc, stream=stream) as sim:
+        sim.autotune()
+        sim.step(10)
+        ms_lat, _ = tick_rate(torch, sim, stream, 10, timing_every=0)
+        with sfm.Surrogate(coarsen=8, near_radius=3, stream=stream) as sur:
+            sur.set_delta(float("inf"))
+            sur.step(sim, 2)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            sur.step(sim, 10)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms_cand = e0.elapsed_time(e1) / 10
+        alive = sim.stats()["alive"]
+    out["floor_candidates_only"] = {
+        "workload": desc + ", unbanded", "ms_per_tick_lattice": ms_lat,
+        "ms_per_tick_candidates_only": ms_cand,
+        "ped_steps_per_s_candidates_only": alive / (ms_cand / 1e3),
+        "how": "exact moves either way (bit for bit); the candidate-only tick computes the "
+               "field at each pedestrian's 9 candidates, not on the lattice"}
+    return out
+
+
 # ------------------------------------------------------------------ GPU arm
 def run_gpu(args):
     import torch
@@ -498,6 +581,10 @@ def run_gpu(args):
             dist.destroy_process_group()
         return 0
 
+    secondary = None
+    if args.workload == "floor" and world == 1 and not args.no_secondary:
+        secondary = secondary_measurements(torch, sfm, stream, nsm, mhz, mhz_src)
+
     # CPU baseline: the oracle on a bounded sample of the same workload
     cpu = None
     if not args.no_cpu_baseline and world == 1:
@@ -534,6 +621,7 @@ def run_gpu(args):
         "roofline": roofline,
         "cpu_baseline": cpu,
         "e2e": e2e,
+        "secondary": secondary,
         "clocks": clk,
         "gpu_launches": int(launches),
         "peaks_source": pk_src,
@@ -1033,6 +1121,8 @@ def main():
                     help="field gather footprint: autotuned, or fixed")
     ap.add_argument("--ref-sample", type=int, default=100000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-secondary", action="store_true",
+                    help="skip the corridor / room / batch / candidate-only measurements")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)  # timing rule: at least 3 untimed warm-up ticks
     if args.impl == "reference":
