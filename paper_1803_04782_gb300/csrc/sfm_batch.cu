@@ -315,7 +315,7 @@ __global__ void __launch_bounds__(kBatchThreads, 1) k_tick_batch(BatchArgs a) {
     if (s_loaded != ch.scene) {
       const float2* src = reinterpret_cast<const float2*>(a.CT + sc.ct_off);
       float2* dst = reinterpret_cast<float2*>(sT);
-      for (int i = tid; i < 2 * sc.ts; i += blockDim.x) dst[i] = src[i];  // 4*ts floats
+      copy_to_shared<4>(dst, src, 2 * sc.ts);  // 4*ts floats
       __syncthreads();
       if (tid == 0) s_loaded = ch.scene;
     }

@@ -125,7 +125,7 @@ __global__ void __launch_bounds__(kV2Threads, 1)
   {
     const float2* src = reinterpret_cast<const float2*>(CT);
     float2* dst = reinterpret_cast<float2*>(sT);
-    for (int i = threadIdx.x; i < 2 * TS; i += blockDim.x) dst[i] = src[i];  // 4*TS floats
+    copy_to_shared<12>(dst, src, 2 * TS);  // 4*TS floats
     if (threadIdx.x < kTableGuard) sm[threadIdx.x] = 0.f;
   }
   __syncthreads();

@@ -1,22 +1,20 @@
 // sfm_field3.cu -- the row-trimmed class-table field gather (S2, radius 1
-// .. 44): the per-su superposition of the pedestrian field of one tick, F =
+// .. 40): the per-su superposition of the pedestrian field of one tick, F =
 // F_static + sum of K_P over the pedestrians in reach (k-5 of the paper's
 // Alg. 1, Sec. 3.1), gathered over binned pedestrians.
 //
 // A warp owns a footprint of 32 x 32 su (lane = column), in blocks of 8
-// rows.  A pedestrian visit reads only the blocks its
-// window reaches: each block is eight shared-memory reads and four packed
-// FP32 adds per lane, predicated on the block being in reach, so the visit
-// has no branch on its rows and all its reads are in flight together.  The
-// 16-row gathers of sfm_field.cu read all 16 rows of every visit, the zero
-// rows above and below a window included; the 32 x 32 footprint also
-// visits each pedestrian about 40 % fewer times per su than a 32 x 16 one
-// at r = 40.  The tables carry 7 zero rows above and below each window (a
-// block may start 7 rows before the reach) and at least 31 zero columns
-// after each row (a lane left or right of the window reads a zero of its own
-// row or of the row before), so no lane needs a range test.  Each su adds
-// its terms in the record-walk order of the other gathers, so the field is
-// the same bit for bit.
+// rows.  A pedestrian visit reads only the blocks its window reaches: each
+// block is eight shared-memory reads and four packed FP32 adds per lane,
+// behind one test that is uniform over the warp.  The 16-row gathers of
+// sfm_field.cu read all 16 rows of every visit, the zero rows above and
+// below a window included; the 32 x 32 footprint also visits each pedestrian
+// about 40 % fewer times per su than a 32 x 16 one at r = 40.  The tables
+// carry 7 zero rows above and below each window (a block may start 7 rows
+// before the reach) and at least 31 zero columns after each row (a lane left
+// or right of the window reads a zero of its own row or of the row before),
+// so no lane needs a range test.  Each su adds its terms in the record-walk
+// order of the other gathers, so the field is the same bit for bit.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -27,34 +25,29 @@ namespace sfm {
 
 namespace {
 
-// Block G of a lane: footprint rows 8G .. 8G + 7 (acc[4G] .. acc[4G + 3],
-// .x even rows, .y odd) at byte offsets 4 (8G + j) S from the lane's shared
-// address sa (S = +-SP, the signed row stride): eight reads and four packed
-// FP32 adds (each half rounded as a scalar add), all predicated on `on` --
-// a block outside the window's rows issues but reads and adds nothing, and
-// no branch splits the visit, so the reads of all blocks are in flight
-// together.
-// Block G of a lane: footprint rows 8G .. 8G + 7 (acc[4G] .. acc[4G + 3],
-// .x even rows, .y odd) at table offsets (8G + j) S from the lane's row-0
-// address p, S = +-SP the signed row stride: eight reads and four packed
+// Rows per block of the visit: a visit reads the blocks its window reaches.
+constexpr int kBlockRows = 8;
+
+// Block G of a lane: footprint rows BR G .. BR G + BR - 1 (acc[BR G / 2] ..,
+// .x even rows, .y odd) at table offsets (BR G + j) S from the lane's row-0
+// address p, S = +-SP the signed row stride: BR reads and BR / 2 packed
 // adds, done only when the block is in reach (`on`, uniform over the warp).
 template <int S, int G, int NG>
 __device__ __forceinline__ void add_block(const float* __restrict__ p, uint32_t on, float2 (&acc)[NG]) {
+  constexpr int BR = kBlockRows;
   if (on) {
 #pragma unroll
-    for (int j = 0; j < 4; ++j)
-      acc[4 * G + j] = __fadd2_rn(acc[4 * G + j],
-                                  make_float2(p[(8 * G + 2 * j) * S], p[(8 * G + 2 * j + 1) * S]));
+    for (int j = 0; j < BR / 2; ++j)
+      acc[BR / 2 * G + j] = __fadd2_rn(acc[BR / 2 * G + j],
+                                       make_float2(p[(BR * G + 2 * j) * S], p[(BR * G + 2 * j + 1) * S]));
   }
 }
 
 // the blocks of a visit; bit b of `mask` says whether block b is in reach
-template <int S, int NB, int NG>
+template <int S, int NB, int NG, int G = 0>
 __device__ __forceinline__ void add_blocks(const float* __restrict__ p, uint32_t mask, float2 (&acc)[NG]) {
-  add_block<S, 0, NG>(p, mask & 1u, acc);
-  if constexpr (NB > 1) add_block<S, 1, NG>(p, mask & 2u, acc);
-  if constexpr (NB > 2) add_block<S, 2, NG>(p, mask & 4u, acc);
-  if constexpr (NB > 3) add_block<S, 3, NG>(p, mask & 8u, acc);
+  add_block<S, G, NG>(p, mask & (1u << G), acc);
+  if constexpr (G + 1 < NB) add_blocks<S, NB, NG, G + 1>(p, mask, acc);
 }
 
 template <int SP, int FH>
@@ -63,10 +56,10 @@ __global__ void __launch_bounds__(kV2Threads, 1)
                const float* __restrict__ CT3, const float* __restrict__ Fs,
                float* __restrict__ out, int out_row0, int fy0, int fy1, int store_lo,
                int store_hi, unsigned int* __restrict__ tickets) {
-  static_assert(FH % 8 == 0 && FH / 8 <= 4, "footprint height: whole blocks, at most 4");
+  static_assert(FH % kBlockRows == 0 && FH / kBlockRows <= 16, "footprint height: whole blocks, at most 16");
   // launched only for radii whose row stride class SP >= 2r + 32 (launch_field_v3)
   extern __shared__ __align__(16) float sm[];
-  constexpr int FW = 32, NB = FH / 8, NG = FH / 2;  // NG: float2 accumulators a lane
+  constexpr int FW = 32, NB = FH / kBlockRows, NG = FH / 2;  // NG: float2 accumulators a lane
   const int r = g.r;
   const int TS = (2 * r + 1 + 2 * kField3PadRows) * SP;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -75,7 +68,7 @@ __global__ void __launch_bounds__(kV2Threads, 1)
   {
     const float4* src = reinterpret_cast<const float4*>(CT3);
     float4* dst = reinterpret_cast<float4*>(sT);
-    for (int i = threadIdx.x; i < TS; i += blockDim.x) dst[i] = src[i];  // 4 * TS floats
+    copy_to_shared<8>(dst, src, TS);  // 4 * TS floats
     if (threadIdx.x < kTableGuard) sm[threadIdx.x] = 0.f;
   }
   __syncthreads();
@@ -101,7 +94,7 @@ __global__ void __launch_bounds__(kV2Threads, 1)
         [&](int rx, int ry, int cls) {
           const int sx = class_sx(cls), sy = class_sy(cls);
           // blocks b0 .. b1 hold the rows in reach
-          const int b0 = max(0, ry - r) >> 3, b1 = min(FH - 1, ry + r) >> 3;
+          const int b0 = max(0, ry - r) / kBlockRows, b1 = min(FH - 1, ry + r) / kBlockRows;
           const int mask = (2 << b1) - (1 << b0);
           return make_int2(class_table(cls) * TS + (kField3PadRows + r - sy * ry) * SP + r - sx * rx,
                            mask | (sx < 0 ? 0x10000 : 0) | (sy < 0 ? 0x20000 : 0));

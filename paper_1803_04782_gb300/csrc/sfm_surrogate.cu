@@ -1177,7 +1177,7 @@ __global__ void __launch_bounds__(kFbThreads, 1)
   float* sT = sm + kTableGuard;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   int2* scr = reinterpret_cast<int2*>(sT + 4 * TS) + w * 32;
-  for (int i = threadIdx.x; i < 4 * TS; i += blockDim.x) sT[i] = CT[i];
+  copy_to_shared<8>(reinterpret_cast<float2*>(sT), reinterpret_cast<const float2*>(CT), 2 * TS);
   __syncthreads();
   const int nrec = bin_start[nbins], r = g.r;
   const int nchunks = (nrec + 31) / 32;
