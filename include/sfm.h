@@ -48,7 +48,7 @@
 extern "C" {
 #endif
 
-#define SFM_ABI_VERSION 4
+#define SFM_ABI_VERSION 5
 #define SFM_MAX_RADIUS 64
 #define SFM_NSTAGES 6
 
@@ -125,8 +125,9 @@ int32_t sfm_abi_version(void);
 
 /* Bytes of the lattice-sized arrays a context keeps resident whatever the
  * budget (cells, static field, guidance distances, occupancy and its class
- * grid).  A budget of sfm_resident_bytes(lat) + 4*W*(rows+2) leaves room for
- * field bands of `rows` rows (rounded down to a multiple of 32). */
+ * grid).  A budget of sfm_resident_bytes(lat) + 4*W*(rows+33) leaves room for
+ * field bands of `rows` rows (rounded down to a multiple of 32): the band
+ * buffer holds a band, the row above it and the next band's first 32 rows. */
 uint64_t sfm_resident_bytes(const sfm_lattice* lat);
 
 /* Create a context for one lattice: the discrete space of Sec. 2 (space

@@ -197,10 +197,14 @@ def sfm_resident_bytes(lat: Lattice) -> int:
     return int(lib().sfm_resident_bytes(C.byref(lat)))
 
 
+# rows of the band buffer beyond a band's own (sfm_resident_bytes in sfm.h)
+BAND_EXTRA_ROWS = 33
+
+
 def band_budget(W: int, H: int, rows: int, periodic_x: int = 0, periodic_y: int = 0) -> int:
     """HBM budget that makes the field pass run in bands of ``rows`` rows."""
     lat = Lattice(int(W), int(H), int(periodic_x), int(periodic_y))
-    return sfm_resident_bytes(lat) + 4 * int(W) * (int(rows) + 2)
+    return sfm_resident_bytes(lat) + 4 * int(W) * (int(rows) + BAND_EXTRA_ROWS)
 
 
 def sfm_create(lat: Lattice, cell, prm: Params, stream=None):

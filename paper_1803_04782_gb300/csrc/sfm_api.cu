@@ -192,6 +192,35 @@ void run_tick(sfm_ctx* c) {
                   c->ocls, c->D, c->F, 0, -1, -1, 0, 0, g.H, g, c->prm.beta, tb, c->choice,
                   c->stream, c->walk(), c->sizes(), c->occ, c->ctr);
     if (c->n > 0) ++c->launches;
+  } else if (!g.py && field3_shape_ok(tb.shape, g.r) && tb.CT3) {
+    // The band buffer as a ring of R = band rows + 33 rows, lattice row y at
+    // ring row y mod R.  Band b's launch stores the rows no earlier launch
+    // stored, through the first tile row of band b + 1 (the lower halo row
+    // yb and the 32 rows the next band's decisions start on); the upper halo
+    // row ya - 1 and the band's first tile row come from band b - 1's
+    // launch.  So every tile row of the lattice is gathered once a tick, and
+    // the rows that band b's decisions read, [ya - 1, yb], are all in the
+    // ring: band b's launch overwrites the rows before ya - 1 only.
+    const int R = c->band_rows + kBandExtraRows;
+    for (int b = 0; b < c->bands; ++b) {
+      const int ya = b * c->band_rows;
+      const int yb = ya + c->band_rows < g.H ? ya + c->band_rows : g.H;
+      const int s_lo = b == 0 ? 0 : (ya + kTile < g.H ? ya + kTile : g.H);
+      const int s_hi = yb + kTile < g.H ? yb + kTile : g.H;
+      if (s_hi > s_lo) {
+        StageScope sc(c, SFM_STAGE_FIELD);
+        launch_field(g, c->bin_start, c->rec, tb, c->Fs, c->band_buf, s_lo - s_lo % R, s_lo, s_hi,
+                     c->ctr, c->stream, FarPart(), R);
+        ++c->launches;
+      }
+      const int y_lo = ya > 0 ? ya - 1 : 0, y_hi = yb + 1 < g.H ? yb + 1 : g.H;
+      StageScope sc(c, SFM_STAGE_DECIDE);
+      launch_decide(c->n, c->rec_id, c->bin_start, (ya / kBin) * g.nbx,
+                    ((yb + kBin - 1) / kBin) * g.nbx, c->xy, c->heading, c->goal, c->cell, c->ocls,
+                    c->D, c->band_buf, y_lo % R, -1, -1, 0, y_lo, y_hi, g, c->prm.beta, tb,
+                    c->choice, c->stream, c->walk(), c->sizes(), c->occ, c->ctr, R);
+      if (c->n > 0) ++c->launches;
+    }
   } else {
     for (int b = 0; b < c->bands; ++b) {
       const int ya = b * c->band_rows;
@@ -507,7 +536,7 @@ sfm_status sfm_create(const sfm_lattice* lat, const uint8_t* cell, int32_t cell_
            (unsigned long long)resident, (unsigned long long)budget);
       return bail(SFM_EBUDGET);
     }
-    int64_t rows = (int64_t)((budget - resident) / ((uint64_t)g.W * 4)) - 2;
+    int64_t rows = (int64_t)((budget - resident) / ((uint64_t)g.W * 4)) - kBandExtraRows;
     rows = rows / kTile * kTile;
     if (rows < kTile) {
       fail(ctx, SFM_EBUDGET, "budget leaves room for fewer than %d field rows", kTile);
@@ -528,7 +557,7 @@ sfm_status sfm_create(const sfm_lattice* lat, const uint8_t* cell, int32_t cell_
   if (ctx->bands <= 1) {
     ALLOC(ctx->F, nsu);
   } else {
-    ALLOC(ctx->band_buf, (size_t)(ctx->band_rows + 2) * g.W);
+    ALLOC(ctx->band_buf, (size_t)(ctx->band_rows + kBandExtraRows) * g.W);
   }
   ALLOC(ctx->T0, (size_t)S * S);
   ALLOC(ctx->TX, (size_t)S * S);

@@ -219,7 +219,8 @@ __device__ __forceinline__ bool in_entered(const Geo& g, int sx, int sy, int qx,
 // ---------------------------------------------------------------- S3 decide
 // E over the 9 candidates (stay + 8 neighbours), admissible iff inside, not
 // WALL and unoccupied at tick start; the minimum with ties to the smallest
-// class.  F rows: lattice rows [y_lo, y_hi) at buffer row y - y_lo + main_off,
+// class.  F rows: lattice rows [y_lo, y_hi) at buffer row y - y_lo + main_off
+// (less `ring` when that is >= ring > 0: a ring buffer of `ring` rows),
 // lo_row at buffer row 0 and hi_row at hi_off.  own / dirdot: this lattice's
 // 81-entry tables.
 // Admissible candidates (stay, or inside, not WALL and unoccupied at tick
@@ -311,7 +312,7 @@ __device__ __forceinline__ uint8_t decide_one(
     int main_off, int lo_row, int hi_row, int hi_off, int y_lo, int y_hi, float beta,
     const float* __restrict__ own, const float* __restrict__ dirdot,
     const uint8_t* __restrict__ pw = nullptr, const uint8_t* __restrict__ ph = nullptr,
-    const int32_t* __restrict__ occ = nullptr, bool* tie = nullptr) {
+    const int32_t* __restrict__ occ = nullptr, bool* tie = nullptr, int ring = 0) {
   const int2 q = xy[p];
   const int h = heading[p], gl = goal[p];
   // the 3 x 3 neighbourhood (wrapped or clipped); every load is issued
@@ -327,6 +328,7 @@ __device__ __forceinline__ uint8_t decide_one(
     const int ny = ry[d];
     fr[d] = (ny >= y_lo && ny < y_hi) ? ny - y_lo + main_off
                                       : (ny == lo_row ? 0 : (ny == hi_row ? hi_off : 0));
+    if (ring && fr[d] >= ring) fr[d] -= ring;
   }
   float f[9];
   int32_t dd[9];

@@ -276,7 +276,7 @@ static void launch_v2_shape(const Geo& g, const int32_t* bin_start, const uint32
 
 void launch_field(const Geo& g, const int32_t* bin_start, const uint32_t* rec, const Tables& tb,
                   const float* Fs, float* out, int out_row0, int store_lo, int store_hi,
-                  Counters* ctr, cudaStream_t s, const FarPart& far) {
+                  Counters* ctr, cudaStream_t s, const FarPart& far, int ring) {
   if (store_hi <= store_lo) return;
   const int sp = tb.CT ? class_table_stride(g.r) : 0;
   if (!sp) {
@@ -290,8 +290,9 @@ void launch_field(const Geo& g, const int32_t* bin_start, const uint32_t* rec, c
   // footprints per warp (launch_v2).
   unsigned int* tickets = ctr && !far.Y ? ctr->field_tickets : nullptr;
   if (!far.Y && launch_field_v3(g, bin_start, rec, tb, Fs, out, out_row0, store_lo, store_hi,
-                                tickets, s))
+                                tickets, s, ring))
     return;
+  if (ring) return;  // the caller checked that the row-trimmed gather is in use
   switch (sp) {
     case 34: launch_v2_shape<34>(g, bin_start, rec, tb, Fs, out, out_row0, store_lo, store_hi, s, far, tickets); break;
     case 50: launch_v2_shape<50>(g, bin_start, rec, tb, Fs, out, out_row0, store_lo, store_hi, s, far, tickets); break;

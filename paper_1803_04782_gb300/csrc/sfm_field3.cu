@@ -55,7 +55,7 @@ __global__ void __launch_bounds__(kV2Threads, 1)
     k_field_v3(Geo g, const int32_t* __restrict__ bin_start, const uint32_t* __restrict__ rec,
                const float* __restrict__ CT3, const float* __restrict__ Fs,
                float* __restrict__ out, int out_row0, int fy0, int fy1, int store_lo,
-               int store_hi, unsigned int* __restrict__ tickets) {
+               int store_hi, unsigned int* __restrict__ tickets, int ring) {
   static_assert(FH % kBlockRows == 0 && FH / kBlockRows <= 16, "footprint height: whole blocks, at most 16");
   // launched only for radii whose row stride class SP >= 2r + 32 (launch_field_v3)
   extern __shared__ __align__(16) float sm[];
@@ -114,9 +114,12 @@ __global__ void __launch_bounds__(kV2Threads, 1)
 #pragma unroll
     for (int j = 0; j < FH; ++j) {
       const int y = y0 + j;
-      if (xx < g.W && y < g.H && y >= store_lo && y < store_hi)
-        out[(size_t)(y - out_row0) * g.W + xx] =
+      if (xx < g.W && y < g.H && y >= store_lo && y < store_hi) {
+        int row = y - out_row0;
+        if (ring && row >= ring) row -= ring;
+        out[(size_t)row * g.W + xx] =
             Fs[(size_t)y * g.W + xx] + ((j & 1) ? acc[j >> 1].y : acc[j >> 1].x);
+      }
     }
   };
   unsigned int t = 0;
@@ -154,7 +157,7 @@ __global__ void __launch_bounds__(kV2Threads, 1)
 template <int SP, int FH>
 void launch_v3(const Geo& g, const int32_t* bin_start, const uint32_t* rec, const float* CT3,
                const float* Fs, float* out, int out_row0, int store_lo, int store_hi,
-               cudaStream_t s, unsigned int* tickets) {
+               cudaStream_t s, unsigned int* tickets, int ring) {
   constexpr int FW = 32;
   const size_t smem = (kTableGuard + field3_table_floats(g.r)) * sizeof(float) +
                       kV2Threads / 32 * 32 * sizeof(int2);
@@ -170,7 +173,7 @@ void launch_v3(const Geo& g, const int32_t* bin_start, const uint32_t* rec, cons
   if (blocks < 1) blocks = 1;
   if (nf < 4 * wpb * blocks) tickets = nullptr;
   k_field_v3<SP, FH><<<blocks, kV2Threads, smem, s>>>(g, bin_start, rec, CT3, Fs, out, out_row0,
-                                                      fy0, fy1, store_lo, store_hi, tickets);
+                                                      fy0, fy1, store_lo, store_hi, tickets, ring);
 }
 
 // the class tables in the layout of the row-trimmed gather: [4][2r+3][SP],
@@ -190,10 +193,10 @@ __global__ void k_class_tables3(int r, int SP, double kP, double aP, double gamm
 
 bool launch_field_v3(const Geo& g, const int32_t* bin_start, const uint32_t* rec,
                      const Tables& tb, const float* Fs, float* out, int out_row0, int store_lo,
-                     int store_hi, unsigned int* tickets, cudaStream_t s) {
+                     int store_hi, unsigned int* tickets, cudaStream_t s, int ring) {
   if (!tb.CT3 || !field3_shape_ok(tb.shape, g.r)) return false;
 #define SFM_V3(SP) \
-  case SP: launch_v3<SP, 32>(g, bin_start, rec, tb.CT3, Fs, out, out_row0, store_lo, store_hi, s, tickets); break;
+  case SP: launch_v3<SP, 32>(g, bin_start, rec, tb.CT3, Fs, out, out_row0, store_lo, store_hi, s, tickets, ring); break;
   // one footprint: 32 x 32 su (measured against 32 x 16 and 16 x 32 row-
   // trimmed footprints, it was the fastest on the 16384^2 floor at r = 40)
   switch (field3_stride(g.r)) {

@@ -18,6 +18,9 @@ constexpr int32_t kDWall = kDInf + 1;
 // Three-component field gather (radius > 50): a CTA owns a 32 x 32 su tile;
 // warp w owns rows 4w..4w+3 of it, lane l owns column l.
 constexpr int kTile = 32;
+// Rows of the band buffer beyond a band's: the row above the band and the
+// next band's first tile row (the ring of run_tick's banded field)
+constexpr int kBandExtraRows = kTile + 1;
 constexpr int kFieldThreads = 256;
 constexpr int kRowsPerThread = kTile / (kFieldThreads / 32);  // 4
 constexpr int kStageCap = 2048;    // pedestrians staged in shared memory per chunk
@@ -224,9 +227,12 @@ void launch_clear_dead(int n, const uint8_t* alive, uint8_t* choice, uint8_t* wo
 void launch_field_v1(const Geo& g, const int32_t* bin_start, const uint32_t* rec, const Tables& tb,
                      const float* Fs, float* out, int out_row0, int store_lo, int store_hi,
                      Counters* ctr, cudaStream_t s);
+// ring > 0: out is a ring of `ring` rows, row y stored at (y - out_row0) mod
+// ring (y - out_row0 < 2 ring); only the row-trimmed gather takes one
+// (launch_field_v3 returns false otherwise)
 void launch_field(const Geo& g, const int32_t* bin_start, const uint32_t* rec, const Tables& tb,
                   const float* Fs, float* out, int out_row0, int store_lo, int store_hi,
-                  Counters* ctr, cudaStream_t s, const FarPart& far = FarPart());
+                  Counters* ctr, cudaStream_t s, const FarPart& far = FarPart(), int ring = 0);
 int class_table_stride(int r);
 size_t class_table_floats(int r);
 // taper_in < r: entries weighted by 1 up to Euclidean distance taper_in and
@@ -237,7 +243,7 @@ void launch_class_tables(int r, const sfm_params& p, float* T, cudaStream_t s,
 // radius, the tables or the footprint do not select it
 bool launch_field_v3(const Geo& g, const int32_t* bin_start, const uint32_t* rec,
                      const Tables& tb, const float* Fs, float* out, int out_row0, int store_lo,
-                     int store_hi, unsigned int* tickets, cudaStream_t s);
+                     int store_hi, unsigned int* tickets, cudaStream_t s, int ring = 0);
 void launch_class_tables3(int r, const sfm_params& p, float* T, cudaStream_t s);
 
 // The per-pedestrian stages visit the live pedestrians of bins [b_lo, b_hi)
@@ -261,7 +267,7 @@ void launch_decide(int n, const int32_t* rec_id, const int32_t* bin_start, int b
                    int main_off, int lo_row, int hi_row, int hi_off, int y_lo, int y_hi,
                    const Geo& g, float beta, const Tables& tb, uint8_t* choice, cudaStream_t s,
                    const WalkPeriods& wp = WalkPeriods(), const Sizes& sz = Sizes(),
-                   const int32_t* occ = nullptr, Counters* ctr = nullptr);
+                   const int32_t* occ = nullptr, Counters* ctr = nullptr, int ring = 0);
 void launch_vote(int n, const int32_t* rec_id, const int32_t* bin_start, const int2* xy,
                  const uint8_t* choice, const int32_t* occ, const Geo& g, uint64_t seed,
                  Counters* ctr, uint8_t* won, cudaStream_t s, const Sizes& sz = Sizes(),

@@ -902,7 +902,7 @@ __global__ void __launch_bounds__(256, 4) k_decide(const int32_t* __restrict__ r
                          float beta, const float* __restrict__ own,
                          const float* __restrict__ dirdot, uint8_t* __restrict__ choice,
                          WalkPeriods wp, Sizes sz, const int32_t* __restrict__ occ,
-                         Counters* __restrict__ ctr) {
+                         Counters* __restrict__ ctr, int ring) {
   // grid-stride over the records of bins [b_lo, b_hi): a band's launch needs
   // no more blocks than the GPU holds, whatever its share of the crowd.  The
   // records are taken from the last backwards: the gather wrote the band's
@@ -921,7 +921,7 @@ __global__ void __launch_bounds__(256, 4) k_decide(const int32_t* __restrict__ r
     bool tie = false;
     choice[p] = decide_one<true>(p, g, xy, heading, goal, cell, ocls, D, F, main_off, lo_row,
                                  hi_row, hi_off, y_lo, y_hi, beta, own, dirdot, sz.w, sz.h, occ,
-                                 &tie);
+                                 &tie, ring);
     ++decided;
     ties += tie ? 1u : 0u;
   }
@@ -940,7 +940,7 @@ void launch_decide(int n, const int32_t* rec_id, const int32_t* bin_start, int b
                    int main_off, int lo_row, int hi_row, int hi_off, int y_lo, int y_hi,
                    const Geo& g, float beta, const Tables& tb, uint8_t* choice, cudaStream_t s,
                    const WalkPeriods& wp, const Sizes& sz, const int32_t* occ,
-                   Counters* ctr) {
+                   Counters* ctr, int ring) {
   if (n <= 0 || b_hi <= b_lo) return;
   static int max_blocks = 0;
   if (!max_blocks) {
@@ -952,7 +952,7 @@ void launch_decide(int n, const int32_t* rec_id, const int32_t* bin_start, int b
   const int blocks = cdiv(n, 256) < max_blocks ? cdiv(n, 256) : max_blocks;
   k_decide<<<blocks, 256, 0, s>>>(rec_id, bin_start, b_lo, b_hi, xy, heading, goal, cell,
                                         ocls, D, F, main_off, lo_row, hi_row, hi_off, y_lo, y_hi,
-                                        g, beta, tb.own, tb.dirdot, choice, wp, sz, occ, ctr);
+                                        g, beta, tb.own, tb.dirdot, choice, wp, sz, occ, ctr, ring);
 }
 
 // ------------------------------------------------------------ S4: vote

@@ -40,7 +40,7 @@ def test_library_exports_every_declared_entry_point(libpath):
 
 def test_binding_loads_and_reports_version(libpath):
     assert sfm.lib() is not None
-    assert sfm.sfm_abi_version() == 4
+    assert sfm.sfm_abi_version() == 5
 
 
 def test_struct_layouts_match_header(tmp_path):
@@ -105,7 +105,7 @@ def test_resident_bytes_and_band_budget():
     assert sfm.sfm_resident_bytes(lat) == 100 * 77 * 13 + 128 * 77
     lat = sfm.Lattice(16384, 16384, 0, 0)
     assert sfm.sfm_resident_bytes(lat) == 16384 * 16384 * 14
-    assert sfm.band_budget(16384, 16384, 4096) == 16384 * 16384 * 14 + 4 * 16384 * 4098
+    assert sfm.band_budget(16384, 16384, 4096) == 16384 * 16384 * 14 + 4 * 16384 * (4096 + 33)
 
 
 def test_snapshot_calls_reject_null_without_a_gpu():

@@ -363,17 +363,21 @@ def test_multi_su_placement_errors():
         assert sim.stats()["error_flags"] == 0
 
 
-@pytest.mark.parametrize("periodic,footprint,r", [(0, "32x16", 7), (1, "16x16", 7),
-                                                  (0, "32x32r", 20), (1, "32x32r", 16),
-                                                  (1, "32x32r", 9)])
-def test_banded_field_is_bitwise_the_unbanded_field(periodic, footprint, r):
+@pytest.mark.parametrize("periodic,footprint,r,rows", [(0, "32x16", 7, 64), (1, "16x16", 7, 64),
+                                                       (0, "32x32r", 20, 64), (1, "32x32r", 16, 64),
+                                                       (1, "32x32r", 9, 64), (0, "32x32r", 40, 32)])
+def test_banded_field_is_bitwise_the_unbanded_field(periodic, footprint, r, rows):
     """Divide-and-conquer (Eq. 1): row bands under an HBM budget give exactly
     the unbanded field and the same ticks, whatever the footprint (the band
-    halo rows fall inside footprints)."""
+    halo rows fall inside footprints).  With the row-trimmed footprint and y
+    not periodic the band buffer is a ring that each band's launch extends
+    by the next band's first 32 rows, here also with bands of 32 rows (the
+    upper halo row then comes from two bands back) and a last band shorter
+    than 32 rows (no launch of its own)."""
     sc = SG.random_scene(300, 260, 5000, r=r, seed=111, periodic_x=periodic, periodic_y=periodic,
                          ring=not periodic, exits=() if periodic else ("east",),
                          goal_mode="mixed", heading_mode="random")
-    budget = sfm.band_budget(sc.W, sc.H, 64)
+    budget = sfm.band_budget(sc.W, sc.H, rows)
     with sfm.Sim(sc) as a, sfm.Sim(sc, hbm_budget_bytes=budget) as b:
         b.set_footprint(footprint)
         assert b.stats()["bands"] >= 4
