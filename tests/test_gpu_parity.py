@@ -770,3 +770,46 @@ def test_empty_crowd_field_is_static_field():
         np.testing.assert_array_equal(sim.field(), sim.static_field())
         sim.step(2)
         assert sim.stats()["t"] == 2
+
+
+@pytest.mark.parametrize("variant", ["closed_banded", "closed", "torus", "periods_banded"])
+def test_sparse_crowd_ticks_follow_the_oracle(variant):
+    """A crowd under one pedestrian per 64 su, like the 16384^2 floor's
+    (binned from the pedestrian list, few pedestrians a bin): every tick
+    follows the oracle's, with the row-trimmed footprint at r = 33, in 4 row
+    bands (the ring band buffer) or one, on a closed room with exits and on
+    a torus, with and without walk periods."""
+    periodic = variant == "torus"
+    sc = SG.random_scene(640, 512, 2000, r=33, seed=171, obstacles=0 if periodic else 5,
+                         periodic_x=int(periodic), periodic_y=int(periodic), ring=not periodic,
+                         exits=() if periodic else ("east", "north", "south"), exit_len=40,
+                         goal_mode="mixed", heading_mode="random")
+    assert sc.n * 64 < sc.W * sc.H
+    banded = variant.endswith("banded")
+    orc = OracleRun(sc)
+    period = phase = None
+    if variant.startswith("periods"):
+        rng = np.random.default_rng(17)
+        period = rng.integers(1, 4, size=sc.n).astype(np.uint8)
+        phase = (rng.integers(0, 255, size=sc.n) % period).astype(np.uint8)
+        orc.st.period, orc.st.phase = period, phase
+    budget = sfm.band_budget(sc.W, sc.H, 128) if banded else 0
+    with sfm.Sim(sc, hbm_budget_bytes=budget) as sim:
+        assert (sim.stats()["bands"] == 4) == banded
+        sim.set_footprint("32x32r")
+        if period is not None:
+            sim.set_walk_periods(period, phase)
+        for t in range(8):
+            sim.step(1)
+            Fo, So = orc.field()
+            ch_o, E, T, adm = orc.decide(Ffull=Fo.ravel(), Sfull=So.ravel())
+            if period is not None:
+                ch_o = O.gate_periods(orc.st.t, period, phase, ch_o)
+            ch_g, won_g = sim.decisions()
+            assert compare_choices(ch_g, ch_o, E, T, adm) == 0, f"tie flip at tick {t}"
+            won_o, _ = orc.advance(ch_o)
+            np.testing.assert_array_equal(won_g, won_o)
+            for x, y in zip(sim.peds(), (orc.st.xy, orc.st.heading, orc.st.alive)):
+                np.testing.assert_array_equal(x, y)
+        assert sim.stats()["exited"] == orc.st.exited
+        assert sim.stats()["error_flags"] == 0
