@@ -128,8 +128,10 @@ def pair_count(sc, xy, alive) -> int:
 
 
 class Clocks:
-    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
-    Q = ("index,uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region:
+    samples every 100 ms, of which those stamped between region_begin() and
+    region_end() are kept (all of them, said so, when none falls inside)."""
+    Q = ("timestamp,index,uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -137,6 +139,13 @@ class Clocks:
         self.uuid = uuid
         self.proc = None
         self.path = None
+        self.t0 = self.t1 = None
+
+    def region_begin(self):
+        self.t0 = time.time()
+
+    def region_end(self):
+        self.t1 = time.time()
 
     def start(self):
         fd, self.path = tempfile.mkstemp(suffix=".csv")
@@ -144,7 +153,7 @@ class Clocks:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
 
@@ -156,29 +165,49 @@ class Clocks:
             self.proc.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
-        rows = []
+        rows, stamps = [], []
         for line in open(self.path):
             f = [c.strip() for c in line.split(",")]
-            if len(f) < 10:
+            if len(f) < 11:
                 continue
-            if self.uuid and self.uuid not in f[1]:
+            if self.uuid and self.uuid not in f[2]:
                 continue
-            rows.append(f)
+            stamps.append(sample_time(f[0]))
+            rows.append(f[1:])
         os.unlink(self.path)
         if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
         if not self.uuid:
             idx = rows[0][0]
-            rows = [r for r in rows if r[0] == idx]
+            keep = [i for i, r in enumerate(rows) if r[0] == idx]
+            rows, stamps = [rows[i] for i in keep], [stamps[i] for i in keep]
+        inside = [i for i, t in enumerate(stamps)
+                  if t is not None and self.t0 is not None and self.t1 is not None
+                  and self.t0 - 0.05 <= t <= self.t1 + 0.05]
+        window = "timed region"
+        if inside:
+            rows = [rows[i] for i in inside]
+        else:
+            window = "whole sampling (no sample fell inside the timed region)"
         sm = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
         mx = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = sorted({names[i] for r in rows for i in range(4) if r[6 + i] == "Active"})
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
-                "samples": len(rows),
+                "samples": len(rows), "window": window,
                 "power_w_max": max(float(r[4]) for r in rows if r[4].replace(".", "").isdigit())
                 if any(r[4].replace(".", "").isdigit() for r in rows) else None}
+
+
+def sample_time(stamp: str):
+    """Seconds since the epoch of an nvidia-smi timestamp (local time,
+    "YYYY/MM/DD HH:MM:SS.mmm"), or None."""
+    import datetime
+    try:
+        return datetime.datetime.strptime(stamp, "%Y/%m/%d %H:%M:%S.%f").timestamp()
+    except ValueError:
+        return None
 
 
 def peaks():
@@ -509,10 +538,12 @@ def run_gpu(args):
     torch.cuda.synchronize()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
+    clocks.region_begin()
     ev0.record(stream)
     sim.step(args.steps)
     ev1.record(stream)
     torch.cuda.synchronize()
+    clocks.region_end()
     barrier()
     clk = clocks.stop()
     elapsed = ev0.elapsed_time(ev1) / 1e3
@@ -672,10 +703,12 @@ def run_batch(args):
         torch.cuda.synchronize()
         ev0 = torch.cuda.Event(enable_timing=True)
         ev1 = torch.cuda.Event(enable_timing=True)
+        clocks.region_begin()
         ev0.record(stream)
         bt.step(args.steps)
         ev1.record(stream)
         torch.cuda.synchronize()
+        clocks.region_end()
         clk = clocks.stop()
         bt.sync()
         elapsed = ev0.elapsed_time(ev1) / 1e3
@@ -1106,7 +1139,7 @@ def run_paper_sizes(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="floor",

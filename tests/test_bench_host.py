@@ -90,3 +90,41 @@ def test_reference_arm_reports_the_time_it_spent_and_the_same_config(capsys):
     assert abs(line["value"] - 50 * args.steps / cb["seconds_timed"]) < 1e-6 * line["value"]
     sc, desc = bench.workload("room")
     assert line["config"] == bench.workload_config(args, sc, desc)
+
+
+def test_clock_samples_are_kept_inside_the_timed_region(tmp_path):
+    """The clock record keeps the nvidia-smi samples stamped inside the timed
+    region (with 50 ms of slack), and falls back to all samples, saying so,
+    when none lies inside."""
+    import datetime
+    base = datetime.datetime(2026, 1, 2, 3, 4, 5)
+
+    def line(dt_ms, mhz, reason="Not Active"):
+        ts = (base + datetime.timedelta(milliseconds=dt_ms)).strftime("%Y/%m/%d %H:%M:%S.%f")[:-3]
+        return (f"{ts}, 0, GPU-abc, {mhz}, 2070, 300.0, 0x0, {reason}, Not Active, "
+                f"Not Active, Not Active\n")
+
+    t0 = base.timestamp()
+    c = bench.Clocks("GPU-abc")
+    c.path = str(tmp_path / "c.csv")
+    with open(c.path, "w") as f:
+        f.write(line(0, 900) + line(200, 2070) + line(300, 2070, "Active") + line(400, 2070)
+                + line(900, 1000))
+
+    class Done:
+        def terminate(self):
+            pass
+
+        def wait(self, timeout=None):
+            return 0
+
+    c.proc = Done()
+    c.t0, c.t1 = t0 + 0.15, t0 + 0.45
+    out = c.stop()
+    assert out["samples"] == 3 and out["window"] == "timed region"
+    assert out["sm_mhz"] == 2070.0 and out["reasons"] == ["hw_slowdown"]
+    c.path = str(tmp_path / "d.csv")
+    with open(c.path, "w") as f:
+        f.write(line(0, 900) + line(900, 1000))
+    out = c.stop()
+    assert out["samples"] == 2 and out["window"].startswith("whole sampling")
