@@ -200,6 +200,24 @@ class Clocks:
                 if any(r[4].replace(".", "").isdigit() for r in rows) else None}
 
 
+# consecutive chunks of the timed region, each timed on its own
+REPEATS = 5
+
+
+def chunk_sizes(steps: int, n: int):
+    """steps split into min(n, steps) consecutive chunks, sizes within one."""
+    n = max(1, min(n, steps))
+    return [steps // n + (1 if k < steps % n else 0) for k in range(n)]
+
+
+def repeat_record(chunks, ms):
+    """ms per tick of each chunk, their median and relative spread."""
+    per = [m / c for m, c in zip(ms, chunks)]
+    med = statistics.median(per)
+    return {"n": len(per), "ticks": chunks, "ms_per_step": per, "median_ms_per_step": med,
+            "spread": (max(per) - min(per)) / med if med > 0 else 0.0}
+
+
 def sample_time(stamp: str):
     """Seconds since the epoch of an nvidia-smi timestamp (local time,
     "YYYY/MM/DD HH:MM:SS.mmm"), or None."""
@@ -539,14 +557,21 @@ def run_gpu(args):
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     clocks.region_begin()
+    # the K ticks in REPEATS consecutive chunks, an event between chunks: the
+    # chunks give repeated measurements of the same loop (their median and
+    # spread); `value` is the whole region
+    chunks = chunk_sizes(args.steps, REPEATS)
+    evs = [ev0] + [torch.cuda.Event(enable_timing=True) for _ in chunks[:-1]] + [ev1]
     ev0.record(stream)
-    sim.step(args.steps)
-    ev1.record(stream)
+    for k, m in enumerate(chunks):
+        sim.step(m)
+        evs[k + 1].record(stream)
     torch.cuda.synchronize()
     clocks.region_end()
     barrier()
     clk = clocks.stop()
     elapsed = ev0.elapsed_time(ev1) / 1e3
+    repeats = repeat_record(chunks, [evs[k].elapsed_time(evs[k + 1]) for k in range(len(chunks))])
     stage_ms, ticks = sim.stage_times()
     sim.set_timing(False)
     st1 = sim.stats()
@@ -650,6 +675,7 @@ def run_gpu(args):
         "stage_timing": f"CUDA events around each stage of every {TIMING_EVERY}th tick of the "
                         f"timed region ({ticks} of {args.steps} ticks)",
         "graph_ms_per_step": graph_ms,
+        "repeats": repeats,
         "roofline": roofline,
         "cpu_baseline": cpu,
         "e2e": e2e,

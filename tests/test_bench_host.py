@@ -128,3 +128,12 @@ def test_clock_samples_are_kept_inside_the_timed_region(tmp_path):
         f.write(line(0, 900) + line(900, 1000))
     out = c.stop()
     assert out["samples"] == 2 and out["window"].startswith("whole sampling")
+
+
+def test_timed_region_chunks_and_their_median():
+    assert bench.chunk_sizes(400, 5) == [80] * 5
+    assert bench.chunk_sizes(23, 5) == [5, 5, 5, 4, 4]
+    assert bench.chunk_sizes(3, 5) == [1, 1, 1]
+    r = bench.repeat_record([2, 2, 1], [4.0, 5.0, 1.5])
+    assert r["ms_per_step"] == [2.0, 2.5, 1.5] and r["median_ms_per_step"] == 2.0
+    assert abs(r["spread"] - 0.5) < 1e-12 and r["n"] == 3
