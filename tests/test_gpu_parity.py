@@ -827,3 +827,45 @@ def test_sparse_crowd_ticks_follow_the_oracle(variant):
         assert sim.stats()["exited"] == orc.st.exited
         assert sim.stats()["error_flags"] == 0
         assert flips <= 2, f"{flips} tie flips in 8 ticks"
+
+
+def test_clustered_crowd_under_the_ticket_schedule_keeps_the_field_and_ticks():
+    """A sparse crowd with one dense cluster, on a lattice large enough for
+    the row-trimmed gather's schedule of dealt rounds and tickets (4608^2 su,
+    r = 40, footprints of very uneven cost): the field and the ticks are
+    bit-identical to the 16x16 gather's, unbanded and in 4 bands (a
+    footprint the schedule missed or took twice would show)."""
+    W = H = 4608
+    base = SG.random_scene(W, H, 70000, r=40, seed=181, exits=("east", "west"), exit_len=64,
+                           goal_mode="mixed", heading_mode="random")
+    x0, y0, side = 2200, 2300, 150
+    rng = np.random.default_rng(182)
+    inside = ((base.xy[:, 0] >= x0) & (base.xy[:, 0] < x0 + side) &
+              (base.xy[:, 1] >= y0) & (base.xy[:, 1] < y0 + side))
+    ys, xs = np.nonzero(base.cell[y0:y0 + side, x0:x0 + side] == SG.FREE)
+    pick = rng.random(ys.size) < 0.6
+    cl = np.stack([xs[pick] + x0, ys[pick] + y0], axis=1).astype(np.int32)
+    xy = np.concatenate([base.xy[~inside], cl]).astype(np.int32)
+    n = xy.shape[0]
+    sc = SG.Scene("cluster", W, H, 0, 0, base.cell, xy,
+                  rng.integers(0, 9, n).astype(np.uint8),
+                  np.where(rng.random(n) < 0.5, 0, rng.integers(1, 9, n)).astype(np.uint8),
+                  base.params)
+    assert cl.shape[0] > 10000
+    budget = sfm.band_budget(W, H, H // 4)
+    with sfm.Sim(sc) as a, sfm.Sim(sc) as b, sfm.Sim(sc, hbm_budget_bytes=budget) as c:
+        a.set_footprint("16x16")
+        b.set_footprint("32x32r")
+        c.set_footprint("32x32r")
+        assert c.stats()["bands"] == 4
+        for _ in range(3):
+            for s in (a, b, c):
+                s.step(1)
+            # the field of the tick just taken
+            np.testing.assert_array_equal(a.field(), b.field())
+            for s in (b, c):
+                np.testing.assert_array_equal(a.decisions()[0], s.decisions()[0])
+                for x, y in zip(a.peds(), s.peds()):
+                    np.testing.assert_array_equal(x, y)
+        for s in (a, b, c):
+            assert s.stats()["error_flags"] == 0
