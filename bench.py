@@ -255,9 +255,9 @@ def gather_roofline(pairs, field_s, nsm, mhz, mhz_src, kernel, traffic=None):
     """Roofline of the class-table field gather for `pairs` (su, pedestrian)
     pairs computed in `field_s` seconds.  Each pair costs one table word read
     from shared memory, and the shared-memory pipe (32 banks x 4 bytes per
-    clock per SM) is the resource that binds it; the survey's algorithmic
-    FP32 figure (6 flops per pair) and the FP32 actually executed (1 add per
-    pair) are given beside it."""
+    clock per SM) is the resource that binds it; the algorithmic FP32 figure
+    of the 3-channel kernel-table formulation (6 flops per pair) and the FP32
+    actually executed (1 add per pair) are given beside it."""
     words = pairs / field_s
     smem_peak = nsm * SMEM_WORDS * mhz * 1e6
     fp32_peak = nsm * FP32_LANES * 2 * mhz * 1e6
