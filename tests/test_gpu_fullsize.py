@@ -119,6 +119,27 @@ def test_floor_16384_full_size_ticks_against_the_oracle():
             assert s["alive"] + s["exited"] == sc.n
 
 
+def test_floor_8192_bands_equal_one_launch_over_200_ticks():
+    """The 8192^2 floor (250 000 exit-seekers, r = 40) for 200 ticks: in 4
+    row bands (the ring band buffer) and in one launch a tick, with the
+    row-trimmed gather's dealt rounds and tickets, the crowd's positions,
+    headings and decisions stay bit-identical at every 25th tick while the
+    crowd gathers at the exits (footprints of ever more uneven cost)."""
+    sc, _ = bench.workload("floor-mid")
+    with sfm.Sim(sc, hbm_budget_bytes=bench.band_budget(sc, 4)) as a, sfm.Sim(sc) as b:
+        assert a.stats()["bands"] == 4 and b.stats()["bands"] == 1
+        for s in (a, b):
+            s.set_footprint("32x32r")
+        for _ in range(8):
+            a.step(25)
+            b.step(25)
+            np.testing.assert_array_equal(a.decisions()[0], b.decisions()[0])
+            for x, y in zip(a.peds(), b.peds()):
+                np.testing.assert_array_equal(x, y)
+        assert a.stats()["exited"] == b.stats()["exited"] > 0
+        assert a.stats()["error_flags"] == 0 and b.stats()["error_flags"] == 0
+
+
 def test_corridor_full_size_ticks_against_the_oracle():
     sc, sim = _bench_sim("corridor")
     with sim:
