@@ -374,7 +374,8 @@ def test_multi_su_placement_errors():
 
 @pytest.mark.parametrize("periodic,footprint,r,rows", [(0, "32x16", 7, 64), (1, "16x16", 7, 64),
                                                        (0, "32x32r", 20, 64), (1, "32x32r", 16, 64),
-                                                       (1, "32x32r", 9, 64), (0, "32x32r", 40, 32)])
+                                                       (1, "32x32r", 9, 64), (0, "32x32r", 40, 32),
+                                                       ("x", "32x32r", 36, 64)])
 def test_banded_field_is_bitwise_the_unbanded_field(periodic, footprint, r, rows):
     """Divide-and-conquer (Eq. 1): row bands under an HBM budget give exactly
     the unbanded field and the same ticks, whatever the footprint (the band
@@ -382,9 +383,11 @@ def test_banded_field_is_bitwise_the_unbanded_field(periodic, footprint, r, rows
     not periodic the band buffer is a ring that each band's launch extends
     by the next band's first 32 rows, here also with bands of 32 rows (the
     upper halo row then comes from two bands back) and a last band shorter
-    than 32 rows (no launch of its own)."""
-    sc = SG.random_scene(300, 260, 5000, r=r, seed=111, periodic_x=periodic, periodic_y=periodic,
-                         ring=not periodic, exits=() if periodic else ("east",),
+    than 32 rows (no launch of its own), and periodic in x only (a
+    corridor-like lattice: the ring with wrapped columns)."""
+    px, py = (1, 0) if periodic == "x" else (periodic, periodic)
+    sc = SG.random_scene(300, 260, 5000, r=r, seed=111, periodic_x=px, periodic_y=py,
+                         ring=not (px or py), exits=() if (px or py) else ("east",),
                          goal_mode="mixed", heading_mode="random")
     budget = sfm.band_budget(sc.W, sc.H, rows)
     with sfm.Sim(sc) as a, sfm.Sim(sc, hbm_budget_bytes=budget) as b:
