@@ -29,8 +29,8 @@ bands, are the whole lattice's (sfm_set_guidance); the election numbers are
 the whole lattice's pedestrian numbers (sfm_set_ids).
 
 The exchange goes through a `comm` object with exchange(sends) -> receives
-(`TorchComm` on torch.distributed point-to-point sends; the gloo backend
-moves host tensors).  Walk periods and multi-su pedestrians are not
+(`TorchComm` on torch.distributed point-to-point sends: host tensors with
+the gloo backend, device tensors with NCCL).  Walk periods and multi-su pedestrians are not
 carried.
 """
 from __future__ import annotations
@@ -162,27 +162,33 @@ def sends_of(layout: BandLayout, k: int, own: Peds) -> Dict[int, Peds]:
 
 class TorchComm:
     """Neighbour exchange over torch.distributed point-to-point messages: a
-    count, then the packed pedestrians.  Host tensors (gloo)."""
+    count, then the packed pedestrians.  The messages are tensors on
+    `device`: host tensors for the gloo backend (the default), CUDA tensors
+    of the rank's device for NCCL."""
 
-    def __init__(self, dist):
+    def __init__(self, dist, device="cpu"):
         self.dist = dist
+        self.device = device
 
     def exchange(self, sends: Dict[int, np.ndarray]) -> Dict[int, np.ndarray]:
         import torch
-        d = self.dist
-        counts = {j: torch.tensor([a.shape[0]], dtype=torch.int64) for j, a in sends.items()}
-        rcounts = {j: torch.zeros(1, dtype=torch.int64) for j in sends}
+        d, dev = self.dist, self.device
+        counts = {j: torch.tensor([a.shape[0]], dtype=torch.int64, device=dev)
+                  for j, a in sends.items()}
+        rcounts = {j: torch.zeros(1, dtype=torch.int64, device=dev) for j in sends}
         reqs = [d.irecv(rcounts[j], src=j) for j in sends]
         reqs += [d.isend(counts[j], dst=j) for j in sends]
         for q in reqs:
             q.wait()
-        bufs = {j: torch.zeros((int(rcounts[j].item()), 5), dtype=torch.int32) for j in sends}
-        data = {j: torch.from_numpy(np.ascontiguousarray(a, np.int32).reshape(-1, 5)) for j, a in sends.items()}
+        bufs = {j: torch.zeros((int(rcounts[j].item()), 5), dtype=torch.int32, device=dev)
+                for j in sends}
+        data = {j: torch.from_numpy(np.ascontiguousarray(a, np.int32).reshape(-1, 5)).to(dev)
+                for j, a in sends.items()}
         reqs = [d.irecv(bufs[j], src=j) for j in sends if bufs[j].numel()]
         reqs += [d.isend(data[j], dst=j) for j in sends if data[j].numel()]
         for q in reqs:
             q.wait()
-        return {j: bufs[j].numpy() for j in sends}
+        return {j: bufs[j].cpu().numpy() for j in sends}
 
 
 # a stepper advances the placed pedestrians of a sub-lattice by one tick:
