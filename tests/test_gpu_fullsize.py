@@ -69,7 +69,8 @@ def _edge_rows(H, rows_per_band):
 
 def test_floor_16384_full_size_ticks_against_the_oracle():
     """Checked at ticks 0 (run stage by stage, the first after the
-    placement), 6 and 60 (replayed from graphs)."""
+    placement), 6, 60 and 200 (replayed from graphs; by tick 200, the
+    workload's run length, the crowd has gathered at the exits)."""
     sc, sim = _bench_sim("floor", warm=0)
     with sim:
         st = sim.stats()
@@ -84,7 +85,7 @@ def test_floor_16384_full_size_ticks_against_the_oracle():
         edges = _edge_rows(H, band_rows)
         exits = np.flatnonzero(sc.cell.ravel() == SG.EXIT)
         done = 0
-        for tick in (0, WARM_TICKS, 60):
+        for tick in (0, WARM_TICKS, 60, 200):
             if tick > done:
                 sim.step(tick - done)
             xy, hd, al = sim.peds()
