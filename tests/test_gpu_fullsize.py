@@ -142,6 +142,9 @@ def test_floor_8192_bands_equal_one_launch_over_200_ticks():
 
 
 def test_corridor_full_size_ticks_against_the_oracle():
+    """Two replayed ticks after the warm-up, then two at tick 500 (the
+    configuration's run length, the counter-flow jammed): the whole field,
+    every decision, and the exact vote and commit."""
     sc, sim = _bench_sim("corridor")
     with sim:
         st = sim.stats()
@@ -149,7 +152,9 @@ def test_corridor_full_size_ticks_against_the_oracle():
         m = O.model(sc)
         D = O.guidance(m, sc.cell)
         flips = 0
-        for _ in range(2):
+        for k in range(4):
+            if k == 2:
+                sim.step(500 - sim.stats()["t"])
             xy, hd, al = sim.peds()
             t = sim.stats()["t"]
             F = sim.field_banded()
@@ -165,7 +170,7 @@ def test_corridor_full_size_ticks_against_the_oracle():
             flips += compare_choices(ch, ch_o, E, T, adm)
             _check_vote_and_commit(m, sc, t, xy, hd, al, ch, won, after)
             assert int(after[2].sum()) == sc.n  # periodic in x, no exits: nobody leaves
-        assert flips <= 3, f"{flips} tie flips"
+        assert flips <= 6, f"{flips} tie flips"
 
 
 def test_batch_of_256_rooms_full_size_tick_against_the_oracle():
